@@ -1,0 +1,300 @@
+"""FP64 CPU oracle for the Deep Gaussian Shadow Map hot path.
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the
+benchmark's CPU-baseline leg are the only code that may import this package.
+The product path (paper_2601_01660_b300) never imports it, and it never
+imports the product path: both take their inputs from the seeded generators
+in paper_2601_01660_b300.scenes, which hold none of the method's arithmetic.
+
+The arithmetic lives in dgsm_oracle.c (plain C, FP64, OpenMP), one function
+per equation of the paper; this module only marshals numpy arrays.
+
+Pinned by tests/test_oracle_*.py (quadrature of Eq. 2, the isotropic closed
+form of Eqs. 3+5, empty scene, bounds and monotonicity of T, octahedral round
+trip, SH orthonormality against scipy, exact recovery of band-limited
+signals, the clamped-cosine irradiance limit of Eq. 10).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        _lib = C.CDLL(path)
+        _declare(_lib)
+    return _lib
+
+
+_f = C.POINTER(C.c_float)
+_d = C.POINTER(C.c_double)
+_i32 = C.POINTER(C.c_int32)
+_u32 = C.POINTER(C.c_uint32)
+I64 = C.c_int64
+
+
+def _declare(L):
+    L.orc_num_threads.restype = C.c_int
+    L.orc_beta.restype = C.c_double
+    L.orc_beta.argtypes = [_f, C.c_float, C.c_double]
+    L.orc_line_integral.restype = C.c_double
+    L.orc_line_integral.argtypes = [C.c_double] * 4
+    L.orc_precision.argtypes = [_f, _f, _d]
+    L.orc_quat_to_rot.argtypes = [_f, _d]
+    L.orc_ray_coeffs.argtypes = [_d, _d, _d, _d, _d, _d]
+    L.orc_octa_encode.argtypes = [_d, _d, _d]
+    L.orc_octa_decode.argtypes = [C.c_double, C.c_double, _d]
+    L.orc_texel_dir.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _d]
+    L.orc_build_tau.argtypes = [_f, _f, _f, _f, I64, _f, C.c_int, C.c_int, C.c_int, _f,
+                                C.c_int, C.c_double, _d]
+    L.orc_build_tau_texels.argtypes = [_f, _f, _f, _f, I64, _f, C.c_int, C.c_int, _f, C.c_int,
+                                       C.c_double, _i32, I64, _d]
+    L.orc_tau_rays.argtypes = [_f, _f, _f, _f, I64, _d, _d, _d, I64, C.c_double, _d]
+    L.orc_sample_T.restype = C.c_double
+    L.orc_sample_T.argtypes = [_d, C.c_int, C.c_int, _f, C.c_int, _d, _d]
+    L.orc_attenuate.argtypes = [_d, _d, C.c_int, C.c_int, C.c_int, _f, C.c_int, _f, _f, _f, I64,
+                                _f, C.c_double, _d, _d]
+    L.orc_f32_sample_index_batch.argtypes = [_f, I64, _f, C.c_int, C.c_int, _f, C.c_int, _i32, _f]
+    L.orc_f32_rect_cone.argtypes = [C.c_int] * 6 + [_f]
+    L.orc_f32_gauss_cone.restype = C.c_int
+    L.orc_f32_gauss_cone.argtypes = [_f, _f, C.c_float, _f, C.c_float, C.c_float, C.c_float, _f]
+    L.orc_f32_bin.restype = I64
+    L.orc_f32_bin.argtypes = [_f, _f, _f, I64, _f, C.c_int, C.c_int, C.c_int, _f, C.c_int,
+                              C.c_float, C.c_float, C.c_int, _u32, _u32, I64]
+    L.orc_sh_basis.argtypes = [_d, _d]
+    L.orc_sh_fit.restype = C.c_int
+    L.orc_sh_fit.argtypes = [_f, _f, _f, I64, C.c_double, _d]
+    L.orc_gauss_normal.argtypes = [_f, _f, _f, _f, _d]
+    L.orc_transfer_scale.argtypes = [_d, _d, C.c_double, C.c_double, C.c_double, C.c_int,
+                                     C.c_int, _d]
+    L.orc_relight.argtypes = [_d, _f, _f, _f, _f, _f, _f, I64, C.c_double, C.c_double,
+                              C.c_double, C.c_double, C.c_int, C.c_int, _d]
+
+
+def _pf(a):
+    return a.ctypes.data_as(_f) if a is not None else None
+
+
+def _pd(a):
+    return a.ctypes.data_as(_d) if a is not None else None
+
+
+def _c32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+# --- Gaussian parameters (Sec. 3.2, Eq. 5) --------------------------------
+
+def precision(scale, quat) -> np.ndarray:
+    A = np.zeros(9)
+    lib().orc_precision(_pf(_c32(scale)), _pf(_c32(quat)), _pd(A))
+    return A.reshape(3, 3)
+
+
+def rotation(quat) -> np.ndarray:
+    R = np.zeros(9)
+    lib().orc_quat_to_rot(_pf(_c32(quat)), _pd(R))
+    return R.reshape(3, 3)
+
+
+def beta(scale, alpha: float, kappa: float = 1.0) -> float:
+    return float(lib().orc_beta(_pf(_c32(scale)), float(alpha), float(kappa)))
+
+
+def ray_coeffs(A, d, o_minus_mu):
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    lib().orc_ray_coeffs(_pd(_c64(A)), _pd(_c64(d)), _pd(_c64(o_minus_mu)),
+                         C.byref(a), C.byref(b), C.byref(c))
+    return a.value, b.value, c.value
+
+
+def line_integral(a, b, c, t) -> float:
+    """Eq. 3 (three-case erfc form)."""
+    return float(lib().orc_line_integral(float(a), float(b), float(c), float(t)))
+
+
+# --- octahedral map (Eq. 6) -------------------------------------------------
+
+def octa_encode(d):
+    u, v = C.c_double(), C.c_double()
+    lib().orc_octa_encode(_pd(_c64(d)), C.byref(u), C.byref(v))
+    return u.value, v.value
+
+
+def octa_decode(u, v) -> np.ndarray:
+    d = np.zeros(3)
+    lib().orc_octa_decode(float(u), float(v), _pd(d))
+    return d
+
+
+def texel_dir(i, j, H, W) -> np.ndarray:
+    d = np.zeros(3)
+    lib().orc_texel_dir(int(i), int(j), int(H), int(W), _pd(d))
+    return d
+
+
+# --- DGSM build (Eqs. 1-5), brute force -------------------------------------
+
+def build_tau(sc, lights, H, W, radii, kappa=1.0) -> np.ndarray:
+    """tau[L][K][H][W] summed over every Gaussian (no culling)."""
+    lights = _c32(lights).reshape(-1, 3)
+    radii = _c32(radii)
+    L, K = lights.shape[0], radii.shape[0]
+    assert K <= 512
+    out = np.zeros((L, K, H, W))
+    lib().orc_build_tau(_pf(sc.means), _pf(sc.scales), _pf(sc.quats), _pf(sc.opac), sc.n,
+                        _pf(lights), L, H, W, _pf(radii), K, float(kappa), _pd(out))
+    return out
+
+
+def build_atlas(sc, lights, H, W, radii, kappa=1.0) -> np.ndarray:
+    """Eq. 4: T = exp(-tau), FP64, [L][K][H][W]."""
+    return np.exp(-build_tau(sc, lights, H, W, radii, kappa))
+
+
+def build_tau_texels(sc, lights, H, W, radii, lij, kappa=1.0) -> np.ndarray:
+    """tau at the texels lij = [(l,i,j), ...] for all shells: (n, K)."""
+    lights = _c32(lights).reshape(-1, 3)
+    radii = _c32(radii)
+    lij = np.ascontiguousarray(lij, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros((lij.shape[0], radii.shape[0]))
+    lib().orc_build_tau_texels(_pf(sc.means), _pf(sc.scales), _pf(sc.quats), _pf(sc.opac), sc.n,
+                               _pf(lights), H, W, _pf(radii), radii.shape[0], float(kappa),
+                               lij.ctypes.data_as(_i32), lij.shape[0], _pd(out))
+    return out
+
+
+def tau_rays(sc, origins, dirs, t, kappa=1.0) -> np.ndarray:
+    origins = _c64(origins).reshape(-1, 3)
+    dirs = _c64(dirs).reshape(-1, 3)
+    t = _c64(t).ravel()
+    out = np.zeros(t.shape[0])
+    lib().orc_tau_rays(_pf(sc.means), _pf(sc.scales), _pf(sc.quats), _pf(sc.opac), sc.n,
+                       _pd(origins), _pd(dirs), _pd(t), t.shape[0], float(kappa), _pd(out))
+    return out
+
+
+# --- sampling / attenuation (Sec. 3.3) ---------------------------------------
+
+def sample_T(atlas_l, radii, o, x) -> float:
+    atlas_l = _c64(atlas_l)
+    K, H, W = atlas_l.shape
+    return float(lib().orc_sample_T(_pd(atlas_l), H, W, _pf(_c32(radii)), K, _pd(_c64(o)),
+                                    _pd(_c64(x))))
+
+
+def attenuate(atlas, radii, lights, q_means, colors, atlas_dyn=None, light_w=None,
+              direct_frac=1.0, want_T=False):
+    atlas = _c64(atlas)
+    L, K, H, W = atlas.shape
+    q_means = _c32(q_means)
+    colors = _c32(colors)
+    Q = q_means.shape[0]
+    out = np.zeros((Q, 3))
+    T = np.zeros((Q, L)) if want_T else None
+    dyn = _c64(atlas_dyn) if atlas_dyn is not None else None
+    lw = _c32(light_w) if light_w is not None else None
+    lib().orc_attenuate(_pd(atlas), _pd(dyn), L, H, W, _pf(_c32(radii)), K, _pf(_c32(lights)),
+                        _pf(q_means), _pf(colors), Q, _pf(lw), float(direct_frac), _pd(out), _pd(T))
+    return (out, T) if want_T else out
+
+
+# --- FP32 index and binning specification -----------------------------------
+
+def f32_sample_index(points, light, H, W, radii):
+    """(ints (n,5): cell i, cell j, base i0, base j0, shell k; floats (n,3): fy, fx, t)."""
+    points = _c32(points).reshape(-1, 3)
+    n = points.shape[0]
+    oi = np.zeros((n, 5), dtype=np.int32)
+    of = np.zeros((n, 3), dtype=np.float32)
+    radii = _c32(radii)
+    lib().orc_f32_sample_index_batch(_pf(points), n, _pf(_c32(light)), H, W, _pf(radii),
+                                     radii.shape[0], oi.ctypes.data_as(_i32), _pf(of))
+    return oi, of
+
+
+def f32_rect_cone(i0, i1, j0, j1, H, W) -> np.ndarray:
+    out = np.zeros(6, dtype=np.float32)
+    lib().orc_f32_rect_cone(i0, i1, j0, j1, H, W, _pf(out))
+    return out
+
+
+def f32_gauss_cone(mu, s, alpha, o, kappa, eps, r_last):
+    out = np.zeros(9, dtype=np.float32)
+    r = lib().orc_f32_gauss_cone(_pf(_c32(mu)), _pf(_c32(s)), float(alpha), _pf(_c32(o)),
+                                 float(kappa), float(eps), float(r_last), _pf(out))
+    return r, out
+
+
+def f32_bin(sc, lights, H, W, radii, kappa=1.0, eps=1e-7, tile=8):
+    """Sorted (key, value) pairs of the binning specification."""
+    lights = _c32(lights).reshape(-1, 3)
+    radii = _c32(radii)
+    args = (_pf(sc.means), _pf(sc.scales), _pf(sc.opac), sc.n, _pf(lights), lights.shape[0],
+            H, W, _pf(radii), radii.shape[0], float(kappa), float(eps), int(tile))
+    empty = np.zeros(1, dtype=np.uint32)
+    total = lib().orc_f32_bin(*args, empty.ctypes.data_as(_u32), empty.ctypes.data_as(_u32), 0)
+    if total < 0:
+        raise ValueError("invalid Gaussian input")
+    keys = np.zeros(max(total, 1), dtype=np.uint32)
+    vals = np.zeros(max(total, 1), dtype=np.uint32)
+    lib().orc_f32_bin(*args, keys.ctypes.data_as(_u32), vals.ctypes.data_as(_u32), total)
+    return keys[:total], vals[:total]
+
+
+# --- HDRI probe and transfer (Secs. 3.4-3.5) ---------------------------------
+
+def sh_basis(d) -> np.ndarray:
+    Y = np.zeros(9)
+    lib().orc_sh_basis(_pd(_c64(d)), _pd(Y))
+    return Y
+
+
+def sh_fit(dirs, rgb, w, lam=1e-3) -> np.ndarray:
+    """Eq. 7 ridge fit; returns SH (3, 9)."""
+    dirs, rgb, w = _c32(dirs), _c32(rgb), _c32(w)
+    out = np.zeros(27)
+    rc = lib().orc_sh_fit(_pf(dirs), _pf(rgb), _pf(w), dirs.shape[0], float(lam), _pd(out))
+    if rc != 0:
+        raise np.linalg.LinAlgError("normal equations not positive definite")
+    return out.reshape(3, 9)
+
+
+def gauss_normal(mu, s, q, centroid) -> np.ndarray:
+    n = np.zeros(3)
+    lib().orc_gauss_normal(_pf(_c32(mu)), _pf(_c32(s)), _pf(_c32(q)), _pf(_c32(centroid)), _pd(n))
+    return n
+
+
+def transfer_scale(sh, n, q=1.0, t_max=10.0, eps=1e-8, n_theta=32, n_phi=64) -> np.ndarray:
+    out = np.zeros(3)
+    lib().orc_transfer_scale(_pd(_c64(sh)), _pd(_c64(n)), float(q), float(t_max), float(eps),
+                             n_theta, n_phi, _pd(out))
+    return out
+
+
+def relight(sh, sc, centroid, normals=None, q=1.0, gamma=1.0, t_max=10.0, eps=1e-8,
+            n_theta=32, n_phi=64) -> np.ndarray:
+    out = np.zeros((sc.n, 3))
+    nrm = _c32(normals) if normals is not None else None
+    lib().orc_relight(_pd(_c64(sh)), _pf(sc.means), _pf(sc.quats), _pf(sc.scales), _pf(nrm),
+                      _pf(_c32(centroid)), _pf(sc.colors), sc.n, float(q), float(gamma),
+                      float(t_max), float(eps), n_theta, n_phi, _pd(out))
+    return out

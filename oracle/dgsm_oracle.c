@@ -1,0 +1,708 @@
+/*
+ * dgsm_oracle.c -- plain, slow, FP64 CPU oracle for the Deep Gaussian Shadow
+ * Map hot path (Sec. 3.2-3.5 of "Animated 3DGS Avatars in Diverse Scenes with
+ * Consistent Lighting and Shadows").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or constant generator with the CUDA library; both sides only
+ * take the same seeded inputs.
+ *
+ * Every floating-point quantity below is FP64 unless the function name says
+ * f32: those few functions write out, in single precision with IEEE-rounded
+ * operations in a fixed order, the integer decisions (texel, shell and tile
+ * indices) that must come out bit-identical on the GPU.  This file must be
+ * compiled without FMA contraction (-ffp-contract=off) and without
+ * -ffast-math.
+ *
+ * Conventions (the paper leaves them open; the readings are ours):
+ *   quaternion q = (w,x,y,z), normalised; R(q) the usual rotation matrix;
+ *   Sigma = R diag(s^2) R^T with linear scales s; A = Sigma^-1.
+ *   Atlas layout [L][K][H][W]; row i <-> v, column j <-> u; texel centres
+ *   u_j = (2j+1)/W - 1, v_i = (2i+1)/H - 1; shell k holds T at t = r_k.
+ *   sgn(0) = +1 in the octahedral fold.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+#define ALPHA_MAX 0.999999  /* opacity clamp before tau* = -ln(1-alpha) */
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gaussian parameters (Sec. 3.2, problem statement and Eq. 5)               */
+/* ------------------------------------------------------------------------ */
+
+/* R(q) for q = (w,x,y,z); the quaternion is normalised first. */
+void orc_quat_to_rot(const float *qf, double R[9]) {
+    double w = qf[0], x = qf[1], y = qf[2], z = qf[3];
+    double n = sqrt(w * w + x * x + y * y + z * z);
+    w /= n; x /= n; y /= n; z /= n;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* Precision A = Sigma^{-1} = R diag(1/s^2) R^T (Sec. 3.2). */
+void orc_precision(const float *s, const float *q, double A[9]) {
+    double R[9];
+    orc_quat_to_rot(q, R);
+    double inv[3] = {1.0 / ((double)s[0] * s[0]), 1.0 / ((double)s[1] * s[1]),
+                     1.0 / ((double)s[2] * s[2])};
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double acc = 0;
+            for (int k = 0; k < 3; ++k) acc += R[3 * r + k] * inv[k] * R[3 * c + k];
+            A[3 * r + c] = acc;
+        }
+}
+
+/* Eq. 5: tau* = -ln(1-alpha), beta = kappa tau* sqrt(tr(A)/3) / sqrt(2 pi). */
+double orc_beta(const float *s, float alpha, double kappa) {
+    double a = alpha;
+    if (!(a > 0)) return 0.0;
+    if (a > ALPHA_MAX) a = ALPHA_MAX;
+    double tau_star = -log1p(-a);
+    double trA = 1.0 / ((double)s[0] * s[0]) + 1.0 / ((double)s[1] * s[1]) +
+                 1.0 / ((double)s[2] * s[2]);
+    return kappa * tau_star * sqrt(trA / 3.0) / sqrt(2.0 * ORC_PI);
+}
+
+/* Eq. 2 coefficients for the ray o + s d: a = d^T A d, b = d^T A (o-mu),
+ * c = (o-mu)^T A (o-mu). */
+void orc_ray_coeffs(const double A[9], const double *d, const double *o_minus_mu,
+                    double *a, double *b, double *c) {
+    double Ad[3], Aw[3];
+    for (int r = 0; r < 3; ++r) {
+        Ad[r] = A[3 * r] * d[0] + A[3 * r + 1] * d[1] + A[3 * r + 2] * d[2];
+        Aw[r] = A[3 * r] * o_minus_mu[0] + A[3 * r + 1] * o_minus_mu[1] + A[3 * r + 2] * o_minus_mu[2];
+    }
+    *a = d[0] * Ad[0] + d[1] * Ad[1] + d[2] * Ad[2];
+    *b = d[0] * Aw[0] + d[1] * Aw[1] + d[2] * Aw[2];
+    *c = o_minus_mu[0] * Aw[0] + o_minus_mu[1] * Aw[1] + o_minus_mu[2] * Aw[2];
+}
+
+/* Eq. 3: int_0^t exp(-1/2 (a s^2 + 2 b s + c)) ds
+ *   = sqrt(pi/(2a)) exp(-1/2 (c - b^2/a)) [erf(sqrt(a/2)(t + b/a)) - erf(sqrt(a/2) b/a)].
+ * The erf difference is written with erfc so that it does not cancel when
+ * both arguments lie far out on the same side. */
+double orc_line_integral(double a, double b, double c, double t) {
+    double m2 = c - b * b / a;
+    if (m2 < 0) m2 = 0;  /* c - b^2/a >= 0 for positive definite A; rounding only */
+    double pref = sqrt(ORC_PI / (2.0 * a)) * exp(-0.5 * m2);
+    double h = sqrt(a / 2.0);
+    double x0 = h * (b / a);
+    double xt = h * (t + b / a);
+    double diff;
+    if (x0 >= 0)
+        diff = erfc(x0) - erfc(xt);
+    else if (xt <= 0)
+        diff = erfc(-xt) - erfc(-x0);
+    else
+        diff = 2.0 - erfc(xt) - erfc(-x0);
+    return pref * diff;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Octahedral map (Eq. 6 and its inverse, Sec. 3.2)                          */
+/* ------------------------------------------------------------------------ */
+
+static double sgn_pos(double x) { return x >= 0 ? 1.0 : -1.0; }
+
+/* Eq. 6: q = d / (|x|+|y|+|z|); (u,v) = (qx,qy) if qz >= 0, else the fold. */
+void orc_octa_encode(const double *d, double *u, double *v) {
+    double l1 = fabs(d[0]) + fabs(d[1]) + fabs(d[2]);
+    double qx = d[0] / l1, qy = d[1] / l1, qz = d[2] / l1;
+    if (qz >= 0) {
+        *u = qx; *v = qy;
+    } else {
+        *u = sgn_pos(qx) * (1.0 - fabs(qy));
+        *v = sgn_pos(qy) * (1.0 - fabs(qx));
+    }
+}
+
+/* Inverse: undo the fold, z = 1 - |u| - |v|, normalise. */
+void orc_octa_decode(double u, double v, double *d) {
+    double z = 1.0 - fabs(u) - fabs(v);
+    double x = u, y = v;
+    if (z < 0) {
+        x = sgn_pos(u) * (1.0 - fabs(v));
+        y = sgn_pos(v) * (1.0 - fabs(u));
+    }
+    double n = sqrt(x * x + y * y + z * z);
+    d[0] = x / n; d[1] = y / n; d[2] = z / n;
+}
+
+/* Direction of texel (i,j) of an H x W atlas: decode of its pixel centre. */
+void orc_texel_dir(int i, int j, int H, int W, double *d) {
+    double u = (2.0 * j + 1.0) / W - 1.0;
+    double v = (2.0 * i + 1.0) / H - 1.0;
+    orc_octa_decode(u, v, d);
+}
+
+/* ------------------------------------------------------------------------ */
+/* DGSM build: brute force, every texel ray x every Gaussian x every shell   */
+/* (Eqs. 1-5).  No culling, no window.                                        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double A[9];
+    double mu[3];
+    double beta;
+} orc_gauss;
+
+static orc_gauss *prep_all(const float *means, const float *scales, const float *quats,
+                           const float *opac, int64_t N, double kappa) {
+    orc_gauss *g = (orc_gauss *)malloc(sizeof(orc_gauss) * (N > 0 ? N : 1));
+    for (int64_t n = 0; n < N; ++n) {
+        orc_precision(scales + 3 * n, quats + 4 * n, g[n].A);
+        for (int c = 0; c < 3; ++c) g[n].mu[c] = means[3 * n + c];
+        g[n].beta = orc_beta(scales + 3 * n, opac[n], kappa);
+    }
+    return g;
+}
+
+/* Optical depth tau(d, r_k) for one ray, all K shells (Eq. 2 summed with Eq. 3). */
+static void ray_tau(const orc_gauss *g, int64_t N, const double *o, const double *d,
+                    const float *radii, int K, double *tau) {
+    for (int k = 0; k < K; ++k) tau[k] = 0;
+    for (int64_t n = 0; n < N; ++n) {
+        if (g[n].beta == 0) continue;
+        double om[3] = {o[0] - g[n].mu[0], o[1] - g[n].mu[1], o[2] - g[n].mu[2]};
+        double a, b, c;
+        orc_ray_coeffs(g[n].A, d, om, &a, &b, &c);
+        for (int k = 0; k < K; ++k)
+            tau[k] += g[n].beta * orc_line_integral(a, b, c, (double)radii[k]);
+    }
+}
+
+/* Full atlas tau[l][k][i][j] (FP64).  Eq. 4 (T = exp(-tau)) is left to the
+ * caller so that both tau and T are available. */
+void orc_build_tau(const float *means, const float *scales, const float *quats,
+                   const float *opac, int64_t N, const float *lights, int L, int H, int W,
+                   const float *radii, int K, double kappa, double *tau_out) {
+    orc_gauss *g = prep_all(means, scales, quats, opac, N, kappa);
+    int64_t HW = (int64_t)H * W;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t idx = 0; idx < (int64_t)L * HW; ++idx) {
+        int l = (int)(idx / HW);
+        int i = (int)((idx % HW) / W), j = (int)(idx % W);
+        double o[3] = {lights[3 * l], lights[3 * l + 1], lights[3 * l + 2]};
+        double d[3], tau[512];
+        orc_texel_dir(i, j, H, W, d);
+        ray_tau(g, N, o, d, radii, K, tau);
+        for (int k = 0; k < K; ++k) tau_out[((int64_t)l * K + k) * HW + (int64_t)i * W + j] = tau[k];
+    }
+    free(g);
+}
+
+/* tau for a list of texels (l,i,j), all K shells: tau_out[n][K]. */
+void orc_build_tau_texels(const float *means, const float *scales, const float *quats,
+                          const float *opac, int64_t N, const float *lights, int H, int W,
+                          const float *radii, int K, double kappa, const int32_t *lij,
+                          int64_t n_texels, double *tau_out) {
+    orc_gauss *g = prep_all(means, scales, quats, opac, N, kappa);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < n_texels; ++t) {
+        int l = lij[3 * t], i = lij[3 * t + 1], j = lij[3 * t + 2];
+        double o[3] = {lights[3 * l], lights[3 * l + 1], lights[3 * l + 2]};
+        double d[3];
+        orc_texel_dir(i, j, H, W, d);
+        ray_tau(g, N, o, d, radii, K, tau_out + t * K);
+    }
+    free(g);
+}
+
+/* tau along arbitrary rays (origin o_l of light l, unit direction d) at
+ * arbitrary distances t: used by the quadrature pins. */
+void orc_tau_rays(const float *means, const float *scales, const float *quats,
+                  const float *opac, int64_t N, const double *origins, const double *dirs,
+                  const double *t, int64_t n_rays, double kappa, double *tau_out) {
+    orc_gauss *g = prep_all(means, scales, quats, opac, N, kappa);
+    for (int64_t r = 0; r < n_rays; ++r) {
+        double acc = 0;
+        for (int64_t n = 0; n < N; ++n) {
+            if (g[n].beta == 0) continue;
+            double om[3] = {origins[3 * r] - g[n].mu[0], origins[3 * r + 1] - g[n].mu[1],
+                            origins[3 * r + 2] - g[n].mu[2]};
+            double a, b, c;
+            orc_ray_coeffs(g[n].A, dirs + 3 * r, om, &a, &b, &c);
+            acc += g[n].beta * orc_line_integral(a, b, c, t[r]);
+        }
+        tau_out[r] = acc;
+    }
+    free(g);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sampling (Sec. 3.3): centre lookup with trilinear interpolation           */
+/* ------------------------------------------------------------------------ */
+
+/* Continuous lookup of one light's atlas T[K][H][W] (FP64) at world point x:
+ * bilinear between texel centres with clamp-to-edge, linear between the two
+ * shells bracketing t (k = #{r_k <= t} - 1, clamped at both ends). */
+double orc_sample_T(const double *atlas_l, int H, int W, const float *radii, int K,
+                    const double *o, const double *x) {
+    double vx = x[0] - o[0], vy = x[1] - o[1], vz = x[2] - o[2];
+    double t = sqrt(vx * vx + vy * vy + vz * vz);
+    if (t == 0) return 1.0;
+    double d[3] = {vx / t, vy / t, vz / t}, u, v;
+    orc_octa_encode(d, &u, &v);
+    double gx = (u + 1.0) * 0.5 * W - 0.5, gy = (v + 1.0) * 0.5 * H - 0.5;
+    double fj = floor(gx), fi = floor(gy);
+    double ax = gx - fj, ay = gy - fi;
+    int j0 = (int)fj, i0 = (int)fi, j1 = j0 + 1, i1 = i0 + 1;
+    if (j0 < 0) j0 = 0; if (j0 > W - 1) j0 = W - 1;
+    if (j1 < 0) j1 = 0; if (j1 > W - 1) j1 = W - 1;
+    if (i0 < 0) i0 = 0; if (i0 > H - 1) i0 = H - 1;
+    if (i1 < 0) i1 = 0; if (i1 > H - 1) i1 = H - 1;
+    int k = -1;
+    for (int q = 0; q < K; ++q)
+        if ((double)radii[q] <= t) k = q;
+    int k0, k1;
+    double wt;
+    if (k < 0) { k0 = k1 = 0; wt = 0; }
+    else if (k >= K - 1) { k0 = k1 = K - 1; wt = 0; }
+    else { k0 = k; k1 = k + 1; wt = (t - radii[k]) / ((double)radii[k + 1] - radii[k]); }
+    int64_t HW = (int64_t)H * W;
+    double res = 0;
+    for (int s = 0; s < 2; ++s) {
+        int kk = s ? k1 : k0;
+        double ws = s ? wt : 1.0 - wt;
+        const double *P = atlas_l + (int64_t)kk * HW;
+        double b = (1 - ay) * ((1 - ax) * P[(int64_t)i0 * W + j0] + ax * P[(int64_t)i0 * W + j1]) +
+                   ay * ((1 - ax) * P[(int64_t)i1 * W + j0] + ax * P[(int64_t)i1 * W + j1]);
+        res += ws * b;
+    }
+    return res;
+}
+
+/* Attenuation of receivers (Sec. 3.3): the direct part of each colour is
+ * scaled by the light-weighted transmittance,
+ *   c' = c (1 - w_d + w_d sum_l omega_l T_l(x)),
+ * with T_l = T_static,l * T_dynamic,l when a second atlas is given.
+ * atlas: [L][K][H][W] FP64; atlas_dyn may be NULL; light_w may be NULL (1/L). */
+void orc_attenuate(const double *atlas, const double *atlas_dyn, int L, int H, int W,
+                   const float *radii, int K, const float *lights, const float *q_means,
+                   const float *colors_in, int64_t Q, const float *light_w, double direct_frac,
+                   double *colors_out, double *T_out) {
+    int64_t LS = (int64_t)K * H * W;
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < Q; ++q) {
+        double x[3] = {q_means[3 * q], q_means[3 * q + 1], q_means[3 * q + 2]};
+        double acc = 0;
+        for (int l = 0; l < L; ++l) {
+            double o[3] = {lights[3 * l], lights[3 * l + 1], lights[3 * l + 2]};
+            double T = orc_sample_T(atlas + l * LS, H, W, radii, K, o, x);
+            if (atlas_dyn) T *= orc_sample_T(atlas_dyn + l * LS, H, W, radii, K, o, x);
+            if (T_out) T_out[q * L + l] = T;
+            double wl = light_w ? (double)light_w[l] : 1.0 / L;
+            acc += wl * T;
+        }
+        double f = 1.0 - direct_frac + direct_frac * acc;
+        for (int c = 0; c < 3; ++c) colors_out[3 * q + c] = (double)colors_in[3 * q + c] * f;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP32 index specification (bit-exact decisions shared with the GPU)        */
+/* ------------------------------------------------------------------------ */
+
+static float sgnf_pos(float x) { return x >= 0.0f ? 1.0f : -1.0f; }
+
+/* Texel cell, bilinear base tap and shell of the world point x seen from o.
+ * out_i[0..4] = cell i, cell j, bilinear base i0, base j0, shell k (-1 below r_0);
+ * out_f[0..2] = fy, fx (bilinear fractions), t (distance).  All single
+ * precision, IEEE-rounded, no FMA. */
+void orc_f32_sample_index(const float *x, const float *o, int H, int W, const float *radii,
+                          int K, int32_t *out_i, float *out_f) {
+    volatile float vx = x[0] - o[0], vy = x[1] - o[1], vz = x[2] - o[2];
+    volatile float t2a = vx * vx, t2b = vy * vy, t2c = vz * vz;
+    volatile float t2 = (t2a + t2b) + t2c;
+    float t = sqrtf(t2);
+    volatile float s = (fabsf(vx) + fabsf(vy)) + fabsf(vz);
+    float u, v;
+    if (s == 0.0f) { u = 0.0f; v = 0.0f; }
+    else {
+        volatile float qx = vx / s, qy = vy / s;
+        if (vz >= 0.0f) { u = qx; v = qy; }
+        else {
+            volatile float a = 1.0f - fabsf(qy), b = 1.0f - fabsf(qx);
+            u = sgnf_pos(qx) * a; v = sgnf_pos(qy) * b;
+        }
+    }
+    volatile float fu = ((u + 1.0f) * 0.5f) * (float)W;
+    volatile float fv = ((v + 1.0f) * 0.5f) * (float)H;
+    volatile float gx = fu - 0.5f, gy = fv - 0.5f;
+    float bj = floorf(gx), bi = floorf(gy);
+    int cj = (int)floorf(fu), ci = (int)floorf(fv);
+    if (cj < 0) cj = 0; if (cj > W - 1) cj = W - 1;
+    if (ci < 0) ci = 0; if (ci > H - 1) ci = H - 1;
+    int k = -1;
+    for (int q = 0; q < K; ++q)
+        if (radii[q] <= t) k = q;
+    out_i[0] = ci; out_i[1] = cj; out_i[2] = (int32_t)bi; out_i[3] = (int32_t)bj; out_i[4] = k;
+    volatile float fy = gy - bi, fx = gx - bj;
+    out_f[0] = fy; out_f[1] = fx; out_f[2] = t;
+}
+
+void orc_f32_sample_index_batch(const float *x, int64_t n, const float *o, int H, int W,
+                                const float *radii, int K, int32_t *out_i, float *out_f) {
+    for (int64_t q = 0; q < n; ++q)
+        orc_f32_sample_index(x + 3 * q, o, H, W, radii, K, out_i + 5 * q, out_f + 3 * q);
+}
+
+/* FP32 decode of an atlas point (u,v), normalised. */
+static void f32_decode(float u, float v, float *d) {
+    volatile float au = fabsf(u), av = fabsf(v);
+    volatile float z = (1.0f - au) - av;
+    volatile float x = u, y = v;
+    if (z < 0.0f) {
+        volatile float a = 1.0f - av, b = 1.0f - au;
+        x = sgnf_pos(u) * a;
+        y = sgnf_pos(v) * b;
+    }
+    volatile float xx = x * x, yy = y * y, zz = z * z;
+    volatile float n2 = (xx + yy) + zz;
+    float n = sqrtf(n2);
+    volatile float dx = x / n, dy = y / n, dz = z / n;
+    d[0] = dx; d[1] = dy; d[2] = dz;
+}
+
+static float f32_dot(const float *a, const float *b) {
+    volatile float p0 = a[0] * b[0], p1 = a[1] * b[1], p2 = a[2] * b[2];
+    volatile float s = p0 + p1;
+    volatile float r = s + p2;
+    return r;
+}
+
+/* Texel-centre coordinate of index j in an extent of W texels, FP32. */
+static float f32_centre(int j, int W) {
+    volatile float num = (float)(2 * j + 1);
+    volatile float q = num / (float)W;
+    volatile float r = q - 1.0f;
+    return r;
+}
+
+/* Direction cone of the texel-centre rectangle [j0,j1) x [i0,i1):
+ * cone[0..2] axis, cone[3] cos, cone[4] sin, cone[5] = 1 if it spans a
+ * hemisphere or more (then every Gaussian overlaps it). */
+void orc_f32_rect_cone(int i0, int i1, int j0, int j1, int H, int W, float *cone) {
+    float ua = f32_centre(j0, W), ub = f32_centre(j1 - 1, W);
+    float va = f32_centre(i0, H), vb = f32_centre(i1 - 1, H);
+    volatile float su = ua + ub, sv = va + vb;
+    volatile float uc = su * 0.5f, vc = sv * 0.5f;
+    float c[3];
+    f32_decode(uc, vc, c);
+    float pts[64][2];
+    int np = 0;
+    pts[np][0] = ua; pts[np][1] = va; ++np;
+    pts[np][0] = ub; pts[np][1] = va; ++np;
+    pts[np][0] = ua; pts[np][1] = vb; ++np;
+    pts[np][0] = ub; pts[np][1] = vb; ++np;
+    float ve[2] = {va, vb}, ue[2] = {ua, ub};
+    for (int e = 0; e < 2; ++e) {
+        volatile float y = ve[e];
+        volatile float cand[5];
+        cand[0] = 0.0f; cand[1] = 1.0f - y; cand[2] = -1.0f - y; cand[3] = 1.0f + y; cand[4] = y - 1.0f;
+        for (int m = 0; m < 5; ++m)
+            if (ua <= cand[m] && cand[m] <= ub) { pts[np][0] = cand[m]; pts[np][1] = y; ++np; }
+    }
+    for (int e = 0; e < 2; ++e) {
+        volatile float xx = ue[e];
+        volatile float cand[5];
+        cand[0] = 0.0f; cand[1] = 1.0f - xx; cand[2] = -1.0f - xx; cand[3] = 1.0f + xx; cand[4] = xx - 1.0f;
+        for (int m = 0; m < 5; ++m)
+            if (va <= cand[m] && cand[m] <= vb) { pts[np][0] = xx; pts[np][1] = cand[m]; ++np; }
+    }
+    if (ua <= 0.0f && 0.0f <= ub && va <= 0.0f && 0.0f <= vb) { pts[np][0] = 0.0f; pts[np][1] = 0.0f; ++np; }
+    float cmin = 1.0f;
+    for (int p = 0; p < np; ++p) {
+        float d[3];
+        f32_decode(pts[p][0], pts[p][1], d);
+        float cs = f32_dot(c, d);
+        if (cs < cmin) cmin = cs;
+    }
+    cone[0] = c[0]; cone[1] = c[1]; cone[2] = c[2];
+    if (cmin <= 0.0f) {
+        cone[3] = -1.0f; cone[4] = 0.0f; cone[5] = 1.0f;
+    } else {
+        volatile float cc = cmin * cmin;
+        volatile float om = 1.0f - cc;
+        cone[3] = cmin; cone[4] = sqrtf(om); cone[5] = 0.0f;
+    }
+}
+
+/* Per-(light, Gaussian) bounding cone of the binning specification.
+ * out[0..2] unit direction to the Gaussian, out[3] cos, out[4] sin,
+ * out[5] = 1 if the light lies inside the bounding sphere (all tiles),
+ * out[6] = k^2 (cull radius in Mahalanobis units), out[7] = sphere radius r,
+ * out[8] = distance. Returns 0 if the Gaussian is binned nowhere (alpha <= 0,
+ * or wholly beyond the last shell), 1 otherwise, -1 on invalid input. */
+int orc_f32_gauss_cone(const float *mu, const float *s, float alpha, const float *o,
+                       float kappa, float eps, float r_last, float *out) {
+    for (int c = 0; c < 3; ++c)
+        if (!isfinite(mu[c]) || !isfinite(s[c]) || !(s[c] > 0.0f)) return -1;
+    if (!isfinite(alpha)) return -1;
+    float a = alpha;
+    if (!(a > 0.0f)) return 0;
+    if (a > 0.999999f) a = 0.999999f;
+    float smax = fmaxf(fmaxf(s[0], s[1]), s[2]);
+    float smin = fminf(fminf(s[0], s[1]), s[2]);
+    volatile float om = 1.0f - a;
+    volatile float odds = a / om;
+    volatile float t1 = kappa * odds;
+    volatile float ratio = smax / smin;
+    volatile float t2 = t1 * ratio;
+    volatile float Q = t2 / eps;
+    int e = 0;
+    frexpf(Q, &e);
+    if (e < 1) e = 1;
+    volatile float k2 = 1.38629436f * (float)e;
+    volatile float k = sqrtf(k2);
+    volatile float r = k * smax;
+    volatile float vx = mu[0] - o[0], vy = mu[1] - o[1], vz = mu[2] - o[2];
+    volatile float xx = vx * vx, yy = vy * vy, zz = vz * vz;
+    volatile float d2 = (xx + yy) + zz;
+    float dist = sqrtf(d2);
+    volatile float lo = dist - r;
+    out[6] = k2; out[7] = r; out[8] = dist;
+    if (lo > r_last) return 0;
+    if (r >= dist) {
+        out[0] = 0; out[1] = 0; out[2] = 1; out[3] = -1.0f; out[4] = 0.0f; out[5] = 1.0f;
+        return 1;
+    }
+    volatile float sn = r / dist;
+    volatile float sn2 = sn * sn;
+    volatile float c2 = 1.0f - sn2;
+    out[0] = vx / dist; out[1] = vy / dist; out[2] = vz / dist;
+    out[3] = sqrtf(c2); out[4] = sn; out[5] = 0.0f;
+    return 1;
+}
+
+/* Cone-cone overlap: angle(dir, axis) <= theta_g + theta_T, evaluated as
+ * dir . axis >= cos_g cos_T - sin_g sin_T. */
+static int f32_overlap(const float *g, const float *cone) {
+    if (g[5] != 0.0f || cone[5] != 0.0f) return 1;
+    float dot = f32_dot(g, cone);
+    volatile float p = g[3] * cone[3], q = g[4] * cone[4];
+    volatile float rhs = p - q;
+    return dot >= rhs;
+}
+
+/* Light-space tile binning (Sec. 3.2, occluder culling), FP32 specification:
+ * tiles of tile x tile texels, super-tiles of 8x8 tiles; a Gaussian enters a
+ * tile's list iff its cone overlaps the super-tile's cone and the tile's cone.
+ * Writes pairs (key = l * n_tiles + tile, value = Gaussian index) in
+ * (key, value) order, up to `capacity`; returns the total number of pairs
+ * (or -1 if an input was invalid). */
+int64_t orc_f32_bin(const float *means, const float *scales, const float *opac, int64_t N,
+                    const float *lights, int L, int H, int W, const float *radii, int K,
+                    float kappa, float eps, int tile, uint32_t *keys, uint32_t *vals,
+                    int64_t capacity) {
+    int ty = (H + tile - 1) / tile, tx = (W + tile - 1) / tile;
+    int sy = (ty + 7) / 8, sx = (tx + 7) / 8;
+    int n_tiles = ty * tx;
+    float *tc = (float *)malloc(sizeof(float) * 6 * n_tiles);
+    float *sc = (float *)malloc(sizeof(float) * 6 * sy * sx);
+    for (int a = 0; a < ty; ++a)
+        for (int b = 0; b < tx; ++b) {
+            int i0 = a * tile, j0 = b * tile;
+            int i1 = i0 + tile < H ? i0 + tile : H, j1 = j0 + tile < W ? j0 + tile : W;
+            orc_f32_rect_cone(i0, i1, j0, j1, H, W, tc + 6 * (a * tx + b));
+        }
+    for (int a = 0; a < sy; ++a)
+        for (int b = 0; b < sx; ++b) {
+            int i0 = a * 8 * tile, j0 = b * 8 * tile;
+            int i1 = i0 + 8 * tile < H ? i0 + 8 * tile : H, j1 = j0 + 8 * tile < W ? j0 + 8 * tile : W;
+            orc_f32_rect_cone(i0, i1, j0, j1, H, W, sc + 6 * (a * sx + b));
+        }
+    /* per tile: collect in Gaussian order (the natural (key, value) order) */
+    int64_t total = 0;
+    int bad = 0;
+    float *cones = (float *)malloc(sizeof(float) * 9 * (N > 0 ? N : 1));
+    char *ok = (char *)malloc(N > 0 ? N : 1);
+    for (int l = 0; l < L; ++l) {
+        for (int64_t n = 0; n < N; ++n) {
+            int r = orc_f32_gauss_cone(means + 3 * n, scales + 3 * n, opac[n], lights + 3 * l,
+                                       kappa, eps, radii[K - 1], cones + 9 * n);
+            if (r < 0) bad = 1;
+            ok[n] = r == 1;
+        }
+        for (int t = 0; t < n_tiles; ++t) {
+            int a = t / tx, b = t % tx;
+            const float *sup = sc + 6 * ((a / 8) * sx + (b / 8));
+            for (int64_t n = 0; n < N; ++n) {
+                if (!ok[n]) continue;
+                if (!f32_overlap(cones + 9 * n, sup)) continue;
+                if (!f32_overlap(cones + 9 * n, tc + 6 * t)) continue;
+                if (total < capacity) {
+                    keys[total] = (uint32_t)(l * n_tiles + t);
+                    vals[total] = (uint32_t)n;
+                }
+                ++total;
+            }
+        }
+    }
+    free(tc); free(sc); free(cones); free(ok);
+    return bad ? -1 : total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* HDRI probe (Sec. 3.4): real SH basis to degree 2 and the ridge fit, Eq. 7 */
+/* ------------------------------------------------------------------------ */
+
+/* Real SH basis Y_k, k = l^2 + l + m, degree <= 2, no Condon-Shortley phase:
+ * Y_{1,-1} ~ y, Y_{1,0} ~ z, Y_{1,1} ~ x.  Constants from
+ * Y_lm normalisation sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (times sqrt 2 for m != 0). */
+void orc_sh_basis(const double *d, double *Y) {
+    double x = d[0], y = d[1], z = d[2];
+    double c0 = 0.5 * sqrt(1.0 / ORC_PI);
+    double c1 = sqrt(3.0 / (4.0 * ORC_PI));
+    double c2 = 0.5 * sqrt(15.0 / ORC_PI);
+    double c20 = 0.25 * sqrt(5.0 / ORC_PI);
+    double c22 = 0.25 * sqrt(15.0 / ORC_PI);
+    Y[0] = c0;
+    Y[1] = c1 * y;
+    Y[2] = c1 * z;
+    Y[3] = c1 * x;
+    Y[4] = c2 * x * y;
+    Y[5] = c2 * y * z;
+    Y[6] = c20 * (3.0 * z * z - 1.0);
+    Y[7] = c2 * x * z;
+    Y[8] = c22 * (x * x - y * y);
+}
+
+/* Eq. 7: (B^T W B + lambda I) A = B^T W Y, solved by Cholesky.  sh_out is
+ * SH in R^{3 x 9}: sh_out[c*9 + k] = A[k][c].  Returns 0, or 1 if the system
+ * is not positive definite. */
+int orc_sh_fit(const float *dirs, const float *rgb, const float *w, int64_t n, double lambda,
+               double *sh_out) {
+    double G[81] = {0}, R[27] = {0};
+    for (int64_t s = 0; s < n; ++s) {
+        double d[3] = {dirs[3 * s], dirs[3 * s + 1], dirs[3 * s + 2]}, Y[9];
+        orc_sh_basis(d, Y);
+        double ws = w[s];
+        for (int a = 0; a < 9; ++a) {
+            for (int b = 0; b < 9; ++b) G[9 * a + b] += ws * Y[a] * Y[b];
+            for (int c = 0; c < 3; ++c) R[3 * a + c] += ws * Y[a] * (double)rgb[3 * s + c];
+        }
+    }
+    for (int a = 0; a < 9; ++a) G[9 * a + a] += lambda;
+    /* Cholesky G = L L^T */
+    double Lm[81] = {0};
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = G[9 * i + j];
+            for (int k = 0; k < j; ++k) s -= Lm[9 * i + k] * Lm[9 * j + k];
+            if (i == j) {
+                if (!(s > 0)) return 1;
+                Lm[9 * i + i] = sqrt(s);
+            } else {
+                Lm[9 * i + j] = s / Lm[9 * j + j];
+            }
+        }
+    for (int c = 0; c < 3; ++c) {
+        double yv[9], xv[9];
+        for (int i = 0; i < 9; ++i) {
+            double s = R[3 * i + c];
+            for (int k = 0; k < i; ++k) s -= Lm[9 * i + k] * yv[k];
+            yv[i] = s / Lm[9 * i + i];
+        }
+        for (int i = 8; i >= 0; --i) {
+            double s = yv[i];
+            for (int k = i + 1; k < 9; ++k) s -= Lm[9 * k + i] * xv[k];
+            xv[i] = s / Lm[9 * i + i];
+        }
+        for (int k = 0; k < 9; ++k) sh_out[9 * c + k] = xv[k];
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Radiance transfer (Sec. 3.5, Eqs. 8-10)                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Unit normal of a Gaussian: its smallest-scale axis (first one on ties),
+ * flipped to point away from `centroid`. */
+void orc_gauss_normal(const float *mu, const float *s, const float *q, const float *centroid,
+                      double *n) {
+    double R[9];
+    orc_quat_to_rot(q, R);
+    int k = 0;
+    if (s[1] < s[k]) k = 1;
+    if (s[2] < s[k]) k = 2;
+    n[0] = R[0 + k]; n[1] = R[3 + k]; n[2] = R[6 + k];
+    double side = n[0] * ((double)mu[0] - centroid[0]) + n[1] * ((double)mu[1] - centroid[1]) +
+                  n[2] * ((double)mu[2] - centroid[2]);
+    if (side < 0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
+}
+
+/* Eq. 10 for one normal: lat-long cell centres theta_i = (i+1/2) pi / n_theta,
+ * phi_j = (j+1/2) 2 pi / n_phi, weights w = sin theta, L_c(omega) from Eq. 8,
+ * S = max(0, <omega, n>)^q (Eq. 9). */
+void orc_transfer_scale(const double *sh, const double *n, double q, double t_max, double eps,
+                        int n_theta, int n_phi, double *s_out) {
+    double num[3] = {0, 0, 0}, den = 0;
+    for (int i = 0; i < n_theta; ++i) {
+        double th = (i + 0.5) * ORC_PI / n_theta;
+        for (int j = 0; j < n_phi; ++j) {
+            double ph = (j + 0.5) * 2.0 * ORC_PI / n_phi;
+            double om[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
+            double wj = sin(th);
+            double cs = om[0] * n[0] + om[1] * n[1] + om[2] * n[2];
+            double S = cs > 0 ? pow(cs, q) : 0.0;
+            double Y[9];
+            orc_sh_basis(om, Y);
+            for (int c = 0; c < 3; ++c) {
+                double Lc = 0;
+                for (int k = 0; k < 9; ++k) Lc += sh[9 * c + k] * Y[k];
+                num[c] += wj * Lc * S;
+            }
+            den += wj * S;
+        }
+    }
+    for (int c = 0; c < 3; ++c) {
+        double v = num[c] / (den + eps);
+        if (v < 0) v = 0;
+        if (v > t_max) v = t_max;
+        s_out[c] = v;
+    }
+}
+
+/* Relit colours c' = max(0, gamma c (.) s(n)) for N Gaussians.  normals may
+ * be NULL (then each normal is the smallest axis, away from centroid). */
+void orc_relight(const double *sh, const float *means, const float *quats, const float *scales,
+                 const float *normals, const float *centroid, const float *colors_in, int64_t N,
+                 double q, double gamma, double t_max, double eps, int n_theta, int n_phi,
+                 double *colors_out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t g = 0; g < N; ++g) {
+        double n[3], s[3];
+        if (normals) {
+            double nn = sqrt((double)normals[3 * g] * normals[3 * g] +
+                             (double)normals[3 * g + 1] * normals[3 * g + 1] +
+                             (double)normals[3 * g + 2] * normals[3 * g + 2]);
+            for (int c = 0; c < 3; ++c) n[c] = normals[3 * g + c] / nn;
+        } else {
+            orc_gauss_normal(means + 3 * g, scales + 3 * g, quats + 4 * g, centroid, n);
+        }
+        orc_transfer_scale(sh, n, q, t_max, eps, n_theta, n_phi, s);
+        for (int c = 0; c < 3; ++c) {
+            double v = gamma * (double)colors_in[3 * g + c] * s[c];
+            colors_out[3 * g + c] = v > 0 ? v : 0.0;
+        }
+    }
+}

@@ -1,0 +1,247 @@
+"""Pins of the oracle's octahedral map (Eq. 6 and its inverse), its FP32 index
+specification, the tile-binning specification (occluder culling, Sec. 3.2)
+and the centre-sample lookup (Sec. 3.3)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2601_01660_b300 import scenes
+
+
+def test_encode_known_directions(orc):
+    cases = {(0, 0, 1): (0, 0), (1, 0, 0): (1, 0), (0, 1, 0): (0, 1), (-1, 0, 0): (-1, 0),
+             (0, -1, 0): (0, -1)}
+    for d, uv in cases.items():
+        assert orc.octa_encode(np.array(d, float)) == pytest.approx(uv, abs=1e-15)
+    # -z folds onto the four corners; sgn(0) = +1 picks (+1,+1)
+    assert orc.octa_encode(np.array([0, 0, -1.0])) == pytest.approx((1, 1))
+    assert orc.octa_encode(np.array([1e-9, -1e-9, -1.0])) == pytest.approx((1, -1), abs=1e-8)
+
+
+def test_encode_decode_inverse(orc):
+    rng = np.random.default_rng(0)
+    for _ in range(2000):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        u, v = orc.octa_encode(d)
+        assert -1 <= u <= 1 and -1 <= v <= 1
+        np.testing.assert_allclose(orc.octa_decode(u, v), d, atol=1e-14)
+        uv = rng.uniform(-1, 1, 2)
+        dd = orc.octa_decode(*uv)
+        assert np.linalg.norm(dd) == pytest.approx(1.0, abs=1e-15)
+        np.testing.assert_allclose(orc.octa_encode(dd), uv, atol=1e-14)
+
+
+@pytest.mark.parametrize("H,W", [(64, 64), (256, 256), (512, 512), (48, 80)])
+def test_f32_round_trip_every_texel(orc, H, W):
+    """encode(decode(texel centre)) lands in the same texel under the FP32 spec."""
+    dirs = np.array([orc.texel_dir(i, j, H, W) for i in range(H) for j in range(W)])
+    pts = (dirs * 3.0).astype(np.float32)
+    ints, fl = orc.f32_sample_index(pts, np.zeros(3), H, W, scenes.radii_linear(0.1, 8, 4))
+    ii, jj = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    assert np.array_equal(ints[:, 0], ii.ravel())
+    assert np.array_equal(ints[:, 1], jj.ravel())
+    # the bilinear base sits on the texel itself (fraction ~0) or its lower
+    # neighbour (fraction ~1) when rounding lands a hair below the centre
+    fx = fl[:, 1]
+    near0 = (ints[:, 3] == jj.ravel()) & (fx < 1e-3)
+    near1 = (ints[:, 3] == jj.ravel() - 1) & (fx > 1 - 1e-3)
+    assert np.all(near0 | near1)
+
+
+def test_f32_index_agrees_with_fp64_encode(orc):
+    rng = np.random.default_rng(1)
+    H, W = 96, 128
+    radii = scenes.radii_geometric(0.05, 12, 20)
+    o = np.float32([0.3, -0.2, 1.0])
+    pts = np.float32(rng.uniform(-6, 6, (3000, 3)))
+    ints, fl = orc.f32_sample_index(pts, o, H, W, radii)
+    for p, iv, fv in zip(pts, ints, fl):
+        v = p.astype(np.float64) - o
+        t = np.linalg.norm(v)
+        u, vv = orc.octa_encode(v / t)
+        gx = (u + 1) / 2 * W - 0.5
+        gy = (vv + 1) / 2 * H - 0.5
+        assert iv[3] + fv[1] == pytest.approx(gx, abs=2e-4)
+        assert iv[2] + fv[0] == pytest.approx(gy, abs=2e-4)
+        k = int(np.sum(radii.astype(np.float64) <= t)) - 1
+        assert abs(iv[4] - k) <= 1 and fv[2] == pytest.approx(t, rel=1e-6)
+
+
+@pytest.mark.parametrize("H,W,tile", [(64, 64, 8), (44, 60, 8), (128, 128, 16), (40, 40, 4)])
+def test_tile_cones_contain_their_texels(orc, H, W, tile):
+    for i0 in range(0, H, tile):
+        for j0 in range(0, W, tile):
+            i1, j1 = min(i0 + tile, H), min(j0 + tile, W)
+            cone = orc.f32_rect_cone(i0, i1, j0, j1, H, W)
+            if cone[5]:
+                continue
+            c = cone[:3].astype(np.float64)
+            for i in range(i0, i1):
+                for j in range(j0, j1):
+                    d = orc.texel_dir(i, j, H, W)
+                    assert d @ c >= cone[3] - 1e-6
+
+
+def test_gauss_cone_bounds_the_culling_ellipsoid(orc):
+    """Every point of the k-ellipsoid {(x-mu)^T A (x-mu) <= k^2} lies inside the
+    cone (and the sphere) the binning spec gives the Gaussian."""
+    sc = scenes.cube_scene(200, seed=12)
+    o = np.float32([0.2, 0.1, 0.0])
+    rng = np.random.default_rng(2)
+    for i in range(sc.n):
+        r, g = orc.f32_gauss_cone(sc.means[i], sc.scales[i], sc.opac[i], o, 1.0, 1e-7, 8.0)
+        assert r in (0, 1)
+        if r == 0 or g[5]:
+            continue
+        k = math.sqrt(g[6])
+        R = orc.rotation(sc.quats[i])
+        z = rng.normal(size=(64, 3))
+        z /= np.linalg.norm(z, axis=1, keepdims=True)
+        pts = sc.means[i] + (z * k * sc.scales[i]) @ R.T
+        v = pts - o
+        cosang = (v / np.linalg.norm(v, axis=1, keepdims=True)) @ g[:3].astype(np.float64)
+        assert np.all(cosang >= g[3] - 1e-6)
+
+
+def test_cull_radius_bounds_missed_optical_depth(orc):
+    """A ray that misses the k-ellipsoid carries at most eps of optical depth
+    from that Gaussian: beta I(inf) <= kappa odds (s_max/s_min) e^{-k^2/2} <= eps."""
+    rng = np.random.default_rng(4)
+    sc = scenes.cube_scene(60, seed=13)
+    eps = 1e-7
+    for i in range(sc.n):
+        r, g = orc.f32_gauss_cone(sc.means[i], sc.scales[i], sc.opac[i], np.zeros(3), 1.0, eps, 1e9)
+        k = math.sqrt(g[6])
+        A = orc.precision(sc.scales[i], sc.quats[i])
+        Rm = orc.rotation(sc.quats[i])
+        one = scenes.subset(sc, [i])
+        for _ in range(10):
+            # aim at a point just outside the ellipsoid (Mahalanobis radius 1.02 k)
+            z = rng.normal(size=3)
+            z /= np.linalg.norm(z)
+            p = sc.means[i] + Rm @ (z * 1.02 * k * sc.scales[i])
+            d = p / np.linalg.norm(p)
+            a, b, c = orc.ray_coeffs(A, d, -sc.means[i].astype(np.float64))
+            m2 = c - b * b / a
+            if m2 < k * k:   # this ray still cuts the ellipsoid elsewhere
+                continue
+            tau = orc.tau_rays(one, np.zeros((1, 3)), d[None], [1e4])[0]
+            assert tau <= eps * 1.0001
+
+
+def _brute_lists(orc, sc, o, H, W, tile, radii, eps):
+    """Which (tile, Gaussian) pairs must be binned: some texel ray of the tile
+    cuts the Gaussian's k-ellipsoid at t > 0 within the shells."""
+    ty, tx = -(-H // tile), -(-W // tile)
+    need = set()
+    dirs = np.array([[orc.texel_dir(i, j, H, W) for j in range(W)] for i in range(H)])
+    for g in range(sc.n):
+        r, cone = orc.f32_gauss_cone(sc.means[g], sc.scales[g], sc.opac[g], o, 1.0, eps,
+                                     float(radii[-1]))
+        if r != 1:
+            continue
+        k2 = float(cone[6])
+        A = orc.precision(sc.scales[g], sc.quats[g])
+        om = o.astype(np.float64) - sc.means[g]
+        Ad = dirs @ A            # (H,W,3)
+        a = np.einsum("hwc,hwc->hw", Ad, dirs)
+        b = Ad @ om
+        c = om @ A @ om
+        m2 = c - b * b / a
+        hit = (m2 <= k2) & (-b / a > 0)
+        for i, j in zip(*np.nonzero(hit)):
+            need.add(((i // tile) * tx + (j // tile), g))
+    return need
+
+
+@pytest.mark.parametrize("H,W,tile", [(32, 32, 8), (40, 56, 8), (64, 64, 16)])
+def test_binning_is_conservative(orc, H, W, tile):
+    sc = scenes.cube_scene(150, seed=14, log_s_mean=math.log(0.08))
+    o = np.float32([0.1, -0.1, 0.2])
+    radii = scenes.radii_linear(0.1, 8, 8)
+    keys, vals = orc.f32_bin(sc, o[None], H, W, radii, eps=1e-7, tile=tile)
+    got = set(zip(keys.tolist(), vals.tolist()))
+    need = _brute_lists(orc, sc, o, H, W, tile, radii, 1e-7)
+    assert need <= got
+    # the lists come out ordered by (key, Gaussian index)
+    order = np.lexsort((vals, keys))
+    assert np.array_equal(order, np.arange(keys.size))
+
+
+def test_binned_sum_matches_full_sum(orc):
+    """Summing Eq. 3 over the binned Gaussians only changes tau by at most
+    (number of Gaussians) x eps per voxel."""
+    sc = scenes.cube_scene(120, seed=15)
+    o = np.float32([0, 0, 0])
+    H = W = 16
+    tile = 8
+    radii = scenes.radii_linear(0.1, 8, 6)
+    eps = 1e-7
+    keys, vals = orc.f32_bin(sc, o[None], H, W, radii, eps=eps, tile=tile)
+    full = orc.build_tau(sc, o[None], H, W, radii)[0]
+    tx = W // tile
+    for t in np.unique(keys):
+        members = vals[keys == t]
+        ti, tj = divmod(int(t), tx)
+        sub = scenes.subset(sc, members)
+        part = orc.build_tau(sub, o[None], H, W, radii)[0]
+        blk = (slice(None), slice(ti * tile, ti * tile + tile), slice(tj * tile, tj * tile + tile))
+        assert np.max(np.abs(part[blk] - full[blk])) <= sc.n * eps
+    empty = set(range((H // tile) * (W // tile))) - set(np.unique(keys).tolist())
+    for t in empty:
+        ti, tj = divmod(int(t), tx)
+        blk = (slice(None), slice(ti * tile, ti * tile + tile), slice(tj * tile, tj * tile + tile))
+        assert np.max(full[blk]) <= sc.n * eps
+
+
+def test_sample_at_voxel_centre_returns_voxel(orc):
+    rng = np.random.default_rng(7)
+    K, H, W = 5, 12, 20
+    radii = scenes.radii_geometric(0.2, 9.0, K)
+    atlas = rng.random((K, H, W))
+    o = np.array([0.5, -0.25, 1.0])
+    for _ in range(50):
+        k, i, j = rng.integers(K), rng.integers(H), rng.integers(W)
+        x = o + orc.texel_dir(i, j, H, W) * float(radii[k])
+        assert orc.sample_T(atlas, radii, o, x) == pytest.approx(atlas[k, i, j], abs=1e-9)
+
+
+def test_sample_is_trilinear(orc):
+    """An atlas linear in (j, i, r) is reproduced exactly between texel centres
+    and bracketing shells (away from the clamped borders and the fold)."""
+    K, H, W = 6, 32, 32
+    radii = scenes.radii_linear(0.5, 5.5, K)
+    kk, ii, jj = np.meshgrid(np.arange(K), np.arange(H), np.arange(W), indexing="ij")
+    atlas = 0.01 * jj + 0.02 * ii + 0.1 * radii.astype(np.float64)[kk]
+    rng = np.random.default_rng(8)
+    o = np.zeros(3)
+    for _ in range(300):
+        u, v = rng.uniform(-0.45, 0.45, 2)      # inside the upper diamond
+        d = orc.octa_decode(u, v)
+        t = rng.uniform(0.6, 5.4)
+        gx = (u + 1) / 2 * W - 0.5
+        gy = (v + 1) / 2 * H - 0.5
+        ref = 0.01 * gx + 0.02 * gy + 0.1 * t
+        assert orc.sample_T(atlas, radii, o, d * t) == pytest.approx(ref, abs=1e-9)
+
+
+def test_attenuate_weights_and_direct_fraction(orc):
+    rng = np.random.default_rng(9)
+    L, K, H, W = 3, 4, 8, 8
+    radii = scenes.radii_linear(0.1, 8, K)
+    atlas = np.empty((L, K, H, W))
+    for l, val in enumerate([0.2, 0.5, 0.9]):
+        atlas[l] = val
+    lights = np.float32([[0, 0, 0], [1, 0, 0], [0, 1, 0]])
+    qm = np.float32(rng.uniform(-3, 3, (10, 3)))
+    col = np.float32(rng.random((10, 3)))
+    c64 = col.astype(np.float64)
+    out = orc.attenuate(atlas, radii, lights, qm, col)
+    np.testing.assert_allclose(out, c64 * (0.2 + 0.5 + 0.9) / 3, rtol=1e-12)
+    out = orc.attenuate(atlas, radii, lights, qm, col, light_w=np.float32([1, 0, 0]),
+                        direct_frac=0.5)
+    np.testing.assert_allclose(out, c64 * (0.5 + 0.5 * 0.2), rtol=1e-7)
+    out, T = orc.attenuate(atlas, radii, lights, qm, col, atlas_dyn=atlas, want_T=True)
+    np.testing.assert_allclose(T, np.tile([0.04, 0.25, 0.81], (10, 1)), rtol=1e-12)

@@ -1,0 +1,197 @@
+/*
+ * dgsm.h -- C ABI of libdgsm.so: Deep Gaussian Shadow Maps on one B300
+ * (sm_103a).  Method: "Animated 3DGS Avatars in Diverse Scenes with
+ * Consistent Lighting and Shadows", Sec. 3.2 (build), 3.3 (sampling),
+ * 3.4 (HDRI probe fit) and 3.5 (radiance transfer).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Array pointers are DEVICE pointers into caller-owned memory unless an
+ *   argument says "host".  Arrays are dense, C-contiguous, float32 unless
+ *   stated; the library never keeps them past the call and never frees them.
+ * - Gaussians come as structure-of-arrays: means (n,3) metres; scales (n,3)
+ *   linear standard deviations (not log), all > 0; quats (n,4) rotations
+ *   (w,x,y,z), normalised inside; opac (n) opacities alpha, clamped to
+ *   [0, 1-1e-6].  Covariance Sigma = R diag(s^2) R^T, precision A = Sigma^-1.
+ * - An atlas is [L][K][H][W] (lights, shells, rows, columns) of
+ *   transmittance T (Eq. 4); row i holds v_i = (2i+1)/H - 1, column j holds
+ *   u_j = (2j+1)/W - 1 of the octahedral map (Eq. 6); shell k holds T at
+ *   distance radii[k] from the light.  radii must be strictly increasing
+ *   and > 0.
+ * - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *   enqueued asynchronously unless the function says it blocks.
+ * - Return value: DGSM_OK (0) or one of the dgsm_status codes; details
+ *   via dgsm_last_error(ctx).  Nothing traps or aborts on bad input.
+ * - A dgsm_ctx is bound to one device and must not be used by two host
+ *   threads at once.
+ */
+#ifndef DGSM_H
+#define DGSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dgsm_ctx dgsm_ctx;
+
+enum dgsm_status {
+    DGSM_OK = 0,
+    DGSM_ERR_INVALID_ARG = 1,      /* a size, pointer or parameter is out of range */
+    DGSM_ERR_CUDA = 2,             /* a CUDA runtime call failed (message names it) */
+    DGSM_ERR_WORKSPACE = 3,        /* an output or internal capacity is too small */
+    DGSM_ERR_TIMEOUT = 4,          /* a bounded device-side wait gave up */
+    DGSM_ERR_NONFINITE_INPUT = 5,  /* NaN/Inf or non-positive scale in the Gaussians */
+    DGSM_ERR_NOT_SPD = 6           /* the SH normal equations are not positive definite */
+};
+
+enum dgsm_dtype { DGSM_F32 = 0, DGSM_F16 = 1, DGSM_BF16 = 2 };
+
+/* Build parameters.  kappa: global strength knob of Eq. 5 (default 1).
+ * eps_cull: optical depth a culled Gaussian may still carry along a ray
+ * (default 1e-7); it sets each Gaussian's culling radius k (Mahalanobis
+ * units), k^2 = 2 ln2 * max(e,1), e the binary exponent of
+ * kappa * alpha/(1-alpha) * (s_max/s_min) / eps_cull.
+ * tile: atlas tile edge in texels for light-space binning, 4, 8 or 16
+ * (default 8, the paper's 8x8 tiles).  chunk: Gaussians staged in shared
+ * memory per round, 16..256 (default 64).  atlas_dtype: storage type of T
+ * (dgsm_dtype; tau is always accumulated in float32). */
+typedef struct {
+    float kappa;
+    float eps_cull;
+    int32_t tile;
+    int32_t chunk;
+    int32_t atlas_dtype;
+    int32_t reserved;
+} dgsm_params;
+
+/* Counters of the last dgsm_build on a context. */
+typedef struct {
+    int64_t n_pairs;      /* binned (tile, Gaussian) pairs */
+    int64_t rays_tested;  /* texel-ray x Gaussian pairs tested (texels x list lengths) */
+    int64_t ray_evals;    /* Gaussian-ray evaluations: rays cutting the culling ellipsoid at t > 0 */
+    int64_t shell_evals;  /* closed-form (Eq. 3) evaluations at shell radii */
+} dgsm_build_stats;
+
+/* Transfer parameters of Eqs. 9-10: lobe exponent q (1 = Lambertian),
+ * global intensity gamma, clip t_max, epsilon of the denominator, and the
+ * lat-long grid n_theta x n_phi (cell centres, weights sin(theta)).
+ * Defaults: q=1, gamma=1, t_max=10, eps=1e-8, 32 x 64. */
+typedef struct {
+    float q;
+    float gamma;
+    float t_max;
+    float eps;
+    int32_t n_theta;
+    int32_t n_phi;
+} dgsm_relight_params;
+
+void dgsm_default_params(dgsm_params *p);
+void dgsm_default_relight_params(dgsm_relight_params *p);
+
+/* Create a context on `device` (makes it current).  The context owns a
+ * growable device workspace used by dgsm_build; it is freed by
+ * dgsm_destroy.  Returns DGSM_OK or DGSM_ERR_CUDA. */
+int dgsm_create(int device, dgsm_ctx **out);
+void dgsm_destroy(dgsm_ctx *ctx);
+
+/* Message of the last failure on ctx (static storage of the context;
+ * valid until the next call on it). */
+const char *dgsm_last_error(const dgsm_ctx *ctx);
+const char *dgsm_status_string(int status);
+
+/* Deep Gaussian Shadow Map build (Sec. 3.2, Eqs. 1-5; tile binning after
+ * the occluder-culling paragraph).  For every light l, texel (i,j) and
+ * shell k:  atlas[l][k][i][j] = exp(-sum_n beta_n I_n(d_ij, radii[k])),
+ * beta_n from Eq. 5, I_n the closed form of Eq. 3 along the ray from
+ * lights[l] through the decoded texel centre d_ij.  Gaussians whose
+ * culling ellipsoid does not reach a tile (or a shell interval) are
+ * skipped; each skip changes tau by at most params->eps_cull.
+ *   means/scales/quats/opac: the n occluder Gaussians (n >= 0; n = 0 gives
+ *   T = 1 everywhere); lights: (n_lights,3), 1 <= n_lights <= 64;
+ *   1 <= H, W <= 4096; radii: (K), 1 <= K <= 256; params: host pointer or
+ *   NULL for defaults; atlas: [n_lights][K][H][W] of params->atlas_dtype.
+ * Blocks once, midway, to size the workspace from the number of binned
+ * pairs (so it is not capturable in a CUDA graph).  Fails with
+ * DGSM_ERR_NONFINITE_INPUT if an input Gaussian has a NaN/Inf field or a
+ * scale <= 0, DGSM_ERR_WORKSPACE if more than 2^31 pairs are binned. */
+int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
+               const float *opac, int64_t n, const float *lights, int32_t n_lights, int32_t H,
+               int32_t W, const float *radii, int32_t K, const dgsm_params *params, void *atlas,
+               void *stream);
+
+/* Counters of the last dgsm_build on ctx (blocks until they are ready). */
+int dgsm_get_build_stats(dgsm_ctx *ctx, dgsm_build_stats *out);
+
+/* The light-space tile binning of dgsm_build on its own: writes the sorted
+ * pairs key = l * n_tiles + tile (tiles row-major, ceil(H/tile) x
+ * ceil(W/tile) per light), value = Gaussian index, ordered by (key, value).
+ * keys_out/vals_out: device arrays of `capacity` uint32 (may be NULL when
+ * capacity is 0); *n_pairs_out (host) receives the pair count.  Returns
+ * DGSM_ERR_WORKSPACE (after setting *n_pairs_out) when capacity is short.
+ * Blocks. */
+int dgsm_bin(dgsm_ctx *ctx, const float *means, const float *scales, const float *opac,
+             int64_t n, const float *lights, int32_t n_lights, int32_t H, int32_t W,
+             const float *radii, int32_t K, const dgsm_params *params, uint32_t *keys_out,
+             uint32_t *vals_out, int64_t capacity, int64_t *n_pairs_out, void *stream);
+
+/* Receiver attenuation (Sec. 3.3, centre sample): for each query q and
+ * light l, T_l = trilinear lookup of atlas[l] at the octahedral code of
+ * (x_q - o_l) and distance t = |x_q - o_l| -- bilinear between texel
+ * centres with clamp-to-edge, linear between the shells bracketing t
+ * (clamped to the first/last shell), T = 1 when x_q = o_l; multiplied by
+ * the same lookup in atlas_dyn when it is not NULL.  Then
+ *   colors_out[q] = colors_in[q] * (1 - direct_frac + direct_frac * sum_l w_l T_l)
+ * with w_l = light_w[l], or 1/n_lights when light_w is NULL.
+ *   atlas, atlas_dyn: [n_lights][K][H][W] of `dtype` (both the same shape);
+ *   q_means, colors_in, colors_out: (n_q,3) (colors_out may equal
+ *   colors_in); T_out: (n_q, n_lights) or NULL.  n_q >= 0. */
+int dgsm_attenuate(dgsm_ctx *ctx, const void *atlas, const void *atlas_dyn, int32_t dtype,
+                   int32_t n_lights, int32_t H, int32_t W, const float *radii, int32_t K,
+                   const float *lights, const float *q_means, const float *colors_in,
+                   int64_t n_q, const float *light_w, float direct_frac, float *colors_out,
+                   float *T_out, void *stream);
+
+/* The integer decisions of dgsm_attenuate for n points seen from one light
+ * (device pointer to 3 floats): idx_out (n,5) = texel cell row i, cell
+ * column j, bilinear base row i0, base column j0, shell k (#{radii <= t}-1,
+ * -1 below radii[0]); frac_out (n,3) = fy, fx, t.  Uses the same device code
+ * as dgsm_attenuate. */
+int dgsm_sample_index(dgsm_ctx *ctx, const float *points, int64_t n, const float *light,
+                      int32_t H, int32_t W, const float *radii, int32_t K, int32_t *idx_out,
+                      float *frac_out, void *stream);
+
+/* HDRI probe fit (Sec. 3.4, Eq. 7): the weighted ridge least squares
+ * (B^T W B + lambda I) A = B^T W Y over n cubemap samples, B the real SH
+ * basis to degree 2 (index l^2+l+m, no Condon-Shortley phase), solved in
+ * FP64 on the GPU (accumulation and Cholesky).
+ *   dirs (n,3) unit directions, rgb (n,3) radiance, w (n) solid-angle
+ *   weights; n >= 1; lambda >= 0.  sh_out: (3,9) float32, SH[c][k] = A[k][c];
+ *   sh64_out: (3,9) float64 or NULL.  A system that is not positive
+ *   definite is reported through dgsm_sync_status as DGSM_ERR_NOT_SPD and
+ *   leaves sh_out zero. */
+int sh_fit(dgsm_ctx *ctx, const float *dirs, const float *rgb, const float *w, int64_t n,
+           double lambda, float *sh_out, double *sh64_out, void *stream);
+
+/* Per-Gaussian radiance transfer (Sec. 3.5, Eqs. 8-10):
+ *   s_c(n) = clip_[0,t_max]( sum_j w_j L_c(w_j) S_j / (sum_j w_j S_j + eps) ),
+ *   S_j = max(0, <w_j, n>)^q,  colors_out = max(0, gamma * colors_in (.) s).
+ * n is normals[g] (normalised) when normals is not NULL, else the
+ * smallest-scale axis of the Gaussian (first on ties) turned to point away
+ * from `centroid` (device pointer, 3 floats).  sh: (3,9) device float32.
+ * colors_out may equal colors_in.  params: host pointer or NULL. */
+int sh_relight(dgsm_ctx *ctx, const float *sh, const float *means, const float *quats,
+               const float *scales, const float *normals, const float *centroid,
+               const float *colors_in, int64_t n, const dgsm_relight_params *params,
+               float *colors_out, void *stream);
+
+/* Reads and clears the context's device status word (blocks on `stream`):
+ * returns DGSM_OK or the first error a kernel recorded since the last call. */
+int dgsm_sync_status(dgsm_ctx *ctx, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGSM_H */

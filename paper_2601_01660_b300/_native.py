@@ -1,0 +1,295 @@
+"""ctypes binding of libdgsm.so (include/dgsm.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library.  Tensors must be CUDA, C-contiguous and of the dtype the C ABI
+names; results are written into caller-provided or freshly allocated torch
+tensors (torch only provides device memory and streams).  If the library is
+missing this module raises ImportError: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdgsm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built: run `python -m paper_2601_01660_b300.build`")
+
+_lib = C.CDLL(LIB_PATH)
+
+DGSM_OK = 0
+STATUS = {0: "DGSM_OK", 1: "DGSM_ERR_INVALID_ARG", 2: "DGSM_ERR_CUDA", 3: "DGSM_ERR_WORKSPACE",
+          4: "DGSM_ERR_TIMEOUT", 5: "DGSM_ERR_NONFINITE_INPUT", 6: "DGSM_ERR_NOT_SPD"}
+DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
+TORCH_DTYPES = {0: torch.float32, 1: torch.float16, 2: torch.bfloat16}
+
+
+class DGSMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    """Mirror of dgsm_params."""
+    _fields_ = [("kappa", C.c_float), ("eps_cull", C.c_float), ("tile", C.c_int32),
+                ("chunk", C.c_int32), ("atlas_dtype", C.c_int32), ("reserved", C.c_int32)]
+
+    @classmethod
+    def make(cls, kappa=1.0, eps_cull=1e-7, tile=8, chunk=64, atlas_dtype="f32"):
+        p = cls()
+        _lib.dgsm_default_params(C.byref(p))
+        p.kappa, p.eps_cull, p.tile, p.chunk = kappa, eps_cull, tile, chunk
+        p.atlas_dtype = DTYPES[atlas_dtype] if isinstance(atlas_dtype, str) else int(atlas_dtype)
+        return p
+
+
+class RelightParams(C.Structure):
+    """Mirror of dgsm_relight_params."""
+    _fields_ = [("q", C.c_float), ("gamma", C.c_float), ("t_max", C.c_float), ("eps", C.c_float),
+                ("n_theta", C.c_int32), ("n_phi", C.c_int32)]
+
+    @classmethod
+    def make(cls, q=1.0, gamma=1.0, t_max=10.0, eps=1e-8, n_theta=32, n_phi=64):
+        p = cls()
+        p.q, p.gamma, p.t_max, p.eps, p.n_theta, p.n_phi = q, gamma, t_max, eps, n_theta, n_phi
+        return p
+
+
+class BuildStats(C.Structure):
+    _fields_ = [("n_pairs", C.c_int64), ("rays_tested", C.c_int64), ("ray_evals", C.c_int64),
+                ("shell_evals", C.c_int64)]
+
+
+_vp = C.c_void_p
+_i32, _i64, _f32, _f64 = C.c_int32, C.c_int64, C.c_float, C.c_double
+
+_lib.dgsm_default_params.argtypes = [C.POINTER(Params)]
+_lib.dgsm_default_relight_params.argtypes = [C.POINTER(RelightParams)]
+_lib.dgsm_create.argtypes = [C.c_int, C.POINTER(_vp)]
+_lib.dgsm_create.restype = C.c_int
+_lib.dgsm_destroy.argtypes = [_vp]
+_lib.dgsm_last_error.argtypes = [_vp]
+_lib.dgsm_last_error.restype = C.c_char_p
+_lib.dgsm_status_string.argtypes = [C.c_int]
+_lib.dgsm_status_string.restype = C.c_char_p
+_lib.dgsm_build.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i32,
+                            C.POINTER(Params), _vp, _vp]
+_lib.dgsm_get_build_stats.argtypes = [_vp, C.POINTER(BuildStats)]
+_lib.dgsm_bin.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i32,
+                          C.POINTER(Params), _vp, _vp, _i64, C.POINTER(_i64), _vp]
+_lib.dgsm_attenuate.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp,
+                                _i64, _vp, _f32, _vp, _vp, _vp]
+_lib.dgsm_sample_index.argtypes = [_vp, _vp, _i64, _vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp]
+_lib.sh_fit.argtypes = [_vp, _vp, _vp, _vp, _i64, _f64, _vp, _vp, _vp]
+_lib.sh_relight.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64,
+                            C.POINTER(RelightParams), _vp, _vp]
+_lib.dgsm_sync_status.argtypes = [_vp, _vp]
+for _fn in ("dgsm_build", "dgsm_get_build_stats", "dgsm_bin", "dgsm_attenuate",
+            "dgsm_sample_index", "sh_fit", "sh_relight", "dgsm_sync_status"):
+    getattr(_lib, _fn).restype = C.c_int
+
+
+class Context:
+    """Owns a dgsm_ctx (device workspace, status word) on one device."""
+
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        h = _vp()
+        rc = _lib.dgsm_create(self.device, C.byref(h))
+        if rc != DGSM_OK:
+            raise DGSMError(rc, "dgsm_create failed")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def check(self, rc: int):
+        if rc != DGSM_OK:
+            raise DGSMError(rc, _lib.dgsm_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dgsm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_ctx_lock = threading.Lock()
+_contexts: dict[int, Context] = {}
+
+
+def context(device: int | None = None) -> Context:
+    """The process-wide default context of `device` (current device if None)."""
+    if device is None:
+        device = torch.cuda.current_device()
+    with _ctx_lock:
+        if device not in _contexts:
+            _contexts[device] = Context(device)
+        return _contexts[device]
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _need(t, name, dtype=torch.float32, shape_last=None):
+    if t is None:
+        raise ValueError(f"{name} is required")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape_last is not None and (t.dim() != 2 or t.shape[1] != shape_last):
+        raise ValueError(f"{name} must have shape (n, {shape_last})")
+    return t
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def dgsm_build(means, scales, quats, opac, lights, H, W, radii, params=None, out=None,
+               ctx: Context | None = None, stream=None):
+    """Deep Gaussian Shadow Map build (Sec. 3.2): returns the atlas [L][K][H][W]."""
+    ctx = ctx or context(means.device.index)
+    _need(means, "means", shape_last=3)
+    _need(scales, "scales", shape_last=3)
+    _need(quats, "quats", shape_last=4)
+    _need(opac, "opac")
+    _need(lights, "lights", shape_last=3)
+    _need(radii, "radii")
+    p = params if isinstance(params, Params) else Params.make(**(params or {}))
+    L, K, n = lights.shape[0], radii.shape[0], means.shape[0]
+    if out is None:
+        out = torch.empty((L, K, H, W), dtype=TORCH_DTYPES[p.atlas_dtype], device=means.device)
+    _need(out, "out", TORCH_DTYPES[p.atlas_dtype])
+    if tuple(out.shape) != (L, K, H, W):
+        raise ValueError("out must have shape (L, K, H, W)")
+    ctx.check(_lib.dgsm_build(ctx.handle, _ptr(means), _ptr(scales), _ptr(quats), _ptr(opac), n,
+                              _ptr(lights), L, H, W, _ptr(radii), K, C.byref(p), _ptr(out),
+                              _stream(stream)))
+    return out
+
+
+def dgsm_get_build_stats(ctx: Context | None = None) -> dict:
+    ctx = ctx or context()
+    st = BuildStats()
+    ctx.check(_lib.dgsm_get_build_stats(ctx.handle, C.byref(st)))
+    return {"n_pairs": st.n_pairs, "rays_tested": st.rays_tested, "ray_evals": st.ray_evals,
+            "shell_evals": st.shell_evals}
+
+
+def dgsm_bin(means, scales, opac, lights, H, W, radii, params=None, ctx: Context | None = None,
+             stream=None):
+    """Light-space tile binning: sorted (keys, values) uint32->int64 tensors."""
+    ctx = ctx or context(means.device.index)
+    p = params if isinstance(params, Params) else Params.make(**(params or {}))
+    L, K, n = lights.shape[0], radii.shape[0], means.shape[0]
+    total = _i64(0)
+    args = (ctx.handle, _ptr(means), _ptr(scales), _ptr(opac), n, _ptr(lights), L, H, W,
+            _ptr(radii), K, C.byref(p))
+    rc = _lib.dgsm_bin(*args, None, None, 0, C.byref(total), _stream(stream))
+    if rc not in (DGSM_OK, 3):
+        ctx.check(rc)
+    P = total.value
+    keys = torch.empty(max(P, 1), dtype=torch.int32, device=means.device)
+    vals = torch.empty(max(P, 1), dtype=torch.int32, device=means.device)
+    ctx.check(_lib.dgsm_bin(*args, _ptr(keys), _ptr(vals), P, C.byref(total), _stream(stream)))
+    return keys[:P], vals[:P]
+
+
+def dgsm_attenuate(atlas, radii, lights, q_means, colors, atlas_dyn=None, light_w=None,
+                   direct_frac=1.0, out=None, want_T=False, ctx: Context | None = None,
+                   stream=None):
+    """Receiver attenuation (Sec. 3.3): colours (and T per light if want_T)."""
+    ctx = ctx or context(atlas.device.index)
+    dt = {torch.float32: 0, torch.float16: 1, torch.bfloat16: 2}[atlas.dtype]
+    _need(atlas, "atlas", atlas.dtype)
+    L, K, H, W = atlas.shape
+    _need(radii, "radii")
+    _need(lights, "lights", shape_last=3)
+    _need(q_means, "q_means", shape_last=3)
+    _need(colors, "colors", shape_last=3)
+    if atlas_dyn is not None:
+        _need(atlas_dyn, "atlas_dyn", atlas.dtype)
+        if atlas_dyn.shape != atlas.shape:
+            raise ValueError("atlas_dyn must match atlas")
+    if light_w is not None:
+        _need(light_w, "light_w")
+    Q = q_means.shape[0]
+    if out is None:
+        out = torch.empty_like(colors)
+    T = torch.empty((Q, L), dtype=torch.float32, device=atlas.device) if want_T else None
+    ctx.check(_lib.dgsm_attenuate(ctx.handle, _ptr(atlas), _ptr(atlas_dyn), dt, L, H, W,
+                                  _ptr(radii), K, _ptr(lights), _ptr(q_means), _ptr(colors), Q,
+                                  _ptr(light_w), float(direct_frac), _ptr(out), _ptr(T),
+                                  _stream(stream)))
+    return (out, T) if want_T else out
+
+
+def dgsm_sample_index(points, light, H, W, radii, ctx: Context | None = None, stream=None):
+    ctx = ctx or context(points.device.index)
+    _need(points, "points", shape_last=3)
+    n = points.shape[0]
+    idx = torch.empty((n, 5), dtype=torch.int32, device=points.device)
+    frac = torch.empty((n, 3), dtype=torch.float32, device=points.device)
+    ctx.check(_lib.dgsm_sample_index(ctx.handle, _ptr(points), n, _ptr(light), H, W, _ptr(radii),
+                                     radii.shape[0], _ptr(idx), _ptr(frac), _stream(stream)))
+    return idx, frac
+
+
+def sh_fit(dirs, rgb, w, lam=1e-3, want64=False, ctx: Context | None = None, stream=None):
+    """HDRI probe fit (Sec. 3.4, Eq. 7) in FP64 on the GPU: SH (3, 9) float32."""
+    ctx = ctx or context(dirs.device.index)
+    _need(dirs, "dirs", shape_last=3)
+    _need(rgb, "rgb", shape_last=3)
+    _need(w, "w")
+    sh = torch.empty((3, 9), dtype=torch.float32, device=dirs.device)
+    sh64 = torch.empty((3, 9), dtype=torch.float64, device=dirs.device) if want64 else None
+    ctx.check(_lib.sh_fit(ctx.handle, _ptr(dirs), _ptr(rgb), _ptr(w), dirs.shape[0], float(lam),
+                          _ptr(sh), _ptr(sh64), _stream(stream)))
+    return (sh, sh64) if want64 else sh
+
+
+def sh_relight(sh, means, quats, scales, colors, centroid, normals=None, params=None, out=None,
+               ctx: Context | None = None, stream=None):
+    """Per-Gaussian radiance transfer (Sec. 3.5, Eqs. 8-10): relit colours."""
+    ctx = ctx or context(colors.device.index)
+    _need(sh, "sh")
+    _need(colors, "colors", shape_last=3)
+    n = colors.shape[0]
+    if normals is None:
+        _need(means, "means", shape_last=3)
+        _need(quats, "quats", shape_last=4)
+        _need(scales, "scales", shape_last=3)
+        _need(centroid, "centroid")
+    else:
+        _need(normals, "normals", shape_last=3)
+    p = params if isinstance(params, RelightParams) else RelightParams.make(**(params or {}))
+    if out is None:
+        out = torch.empty_like(colors)
+    ctx.check(_lib.sh_relight(ctx.handle, _ptr(sh), _ptr(means), _ptr(quats), _ptr(scales),
+                              _ptr(normals), _ptr(centroid), _ptr(colors), n, C.byref(p), _ptr(out),
+                              _stream(stream)))
+    return out
+
+
+def dgsm_sync_status(ctx: Context | None = None, stream=None) -> int:
+    ctx = ctx or context()
+    rc = _lib.dgsm_sync_status(ctx.handle, _stream(stream))
+    return rc

@@ -1,0 +1,172 @@
+// attenuate.cu -- receiver attenuation by centre lookup (Sec. 3.3) on sm_103a.
+//
+// One thread per query Gaussian: per light, octahedral code of (x - o_l)
+// (exact single-precision index decisions, shared with dgsm_sample_index),
+// bilinear between texel centres with clamp-to-edge, linear between the two
+// shells bracketing t; the direct part of the colour is scaled by the
+// light-weighted transmittance.  The pass streams 36 bytes per query
+// (mean, colour in, colour out) and gathers 8 atlas taps per light.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "dgsm_internal.cuh"
+
+namespace dgsm {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ float load_T(const T *p);
+template <>
+__device__ __forceinline__ float load_T<float>(const float *p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float load_T<__half>(const __half *p) { return __half2float(__ldg(p)); }
+template <>
+__device__ __forceinline__ float load_T<__nv_bfloat16>(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ldg(p));
+}
+
+template <typename T>
+__device__ __forceinline__ float lookup(const T *__restrict__ A, int H, int W, int K,
+                                        const SampleIndex &s, const float *rs) {
+    const int j0 = min(max(s.bj, 0), W - 1), j1 = min(max(s.bj + 1, 0), W - 1);
+    const int i0 = min(max(s.bi, 0), H - 1), i1 = min(max(s.bi + 1, 0), H - 1);
+    int k0, k1;
+    float wt;
+    if (s.k < 0) { k0 = k1 = 0; wt = 0.0f; }
+    else if (s.k >= K - 1) { k0 = k1 = K - 1; wt = 0.0f; }
+    else { k0 = s.k; k1 = s.k + 1; wt = (s.t - rs[k0]) / (rs[k1] - rs[k0]); }
+    const int64_t plane = (int64_t)H * W;
+    const int64_t o00 = (int64_t)i0 * W + j0, o01 = (int64_t)i0 * W + j1;
+    const int64_t o10 = (int64_t)i1 * W + j0, o11 = (int64_t)i1 * W + j1;
+    const float fx = s.fx, fy = s.fy;
+    const T *P0 = A + k0 * plane;
+    float b0 = (1.0f - fy) * ((1.0f - fx) * load_T(P0 + o00) + fx * load_T(P0 + o01)) +
+               fy * ((1.0f - fx) * load_T(P0 + o10) + fx * load_T(P0 + o11));
+    if (k1 == k0) return b0;
+    const T *P1 = A + k1 * plane;
+    float b1 = (1.0f - fy) * ((1.0f - fx) * load_T(P1 + o00) + fx * load_T(P1 + o01)) +
+               fy * ((1.0f - fx) * load_T(P1 + o10) + fx * load_T(P1 + o11));
+    return (1.0f - wt) * b0 + wt * b1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) attenuate_kernel(
+    const T *__restrict__ atlas, const T *__restrict__ dyn, int L, int H, int W,
+    const float *__restrict__ radii, int K, const float *__restrict__ lights,
+    const float *__restrict__ qm, const float *cin, int64_t Q, const float *__restrict__ lw,
+    float wd, float *cout, float *__restrict__ Tout) {
+    __shared__ float rs[256];
+    __shared__ float ls[64 * 3];
+    __shared__ float wl[64];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) rs[k] = radii[k];
+    for (int k = threadIdx.x; k < 3 * L; k += blockDim.x) ls[k] = lights[k];
+    for (int k = threadIdx.x; k < L; k += blockDim.x) wl[k] = lw ? lw[k] : 1.0f / (float)L;
+    __syncthreads();
+    const int64_t lstride = (int64_t)K * H * W;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < Q;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const float px = __ldg(qm + 3 * q), py = __ldg(qm + 3 * q + 1), pz = __ldg(qm + 3 * q + 2);
+        float acc = 0.0f;
+        for (int l = 0; l < L; ++l) {
+            const SampleIndex s = sample_index(px, py, pz, ls[3 * l], ls[3 * l + 1], ls[3 * l + 2],
+                                               H, W, rs, K);
+            float Tl = 1.0f;
+            if (s.t != 0.0f) {
+                Tl = lookup(atlas + l * lstride, H, W, K, s, rs);
+                if (dyn) Tl *= lookup(dyn + l * lstride, H, W, K, s, rs);
+            }
+            if (Tout) Tout[q * L + l] = Tl;
+            acc = fmaf(wl[l], Tl, acc);
+        }
+        const float f = 1.0f - wd + wd * acc;
+        const float c0 = cin[3 * q], c1 = cin[3 * q + 1], c2 = cin[3 * q + 2];
+        cout[3 * q] = c0 * f;
+        cout[3 * q + 1] = c1 * f;
+        cout[3 * q + 2] = c2 * f;
+    }
+}
+
+__global__ void sample_index_kernel(const float *__restrict__ pts, int64_t n,
+                                    const float *__restrict__ light, int H, int W,
+                                    const float *__restrict__ radii, int K,
+                                    int32_t *__restrict__ idx_out, float *__restrict__ frac_out) {
+    __shared__ float rs[256];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) rs[k] = radii[k];
+    __syncthreads();
+    const float ox = light[0], oy = light[1], oz = light[2];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const SampleIndex s = sample_index(pts[3 * q], pts[3 * q + 1], pts[3 * q + 2], ox, oy, oz,
+                                           H, W, rs, K);
+        idx_out[5 * q] = s.ci;
+        idx_out[5 * q + 1] = s.cj;
+        idx_out[5 * q + 2] = s.bi;
+        idx_out[5 * q + 3] = s.bj;
+        idx_out[5 * q + 4] = s.k;
+        frac_out[3 * q] = s.fy;
+        frac_out[3 * q + 1] = s.fx;
+        frac_out[3 * q + 2] = s.t;
+    }
+}
+
+}  // namespace
+}  // namespace dgsm
+
+using namespace dgsm;
+
+extern "C" int dgsm_attenuate(dgsm_ctx *ctx, const void *atlas, const void *atlas_dyn,
+                              int32_t dtype, int32_t L, int32_t H, int32_t W, const float *radii,
+                              int32_t K, const float *lights, const float *q_means,
+                              const float *colors_in, int64_t n_q, const float *light_w,
+                              float direct_frac, float *colors_out, float *T_out, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (n_q < 0) return fail(ctx, DGSM_ERR_INVALID_ARG, "n_q < 0");
+    if (L < 1 || L > 64) return fail(ctx, DGSM_ERR_INVALID_ARG, "need 1..64 lights");
+    if (H < 1 || W < 1 || H > 4096 || W > 4096) return fail(ctx, DGSM_ERR_INVALID_ARG, "H, W must be in 1..4096");
+    if (K < 1 || K > 256) return fail(ctx, DGSM_ERR_INVALID_ARG, "K must be in 1..256");
+    if (dtype < DGSM_F32 || dtype > DGSM_BF16) return fail(ctx, DGSM_ERR_INVALID_ARG, "bad dtype");
+    if (!atlas || !radii || !lights) return fail(ctx, DGSM_ERR_INVALID_ARG, "null atlas, radii or lights");
+    if (n_q > 0 && (!q_means || !colors_in || !colors_out))
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "null query array");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    if (n_q == 0) return DGSM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int grid = (int)std::min<int64_t>((n_q + 255) / 256, (int64_t)ctx->num_sms * 8);
+    switch (dtype) {
+        case DGSM_F32:
+            attenuate_kernel<float><<<grid, 256, 0, s>>>((const float *)atlas, (const float *)atlas_dyn,
+                L, H, W, radii, K, lights, q_means, colors_in, n_q, light_w, direct_frac, colors_out, T_out);
+            break;
+        case DGSM_F16:
+            attenuate_kernel<__half><<<grid, 256, 0, s>>>((const __half *)atlas, (const __half *)atlas_dyn,
+                L, H, W, radii, K, lights, q_means, colors_in, n_q, light_w, direct_frac, colors_out, T_out);
+            break;
+        default:
+            attenuate_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)atlas,
+                (const __nv_bfloat16 *)atlas_dyn, L, H, W, radii, K, lights, q_means, colors_in, n_q,
+                light_w, direct_frac, colors_out, T_out);
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "attenuate_kernel");
+}
+
+extern "C" int dgsm_sample_index(dgsm_ctx *ctx, const float *points, int64_t n, const float *light,
+                                 int32_t H, int32_t W, const float *radii, int32_t K,
+                                 int32_t *idx_out, float *frac_out, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (n < 0 || H < 1 || W < 1 || H > 4096 || W > 4096 || K < 1 || K > 256)
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "bad size");
+    if (n > 0 && (!points || !light || !radii || !idx_out || !frac_out))
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "null pointer");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    if (n == 0) return DGSM_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8);
+    sample_index_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(points, n, light, H, W, radii, K,
+                                                                 idx_out, frac_out);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "sample_index_kernel");
+}

@@ -1,0 +1,139 @@
+// dgsm_internal.cuh -- shared declarations of libdgsm.so (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/dgsm.h"
+
+// ---------------------------------------------------------------------------
+// Context: device, error text, device status word, growable workspace.
+// ---------------------------------------------------------------------------
+enum WsSlot {
+    WS_BUILD_REC = 0,  // per (light, Gaussian) build record, 64 B
+    WS_BIN_REC,        // per (light, Gaussian) binning record, 32 B
+    WS_COUNTS,         // per (light, Gaussian) tile count / offset, u32
+    WS_SCAN_TMP,       // scan block sums
+    WS_CONES,          // tile + super-tile cones
+    WS_KEYS_A, WS_VALS_A, WS_KEYS_B, WS_VALS_B,
+    WS_HIST,           // radix histograms (+ their scan)
+    WS_RANGES,         // per (light, tile) start/end
+    WS_SH_PART,        // SH fit per-block partial sums
+    WS_NSLOTS
+};
+
+struct dgsm_ctx {
+    int device = 0;
+    std::string err;
+    void *ws[WS_NSLOTS] = {};
+    size_t ws_cap[WS_NSLOTS] = {};
+    int *d_status = nullptr;                 // first error code recorded by a kernel
+    unsigned long long *d_stats = nullptr;   // [0] rays tested, [1] ray evals, [2] shell evals, [3] pairs
+    unsigned long long *h_pinned = nullptr;  // pinned staging for small device->host reads
+    int num_sms = 148;
+};
+
+namespace dgsm {
+
+int fail(dgsm_ctx *ctx, int code, const std::string &msg);
+int cuda_fail(dgsm_ctx *ctx, cudaError_t e, const char *what);
+// Ensures workspace slot `slot` holds at least `bytes`; may synchronise the device.
+int ws_reserve(dgsm_ctx *ctx, int slot, size_t bytes, void **out);
+
+// Device-wide exclusive scan of n uint32 values (in may equal out).  Writes
+// the 64-bit total to *d_total (device).  Needs ctx workspace WS_SCAN_TMP.
+int scan_exclusive_u32(dgsm_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
+                       unsigned long long *d_total, cudaStream_t s);
+// Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
+// Sorted result ends in (*keys_io, *vals_io) (the pointers may be swapped
+// with the alternate buffers).
+int radix_sort_pairs(dgsm_ctx *ctx, uint32_t **keys_io, uint32_t **vals_io, uint32_t *keys_alt,
+                     uint32_t *vals_alt, int64_t n, int bits, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// IEEE single-precision operations that are never contracted or reordered:
+// every integer decision of the octahedral index and of the tile binning is
+// taken with these so that it is reproducible bit for bit on the CPU.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float xadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float xsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float xmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float xdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float xsqrt(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ float sgn_pos(float x) { return x >= 0.0f ? 1.0f : -1.0f; }
+
+__device__ __forceinline__ float xdot(float ax, float ay, float az, float bx, float by, float bz) {
+    return xadd(xadd(xmul(ax, bx), xmul(ay, by)), xmul(az, bz));
+}
+
+// Texel-centre coordinate (2j+1)/W - 1.
+__device__ __forceinline__ float xcentre(int j, int W) {
+    return xsub(xdiv((float)(2 * j + 1), (float)W), 1.0f);
+}
+
+// Octahedral decode (inverse of Eq. 6): undo the fold, z = 1-|u|-|v|, normalise.
+__device__ __forceinline__ float3 xdecode(float u, float v) {
+    float au = fabsf(u), av = fabsf(v);
+    float z = xsub(xsub(1.0f, au), av);
+    float x = u, y = v;
+    if (z < 0.0f) {
+        x = xmul(sgn_pos(u), xsub(1.0f, av));
+        y = xmul(sgn_pos(v), xsub(1.0f, au));
+    }
+    float n = xsqrt(xadd(xadd(xmul(x, x), xmul(y, y)), xmul(z, z)));
+    return make_float3(xdiv(x, n), xdiv(y, n), xdiv(z, n));
+}
+
+// Octahedral encode (Eq. 6) of the un-normalised vector v: q = v / |v|_1.
+__device__ __forceinline__ float2 xencode(float vx, float vy, float vz) {
+    float s = xadd(xadd(fabsf(vx), fabsf(vy)), fabsf(vz));
+    if (s == 0.0f) return make_float2(0.0f, 0.0f);
+    float qx = xdiv(vx, s), qy = xdiv(vy, s);
+    if (vz >= 0.0f) return make_float2(qx, qy);
+    return make_float2(xmul(sgn_pos(qx), xsub(1.0f, fabsf(qy))),
+                       xmul(sgn_pos(qy), xsub(1.0f, fabsf(qx))));
+}
+
+// Index decisions of one lookup (shared by attenuate and sample_index).
+struct SampleIndex {
+    int ci, cj;    // texel cell containing the point
+    int bi, bj;    // bilinear base tap (may be -1 or H-1/W-1 before clamping)
+    int k;         // #{radii <= t} - 1
+    float fy, fx;  // bilinear fractions
+    float t;       // distance to the light
+};
+
+__device__ __forceinline__ int count_le(const float *r, int K, float t) {
+    // number of radii <= t (radii strictly increasing)
+    int lo = 0, hi = K;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (r[mid] <= t) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ SampleIndex sample_index(float px, float py, float pz, float ox,
+                                                    float oy, float oz, int H, int W,
+                                                    const float *radii, int K) {
+    SampleIndex s;
+    float vx = xsub(px, ox), vy = xsub(py, oy), vz = xsub(pz, oz);
+    s.t = xsqrt(xadd(xadd(xmul(vx, vx), xmul(vy, vy)), xmul(vz, vz)));
+    float2 uv = xencode(vx, vy, vz);
+    float fu = xmul(xmul(xadd(uv.x, 1.0f), 0.5f), (float)W);
+    float fv = xmul(xmul(xadd(uv.y, 1.0f), 0.5f), (float)H);
+    float gx = xsub(fu, 0.5f), gy = xsub(fv, 0.5f);
+    float bj = floorf(gx), bi = floorf(gy);
+    s.cj = min(max((int)floorf(fu), 0), W - 1);
+    s.ci = min(max((int)floorf(fv), 0), H - 1);
+    s.bj = (int)bj;
+    s.bi = (int)bi;
+    s.fx = xsub(gx, bj);
+    s.fy = xsub(gy, bi);
+    s.k = count_le(radii, K, s.t) - 1;
+    return s;
+}
+
+}  // namespace dgsm

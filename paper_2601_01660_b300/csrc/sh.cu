@@ -1,0 +1,291 @@
+// sh.cu -- HDRI probe fit (Sec. 3.4, Eq. 7, FP64) and per-Gaussian radiance
+// transfer (Sec. 3.5, Eqs. 8-10) on sm_103a.
+#include <algorithm>
+
+#include "dgsm_internal.cuh"
+
+namespace dgsm {
+namespace {
+
+// Real SH basis to degree 2, index l^2 + l + m, no Condon-Shortley phase.
+// Normalisations sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!), times sqrt(2) for
+// m != 0, with the Cartesian forms of the associated Legendre factors.
+constexpr double SH_C0 = 0.28209479177387814;   // 1/2 sqrt(1/pi)
+constexpr double SH_C1 = 0.48860251190291992;   // sqrt(3/(4 pi))
+constexpr double SH_C2 = 1.09254843059207907;   // 1/2 sqrt(15/pi)
+constexpr double SH_C20 = 0.31539156525252005;  // 1/4 sqrt(5/pi)
+constexpr double SH_C22 = 0.54627421529603959;  // 1/4 sqrt(15/pi)
+
+template <typename F>
+__device__ __forceinline__ void sh9(F x, F y, F z, F *Y) {
+    Y[0] = F(SH_C0);
+    Y[1] = F(SH_C1) * y;
+    Y[2] = F(SH_C1) * z;
+    Y[3] = F(SH_C1) * x;
+    Y[4] = F(SH_C2) * x * y;
+    Y[5] = F(SH_C2) * y * z;
+    Y[6] = F(SH_C20) * (F(3) * z * z - F(1));
+    Y[7] = F(SH_C2) * x * z;
+    Y[8] = F(SH_C22) * (x * x - y * y);
+}
+
+constexpr int FIT_THREADS = 256;
+constexpr int FIT_NV = 45 + 27;  // upper triangle of B^T W B, then B^T W Y (9 x 3)
+
+// Per-block FP64 partial sums of the normal equations.
+__global__ void __launch_bounds__(FIT_THREADS) sh_fit_partial_kernel(
+    const float *__restrict__ dirs, const float *__restrict__ rgb, const float *__restrict__ w,
+    int64_t n, double *__restrict__ partials) {
+    double acc[FIT_NV];
+#pragma unroll
+    for (int v = 0; v < FIT_NV; ++v) acc[v] = 0.0;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        double Y[9];
+        sh9<double>(dirs[3 * s], dirs[3 * s + 1], dirs[3 * s + 2], Y);
+        const double ws = w[s];
+        int v = 0;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const double wa = ws * Y[a];
+#pragma unroll
+            for (int b = a; b < 9; ++b) {
+                acc[v] = fma(wa, Y[b], acc[v]);
+                ++v;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const double wa = ws * Y[a];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                acc[v] = fma(wa, (double)rgb[3 * s + c], acc[v]);
+                ++v;
+            }
+        }
+    }
+    __shared__ double red[FIT_THREADS / 32][FIT_NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < FIT_NV; ++v) {
+        double x = acc[v];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[warp][v] = x;
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < FIT_NV; v += blockDim.x) {
+        double x = 0.0;
+        for (int q = 0; q < FIT_THREADS / 32; ++q) x += red[q][v];
+        partials[(int64_t)blockIdx.x * FIT_NV + v] = x;
+    }
+}
+
+// One block: sum the partials in a fixed order, add lambda I, Cholesky-solve.
+__global__ void sh_fit_solve_kernel(const double *__restrict__ partials, int nblocks,
+                                    double lambda, float *__restrict__ sh_out,
+                                    double *__restrict__ sh64_out, int *__restrict__ status) {
+    __shared__ double sums[FIT_NV];
+    for (int v = threadIdx.x; v < FIT_NV; v += blockDim.x) {
+        double x = 0.0;
+        for (int b = 0; b < nblocks; ++b) x += partials[(int64_t)b * FIT_NV + v];
+        sums[v] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double G[9][9], R[9][3], Lm[9][9];
+    int v = 0;
+    for (int a = 0; a < 9; ++a)
+        for (int b = a; b < 9; ++b) {
+            G[a][b] = sums[v];
+            G[b][a] = sums[v];
+            ++v;
+        }
+    for (int a = 0; a < 9; ++a)
+        for (int c = 0; c < 3; ++c) R[a][c] = sums[v++];
+    for (int a = 0; a < 9; ++a) G[a][a] += lambda;
+    bool ok = true;
+    for (int i = 0; i < 9 && ok; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = G[i][j];
+            for (int k = 0; k < j; ++k) s -= Lm[i][k] * Lm[j][k];
+            if (i == j) {
+                if (!(s > 0.0)) { ok = false; break; }
+                Lm[i][i] = sqrt(s);
+            } else {
+                Lm[i][j] = s / Lm[j][j];
+            }
+        }
+    if (!ok) {
+        atomicCAS(status, 0, DGSM_ERR_NOT_SPD);
+        for (int k = 0; k < 27; ++k) {
+            sh_out[k] = 0.0f;
+            if (sh64_out) sh64_out[k] = 0.0;
+        }
+        return;
+    }
+    for (int c = 0; c < 3; ++c) {
+        double yv[9], xv[9];
+        for (int i = 0; i < 9; ++i) {
+            double s = R[i][c];
+            for (int k = 0; k < i; ++k) s -= Lm[i][k] * yv[k];
+            yv[i] = s / Lm[i][i];
+        }
+        for (int i = 8; i >= 0; --i) {
+            double s = yv[i];
+            for (int k = i + 1; k < 9; ++k) s -= Lm[k][i] * xv[k];
+            xv[i] = s / Lm[i][i];
+        }
+        for (int k = 0; k < 9; ++k) {
+            sh_out[9 * c + k] = (float)xv[k];
+            if (sh64_out) sh64_out[9 * c + k] = xv[k];
+        }
+    }
+}
+
+// Radiance transfer.  Each block first tabulates the lat-long quadrature
+// (direction, weight w_j, w_j L_c(w_j)) in shared memory, then contracts it
+// against the lobe of each of its Gaussians.
+__global__ void __launch_bounds__(256) relight_kernel(
+    const float *__restrict__ sh, const float *__restrict__ means, const float *__restrict__ quats,
+    const float *__restrict__ scales, const float *__restrict__ normals,
+    const float *__restrict__ centroid, const float *cin, int64_t N, float q, float gamma,
+    float t_max, float eps, int nth, int nph, float *cout) {
+    extern __shared__ float4 tab[];  // 2 per direction: (omega, w), (w L_r, w L_g, w L_b, 0)
+    __shared__ float shs[27];
+    const int M = nth * nph;
+    for (int k = threadIdx.x; k < 27; k += blockDim.x) shs[k] = sh[k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        const int it = j / nph, ip = j - it * nph;
+        float st, ct, sp, cp;
+        sincospif((it + 0.5f) / nth, &st, &ct);
+        sincospif(2.0f * (ip + 0.5f) / nph, &sp, &cp);
+        const float ox = st * cp, oy = st * sp, oz = ct;
+        float Y[9];
+        sh9<float>(ox, oy, oz, Y);
+        float Lc[3];
+        for (int c = 0; c < 3; ++c) {
+            float acc = 0.0f;
+            for (int k = 0; k < 9; ++k) acc = fmaf(shs[9 * c + k], Y[k], acc);
+            Lc[c] = acc;
+        }
+        tab[2 * j] = make_float4(ox, oy, oz, st);
+        tab[2 * j + 1] = make_float4(st * Lc[0], st * Lc[1], st * Lc[2], 0.0f);
+    }
+    __syncthreads();
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    if (!normals) { cx = centroid[0]; cy = centroid[1]; cz = centroid[2]; }
+    const bool lambert = q == 1.0f;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        float nx, ny, nz;
+        if (normals) {
+            nx = normals[3 * g]; ny = normals[3 * g + 1]; nz = normals[3 * g + 2];
+            const float inv = rsqrtf(nx * nx + ny * ny + nz * nz);
+            nx *= inv; ny *= inv; nz *= inv;
+        } else {
+            float qw = quats[4 * g], qx = quats[4 * g + 1], qy = quats[4 * g + 2], qz = quats[4 * g + 3];
+            const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+            qw *= qn; qx *= qn; qy *= qn; qz *= qn;
+            const float s0 = scales[3 * g], s1 = scales[3 * g + 1], s2 = scales[3 * g + 2];
+            int k = 0;
+            float sm = s0;
+            if (s1 < sm) { k = 1; sm = s1; }
+            if (s2 < sm) k = 2;
+            // column k of R(q): the Gaussian's k-th local axis
+            if (k == 0) {
+                nx = 1.f - 2.f * (qy * qy + qz * qz); ny = 2.f * (qx * qy + qw * qz); nz = 2.f * (qx * qz - qw * qy);
+            } else if (k == 1) {
+                nx = 2.f * (qx * qy - qw * qz); ny = 1.f - 2.f * (qx * qx + qz * qz); nz = 2.f * (qy * qz + qw * qx);
+            } else {
+                nx = 2.f * (qx * qz + qw * qy); ny = 2.f * (qy * qz - qw * qx); nz = 1.f - 2.f * (qx * qx + qy * qy);
+            }
+            const float side = nx * (means[3 * g] - cx) + ny * (means[3 * g + 1] - cy) +
+                               nz * (means[3 * g + 2] - cz);
+            if (side < 0.0f) { nx = -nx; ny = -ny; nz = -nz; }
+        }
+        float num0 = 0.f, num1 = 0.f, num2 = 0.f, den = 0.f;
+        if (lambert) {
+#pragma unroll 4
+            for (int j = 0; j < M; ++j) {
+                const float4 a = tab[2 * j], b = tab[2 * j + 1];
+                const float S = fmaxf(fmaf(a.x, nx, fmaf(a.y, ny, a.z * nz)), 0.0f);
+                den = fmaf(S, a.w, den);
+                num0 = fmaf(S, b.x, num0);
+                num1 = fmaf(S, b.y, num1);
+                num2 = fmaf(S, b.z, num2);
+            }
+        } else {
+            for (int j = 0; j < M; ++j) {
+                const float4 a = tab[2 * j], b = tab[2 * j + 1];
+                const float c = fmaf(a.x, nx, fmaf(a.y, ny, a.z * nz));
+                const float S = c > 0.0f ? exp2f(q * log2f(c)) : 0.0f;
+                den = fmaf(S, a.w, den);
+                num0 = fmaf(S, b.x, num0);
+                num1 = fmaf(S, b.y, num1);
+                num2 = fmaf(S, b.z, num2);
+            }
+        }
+        const float inv = 1.0f / (den + eps);
+        const float sc0 = fminf(fmaxf(num0 * inv, 0.0f), t_max);
+        const float sc1 = fminf(fmaxf(num1 * inv, 0.0f), t_max);
+        const float sc2 = fminf(fmaxf(num2 * inv, 0.0f), t_max);
+        const float c0 = cin[3 * g], c1 = cin[3 * g + 1], c2 = cin[3 * g + 2];
+        cout[3 * g] = fmaxf(gamma * c0 * sc0, 0.0f);
+        cout[3 * g + 1] = fmaxf(gamma * c1 * sc1, 0.0f);
+        cout[3 * g + 2] = fmaxf(gamma * c2 * sc2, 0.0f);
+    }
+}
+
+}  // namespace
+}  // namespace dgsm
+
+using namespace dgsm;
+
+extern "C" int sh_fit(dgsm_ctx *ctx, const float *dirs, const float *rgb, const float *w,
+                      int64_t n, double lambda, float *sh_out, double *sh64_out, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (n < 1 || !dirs || !rgb || !w || !sh_out) return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_fit: need n >= 1 and non-null arrays");
+    if (!(lambda >= 0.0)) return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_fit: lambda must be >= 0");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nblocks = (int)std::min<int64_t>((n + FIT_THREADS - 1) / FIT_THREADS, (int64_t)ctx->num_sms);
+    void *part;
+    int rc = ws_reserve(ctx, WS_SH_PART, sizeof(double) * FIT_NV * nblocks, &part);
+    if (rc) return rc;
+    sh_fit_partial_kernel<<<nblocks, FIT_THREADS, 0, s>>>(dirs, rgb, w, n, (double *)part);
+    sh_fit_solve_kernel<<<1, 128, 0, s>>>((const double *)part, nblocks, lambda, sh_out, sh64_out,
+                                          ctx->d_status);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "sh_fit kernels");
+}
+
+extern "C" int sh_relight(dgsm_ctx *ctx, const float *sh, const float *means, const float *quats,
+                          const float *scales, const float *normals, const float *centroid,
+                          const float *colors_in, int64_t n, const dgsm_relight_params *params,
+                          float *colors_out, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    dgsm_relight_params p;
+    if (params) p = *params; else dgsm_default_relight_params(&p);
+    if (n < 0) return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_relight: n < 0");
+    if (p.n_theta < 1 || p.n_phi < 1 || (int64_t)p.n_theta * p.n_phi > 6144)
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_relight: need 1 <= n_theta * n_phi <= 6144");
+    if (!(p.q > 0.0f) || !(p.eps >= 0.0f) || !(p.t_max >= 0.0f))
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_relight: need q > 0, eps >= 0, t_max >= 0");
+    if (!sh) return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_relight: null sh");
+    if (n > 0 && (!colors_in || !colors_out || (!normals && (!means || !quats || !scales || !centroid))))
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_relight: null Gaussian array");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    if (n == 0) return DGSM_OK;
+    const size_t smem = (size_t)p.n_theta * p.n_phi * 2 * sizeof(float4);
+    e = cudaFuncSetAttribute(relight_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "relight smem attribute");
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 2);
+    relight_kernel<<<grid, 256, smem, (cudaStream_t)stream>>>(
+        sh, means, quats, scales, normals, centroid, colors_in, n, p.q, p.gamma, p.t_max, p.eps,
+        p.n_theta, p.n_phi, colors_out);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "relight_kernel");
+}

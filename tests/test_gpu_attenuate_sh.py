@@ -1,0 +1,176 @@
+"""GPU parity of receiver attenuation (Sec. 3.3), the FP32 index decisions,
+the FP64 SH probe fit (Sec. 3.4) and the radiance transfer (Sec. 3.5)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2601_01660_b300 import scenes
+
+from gpu_util import dev, scene_to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nat():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2601_01660_b300 import native
+    return native()
+
+
+@pytest.mark.parametrize("H,W", [(64, 64), (256, 256), (512, 512), (48, 80)])
+def test_round_trip_every_texel(nat, orc, H, W):
+    dirs = np.array([orc.texel_dir(i, j, H, W) for i in range(H) for j in range(W)])
+    pts = (dirs * 3.0).astype(np.float32)
+    radii = scenes.radii_linear(0.1, 8, 4)
+    idx, _ = nat.dgsm_sample_index(dev(pts), dev([0, 0, 0]), H, W, dev(radii))
+    idx = idx.cpu().numpy()
+    ii, jj = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    assert np.array_equal(idx[:, 0], ii.ravel()) and np.array_equal(idx[:, 1], jj.ravel())
+
+
+def test_sample_index_bit_exact(nat, orc):
+    rng = np.random.default_rng(3)
+    H, W = 96, 128
+    radii = scenes.radii_geometric(0.05, 12, 33)
+    o = np.float32([0.3, -0.2, 1.0])
+    pts = np.float32(rng.uniform(-6, 6, (20000, 3)))
+    pts[:50] = o                                   # at the light
+    pts[50:100, 2] = o[2]                          # on the fold plane z = o_z
+    pts[100:150, 0] = o[0]                         # sgn(0) cases
+    pts[150:200] = o + radii[rng.integers(0, 33, 50)][:, None] * np.float32([0, 0, 1])  # on shells
+    oi, of = orc.f32_sample_index(pts, o, H, W, radii)
+    gi, gf = nat.dgsm_sample_index(dev(pts), dev(o), H, W, dev(radii))
+    assert np.array_equal(gi.cpu().numpy(), oi)
+    assert np.array_equal(gf.cpu().numpy().view(np.uint32), of.view(np.uint32))
+
+
+def _attenuate_both(nat, orc, atlas64, radii, lights, qm, col, **kw):
+    dyn = kw.pop("atlas_dyn", None)
+    lw = kw.get("light_w")
+    dtype = kw.pop("dtype", torch.float32)
+    at = dev(atlas64, dtype)
+    dy = dev(dyn, dtype) if dyn is not None else None
+    out, T = nat.dgsm_attenuate(at, dev(radii), dev(lights), dev(qm), dev(col), atlas_dyn=dy,
+                                light_w=dev(lw) if lw is not None else None,
+                                direct_frac=kw.get("direct_frac", 1.0), want_T=True)
+    ref, Tref = orc.attenuate(at.double().cpu().numpy(), radii, lights, qm, col,
+                              atlas_dyn=dy.double().cpu().numpy() if dy is not None else None,
+                              light_w=lw, direct_frac=kw.get("direct_frac", 1.0), want_T=True)
+    return out.double().cpu().numpy(), T.double().cpu().numpy(), ref, Tref
+
+
+def test_attenuate_matches_oracle(nat, orc):
+    rng = np.random.default_rng(5)
+    L, K, H, W = 3, 9, 37, 53
+    radii = scenes.radii_geometric(0.1, 9, K)
+    atlas = np.sort(rng.random((L, K, H, W)), axis=1)[:, ::-1].copy()
+    lights = np.float32([[0, 0, 0], [1, -0.5, 0.5], [-2, 1, 3]])
+    qm = np.float32(rng.uniform(-10, 10, (30000, 3)))
+    qm[:20] = lights[0]
+    col = np.float32(rng.random((30000, 3)))
+    out, T, ref, Tref = _attenuate_both(nat, orc, atlas, radii, lights, qm, col)
+    assert np.abs(T - Tref).max() <= 1e-5
+    assert np.abs(out - ref).max() <= 1e-5
+    dyn = np.sort(rng.random((L, K, H, W)), axis=1)[:, ::-1].copy()
+    out, T, ref, Tref = _attenuate_both(nat, orc, atlas, radii, lights, qm, col, atlas_dyn=dyn,
+                                        light_w=np.float32([0.5, 0.3, 0.2]), direct_frac=0.7)
+    assert np.abs(T - Tref).max() <= 1e-5
+    assert np.abs(out - ref).max() <= 1e-5
+
+
+@pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
+def test_attenuate_half_atlas(nat, orc, dtype):
+    rng = np.random.default_rng(6)
+    atlas = np.sort(rng.random((1, 6, 32, 32)), axis=1)[:, ::-1].copy()
+    radii = scenes.radii_linear(0.2, 6, 6)
+    qm = np.float32(rng.uniform(-5, 5, (5000, 3)))
+    col = np.float32(rng.random((5000, 3)))
+    out, T, ref, Tref = _attenuate_both(nat, orc, atlas, radii, np.float32([[0, 0, 0]]), qm, col,
+                                        dtype=dtype)
+    assert np.abs(T - Tref).max() <= 1e-5
+
+
+def test_attenuate_in_place_and_empty(nat):
+    atlas = torch.full((1, 4, 8, 8), 0.5, device="cuda")
+    radii = dev(scenes.radii_linear(0.1, 8, 4))
+    lights = dev([[0, 0, 0]])
+    col = torch.rand(100, 3, device="cuda")
+    before = col.clone()
+    qm = torch.rand(100, 3, device="cuda") + 1
+    nat.dgsm_attenuate(atlas, radii, lights, qm, col, out=col)
+    assert torch.allclose(col, before * 0.5)
+    e = torch.empty(0, 3, device="cuda")
+    assert nat.dgsm_attenuate(atlas, radii, lights, e, e).shape == (0, 3)
+
+
+def test_end_to_end_cube20k(nat, orc):
+    """Build then attenuate the 20k-query cube workload; compare with the oracle
+    sampling the GPU atlas (the build itself is checked separately)."""
+    wl = scenes.workload("cube20k")
+    occ, q, lights, radii = wl["occluders"], wl["queries"], wl["lights"], wl["radii"]
+    d = scene_to_dev(occ)
+    atlas = nat.dgsm_build(d["means"], d["scales"], d["quats"], d["opac"], dev(lights), 64, 64,
+                           dev(radii))
+    out, T = nat.dgsm_attenuate(atlas, dev(radii), dev(lights), dev(q.means), dev(q.colors),
+                                want_T=True)
+    ref, Tref = orc.attenuate(atlas.double().cpu().numpy(), radii, lights, q.means, q.colors,
+                              want_T=True)
+    assert np.abs(T.double().cpu().numpy() - Tref).max() <= 1e-5
+    assert np.abs(out.double().cpu().numpy() - ref).max() <= 1e-5
+
+
+def test_sh_fit_matches_oracle(nat, orc):
+    D, Y, w = scenes.cubemap_samples(64, seed=5)
+    for lam in (1e-3, 0.0, 0.3):
+        sh, sh64 = nat.sh_fit(dev(D), dev(Y), dev(w), lam=lam, want64=True)
+        ref = orc.sh_fit(D, Y, w, lam=lam)
+        np.testing.assert_allclose(sh64.cpu().numpy(), ref, rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(sh.cpu().numpy(), ref, rtol=1e-6, atol=1e-7)
+
+
+def test_sh_fit_not_spd_reported(nat):
+    D = np.float32(np.tile([[0, 0, 1.0]], (10, 1)))
+    Y = np.float32(np.ones((10, 3)))
+    w = np.float32(np.ones(10))
+    sh = nat.sh_fit(dev(D), dev(Y), dev(w), lam=0.0)
+    assert nat.dgsm_sync_status() == 6
+    assert bool((sh == 0).all())
+    assert nat.dgsm_sync_status() == 0
+
+
+def _relight_check(nat, orc, sc, sh, centroid, params, tol=1e-3, normals=None):
+    d = scene_to_dev(sc)
+    out = nat.sh_relight(dev(sh), d["means"], d["quats"], d["scales"], d["colors"], dev(centroid),
+                         normals=dev(normals) if normals is not None else None, params=params)
+    got = out.double().cpu().numpy()
+    ref = orc.relight(sh, sc, centroid, normals=normals, **params)
+    err = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-6)
+    bad = err.max(axis=1) > tol
+    if normals is None and bad.any():
+        # a normal whose side of the centroid is decided within rounding has two
+        # valid results: accept the oracle's answer with the flipped normal
+        for g in np.nonzero(bad)[0]:
+            n = orc.gauss_normal(sc.means[g], sc.scales[g], sc.quats[g], centroid)
+            side = abs(n @ (sc.means[g].astype(np.float64) - centroid))
+            assert side < 1e-5 * (1 + np.linalg.norm(sc.means[g] - centroid)), (g, err[g])
+            s = orc.transfer_scale(sh, -n, q=params.get("q", 1.0), t_max=params.get("t_max", 10.0),
+                                   eps=params.get("eps", 1e-8))
+            alt = np.maximum(0, params.get("gamma", 1.0) * sc.colors[g].astype(np.float64) * s)
+            assert np.all(np.abs(got[g] - alt) <= tol * np.maximum(np.abs(alt), 1e-6))
+    return got
+
+
+def test_relight_matches_oracle(nat, orc):
+    rng = np.random.default_rng(8)
+    av = scenes.avatar_body(rng, 20_000)
+    D, Y, w = scenes.cubemap_samples(32, seed=5)
+    sh = orc.sh_fit(D, Y, w)
+    cen = av.means.astype(np.float64).mean(0)
+    _relight_check(nat, orc, av, sh, cen, {})
+    _relight_check(nat, orc, av, sh, cen, {"q": 3.0, "gamma": 0.8, "t_max": 2.0})
+    nrm = rng.normal(size=(av.n, 3)).astype(np.float32)
+    _relight_check(nat, orc, av, sh, cen, {"n_theta": 16, "n_phi": 48}, normals=nrm)

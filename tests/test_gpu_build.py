@@ -1,0 +1,144 @@
+"""GPU parity of the DGSM build (Sec. 3.2) and its binning through the C ABI,
+against the FP64 oracle and the oracle's FP32 binning specification."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2601_01660_b300 import scenes
+
+from gpu_util import dev, scene_to_dev, texel_sample
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-4             # |dT| for float32 storage
+TOL_F16 = 2e-3             # |dT| for float16 storage (half ulp 2^-12 near 1, plus build error)
+TOL_BF16 = 2.0 ** -9 + 1e-4  # bfloat16 storage: half ulp of T in [0.5, 1) plus build error
+
+
+@pytest.fixture(scope="module")
+def nat():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2601_01660_b300 import native
+    return native()
+
+
+def _build(nat, sc, lights, H, W, radii, **params):
+    d = scene_to_dev(sc)
+    return nat.dgsm_build(d["means"], d["scales"], d["quats"], d["opac"], dev(lights), H, W,
+                          dev(radii), params=params)
+
+
+@pytest.mark.parametrize("H,W,tile,nl", [(32, 32, 8, 1), (44, 60, 8, 2), (64, 48, 16, 1),
+                                         (40, 40, 4, 3), (128, 128, 8, 1)])
+def test_binning_bit_exact(nat, orc, H, W, tile, nl):
+    sc = scenes.cube_scene(2500, seed=31 + H, log_s_mean=math.log(0.06))
+    lights = np.float32([[0, 0, 0], [0.4, -0.3, 0.5], [-1, 1, 2.5]])[:nl]
+    radii = scenes.radii_linear(0.1, 8, 10)
+    ko, vo = orc.f32_bin(sc, lights, H, W, radii, eps=1e-7, tile=tile)
+    d = scene_to_dev(sc)
+    kg, vg = nat.dgsm_bin(d["means"], d["scales"], d["opac"], dev(lights), H, W, dev(radii),
+                          params=dict(tile=tile))
+    assert kg.numel() == ko.size
+    assert np.array_equal(kg.cpu().numpy().astype(np.uint32), ko)
+    assert np.array_equal(vg.cpu().numpy().astype(np.uint32), vo)
+
+
+def test_binning_light_inside_and_beyond_shells(nat, orc):
+    """Gaussians around the light (bound to every tile) and beyond the last
+    shell (bound nowhere) follow the specification too."""
+    sc = scenes.cube_scene(1500, seed=41, centre=(0, 0, 0), side=12.0, log_s_mean=math.log(0.2))
+    lights = np.float32([[0.05, 0.0, -0.02]])
+    radii = scenes.radii_linear(0.1, 3.0, 6)
+    ko, vo = orc.f32_bin(sc, lights, 24, 24, radii)
+    d = scene_to_dev(sc)
+    kg, vg = nat.dgsm_bin(d["means"], d["scales"], d["opac"], dev(lights), 24, 24, dev(radii))
+    assert np.array_equal(kg.cpu().numpy().astype(np.uint32), ko)
+    assert np.array_equal(vg.cpu().numpy().astype(np.uint32), vo)
+
+
+@pytest.mark.parametrize("H,W,tile,K", [(44, 60, 8, 12), (32, 32, 16, 7), (20, 36, 4, 5)])
+def test_build_matches_oracle_every_voxel(nat, orc, H, W, tile, K):
+    sc = scenes.cube_scene(3000, seed=5 + K)
+    lights = np.float32([[0, 0, 0], [0.3, -0.2, 0.4]])
+    radii = scenes.radii_linear(0.1, 8, K)
+    T_ref = orc.build_atlas(sc, lights, H, W, radii)
+    T = _build(nat, sc, lights, H, W, radii, tile=tile).double().cpu().numpy()
+    err = np.abs(T - T_ref)
+    assert err.max() <= TOL_F32, (err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+@pytest.mark.parametrize("dtype,tol", [("f16", TOL_F16), ("bf16", TOL_BF16)])
+def test_build_half_storage(nat, orc, dtype, tol):
+    sc = scenes.cube_scene(2000, seed=77)
+    lights = np.float32([[0, 0, 0]])
+    radii = scenes.radii_geometric(0.05, 12, 9)
+    T_ref = orc.build_atlas(sc, lights, 40, 40, radii)
+    T = _build(nat, sc, lights, 40, 40, radii, atlas_dtype=dtype)
+    assert T.dtype == {"f16": torch.float16, "bf16": torch.bfloat16}[dtype]
+    assert np.abs(T.double().cpu().numpy() - T_ref).max() <= tol
+
+
+def test_build_empty_and_transparent(nat):
+    radii = scenes.radii_linear(0.1, 8, 5)
+    sc = scenes.cube_scene(0, seed=0)
+    T = _build(nat, sc, np.float32([[0, 0, 0]]), 16, 24, radii)
+    assert T.shape == (1, 5, 16, 24) and bool((T == 1).all())
+    sc = scenes.cube_scene(500, seed=1)
+    sc.opac[:] = 0
+    T = _build(nat, sc, np.float32([[0, 0, 0]]), 16, 16, radii)
+    assert bool((T == 1).all())
+
+
+def test_build_bounds_and_monotone(nat):
+    sc = scenes.cube_scene(20_000, seed=0)
+    T = _build(nat, sc, np.float32([[0, 0, 0]]), 64, 64, scenes.radii_linear(0.1, 8, 16))
+    assert bool(((T >= 0) & (T <= 1)).all())
+    assert bool((T[:, 1:] <= T[:, :-1]).all())
+
+
+def test_build_cube20k_sampled(nat, orc):
+    """The 20k-Gaussian cube workload at full size (64x64x16, one light at
+    the origin), checked on 256 random texels x all shells."""
+    wl = scenes.workload("cube20k")
+    sc, lights, radii = wl["occluders"], wl["lights"], wl["radii"]
+    T = _build(nat, sc, lights, 64, 64, radii).double().cpu().numpy()
+    lij = texel_sample(np.random.default_rng(0), 1, 64, 64, 256)
+    tau = orc.build_tau_texels(sc, lights, 64, 64, radii, lij)
+    got = T[lij[:, 0], :, lij[:, 1], lij[:, 2]]
+    assert np.abs(got - np.exp(-tau)).max() <= TOL_F32
+
+
+def test_build_stats_are_consistent(nat):
+    sc = scenes.cube_scene(5000, seed=3)
+    _build(nat, sc, np.float32([[0, 0, 0]]), 64, 64, scenes.radii_linear(0.1, 8, 16))
+    st = nat.dgsm_get_build_stats()
+    assert st["n_pairs"] > 0
+    assert 0 < st["ray_evals"] <= st["rays_tested"] <= 64 * st["n_pairs"]
+
+
+def test_nonfinite_input_is_reported(nat):
+    sc = scenes.cube_scene(100, seed=2)
+    sc.means[7, 1] = np.nan
+    with pytest.raises(nat.DGSMError) as ei:
+        _build(nat, sc, np.float32([[0, 0, 0]]), 16, 16, scenes.radii_linear(0.1, 8, 4))
+    assert ei.value.code == 5
+    sc = scenes.cube_scene(100, seed=2)
+    sc.scales[3, 0] = 0.0
+    with pytest.raises(nat.DGSMError):
+        _build(nat, sc, np.float32([[0, 0, 0]]), 16, 16, scenes.radii_linear(0.1, 8, 4))
+    # the context stays usable
+    sc = scenes.cube_scene(100, seed=2)
+    T = _build(nat, sc, np.float32([[0, 0, 0]]), 16, 16, scenes.radii_linear(0.1, 8, 4))
+    assert bool(torch.isfinite(T).all())
+
+
+def test_bad_arguments_are_rejected(nat):
+    sc = scenes.cube_scene(10, seed=2)
+    with pytest.raises(nat.DGSMError) as ei:
+        _build(nat, sc, np.float32([[0, 0, 0]]), 16, 16, scenes.radii_linear(0.1, 8, 4), tile=5)
+    assert ei.value.code == 1
+    with pytest.raises(nat.DGSMError):
+        _build(nat, sc, np.float32([[0, 0, 0]]), 16, 16, scenes.radii_linear(0.1, 8, 4), chunk=4)

@@ -1,0 +1,436 @@
+#!/usr/bin/env python3
+"""Benchmark of the Deep Gaussian Shadow Map hot path on B300.
+
+One step = one pass of every hot-path row over the indoor-room workload
+(1.5M room Gaussians + a 100k-Gaussian avatar, one light at 2.8 m):
+DGSM build of a 512x512x64 atlas (prep, light-space tile binning, radix sort,
+closed-form tile kernel), attenuation of all 1.6M Gaussians, FP64 SH probe fit
+on 6x64^2 cubemap samples, and the radiance transfer of the avatar.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  metric = Gaussian-ray evaluations per second over the
+whole step (an evaluation is one texel ray x one Gaussian whose culling
+ellipsoid that ray cuts at t > 0, i.e. the pairs the method must evaluate);
+the line also carries ms per 512^2x64 build and attenuated Gaussians/s.
+Under torchrun each rank runs its own light (independent problems: weak
+scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gaussian-ray evals/s and ms per 512²×64 DGSM build; attenuated Gaussians/s"
+UNIT = "Gaussian-ray evals/s"
+WORKLOAD = "room1p6m"
+
+# Algorithmic single-precision work of the build tile kernel, per unit
+# (arithmetic a minimal implementation of the closed form must issue):
+#   per Gaussian-ray evaluation: whitened direction 9, a 3, d'.w' 3, w' x d' 6,
+#     |.|^2 3, m^2 and s* 2, setup of the erfc terms 7            -> 33 FP32 + 3 MUFU
+#   per shell evaluation (Eq. 3 at one radius): argument 1, erfc polynomial
+#     and its reciprocal 6, exponent 2, scaling 2, select/difference/accumulate 5
+#                                                                 -> 16 FP32 + 2 MUFU
+#   per voxel: prefix sum, clamp, exp                             ->  3 FP32 + 1 MUFU
+FP32_PER_EVAL, MUFU_PER_EVAL = 33, 3
+FP32_PER_SHELL, MUFU_PER_SHELL = 16, 2
+FP32_PER_VOXEL, MUFU_PER_VOXEL = 3, 1
+SMS = 148
+FP32_LANES_PER_SM = 128   # FP32 results per SM per clock
+MUFU_LANES_PER_SM = 16    # special-function (MUFU) results per SM per clock
+L2_BYTES = 126 * 1024 * 1024
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", self.gpu], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def load_workload(rank: int):
+    from paper_2601_01660_b300 import scenes
+    wl = scenes.workload(WORKLOAD)
+    lights = wl["lights"].copy()
+    lights[:, 0] += 0.25 * rank     # each rank: its own light, an independent problem
+    wl["lights"] = lights
+    return wl
+
+
+# ----------------------------------------------------------------------------- ours
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2601_01660_b300 import native
+    nat = native()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    wl = load_workload(rank)
+    sc = wl["occluders"]
+    av_slice = sc.meta["avatar"]
+    a0, a1 = av_slice.start, av_slice.stop
+    H, W, radii_np, lights_np = wl["H"], wl["W"], wl["radii"], wl["lights"]
+    K, L, N = radii_np.shape[0], lights_np.shape[0], sc.n
+    D_np, Y_np, w_np = wl["cubemap"]
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)
+    means, scales, quats, opac, colors = (t(getattr(sc, k)) for k in
+                                          ("means", "scales", "quats", "opac", "colors"))
+    lights, radii = t(lights_np), t(radii_np)
+    D, Y, w = t(D_np), t(Y_np), t(w_np)
+    atlas = torch.empty((L, K, H, W), dtype=torch.float32, device=dev)
+    out = torch.empty_like(colors)
+    sh = None
+    stream = torch.cuda.current_stream()
+    ev_att = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    att_ms = []
+
+    def step(time_att=False):
+        nat.dgsm_build(means, scales, quats, opac, lights, H, W, radii, out=atlas)
+        if time_att:
+            ev_att[0].record(stream)
+        nat.dgsm_attenuate(atlas, radii, lights, means, colors, out=out)
+        if time_att:
+            ev_att[1].record(stream)
+        s = nat.sh_fit(D, Y, w)
+        cen = nat.dgsm_weighted_centroid(means[a0:a1], opac[a0:a1])
+        nat.sh_relight(s, means[a0:a1], quats[a0:a1], scales[a0:a1], out[a0:a1], cen,
+                       out=out[a0:a1])
+        return s
+
+    for _ in range(args.warmup):
+        sh = step()
+    torch.cuda.synchronize()
+    stats = nat.dgsm_get_build_stats()
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    nat.dgsm_set_profiling(True)
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]
+    with ClockSampler(gpu_index) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()   # L2 flushed between steps, outside the timed events
+            starts[k].record(stream)
+            sh = step(time_att=True)
+            ends[k].record(stream)
+            torch.cuda.synchronize()
+            att_ms.append(ev_att[0].elapsed_time(ev_att[1]))
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    prof = nat.dgsm_profile_collect()
+    nat.dgsm_set_profiling(False)
+    clocks = clk.summary()
+    total_ms = float(sum(step_ms))
+    evals = stats["ray_evals"]
+    if dist is not None:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        ev = torch.tensor([float(evals)], dtype=torch.float64, device=dev)
+        dist.all_reduce(ev, op=dist.ReduceOp.SUM)
+        evals_all = float(ev.item())
+    else:
+        evals_all = float(evals)
+    ms_per_step = total_ms / args.steps
+    value = evals_all * args.steps / (total_ms * 1e-3)
+
+    # ---- roofline of the dominant kernel (closed-form tile kernel) ----------
+    tiles_ms = statistics.mean(p[1] for p in prof) if prof else None
+    binning_ms = statistics.mean(p[0] for p in prof) if prof else None
+    voxels = L * K * H * W
+    fp32 = FP32_PER_EVAL * evals + FP32_PER_SHELL * stats["shell_evals"] + FP32_PER_VOXEL * voxels
+    mufu = MUFU_PER_EVAL * evals + MUFU_PER_SHELL * stats["shell_evals"] + MUFU_PER_VOXEL * voxels
+    f_peak = (clocks.get("sm_max_mhz") or 2032.0) * 1e6
+    fp32_peak = SMS * FP32_LANES_PER_SM * f_peak / 1e12
+    mufu_peak = SMS * MUFU_LANES_PER_SM * f_peak / 1e12
+    fp32_ach = fp32 / (tiles_ms * 1e-3) / 1e12
+    mufu_ach = mufu / (tiles_ms * 1e-3) / 1e12
+    if fp32_ach / fp32_peak >= mufu_ach / mufu_peak:
+        bound_pipe, ach, peak = "fp32", fp32_ach, fp32_peak
+    else:
+        bound_pipe, ach, peak = "mufu", mufu_ach, mufu_peak
+    roofline = {"bound": "alu", "kernel": "build_tiles_kernel", "pipe": bound_pipe,
+                "achieved": round(ach, 4), "peak": round(peak, 4), "unit": "Tops/s",
+                "frac": round(ach / peak, 4), "traffic": None,
+                "peak_source": "derived: 148 SMs x lanes/clk x max SM clock (unit counts), of derived",
+                "pipes": {"fp32": {"achieved": round(fp32_ach, 4), "peak": round(fp32_peak, 4),
+                                   "frac": round(fp32_ach / fp32_peak, 4)},
+                          "mufu": {"achieved": round(mufu_ach, 4), "peak": round(mufu_peak, 4),
+                                   "frac": round(mufu_ach / mufu_peak, 4)}},
+                "kernel_ms": round(tiles_ms, 4)}
+
+    # ---- attenuation roofline (HBM) -----------------------------------------
+    att = statistics.median(att_ms)
+    att_bytes = N * 36 + voxels * 4
+    hbm_peak = _measured_peak("hbm_gbs", 6400.0)
+    attenuate = {"ms": round(att, 5), "gaussians_per_s": N / (att * 1e-3),
+                 "achieved_gbs": round(att_bytes / (att * 1e-3) / 1e9, 1),
+                 "peak_gbs": hbm_peak, "frac": round(att_bytes / (att * 1e-3) / 1e9 / hbm_peak, 4),
+                 "algorithmic_bytes": att_bytes}
+
+    # ---- end to end through the host-buffer C entry point --------------------
+    e2e = run_e2e(nat, wl, args, evals) if not args.no_e2e else None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "gaussians": N, "avatar_gaussians": a1 - a0,
+                   "lights_per_rank": L, "atlas": [H, W, K], "shells": "geometric 0.05-12 m",
+                   "cubemap_samples": int(D_np.shape[0]), "relight_grid": [32, 64],
+                   "l2": "flushed between steps (2x L2 write), outside the timed events",
+                   "parallelism": f"{world} independent light(s), one per GPU"},
+        "ms_per_build": round(statistics.mean(p[0] + p[1] for p in prof), 4) if prof else None,
+        "build_phases_ms": {"prep_binning_sort": round(binning_ms, 4), "tile_kernel": round(tiles_ms, 4)},
+        "attenuated_gaussians_per_s": attenuate["gaussians_per_s"],
+        "attenuate": attenuate,
+        "build_stats": stats,
+        "roofline": roofline,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": None,
+    }
+    line["gpu_launches"] = count_launches(args, L)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, evals, args.cpu_texels)
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def count_launches(args, L):
+    """Kernels of ours per step: prep 1, cones 1, count 1, scan 3, emit 1, 2 radix passes
+    x (hist 1 + scan 3 + scatter 1), ranges 1, tiles 1; attenuate 1; sh_fit 2;
+    centroid 2; relight 1."""
+    per_step = 1 + 1 + 1 + 3 + 1 + 2 * 5 + 1 + 1 + 1 + 2 + 2 + 1
+    return per_step * args.steps
+
+
+def _measured_peak(key, fallback):
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))[key])
+    except (OSError, KeyError, ValueError):
+        return fallback
+
+
+def run_e2e(nat, wl, args, evals):
+    import torch
+    sc = wl["occluders"]
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+    h = {k: pin(getattr(sc, k)) for k in ("means", "scales", "quats", "opac", "colors")}
+    D, Y, w = (pin(a) for a in wl["cubemap"])
+    lights, radii = pin(wl["lights"]), pin(wl["radii"])
+    sl = sc.meta["avatar"]
+    cout = torch.empty((sc.n, 3), dtype=torch.float32).pin_memory()
+    shout = torch.empty((3, 9), dtype=torch.float32).pin_memory()
+    call = lambda: nat.dgsm_frame_host(h["means"], h["scales"], h["quats"], h["opac"], h["colors"],
+                                       lights, wl["H"], wl["W"], radii, D, Y, w,
+                                       relight_range=(sl.start, sl.stop), colors_out=cout,
+                                       sh_out=shout)
+    for _ in range(max(1, args.warmup)):
+        call()
+    n = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n):
+        call()
+    dt = (time.perf_counter() - t0) / n
+    h2d = sum(t.numel() * 4 for t in h.values()) + (D.numel() + Y.numel() + w.numel()
+                                                    + lights.numel() + radii.numel()) * 4
+    d2h = cout.numel() * 4 + shout.numel() * 4
+    return {"value": evals / dt, "unit": UNIT, "ms_per_step": round(dt * 1e3, 4),
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "api": "dgsm_frame_host (host buffers, pinned)"}
+
+
+# ----------------------------------------------------------------------------- oracle
+
+def oracle_step(wl, lij, q_idx, r_idx):
+    """One bounded sample of the step on the FP64 oracle: the build at texels lij,
+    attenuation of queries q_idx, the full SH fit, relight of avatar Gaussians r_idx."""
+    import oracle
+    from paper_2601_01660_b300 import scenes
+    sc, lights, radii, H, W = wl["occluders"], wl["lights"], wl["radii"], wl["H"], wl["W"]
+    t0 = time.perf_counter()
+    tau = oracle.build_tau_texels(sc, lights, H, W, radii, lij)
+    t1 = time.perf_counter()
+    # attenuate the sampled queries against an atlas that holds the sampled texels
+    K = radii.shape[0]
+    atlas = np.ones((lights.shape[0], K, H, W))
+    atlas[lij[:, 0], :, lij[:, 1], lij[:, 2]] = np.exp(-tau)
+    q = scenes.subset(sc, q_idx)
+    oracle.attenuate(atlas, radii, lights, q.means, q.colors)
+    t2 = time.perf_counter()
+    D, Y, w = wl["cubemap"]
+    shc = oracle.sh_fit(D, Y, w)
+    av = scenes.subset(sc, r_idx)
+    oracle.relight(shc, av, av.means.astype(np.float64).mean(0))
+    t3 = time.perf_counter()
+    return t1 - t0, t2 - t1, t3 - t2
+
+
+def _oracle_sample(wl, n_texels, seed=0):
+    rng = np.random.default_rng(seed)
+    sc = wl["occluders"]
+    H, W, L = wl["H"], wl["W"], wl["lights"].shape[0]
+    flat = rng.choice(L * H * W, size=n_texels, replace=False)
+    l, rem = np.divmod(flat, H * W)
+    lij = np.stack([l, rem // W, rem % W], 1).astype(np.int32)
+    frac = n_texels / (L * H * W)
+    n_q = max(1, int(round(frac * sc.n)))
+    sl = sc.meta["avatar"]
+    n_r = max(1, int(round(frac * (sl.stop - sl.start))))
+    q_idx = rng.choice(sc.n, size=n_q, replace=False)
+    r_idx = sl.start + rng.choice(sl.stop - sl.start, size=n_r, replace=False)
+    return lij, q_idx, r_idx, frac
+
+
+def cpu_baseline(wl, evals_full, n_texels):
+    """The oracle (FP64 brute force, OpenMP on the host cores) on a bounded
+    sample of the step, scaled to the metric's unit."""
+    import oracle
+    lij, q_idx, r_idx, frac = _oracle_sample(wl, n_texels)
+    tb, ta, tr = oracle_step(wl, lij, q_idx, r_idx)
+    sample_evals = oracle.count_ray_evals(wl["occluders"], wl["lights"], wl["H"], wl["W"],
+                                          wl["radii"], lij)
+    t_full = (tb + ta) / frac + tr
+    value = sample_evals / frac / t_full
+    return {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"{n_texels} random texels of the 512x512x64 build x all 1.6M Gaussians x 64 "
+                       f"shells, {q_idx.size} attenuated queries, {r_idx.size} relit avatar "
+                       f"Gaussians, full SH fit; extrapolated to the full step "
+                       f"({t_full:.0f} s); {sample_evals} Gaussian-ray evals in the sample"),
+            "sample_seconds": round(tb + ta + tr, 2), "evals_full_gpu_count": int(evals_full)}
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step is one bounded sample."""
+    if rank != 0:
+        return
+    import oracle
+    wl = load_workload(0)
+    # keep the whole --steps/--warmup run to a couple of minutes
+    n_tex = max(2, min(args.cpu_texels, 384 // max(1, args.steps)))
+    lij, q_idx, r_idx, frac = _oracle_sample(wl, n_tex)
+    sample_evals = oracle.count_ray_evals(wl["occluders"], wl["lights"], wl["H"], wl["W"],
+                                          wl["radii"], lij)
+    for _ in range(args.warmup):
+        oracle_step(wl, lij[:2], q_idx[:2], r_idx[:1])
+    times = []
+    for _ in range(args.steps):
+        tb, ta, tr = oracle_step(wl, lij, q_idx, r_idx)
+        times.append((tb + ta) / frac + tr)
+    t_full = statistics.mean(times)
+    value = sample_evals / frac / t_full
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_full * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gaussians": wl["occluders"].n,
+                       "atlas": [wl["H"], wl["W"], wl["radii"].shape[0]]},
+            "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": value,
+                             "sample": (f"{n_tex} random texels of the 512x512x64 build x all "
+                                        f"Gaussians x 64 shells per step, matching fractions of the "
+                                        f"attenuation and relight, full SH fit; extrapolated")},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-texels", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local_rank = _env_rank()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

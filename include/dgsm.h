@@ -53,10 +53,12 @@ enum dgsm_dtype { DGSM_F32 = 0, DGSM_F16 = 1, DGSM_BF16 = 2 };
  * (default 1e-7); it sets each Gaussian's culling radius k (Mahalanobis
  * units), k^2 = 2 ln2 * max(e,1), e the binary exponent of
  * kappa * alpha/(1-alpha) * (s_max/s_min) / eps_cull.
- * tile: atlas tile edge in texels for light-space binning, 4, 8 or 16
- * (default 8, the paper's 8x8 tiles).  chunk: Gaussians staged in shared
- * memory per round, 16..256 (default 64).  atlas_dtype: storage type of T
- * (dgsm_dtype; tau is always accumulated in float32). */
+ * tile: atlas tile edge in texels for light-space binning: 8 or 16 for
+ * dgsm_build (default 8, the paper's 8x8 tiles), also 4 for dgsm_bin.
+ * chunk: Gaussians staged in shared memory per round, 16..64 (default 64);
+ * a tile's list is processed in work items of at most 16 chunks.
+ * atlas_dtype: storage type of T (dgsm_dtype; tau is always accumulated in
+ * float32). */
 typedef struct {
     float kappa;
     float eps_cull;
@@ -113,7 +115,10 @@ const char *dgsm_status_string(int status);
  *   1 <= H, W <= 4096; radii: (K), 1 <= K <= 256; params: host pointer or
  *   NULL for defaults; atlas: [n_lights][K][H][W] of params->atlas_dtype.
  * Blocks once, midway, to size the workspace from the number of binned
- * pairs (so it is not capturable in a CUDA graph).  Fails with
+ * pairs (so it is not capturable in a CUDA graph).  Within a voxel the
+ * contributions of different Gaussians are summed in an order that can vary
+ * from run to run (float32 atomics), so repeated builds agree to rounding,
+ * not bit for bit.  Fails with
  * DGSM_ERR_NONFINITE_INPUT if an input Gaussian has a NaN/Inf field or a
  * scale <= 0, DGSM_ERR_WORKSPACE if more than 2^31 pairs are binned. */
 int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
@@ -185,6 +190,47 @@ int sh_relight(dgsm_ctx *ctx, const float *sh, const float *means, const float *
                const float *scales, const float *normals, const float *centroid,
                const float *colors_in, int64_t n, const dgsm_relight_params *params,
                float *colors_out, void *stream);
+
+/* Alpha-weighted centroid sum_i w_i mu_i / sum_i w_i of n Gaussians (the
+ * receiver centroid the relight normals are turned away from, Sec. 3.2's
+ * alpha-weighted avatar centroid), accumulated in FP64.  weights may be
+ * NULL (plain mean); out: device pointer to 3 floats ((0,0,0) if the
+ * weights sum to 0). */
+int dgsm_weighted_centroid(dgsm_ctx *ctx, const float *means, const float *weights, int64_t n,
+                           float *out, void *stream);
+
+/* One frame from HOST memory: copy in, build the atlas from all n Gaussians
+ * (dgsm_build), attenuate all n (dgsm_attenuate with one weight 1/L per light,
+ * direct_frac 1), fit the probe (sh_fit), relight Gaussians
+ * [relight_begin, relight_end) in place on their attenuated colours
+ * (sh_relight, centroid = their alpha-weighted centroid), copy out.
+ * All array fields of `in` are host pointers (pinned memory makes the copies
+ * asynchronous); colors_out: host (n,3); sh_out: host (3,9) or NULL.
+ * Device buffers come from the context's workspace.  Blocks until the
+ * results are in host memory. */
+typedef struct {
+    const float *means, *scales, *quats, *opac, *colors; /* (n,3) (n,3) (n,4) (n) (n,3) */
+    int64_t n;
+    int64_t relight_begin, relight_end;
+    const float *lights;                                  /* (n_lights,3) */
+    int32_t n_lights, H, W, K;
+    const float *radii;                                   /* (K) */
+    const float *cube_dirs, *cube_rgb, *cube_w;           /* (n_cube,3) (n_cube,3) (n_cube) */
+    int64_t n_cube;
+    double lambda;
+} dgsm_frame_host_in;
+
+int dgsm_frame_host(dgsm_ctx *ctx, const dgsm_frame_host_in *in, const dgsm_params *params,
+                    const dgsm_relight_params *rparams, float *colors_out, float *sh_out,
+                    void *stream);
+
+/* Phase timing of dgsm_build.  While enabled, each dgsm_build records three
+ * CUDA events on its stream (start; before the tile kernel; after it) for
+ * up to 256 builds.  dgsm_profile_collect blocks until they complete and
+ * writes, per build, ms_out[2b] = prep + binning + sort time and
+ * ms_out[2b+1] = tile-kernel time (n_out builds), then forgets them. */
+int dgsm_set_profiling(dgsm_ctx *ctx, int enable);
+int dgsm_profile_collect(dgsm_ctx *ctx, double *ms_out, int max_builds, int *n_out);
 
 /* Reads and clears the context's device status word (blocks on `stream`):
  * returns DGSM_OK or the first error a kernel recorded since the last call. */

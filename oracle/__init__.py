@@ -70,6 +70,9 @@ def _declare(L):
     L.orc_f32_bin.restype = I64
     L.orc_f32_bin.argtypes = [_f, _f, _f, I64, _f, C.c_int, C.c_int, C.c_int, _f, C.c_int,
                               C.c_float, C.c_float, C.c_int, _u32, _u32, I64]
+    L.orc_count_ray_evals.restype = I64
+    L.orc_count_ray_evals.argtypes = [_f, _f, _f, _f, I64, _f, C.c_int, C.c_int, _f, C.c_int,
+                                      C.c_float, C.c_float, _i32, I64]
     L.orc_sh_basis.argtypes = [_d, _d]
     L.orc_sh_fit.restype = C.c_int
     L.orc_sh_fit.argtypes = [_f, _f, _f, I64, C.c_double, _d]
@@ -257,6 +260,17 @@ def f32_bin(sc, lights, H, W, radii, kappa=1.0, eps=1e-7, tile=8):
     vals = np.zeros(max(total, 1), dtype=np.uint32)
     lib().orc_f32_bin(*args, keys.ctypes.data_as(_u32), vals.ctypes.data_as(_u32), total)
     return keys[:total], vals[:total]
+
+
+def count_ray_evals(sc, lights, H, W, radii, lij, kappa=1.0, eps=1e-7) -> int:
+    """Gaussian-ray evaluations the method must make at texels lij (metric units)."""
+    lights = _c32(lights).reshape(-1, 3)
+    radii = _c32(radii)
+    lij = np.ascontiguousarray(lij, dtype=np.int32).reshape(-1, 3)
+    return int(lib().orc_count_ray_evals(_pf(sc.means), _pf(sc.scales), _pf(sc.quats), _pf(sc.opac),
+                                         sc.n, _pf(lights), H, W, _pf(radii), radii.shape[0],
+                                         float(kappa), float(eps), lij.ctypes.data_as(_i32),
+                                         lij.shape[0]))
 
 
 # --- HDRI probe and transfer (Secs. 3.4-3.5) ---------------------------------

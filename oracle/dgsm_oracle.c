@@ -560,6 +560,38 @@ int64_t orc_f32_bin(const float *means, const float *scales, const float *opac, 
     return bad ? -1 : total;
 }
 
+/* Number of Gaussian-ray evaluations the method must make at the listed
+ * texels (l,i,j): pairs whose ray from light l cuts the Gaussian's culling
+ * ellipsoid {(x-mu)^T A (x-mu) <= k^2} at t > 0 (k^2 from the binning
+ * specification).  m^2 = c - b^2/a and s* = -b/a in FP64.  This is the unit
+ * count of the throughput metric. */
+int64_t orc_count_ray_evals(const float *means, const float *scales, const float *quats,
+                            const float *opac, int64_t N, const float *lights, int H, int W,
+                            const float *radii, int K, float kappa, float eps,
+                            const int32_t *lij, int64_t n_texels) {
+    int64_t total = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : total)
+    for (int64_t t = 0; t < n_texels; ++t) {
+        int l = lij[3 * t], i = lij[3 * t + 1], j = lij[3 * t + 2];
+        const float *o = lights + 3 * l;
+        double od[3] = {o[0], o[1], o[2]}, d[3];
+        orc_texel_dir(i, j, H, W, d);
+        for (int64_t n = 0; n < N; ++n) {
+            float cone[9];
+            if (orc_f32_gauss_cone(means + 3 * n, scales + 3 * n, opac[n], o, kappa, eps,
+                                   radii[K - 1], cone) != 1)
+                continue;
+            double A[9], a, b, c;
+            orc_precision(scales + 3 * n, quats + 4 * n, A);
+            double om[3] = {od[0] - means[3 * n], od[1] - means[3 * n + 1], od[2] - means[3 * n + 2]};
+            orc_ray_coeffs(A, d, om, &a, &b, &c);
+            double m2 = c - b * b / a;
+            if (m2 <= (double)cone[6] && (cone[5] != 0.0f || -b / a > 0)) ++total;
+        }
+    }
+    return total;
+}
+
 /* ------------------------------------------------------------------------ */
 /* HDRI probe (Sec. 3.4): real SH basis to degree 2 and the ridge fit, Eq. 7 */
 /* ------------------------------------------------------------------------ */

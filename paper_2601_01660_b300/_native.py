@@ -66,6 +66,16 @@ class BuildStats(C.Structure):
                 ("shell_evals", C.c_int64)]
 
 
+class FrameHostIn(C.Structure):
+    """Mirror of dgsm_frame_host_in (host pointers)."""
+    _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opac", C.c_void_p), ("colors", C.c_void_p), ("n", C.c_int64),
+                ("relight_begin", C.c_int64), ("relight_end", C.c_int64), ("lights", C.c_void_p),
+                ("n_lights", C.c_int32), ("H", C.c_int32), ("W", C.c_int32), ("K", C.c_int32),
+                ("radii", C.c_void_p), ("cube_dirs", C.c_void_p), ("cube_rgb", C.c_void_p),
+                ("cube_w", C.c_void_p), ("n_cube", C.c_int64), ("lam", C.c_double)]
+
+
 _vp = C.c_void_p
 _i32, _i64, _f32, _f64 = C.c_int32, C.c_int64, C.c_float, C.c_double
 
@@ -90,8 +100,15 @@ _lib.sh_fit.argtypes = [_vp, _vp, _vp, _vp, _i64, _f64, _vp, _vp, _vp]
 _lib.sh_relight.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64,
                             C.POINTER(RelightParams), _vp, _vp]
 _lib.dgsm_sync_status.argtypes = [_vp, _vp]
+_lib.dgsm_weighted_centroid.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp]
+_lib.dgsm_frame_host.argtypes = [_vp, C.POINTER(FrameHostIn), C.POINTER(Params),
+                                 C.POINTER(RelightParams), _vp, _vp, _vp]
+_lib.dgsm_set_profiling.argtypes = [_vp, C.c_int]
+_lib.dgsm_profile_collect.argtypes = [_vp, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]
 for _fn in ("dgsm_build", "dgsm_get_build_stats", "dgsm_bin", "dgsm_attenuate",
-            "dgsm_sample_index", "sh_fit", "sh_relight", "dgsm_sync_status"):
+            "dgsm_sample_index", "sh_fit", "sh_relight", "dgsm_sync_status",
+            "dgsm_weighted_centroid", "dgsm_frame_host", "dgsm_set_profiling",
+            "dgsm_profile_collect"):
     getattr(_lib, _fn).restype = C.c_int
 
 
@@ -293,3 +310,62 @@ def dgsm_sync_status(ctx: Context | None = None, stream=None) -> int:
     ctx = ctx or context()
     rc = _lib.dgsm_sync_status(ctx.handle, _stream(stream))
     return rc
+
+
+def dgsm_weighted_centroid(means, weights=None, ctx: Context | None = None, stream=None):
+    """Alpha-weighted centroid (3,) float32 on the device."""
+    ctx = ctx or context(means.device.index)
+    _need(means, "means", shape_last=3)
+    if weights is not None:
+        _need(weights, "weights")
+    out = torch.empty(3, dtype=torch.float32, device=means.device)
+    ctx.check(_lib.dgsm_weighted_centroid(ctx.handle, _ptr(means), _ptr(weights), means.shape[0],
+                                          _ptr(out), _stream(stream)))
+    return out
+
+
+def _host(t, name, dtype=torch.float32):
+    if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} CPU tensor (pinned for async copies)")
+    return t
+
+
+def dgsm_frame_host(means, scales, quats, opac, colors, lights, H, W, radii, cube_dirs,
+                    cube_rgb, cube_w, relight_range=(0, 0), lam=1e-3, params=None,
+                    rparams=None, colors_out=None, sh_out=None, ctx: Context | None = None,
+                    stream=None):
+    """One frame from host tensors: shadowed + relit colours (host), SH (host)."""
+    ctx = ctx or context()
+    ts = dict(means=means, scales=scales, quats=quats, opac=opac, colors=colors, lights=lights,
+              radii=radii, cube_dirs=cube_dirs, cube_rgb=cube_rgb, cube_w=cube_w)
+    for k, t in ts.items():
+        _host(t, k)
+    n = means.shape[0]
+    if colors_out is None:
+        colors_out = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    if sh_out is None:
+        sh_out = torch.empty((3, 9), dtype=torch.float32).pin_memory()
+    fi = FrameHostIn(*(ts[k].data_ptr() for k in ("means", "scales", "quats", "opac", "colors")),
+                     n, int(relight_range[0]), int(relight_range[1]), lights.data_ptr(),
+                     lights.shape[0], H, W, radii.shape[0], radii.data_ptr(), cube_dirs.data_ptr(),
+                     cube_rgb.data_ptr(), cube_w.data_ptr(), cube_dirs.shape[0], float(lam))
+    p = params if isinstance(params, Params) else Params.make(**(params or {}))
+    rp = rparams if isinstance(rparams, RelightParams) else RelightParams.make(**(rparams or {}))
+    ctx.check(_lib.dgsm_frame_host(ctx.handle, C.byref(fi), C.byref(p), C.byref(rp),
+                                   C.c_void_p(colors_out.data_ptr()), C.c_void_p(sh_out.data_ptr()),
+                                   _stream(stream)))
+    return colors_out, sh_out
+
+
+def dgsm_set_profiling(enable: bool, ctx: Context | None = None):
+    ctx = ctx or context()
+    ctx.check(_lib.dgsm_set_profiling(ctx.handle, int(bool(enable))))
+
+
+def dgsm_profile_collect(ctx: Context | None = None):
+    """[(ms prep+binning+sort, ms tile kernel), ...] of the builds since the last call."""
+    ctx = ctx or context()
+    buf = (C.c_double * 512)()
+    n = C.c_int(0)
+    ctx.check(_lib.dgsm_profile_collect(ctx.handle, buf, 256, C.byref(n)))
+    return [(buf[2 * i], buf[2 * i + 1]) for i in range(n.value)]

@@ -4,15 +4,23 @@
 //   rect_cones_kernel   direction cones of every atlas tile and super-tile
 //   prep_kernel         per (light, Gaussian): whitening matrix M = S^-1 R^T,
 //                       w' = M (mu - o), beta (Eq. 5), culling radius, shell
-//                       window and the binning cone
-//   bin_count_kernel    tiles overlapped by each Gaussian's cone
+//                       window, bounding cone
+//   bin_kernel<false>   tiles overlapped by each Gaussian's cone (one warp per
+//                       Gaussian, 32 cone tests at a time)
 //   scan                exclusive prefix sum -> pair offsets   (one host sync)
-//   bin_emit_kernel     (key = light*tiles + tile, value = Gaussian) pairs
-//   radix sort          stable, by key
+//   bin_kernel<true>    (key = light*tiles + tile, value = Gaussian) pairs
+//   radix sort          stable, by key -> per-tile lists in Gaussian order
 //   tile_ranges_kernel  [start, end) of every key
-//   build_tiles_kernel  per tile: stage the tile's Gaussians in shared
-//                       memory, evaluate Eq. 3 per (texel ray, Gaussian,
-//                       shell), prefix-sum over shells, T = exp(-tau) (Eq. 4)
+//   item kernels        cut every tile's list into work items of <= ITEM
+//                       Gaussians
+//   build_items_kernel  persistent: blocks pull items from an atomic counter;
+//                       stage the item's records with cp.async (double
+//                       buffered); per (texel ray, Gaussian) a cone pre-test,
+//                       then the surviving pairs are compacted per warp and
+//                       evaluated densely: the exact culling test and Eq. 3 at
+//                       the shells of the Gaussian's window, accumulated as
+//                       per-shell increments; the last item of a tile takes
+//                       the shell-wise prefix sum and T = exp(-tau) (Eq. 4).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -24,21 +32,31 @@
 namespace dgsm {
 namespace {
 
-constexpr int SUPER = 8;  // super-tile edge, in tiles
+constexpr int SUPER = 8;       // super-tile edge, in tiles
+constexpr int REC_F4 = 5;      // float4 per build record
+constexpr int BT_THREADS = 256;
+constexpr int BT_WARPS = BT_THREADS / 32;
+constexpr int QCAP = 64;       // per-warp queue of (record, texel) pairs
+constexpr int ITEM_CHUNKS = 16;  // a work item holds at most ITEM_CHUNKS * chunk Gaussians
 
-// Per (light, Gaussian) record read by the build kernel (64 bytes):
-//   a = (M00 M01 M02 M10), b = (M11 M12 M20 M21), c = (M22 w'x w'y w'z),
-//   d = (beta sqrt(pi/2), k^2, packed window, unused)
+// Per (light, Gaussian) record read by the build kernel (80 bytes):
+//   r0 = (M00 M01 M02 M10), r1 = (M11 M12 M20 M21), r2 = (M22 w'x w'y w'z),
+//   r3 = (beta sqrt(pi/2), k^2, packed window, cos of the bounding cone - margin),
+//   r4 = (unit direction to the Gaussian, 0)
 // packed window: bits 0-9 first shell of the window, 10-19 first shell past
 // it, bit 20 = light inside the Gaussian's culling sphere.
 struct __align__(16) BuildRec {
-    float4 a, b, c, d;
+    float4 r0, r1, r2, r3, r4;
 };
 
 // Per (light, Gaussian) binning record (32 bytes): a = (dir xyz, cos theta),
 // b = (sin theta, mode, -, -); mode 0 = not binned, 1 = cone test, 2 = all tiles.
 struct __align__(16) BinRec {
     float4 a, b;
+};
+
+struct __align__(16) Item {
+    uint32_t key, start, end, n_items;
 };
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -55,6 +73,15 @@ __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ void record_status(int *status, int code) {
@@ -188,14 +215,18 @@ __global__ void __launch_bounds__(256) prep_kernel(
             continue;
         }
         const bool inside = r >= dist;
+        float cone_cos = -2.0f;
+        float3 dir = make_float3(0.f, 0.f, 1.f);
         if (inside) {
             br.a = make_float4(0.f, 0.f, 1.f, -1.f);
             br.b = make_float4(0.f, 2.f, 0.f, 0.f);
         } else {
             const float sn = xdiv(r, dist);
             const float cs = xsqrt(xsub(1.0f, xmul(sn, sn)));
-            br.a = make_float4(xdiv(vx, dist), xdiv(vy, dist), xdiv(vz, dist), cs);
+            dir = make_float3(xdiv(vx, dist), xdiv(vy, dist), xdiv(vz, dist));
+            br.a = make_float4(dir.x, dir.y, dir.z, cs);
             br.b = make_float4(sn, 1.f, 0.f, 0.f);
+            cone_cos = cs - 1e-5f;  // pre-test margin for rounding of the texel directions
         }
         bin[idx] = br;
         if (!quats) continue;
@@ -231,10 +262,11 @@ __global__ void __launch_bounds__(256) prep_kernel(
         while (kend < K && radii[kend] <= hi) ++kend;
         const int packed = klo | (kend << 10) | ((inside ? 1 : 0) << 20);
         BuildRec rec;
-        rec.a = make_float4(M00, M01, M02, M10);
-        rec.b = make_float4(M11, M12, M20, M21);
-        rec.c = make_float4(M22, wx, wy, wz);
-        rec.d = make_float4(bpref, k2, __int_as_float(packed), 0.f);
+        rec.r0 = make_float4(M00, M01, M02, M10);
+        rec.r1 = make_float4(M11, M12, M20, M21);
+        rec.r2 = make_float4(M22, wx, wy, wz);
+        rec.r3 = make_float4(bpref, k2, __int_as_float(packed), cone_cos);
+        rec.r4 = make_float4(dir.x, dir.y, dir.z, 0.f);
         brec[idx] = rec;
     }
 }
@@ -247,50 +279,64 @@ __device__ __forceinline__ bool cone_overlap(const BinRec &g, const float4 *cone
     return dot >= rhs;
 }
 
-// Count (emit = false) or write (emit = true) the tiles each Gaussian overlaps.
+// Count (EMIT = false) or write (EMIT = true) the tiles each Gaussian
+// overlaps.  One warp per (light, Gaussian): 32 super-tile tests at a time,
+// then the 64 tiles of every overlapped super-tile, 32 at a time; the pairs
+// of one Gaussian are written contiguously from its scanned offset.
 template <bool EMIT>
-__global__ void __launch_bounds__(256) bin_tiles_kernel(
+__global__ void __launch_bounds__(256) bin_kernel(
     const BinRec *__restrict__ bin, int64_t N, int L, int tx, int ty, int sx, int sy,
     const float4 *__restrict__ cones, uint32_t *__restrict__ counts,
     const uint32_t *__restrict__ offsets, uint32_t *__restrict__ keys,
     uint32_t *__restrict__ vals) {
     const int64_t total = (int64_t)L * N;
-    const int n_tiles = tx * ty;
+    const int n_tiles = tx * ty, n_super = sx * sy;
     const float4 *scones = cones + 2 * n_tiles;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < total;
+         idx += nwarps) {
         const BinRec g = bin[idx];
         const int mode = (int)g.b.y;
         const int l = (int)(idx / N);
         const uint32_t gi = (uint32_t)(idx - (int64_t)l * N);
+        const uint32_t kbase = (uint32_t)l * (uint32_t)n_tiles;
         uint32_t c = 0, off = 0;
         if (EMIT) off = offsets[idx];
         if (mode == 2) {
-            if (EMIT) {
-                for (int t = 0; t < n_tiles; ++t) {
-                    keys[off + t] = (uint32_t)(l * n_tiles + t);
+            if (EMIT)
+                for (int t = lane; t < n_tiles; t += 32) {
+                    keys[off + t] = kbase + t;
                     vals[off + t] = gi;
                 }
-            }
             c = n_tiles;
         } else if (mode == 1) {
-            for (int sa = 0; sa < sy; ++sa)
-                for (int sb = 0; sb < sx; ++sb) {
-                    if (!cone_overlap(g, scones + 2 * (sa * sx + sb))) continue;
-                    const int a1 = min(sa * SUPER + SUPER, ty), b1 = min(sb * SUPER + SUPER, tx);
-                    for (int a = sa * SUPER; a < a1; ++a)
-                        for (int b = sb * SUPER; b < b1; ++b) {
-                            const int t = a * tx + b;
-                            if (!cone_overlap(g, cones + 2 * t)) continue;
-                            if (EMIT) {
-                                keys[off + c] = (uint32_t)(l * n_tiles + t);
-                                vals[off + c] = gi;
-                            }
-                            ++c;
+            for (int sb = 0; sb < n_super; sb += 32) {
+                const int s = sb + lane;
+                unsigned m = __ballot_sync(0xffffffffu, s < n_super && cone_overlap(g, scones + 2 * s));
+                while (m) {
+                    const int si = sb + __ffs(m) - 1;
+                    m &= m - 1;
+                    const int sa = si / sx, sbb = si - sa * sx;
+#pragma unroll
+                    for (int rnd = 0; rnd < SUPER * SUPER / 32; ++rnd) {
+                        const int local = rnd * 32 + lane;
+                        const int a = sa * SUPER + local / SUPER, b = sbb * SUPER + local % SUPER;
+                        const int t = a * tx + b;
+                        const bool ov = a < ty && b < tx && cone_overlap(g, cones + 2 * t);
+                        const unsigned m2 = __ballot_sync(0xffffffffu, ov);
+                        if (EMIT && ov) {
+                            const uint32_t pos = off + c + __popc(m2 & lt);
+                            keys[pos] = kbase + t;
+                            vals[pos] = gi;
                         }
+                        c += __popc(m2);
+                    }
                 }
+            }
         }
-        if (!EMIT) counts[idx] = c;
+        if (!EMIT && lane == 0) counts[idx] = c;
     }
 }
 
@@ -301,6 +347,33 @@ __global__ void tile_ranges_kernel(const uint32_t *__restrict__ keys, int64_t P,
         const uint32_t k = keys[p];
         if (p == 0 || keys[p - 1] != k) start[k] = (uint32_t)p;
         if (p == P - 1 || keys[p + 1] != k) end[k] = (uint32_t)(p + 1);
+    }
+}
+
+// Items per key: ceil(count / item) (one, possibly empty, for an empty tile).
+__global__ void item_count_kernel(const uint32_t *__restrict__ ts, const uint32_t *__restrict__ te,
+                                  int nkeys, uint32_t item, uint32_t *__restrict__ n_items) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nkeys) return;
+    const uint32_t c = te[k] - ts[k];
+    n_items[k] = c == 0 ? 1u : (c + item - 1) / item;
+}
+
+__global__ void item_expand_kernel(const uint32_t *__restrict__ ts, const uint32_t *__restrict__ te,
+                                   int nkeys, uint32_t item, const uint32_t *__restrict__ item_off,
+                                   Item *__restrict__ items) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nkeys) return;
+    const uint32_t s = ts[k], e = te[k];
+    const uint32_t n = e == s ? 1u : (e - s + item - 1) / item;
+    const uint32_t o = item_off[k];
+    for (uint32_t q = 0; q < n; ++q) {
+        Item it;
+        it.key = (uint32_t)k;
+        it.start = s + q * item;
+        it.end = min(s + (q + 1) * item, e);
+        it.n_items = n;
+        items[o + q] = it;
     }
 }
 
@@ -333,138 +406,265 @@ __device__ __forceinline__ float mass_below(float x, float A0, float hm2, float 
     return x >= 0.0f ? full - tail : tail;
 }
 
-// One block per (light, tile); one thread per texel of the tile.
-template <typename OutT>
-__global__ void __launch_bounds__(256) build_tiles_kernel(
-    const BuildRec *__restrict__ brec, const uint32_t *__restrict__ vals,
-    const uint32_t *__restrict__ tstart, const uint32_t *__restrict__ tend,
-    const float *__restrict__ radii, int K, int H, int W, int tile, int tx, int n_tiles,
-    int64_t N, int chunk, OutT *__restrict__ atlas, unsigned long long *__restrict__ stats) {
-    extern __shared__ float4 smem4[];
-    const int nt = tile * tile;
-    float4 *stage = smem4;                              // chunk x 4 float4
-    float *D = reinterpret_cast<float *>(smem4 + 4 * chunk);  // K x nt shell increments
-    float *rs = D + K * nt;                             // K radii
-    const int key = blockIdx.x;
-    const int l = key / n_tiles, t = key - l * n_tiles;
-    const int tile_i = t / tx, tile_j = t - tile_i * tx;
-    const int tid = threadIdx.x;
-    const int i = tile_i * tile + tid / tile, j = tile_j * tile + tid % tile;
-    const bool valid = i < H && j < W;
-    for (int k = 0; k < K; ++k) D[k * nt + tid] = 0.0f;
-    for (int k = tid; k < K; k += nt) rs[k] = radii[k];
-    // texel ray direction: decoded texel centre
-    const float u = (2.0f * j + 1.0f) / W - 1.0f, v = (2.0f * i + 1.0f) / H - 1.0f;
-    float z = 1.0f - fabsf(u) - fabsf(v), x = u, y = v;
-    if (z < 0.0f) {
-        x = copysignf(1.0f - fabsf(v), u >= 0.f ? 1.f : -1.f);
-        y = copysignf(1.0f - fabsf(u), v >= 0.f ? 1.f : -1.f);
+// Exact culling test and Eq. 3 at the shells of the Gaussian's window for one
+// (texel ray, Gaussian) pair; adds the per-shell optical-depth increments to
+// D[k * nt + texel].  Returns true when the ray cuts the culling ellipsoid.
+__device__ __forceinline__ bool eval_pair(const float4 *rec, float dx, float dy, float dz,
+                                          const float *rs, int K, float *D, int nt, int texel,
+                                          unsigned long long &n_shell) {
+    const float4 q0 = rec[0], q1 = rec[1], q2 = rec[2], q3 = rec[3];
+    // whitened ray direction d' = M d
+    const float px = fmaf(q0.x, dx, fmaf(q0.y, dy, q0.z * dz));
+    const float py = fmaf(q0.w, dx, fmaf(q1.x, dy, q1.y * dz));
+    const float pz = fmaf(q1.z, dx, fmaf(q1.w, dy, q2.x * dz));
+    const float wx = q2.y, wy = q2.z, wz = q2.w;
+    const float a = fmaf(px, px, fmaf(py, py, pz * pz));   // d^T A d
+    const float pw = fmaf(px, wx, fmaf(py, wy, pz * wz));  // -b
+    const float cx = fmaf(wy, pz, -wz * py);               // w' x d'
+    const float cy = fmaf(wz, px, -wx * pz);
+    const float cz = fmaf(wx, py, -wy * px);
+    const float c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+    const float ia = rcp_approx(a);
+    const float m2 = c2 * ia;  // c - b^2/a without cancellation
+    const float ss = pw * ia;  // closest approach s* = -b/a
+    const int packed = __float_as_int(q3.z);
+    const bool inside = (packed >> 20) & 1;
+    if (!(m2 <= q3.y && (inside || ss > 0.0f))) return false;
+    const int klo = packed & 1023, kend = (packed >> 10) & 1023;
+    n_shell += kend - klo;
+    const float rsa = rsqrt_approx(a);
+    const float A0 = q3.x * rsa;                 // beta sqrt(pi/(2a))
+    const float h = a * rsa * 0.70710678118f;    // sqrt(a/2)
+    const float hm2 = -0.72134752044f * m2;      // -m^2/2 log2(e)
+    const float full = 2.0f * A0 * ex2_approx(hm2);
+    const float hs = h * ss;
+    const float F0 = inside ? mass_below(-hs, A0, hm2, full) : 0.0f;
+    float Gprev = 0.0f;
+    for (int k = klo; k < kend; ++k) {
+        const float G = mass_below(fmaf(h, rs[k], -hs), A0, hm2, full) - F0;
+        atomicAdd(D + k * nt + texel, fmaxf(G - Gprev, 0.0f));
+        Gprev = fmaxf(G, Gprev);
     }
-    const float inv = rsqrtf(x * x + y * y + z * z);
-    const float dx = x * inv, dy = y * inv, dz = z * inv;
-
-    const uint32_t p0 = tstart[key], p1 = tend[key];
-    unsigned long long n_hit = 0, n_shell = 0;
-    __syncthreads();
-    for (uint32_t base = p0; base < p1; base += chunk) {
-        const int cnt = (int)min((uint32_t)chunk, p1 - base);
-        const float4 *src = reinterpret_cast<const float4 *>(brec) + (int64_t)l * N * 4;
-        for (int e = tid; e < cnt * 4; e += nt) {
-            const uint32_t g = vals[base + (e >> 2)];
-            stage[e] = __ldg(src + (int64_t)g * 4 + (e & 3));
-        }
-        __syncthreads();
-        if (valid) {
-            for (int r = 0; r < cnt; ++r) {
-                const float4 q0 = stage[4 * r], q1 = stage[4 * r + 1], q2 = stage[4 * r + 2],
-                             q3 = stage[4 * r + 3];
-                // whitened ray direction d' = M d
-                const float px = fmaf(q0.x, dx, fmaf(q0.y, dy, q0.z * dz));
-                const float py = fmaf(q0.w, dx, fmaf(q1.x, dy, q1.y * dz));
-                const float pz = fmaf(q1.z, dx, fmaf(q1.w, dy, q2.x * dz));
-                const float wx = q2.y, wy = q2.z, wz = q2.w;
-                const float a = fmaf(px, px, fmaf(py, py, pz * pz));      // d^T A d
-                const float pw = fmaf(px, wx, fmaf(py, wy, pz * wz));     // -b
-                const float cx = fmaf(wy, pz, -wz * py);                  // w' x d'
-                const float cy = fmaf(wz, px, -wx * pz);
-                const float cz = fmaf(wx, py, -wy * px);
-                const float c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-                const float ia = rcp_approx(a);
-                const float m2 = c2 * ia;   // c - b^2/a without cancellation
-                const float ss = pw * ia;   // closest approach s* = -b/a
-                const int packed = __float_as_int(q3.z);
-                const bool inside = (packed >> 20) & 1;
-                if (m2 <= q3.y && (inside || ss > 0.0f)) {
-                    const int klo = packed & 1023, kend = (packed >> 10) & 1023;
-                    ++n_hit;
-                    n_shell += kend - klo;
-                    const float rsa = rsqrt_approx(a);
-                    const float A0 = q3.x * rsa;                 // beta sqrt(pi/(2a))
-                    const float h = a * rsa * 0.70710678118f;    // sqrt(a/2)
-                    const float hm2 = -0.72134752044f * m2;      // -m^2/2 log2(e)
-                    const float full = 2.0f * A0 * ex2_approx(hm2);
-                    const float hs = h * ss;
-                    const float F0 = inside ? mass_below(-hs, A0, hm2, full) : 0.0f;
-                    float Gprev = 0.0f;
-                    for (int k = klo; k < kend; ++k) {
-                        const float G = mass_below(fmaf(h, rs[k], -hs), A0, hm2, full) - F0;
-                        D[k * nt + tid] += fmaxf(G - Gprev, 0.0f);
-                        Gprev = fmaxf(G, Gprev);
-                    }
-                    if (kend < K) D[kend * nt + tid] += fmaxf(full - F0 - Gprev, 0.0f);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    if (valid) {
-        float tau = 0.0f, Tprev = 1.0f;
-        const int64_t plane = (int64_t)H * W;
-        OutT *dst = atlas + (int64_t)l * K * plane + (int64_t)i * W + j;
-        for (int k = 0; k < K; ++k) {
-            tau += D[k * nt + tid];
-            const float T = fminf(expf(-tau), Tprev);  // Eq. 4, kept non-increasing in k
-            Tprev = T;
-            dst[k * plane] = to_store<OutT>(T);
-        }
-    }
-    if (stats) {
-        // block counters in shared memory (blocks of 16 threads fill half a warp)
-        __shared__ unsigned long long cnt[2];
-        if (tid == 0) cnt[0] = cnt[1] = 0ull;
-        __syncthreads();
-        if (n_hit) atomicAdd(&cnt[0], n_hit);
-        if (n_shell) atomicAdd(&cnt[1], n_shell);
-        __syncthreads();
-        if (tid == 0) {
-            const int nvalid = (min(tile_i * tile + tile, H) - tile_i * tile) *
-                               (min(tile_j * tile + tile, W) - tile_j * tile);
-            atomicAdd(stats + 0, (unsigned long long)nvalid * (p1 - p0));
-            atomicAdd(stats + 1, cnt[0]);
-            atomicAdd(stats + 2, cnt[1]);
-        }
-    }
+    if (kend < K) atomicAdd(D + kend * nt + texel, fmaxf(full - F0 - Gprev, 0.0f));
+    return true;
 }
 
 size_t build_smem_bytes(int K, int tile, int chunk) {
-    return (size_t)chunk * 4 * sizeof(float4) + (size_t)K * tile * tile * sizeof(float) +
-           (size_t)K * sizeof(float);
+    const int nt = tile * tile;
+    return (size_t)2 * chunk * REC_F4 * sizeof(float4) + (size_t)nt * sizeof(float4) +
+           (size_t)K * nt * sizeof(float) + (size_t)((K + 3) & ~3) * sizeof(float) +
+           (size_t)BT_WARPS * QCAP * sizeof(uint16_t);
+}
+
+// Persistent build kernel: 8 warps per block; tile 8 -> 2 texel groups x 4
+// record groups, tile 16 -> 8 texel groups x 1 record group.
+template <typename OutT>
+__global__ void __launch_bounds__(BT_THREADS) build_items_kernel(
+    const float4 *__restrict__ brec, const uint32_t *__restrict__ vals,
+    const Item *__restrict__ items, const unsigned long long *__restrict__ n_items_total,
+    unsigned int *__restrict__ item_counter, const float *__restrict__ radii, int K, int H, int W,
+    int tile, int tx, int n_tiles, int64_t N, int chunk, float *__restrict__ accum,
+    unsigned int *__restrict__ done, OutT *__restrict__ atlas,
+    unsigned long long *__restrict__ stats) {
+    extern __shared__ float4 smem4[];
+    const int nt = tile * tile;
+    const int n_tg = nt / 32;
+    const int n_rg = BT_WARPS / n_tg;
+    float4 *stage = smem4;                                   // [2][chunk * REC_F4]
+    float4 *tdir = stage + 2 * chunk * REC_F4;               // [nt] (dir, valid)
+    float *D = reinterpret_cast<float *>(tdir + nt);         // [K][nt]
+    float *rs = D + K * nt;                                  // [K]
+    uint16_t *queue = reinterpret_cast<uint16_t *>(rs + ((K + 3) & ~3));  // [BT_WARPS][QCAP]
+    __shared__ uint4 s_item;
+    __shared__ int s_last;
+    __shared__ unsigned long long s_cnt[3];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tg = warp % n_tg, rg = warp / n_tg;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t HW = (int64_t)H * W;
+    const unsigned long long total_items = *n_items_total;
+    for (int k = tid; k < K; k += BT_THREADS) rs[k] = radii[k];
+    if (tid < 3) s_cnt[tid] = 0ull;
+    unsigned long long n_hit = 0, n_shell = 0, n_tested = 0;
+    uint16_t *q = queue + warp * QCAP;
+
+    for (;;) {
+        if (tid == 0) {
+            const unsigned it = atomicAdd(item_counter, 1u);
+            s_item = it < total_items ? *reinterpret_cast<const uint4 *>(items + it)
+                                      : make_uint4(0xffffffffu, 0u, 0u, 0u);
+        }
+        __syncthreads();
+        const uint4 item = s_item;
+        if (item.x == 0xffffffffu) break;
+        const uint32_t key = item.x, start = item.y, end = item.z, n_items = item.w;
+        const int l = key / n_tiles, t = key - l * n_tiles;
+        const int tile_i = t / tx, tile_j = t - tile_i * tx;
+        for (int e = tid; e < K * nt; e += BT_THREADS) D[e] = 0.0f;
+        for (int e = tid; e < nt; e += BT_THREADS) {
+            const int i = tile_i * tile + e / tile, j = tile_j * tile + e % tile;
+            const float u = (2.0f * j + 1.0f) / W - 1.0f, v = (2.0f * i + 1.0f) / H - 1.0f;
+            float z = 1.0f - fabsf(u) - fabsf(v), x = u, y = v;
+            if (z < 0.0f) {
+                x = (u >= 0.f ? 1.f : -1.f) * (1.0f - fabsf(v));
+                y = (v >= 0.f ? 1.f : -1.f) * (1.0f - fabsf(u));
+            }
+            const float inv = rsqrtf(x * x + y * y + z * z);
+            tdir[e] = make_float4(x * inv, y * inv, z * inv, (i < H && j < W) ? 1.0f : 0.0f);
+        }
+        const int my_t = tg * 32 + lane;
+        const float4 *src = brec + (int64_t)l * N * REC_F4;
+        const int nrec = (int)(end - start);
+        const int nchunks = (nrec + chunk - 1) / chunk;
+        // staging: entry e of a chunk = record e / 5, part e % 5; a thread owns e = tid, tid + 256
+        uint32_t gnext[2] = {0u, 0u};
+        auto load_idx = [&](int c, uint32_t *g) {
+            const int base = (int)start + c * chunk, cnt = min(chunk, (int)end - base);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int e = tid + h * BT_THREADS;
+                g[h] = e < cnt * REC_F4 ? __ldg(vals + base + e / REC_F4) : 0u;
+            }
+        };
+        auto issue = [&](int c, const uint32_t *g) {
+            const int base = (int)start + c * chunk, cnt = min(chunk, (int)end - base);
+            float4 *dst = stage + (c & 1) * chunk * REC_F4;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int e = tid + h * BT_THREADS;
+                if (e < cnt * REC_F4) cp_async16(dst + e, src + (int64_t)g[h] * REC_F4 + e % REC_F4);
+            }
+            cp_async_commit();
+        };
+        if (nchunks > 0) {
+            uint32_t g0[2];
+            load_idx(0, g0);
+            issue(0, g0);
+            if (nchunks > 1) load_idx(1, gnext);
+        }
+        __syncthreads();
+        const float4 md = tdir[my_t];
+        const bool mvalid = md.w != 0.0f;
+        for (int c = 0; c < nchunks; ++c) {
+            if (c + 1 < nchunks) {
+                issue(c + 1, gnext);
+                if (c + 2 < nchunks) load_idx(c + 2, gnext);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            const float4 *st = stage + (c & 1) * chunk * REC_F4;
+            const int cnt = min(chunk, (int)end - ((int)start + c * chunk));
+            int qn = 0;
+            for (int r = rg; r < cnt; r += n_rg) {
+                const float4 r3 = st[r * REC_F4 + 3], r4 = st[r * REC_F4 + 4];
+                const bool pass = mvalid && fmaf(md.x, r4.x, fmaf(md.y, r4.y, md.z * r4.z)) >= r3.w;
+                const unsigned m = __ballot_sync(0xffffffffu, pass);
+                if (pass) q[qn + __popc(m & lt)] = (uint16_t)((r << 5) | lane);
+                qn += __popc(m);
+                if (qn >= 32) {
+                    __syncwarp();
+                    const unsigned e = q[qn - 32 + lane];
+                    const int tt = tg * 32 + (int)(e & 31u);
+                    const float4 d = tdir[tt];
+                    n_hit += eval_pair(st + (e >> 5) * REC_F4, d.x, d.y, d.z, rs, K, D, nt, tt, n_shell);
+                    qn -= 32;
+                    __syncwarp();
+                }
+            }
+            if (qn > 0) {
+                __syncwarp();
+                if (lane < qn) {
+                    const unsigned e = q[lane];
+                    const int tt = tg * 32 + (int)(e & 31u);
+                    const float4 d = tdir[tt];
+                    n_hit += eval_pair(st + (e >> 5) * REC_F4, d.x, d.y, d.z, rs, K, D, nt, tt, n_shell);
+                }
+                __syncwarp();
+            }
+            __syncthreads();  // the buffer is refilled two chunks later
+        }
+        if (tid == 0) {
+            const int nvalid = (min(tile_i * tile + tile, H) - tile_i * tile) *
+                               (min(tile_j * tile + tile, W) - tile_j * tile);
+            n_tested += (unsigned long long)nvalid * (unsigned long long)nrec;
+        }
+        // ---- finalize: prefix over shells, T = exp(-tau) (Eq. 4) ----
+        if (n_items == 1) {
+            for (int e = tid; e < nt; e += BT_THREADS) {
+                if (tdir[e].w == 0.0f) continue;
+                const int i = tile_i * tile + e / tile, j = tile_j * tile + e % tile;
+                OutT *dst = atlas + (int64_t)l * K * HW + (int64_t)i * W + j;
+                float tau = 0.0f, Tprev = 1.0f;
+                for (int k = 0; k < K; ++k) {
+                    tau += D[k * nt + e];
+                    const float T = fminf(expf(-tau), Tprev);  // kept non-increasing in k
+                    Tprev = T;
+                    dst[k * HW] = to_store<OutT>(T);
+                }
+            }
+        } else {
+            for (int e = tid; e < K * nt; e += BT_THREADS) {
+                const int k = e / nt, te = e - k * nt;
+                const float v = D[e];
+                if (v == 0.0f || tdir[te].w == 0.0f) continue;
+                const int i = tile_i * tile + te / tile, j = tile_j * tile + te % tile;
+                atomicAdd(accum + ((int64_t)l * K + k) * HW + (int64_t)i * W + j, v);
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) s_last = atomicAdd(done + key, 1u) == n_items - 1u;
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                for (int e = tid; e < nt; e += BT_THREADS) {
+                    if (tdir[e].w == 0.0f) continue;
+                    const int i = tile_i * tile + e / tile, j = tile_j * tile + e % tile;
+                    OutT *dst = atlas + (int64_t)l * K * HW + (int64_t)i * W + j;
+                    float *acc = accum + (int64_t)l * K * HW + (int64_t)i * W + j;
+                    float tau = 0.0f, Tprev = 1.0f;
+                    for (int k = 0; k < K; ++k) {
+                        tau += __ldcg(acc + k * HW);
+                        acc[k * HW] = 0.0f;  // ready for the next build
+                        const float T = fminf(expf(-tau), Tprev);
+                        Tprev = T;
+                        dst[k * HW] = to_store<OutT>(T);
+                    }
+                }
+                if (tid == 0) done[key] = 0u;
+            }
+        }
+        __syncthreads();  // shared state is reused by the next item
+    }
+    if (stats) {
+        if (n_tested) atomicAdd(&s_cnt[0], n_tested);
+        if (n_hit) atomicAdd(&s_cnt[1], n_hit);
+        if (n_shell) atomicAdd(&s_cnt[2], n_shell);
+        __syncthreads();
+        if (tid < 3) atomicAdd(stats + tid, s_cnt[tid]);
+    }
 }
 
 template <typename OutT>
-int launch_build_tiles(dgsm_ctx *ctx, const BuildRec *brec, const uint32_t *vals,
-                       const uint32_t *ts, const uint32_t *te, const float *radii, int K, int H,
-                       int W, int tile, int tx, int n_tiles, int L, int64_t N, int chunk, void *atlas,
-                       cudaStream_t s) {
-    size_t smem = build_smem_bytes(K, tile, chunk);
-    cudaError_t e = cudaFuncSetAttribute(build_tiles_kernel<OutT>,
+int launch_build_items(dgsm_ctx *ctx, const BuildRec *brec, const uint32_t *vals, const Item *items,
+                       const unsigned long long *n_items, unsigned int *counter, const float *radii,
+                       int K, int H, int W, int tile, int tx, int n_tiles, int64_t N, int chunk,
+                       float *accum, unsigned int *done, void *atlas, cudaStream_t s) {
+    const size_t smem = build_smem_bytes(K, tile, chunk);
+    cudaError_t e = cudaFuncSetAttribute(build_items_kernel<OutT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "build: smem attribute");
-    build_tiles_kernel<OutT><<<L * n_tiles, tile * tile, smem, s>>>(
-        brec, vals, ts, te, radii, K, H, W, tile, tx, n_tiles, N, chunk, (OutT *)atlas,
-        ctx->d_stats);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_items_kernel<OutT>, BT_THREADS, smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "build: occupancy query");
+    const int grid = std::max(1, per_sm) * ctx->num_sms;
+    build_items_kernel<OutT><<<grid, BT_THREADS, smem, s>>>(
+        reinterpret_cast<const float4 *>(brec), vals, items, n_items, counter, radii, K, H, W, tile,
+        tx, n_tiles, N, chunk, accum, done, (OutT *)atlas, ctx->d_stats);
     e = cudaGetLastError();
-    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "build_tiles_kernel");
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "build_items_kernel");
 }
 
 struct BinOut {
@@ -486,10 +686,8 @@ int check_common(dgsm_ctx *ctx, const float *means, const float *scales, const f
     if (H < 1 || W < 1 || H > 4096 || W > 4096) return fail(ctx, DGSM_ERR_INVALID_ARG, "H, W must be in 1..4096");
     if (!radii || K < 1 || K > 256) return fail(ctx, DGSM_ERR_INVALID_ARG, "K must be in 1..256");
     if (p.tile != 4 && p.tile != 8 && p.tile != 16) return fail(ctx, DGSM_ERR_INVALID_ARG, "tile must be 4, 8 or 16");
-    if (p.chunk < 16 || p.chunk > 256) return fail(ctx, DGSM_ERR_INVALID_ARG, "chunk must be in 16..256");
+    if (p.chunk < 16 || p.chunk > 64) return fail(ctx, DGSM_ERR_INVALID_ARG, "chunk must be in 16..64");
     if (!(p.kappa >= 0.f) || !(p.eps_cull > 0.f)) return fail(ctx, DGSM_ERR_INVALID_ARG, "kappa >= 0 and eps_cull > 0 required");
-    if (build_smem_bytes(K, p.tile, p.chunk) > 220 * 1024)
-        return fail(ctx, DGSM_ERR_INVALID_ARG, "K x tile^2 too large for shared memory: use a smaller tile");
     return DGSM_OK;
 }
 
@@ -525,9 +723,10 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     const int grid = (int)std::min<int64_t>((LN + 255) / 256, (int64_t)ctx->num_sms * 16);
     prep_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, N, lights, L, radii, K, p.kappa,
                                      p.eps_cull, (BuildRec *)w_br, (BinRec *)w_bin, ctx->d_status);
-    bin_tiles_kernel<false><<<grid, 256, 0, s>>>((const BinRec *)w_bin, N, L, tx, ty, sx, sy,
-                                                  (const float4 *)w_cones, (uint32_t *)w_cnt,
-                                                  nullptr, nullptr, nullptr);
+    const int wgrid = (int)std::min<int64_t>((LN * 32 + 255) / 256, (int64_t)ctx->num_sms * 16);
+    bin_kernel<false><<<wgrid, 256, 0, s>>>((const BinRec *)w_bin, N, L, tx, ty, sx, sy,
+                                             (const float4 *)w_cones, (uint32_t *)w_cnt, nullptr,
+                                             nullptr, nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "prep/count kernels");
     if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_cnt, (uint32_t *)w_cnt, LN, ctx->d_stats + 3, s)))
@@ -552,10 +751,9 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     if ((rc = ws_reserve(ctx, WS_VALS_A, sizeof(uint32_t) * P, &va))) return rc;
     if ((rc = ws_reserve(ctx, WS_KEYS_B, sizeof(uint32_t) * P, &kb))) return rc;
     if ((rc = ws_reserve(ctx, WS_VALS_B, sizeof(uint32_t) * P, &vb))) return rc;
-    bin_tiles_kernel<true><<<grid, 256, 0, s>>>((const BinRec *)w_bin, N, L, tx, ty, sx, sy,
-                                                 (const float4 *)w_cones, nullptr,
-                                                 (const uint32_t *)w_cnt, (uint32_t *)ka,
-                                                 (uint32_t *)va);
+    bin_kernel<true><<<wgrid, 256, 0, s>>>((const BinRec *)w_bin, N, L, tx, ty, sx, sy,
+                                            (const float4 *)w_cones, nullptr,
+                                            (const uint32_t *)w_cnt, (uint32_t *)ka, (uint32_t *)va);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "bin emit kernel");
     int bits = 0;
@@ -586,31 +784,77 @@ extern "C" int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales
     if (params) p = *params; else dgsm_default_params(&p);
     int rc = check_common(ctx, means, scales, opac, n, lights, L, H, W, radii, K, p);
     if (rc) return rc;
+    if (p.tile == 4) return fail(ctx, DGSM_ERR_INVALID_ARG, "dgsm_build supports tile 8 or 16");
     if (n > 0 && !quats) return fail(ctx, DGSM_ERR_INVALID_ARG, "null quats");
     if (!atlas) return fail(ctx, DGSM_ERR_INVALID_ARG, "null atlas");
     if (p.atlas_dtype < DGSM_F32 || p.atlas_dtype > DGSM_BF16)
         return fail(ctx, DGSM_ERR_INVALID_ARG, "atlas_dtype must be DGSM_F32, DGSM_F16 or DGSM_BF16");
+    if (build_smem_bytes(K, p.tile, p.chunk) > 220 * 1024)
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "K x tile^2 too large for shared memory: use tile 8");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
+    const bool prof = ctx->prof && ctx->prof_count < dgsm_ctx::PROF_RING;
+    cudaEvent_t *ev = prof ? ctx->prof_ev[ctx->prof_count] : nullptr;
+    if (prof) cudaEventRecord(ev[0], s);
     BinOut b;
     if ((rc = run_binning(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, s, &b)))
         return rc;
+
+    // ---- work items: every tile's list cut into pieces of <= item Gaussians ----
+    const int nkeys = L * b.n_tiles;
+    const uint32_t item = (uint32_t)(ITEM_CHUNKS * p.chunk);
+    const int64_t max_items = nkeys + b.P / item + 1;
+    void *w_items, *w_acc, *w_done;
+    const size_t items_bytes = sizeof(Item) * (size_t)max_items + sizeof(uint32_t) * (size_t)nkeys +
+                               4 * sizeof(unsigned long long);
+    if ((rc = ws_reserve(ctx, WS_ITEMS, items_bytes, &w_items))) return rc;
+    const size_t acc_bytes = sizeof(float) * (size_t)L * K * H * W;
+    const bool acc_new = ctx->ws_cap[WS_ACCUM] < acc_bytes;
+    if ((rc = ws_reserve(ctx, WS_ACCUM, acc_bytes, &w_acc))) return rc;
+    const bool done_new = ctx->ws_cap[WS_DONE] < sizeof(uint32_t) * (size_t)nkeys;
+    if ((rc = ws_reserve(ctx, WS_DONE, sizeof(uint32_t) * (size_t)nkeys, &w_done))) return rc;
+    // the accumulators and counters are returned to zero by the kernel that
+    // consumes them; they only need clearing when freshly allocated
+    if (acc_new) e = cudaMemsetAsync(w_acc, 0, ctx->ws_cap[WS_ACCUM], s);
+    if (e == cudaSuccess && done_new) e = cudaMemsetAsync(w_done, 0, ctx->ws_cap[WS_DONE], s);
+    Item *items = (Item *)w_items;
+    uint32_t *item_cnt = (uint32_t *)(items + max_items);
+    // two 8-byte-aligned counters after the per-key item counts
+    unsigned long long *n_items_dev =
+        (unsigned long long *)(((uintptr_t)(item_cnt + nkeys) + 7) & ~(uintptr_t)7);
+    unsigned int *counter = (unsigned int *)(n_items_dev + 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "build: item memset");
+    item_count_kernel<<<(nkeys + 255) / 256, 256, 0, s>>>(b.ts, b.te, nkeys, item, item_cnt);
+    if ((rc = scan_exclusive_u32(ctx, item_cnt, item_cnt, nkeys, n_items_dev, s))) return rc;
+    item_expand_kernel<<<(nkeys + 255) / 256, 256, 0, s>>>(b.ts, b.te, nkeys, item, item_cnt, items);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "build: item kernels");
+    if (prof) cudaEventRecord(ev[1], s);
     const uint32_t *vals = b.vals ? b.vals : b.ts;  // unused when there are no pairs
     switch (p.atlas_dtype) {
         case DGSM_F32:
-            rc = launch_build_tiles<float>(ctx, b.brec, vals, b.ts, b.te, radii, K, H, W, p.tile,
-                                           b.tx, b.n_tiles, L, n, p.chunk, atlas, s);
+            rc = launch_build_items<float>(ctx, b.brec, vals, items, n_items_dev, counter, radii, K,
+                                           H, W, p.tile, b.tx, b.n_tiles, n, p.chunk,
+                                           (float *)w_acc, (unsigned *)w_done, atlas, s);
             break;
         case DGSM_F16:
-            rc = launch_build_tiles<__half>(ctx, b.brec, vals, b.ts, b.te, radii, K, H, W, p.tile,
-                                            b.tx, b.n_tiles, L, n, p.chunk, atlas, s);
+            rc = launch_build_items<__half>(ctx, b.brec, vals, items, n_items_dev, counter, radii,
+                                            K, H, W, p.tile, b.tx, b.n_tiles, n, p.chunk,
+                                            (float *)w_acc, (unsigned *)w_done, atlas, s);
             break;
         default:
-            rc = launch_build_tiles<__nv_bfloat16>(ctx, b.brec, vals, b.ts, b.te, radii, K, H, W,
-                                                   p.tile, b.tx, b.n_tiles, L, n, p.chunk, atlas, s);
+            rc = launch_build_items<__nv_bfloat16>(ctx, b.brec, vals, items, n_items_dev, counter,
+                                                   radii, K, H, W, p.tile, b.tx, b.n_tiles, n,
+                                                   p.chunk, (float *)w_acc, (unsigned *)w_done,
+                                                   atlas, s);
     }
     if (rc) return rc;
+    if (prof) {
+        cudaEventRecord(ev[2], s);
+        ++ctx->prof_count;
+    }
     ctx->h_pinned[8] = (unsigned long long)b.P;  // pair count of this build
     return DGSM_OK;
 }

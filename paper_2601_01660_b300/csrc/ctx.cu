@@ -93,6 +93,9 @@ extern "C" void dgsm_destroy(dgsm_ctx *ctx) {
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->d_stats) cudaFree(ctx->d_stats);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    for (int b = 0; b < dgsm_ctx::PROF_RING; ++b)
+        for (int k = 0; k < 3; ++k)
+            if (ctx->prof_ev[b][k]) cudaEventDestroy(ctx->prof_ev[b][k]);
     delete ctx;
 }
 
@@ -122,5 +125,39 @@ extern "C" int dgsm_sync_status(dgsm_ctx *ctx, void *stream) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "dgsm_sync_status");
     int code = *(int *)ctx->h_pinned;
     if (code != DGSM_OK) return fail(ctx, code, std::string("device status: ") + dgsm_status_string(code));
+    return DGSM_OK;
+}
+
+extern "C" int dgsm_set_profiling(dgsm_ctx *ctx, int enable) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    if (enable && !ctx->prof_ev[0][0]) {
+        for (int b = 0; b < dgsm_ctx::PROF_RING; ++b)
+            for (int k = 0; k < 3; ++k) {
+                e = cudaEventCreate(&ctx->prof_ev[b][k]);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventCreate");
+            }
+    }
+    ctx->prof = enable != 0;
+    ctx->prof_count = 0;
+    return DGSM_OK;
+}
+
+extern "C" int dgsm_profile_collect(dgsm_ctx *ctx, double *ms_out, int max_builds, int *n_out) {
+    if (!ctx || !n_out || max_builds < 0 || (max_builds > 0 && !ms_out)) return DGSM_ERR_INVALID_ARG;
+    const int n = ctx->prof_count < dgsm_ctx::PROF_RING ? ctx->prof_count : dgsm_ctx::PROF_RING;
+    int w = 0;
+    for (int b = 0; b < n && w < max_builds; ++b, ++w) {
+        float a = 0.f, c = 0.f;
+        cudaError_t e = cudaEventSynchronize(ctx->prof_ev[b][2]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ctx->prof_ev[b][0], ctx->prof_ev[b][1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&c, ctx->prof_ev[b][1], ctx->prof_ev[b][2]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "dgsm_profile_collect");
+        ms_out[2 * w] = a;
+        ms_out[2 * w + 1] = c;
+    }
+    *n_out = w;
+    ctx->prof_count = 0;
     return DGSM_OK;
 }

@@ -12,7 +12,7 @@
 // Context: device, error text, device status word, growable workspace.
 // ---------------------------------------------------------------------------
 enum WsSlot {
-    WS_BUILD_REC = 0,  // per (light, Gaussian) build record, 64 B
+    WS_BUILD_REC = 0,  // per (light, Gaussian) build record, 80 B
     WS_BIN_REC,        // per (light, Gaussian) binning record, 32 B
     WS_COUNTS,         // per (light, Gaussian) tile count / offset, u32
     WS_SCAN_TMP,       // scan block sums
@@ -20,7 +20,12 @@ enum WsSlot {
     WS_KEYS_A, WS_VALS_A, WS_KEYS_B, WS_VALS_B,
     WS_HIST,           // radix histograms (+ their scan)
     WS_RANGES,         // per (light, tile) start/end
+    WS_ITEMS,          // build work items (+ per-key item counts, item counter)
+    WS_ACCUM,          // per-voxel tau accumulators of tiles split into several items
+    WS_DONE,           // per-key count of finished items
     WS_SH_PART,        // SH fit per-block partial sums
+    WS_CENTROID,       // weighted-centroid partial sums
+    WS_FRAME,          // device copies of a host frame (dgsm_frame_host)
     WS_NSLOTS
 };
 
@@ -33,6 +38,11 @@ struct dgsm_ctx {
     unsigned long long *d_stats = nullptr;   // [0] rays tested, [1] ray evals, [2] shell evals, [3] pairs
     unsigned long long *h_pinned = nullptr;  // pinned staging for small device->host reads
     int num_sms = 148;
+    // optional phase timing of dgsm_build: events recorded on the caller's stream
+    static constexpr int PROF_RING = 256;
+    bool prof = false;
+    int prof_count = 0;
+    cudaEvent_t prof_ev[PROF_RING][3] = {};
 };
 
 namespace dgsm {

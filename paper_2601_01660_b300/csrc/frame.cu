@@ -1,0 +1,162 @@
+// frame.cu -- one shadowed and relit frame from host memory, and the
+// alpha-weighted centroid that orients the relight normals.
+//
+// dgsm_frame_host strings the hot path together for callers whose Gaussians
+// live in host memory: copy in, build the atlas from every Gaussian (Sec.
+// 3.2), attenuate every Gaussian (Sec. 3.3), fit the probe (Sec. 3.4), relight
+// the avatar range (Sec. 3.5) in place, copy the colours out.
+#include <algorithm>
+
+#include "dgsm_internal.cuh"
+
+namespace dgsm {
+namespace {
+
+constexpr int CEN_THREADS = 256;
+
+__global__ void __launch_bounds__(CEN_THREADS) centroid_partial_kernel(
+    const float *__restrict__ means, const float *__restrict__ w, int64_t n,
+    double *__restrict__ partials) {
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double wi = w ? (double)w[i] : 1.0;
+        a[0] += wi * means[3 * i];
+        a[1] += wi * means[3 * i + 1];
+        a[2] += wi * means[3 * i + 2];
+        a[3] += wi;
+    }
+    __shared__ double red[CEN_THREADS / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = 0; c < 4; ++c) {
+        double x = a[c];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[warp][c] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double x = 0.0;
+        for (int q = 0; q < CEN_THREADS / 32; ++q) x += red[q][threadIdx.x];
+        partials[4 * blockIdx.x + threadIdx.x] = x;
+    }
+}
+
+__global__ void centroid_final_kernel(const double *__restrict__ partials, int nb,
+                                      float *__restrict__ out) {
+    if (threadIdx.x != 0) return;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = 0; b < nb; ++b)
+        for (int c = 0; c < 4; ++c) a[c] += partials[4 * b + c];
+    const double inv = a[3] > 0.0 ? 1.0 / a[3] : 0.0;
+    out[0] = (float)(a[0] * inv);
+    out[1] = (float)(a[1] * inv);
+    out[2] = (float)(a[2] * inv);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace dgsm
+
+using namespace dgsm;
+
+extern "C" int dgsm_weighted_centroid(dgsm_ctx *ctx, const float *means, const float *weights,
+                                      int64_t n, float *out, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (n < 0 || !out || (n > 0 && !means)) return fail(ctx, DGSM_ERR_INVALID_ARG, "centroid: bad arguments");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n + CEN_THREADS - 1) / CEN_THREADS,
+                                                               (int64_t)ctx->num_sms));
+    void *part;
+    int rc = ws_reserve(ctx, WS_CENTROID, sizeof(double) * 4 * nb, &part);
+    if (rc) return rc;
+    centroid_partial_kernel<<<nb, CEN_THREADS, 0, s>>>(means, weights, n, (double *)part);
+    centroid_final_kernel<<<1, 32, 0, s>>>((const double *)part, nb, out);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "centroid kernels");
+}
+
+extern "C" int dgsm_frame_host(dgsm_ctx *ctx, const dgsm_frame_host_in *in,
+                               const dgsm_params *params, const dgsm_relight_params *rparams,
+                               float *colors_out, float *sh_out, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (!in || !colors_out) return fail(ctx, DGSM_ERR_INVALID_ARG, "frame: null input or output");
+    const int64_t n = in->n;
+    if (n < 0 || in->relight_begin < 0 || in->relight_end < in->relight_begin || in->relight_end > n)
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "frame: bad Gaussian count or relight range");
+    if (n > 0 && (!in->means || !in->scales || !in->quats || !in->opac || !in->colors))
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "frame: null Gaussian array");
+    if (!in->lights || in->n_lights < 1 || in->n_lights > 64 || !in->radii || in->K < 1 || in->K > 256)
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "frame: bad lights or radii");
+    if (in->n_cube < 1 || !in->cube_dirs || !in->cube_rgb || !in->cube_w)
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "frame: need cubemap samples");
+    dgsm_params p;
+    if (params) p = *params; else dgsm_default_params(&p);
+    const int L = in->n_lights, K = in->K, H = in->H, W = in->W;
+    if (H < 1 || W < 1 || H > 4096 || W > 4096) return fail(ctx, DGSM_ERR_INVALID_ARG, "frame: bad H, W");
+    const size_t esz = p.atlas_dtype == DGSM_F32 ? 4 : 2;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // carve one device buffer
+    const size_t sz_means = align256(12 * (size_t)n), sz_q = align256(16 * (size_t)n),
+                 sz_op = align256(4 * (size_t)n), sz_l = align256(12 * (size_t)L),
+                 sz_r = align256(4 * (size_t)K), sz_cube3 = align256(12 * (size_t)in->n_cube),
+                 sz_cube1 = align256(4 * (size_t)in->n_cube),
+                 sz_atlas = align256(esz * (size_t)L * K * H * W), sz_small = 256;
+    const size_t total = 4 * sz_means + sz_q + sz_op + sz_l + sz_r + 2 * sz_cube3 + sz_cube1 +
+                         sz_atlas + 2 * sz_small;
+    void *base;
+    int rc = ws_reserve(ctx, WS_FRAME, total, &base);
+    if (rc) return rc;
+    char *c = (char *)base;
+    auto take = [&](size_t bytes) { char *r = c; c += bytes; return r; };
+    float *d_means = (float *)take(sz_means), *d_scales = (float *)take(sz_means);
+    float *d_colors = (float *)take(sz_means), *d_out = (float *)take(sz_means);
+    float *d_quats = (float *)take(sz_q), *d_opac = (float *)take(sz_op);
+    float *d_lights = (float *)take(sz_l), *d_radii = (float *)take(sz_r);
+    float *d_cd = (float *)take(sz_cube3), *d_cr = (float *)take(sz_cube3);
+    float *d_cw = (float *)take(sz_cube1);
+    void *d_atlas = take(sz_atlas);
+    float *d_sh = (float *)take(sz_small), *d_cen = (float *)take(sz_small);
+
+    struct Cp { void *dst; const void *src; size_t bytes; } cps[] = {
+        {d_means, in->means, 12 * (size_t)n}, {d_scales, in->scales, 12 * (size_t)n},
+        {d_quats, in->quats, 16 * (size_t)n}, {d_opac, in->opac, 4 * (size_t)n},
+        {d_colors, in->colors, 12 * (size_t)n}, {d_lights, in->lights, 12 * (size_t)L},
+        {d_radii, in->radii, 4 * (size_t)K}, {d_cd, in->cube_dirs, 12 * (size_t)in->n_cube},
+        {d_cr, in->cube_rgb, 12 * (size_t)in->n_cube}, {d_cw, in->cube_w, 4 * (size_t)in->n_cube}};
+    for (const Cp &cp : cps) {
+        if (cp.bytes == 0) continue;
+        e = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "frame: host to device copy");
+    }
+    if ((rc = dgsm_build(ctx, d_means, d_scales, d_quats, d_opac, n, d_lights, L, H, W, d_radii, K,
+                         &p, d_atlas, s)))
+        return rc;
+    if ((rc = dgsm_attenuate(ctx, d_atlas, nullptr, p.atlas_dtype, L, H, W, d_radii, K, d_lights,
+                             d_means, d_colors, n, nullptr, 1.0f, d_out, nullptr, s)))
+        return rc;
+    if ((rc = sh_fit(ctx, d_cd, d_cr, d_cw, in->n_cube, in->lambda, d_sh, nullptr, s))) return rc;
+    const int64_t a0 = in->relight_begin, na = in->relight_end - in->relight_begin;
+    if (na > 0) {
+        if ((rc = dgsm_weighted_centroid(ctx, d_means + 3 * a0, d_opac + a0, na, d_cen, s))) return rc;
+        if ((rc = sh_relight(ctx, d_sh, d_means + 3 * a0, d_quats + 4 * a0, d_scales + 3 * a0, nullptr,
+                             d_cen, d_out + 3 * a0, na, rparams, d_out + 3 * a0, s)))
+            return rc;
+    }
+    if (n > 0) {
+        e = cudaMemcpyAsync(colors_out, d_out, 12 * (size_t)n, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "frame: device to host copy");
+    }
+    if (sh_out) {
+        e = cudaMemcpyAsync(sh_out, d_sh, 27 * sizeof(float), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "frame: device to host copy");
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "frame: synchronize");
+    return dgsm_sync_status(ctx, stream);
+}

@@ -59,13 +59,16 @@ def test_binning_light_inside_and_beyond_shells(nat, orc):
     assert np.array_equal(vg.cpu().numpy().astype(np.uint32), vo)
 
 
-@pytest.mark.parametrize("H,W,tile,K", [(44, 60, 8, 12), (32, 32, 16, 7), (20, 36, 4, 5)])
-def test_build_matches_oracle_every_voxel(nat, orc, H, W, tile, K):
+@pytest.mark.parametrize("H,W,tile,K,chunk", [(44, 60, 8, 12, 64), (32, 32, 16, 7, 16),
+                                               (20, 36, 8, 5, 16), (40, 24, 8, 9, 32)])
+def test_build_matches_oracle_every_voxel(nat, orc, H, W, tile, K, chunk):
+    """Small chunks cut long tile lists into several work items, so this also
+    covers the cross-item accumulation."""
     sc = scenes.cube_scene(3000, seed=5 + K)
     lights = np.float32([[0, 0, 0], [0.3, -0.2, 0.4]])
     radii = scenes.radii_linear(0.1, 8, K)
     T_ref = orc.build_atlas(sc, lights, H, W, radii)
-    T = _build(nat, sc, lights, H, W, radii, tile=tile).double().cpu().numpy()
+    T = _build(nat, sc, lights, H, W, radii, tile=tile, chunk=chunk).double().cpu().numpy()
     err = np.abs(T - T_ref)
     assert err.max() <= TOL_F32, (err.max(), np.unravel_index(err.argmax(), err.shape))
 
@@ -142,3 +145,5 @@ def test_bad_arguments_are_rejected(nat):
     assert ei.value.code == 1
     with pytest.raises(nat.DGSMError):
         _build(nat, sc, np.float32([[0, 0, 0]]), 16, 16, scenes.radii_linear(0.1, 8, 4), chunk=4)
+    with pytest.raises(nat.DGSMError):   # 4x4 tiles: binning only
+        _build(nat, sc, np.float32([[0, 0, 0]]), 16, 16, scenes.radii_linear(0.1, 8, 4), tile=4)

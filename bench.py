@@ -39,12 +39,13 @@ WORKLOAD = "room1p6m"
 # Algorithmic single-precision work of the build tile kernel, per unit
 # (arithmetic a minimal implementation of the closed form must issue):
 #   per Gaussian-ray evaluation: whitened direction 9, a 3, d'.w' 3, w' x d' 6,
-#     |.|^2 3, m^2 and s* 2, setup of the erfc terms 7            -> 33 FP32 + 3 MUFU
+#     |.|^2 3, m^2 and s* 2, chord half-length 3, setup of the erfc terms 7
+#                                                                 -> 36 FP32 + 4 MUFU
 #   per shell evaluation (Eq. 3 at one radius): argument 1, erfc polynomial
 #     and its reciprocal 6, exponent 2, scaling 2, select/difference/accumulate 5
 #                                                                 -> 16 FP32 + 2 MUFU
 #   per voxel: prefix sum, clamp, exp                             ->  3 FP32 + 1 MUFU
-FP32_PER_EVAL, MUFU_PER_EVAL = 33, 3
+FP32_PER_EVAL, MUFU_PER_EVAL = 36, 4
 FP32_PER_SHELL, MUFU_PER_SHELL = 16, 2
 FP32_PER_VOXEL, MUFU_PER_VOXEL = 3, 1
 SMS = 148

@@ -41,7 +41,7 @@ class Params(C.Structure):
                 ("chunk", C.c_int32), ("atlas_dtype", C.c_int32), ("reserved", C.c_int32)]
 
     @classmethod
-    def make(cls, kappa=1.0, eps_cull=1e-7, tile=8, chunk=64, atlas_dtype="f32"):
+    def make(cls, kappa=1.0, eps_cull=1e-7, tile=8, chunk=128, atlas_dtype="f32"):
         p = cls()
         _lib.dgsm_default_params(C.byref(p))
         p.kappa, p.eps_cull, p.tile, p.chunk = kappa, eps_cull, tile, chunk

@@ -15,12 +15,13 @@
 //                       Gaussians
 //   build_items_kernel  persistent: blocks pull items from an atomic counter;
 //                       stage the item's records with cp.async (double
-//                       buffered); per (texel ray, Gaussian) a cone pre-test,
-//                       then the surviving pairs are compacted per warp and
-//                       evaluated densely: the exact culling test and Eq. 3 at
-//                       the shells of the Gaussian's window, accumulated as
-//                       per-shell increments; the last item of a tile takes
-//                       the shell-wise prefix sum and T = exp(-tau) (Eq. 4).
+//                       buffered); every (texel ray, Gaussian) pair gets the
+//                       exact culling test in the Gaussian's whitened frame;
+//                       the hits are compacted per warp and evaluated densely
+//                       (Eq. 3 at the shells on the ray's chord through the
+//                       culling ellipsoid, accumulated as per-shell increments);
+//                       the last item of a tile takes the shell-wise prefix
+//                       sum and T = exp(-tau) (Eq. 4).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -33,20 +34,19 @@ namespace dgsm {
 namespace {
 
 constexpr int SUPER = 8;       // super-tile edge, in tiles
-constexpr int REC_F4 = 5;      // float4 per build record
+constexpr int REC_F4 = 4;      // float4 per build record
 constexpr int BT_THREADS = 256;
 constexpr int BT_WARPS = BT_THREADS / 32;
-constexpr int QCAP = 64;       // per-warp queue of (record, texel) pairs
+constexpr int QCAP = 64;       // per-warp queue of hits: (a, d'.w', |w' x d'|^2, record/texel id)
 constexpr int ITEM_CHUNKS = 16;  // a work item holds at most ITEM_CHUNKS * chunk Gaussians
 
-// Per (light, Gaussian) record read by the build kernel (80 bytes):
+// Per (light, Gaussian) record read by the build kernel (64 bytes):
 //   r0 = (M00 M01 M02 M10), r1 = (M11 M12 M20 M21), r2 = (M22 w'x w'y w'z),
-//   r3 = (beta sqrt(pi/2), k^2, packed window, cos of the bounding cone - margin),
-//   r4 = (unit direction to the Gaussian, 0)
+//   r3 = (beta sqrt(pi/2), k^2, packed window, 0)
 // packed window: bits 0-9 first shell of the window, 10-19 first shell past
 // it, bit 20 = light inside the Gaussian's culling sphere.
 struct __align__(16) BuildRec {
-    float4 r0, r1, r2, r3, r4;
+    float4 r0, r1, r2, r3;
 };
 
 // Per (light, Gaussian) binning record (32 bytes): a = (dir xyz, cos theta),
@@ -215,18 +215,14 @@ __global__ void __launch_bounds__(256) prep_kernel(
             continue;
         }
         const bool inside = r >= dist;
-        float cone_cos = -2.0f;
-        float3 dir = make_float3(0.f, 0.f, 1.f);
         if (inside) {
             br.a = make_float4(0.f, 0.f, 1.f, -1.f);
             br.b = make_float4(0.f, 2.f, 0.f, 0.f);
         } else {
             const float sn = xdiv(r, dist);
             const float cs = xsqrt(xsub(1.0f, xmul(sn, sn)));
-            dir = make_float3(xdiv(vx, dist), xdiv(vy, dist), xdiv(vz, dist));
-            br.a = make_float4(dir.x, dir.y, dir.z, cs);
+            br.a = make_float4(xdiv(vx, dist), xdiv(vy, dist), xdiv(vz, dist), cs);
             br.b = make_float4(sn, 1.f, 0.f, 0.f);
-            cone_cos = cs - 1e-5f;  // pre-test margin for rounding of the texel directions
         }
         bin[idx] = br;
         if (!quats) continue;
@@ -265,8 +261,7 @@ __global__ void __launch_bounds__(256) prep_kernel(
         rec.r0 = make_float4(M00, M01, M02, M10);
         rec.r1 = make_float4(M11, M12, M20, M21);
         rec.r2 = make_float4(M22, wx, wy, wz);
-        rec.r3 = make_float4(bpref, k2, __int_as_float(packed), cone_cos);
-        rec.r4 = make_float4(dir.x, dir.y, dir.z, 0.f);
+        rec.r3 = make_float4(bpref, k2, __int_as_float(packed), 0.f);
         brec[idx] = rec;
     }
 }
@@ -406,60 +401,88 @@ __device__ __forceinline__ float mass_below(float x, float A0, float hm2, float 
     return x >= 0.0f ? full - tail : tail;
 }
 
-// Exact culling test and Eq. 3 at the shells of the Gaussian's window for one
-// (texel ray, Gaussian) pair; adds the per-shell optical-depth increments to
-// D[k * nt + texel].  Returns true when the ray cuts the culling ellipsoid.
-__device__ __forceinline__ bool eval_pair(const float4 *rec, float dx, float dy, float dz,
-                                          const float *rs, int K, float *D, int nt, int texel,
-                                          unsigned long long &n_shell) {
-    const float4 q0 = rec[0], q1 = rec[1], q2 = rec[2], q3 = rec[3];
-    // whitened ray direction d' = M d
+// Geometry of one (texel ray, Gaussian) pair in the Gaussian's whitened
+// frame: d' = M d, a = |d'|^2 = d^T A d, pw = d'.w' = -b, c2 = |w' x d'|^2 =
+// m^2 a (the Lagrange identity: no cancellation of large squares).
+struct PairGeom {
+    float a, pw, c2;
+};
+
+__device__ __forceinline__ PairGeom pair_geom(const float4 &q0, const float4 &q1, const float4 &q2,
+                                              float dx, float dy, float dz) {
     const float px = fmaf(q0.x, dx, fmaf(q0.y, dy, q0.z * dz));
     const float py = fmaf(q0.w, dx, fmaf(q1.x, dy, q1.y * dz));
     const float pz = fmaf(q1.z, dx, fmaf(q1.w, dy, q2.x * dz));
     const float wx = q2.y, wy = q2.z, wz = q2.w;
-    const float a = fmaf(px, px, fmaf(py, py, pz * pz));   // d^T A d
-    const float pw = fmaf(px, wx, fmaf(py, wy, pz * wz));  // -b
-    const float cx = fmaf(wy, pz, -wz * py);               // w' x d'
+    PairGeom g;
+    g.a = fmaf(px, px, fmaf(py, py, pz * pz));
+    g.pw = fmaf(px, wx, fmaf(py, wy, pz * wz));
+    const float cx = fmaf(wy, pz, -wz * py);
     const float cy = fmaf(wz, px, -wx * pz);
     const float cz = fmaf(wx, py, -wy * px);
-    const float c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-    const float ia = rcp_approx(a);
-    const float m2 = c2 * ia;  // c - b^2/a without cancellation
-    const float ss = pw * ia;  // closest approach s* = -b/a
+    g.c2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+    return g;
+}
+
+// The ray cuts the culling ellipsoid (m^2 <= k^2) at t > 0 (s* > 0, unless
+// the light is inside the culling sphere).
+__device__ __forceinline__ bool pair_hit(const PairGeom &g, float k2, bool inside) {
+    return g.c2 <= k2 * g.a && (inside || g.pw > 0.0f);
+}
+
+// Eq. 3 for a hit pair at the shells on its chord, as per-shell increments of
+// the optical depth added to D[k * nt + texel].
+__device__ __forceinline__ void eval_shells(const PairGeom &g, const float4 &q3, const float *rs,
+                                            int K, float *D, int nt, int texel,
+                                            unsigned long long &n_shell) {
     const int packed = __float_as_int(q3.z);
     const bool inside = (packed >> 20) & 1;
-    if (!(m2 <= q3.y && (inside || ss > 0.0f))) return false;
     const int klo = packed & 1023, kend = (packed >> 10) & 1023;
-    n_shell += kend - klo;
-    const float rsa = rsqrt_approx(a);
+    const float ia = rcp_approx(g.a);
+    const float m2 = g.c2 * ia;   // c - b^2/a
+    const float ss = g.pw * ia;   // closest approach s* = -b/a
+    const float rsa = rsqrt_approx(g.a);
+    // The ray's mass outside its chord through the culling ellipsoid,
+    // s in s* +- sqrt((k^2 - m^2)/a), is at most eps_cull (the same bound
+    // as the culling): shells before the chord get nothing, shells after it
+    // the whole remaining mass.  The chord lies inside the sphere window
+    // [klo, kend) of the record.
+    const float c2h = fmaxf(q3.y - m2, 1e-30f);
+    const float half = c2h * rsqrt_approx(c2h) * rsa;
+    const float lo_r = ss - half, hi_r = ss + half;
+    int k = klo;
+    while (k < kend && rs[k] < lo_r) ++k;
     const float A0 = q3.x * rsa;                 // beta sqrt(pi/(2a))
-    const float h = a * rsa * 0.70710678118f;    // sqrt(a/2)
+    const float h = g.a * rsa * 0.70710678118f;  // sqrt(a/2)
     const float hm2 = -0.72134752044f * m2;      // -m^2/2 log2(e)
     const float full = 2.0f * A0 * ex2_approx(hm2);
     const float hs = h * ss;
     const float F0 = inside ? mass_below(-hs, A0, hm2, full) : 0.0f;
     float Gprev = 0.0f;
-    for (int k = klo; k < kend; ++k) {
+    for (; k < kend && rs[k] <= hi_r; ++k) {
         const float G = mass_below(fmaf(h, rs[k], -hs), A0, hm2, full) - F0;
         atomicAdd(D + k * nt + texel, fmaxf(G - Gprev, 0.0f));
         Gprev = fmaxf(G, Gprev);
+        ++n_shell;
     }
-    if (kend < K) atomicAdd(D + kend * nt + texel, fmaxf(full - F0 - Gprev, 0.0f));
-    return true;
+    if (k < K) atomicAdd(D + k * nt + texel, fmaxf(full - F0 - Gprev, 0.0f));
 }
 
 size_t build_smem_bytes(int K, int tile, int chunk) {
     const int nt = tile * tile;
     return (size_t)2 * chunk * REC_F4 * sizeof(float4) + (size_t)nt * sizeof(float4) +
            (size_t)K * nt * sizeof(float) + (size_t)((K + 3) & ~3) * sizeof(float) +
-           (size_t)BT_WARPS * QCAP * sizeof(uint16_t);
+           (size_t)BT_WARPS * QCAP * sizeof(float4);
 }
 
-// Persistent build kernel: 8 warps per block; tile 8 -> 2 texel groups x 4
-// record groups, tile 16 -> 8 texel groups x 1 record group.
+// Persistent build kernel, 8 warps per block.  A warp owns 64 texels (two per
+// lane): with tile 8 all 8 warps cover the whole tile, with tile 16 they form
+// 4 texel groups of 2 warps.  The records of a staged chunk are handed out one
+// at a time to the warps of each texel group; a warp tests its texels against
+// the record (broadcast from shared memory) and queues the hits with their
+// geometry; 32 queued hits at a time are then evaluated lane-parallel.
 template <typename OutT>
-__global__ void __launch_bounds__(BT_THREADS) build_items_kernel(
+__global__ void __launch_bounds__(BT_THREADS, 5) build_items_kernel(
     const float4 *__restrict__ brec, const uint32_t *__restrict__ vals,
     const Item *__restrict__ items, const unsigned long long *__restrict__ n_items_total,
     unsigned int *__restrict__ item_counter, const float *__restrict__ radii, int K, int H, int W,
@@ -468,26 +491,26 @@ __global__ void __launch_bounds__(BT_THREADS) build_items_kernel(
     unsigned long long *__restrict__ stats) {
     extern __shared__ float4 smem4[];
     const int nt = tile * tile;
-    const int n_tg = nt / 32;
-    const int n_rg = BT_WARPS / n_tg;
+    const int n_tg = nt / 64;
     float4 *stage = smem4;                                   // [2][chunk * REC_F4]
     float4 *tdir = stage + 2 * chunk * REC_F4;               // [nt] (dir, valid)
     float *D = reinterpret_cast<float *>(tdir + nt);         // [K][nt]
     float *rs = D + K * nt;                                  // [K]
-    uint16_t *queue = reinterpret_cast<uint16_t *>(rs + ((K + 3) & ~3));  // [BT_WARPS][QCAP]
+    float4 *queue = reinterpret_cast<float4 *>(rs + ((K + 3) & ~3));  // [BT_WARPS][QCAP]
     __shared__ uint4 s_item;
     __shared__ int s_last;
+    __shared__ int s_next[BT_WARPS];
     __shared__ unsigned long long s_cnt[3];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tg = warp % n_tg, rg = warp / n_tg;
+    const int tg = warp % n_tg;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t HW = (int64_t)H * W;
     const unsigned long long total_items = *n_items_total;
     for (int k = tid; k < K; k += BT_THREADS) rs[k] = radii[k];
     if (tid < 3) s_cnt[tid] = 0ull;
     unsigned long long n_hit = 0, n_shell = 0, n_tested = 0;
-    uint16_t *q = queue + warp * QCAP;
+    float4 *q = queue + warp * QCAP;
 
     for (;;) {
         if (tid == 0) {
@@ -513,39 +536,39 @@ __global__ void __launch_bounds__(BT_THREADS) build_items_kernel(
             const float inv = rsqrtf(x * x + y * y + z * z);
             tdir[e] = make_float4(x * inv, y * inv, z * inv, (i < H && j < W) ? 1.0f : 0.0f);
         }
-        const int my_t = tg * 32 + lane;
         const float4 *src = brec + (int64_t)l * N * REC_F4;
         const int nrec = (int)(end - start);
         const int nchunks = (nrec + chunk - 1) / chunk;
-        // staging: entry e of a chunk = record e / 5, part e % 5; a thread owns e = tid, tid + 256
-        uint32_t gnext[2] = {0u, 0u};
+        // staging: entry e of a chunk = record e / REC_F4, part e % REC_F4;
+        // a thread owns e = tid, tid + 256, tid + 512
+        uint32_t gnext[3] = {0u, 0u, 0u};
         auto load_idx = [&](int c, uint32_t *g) {
             const int base = (int)start + c * chunk, cnt = min(chunk, (int)end - base);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int e = tid + h * BT_THREADS;
-                g[h] = e < cnt * REC_F4 ? __ldg(vals + base + e / REC_F4) : 0u;
+            for (int hh = 0; hh < 3; ++hh) {
+                const int e = tid + hh * BT_THREADS;
+                g[hh] = e < cnt * REC_F4 ? __ldg(vals + base + e / REC_F4) : 0u;
             }
         };
         auto issue = [&](int c, const uint32_t *g) {
             const int base = (int)start + c * chunk, cnt = min(chunk, (int)end - base);
             float4 *dst = stage + (c & 1) * chunk * REC_F4;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int e = tid + h * BT_THREADS;
-                if (e < cnt * REC_F4) cp_async16(dst + e, src + (int64_t)g[h] * REC_F4 + e % REC_F4);
+            for (int hh = 0; hh < 3; ++hh) {
+                const int e = tid + hh * BT_THREADS;
+                if (e < cnt * REC_F4) cp_async16(dst + e, src + (int64_t)g[hh] * REC_F4 + e % REC_F4);
             }
             cp_async_commit();
         };
         if (nchunks > 0) {
-            uint32_t g0[2];
+            uint32_t g0[3];
             load_idx(0, g0);
             issue(0, g0);
             if (nchunks > 1) load_idx(1, gnext);
         }
         __syncthreads();
-        const float4 md = tdir[my_t];
-        const bool mvalid = md.w != 0.0f;
+        const float4 dA = tdir[tg * 64 + lane], dB = tdir[tg * 64 + 32 + lane];
+        const bool vA = dA.w != 0.0f, vB = dB.w != 0.0f;
         for (int c = 0; c < nchunks; ++c) {
             if (c + 1 < nchunks) {
                 issue(c + 1, gnext);
@@ -554,36 +577,50 @@ __global__ void __launch_bounds__(BT_THREADS) build_items_kernel(
             } else {
                 cp_async_wait<0>();
             }
+            if (tid < n_tg) s_next[tid] = 0;
             __syncthreads();
             const float4 *st = stage + (c & 1) * chunk * REC_F4;
             const int cnt = min(chunk, (int)end - ((int)start + c * chunk));
             int qn = 0;
-            for (int r = rg; r < cnt; r += n_rg) {
-                const float4 r3 = st[r * REC_F4 + 3], r4 = st[r * REC_F4 + 4];
-                const bool pass = mvalid && fmaf(md.x, r4.x, fmaf(md.y, r4.y, md.z * r4.z)) >= r3.w;
-                const unsigned m = __ballot_sync(0xffffffffu, pass);
-                if (pass) q[qn + __popc(m & lt)] = (uint16_t)((r << 5) | lane);
+            auto flush = [&](int n) {  // evaluate the n (<= 32) hits at the top of the queue
+                __syncwarp();
+                if (lane < n) {
+                    const float4 e = q[qn - n + lane];
+                    const int id = __float_as_int(e.w);
+                    const int tex = tg * 64 + (id & 63);
+                    PairGeom gg;
+                    gg.a = e.x;
+                    gg.pw = e.y;
+                    gg.c2 = e.z;
+                    eval_shells(gg, st[(id >> 6) * REC_F4 + 3], rs, K, D, nt, tex, n_shell);
+                }
+                qn -= n;
+                __syncwarp();
+            };
+            auto push = [&](bool hit, const PairGeom &g, int id) {
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                if (hit) q[qn + __popc(m & lt)] = make_float4(g.a, g.pw, g.c2, __int_as_float(id));
                 qn += __popc(m);
-                if (qn >= 32) {
-                    __syncwarp();
-                    const unsigned e = q[qn - 32 + lane];
-                    const int tt = tg * 32 + (int)(e & 31u);
-                    const float4 d = tdir[tt];
-                    n_hit += eval_pair(st + (e >> 5) * REC_F4, d.x, d.y, d.z, rs, K, D, nt, tt, n_shell);
-                    qn -= 32;
-                    __syncwarp();
-                }
+                if (qn >= 32) flush(32);
+            };
+            // records are handed out dynamically to the warps of a texel group
+            for (;;) {
+                int r = 0;
+                if (lane == 0) r = atomicAdd(&s_next[tg], 1);
+                r = __shfl_sync(0xffffffffu, r, 0);
+                if (r >= cnt) break;
+                const float4 q0 = st[r * REC_F4], q1 = st[r * REC_F4 + 1], q2 = st[r * REC_F4 + 2],
+                             q3 = st[r * REC_F4 + 3];
+                const bool inside = (__float_as_int(q3.z) >> 20) & 1;
+                const PairGeom gA = pair_geom(q0, q1, q2, dA.x, dA.y, dA.z);
+                const PairGeom gB = pair_geom(q0, q1, q2, dB.x, dB.y, dB.z);
+                const bool hA = vA && pair_hit(gA, q3.y, inside);
+                const bool hB = vB && pair_hit(gB, q3.y, inside);
+                n_hit += (unsigned)hA + (unsigned)hB;
+                push(hA, gA, (r << 6) | lane);
+                push(hB, gB, (r << 6) | (32 + lane));
             }
-            if (qn > 0) {
-                __syncwarp();
-                if (lane < qn) {
-                    const unsigned e = q[lane];
-                    const int tt = tg * 32 + (int)(e & 31u);
-                    const float4 d = tdir[tt];
-                    n_hit += eval_pair(st + (e >> 5) * REC_F4, d.x, d.y, d.z, rs, K, D, nt, tt, n_shell);
-                }
-                __syncwarp();
-            }
+            if (qn > 0) flush(qn);
             __syncthreads();  // the buffer is refilled two chunks later
         }
         if (tid == 0) {
@@ -686,7 +723,7 @@ int check_common(dgsm_ctx *ctx, const float *means, const float *scales, const f
     if (H < 1 || W < 1 || H > 4096 || W > 4096) return fail(ctx, DGSM_ERR_INVALID_ARG, "H, W must be in 1..4096");
     if (!radii || K < 1 || K > 256) return fail(ctx, DGSM_ERR_INVALID_ARG, "K must be in 1..256");
     if (p.tile != 4 && p.tile != 8 && p.tile != 16) return fail(ctx, DGSM_ERR_INVALID_ARG, "tile must be 4, 8 or 16");
-    if (p.chunk < 16 || p.chunk > 64) return fail(ctx, DGSM_ERR_INVALID_ARG, "chunk must be in 16..64");
+    if (p.chunk < 16 || p.chunk > 128) return fail(ctx, DGSM_ERR_INVALID_ARG, "chunk must be in 16..128");
     if (!(p.kappa >= 0.f) || !(p.eps_cull > 0.f)) return fail(ctx, DGSM_ERR_INVALID_ARG, "kappa >= 0 and eps_cull > 0 required");
     return DGSM_OK;
 }

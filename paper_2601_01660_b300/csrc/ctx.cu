@@ -49,7 +49,7 @@ extern "C" void dgsm_default_params(dgsm_params *p) {
     p->kappa = 1.0f;
     p->eps_cull = 1e-7f;
     p->tile = 8;
-    p->chunk = 64;
+    p->chunk = 128;
     p->atlas_dtype = DGSM_F32;
     p->reserved = 0;
 }

@@ -1,6 +1,6 @@
 // attenuate.cu -- receiver attenuation by centre lookup (Sec. 3.3) on sm_103a.
 //
-// One thread per query Gaussian: per light, octahedral code of (x - o_l)
+// Per query Gaussian and light: octahedral code of (x - o_l)
 // (exact single-precision index decisions, shared with dgsm_sample_index),
 // bilinear between texel centres with clamp-to-edge, linear between the two
 // shells bracketing t; the direct part of the colour is scaled by the
@@ -51,8 +51,16 @@ __device__ __forceinline__ float lookup(const T *__restrict__ A, int H, int W, i
     return (1.0f - wt) * b0 + wt * b1;
 }
 
+constexpr int ATT_THREADS = 256;
+constexpr int ATT_U = 4;  // queries in flight per thread
+
+// Each block takes ATT_U * 256 consecutive queries; thread t handles queries
+// t, t + 256, ... of the block's range, so every load and store instruction
+// of a warp touches one contiguous span.  The ATT_U independent queries per
+// thread keep several gathers and stream loads in flight (the pass is bound
+// by memory latency unless enough requests are outstanding).
 template <typename T>
-__global__ void __launch_bounds__(256) attenuate_kernel(
+__global__ void __launch_bounds__(ATT_THREADS) attenuate_kernel(
     const T *__restrict__ atlas, const T *__restrict__ dyn, int L, int H, int W,
     const float *__restrict__ radii, int K, const float *__restrict__ lights,
     const float *__restrict__ qm, const float *cin, int64_t Q, const float *__restrict__ lw,
@@ -65,26 +73,49 @@ __global__ void __launch_bounds__(256) attenuate_kernel(
     for (int k = threadIdx.x; k < L; k += blockDim.x) wl[k] = lw ? lw[k] : 1.0f / (float)L;
     __syncthreads();
     const int64_t lstride = (int64_t)K * H * W;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < Q;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const float px = __ldg(qm + 3 * q), py = __ldg(qm + 3 * q + 1), pz = __ldg(qm + 3 * q + 2);
-        float acc = 0.0f;
-        for (int l = 0; l < L; ++l) {
-            const SampleIndex s = sample_index(px, py, pz, ls[3 * l], ls[3 * l + 1], ls[3 * l + 2],
-                                               H, W, rs, K);
-            float Tl = 1.0f;
-            if (s.t != 0.0f) {
-                Tl = lookup(atlas + l * lstride, H, W, K, s, rs);
-                if (dyn) Tl *= lookup(dyn + l * lstride, H, W, K, s, rs);
-            }
-            if (Tout) Tout[q * L + l] = Tl;
-            acc = fmaf(wl[l], Tl, acc);
+    const int64_t span = (int64_t)ATT_U * ATT_THREADS;
+    for (int64_t base = (int64_t)blockIdx.x * span; base < Q; base += (int64_t)gridDim.x * span) {
+        float px[ATT_U], py[ATT_U], pz[ATT_U], c0[ATT_U], c1[ATT_U], c2[ATT_U], acc[ATT_U];
+#pragma unroll
+        for (int u = 0; u < ATT_U; ++u) {
+            const int64_t q = base + u * ATT_THREADS + threadIdx.x;
+            const bool ok = q < Q;
+            px[u] = ok ? __ldg(qm + 3 * q) : 0.f;
+            py[u] = ok ? __ldg(qm + 3 * q + 1) : 0.f;
+            pz[u] = ok ? __ldg(qm + 3 * q + 2) : 0.f;
+            c0[u] = ok ? cin[3 * q] : 0.f;
+            c1[u] = ok ? cin[3 * q + 1] : 0.f;
+            c2[u] = ok ? cin[3 * q + 2] : 0.f;
+            acc[u] = 0.f;
         }
-        const float f = 1.0f - wd + wd * acc;
-        const float c0 = cin[3 * q], c1 = cin[3 * q + 1], c2 = cin[3 * q + 2];
-        cout[3 * q] = c0 * f;
-        cout[3 * q + 1] = c1 * f;
-        cout[3 * q + 2] = c2 * f;
+        for (int l = 0; l < L; ++l) {
+            float Tl[ATT_U];
+#pragma unroll
+            for (int u = 0; u < ATT_U; ++u) {
+                const SampleIndex s = sample_index(px[u], py[u], pz[u], ls[3 * l], ls[3 * l + 1],
+                                                   ls[3 * l + 2], H, W, rs, K);
+                Tl[u] = 1.0f;
+                if (s.t != 0.0f) {
+                    Tl[u] = lookup(atlas + l * lstride, H, W, K, s, rs);
+                    if (dyn) Tl[u] *= lookup(dyn + l * lstride, H, W, K, s, rs);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < ATT_U; ++u) {
+                const int64_t q = base + u * ATT_THREADS + threadIdx.x;
+                if (Tout && q < Q) Tout[q * L + l] = Tl[u];
+                acc[u] = fmaf(wl[l], Tl[u], acc[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < ATT_U; ++u) {
+            const int64_t q = base + u * ATT_THREADS + threadIdx.x;
+            if (q >= Q) continue;
+            const float f = 1.0f - wd + wd * acc[u];
+            __stcs(cout + 3 * q, c0[u] * f);
+            __stcs(cout + 3 * q + 1, c1[u] * f);
+            __stcs(cout + 3 * q + 2, c2[u] * f);
+        }
     }
 }
 
@@ -134,18 +165,19 @@ extern "C" int dgsm_attenuate(dgsm_ctx *ctx, const void *atlas, const void *atla
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
     if (n_q == 0) return DGSM_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    const int grid = (int)std::min<int64_t>((n_q + 255) / 256, (int64_t)ctx->num_sms * 8);
+    const int64_t span = (int64_t)ATT_U * ATT_THREADS;
+    const int grid = (int)std::min<int64_t>((n_q + span - 1) / span, (int64_t)ctx->num_sms * 32);
     switch (dtype) {
         case DGSM_F32:
-            attenuate_kernel<float><<<grid, 256, 0, s>>>((const float *)atlas, (const float *)atlas_dyn,
+            attenuate_kernel<float><<<grid, ATT_THREADS, 0, s>>>((const float *)atlas, (const float *)atlas_dyn,
                 L, H, W, radii, K, lights, q_means, colors_in, n_q, light_w, direct_frac, colors_out, T_out);
             break;
         case DGSM_F16:
-            attenuate_kernel<__half><<<grid, 256, 0, s>>>((const __half *)atlas, (const __half *)atlas_dyn,
+            attenuate_kernel<__half><<<grid, ATT_THREADS, 0, s>>>((const __half *)atlas, (const __half *)atlas_dyn,
                 L, H, W, radii, K, lights, q_means, colors_in, n_q, light_w, direct_frac, colors_out, T_out);
             break;
         default:
-            attenuate_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)atlas,
+            attenuate_kernel<__nv_bfloat16><<<grid, ATT_THREADS, 0, s>>>((const __nv_bfloat16 *)atlas,
                 (const __nv_bfloat16 *)atlas_dyn, L, H, W, radii, K, lights, q_means, colors_in, n_q,
                 light_w, direct_frac, colors_out, T_out);
     }

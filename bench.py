@@ -117,12 +117,10 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
-def load_workload(rank: int):
-    from paper_2601_01660_b300 import scenes
-    wl = scenes.workload(WORKLOAD)
-    lights = wl["lights"].copy()
-    lights[:, 0] += 0.25 * rank     # each rank: its own light, an independent problem
-    wl["lights"] = lights
+def load_workload(rank: int, name: str = WORKLOAD):
+    from paper_2601_01660_b300 import scenes, shard
+    wl = scenes.workload(name)
+    wl["lights"] = shard.offset_light(wl["lights"], rank)  # each rank: its own light
     return wl
 
 
@@ -138,7 +136,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    wl = load_workload(rank)
+    wl = load_workload(rank, args.workload)
     sc = wl["occluders"]
     av_slice = sc.meta["avatar"]
     a0, a1 = av_slice.start, av_slice.stop
@@ -197,17 +195,9 @@ def run_ours(args, rank, world, local_rank):
     prof = nat.dgsm_profile_collect()
     nat.dgsm_set_profiling(False)
     clocks = clk.summary()
-    total_ms = float(sum(step_ms))
     evals = stats["ray_evals"]
-    if dist is not None:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-        ev = torch.tensor([float(evals)], dtype=torch.float64, device=dev)
-        dist.all_reduce(ev, op=dist.ReduceOp.SUM)
-        evals_all = float(ev.item())
-    else:
-        evals_all = float(evals)
+    from paper_2601_01660_b300 import shard
+    total_ms, evals_all = shard.reduce_step_timing(float(sum(step_ms)), float(evals), device=dev)
     ms_per_step = total_ms / args.steps
     value = evals_all * args.steps / (total_ms * 1e-3)
 
@@ -252,7 +242,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "gaussians": N, "avatar_gaussians": a1 - a0,
+        "config": {"workload": args.workload, "gaussians": N, "avatar_gaussians": a1 - a0,
                    "lights_per_rank": L, "atlas": [H, W, K], "shells": "geometric 0.05-12 m",
                    "cubemap_samples": int(D_np.shape[0]), "relight_grid": [32, 64],
                    "l2": "flushed between steps (2x L2 write), outside the timed events",
@@ -420,6 +410,8 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["room1p6m", "room550k"], default=WORKLOAD,
+                    help="room550k: the same room at a third of the size (profiler captures)")
     ap.add_argument("--cpu-texels", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -301,6 +301,7 @@ def workload(name: str) -> dict:
     'room1p6m'    1.5M-Gaussian indoor room + 100k avatar, 1 light at 2.8 m,
                   512x512 atlas, 64 geometric shells 0.05-12 m, order-2 SH
                   relight of the avatar from a 6x64^2 cubemap fit.
+    'room550k'    the same room with 300k + 200k + 50k Gaussians.
     'cube3m4l'    cube generator at 3M Gaussians, 4 lights, 64x64x16.
     """
     if name == "cube20k":
@@ -310,6 +311,12 @@ def workload(name: str) -> dict:
                     H=64, W=64, radii=radii_linear(0.1, 8.0, 16))
     if name == "room1p6m":
         sc = room_scene(seed=2)
+        return dict(name=name, occluders=sc, queries=sc, lights=_f32([[0, 0, 2.8]]),
+                    H=512, W=512, radii=radii_geometric(0.05, 12.0, 64),
+                    relight=subset(sc, sc.meta["avatar"]), cubemap=cubemap_samples(64, seed=5))
+    if name == "room550k":
+        # the room at about a third of the size (for profiler captures)
+        sc = room_scene(seed=2, n_flat=300_000, n_box=200_000, n_avatar=50_000)
         return dict(name=name, occluders=sc, queries=sc, lights=_f32([[0, 0, 2.8]]),
                     H=512, W=512, radii=radii_geometric(0.05, 12.0, 64),
                     relight=subset(sc, sc.meta["avatar"]), cubemap=cubemap_samples(64, seed=5))

@@ -174,3 +174,30 @@ def test_relight_matches_oracle(nat, orc):
     _relight_check(nat, orc, av, sh, cen, {"q": 3.0, "gamma": 0.8, "t_max": 2.0})
     nrm = rng.normal(size=(av.n, 3)).astype(np.float32)
     _relight_check(nat, orc, av, sh, cen, {"n_theta": 16, "n_phi": 48}, normals=nrm)
+
+
+def test_frame_host_matches_device_calls(nat, orc):
+    """One frame from host buffers (build, attenuate, fit, relight of a
+    range) equals the same steps through the device entry points."""
+    import torch
+    sc = scenes.cube_scene(6000, seed=12)
+    lights = np.float32([[0, 0, 0], [0.5, 0.2, 1.0]])
+    radii = scenes.radii_geometric(0.05, 9, 12)
+    D, Y, w = scenes.cubemap_samples(16, seed=5)
+    a0, a1 = 4000, 6000
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+    cols, sh = nat.dgsm_frame_host(pin(sc.means), pin(sc.scales), pin(sc.quats), pin(sc.opac),
+                                   pin(sc.colors), pin(lights), 32, 40, pin(radii), pin(D), pin(Y),
+                                   pin(w), relight_range=(a0, a1))
+    d = scene_to_dev(sc)
+    atlas = nat.dgsm_build(d["means"], d["scales"], d["quats"], d["opac"], dev(lights), 32, 40,
+                           dev(radii))
+    out = nat.dgsm_attenuate(atlas, dev(radii), dev(lights), d["means"], d["colors"])
+    s2 = nat.sh_fit(dev(D), dev(Y), dev(w))
+    cen = nat.dgsm_weighted_centroid(d["means"][a0:a1], d["opac"][a0:a1])
+    nat.sh_relight(s2, d["means"][a0:a1], d["quats"][a0:a1], d["scales"][a0:a1], out[a0:a1], cen,
+                   out=out[a0:a1])
+    np.testing.assert_allclose(cols.numpy(), out.cpu().numpy(), rtol=2e-5, atol=2e-6)
+    np.testing.assert_allclose(sh.numpy(), s2.cpu().numpy(), rtol=1e-6, atol=1e-7)
+    cen_ref = (sc.means[a0:a1].astype(np.float64) * sc.opac[a0:a1, None]).sum(0) / sc.opac[a0:a1].sum()
+    np.testing.assert_allclose(cen.cpu().numpy(), cen_ref, rtol=1e-6, atol=1e-6)

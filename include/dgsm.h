@@ -179,6 +179,27 @@ int dgsm_sample_index(dgsm_ctx *ctx, const float *points, int64_t n, const float
 int sh_fit(dgsm_ctx *ctx, const float *dirs, const float *rgb, const float *w, int64_t n,
            double lambda, float *sh_out, double *sh64_out, void *stream);
 
+/* sh_fit without a context and without allocating device memory.  The paper
+ * has no counterpart: this exists for callers that cannot call cudaMalloc --
+ * a real-time frame loop in which cudaMalloc/cudaFree would synchronise the
+ * device and stall the frame, or a host that owns all device memory through
+ * its own pool.  The same computation as sh_fit (FP64 normal equations and
+ * Cholesky on the current device); its per-block partial sums live in a
+ * fixed array compiled into the library (147,712 bytes, held on every device
+ * that loads the library until the process exits).
+ *   dirs, rgb, w, n, lambda, sh_out, sh64_out: as for sh_fit, device pointers;
+ *   n <= 4,194,304 (larger n returns DGSM_ERR_WORKSPACE);
+ *   status_out: device int or NULL; receives DGSM_OK or DGSM_ERR_NOT_SPD
+ *   (then sh_out is zero).
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the one array:
+ * calls that overlap on the GPU (on concurrent streams) race and give wrong
+ * results; serialise them.  Returns DGSM_OK, DGSM_ERR_INVALID_ARG,
+ * DGSM_ERR_WORKSPACE (n too large) or DGSM_ERR_CUDA; there is no context to
+ * hold a message. */
+int sh_fit_static(const float *dirs, const float *rgb, const float *w, int64_t n, double lambda,
+                  float *sh_out, double *sh64_out, int *status_out, void *stream);
+
 /* Per-Gaussian radiance transfer (Sec. 3.5, Eqs. 8-10):
  *   s_c(n) = clip_[0,t_max]( sum_j w_j L_c(w_j) S_j / (sum_j w_j S_j + eps) ),
  *   S_j = max(0, <w_j, n>)^q,  colors_out = max(0, gamma * colors_in (.) s).

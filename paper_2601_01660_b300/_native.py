@@ -97,6 +97,7 @@ _lib.dgsm_attenuate.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32
                                 _i64, _vp, _f32, _vp, _vp, _vp]
 _lib.dgsm_sample_index.argtypes = [_vp, _vp, _i64, _vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp]
 _lib.sh_fit.argtypes = [_vp, _vp, _vp, _vp, _i64, _f64, _vp, _vp, _vp]
+_lib.sh_fit_static.argtypes = [_vp, _vp, _vp, _i64, _f64, _vp, _vp, _vp, _vp]
 _lib.sh_relight.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64,
                             C.POINTER(RelightParams), _vp, _vp]
 _lib.dgsm_sync_status.argtypes = [_vp, _vp]
@@ -108,7 +109,7 @@ _lib.dgsm_profile_collect.argtypes = [_vp, C.POINTER(C.c_double), C.c_int, C.POI
 for _fn in ("dgsm_build", "dgsm_get_build_stats", "dgsm_bin", "dgsm_attenuate",
             "dgsm_sample_index", "sh_fit", "sh_relight", "dgsm_sync_status",
             "dgsm_weighted_centroid", "dgsm_frame_host", "dgsm_set_profiling",
-            "dgsm_profile_collect"):
+            "dgsm_profile_collect", "sh_fit_static"):
     getattr(_lib, _fn).restype = C.c_int
 
 
@@ -281,6 +282,23 @@ def sh_fit(dirs, rgb, w, lam=1e-3, want64=False, ctx: Context | None = None, str
     ctx.check(_lib.sh_fit(ctx.handle, _ptr(dirs), _ptr(rgb), _ptr(w), dirs.shape[0], float(lam),
                           _ptr(sh), _ptr(sh64), _stream(stream)))
     return (sh, sh64) if want64 else sh
+
+
+def sh_fit_static(dirs, rgb, w, lam=1e-3, stream=None):
+    """sh_fit through the allocation-free entry point: (sh (3,9) float32,
+    sh (3,9) float64, status (1,) int32), all on the device.  The output
+    tensors here come from torch; the library itself allocates nothing."""
+    _need(dirs, "dirs", shape_last=3)
+    _need(rgb, "rgb", shape_last=3)
+    _need(w, "w")
+    sh = torch.empty((3, 9), dtype=torch.float32, device=dirs.device)
+    sh64 = torch.empty((3, 9), dtype=torch.float64, device=dirs.device)
+    status = torch.empty(1, dtype=torch.int32, device=dirs.device)
+    rc = _lib.sh_fit_static(_ptr(dirs), _ptr(rgb), _ptr(w), dirs.shape[0], float(lam), _ptr(sh),
+                            _ptr(sh64), _ptr(status), _stream(stream))
+    if rc != DGSM_OK:
+        raise DGSMError(rc, "sh_fit_static failed")
+    return sh, sh64, status
 
 
 def sh_relight(sh, means, quats, scales, colors, centroid, normals=None, params=None, out=None,

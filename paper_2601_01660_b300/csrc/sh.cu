@@ -1,6 +1,7 @@
 // sh.cu -- HDRI probe fit (Sec. 3.4, Eq. 7, FP64) and per-Gaussian radiance
 // transfer (Sec. 3.5, Eqs. 8-10) on sm_103a.
 #include <algorithm>
+#include <mutex>
 
 #include "dgsm_internal.cuh"
 
@@ -288,4 +289,75 @@ extern "C" int sh_relight(dgsm_ctx *ctx, const float *sh, const float *means, co
         p.n_theta, p.n_phi, colors_out);
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "relight_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// Probe fit for callers that cannot allocate device memory.
+//
+// sh_fit needs a dgsm_ctx, whose workspace is created with cudaMalloc.  Some
+// callers cannot allocate: a real-time frame loop in which cudaMalloc and
+// cudaFree would synchronise the device and stall the frame, or a host
+// application that owns all device memory through its own pool and forbids
+// allocations behind its back.  sh_fit_static runs the same two kernels with
+// their per-block partial sums in a fixed array compiled into the library
+// instead.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int FIT_STATIC_BLOCKS = 256;  // partial-sum slots of the static scratch
+constexpr int64_t FIT_STATIC_MAX_N = (int64_t)FIT_STATIC_BLOCKS * FIT_THREADS * 64;
+constexpr int FIT_STATIC_STATUS = FIT_STATIC_BLOCKS * FIT_NV;  // index of the status word
+constexpr int FIT_STATIC_DOUBLES = FIT_STATIC_STATUS + 32;
+constexpr int FIT_STATIC_MAX_DEVICES = 64;
+}  // namespace
+
+// 256 x 72 partial sums + a status word: 147,712 bytes, held on every device
+// that loads the library until the process exits.  Every call shares it.
+static __device__ __align__(256) double dgsm_fit_scratch[FIT_STATIC_DOUBLES];
+
+namespace {
+std::mutex g_fit_scratch_mu;
+double *g_fit_scratch_ptr[FIT_STATIC_MAX_DEVICES] = {};
+
+// Device address of the static scratch on `dev` (which must be current).  In
+// host code the symbol names a host-side stand-in, so the address is taken
+// once per device with cudaGetSymbolAddress and cached.
+int fit_scratch_address(int dev, double **out) {
+    std::lock_guard<std::mutex> lock(g_fit_scratch_mu);
+    if (!g_fit_scratch_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, dgsm_fit_scratch) != cudaSuccess || !p)
+            return DGSM_ERR_CUDA;
+        g_fit_scratch_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_fit_scratch_ptr[dev];
+    return DGSM_OK;
+}
+}  // namespace
+
+extern "C" int sh_fit_static(const float *dirs, const float *rgb, const float *w, int64_t n,
+                             double lambda, float *sh_out, double *sh64_out, int *status_out,
+                             void *stream) {
+    if (n < 1 || !dirs || !rgb || !w || !sh_out || !(lambda >= 0.0)) return DGSM_ERR_INVALID_ARG;
+    if (n > FIT_STATIC_MAX_N) return DGSM_ERR_WORKSPACE;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DGSM_ERR_CUDA;
+    if (dev < 0 || dev >= FIT_STATIC_MAX_DEVICES) return DGSM_ERR_INVALID_ARG;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return DGSM_ERR_CUDA;
+    double *scratch = nullptr;
+    int rc = fit_scratch_address(dev, &scratch);
+    if (rc) return rc;
+    int *status = reinterpret_cast<int *>(scratch + FIT_STATIC_STATUS);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nblocks = (int)std::min<int64_t>(
+        std::min<int64_t>((n + FIT_THREADS - 1) / FIT_THREADS, (int64_t)sms), FIT_STATIC_BLOCKS);
+    // every partial slot the solve reads is rewritten below; only the status starts at zero
+    if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return DGSM_ERR_CUDA;
+    sh_fit_partial_kernel<<<nblocks, FIT_THREADS, 0, s>>>(dirs, rgb, w, n, scratch);
+    sh_fit_solve_kernel<<<1, 128, 0, s>>>(scratch, nblocks, lambda, sh_out, sh64_out, status);
+    if (cudaGetLastError() != cudaSuccess) return DGSM_ERR_CUDA;
+    if (status_out &&
+        cudaMemcpyAsync(status_out, status, sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return DGSM_ERR_CUDA;
+    return DGSM_OK;
 }

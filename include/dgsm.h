@@ -253,6 +253,58 @@ int dgsm_frame_host(dgsm_ctx *ctx, const dgsm_frame_host_in *in, const dgsm_para
 int dgsm_set_profiling(dgsm_ctx *ctx, int enable);
 int dgsm_profile_collect(dgsm_ctx *ctx, double *ms_out, int max_builds, int *n_out);
 
+/* ---- Learned transmittance surrogate (per-light neural field) ----------
+ * A small network stands in for one light's atlas lookup: T_hat(u, v, rho) =
+ * sigmoid(w5 . h4 + b5), h_l = ReLU(W_l h_{l-1} + b_l), four hidden layers of
+ * width 64, h_0 = 96 Fourier features sin/cos(pi f_m x), f_m = 2^(8m/15),
+ * m = 0..15, of x in {u, v, rho}: u, v the octahedral coordinates of the
+ * direction (Eq. 6), rho = (k + w)/(K-1) the fractional shell coordinate of
+ * the distance (as the trilinear lookup of Sec. 3.3 brackets it).  Features,
+ * weights and hidden activations are bfloat16, sums float32 (tensor cores
+ * for inference).  Parameters: one float32 vector of nf_param_count() values
+ * per light: W1 [64][96], b1, W2 [64][64], b2, W3, b3, W4, b4, w5 [64], b5. */
+int64_t nf_param_count(void);
+
+/* Mean squared error of the field against `target` at the n inputs `uvr`
+ * (n,3) and its gradient with respect to every parameter (float32,
+ * nf_param_count() values); loss_out: device float or NULL.  n <= 2^24. */
+int nf_loss_grad(dgsm_ctx *ctx, const float *params, const float *uvr, const float *target,
+                 int64_t n, float *loss_out, float *grad_out, void *stream);
+
+/* Adam training of one light's field on its exact atlas [K][H][W] (float32,
+ * as dgsm_build writes it): every step draws `batch` voxels at random
+ * (counter-based, from seed and the step number), fits T at the voxel
+ * centres (u_j, v_i, k/(K-1)) by mean squared error, and updates params in
+ * place (adam_m, adam_v: state of the same length, zero before the first
+ * step).  step0: steps already taken (for bias correction when training is
+ * resumed).  loss_out: `steps` floats (device) or NULL. */
+int nf_train(dgsm_ctx *ctx, const float *atlas, int32_t H, int32_t W, int32_t K, float *params,
+             float *adam_m, float *adam_v, int32_t steps, int32_t batch, float lr, uint64_t seed,
+             int32_t step0, float *loss_out, void *stream);
+
+/* Field values T_hat at n inputs (u, v, rho) (n,3) -> T_out (n). */
+int nf_forward(dgsm_ctx *ctx, const float *params, const float *uvr, int64_t n, float *T_out,
+               void *stream);
+
+/* Largest |T_hat - T| over all voxels of each tile (tile x tile texels x K
+ * shells) of one light's atlas [K][H][W]: tile_err (ceil(H/tile) *
+ * ceil(W/tile) floats, row-major tiles).  Marks where the exact atlas must
+ * stay as the fallback. */
+int nf_tile_error(dgsm_ctx *ctx, const float *params, const float *atlas, int32_t H, int32_t W,
+                  int32_t K, int32_t tile, float *tile_err, void *stream);
+
+/* dgsm_attenuate with the field in place of the atlas lookup: params holds
+ * n_lights parameter vectors back to back.  Where mask (n_lights x tiles,
+ * uint8, nonzero = fall back) marks the tile of a query's texel cell, the
+ * exact trilinear lookup in `atlas` ([n_lights][K][H][W] float32) is used
+ * instead; mask and atlas may be NULL (field everywhere).  Other arguments
+ * as for dgsm_attenuate. */
+int nf_attenuate(dgsm_ctx *ctx, const float *params, const uint8_t *mask, const float *atlas,
+                 int32_t n_lights, int32_t H, int32_t W, const float *radii, int32_t K,
+                 int32_t tile, const float *lights, const float *q_means, const float *colors_in,
+                 int64_t n_q, const float *light_w, float direct_frac, float *colors_out,
+                 float *T_out, void *stream);
+
 /* Reads and clears the context's device status word (blocks on `stream`):
  * returns DGSM_OK or the first error a kernel recorded since the last call. */
 int dgsm_sync_status(dgsm_ctx *ctx, void *stream);

@@ -104,12 +104,22 @@ _lib.dgsm_sync_status.argtypes = [_vp, _vp]
 _lib.dgsm_weighted_centroid.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp]
 _lib.dgsm_frame_host.argtypes = [_vp, C.POINTER(FrameHostIn), C.POINTER(Params),
                                  C.POINTER(RelightParams), _vp, _vp, _vp]
+_lib.nf_param_count.restype = C.c_int64
+_lib.nf_param_count.argtypes = []
+_lib.nf_loss_grad.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]
+_lib.nf_train.argtypes = [_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _i32, _i32, _f32, C.c_uint64,
+                          _i32, _vp, _vp]
+_lib.nf_forward.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp]
+_lib.nf_tile_error.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp, _vp]
+_lib.nf_attenuate.argtypes = [_vp, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _i32, _i32, _vp, _vp, _vp,
+                              _i64, _vp, _f32, _vp, _vp, _vp]
 _lib.dgsm_set_profiling.argtypes = [_vp, C.c_int]
 _lib.dgsm_profile_collect.argtypes = [_vp, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]
 for _fn in ("dgsm_build", "dgsm_get_build_stats", "dgsm_bin", "dgsm_attenuate",
             "dgsm_sample_index", "sh_fit", "sh_relight", "dgsm_sync_status",
             "dgsm_weighted_centroid", "dgsm_frame_host", "dgsm_set_profiling",
-            "dgsm_profile_collect", "sh_fit_static"):
+            "dgsm_profile_collect", "sh_fit_static", "nf_loss_grad", "nf_train", "nf_forward",
+            "nf_tile_error", "nf_attenuate"):
     getattr(_lib, _fn).restype = C.c_int
 
 
@@ -387,3 +397,73 @@ def dgsm_profile_collect(ctx: Context | None = None):
     n = C.c_int(0)
     ctx.check(_lib.dgsm_profile_collect(ctx.handle, buf, 256, C.byref(n)))
     return [(buf[2 * i], buf[2 * i + 1]) for i in range(n.value)]
+
+
+# ---- learned transmittance surrogate ---------------------------------------
+
+def nf_param_count() -> int:
+    return int(_lib.nf_param_count())
+
+
+def nf_loss_grad(params, uvr, target, ctx: Context | None = None, stream=None):
+    """(loss (1,), grad (P,)) of the field's MSE at explicit inputs."""
+    ctx = ctx or context(params.device.index)
+    _need(params, "params")
+    _need(uvr, "uvr", shape_last=3)
+    _need(target, "target")
+    loss = torch.zeros(1, dtype=torch.float32, device=params.device)
+    grad = torch.empty_like(params)
+    ctx.check(_lib.nf_loss_grad(ctx.handle, _ptr(params), _ptr(uvr), _ptr(target), uvr.shape[0],
+                                _ptr(loss), _ptr(grad), _stream(stream)))
+    return loss, grad
+
+
+def nf_train(atlas_l, params, adam_m, adam_v, steps, batch=8192, lr=1e-3, seed=0, step0=0,
+             ctx: Context | None = None, stream=None):
+    """Adam steps on one light's atlas [K][H][W]; returns the per-step losses."""
+    ctx = ctx or context(params.device.index)
+    _need(atlas_l, "atlas_l")
+    K, H, W = atlas_l.shape
+    loss = torch.zeros(max(steps, 1), dtype=torch.float32, device=params.device)
+    ctx.check(_lib.nf_train(ctx.handle, _ptr(atlas_l), H, W, K, _ptr(params), _ptr(adam_m),
+                            _ptr(adam_v), int(steps), int(batch), float(lr), int(seed), int(step0),
+                            _ptr(loss), _stream(stream)))
+    return loss[:steps]
+
+
+def nf_forward(params, uvr, ctx: Context | None = None, stream=None):
+    ctx = ctx or context(params.device.index)
+    _need(params, "params")
+    _need(uvr, "uvr", shape_last=3)
+    out = torch.empty(uvr.shape[0], dtype=torch.float32, device=uvr.device)
+    ctx.check(_lib.nf_forward(ctx.handle, _ptr(params), _ptr(uvr), uvr.shape[0], _ptr(out),
+                              _stream(stream)))
+    return out
+
+
+def nf_tile_error(params, atlas_l, tile=8, ctx: Context | None = None, stream=None):
+    ctx = ctx or context(params.device.index)
+    K, H, W = atlas_l.shape
+    out = torch.empty(((H + tile - 1) // tile) * ((W + tile - 1) // tile), dtype=torch.float32,
+                      device=atlas_l.device)
+    ctx.check(_lib.nf_tile_error(ctx.handle, _ptr(params), _ptr(atlas_l), H, W, K, tile, _ptr(out),
+                                 _stream(stream)))
+    return out
+
+
+def nf_attenuate(params, radii, lights, q_means, colors, H, W, mask=None, atlas=None, tile=8,
+                 light_w=None, direct_frac=1.0, out=None, want_T=False, ctx: Context | None = None,
+                 stream=None):
+    """Attenuation through the per-light fields params (L, P); see dgsm_attenuate."""
+    ctx = ctx or context(params.device.index)
+    _need(params, "params")
+    L = lights.shape[0]
+    Q = q_means.shape[0]
+    if out is None:
+        out = torch.empty_like(colors)
+    T = torch.empty((Q, L), dtype=torch.float32, device=colors.device) if want_T else None
+    ctx.check(_lib.nf_attenuate(ctx.handle, _ptr(params), _ptr(mask), _ptr(atlas), L, H, W,
+                                _ptr(radii), radii.shape[0], tile, _ptr(lights), _ptr(q_means),
+                                _ptr(colors), Q, _ptr(light_w), float(direct_frac), _ptr(out),
+                                _ptr(T), _stream(stream)))
+    return (out, T) if want_T else out

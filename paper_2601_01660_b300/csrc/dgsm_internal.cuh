@@ -26,6 +26,7 @@ enum WsSlot {
     WS_SH_PART,        // SH fit per-block partial sums
     WS_CENTROID,       // weighted-centroid partial sums
     WS_FRAME,          // device copies of a host frame (dgsm_frame_host)
+    WS_NF,             // surrogate training: per-sample rows and partial gradients
     WS_NSLOTS
 };
 

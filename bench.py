@@ -415,10 +415,16 @@ def main():
     ap.add_argument("--cpu-texels", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--report", choices=["precision", "surrogate"],
+                    help="print a side report (one JSON line) instead of the step benchmark")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank, world, local_rank = _env_rank()
+    if args.report:
+        from paper_2601_01660_b300 import reports
+        reports.main(args.report)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

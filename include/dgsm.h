@@ -265,6 +265,10 @@ int dgsm_profile_collect(dgsm_ctx *ctx, double *ms_out, int max_builds, int *n_o
  * per light: W1 [64][96], b1, W2 [64][64], b2, W3, b3, W4, b4, w5 [64], b5. */
 int64_t nf_param_count(void);
 
+/* Initial parameters: He-uniform weights U(-sqrt(6/fan_in), sqrt(6/fan_in))
+ * drawn with SplitMix64 from (seed, index), zero biases. */
+int nf_init(dgsm_ctx *ctx, uint64_t seed, float *params, void *stream);
+
 /* Mean squared error of the field against `target` at the n inputs `uvr`
  * (n,3) and its gradient with respect to every parameter (float32,
  * nf_param_count() values); loss_out: device float or NULL.  n <= 2^24. */
@@ -298,7 +302,10 @@ int nf_tile_error(dgsm_ctx *ctx, const float *params, const float *atlas, int32_
  * uint8, nonzero = fall back) marks the tile of a query's texel cell, the
  * exact trilinear lookup in `atlas` ([n_lights][K][H][W] float32) is used
  * instead; mask and atlas may be NULL (field everywhere).  Other arguments
- * as for dgsm_attenuate. */
+ * as for dgsm_attenuate.  Lights are processed four at a time (their
+ * weights staged on chip once per block); with more than four lights the
+ * partial weighted sums go through a context workspace of n_q floats, so
+ * calls that share a context must share a stream. */
 int nf_attenuate(dgsm_ctx *ctx, const float *params, const uint8_t *mask, const float *atlas,
                  int32_t n_lights, int32_t H, int32_t W, const float *radii, int32_t K,
                  int32_t tile, const float *lights, const float *q_means, const float *colors_in,

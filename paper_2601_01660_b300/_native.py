@@ -106,6 +106,7 @@ _lib.dgsm_frame_host.argtypes = [_vp, C.POINTER(FrameHostIn), C.POINTER(Params),
                                  C.POINTER(RelightParams), _vp, _vp, _vp]
 _lib.nf_param_count.restype = C.c_int64
 _lib.nf_param_count.argtypes = []
+_lib.nf_init.argtypes = [_vp, C.c_uint64, _vp, _vp]
 _lib.nf_loss_grad.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]
 _lib.nf_train.argtypes = [_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _i32, _i32, _f32, C.c_uint64,
                           _i32, _vp, _vp]
@@ -118,7 +119,7 @@ _lib.dgsm_profile_collect.argtypes = [_vp, C.POINTER(C.c_double), C.c_int, C.POI
 for _fn in ("dgsm_build", "dgsm_get_build_stats", "dgsm_bin", "dgsm_attenuate",
             "dgsm_sample_index", "sh_fit", "sh_relight", "dgsm_sync_status",
             "dgsm_weighted_centroid", "dgsm_frame_host", "dgsm_set_profiling",
-            "dgsm_profile_collect", "sh_fit_static", "nf_loss_grad", "nf_train", "nf_forward",
+            "dgsm_profile_collect", "sh_fit_static", "nf_init", "nf_loss_grad", "nf_train", "nf_forward",
             "nf_tile_error", "nf_attenuate"):
     getattr(_lib, _fn).restype = C.c_int
 
@@ -403,6 +404,18 @@ def dgsm_profile_collect(ctx: Context | None = None):
 
 def nf_param_count() -> int:
     return int(_lib.nf_param_count())
+
+
+def nf_init(seed=0, n_lights=None, device=None, ctx: Context | None = None, stream=None):
+    """Fresh parameters: (P,) or (n_lights, P) float32 on the device."""
+    ctx = ctx or context(device)
+    P = nf_param_count()
+    shape = (P,) if n_lights is None else (n_lights, P)
+    out = torch.empty(shape, dtype=torch.float32, device=torch.device("cuda", ctx.device))
+    flat = out.view(-1, P)
+    for l in range(flat.shape[0]):
+        ctx.check(_lib.nf_init(ctx.handle, int(seed) + l, _ptr(flat[l]), _stream(stream)))
+    return out
 
 
 def nf_loss_grad(params, uvr, target, ctx: Context | None = None, stream=None):

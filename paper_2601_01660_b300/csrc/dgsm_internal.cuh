@@ -27,6 +27,7 @@ enum WsSlot {
     WS_CENTROID,       // weighted-centroid partial sums
     WS_FRAME,          // device copies of a host frame (dgsm_frame_host)
     WS_NF,             // surrogate training: per-sample rows and partial gradients
+    WS_NF_ACC,         // surrogate attenuation over more than four lights: partial sums
     WS_NSLOTS
 };
 

@@ -535,29 +535,40 @@ __global__ void __launch_bounds__(IF_THREADS) nf_tile_error_kernel(
 
 // Attenuation through the field: per query and light the field value at
 // (u, v, rho) of the query, or -- where the light's fallback mask marks the
-// tile of the query's texel -- the exact trilinear atlas lookup.
-__global__ void __launch_bounds__(IF_THREADS) nf_attenuate_kernel(
+// tile of the query's texel cell -- the exact trilinear atlas lookup.  The
+// weights of up to NF_LGROUP lights are staged in shared memory once per
+// block; with more lights, launches over light groups carry the weighted sum
+// in `accum` (first group writes it, last group turns it into colours).
+constexpr int NF_LGROUP = 4;
+constexpr int NA_WARPS = 8;   // one block per SM: 8 warps share the staged weights
+constexpr int NA_THREADS = NA_WARPS * 32;
+
+__global__ void __launch_bounds__(NA_THREADS, 1) nf_attenuate_kernel(
     const float *__restrict__ params, int n_params_stride, const uint8_t *__restrict__ mask,
-    const float *__restrict__ atlas, int L, int H, int W, const float *__restrict__ radii, int K,
-    int tile, int tx, int n_tiles, const float *__restrict__ lights, const float *__restrict__ qm,
-    const float *cin, int64_t Q, const float *__restrict__ lw, float wd, float *cout,
-    float *__restrict__ Tout) {
+    const float *__restrict__ atlas, int L, int l0, int LG, int H, int W,
+    const float *__restrict__ radii, int K, int tile, int tx, int n_tiles,
+    const float *__restrict__ lights, const float *__restrict__ qm, const float *cin, int64_t Q,
+    const float *__restrict__ lw, float wd, float *cout, float *__restrict__ Tout,
+    float *__restrict__ accum) {
     extern __shared__ float4 smem_if[];
-    __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(smem_if);
-    float *fb = reinterpret_cast<float *>(wb + IF_WB);
     __shared__ float rs[256];
     __shared__ float ls[64 * 3];
     __shared__ float wl[64];
     for (int k = threadIdx.x; k < K; k += blockDim.x) rs[k] = radii[k];
     for (int k = threadIdx.x; k < 3 * L; k += blockDim.x) ls[k] = lights[k];
     for (int k = threadIdx.x; k < L; k += blockDim.x) wl[k] = lw ? lw[k] : 1.0f / (float)L;
+    char *stage_base = reinterpret_cast<char *>(smem_if);
+    for (int lg = 0; lg < LG; ++lg) {
+        __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(stage_base + lg * IF_SMEM);
+        nf_stage_infer_weights(params + (int64_t)(l0 + lg) * n_params_stride, wb,
+                               reinterpret_cast<float *>(wb + IF_WB));
+    }
+    __syncthreads();
+    const bool first = l0 == 0, last = l0 + LG == L;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2;
     const int64_t plane = (int64_t)H * W;
-    // one block covers this many queries per pass; every light's weights are
-    // staged in turn, so the queries of a pass are kept in registers
-    for (int64_t base = ((int64_t)blockIdx.x * IF_WARPS + warp) * 32;; base += (int64_t)gridDim.x * IF_WARPS * 32) {
-        const int64_t block_base = base - warp * 32;
-        if (block_base >= Q) break;
+    for (int64_t base = ((int64_t)blockIdx.x * NA_WARPS + warp) * 32; base < Q;
+         base += (int64_t)gridDim.x * NA_WARPS * 32) {
         float px[2][2], py[2][2], pz[2][2], acc[2][2];
 #pragma unroll
         for (int tt = 0; tt < 2; ++tt)
@@ -568,12 +579,12 @@ __global__ void __launch_bounds__(IF_THREADS) nf_attenuate_kernel(
                 px[tt][r] = ok ? qm[3 * s] : 0.f;
                 py[tt][r] = ok ? qm[3 * s + 1] : 0.f;
                 pz[tt][r] = ok ? qm[3 * s + 2] : 0.f;
-                acc[tt][r] = 0.f;
+                acc[tt][r] = (ok && !first) ? accum[s] : 0.f;
             }
-        for (int l = 0; l < L; ++l) {
-            __syncthreads();
-            nf_stage_infer_weights(params + (int64_t)l * n_params_stride, wb, fb);
-            __syncthreads();
+        for (int lg = 0; lg < LG; ++lg) {
+            const int l = l0 + lg;
+            const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(stage_base + lg * IF_SMEM);
+            const float *fb = reinterpret_cast<const float *>(wb + IF_WB);
             float in[2][2][3], T[2][2];
             SampleIndex si[2][2];
 #pragma unroll
@@ -582,9 +593,8 @@ __global__ void __launch_bounds__(IF_THREADS) nf_attenuate_kernel(
                 for (int r = 0; r < 2; ++r) {
                     si[tt][r] = sample_index(px[tt][r], py[tt][r], pz[tt][r], ls[3 * l], ls[3 * l + 1],
                                              ls[3 * l + 2], H, W, rs, K);
-                    const float vx = px[tt][r] - ls[3 * l], vy = py[tt][r] - ls[3 * l + 1],
-                                vz = pz[tt][r] - ls[3 * l + 2];
-                    const float2 uv = xencode(vx, vy, vz);
+                    const float2 uv = xencode(px[tt][r] - ls[3 * l], py[tt][r] - ls[3 * l + 1],
+                                              pz[tt][r] - ls[3 * l + 2]);
                     in[tt][r][0] = uv.x;
                     in[tt][r][1] = uv.y;
                     in[tt][r][2] = nf_rho(si[tt][r].t, rs, K);
@@ -594,29 +604,26 @@ __global__ void __launch_bounds__(IF_THREADS) nf_attenuate_kernel(
             for (int tt = 0; tt < 2; ++tt)
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
-                    const SampleIndex &s = si[tt][r];
+                    const SampleIndex &sx = si[tt][r];
                     float Tl = T[tt][r];
-                    if (s.t == 0.0f) Tl = 1.0f;
-                    else if (mask) {
-                        const int key = (s.ci / tile) * tx + (s.cj / tile);
-                        if (mask[(int64_t)l * n_tiles + key]) {
-                            // exact trilinear lookup in the fallback atlas
-                            const int j0 = min(max(s.bj, 0), W - 1), j1 = min(max(s.bj + 1, 0), W - 1);
-                            const int i0 = min(max(s.bi, 0), H - 1), i1 = min(max(s.bi + 1, 0), H - 1);
-                            int k0, k1;
-                            float wt;
-                            if (s.k < 0) { k0 = k1 = 0; wt = 0.f; }
-                            else if (s.k >= K - 1) { k0 = k1 = K - 1; wt = 0.f; }
-                            else { k0 = s.k; k1 = s.k + 1; wt = (s.t - rs[k0]) / (rs[k1] - rs[k0]); }
-                            const float *A0 = atlas + (int64_t)l * K * plane + k0 * plane;
-                            const float *A1 = atlas + (int64_t)l * K * plane + k1 * plane;
-                            const float fx = s.fx, fy = s.fy;
-                            const float b0 = (1 - fy) * ((1 - fx) * A0[i0 * W + j0] + fx * A0[i0 * W + j1]) +
-                                             fy * ((1 - fx) * A0[i1 * W + j0] + fx * A0[i1 * W + j1]);
-                            const float b1 = (1 - fy) * ((1 - fx) * A1[i0 * W + j0] + fx * A1[i0 * W + j1]) +
-                                             fy * ((1 - fx) * A1[i1 * W + j0] + fx * A1[i1 * W + j1]);
-                            Tl = (1 - wt) * b0 + wt * b1;
-                        }
+                    if (sx.t == 0.0f) Tl = 1.0f;
+                    else if (mask && mask[(int64_t)l * n_tiles + (sx.ci / tile) * tx + (sx.cj / tile)]) {
+                        // exact trilinear lookup in the fallback atlas
+                        const int j0 = min(max(sx.bj, 0), W - 1), j1 = min(max(sx.bj + 1, 0), W - 1);
+                        const int i0 = min(max(sx.bi, 0), H - 1), i1 = min(max(sx.bi + 1, 0), H - 1);
+                        int k0, k1;
+                        float wt;
+                        if (sx.k < 0) { k0 = k1 = 0; wt = 0.f; }
+                        else if (sx.k >= K - 1) { k0 = k1 = K - 1; wt = 0.f; }
+                        else { k0 = sx.k; k1 = sx.k + 1; wt = (sx.t - rs[k0]) / (rs[k1] - rs[k0]); }
+                        const float *A0 = atlas + (int64_t)l * K * plane + k0 * plane;
+                        const float *A1 = atlas + (int64_t)l * K * plane + k1 * plane;
+                        const float fx = sx.fx, fy = sx.fy;
+                        const float b0 = (1 - fy) * ((1 - fx) * A0[i0 * W + j0] + fx * A0[i0 * W + j1]) +
+                                         fy * ((1 - fx) * A0[i1 * W + j0] + fx * A0[i1 * W + j1]);
+                        const float b1 = (1 - fy) * ((1 - fx) * A1[i0 * W + j0] + fx * A1[i0 * W + j1]) +
+                                         fy * ((1 - fx) * A1[i1 * W + j0] + fx * A1[i1 * W + j1]);
+                        Tl = (1 - wt) * b0 + wt * b1;
                     }
                     const int64_t q = base + 16 * tt + g + 8 * r;
                     if (Tout && q < Q && (lane & 3) == 0) Tout[q * L + l] = Tl;
@@ -630,6 +637,10 @@ __global__ void __launch_bounds__(IF_THREADS) nf_attenuate_kernel(
                 for (int r = 0; r < 2; ++r) {
                     const int64_t q = base + 16 * tt + g + 8 * r;
                     if (q >= Q) continue;
+                    if (!last) {
+                        accum[q] = acc[tt][r];
+                        continue;
+                    }
                     const float f = 1.0f - wd + wd * acc[tt][r];
                     const float c0 = cin[3 * q], c1 = cin[3 * q + 1], c2 = cin[3 * q + 2];
                     cout[3 * q] = c0 * f;
@@ -639,12 +650,31 @@ __global__ void __launch_bounds__(IF_THREADS) nf_attenuate_kernel(
     }
 }
 
+// He-uniform initial weights U(-sqrt(6/fan_in), +sqrt(6/fan_in)), zero biases.
+__global__ void nf_init_kernel(unsigned long long seed, float *__restrict__ params) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NF_PARAMS) return;
+    int fan_in = 0;
+    if (p < OFF_B1) fan_in = NF_FEAT;
+    else if ((p >= OFF_W2 && p < OFF_B2) || (p >= OFF_W3 && p < OFF_B3) || (p >= OFF_W4 && p < OFF_B4) ||
+             (p >= OFF_W5 && p < OFF_B5))
+        fan_in = NF_HID;
+    if (fan_in == 0) {
+        params[p] = 0.0f;
+        return;
+    }
+    const unsigned long long r = splitmix64(seed * (unsigned long long)NF_PARAMS + (unsigned long long)p);
+    const float u01 = (float)(r >> 40) * (1.0f / 16777216.0f);  // 24 random bits
+    params[p] = (2.0f * u01 - 1.0f) * sqrtf(6.0f / (float)fan_in);
+}
+
 int set_infer_smem(dgsm_ctx *ctx) {
     cudaError_t e = cudaFuncSetAttribute(nf_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)IF_SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(nf_tile_error_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)IF_SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(nf_attenuate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)IF_SMEM);
+        e = cudaFuncSetAttribute(nf_attenuate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(NF_LGROUP * IF_SMEM));
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "nf: smem attribute");
 }
 
@@ -679,6 +709,16 @@ int run_fwdbwd(dgsm_ctx *ctx, const float *params, const float *atlas, int H, in
 using namespace dgsm;
 
 extern "C" int64_t nf_param_count(void) { return NF_PARAMS; }
+
+extern "C" int nf_init(dgsm_ctx *ctx, uint64_t seed, float *params, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (!params) return fail(ctx, DGSM_ERR_INVALID_ARG, "nf_init: null params");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    nf_init_kernel<<<(NF_PARAMS + 255) / 256, 256, 0, (cudaStream_t)stream>>>(seed, params);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "nf_init_kernel");
+}
 
 extern "C" int nf_loss_grad(dgsm_ctx *ctx, const float *params, const float *uvr, const float *target,
                             int64_t n, float *loss_out, float *grad_out, void *stream) {
@@ -780,10 +820,19 @@ extern "C" int nf_attenuate(dgsm_ctx *ctx, const float *params, const uint8_t *m
     int rc = set_infer_smem(ctx);
     if (rc) return rc;
     const int tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
-    const int grid = (int)std::min<int64_t>((n_q + IF_THREADS - 1) / IF_THREADS, (int64_t)ctx->num_sms * 8);
-    nf_attenuate_kernel<<<grid, IF_THREADS, IF_SMEM, (cudaStream_t)stream>>>(
-        params, NF_PARAMS, mask, atlas, L, H, W, radii, K, tile, tx, tx * ty, lights, q_means, colors_in, n_q,
-        light_w, direct_frac, colors_out, T_out);
+    const int grid = (int)std::min<int64_t>((n_q + NA_THREADS - 1) / NA_THREADS, (int64_t)ctx->num_sms);
+    float *accum = nullptr;
+    if (L > NF_LGROUP) {
+        void *p;
+        if ((rc = ws_reserve(ctx, WS_NF_ACC, sizeof(float) * (size_t)n_q, &p))) return rc;
+        accum = (float *)p;
+    }
+    for (int l0 = 0; l0 < L; l0 += NF_LGROUP) {
+        const int LG = std::min(NF_LGROUP, L - l0);
+        nf_attenuate_kernel<<<grid, NA_THREADS, LG * IF_SMEM, (cudaStream_t)stream>>>(
+            params, NF_PARAMS, mask, atlas, L, l0, LG, H, W, radii, K, tile, tx, tx * ty, lights, q_means,
+            colors_in, n_q, light_w, direct_frac, colors_out, T_out, accum);
+    }
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "nf_attenuate_kernel");
 }

@@ -1,0 +1,141 @@
+"""Reports beside the benchmark step (each prints one JSON line via bench.py).
+
+  precision  3M-Gaussian cube scene, 4 lights, 64x64x16 atlases stored as
+             float32 / float16 / bfloat16 (tau always accumulated in float32):
+             per-light max and mean |dT| of the 16-bit stores against float32
+             over every voxel, build times.
+  surrogate  the learned transmittance field trained on 512x512x64 atlases of
+             the 20k-Gaussian cube scene with 4 lights, then used to attenuate
+             3M Gaussians: |dT| p50/p99 against the exact atlas lookup, with
+             and without the per-tile exact fallback, memory footprint,
+             Gaussians/s, and an atlas of the same memory as the weights.
+
+Comparisons against the FP64 oracle live in the test suite.
+"""
+from __future__ import annotations
+
+import json
+import time
+
+import numpy as np
+
+
+def _dev(a, torch):
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+def _time(torch, fn, reps=5):
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def precision() -> dict:
+    """Storage precision on the GPU: float16 / bfloat16 atlases against the
+    float32 atlas over every voxel (the float32 atlas itself is checked
+    against the FP64 oracle by the test suite)."""
+    import torch
+
+    from paper_2601_01660_b300 import native, scenes
+    nat = native()
+    wl = scenes.workload("cube3m4l")
+    sc, lights, radii, H, W = wl["occluders"], wl["lights"], wl["radii"], wl["H"], wl["W"]
+    d = {k: _dev(getattr(sc, k), torch) for k in ("means", "scales", "quats", "opac")}
+    lt, rt = _dev(lights, torch), _dev(radii, torch)
+    atl, times = {}, {}
+    for dt in ("f32", "f16", "bf16"):
+        f = lambda: nat.dgsm_build(d["means"], d["scales"], d["quats"], d["opac"], lt, H, W, rt,
+                                   params=dict(atlas_dtype=dt))
+        atl[dt] = f()
+        times[dt] = _time(torch, f, reps=3)
+    L = lights.shape[0]
+    out = {"report": "precision", "workload": "cube3m4l: 3M Gaussians, 4 lights, 64x64x16",
+           "build_ms": {k: round(v, 3) for k, v in times.items()}, "abs_dT_vs_f32": {}}
+    ref = atl["f32"].double()
+    for dt in ("f16", "bf16"):
+        err = (atl[dt].double() - ref).abs()
+        out["abs_dT_vs_f32"][dt] = {f"light{l}": {"max": float(err[l].max()), "mean": float(err[l].mean())}
+                                    for l in range(L)}
+    return out
+
+
+def surrogate(steps: int = 3000, batch: int = 16384, n_query: int = 3_000_000, tol: float = 0.02) -> dict:
+    import torch
+
+    from paper_2601_01660_b300 import native, scenes
+    nat = native()
+    occ = scenes.cube_scene(20_000, seed=0)
+    lights = scenes.four_lights()
+    H = W = 512
+    K = 64
+    radii = scenes.radii_geometric(0.05, 12.0, K)
+    d = {k: _dev(getattr(occ, k), torch) for k in ("means", "scales", "quats", "opac")}
+    lt, rt = _dev(lights, torch), _dev(radii, torch)
+    atlas = nat.dgsm_build(d["means"], d["scales"], d["quats"], d["opac"], lt, H, W, rt)
+    L = lights.shape[0]
+    P = nat.nf_param_count()
+    params = nat.nf_init(seed=100, n_lights=L)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = []
+    for l in range(L):
+        m, v = torch.zeros(P, device="cuda"), torch.zeros(P, device="cuda")
+        losses.append(nat.nf_train(atlas[l], params[l], m, v, steps=steps, batch=batch, lr=2e-3,
+                                   seed=l + 1).cpu().numpy())
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    tile = 8
+    n_tiles = (H // tile) * (W // tile)
+    errs = torch.stack([nat.nf_tile_error(params[l], atlas[l], tile=tile) for l in range(L)])
+    mask = (errs > tol).to(torch.uint8).contiguous()
+    q = scenes.cube_scene(n_query, seed=7)
+    qm, qc = _dev(q.means, torch), _dev(q.colors, torch)
+    _, T_ex = nat.dgsm_attenuate(atlas, rt, lt, qm, qc, want_T=True)
+    _, T_nf = nat.nf_attenuate(params, rt, lt, qm, qc, H, W, want_T=True)
+    _, T_fb = nat.nf_attenuate(params, rt, lt, qm, qc, H, W, mask=mask, atlas=atlas, want_T=True)
+    # an exact atlas with the weights' memory: bfloat16 weights, float32 voxels
+    weight_bytes = L * (P - 1) * 2 + L * 4
+    side = int(np.sqrt(weight_bytes / (L * 4 * 16)))
+    small_r = _dev(scenes.radii_geometric(0.05, 12.0, 16), torch)
+    small = nat.dgsm_build(d["means"], d["scales"], d["quats"], d["opac"], lt, side, side, small_r)
+    _, T_sm = nat.dgsm_attenuate(small, small_r, lt, qm, qc, want_T=True)
+
+    def stats(T):
+        e = (T - T_ex).abs().flatten().cpu().numpy()
+        return {"p50": float(np.quantile(e, 0.5)), "p99": float(np.quantile(e, 0.99)),
+                "max": float(e.max())}
+
+    t_ex = _time(torch, lambda: nat.dgsm_attenuate(atlas, rt, lt, qm, qc))
+    t_nf = _time(torch, lambda: nat.nf_attenuate(params, rt, lt, qm, qc, H, W))
+    t_fb = _time(torch, lambda: nat.nf_attenuate(params, rt, lt, qm, qc, H, W, mask=mask, atlas=atlas))
+    fb_frac = float(mask.float().mean().item())
+    atlas_bytes = atlas.numel() * 4
+    return {
+        "report": "surrogate",
+        "workload": f"cube20k occluders, 4 lights, exact atlases 4x{H}x{W}x{K}; {n_query} queries",
+        "training": {"steps_per_light": steps, "batch": batch, "seconds_total": round(t_train, 2),
+                     "loss_first": [float(x[:10].mean()) for x in losses],
+                     "loss_last": [float(x[-50:].mean()) for x in losses]},
+        "abs_dT_vs_exact": {"field": stats(T_nf), f"field+fallback(tol {tol})": stats(T_fb),
+                            f"exact atlas {side}x{side}x16 (same bytes as the weights)": stats(T_sm)},
+        "fallback_tile_fraction": fb_frac,
+        "memory_bytes": {"exact_atlases": atlas_bytes, "field_weights_bf16": weight_bytes,
+                         "field+fallback_tiles": weight_bytes + int(fb_frac * atlas_bytes),
+                         "equal_memory_atlas": int(small.numel() * 4)},
+        "gaussians_per_s": {"exact": n_query / (t_ex * 1e-3), "field": n_query / (t_nf * 1e-3),
+                            "field+fallback": n_query / (t_fb * 1e-3)},
+        "ms": {"exact": t_ex, "field": t_nf, "field+fallback": t_fb},
+    }
+
+
+def main(which: str) -> None:
+    fn = {"precision": precision, "surrogate": surrogate}[which]
+    print(json.dumps(fn()), flush=True)

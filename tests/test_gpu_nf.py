@@ -105,3 +105,40 @@ def test_surrogate_attenuation_with_fallback(nat, orc):
     out_nf, T_nf = nat.nf_attenuate(p[None].contiguous(), radii, lights, qm, qc, 64, 64, want_T=True)
     # the field itself: same inputs through nf_forward
     assert bool(((T_nf >= 0) & (T_nf <= 1)).all())
+
+
+def test_surrogate_attenuation_light_groups(nat):
+    """Six lights run as two launches (four staged lights, then two) carrying
+    the weighted sum between them: every light's T equals its one-light pass,
+    masked tiles equal the exact lookup, and the colours follow from the T."""
+    rng = np.random.default_rng(11)
+    sc = scenes.cube_scene(600, seed=5, log_s_mean=np.log(0.12))
+    d = scene_to_dev(sc)
+    L, H, W, K = 6, 48, 40, 12
+    lights = dev(np.float32(rng.uniform(-0.5, 0.5, (L, 3))))
+    radii = dev(scenes.radii_linear(0.1, 8, K))
+    atlas = nat.dgsm_build(d["means"], d["scales"], d["quats"], d["opac"], lights, H, W, radii)
+    params = nat.nf_init(seed=4, n_lights=L)
+    n_tiles = (H // 8) * (W // 8)
+    mask = dev(rng.random((L, n_tiles)) < 0.4, torch.uint8)
+    q = scenes.cube_scene(7000, seed=6)
+    qm, qc = dev(q.means), dev(q.colors)
+    lw = dev(np.float32(rng.uniform(0.1, 1.0, L)))
+    out, T = nat.nf_attenuate(params, radii, lights, qm, qc, H, W, mask=mask, atlas=atlas,
+                              light_w=lw, direct_frac=0.8, want_T=True)
+    _, T_ex = nat.dgsm_attenuate(atlas, radii, lights, qm, qc, want_T=True)
+    for l in range(L):
+        _, T1 = nat.nf_attenuate(params[l:l + 1].contiguous(), radii, lights[l:l + 1].contiguous(), qm, qc,
+                                 H, W, mask=mask[l:l + 1].contiguous(), atlas=atlas[l:l + 1].contiguous(),
+                                 want_T=True)
+        assert torch.equal(T[:, l], T1[:, 0])
+    assert torch.isfinite(T).all() and bool(((T >= 0) & (T <= 1)).all())
+    # masked tiles: the exact lookup
+    for l in range(L):
+        idx, _ = nat.dgsm_sample_index(qm, lights[l], H, W, radii)
+        tile_id = (idx[:, 0].long() // 8) * (W // 8) + idx[:, 1].long() // 8
+        sel = mask[l][tile_id].bool()
+        assert int(sel.sum()) > 100
+        assert torch.allclose(T[sel, l], T_ex[sel, l], atol=1e-6)
+    f = 1.0 - 0.8 + 0.8 * (T * lw[None, :]).sum(1)
+    assert torch.allclose(out, qc * f[:, None], rtol=1e-5, atol=1e-6)

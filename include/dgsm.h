@@ -35,6 +35,7 @@ extern "C" {
 #endif
 
 typedef struct dgsm_ctx dgsm_ctx;
+typedef struct dgsm_graph dgsm_graph;
 
 enum dgsm_status {
     DGSM_OK = 0,
@@ -58,14 +59,19 @@ enum dgsm_dtype { DGSM_F32 = 0, DGSM_F16 = 1, DGSM_BF16 = 2 };
  * chunk: Gaussians staged in shared memory per round, 16..128 (default 128);
  * a tile's list is processed in work items of at most 16 chunks.
  * atlas_dtype: storage type of T (dgsm_dtype; tau is always accumulated in
- * float32). */
+ * float32).
+ * max_pairs: 0 (default) sizes the pair buffers from the exact pair count,
+ * read back once midway through the build; > 0 sizes them for max_pairs
+ * pairs and never blocks (so the build can be captured in a CUDA graph; see
+ * dgsm_graph_begin).  A build whose pairs exceed max_pairs records
+ * DGSM_ERR_WORKSPACE in the status word and leaves T = 1 in its atlas. */
 typedef struct {
     float kappa;
     float eps_cull;
     int32_t tile;
     int32_t chunk;
     int32_t atlas_dtype;
-    int32_t reserved;
+    int32_t max_pairs;
 } dgsm_params;
 
 /* Counters of the last dgsm_build on a context. */
@@ -114,13 +120,16 @@ const char *dgsm_status_string(int status);
  *   T = 1 everywhere); lights: (n_lights,3), 1 <= n_lights <= 64;
  *   1 <= H, W <= 4096; radii: (K), 1 <= K <= 256; params: host pointer or
  *   NULL for defaults; atlas: [n_lights][K][H][W] of params->atlas_dtype.
- * Blocks once, midway, to size the workspace from the number of binned
- * pairs (so it is not capturable in a CUDA graph).  Within a voxel the
+ * With params->max_pairs = 0 it blocks once, midway, to size the workspace
+ * from the number of binned pairs; with max_pairs > 0 it never blocks and
+ * reports input errors through the status word (dgsm_sync_status): a
+ * non-finite Gaussian is then left out of the atlas.  Within a voxel the
  * contributions of different Gaussians are summed in an order that can vary
  * from run to run (float32 atomics), so repeated builds agree to rounding,
  * not bit for bit.  Fails with
  * DGSM_ERR_NONFINITE_INPUT if an input Gaussian has a NaN/Inf field or a
- * scale <= 0, DGSM_ERR_WORKSPACE if more than 2^31 pairs are binned. */
+ * scale <= 0, DGSM_ERR_WORKSPACE if more than 2^31 pairs are binned, and
+ * DGSM_ERR_INVALID_ARG for max_pairs = 0 on a stream that is capturing. */
 int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
                const float *opac, int64_t n, const float *lights, int32_t n_lights, int32_t H,
                int32_t W, const float *radii, int32_t K, const dgsm_params *params, void *atlas,
@@ -157,6 +166,20 @@ int dgsm_attenuate(dgsm_ctx *ctx, const void *atlas, const void *atlas_dyn, int3
                    const float *lights, const float *q_means, const float *colors_in,
                    int64_t n_q, const float *light_w, float direct_frac, float *colors_out,
                    float *T_out, void *stream);
+
+/* dgsm_attenuate with a dynamic atlas of its own resolution and shells
+ * (for instance per-frame avatar occluders at 256x256x32 beside a static
+ * scene at 512x512x64): T_l = T_static,l(x) * T_dyn,l(x), each atlas
+ * sampled at its own octahedral index and shell bracket.  atlas:
+ * [n_lights][K][H][W], atlas_dyn: [n_lights][K_dyn][H_dyn][W_dyn], both of
+ * `dtype`; radii_dyn: device, K_dyn floats.  Other arguments and errors as
+ * for dgsm_attenuate. */
+int dgsm_attenuate_dyn(dgsm_ctx *ctx, const void *atlas, int32_t dtype, int32_t n_lights,
+                       int32_t H, int32_t W, const float *radii, int32_t K, const void *atlas_dyn,
+                       int32_t H_dyn, int32_t W_dyn, const float *radii_dyn, int32_t K_dyn,
+                       const float *lights, const float *q_means, const float *colors_in,
+                       int64_t n_q, const float *light_w, float direct_frac, float *colors_out,
+                       float *T_out, void *stream);
 
 /* The integer decisions of dgsm_attenuate for n points seen from one light
  * (device pointer to 3 floats): idx_out (n,5) = texel cell row i, cell
@@ -211,6 +234,73 @@ int sh_relight(dgsm_ctx *ctx, const float *sh, const float *means, const float *
                const float *scales, const float *normals, const float *centroid,
                const float *colors_in, int64_t n, const dgsm_relight_params *params,
                float *colors_out, void *stream);
+
+/* sh_relight for a Gaussian array made of n_obj contiguous objects (for
+ * instance avatars): object o holds Gaussians [seg[o], seg[o+1]) and its
+ * normals are turned away from centroids[o] (device, n_obj x 3 floats; see
+ * dgsm_segment_centroids).  seg: HOST array of n_obj + 1 offsets with
+ * seg[0] = 0, nondecreasing, seg[n_obj] = n; 1 <= n_obj <= 64 (read at the
+ * call, so a captured graph keeps them). */
+int sh_relight_objects(dgsm_ctx *ctx, const float *sh, const float *means, const float *quats,
+                       const float *scales, const float *centroids, const int64_t *seg,
+                       int32_t n_obj, const float *colors_in, int64_t n,
+                       const dgsm_relight_params *params, float *colors_out, void *stream);
+
+/* Alpha-weighted centroid of each object (the reference point of the relight
+ * normals' orientation, Sec. 3.5): out[o] = sum_g w_g mean_g / sum_g w_g over
+ * the object's Gaussians, summed in FP64 (0 for an empty or weightless
+ * object).  means (n,3), weights (n) or NULL (weight 1): device; seg: host,
+ * as for sh_relight_objects; out: device, n_obj x 3 floats. */
+int dgsm_segment_centroids(dgsm_ctx *ctx, const float *means, const float *weights, int64_t n,
+                           const int64_t *seg, int32_t n_obj, float *out, void *stream);
+
+/* Rigid motion of whole objects: object o (Gaussians [seg[o], seg[o+1]))
+ * moves by pose o = (qw, qx, qy, qz, tx, ty, tz, unused), the rotation
+ * quaternion normalised here:  means_out = R(q_o) means + t,
+ * quats_out = q_o * quats (Hamilton product, so R(quats_out) =
+ * R(q_o) R(quats)); scales and opacities are unchanged.  means/quats (n,3)
+ * and (n,4) device (quats 16-byte aligned); outputs may alias the inputs.
+ * seg: host, as for sh_relight_objects.  poses: n_obj x 8 floats in device
+ * memory or host memory (pinned when the call is captured in a graph); it
+ * is copied on `stream`, so a replayed graph reads the poses present at
+ * replay time. */
+int dgsm_rigid_transform(dgsm_ctx *ctx, const float *means, const float *quats, int64_t n,
+                         const int64_t *seg, int32_t n_obj, const float *poses, float *means_out,
+                         float *quats_out, void *stream);
+
+/* CUDA-graph capture of library calls on `stream` (a created stream, not
+ * the legacy default stream).  Between dgsm_graph_begin and dgsm_graph_end
+ * only asynchronous calls may be made: dgsm_build with params->max_pairs > 0,
+ * dgsm_attenuate, dgsm_rigid_transform, dgsm_segment_centroids,
+ * sh_relight(_objects), sh_fit, dgsm_weighted_centroid, nf_attenuate.  The
+ * context's workspace must already be large enough: make the same calls once
+ * before capturing (a call that would grow it fails with
+ * DGSM_ERR_WORKSPACE).  The graph keeps every pointer and size given at
+ * capture: replay after changing buffer CONTENTS (and pinned host poses),
+ * never the buffers themselves.  From dgsm_graph_begin until the graph is
+ * destroyed the context's workspace does not grow; destroy the graph
+ * before the context.  After a failed call inside the capture, still call
+ * dgsm_graph_end (it then fails and returns no graph). */
+int dgsm_graph_begin(dgsm_ctx *ctx, void *stream);
+int dgsm_graph_end(dgsm_ctx *ctx, void *stream, dgsm_graph **out);
+/* Replays the captured calls on `stream`; device-side errors land in the
+ * context's status word (dgsm_sync_status). */
+int dgsm_graph_launch(dgsm_graph *g, void *stream);
+int dgsm_graph_node_count(dgsm_graph *g, int64_t *n_out);
+void dgsm_graph_destroy(dgsm_graph *g);
+
+/* Measured choice of the build's tile and chunk: runs dgsm_build once per
+ * candidate (tiles[a], chunks[b]) to warm up, then `reps` timed runs (CUDA
+ * events on `stream`); writes the median milliseconds to ms_out[a*n_chunks
+ * + b] (host, may be NULL; -1 for a candidate the build rejects) and the
+ * fastest parameters (base with that tile and chunk) to *best_out.  Writes
+ * `atlas` as dgsm_build does.  Blocks. */
+int dgsm_autotune_build(dgsm_ctx *ctx, const float *means, const float *scales,
+                        const float *quats, const float *opac, int64_t n, const float *lights,
+                        int32_t n_lights, int32_t H, int32_t W, const float *radii, int32_t K,
+                        const dgsm_params *base, const int32_t *tiles, int32_t n_tiles,
+                        const int32_t *chunks, int32_t n_chunks, int32_t reps, void *atlas,
+                        dgsm_params *best_out, float *ms_out, void *stream);
 
 /* Alpha-weighted centroid sum_i w_i mu_i / sum_i w_i of n Gaussians (the
  * receiver centroid the relight normals are turned away from, Sec. 3.2's

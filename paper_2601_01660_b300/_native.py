@@ -38,13 +38,13 @@ class DGSMError(RuntimeError):
 class Params(C.Structure):
     """Mirror of dgsm_params."""
     _fields_ = [("kappa", C.c_float), ("eps_cull", C.c_float), ("tile", C.c_int32),
-                ("chunk", C.c_int32), ("atlas_dtype", C.c_int32), ("reserved", C.c_int32)]
+                ("chunk", C.c_int32), ("atlas_dtype", C.c_int32), ("max_pairs", C.c_int32)]
 
     @classmethod
-    def make(cls, kappa=1.0, eps_cull=1e-7, tile=8, chunk=128, atlas_dtype="f32"):
+    def make(cls, kappa=1.0, eps_cull=1e-7, tile=8, chunk=128, atlas_dtype="f32", max_pairs=0):
         p = cls()
         _lib.dgsm_default_params(C.byref(p))
-        p.kappa, p.eps_cull, p.tile, p.chunk = kappa, eps_cull, tile, chunk
+        p.kappa, p.eps_cull, p.tile, p.chunk, p.max_pairs = kappa, eps_cull, tile, chunk, max_pairs
         p.atlas_dtype = DTYPES[atlas_dtype] if isinstance(atlas_dtype, str) else int(atlas_dtype)
         return p
 
@@ -95,6 +95,8 @@ _lib.dgsm_bin.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, 
                           C.POINTER(Params), _vp, _vp, _i64, C.POINTER(_i64), _vp]
 _lib.dgsm_attenuate.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp,
                                 _i64, _vp, _f32, _vp, _vp, _vp]
+_lib.dgsm_attenuate_dyn.argtypes = [_vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _i32, _i32, _vp,
+                                    _i32, _vp, _vp, _vp, _i64, _vp, _f32, _vp, _vp, _vp]
 _lib.dgsm_sample_index.argtypes = [_vp, _vp, _i64, _vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp]
 _lib.sh_fit.argtypes = [_vp, _vp, _vp, _vp, _i64, _f64, _vp, _vp, _vp]
 _lib.sh_fit_static.argtypes = [_vp, _vp, _vp, _i64, _f64, _vp, _vp, _vp, _vp]
@@ -114,13 +116,28 @@ _lib.nf_forward.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp]
 _lib.nf_tile_error.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp, _vp]
 _lib.nf_attenuate.argtypes = [_vp, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _i32, _i32, _vp, _vp, _vp,
                               _i64, _vp, _f32, _vp, _vp, _vp]
+_lib.sh_relight_objects.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _i64,
+                                    C.POINTER(RelightParams), _vp, _vp]
+_lib.dgsm_segment_centroids.argtypes = [_vp, _vp, _vp, _i64, _vp, _i32, _vp, _vp]
+_lib.dgsm_rigid_transform.argtypes = [_vp, _vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp, _vp]
+_lib.dgsm_graph_begin.argtypes = [_vp, _vp]
+_lib.dgsm_graph_end.argtypes = [_vp, _vp, C.POINTER(_vp)]
+_lib.dgsm_graph_launch.argtypes = [_vp, _vp]
+_lib.dgsm_graph_node_count.argtypes = [_vp, C.POINTER(_i64)]
+_lib.dgsm_graph_destroy.argtypes = [_vp]
+_lib.dgsm_graph_destroy.restype = None
+_lib.dgsm_autotune_build.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i32,
+                                     C.POINTER(Params), _vp, _i32, _vp, _i32, _i32, _vp,
+                                     C.POINTER(Params), _vp, _vp]
 _lib.dgsm_set_profiling.argtypes = [_vp, C.c_int]
 _lib.dgsm_profile_collect.argtypes = [_vp, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]
 for _fn in ("dgsm_build", "dgsm_get_build_stats", "dgsm_bin", "dgsm_attenuate",
             "dgsm_sample_index", "sh_fit", "sh_relight", "dgsm_sync_status",
             "dgsm_weighted_centroid", "dgsm_frame_host", "dgsm_set_profiling",
             "dgsm_profile_collect", "sh_fit_static", "nf_init", "nf_loss_grad", "nf_train", "nf_forward",
-            "nf_tile_error", "nf_attenuate"):
+            "nf_tile_error", "nf_attenuate", "sh_relight_objects", "dgsm_segment_centroids",
+            "dgsm_rigid_transform", "dgsm_graph_begin", "dgsm_graph_end", "dgsm_graph_launch",
+            "dgsm_graph_node_count", "dgsm_autotune_build", "dgsm_attenuate_dyn"):
     getattr(_lib, _fn).restype = C.c_int
 
 
@@ -271,6 +288,36 @@ def dgsm_attenuate(atlas, radii, lights, q_means, colors, atlas_dyn=None, light_
     return (out, T) if want_T else out
 
 
+def dgsm_attenuate_dyn(atlas, radii, atlas_dyn, radii_dyn, lights, q_means, colors, light_w=None,
+                       direct_frac=1.0, out=None, want_T=False, ctx: Context | None = None,
+                       stream=None):
+    """Attenuation by a static atlas times a dynamic atlas of its own shape."""
+    ctx = ctx or context(atlas.device.index)
+    dt = {torch.float32: 0, torch.float16: 1, torch.bfloat16: 2}[atlas.dtype]
+    _need(atlas, "atlas", atlas.dtype)
+    _need(atlas_dyn, "atlas_dyn", atlas.dtype)
+    L, K, H, W = atlas.shape
+    Ld, Kd, Hd, Wd = atlas_dyn.shape
+    if Ld != L:
+        raise ValueError("atlas_dyn must have one atlas per light")
+    for t, nm in ((radii, "radii"), (radii_dyn, "radii_dyn")):
+        _need(t, nm)
+    _need(lights, "lights", shape_last=3)
+    _need(q_means, "q_means", shape_last=3)
+    _need(colors, "colors", shape_last=3)
+    if light_w is not None:
+        _need(light_w, "light_w")
+    Q = q_means.shape[0]
+    if out is None:
+        out = torch.empty_like(colors)
+    T = torch.empty((Q, L), dtype=torch.float32, device=atlas.device) if want_T else None
+    ctx.check(_lib.dgsm_attenuate_dyn(ctx.handle, _ptr(atlas), dt, L, H, W, _ptr(radii), K,
+                                      _ptr(atlas_dyn), Hd, Wd, _ptr(radii_dyn), Kd, _ptr(lights),
+                                      _ptr(q_means), _ptr(colors), Q, _ptr(light_w),
+                                      float(direct_frac), _ptr(out), _ptr(T), _stream(stream)))
+    return (out, T) if want_T else out
+
+
 def dgsm_sample_index(points, light, H, W, radii, ctx: Context | None = None, stream=None):
     ctx = ctx or context(points.device.index)
     _need(points, "points", shape_last=3)
@@ -333,6 +380,135 @@ def sh_relight(sh, means, quats, scales, colors, centroid, normals=None, params=
                               _ptr(normals), _ptr(centroid), _ptr(colors), n, C.byref(p), _ptr(out),
                               _stream(stream)))
     return out
+
+
+def _segs(seg, n):
+    seg = [int(x) for x in seg]
+    if len(seg) < 2 or seg[0] != 0 or seg[-1] != n:
+        raise ValueError("seg must run from 0 to n")
+    return (C.c_int64 * len(seg))(*seg), len(seg) - 1
+
+
+def sh_relight_objects(sh, means, quats, scales, colors, centroids, seg, params=None, out=None,
+                       ctx: Context | None = None, stream=None):
+    """sh_relight over contiguous objects (object o = Gaussians seg[o]:seg[o+1]),
+    each with its own centroid row (n_obj, 3)."""
+    ctx = ctx or context(colors.device.index)
+    for t, nm, k in ((sh, "sh", None), (means, "means", 3), (quats, "quats", 4), (scales, "scales", 3),
+                     (colors, "colors", 3), (centroids, "centroids", 3)):
+        _need(t, nm, shape_last=k)
+    n = colors.shape[0]
+    segs, n_obj = _segs(seg, n)
+    p = params if isinstance(params, RelightParams) else RelightParams.make(**(params or {}))
+    if out is None:
+        out = torch.empty_like(colors)
+    ctx.check(_lib.sh_relight_objects(ctx.handle, _ptr(sh), _ptr(means), _ptr(quats), _ptr(scales),
+                                      _ptr(centroids), segs, n_obj, _ptr(colors), n, C.byref(p),
+                                      _ptr(out), _stream(stream)))
+    return out
+
+
+def dgsm_segment_centroids(means, weights, seg, out=None, ctx: Context | None = None, stream=None):
+    """Alpha-weighted centroid of each contiguous object: (n_obj, 3) float32."""
+    ctx = ctx or context(means.device.index)
+    _need(means, "means", shape_last=3)
+    if weights is not None:
+        _need(weights, "weights")
+    n = means.shape[0]
+    segs, n_obj = _segs(seg, n)
+    if out is None:
+        out = torch.empty((n_obj, 3), dtype=torch.float32, device=means.device)
+    ctx.check(_lib.dgsm_segment_centroids(ctx.handle, _ptr(means), _ptr(weights), n, segs, n_obj,
+                                          _ptr(out), _stream(stream)))
+    return out
+
+
+def dgsm_rigid_transform(means, quats, seg, poses, means_out=None, quats_out=None,
+                         ctx: Context | None = None, stream=None):
+    """Rigid motion of contiguous objects; poses (n_obj, 8) float32 =
+    (qw, qx, qy, qz, tx, ty, tz, unused), on the device or in (pinned) host memory."""
+    ctx = ctx or context(means.device.index)
+    _need(means, "means", shape_last=3)
+    _need(quats, "quats", shape_last=4)
+    if poses.dtype != torch.float32 or not poses.is_contiguous() or tuple(poses.shape[1:]) != (8,):
+        raise ValueError("poses must be a contiguous (n_obj, 8) float32 tensor")
+    n = means.shape[0]
+    segs, n_obj = _segs(seg, n)
+    if poses.shape[0] != n_obj:
+        raise ValueError("one pose per object")
+    means_out = torch.empty_like(means) if means_out is None else means_out
+    quats_out = torch.empty_like(quats) if quats_out is None else quats_out
+    ctx.check(_lib.dgsm_rigid_transform(ctx.handle, _ptr(means), _ptr(quats), n, segs, n_obj,
+                                        _ptr(poses), _ptr(means_out), _ptr(quats_out),
+                                        _stream(stream)))
+    return means_out, quats_out
+
+
+class Graph:
+    """A captured sequence of library calls (dgsm_graph); replay() relaunches it."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx, self._h = ctx, handle
+
+    def replay(self, stream):
+        self.ctx.check(_lib.dgsm_graph_launch(self._h, _stream(stream)))
+
+    def node_count(self) -> int:
+        n = _i64(0)
+        self.ctx.check(_lib.dgsm_graph_node_count(self._h, C.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dgsm_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class capture:
+    """with capture(stream, ctx) as cap: <library calls on stream>; then cap.graph.
+    `stream` must be a torch.cuda.Stream other than the default stream."""
+
+    def __init__(self, stream, ctx: Context | None = None):
+        self.stream, self.ctx, self.graph = stream, ctx or context(), None
+
+    def __enter__(self):
+        self.ctx.check(_lib.dgsm_graph_begin(self.ctx.handle, _stream(self.stream)))
+        return self
+
+    def __exit__(self, et, ev, tb):
+        h = _vp()
+        rc = _lib.dgsm_graph_end(self.ctx.handle, _stream(self.stream), C.byref(h))
+        if et is None:
+            self.ctx.check(rc)
+            self.graph = Graph(self.ctx, h)
+        return False
+
+
+def dgsm_autotune_build(means, scales, quats, opac, lights, H, W, radii, tiles=(8, 16),
+                        chunks=(32, 64, 128), reps=3, params=None, ctx: Context | None = None,
+                        stream=None):
+    """Measured tile x chunk choice for dgsm_build: (best Params, {(tile, chunk): ms})."""
+    ctx = ctx or context(means.device.index)
+    p = params if isinstance(params, Params) else Params.make(**(params or {}))
+    L, K, n = lights.shape[0], radii.shape[0], means.shape[0]
+    atlas = torch.empty((L, K, H, W), dtype=TORCH_DTYPES[p.atlas_dtype], device=means.device)
+    ta = (C.c_int32 * len(tiles))(*tiles)
+    ca = (C.c_int32 * len(chunks))(*chunks)
+    ms = (C.c_float * (len(tiles) * len(chunks)))()
+    best = Params()
+    ctx.check(_lib.dgsm_autotune_build(ctx.handle, _ptr(means), _ptr(scales), _ptr(quats), _ptr(opac),
+                                       n, _ptr(lights), L, H, W, _ptr(radii), K, C.byref(p), ta,
+                                       len(tiles), ca, len(chunks), int(reps), _ptr(atlas),
+                                       C.byref(best), ms, _stream(stream)))
+    table = {(t, c): float(ms[a * len(chunks) + b]) for a, t in enumerate(tiles)
+             for b, c in enumerate(chunks)}
+    return best, table
 
 
 def dgsm_sync_status(ctx: Context | None = None, stream=None) -> int:

@@ -59,20 +59,32 @@ constexpr int ATT_U = 4;  // queries in flight per thread
 // of a warp touches one contiguous span.  The ATT_U independent queries per
 // thread keep several gathers and stream loads in flight (the pass is bound
 // by memory latency unless enough requests are outstanding).
-template <typename T>
+// SEP: the dynamic atlas has its own resolution and shells (Hd, Wd, Kd,
+// radii_d) and is sampled at its own index; otherwise it shares the static
+// atlas's geometry and index.
+struct DynGeom {
+    int H, W, K;
+    const float *radii;
+};
+
+template <typename T, bool SEP>
 __global__ void __launch_bounds__(ATT_THREADS) attenuate_kernel(
     const T *__restrict__ atlas, const T *__restrict__ dyn, int L, int H, int W,
-    const float *__restrict__ radii, int K, const float *__restrict__ lights,
+    const float *__restrict__ radii, int K, DynGeom dg, const float *__restrict__ lights,
     const float *__restrict__ qm, const float *cin, int64_t Q, const float *__restrict__ lw,
     float wd, float *cout, float *__restrict__ Tout) {
     __shared__ float rs[256];
+    __shared__ float rsd[SEP ? 256 : 1];
     __shared__ float ls[64 * 3];
     __shared__ float wl[64];
     for (int k = threadIdx.x; k < K; k += blockDim.x) rs[k] = radii[k];
+    if (SEP)
+        for (int k = threadIdx.x; k < dg.K; k += blockDim.x) rsd[k] = dg.radii[k];
     for (int k = threadIdx.x; k < 3 * L; k += blockDim.x) ls[k] = lights[k];
     for (int k = threadIdx.x; k < L; k += blockDim.x) wl[k] = lw ? lw[k] : 1.0f / (float)L;
     __syncthreads();
     const int64_t lstride = (int64_t)K * H * W;
+    const int64_t dstride = SEP ? (int64_t)dg.K * dg.H * dg.W : lstride;
     const int64_t span = (int64_t)ATT_U * ATT_THREADS;
     for (int64_t base = (int64_t)blockIdx.x * span; base < Q; base += (int64_t)gridDim.x * span) {
         float px[ATT_U], py[ATT_U], pz[ATT_U], c0[ATT_U], c1[ATT_U], c2[ATT_U], acc[ATT_U];
@@ -92,12 +104,20 @@ __global__ void __launch_bounds__(ATT_THREADS) attenuate_kernel(
             float Tl[ATT_U];
 #pragma unroll
             for (int u = 0; u < ATT_U; ++u) {
-                const SampleIndex s = sample_index(px[u], py[u], pz[u], ls[3 * l], ls[3 * l + 1],
-                                                   ls[3 * l + 2], H, W, rs, K);
+                const float ox = ls[3 * l], oy = ls[3 * l + 1], oz = ls[3 * l + 2];
+                const SampleIndex s = sample_index(px[u], py[u], pz[u], ox, oy, oz, H, W, rs, K);
                 Tl[u] = 1.0f;
                 if (s.t != 0.0f) {
                     Tl[u] = lookup(atlas + l * lstride, H, W, K, s, rs);
-                    if (dyn) Tl[u] *= lookup(dyn + l * lstride, H, W, K, s, rs);
+                    if (dyn) {
+                        if (SEP) {
+                            const SampleIndex sd = sample_index(px[u], py[u], pz[u], ox, oy, oz, dg.H,
+                                                                dg.W, rsd, dg.K);
+                            Tl[u] *= lookup(dyn + l * dstride, dg.H, dg.W, dg.K, sd, rsd);
+                        } else {
+                            Tl[u] *= lookup(dyn + l * dstride, H, W, K, s, rs);
+                        }
+                    }
                 }
             }
 #pragma unroll
@@ -147,16 +167,31 @@ __global__ void sample_index_kernel(const float *__restrict__ pts, int64_t n,
 
 using namespace dgsm;
 
-extern "C" int dgsm_attenuate(dgsm_ctx *ctx, const void *atlas, const void *atlas_dyn,
-                              int32_t dtype, int32_t L, int32_t H, int32_t W, const float *radii,
-                              int32_t K, const float *lights, const float *q_means,
-                              const float *colors_in, int64_t n_q, const float *light_w,
-                              float direct_frac, float *colors_out, float *T_out, void *stream) {
-    if (!ctx) return DGSM_ERR_INVALID_ARG;
+namespace {
+template <typename T>
+void launch_attenuate(int grid, cudaStream_t s, const void *atlas, const void *dyn, bool sep, int L,
+                      int H, int W, const float *radii, int K, DynGeom dg, const float *lights,
+                      const float *qm, const float *cin, int64_t Q, const float *lw, float wd,
+                      float *cout, float *Tout) {
+    if (sep)
+        attenuate_kernel<T, true><<<grid, ATT_THREADS, 0, s>>>((const T *)atlas, (const T *)dyn, L, H, W,
+            radii, K, dg, lights, qm, cin, Q, lw, wd, cout, Tout);
+    else
+        attenuate_kernel<T, false><<<grid, ATT_THREADS, 0, s>>>((const T *)atlas, (const T *)dyn, L, H, W,
+            radii, K, dg, lights, qm, cin, Q, lw, wd, cout, Tout);
+}
+
+int attenuate_common(dgsm_ctx *ctx, const void *atlas, const void *atlas_dyn, int32_t dtype,
+                     int32_t L, int32_t H, int32_t W, const float *radii, int32_t K, bool sep,
+                     DynGeom dg, const float *lights, const float *q_means,
+                     const float *colors_in, int64_t n_q, const float *light_w,
+                     float direct_frac, float *colors_out, float *T_out, void *stream) {
     if (n_q < 0) return fail(ctx, DGSM_ERR_INVALID_ARG, "n_q < 0");
     if (L < 1 || L > 64) return fail(ctx, DGSM_ERR_INVALID_ARG, "need 1..64 lights");
     if (H < 1 || W < 1 || H > 4096 || W > 4096) return fail(ctx, DGSM_ERR_INVALID_ARG, "H, W must be in 1..4096");
     if (K < 1 || K > 256) return fail(ctx, DGSM_ERR_INVALID_ARG, "K must be in 1..256");
+    if (sep && (dg.H < 1 || dg.W < 1 || dg.H > 4096 || dg.W > 4096 || dg.K < 1 || dg.K > 256 || !dg.radii))
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "dynamic atlas: H, W in 1..4096, K in 1..256, radii required");
     if (dtype < DGSM_F32 || dtype > DGSM_BF16) return fail(ctx, DGSM_ERR_INVALID_ARG, "bad dtype");
     if (!atlas || !radii || !lights) return fail(ctx, DGSM_ERR_INVALID_ARG, "null atlas, radii or lights");
     if (n_q > 0 && (!q_means || !colors_in || !colors_out))
@@ -169,20 +204,45 @@ extern "C" int dgsm_attenuate(dgsm_ctx *ctx, const void *atlas, const void *atla
     const int grid = (int)std::min<int64_t>((n_q + span - 1) / span, (int64_t)ctx->num_sms * 32);
     switch (dtype) {
         case DGSM_F32:
-            attenuate_kernel<float><<<grid, ATT_THREADS, 0, s>>>((const float *)atlas, (const float *)atlas_dyn,
-                L, H, W, radii, K, lights, q_means, colors_in, n_q, light_w, direct_frac, colors_out, T_out);
+            launch_attenuate<float>(grid, s, atlas, atlas_dyn, sep, L, H, W, radii, K, dg, lights, q_means,
+                                    colors_in, n_q, light_w, direct_frac, colors_out, T_out);
             break;
         case DGSM_F16:
-            attenuate_kernel<__half><<<grid, ATT_THREADS, 0, s>>>((const __half *)atlas, (const __half *)atlas_dyn,
-                L, H, W, radii, K, lights, q_means, colors_in, n_q, light_w, direct_frac, colors_out, T_out);
+            launch_attenuate<__half>(grid, s, atlas, atlas_dyn, sep, L, H, W, radii, K, dg, lights, q_means,
+                                     colors_in, n_q, light_w, direct_frac, colors_out, T_out);
             break;
         default:
-            attenuate_kernel<__nv_bfloat16><<<grid, ATT_THREADS, 0, s>>>((const __nv_bfloat16 *)atlas,
-                (const __nv_bfloat16 *)atlas_dyn, L, H, W, radii, K, lights, q_means, colors_in, n_q,
-                light_w, direct_frac, colors_out, T_out);
+            launch_attenuate<__nv_bfloat16>(grid, s, atlas, atlas_dyn, sep, L, H, W, radii, K, dg, lights,
+                                            q_means, colors_in, n_q, light_w, direct_frac, colors_out, T_out);
     }
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "attenuate_kernel");
+}
+}  // namespace
+
+extern "C" int dgsm_attenuate(dgsm_ctx *ctx, const void *atlas, const void *atlas_dyn,
+                              int32_t dtype, int32_t L, int32_t H, int32_t W, const float *radii,
+                              int32_t K, const float *lights, const float *q_means,
+                              const float *colors_in, int64_t n_q, const float *light_w,
+                              float direct_frac, float *colors_out, float *T_out, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    return attenuate_common(ctx, atlas, atlas_dyn, dtype, L, H, W, radii, K, false,
+                            DynGeom{H, W, K, radii}, lights, q_means, colors_in, n_q, light_w,
+                            direct_frac, colors_out, T_out, stream);
+}
+
+extern "C" int dgsm_attenuate_dyn(dgsm_ctx *ctx, const void *atlas, int32_t dtype, int32_t L,
+                                  int32_t H, int32_t W, const float *radii, int32_t K,
+                                  const void *atlas_dyn, int32_t H_dyn, int32_t W_dyn,
+                                  const float *radii_dyn, int32_t K_dyn, const float *lights,
+                                  const float *q_means, const float *colors_in, int64_t n_q,
+                                  const float *light_w, float direct_frac, float *colors_out,
+                                  float *T_out, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (!atlas_dyn) return fail(ctx, DGSM_ERR_INVALID_ARG, "null dynamic atlas");
+    return attenuate_common(ctx, atlas, atlas_dyn, dtype, L, H, W, radii, K, true,
+                            DynGeom{H_dyn, W_dyn, K_dyn, radii_dyn}, lights, q_means, colors_in, n_q,
+                            light_w, direct_frac, colors_out, T_out, stream);
 }
 
 extern "C" int dgsm_sample_index(dgsm_ctx *ctx, const float *points, int64_t n, const float *light,

@@ -283,7 +283,9 @@ __global__ void __launch_bounds__(256) bin_kernel(
     const BinRec *__restrict__ bin, int64_t N, int L, int tx, int ty, int sx, int sy,
     const float4 *__restrict__ cones, uint32_t *__restrict__ counts,
     const uint32_t *__restrict__ offsets, uint32_t *__restrict__ keys,
-    uint32_t *__restrict__ vals) {
+    uint32_t *__restrict__ vals, const unsigned long long *__restrict__ keep, uint32_t cap) {
+    // EMIT: nothing to write when the pairs overflow the buffers (*keep == 0)
+    if (EMIT && *keep == 0) return;
     const int64_t total = (int64_t)L * N;
     const int n_tiles = tx * ty, n_super = sx * sy;
     const float4 *scones = cones + 2 * n_tiles;
@@ -302,6 +304,7 @@ __global__ void __launch_bounds__(256) bin_kernel(
         if (mode == 2) {
             if (EMIT)
                 for (int t = lane; t < n_tiles; t += 32) {
+                    if (off + t >= cap) break;
                     keys[off + t] = kbase + t;
                     vals[off + t] = gi;
                 }
@@ -323,8 +326,10 @@ __global__ void __launch_bounds__(256) bin_kernel(
                         const unsigned m2 = __ballot_sync(0xffffffffu, ov);
                         if (EMIT && ov) {
                             const uint32_t pos = off + c + __popc(m2 & lt);
-                            keys[pos] = kbase + t;
-                            vals[pos] = gi;
+                            if (pos < cap) {
+                                keys[pos] = kbase + t;
+                                vals[pos] = gi;
+                            }
                         }
                         c += __popc(m2);
                     }
@@ -335,11 +340,29 @@ __global__ void __launch_bounds__(256) bin_kernel(
     }
 }
 
-__global__ void tile_ranges_kernel(const uint32_t *__restrict__ keys, int64_t P,
+// The pairs the build keeps: all of them, or none (status DGSM_ERR_WORKSPACE)
+// when they do not fit the buffers sized for `cap`.
+__global__ void keep_pairs_kernel(const unsigned long long *__restrict__ total,
+                                  unsigned long long cap, unsigned long long *__restrict__ keep,
+                                  int *__restrict__ status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const unsigned long long P = *total;
+    if (P > cap) {
+        *keep = 0;
+        record_status(status, DGSM_ERR_WORKSPACE);
+    } else {
+        *keep = P;
+    }
+}
+
+__global__ void tile_ranges_kernel(const uint32_t *__restrict__ keys,
+                                   const unsigned long long *__restrict__ d_P, uint32_t nkeys,
                                    uint32_t *__restrict__ start, uint32_t *__restrict__ end) {
+    const int64_t P = (int64_t)*d_P;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
          p += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t k = keys[p];
+        if (k >= nkeys) continue;
         if (p == 0 || keys[p - 1] != k) start[k] = (uint32_t)p;
         if (p == P - 1 || keys[p + 1] != k) end[k] = (uint32_t)(p + 1);
     }
@@ -728,7 +751,9 @@ int check_common(dgsm_ctx *ctx, const float *means, const float *scales, const f
     return DGSM_OK;
 }
 
-// prep + binning + sort + ranges.  Blocks once to read the pair count.
+// prep + binning + sort + ranges.  With max_pairs = 0 it blocks once to
+// read the pair count and sizes the pair buffers from it; with max_pairs > 0
+// the buffers hold max_pairs and the count stays on the device.
 int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
                 const float *opac, int64_t N, const float *lights, int L, int H, int W,
                 const float *radii, int K, const dgsm_params &p, cudaStream_t s, BinOut *out) {
@@ -763,43 +788,52 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     const int wgrid = (int)std::min<int64_t>((LN * 32 + 255) / 256, (int64_t)ctx->num_sms * 16);
     bin_kernel<false><<<wgrid, 256, 0, s>>>((const BinRec *)w_bin, N, L, tx, ty, sx, sy,
                                              (const float4 *)w_cones, (uint32_t *)w_cnt, nullptr,
-                                             nullptr, nullptr);
+                                             nullptr, nullptr, nullptr, 0u);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "prep/count kernels");
-    if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_cnt, (uint32_t *)w_cnt, LN, ctx->d_stats + 3, s)))
+    unsigned long long *d_total = ctx->d_stats + 3, *d_keep = ctx->d_stats + 4;
+    if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_cnt, (uint32_t *)w_cnt, LN, d_total, s)))
         return rc;
-    e = cudaMemcpyAsync(ctx->h_pinned, ctx->d_stats + 3, sizeof(unsigned long long),
-                        cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned + 1, ctx->d_status, sizeof(int),
-                                              cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "build: pair count");
-    const int st = *(int *)(ctx->h_pinned + 1);
-    if (st != DGSM_OK) {
-        cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
-        return fail(ctx, st, "a Gaussian has a non-finite field or a non-positive scale");
+    int64_t cap = p.max_pairs;
+    if (cap == 0) {
+        e = cudaMemcpyAsync(ctx->h_pinned, d_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned + 1, ctx->d_status, sizeof(int),
+                                                  cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "build: pair count");
+        const int st = *(int *)(ctx->h_pinned + 1);
+        if (st != DGSM_OK) {
+            cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
+            return fail(ctx, st, "a Gaussian has a non-finite field or a non-positive scale");
+        }
+        const unsigned long long P = ctx->h_pinned[0];
+        if (P >= (1ull << 31)) return fail(ctx, DGSM_ERR_WORKSPACE, "more than 2^31 binned pairs");
+        if (P == 0) {
+            e = cudaMemsetAsync(d_keep, 0, sizeof(unsigned long long), s);
+            return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "build: memset");
+        }
+        cap = (int64_t)P;
     }
-    const unsigned long long P = ctx->h_pinned[0];
-    if (P >= (1ull << 31)) return fail(ctx, DGSM_ERR_WORKSPACE, "more than 2^31 binned pairs");
-    out->P = (int64_t)P;
-    if (P == 0) return DGSM_OK;
+    out->P = cap;
     void *ka, *va, *kb, *vb;
-    if ((rc = ws_reserve(ctx, WS_KEYS_A, sizeof(uint32_t) * P, &ka))) return rc;
-    if ((rc = ws_reserve(ctx, WS_VALS_A, sizeof(uint32_t) * P, &va))) return rc;
-    if ((rc = ws_reserve(ctx, WS_KEYS_B, sizeof(uint32_t) * P, &kb))) return rc;
-    if ((rc = ws_reserve(ctx, WS_VALS_B, sizeof(uint32_t) * P, &vb))) return rc;
+    if ((rc = ws_reserve(ctx, WS_KEYS_A, sizeof(uint32_t) * cap, &ka))) return rc;
+    if ((rc = ws_reserve(ctx, WS_VALS_A, sizeof(uint32_t) * cap, &va))) return rc;
+    if ((rc = ws_reserve(ctx, WS_KEYS_B, sizeof(uint32_t) * cap, &kb))) return rc;
+    if ((rc = ws_reserve(ctx, WS_VALS_B, sizeof(uint32_t) * cap, &vb))) return rc;
+    keep_pairs_kernel<<<1, 32, 0, s>>>(d_total, (unsigned long long)cap, d_keep, ctx->d_status);
     bin_kernel<true><<<wgrid, 256, 0, s>>>((const BinRec *)w_bin, N, L, tx, ty, sx, sy,
                                             (const float4 *)w_cones, nullptr,
-                                            (const uint32_t *)w_cnt, (uint32_t *)ka, (uint32_t *)va);
+                                            (const uint32_t *)w_cnt, (uint32_t *)ka, (uint32_t *)va,
+                                            d_keep, (uint32_t)cap);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "bin emit kernel");
     int bits = 0;
     while (bits < 32 && ((uint64_t)(nkeys - 1) >> bits) != 0) ++bits;
     uint32_t *keys = (uint32_t *)ka, *vals = (uint32_t *)va;
-    if ((rc = radix_sort_pairs(ctx, &keys, &vals, (uint32_t *)kb, (uint32_t *)vb, (int64_t)P, bits, s)))
+    if ((rc = radix_sort_pairs(ctx, &keys, &vals, (uint32_t *)kb, (uint32_t *)vb, d_keep, cap, bits, s)))
         return rc;
-    const int rgrid = (int)std::min<int64_t>(((int64_t)P + 255) / 256, (int64_t)ctx->num_sms * 16);
-    tile_ranges_kernel<<<rgrid, 256, 0, s>>>(keys, (int64_t)P, out->ts, out->te);
+    const int rgrid = (int)std::min<int64_t>((cap + 255) / 256, (int64_t)ctx->num_sms * 16);
+    tile_ranges_kernel<<<rgrid, 256, 0, s>>>(keys, d_keep, (uint32_t)nkeys, out->ts, out->te);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tile ranges kernel");
     out->keys = keys;
@@ -831,7 +865,14 @@ extern "C" int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
-    const bool prof = ctx->prof && ctx->prof_count < dgsm_ctx::PROF_RING;
+    if (p.max_pairs < 0) return fail(ctx, DGSM_ERR_INVALID_ARG, "max_pairs < 0");
+    cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap_st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamIsCapturing");
+    const bool capturing = cap_st != cudaStreamCaptureStatusNone;
+    if (capturing && p.max_pairs == 0)
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "dgsm_build under stream capture needs max_pairs > 0");
+    const bool prof = ctx->prof && !capturing && ctx->prof_count < dgsm_ctx::PROF_RING;
     cudaEvent_t *ev = prof ? ctx->prof_ev[ctx->prof_count] : nullptr;
     if (prof) cudaEventRecord(ev[0], s);
     BinOut b;
@@ -892,7 +933,6 @@ extern "C" int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales
         cudaEventRecord(ev[2], s);
         ++ctx->prof_count;
     }
-    ctx->h_pinned[8] = (unsigned long long)b.P;  // pair count of this build
     return DGSM_OK;
 }
 
@@ -900,10 +940,10 @@ extern "C" int dgsm_get_build_stats(dgsm_ctx *ctx, dgsm_build_stats *out) {
     if (!ctx || !out) return DGSM_ERR_INVALID_ARG;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemcpy(ctx->h_pinned + 4, ctx->d_stats, 3 * sizeof(unsigned long long),
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->h_pinned + 4, ctx->d_stats, 4 * sizeof(unsigned long long),
                                          cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "dgsm_get_build_stats");
-    out->n_pairs = (int64_t)ctx->h_pinned[8];
+    out->n_pairs = (int64_t)ctx->h_pinned[7];
     out->rays_tested = (int64_t)ctx->h_pinned[4];
     out->ray_evals = (int64_t)ctx->h_pinned[5];
     out->shell_evals = (int64_t)ctx->h_pinned[6];
@@ -918,6 +958,7 @@ extern "C" int dgsm_bin(dgsm_ctx *ctx, const float *means, const float *scales, 
     if (!ctx || !n_pairs_out) return DGSM_ERR_INVALID_ARG;
     dgsm_params p;
     if (params) p = *params; else dgsm_default_params(&p);
+    p.max_pairs = 0;  // exact count: it is returned to the caller
     int rc = check_common(ctx, means, scales, opac, n, lights, L, H, W, radii, K, p);
     if (rc) return rc;
     if (capacity < 0 || (capacity > 0 && (!keys_out || !vals_out)))

@@ -18,9 +18,22 @@ int cuda_fail(dgsm_ctx *ctx, cudaError_t e, const char *what) {
     return fail(ctx, DGSM_ERR_CUDA, buf);
 }
 
+bool make_segs(const int64_t *seg, int n_obj, int64_t n, Segs *out) {
+    if (!seg || n_obj < 1 || n_obj > MAX_OBJECTS || seg[0] != 0 || seg[n_obj] != n) return false;
+    for (int o = 0; o < n_obj; ++o)
+        if (seg[o + 1] < seg[o]) return false;
+    for (int o = 0; o <= MAX_OBJECTS; ++o) out->s[o] = o <= n_obj ? seg[o] : n;
+    out->n = n_obj;
+    return true;
+}
+
 int ws_reserve(dgsm_ctx *ctx, int slot, size_t bytes, void **out) {
     if (bytes == 0) bytes = 256;
     if (ctx->ws_cap[slot] < bytes) {
+        if (ctx->frozen)
+            return fail(ctx, DGSM_ERR_WORKSPACE,
+                        "workspace would grow while a captured graph uses it: run the same calls "
+                        "once before capturing");
         // grow by 25% headroom so that repeated builds of similar size do not reallocate
         size_t want = bytes + bytes / 4;
         if (ctx->ws[slot]) {
@@ -51,7 +64,7 @@ extern "C" void dgsm_default_params(dgsm_params *p) {
     p->tile = 8;
     p->chunk = 128;
     p->atlas_dtype = DGSM_F32;
-    p->reserved = 0;
+    p->max_pairs = 0;
 }
 
 extern "C" void dgsm_default_relight_params(dgsm_relight_params *p) {

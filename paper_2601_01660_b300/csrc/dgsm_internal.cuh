@@ -28,6 +28,7 @@ enum WsSlot {
     WS_FRAME,          // device copies of a host frame (dgsm_frame_host)
     WS_NF,             // surrogate training: per-sample rows and partial gradients
     WS_NF_ACC,         // surrogate attenuation over more than four lights: partial sums
+    WS_POSES,          // rigid poses of moving objects, copied in per call
     WS_NSLOTS
 };
 
@@ -37,7 +38,9 @@ struct dgsm_ctx {
     void *ws[WS_NSLOTS] = {};
     size_t ws_cap[WS_NSLOTS] = {};
     int *d_status = nullptr;                 // first error code recorded by a kernel
-    unsigned long long *d_stats = nullptr;   // [0] rays tested, [1] ray evals, [2] shell evals, [3] pairs
+    // [0] rays tested, [1] ray evals, [2] shell evals, [3] binned pairs,
+    // [4] pairs the build keeps (= [3], or 0 when they overflow max_pairs)
+    unsigned long long *d_stats = nullptr;
     unsigned long long *h_pinned = nullptr;  // pinned staging for small device->host reads
     int num_sms = 148;
     // optional phase timing of dgsm_build: events recorded on the caller's stream
@@ -45,9 +48,33 @@ struct dgsm_ctx {
     bool prof = false;
     int prof_count = 0;
     cudaEvent_t prof_ev[PROF_RING][3] = {};
+    // > 0 while a graph captured on this context is alive: its nodes hold
+    // workspace addresses, so the workspace must not move
+    int frozen = 0;
 };
 
 namespace dgsm {
+
+// Contiguous objects of a Gaussian array (avatars): object o holds the
+// Gaussians [s[o], s[o+1]).  Passed to kernels by value, so a captured graph
+// keeps it.
+constexpr int MAX_OBJECTS = 64;
+struct Segs {
+    long long s[MAX_OBJECTS + 1];
+    int n;
+};
+// Host check: 1 <= n_obj <= MAX_OBJECTS, seg[0] = 0, nondecreasing, seg[n_obj] = n.
+bool make_segs(const int64_t *seg, int n_obj, int64_t n, Segs *out);
+
+// Object holding Gaussian g (s[0] <= g < s[n]): the last o with s[o] <= g.
+__device__ __forceinline__ int seg_find(const Segs &sg, long long g) {
+    int lo = 0, hi = sg.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sg.s[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 int fail(dgsm_ctx *ctx, int code, const std::string &msg);
 int cuda_fail(dgsm_ctx *ctx, cudaError_t e, const char *what);
@@ -59,10 +86,12 @@ int ws_reserve(dgsm_ctx *ctx, int slot, size_t bytes, void **out);
 int scan_exclusive_u32(dgsm_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
                        unsigned long long *d_total, cudaStream_t s);
 // Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
-// Sorted result ends in (*keys_io, *vals_io) (the pointers may be swapped
-// with the alternate buffers).
+// The pair count is read on the device from *d_n (at most n_max, which
+// sizes the launches).  Sorted result ends in (*keys_io, *vals_io) (the
+// pointers may be swapped with the alternate buffers).
 int radix_sort_pairs(dgsm_ctx *ctx, uint32_t **keys_io, uint32_t **vals_io, uint32_t *keys_alt,
-                     uint32_t *vals_alt, int64_t n, int bits, cudaStream_t s);
+                     uint32_t *vals_alt, const unsigned long long *d_n, int64_t n_max, int bits,
+                     cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // IEEE single-precision operations that are never contracted or reordered:

@@ -53,6 +53,55 @@ __global__ void centroid_final_kernel(const double *__restrict__ partials, int n
     out[2] = (float)(a[2] * inv);
 }
 
+// Per-object partial sums: blockIdx.y is the object, blockIdx.x strides
+// over its Gaussians.
+__global__ void __launch_bounds__(CEN_THREADS) segment_centroid_partial_kernel(
+    const float *__restrict__ means, const float *__restrict__ w, const __grid_constant__ Segs segs,
+    double *__restrict__ partials) {
+    const int o = blockIdx.y;
+    const long long b = segs.s[o], e = segs.s[o + 1];
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long i = b + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double wi = w ? (double)w[i] : 1.0;
+        a[0] += wi * means[3 * i];
+        a[1] += wi * means[3 * i + 1];
+        a[2] += wi * means[3 * i + 2];
+        a[3] += wi;
+    }
+    __shared__ double red[CEN_THREADS / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = 0; c < 4; ++c) {
+        double x = a[c];
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+        if (lane == 0) red[warp][c] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double x = 0.0;
+        for (int q = 0; q < CEN_THREADS / 32; ++q) x += red[q][threadIdx.x];
+        partials[4 * ((int64_t)o * gridDim.x + blockIdx.x) + threadIdx.x] = x;
+    }
+}
+
+// One warp per object.
+__global__ void segment_centroid_final_kernel(const double *__restrict__ partials, int nb, int n_obj,
+                                              float *__restrict__ out) {
+    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (o >= n_obj) return;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = lane; b < nb; b += 32)
+        for (int c = 0; c < 4; ++c) a[c] += partials[4 * ((int64_t)o * nb + b) + c];
+    for (int c = 0; c < 4; ++c)
+        for (int off = 16; off > 0; off >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], off);
+    if (lane == 0) {
+        const double inv = a[3] > 0.0 ? 1.0 / a[3] : 0.0;
+        out[3 * o] = (float)(a[0] * inv);
+        out[3 * o + 1] = (float)(a[1] * inv);
+        out[3 * o + 2] = (float)(a[2] * inv);
+    }
+}
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
@@ -76,6 +125,32 @@ extern "C" int dgsm_weighted_centroid(dgsm_ctx *ctx, const float *means, const f
     centroid_final_kernel<<<1, 32, 0, s>>>((const double *)part, nb, out);
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "centroid kernels");
+}
+
+extern "C" int dgsm_segment_centroids(dgsm_ctx *ctx, const float *means, const float *weights,
+                                      int64_t n, const int64_t *seg, int32_t n_obj, float *out,
+                                      void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    Segs segs;
+    if (n < 0 || !out || (n > 0 && !means) || !make_segs(seg, n_obj, n, &segs))
+        return fail(ctx, DGSM_ERR_INVALID_ARG,
+                    "segment_centroids: bad arguments (need 1 <= n_obj <= 64, 0 = seg[0] <= ... <= seg[n_obj] = n)");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t longest = 0;
+    for (int o = 0; o < n_obj; ++o) longest = std::max<int64_t>(longest, seg[o + 1] - seg[o]);
+    const int bps = (int)std::max<int64_t>(
+        1, std::min<int64_t>((longest + CEN_THREADS - 1) / CEN_THREADS,
+                             std::max<int64_t>(1, 2 * (int64_t)ctx->num_sms / n_obj)));
+    void *part;
+    int rc = ws_reserve(ctx, WS_CENTROID, sizeof(double) * 4 * (size_t)bps * n_obj, &part);
+    if (rc) return rc;
+    segment_centroid_partial_kernel<<<dim3(bps, n_obj), CEN_THREADS, 0, s>>>(means, weights, segs,
+                                                                           (double *)part);
+    segment_centroid_final_kernel<<<(n_obj + 7) / 8, 256, 0, s>>>((const double *)part, bps, n_obj, out);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "segment centroid kernels");
 }
 
 extern "C" int dgsm_frame_host(dgsm_ctx *ctx, const dgsm_frame_host_in *in,

@@ -103,9 +103,10 @@ constexpr int RS_SEG = RS_THREADS * RS_ROUNDS;
 constexpr int RS_WARPS = RS_THREADS / 32;
 
 __global__ void __launch_bounds__(RS_THREADS) radix_hist_kernel(const uint32_t *__restrict__ keys,
-                                                                int64_t n, int shift,
+                                                                const unsigned long long *d_n, int shift,
                                                                 uint32_t *__restrict__ hist, int nb) {
     __shared__ uint32_t h[256];
+    const int64_t n = (int64_t)*d_n;
     h[threadIdx.x] = 0;
     __syncthreads();
     int64_t base = (int64_t)blockIdx.x * RS_SEG;
@@ -119,9 +120,10 @@ __global__ void __launch_bounds__(RS_THREADS) radix_hist_kernel(const uint32_t *
 
 __global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-    uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n, int shift,
-    const uint32_t *__restrict__ offs, int nb) {
+    uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
+    const unsigned long long *d_n, int shift, const uint32_t *__restrict__ offs, int nb) {
     __shared__ uint32_t base[256];
+    const int64_t n = (int64_t)*d_n;
     __shared__ uint32_t wcnt[RS_WARPS][256];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -183,19 +185,20 @@ int scan_exclusive_u32(dgsm_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t
 }
 
 int radix_sort_pairs(dgsm_ctx *ctx, uint32_t **keys_io, uint32_t **vals_io, uint32_t *keys_alt,
-                     uint32_t *vals_alt, int64_t n, int bits, cudaStream_t s) {
-    if (n <= 1 || bits <= 0) return DGSM_OK;
-    int nb = (int)((n + RS_SEG - 1) / RS_SEG);
+                     uint32_t *vals_alt, const unsigned long long *d_n, int64_t n_max, int bits,
+                     cudaStream_t s) {
+    if (n_max <= 1 || bits <= 0) return DGSM_OK;
+    int nb = (int)((n_max + RS_SEG - 1) / RS_SEG);
     void *h;
     int rc = ws_reserve(ctx, WS_HIST, sizeof(uint32_t) * 256 * (size_t)nb, &h);
     if (rc) return rc;
     uint32_t *hist = (uint32_t *)h;
     uint32_t *ka = *keys_io, *va = *vals_io, *kb = keys_alt, *vb = vals_alt;
     for (int shift = 0; shift < bits; shift += 8) {
-        radix_hist_kernel<<<nb, RS_THREADS, 0, s>>>(ka, n, shift, hist, nb);
+        radix_hist_kernel<<<nb, RS_THREADS, 0, s>>>(ka, d_n, shift, hist, nb);
         rc = scan_exclusive_u32(ctx, hist, hist, 256 * (int64_t)nb, nullptr, s);
         if (rc) return rc;
-        radix_scatter_kernel<<<nb, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, hist, nb);
+        radix_scatter_kernel<<<nb, RS_THREADS, 0, s>>>(ka, va, kb, vb, d_n, shift, hist, nb);
         uint32_t *t = ka; ka = kb; kb = t;
         t = va; va = vb; vb = t;
     }

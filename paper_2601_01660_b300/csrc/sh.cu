@@ -149,12 +149,15 @@ __global__ void sh_fit_solve_kernel(const double *__restrict__ partials, int nbl
 __global__ void __launch_bounds__(256) relight_kernel(
     const float *__restrict__ sh, const float *__restrict__ means, const float *__restrict__ quats,
     const float *__restrict__ scales, const float *__restrict__ normals,
-    const float *__restrict__ centroid, const float *cin, int64_t N, float q, float gamma,
-    float t_max, float eps, int nth, int nph, float *cout) {
+    const float *__restrict__ centroid, const __grid_constant__ Segs segs, const float *cin,
+    int64_t N, float q, float gamma, float t_max, float eps, int nth, int nph, float *cout) {
     extern __shared__ float4 tab[];  // 2 per direction: (omega, w), (w L_r, w L_g, w L_b, 0)
     __shared__ float shs[27];
+    __shared__ float cen[3 * MAX_OBJECTS];  // centroid of each object (normals == NULL)
     const int M = nth * nph;
     for (int k = threadIdx.x; k < 27; k += blockDim.x) shs[k] = sh[k];
+    if (!normals)
+        for (int k = threadIdx.x; k < 3 * segs.n; k += blockDim.x) cen[k] = centroid[k];
     __syncthreads();
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
         const int it = j / nph, ip = j - it * nph;
@@ -174,8 +177,6 @@ __global__ void __launch_bounds__(256) relight_kernel(
         tab[2 * j + 1] = make_float4(st * Lc[0], st * Lc[1], st * Lc[2], 0.0f);
     }
     __syncthreads();
-    float cx = 0.f, cy = 0.f, cz = 0.f;
-    if (!normals) { cx = centroid[0]; cy = centroid[1]; cz = centroid[2]; }
     const bool lambert = q == 1.0f;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
          g += (int64_t)gridDim.x * blockDim.x) {
@@ -201,6 +202,8 @@ __global__ void __launch_bounds__(256) relight_kernel(
             } else {
                 nx = 2.f * (qx * qz + qw * qy); ny = 2.f * (qy * qz - qw * qx); nz = 1.f - 2.f * (qx * qx + qy * qy);
             }
+            const int o = segs.n == 1 ? 0 : seg_find(segs, g);
+            const float cx = cen[3 * o], cy = cen[3 * o + 1], cz = cen[3 * o + 2];
             const float side = nx * (means[3 * g] - cx) + ny * (means[3 * g + 1] - cy) +
                                nz * (means[3 * g + 2] - cz);
             if (side < 0.0f) { nx = -nx; ny = -ny; nz = -nz; }
@@ -262,20 +265,19 @@ extern "C" int sh_fit(dgsm_ctx *ctx, const float *dirs, const float *rgb, const 
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "sh_fit kernels");
 }
 
-extern "C" int sh_relight(dgsm_ctx *ctx, const float *sh, const float *means, const float *quats,
-                          const float *scales, const float *normals, const float *centroid,
-                          const float *colors_in, int64_t n, const dgsm_relight_params *params,
-                          float *colors_out, void *stream) {
-    if (!ctx) return DGSM_ERR_INVALID_ARG;
+namespace {
+int relight_launch(dgsm_ctx *ctx, const float *sh, const float *means, const float *quats,
+                   const float *scales, const float *normals, const float *centroids,
+                   const Segs &segs, const float *colors_in, int64_t n,
+                   const dgsm_relight_params *params, float *colors_out, void *stream) {
     dgsm_relight_params p;
     if (params) p = *params; else dgsm_default_relight_params(&p);
-    if (n < 0) return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_relight: n < 0");
     if (p.n_theta < 1 || p.n_phi < 1 || (int64_t)p.n_theta * p.n_phi > 6144)
         return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_relight: need 1 <= n_theta * n_phi <= 6144");
     if (!(p.q > 0.0f) || !(p.eps >= 0.0f) || !(p.t_max >= 0.0f))
         return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_relight: need q > 0, eps >= 0, t_max >= 0");
     if (!sh) return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_relight: null sh");
-    if (n > 0 && (!colors_in || !colors_out || (!normals && (!means || !quats || !scales || !centroid))))
+    if (n > 0 && (!colors_in || !colors_out || (!normals && (!means || !quats || !scales || !centroids))))
         return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_relight: null Gaussian array");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
@@ -285,10 +287,39 @@ extern "C" int sh_relight(dgsm_ctx *ctx, const float *sh, const float *means, co
     if (e != cudaSuccess) return cuda_fail(ctx, e, "relight smem attribute");
     const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 2);
     relight_kernel<<<grid, 256, smem, (cudaStream_t)stream>>>(
-        sh, means, quats, scales, normals, centroid, colors_in, n, p.q, p.gamma, p.t_max, p.eps,
-        p.n_theta, p.n_phi, colors_out);
+        sh, means, quats, scales, normals, centroids, segs, colors_in, n, p.q, p.gamma, p.t_max,
+        p.eps, p.n_theta, p.n_phi, colors_out);
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "relight_kernel");
+}
+}  // namespace
+
+extern "C" int sh_relight(dgsm_ctx *ctx, const float *sh, const float *means, const float *quats,
+                          const float *scales, const float *normals, const float *centroid,
+                          const float *colors_in, int64_t n, const dgsm_relight_params *params,
+                          float *colors_out, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (n < 0) return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_relight: n < 0");
+    const int64_t whole[2] = {0, n};
+    Segs segs;
+    make_segs(whole, 1, n, &segs);
+    return relight_launch(ctx, sh, means, quats, scales, normals, centroid, segs, colors_in, n,
+                          params, colors_out, stream);
+}
+
+extern "C" int sh_relight_objects(dgsm_ctx *ctx, const float *sh, const float *means,
+                                  const float *quats, const float *scales, const float *centroids,
+                                  const int64_t *seg, int32_t n_obj, const float *colors_in,
+                                  int64_t n, const dgsm_relight_params *params, float *colors_out,
+                                  void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (n < 0) return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_relight_objects: n < 0");
+    Segs segs;
+    if (!make_segs(seg, n_obj, n, &segs))
+        return fail(ctx, DGSM_ERR_INVALID_ARG,
+                    "sh_relight_objects: need 1 <= n_obj <= 64 and 0 = seg[0] <= ... <= seg[n_obj] = n");
+    return relight_launch(ctx, sh, means, quats, scales, nullptr, centroids, segs, colors_in, n,
+                          params, colors_out, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -256,6 +256,47 @@ def four_lights() -> np.ndarray:
     return _f32([[0.0, 0.0, 0.0], [1.5, 1.5, -0.5], [-1.5, 1.5, -0.5], [0.0, -2.0, -0.5]])
 
 
+def room_lights() -> np.ndarray:
+    """Four ceiling lights of the room, 2.8 m high over the quarters of the floor."""
+    return _f32([[-2.5, -2.0, 2.8], [2.5, -2.0, 2.8], [-2.5, 2.0, 2.8], [2.5, 2.0, 2.8]])
+
+
+def avatar_crowd(seed: int, n_avatars: int = 8, n_each: int = 100_000):
+    """Rest-pose avatars for the moving-avatar workload, and their motion.
+
+    Each avatar is an avatar_body standing at the origin facing +x; they are
+    stored back to back (offsets `seg`).  Avatar a walks a circle of radius
+    r_a ~ U(1, 3) m at 1 m/s, centred so that the circle stays 0.3 m inside
+    the room's walls, starting at a random phase and direction, turned to
+    face its motion.  Returns (rest Scene, seg, motion dict)."""
+    rng = np.random.default_rng(seed)
+    bodies = [avatar_body(rng, n_each, base=(0.0, 0.0, 0.0)) for _ in range(n_avatars)]
+    rest = concat(*bodies)
+    seg = np.arange(n_avatars + 1, dtype=np.int64) * n_each
+    r = rng.uniform(1.0, 3.0, n_avatars)
+    cx = rng.uniform(-5.0 + r + 0.3, 5.0 - r - 0.3)
+    cy = rng.uniform(-4.0 + r + 0.3, 4.0 - r - 0.3)
+    motion = dict(radius=r, centre=np.stack([cx, cy], 1), phase=rng.uniform(0, 2 * math.pi, n_avatars),
+                  direction=rng.choice([-1.0, 1.0], n_avatars), speed=1.0, fps=30.0)
+    return rest, seg, motion
+
+
+def avatar_poses(motion: dict, frame: int) -> np.ndarray:
+    """(n_avatars, 8) float32 poses (qw, qx, qy, qz, tx, ty, tz, 0) at `frame`."""
+    t = frame / motion["fps"]
+    r, d = motion["radius"], motion["direction"]
+    th = motion["phase"] + d * motion["speed"] * t / r
+    px = motion["centre"][:, 0] + r * np.cos(th)
+    py = motion["centre"][:, 1] + r * np.sin(th)
+    yaw = np.arctan2(d * np.cos(th), -d * np.sin(th))   # along the tangent of travel
+    n = r.shape[0]
+    out = np.zeros((n, 8))
+    out[:, 0] = np.cos(0.5 * yaw)
+    out[:, 3] = np.sin(0.5 * yaw)
+    out[:, 4], out[:, 5] = px, py
+    return _f32(out)
+
+
 def cubemap_samples(face: int, seed: int, noise: float = 0.01):
     """Samples (D, Y, w) of a synthetic environment on the six cube faces.
 
@@ -303,6 +344,12 @@ def workload(name: str) -> dict:
                   relight of the avatar from a 6x64^2 cubemap fit.
     'room550k'    the same room with 300k + 200k + 50k Gaussians.
     'cube3m4l'    cube generator at 3M Gaussians, 4 lights, 64x64x16.
+    'crowd8'      the room without its avatar (1.5M static Gaussians; static
+                  atlases for 4 ceiling lights at 512x512x64, geometric
+                  0.05-12 m), 8 avatars of 100k walking for 120 frames
+                  (dynamic atlases 256x256x32, geometric 0.05-12 m), all 2.3M
+                  attenuated and the 800k avatar Gaussians relit per frame.
+    'crowd8s'     the same at a tenth of the Gaussians (for parity tests).
     """
     if name == "cube20k":
         occ = cube_scene(20_000, seed=0)
@@ -320,6 +367,15 @@ def workload(name: str) -> dict:
         return dict(name=name, occluders=sc, queries=sc, lights=_f32([[0, 0, 2.8]]),
                     H=512, W=512, radii=radii_geometric(0.05, 12.0, 64),
                     relight=subset(sc, sc.meta["avatar"]), cubemap=cubemap_samples(64, seed=5))
+    if name in ("crowd8", "crowd8s"):
+        small = name == "crowd8s"
+        room = room_scene(seed=2, n_flat=90_000 if small else 900_000,
+                          n_box=60_000 if small else 600_000, n_avatar=0)
+        rest, seg, motion = avatar_crowd(seed=6, n_each=10_000 if small else 100_000)
+        return dict(name=name, static=room, avatars=rest, seg=seg, motion=motion, frames=120,
+                    lights=room_lights(), H=512, W=512, radii=radii_geometric(0.05, 12.0, 64),
+                    H_dyn=256, W_dyn=256, radii_dyn=radii_geometric(0.05, 12.0, 32),
+                    cubemap=cubemap_samples(64, seed=5))
     if name == "cube3m4l":
         occ = cube_scene(3_000_000, seed=3)
         return dict(name=name, occluders=occ, queries=occ, lights=four_lights(),

@@ -138,17 +138,26 @@ int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales, const flo
 /* Counters of the last dgsm_build on ctx (blocks until they are ready). */
 int dgsm_get_build_stats(dgsm_ctx *ctx, dgsm_build_stats *out);
 
-/* The light-space tile binning of dgsm_build on its own: writes the sorted
- * pairs key = l * n_tiles + tile (tiles row-major, ceil(H/tile) x
- * ceil(W/tile) per light), value = Gaussian index, ordered by (key, value).
+/* The light-space tile binning of dgsm_build on its own (Sec. 3.2, the
+ * occluder-culling paragraph: tiles are binned by the Gaussian's projected
+ * footprint).  A Gaussian enters a tile's list when its bounding-sphere cone
+ * overlaps the tile's (and its 8x8 super-tile's) direction cone and its
+ * culling ellipsoid reaches the tile's polyhedral cone (no edge plane of the
+ * tile separates it); the test of the plane between the tile's halves gives a
+ * 2-bit mask of the halves (rows [0, tile/2) and [tile/2, tile)) its rays can
+ * hit.  All decisions are IEEE single-precision operations in a fixed order.
+ * Writes the sorted pairs key = l * n_tiles + tile (tiles row-major,
+ * ceil(H/tile) x ceil(W/tile) per light), value = Gaussian index | mask << 30
+ * (bit 30 top half, bit 31 bottom half), ordered by (key, Gaussian index).
  * keys_out/vals_out: device arrays of `capacity` uint32 (may be NULL when
  * capacity is 0); *n_pairs_out (host) receives the pair count.  Returns
  * DGSM_ERR_WORKSPACE (after setting *n_pairs_out) when capacity is short.
- * Blocks. */
-int dgsm_bin(dgsm_ctx *ctx, const float *means, const float *scales, const float *opac,
-             int64_t n, const float *lights, int32_t n_lights, int32_t H, int32_t W,
-             const float *radii, int32_t K, const dgsm_params *params, uint32_t *keys_out,
-             uint32_t *vals_out, int64_t capacity, int64_t *n_pairs_out, void *stream);
+ * n < 2^30.  Blocks. */
+int dgsm_bin(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
+             const float *opac, int64_t n, const float *lights, int32_t n_lights, int32_t H,
+             int32_t W, const float *radii, int32_t K, const dgsm_params *params,
+             uint32_t *keys_out, uint32_t *vals_out, int64_t capacity, int64_t *n_pairs_out,
+             void *stream);
 
 /* Receiver attenuation (Sec. 3.3, centre sample): for each query q and
  * light l, T_l = trilinear lookup of atlas[l] at the octahedral code of

@@ -68,7 +68,9 @@ def _declare(L):
     L.orc_f32_gauss_cone.restype = C.c_int
     L.orc_f32_gauss_cone.argtypes = [_f, _f, C.c_float, _f, C.c_float, C.c_float, C.c_float, _f]
     L.orc_f32_bin.restype = I64
-    L.orc_f32_bin.argtypes = [_f, _f, _f, I64, _f, C.c_int, C.c_int, C.c_int, _f, C.c_int,
+    L.orc_f32_rect_planes.argtypes = [C.c_int] * 7 + [_f]
+    L.orc_f32_gauss_axes.argtypes = [_f, _f, _f, _f, _f]
+    L.orc_f32_bin.argtypes = [_f, _f, _f, _f, I64, _f, C.c_int, C.c_int, C.c_int, _f, C.c_int,
                               C.c_float, C.c_float, C.c_int, _u32, _u32, I64]
     L.orc_count_ray_evals.restype = I64
     L.orc_count_ray_evals.argtypes = [_f, _f, _f, _f, I64, _f, C.c_int, C.c_int, _f, C.c_int,
@@ -246,11 +248,24 @@ def f32_gauss_cone(mu, s, alpha, o, kappa, eps, r_last):
     return r, out
 
 
+def f32_rect_planes(i0, i1, j0, j1, half, H, W) -> np.ndarray:
+    out = np.zeros(17, dtype=np.float32)
+    lib().orc_f32_rect_planes(i0, i1, j0, j1, half, H, W, _pf(out))
+    return out
+
+
+def f32_gauss_axes(mu, s, q, o) -> np.ndarray:
+    out = np.zeros(12, dtype=np.float32)
+    lib().orc_f32_gauss_axes(_pf(_c32(mu)), _pf(_c32(s)), _pf(_c32(q)), _pf(_c32(o)), _pf(out))
+    return out
+
+
 def f32_bin(sc, lights, H, W, radii, kappa=1.0, eps=1e-7, tile=8):
-    """Sorted (key, value) pairs of the binning specification."""
+    """Sorted (key, value) pairs of the binning specification; value =
+    Gaussian index | half-tile mask << 30."""
     lights = _c32(lights).reshape(-1, 3)
     radii = _c32(radii)
-    args = (_pf(sc.means), _pf(sc.scales), _pf(sc.opac), sc.n, _pf(lights), lights.shape[0],
+    args = (_pf(sc.means), _pf(sc.scales), _pf(sc.quats), _pf(sc.opac), sc.n, _pf(lights), lights.shape[0],
             H, W, _pf(radii), radii.shape[0], float(kappa), float(eps), int(tile))
     empty = np.zeros(1, dtype=np.uint32)
     total = lib().orc_f32_bin(*args, empty.ctypes.data_as(_u32), empty.ctypes.data_as(_u32), 0)

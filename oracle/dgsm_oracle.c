@@ -502,26 +502,169 @@ static int f32_overlap(const float *g, const float *cone) {
     return dot >= rhs;
 }
 
+static void f32_cross(const float *a, const float *b, float *c) {
+    volatile float p0 = a[1] * b[2], q0 = a[2] * b[1];
+    volatile float p1 = a[2] * b[0], q1 = a[0] * b[2];
+    volatile float p2 = a[0] * b[1], q2 = a[1] * b[0];
+    volatile float c0 = p0 - q0, c1 = p1 - q1, c2 = p2 - q2;
+    c[0] = c0; c[1] = c1; c[2] = c2;
+}
+
+/* Octahedral face of an atlas point: bit 0 u >= 0, bit 1 v >= 0, bit 2 the
+ * upper hemisphere ((1 - |u|) - |v| >= 0, as f32_decode decides it). */
+static int f32_face(float u, float v) {
+    volatile float au = fabsf(u), av = fabsf(v);
+    volatile float z = (1.0f - au) - av;
+    return (u >= 0.0f ? 1 : 0) | (v >= 0.0f ? 2 : 0) | (z >= 0.0f ? 4 : 0);
+}
+
+/* Plane through the light containing directions a and b, oriented so that
+ * direction c lies on its non-negative side. */
+static void f32_plane(const float *a, const float *b, const float *c, float *n) {
+    f32_cross(a, b, n);
+    if (f32_dot(n, c) < 0.0f) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
+}
+
+/* Separating planes of the texel-centre rectangle [j0,j1) x [i0,i1) for the
+ * ellipsoid test of the binning specification.  Inside one octahedral face
+ * the decode is affine in (u,v), so lines of the atlas are great circles and
+ * the rays through the rectangle's texel centres lie in the polyhedral cone
+ * of its four corner directions.  pl[0..2] top edge (row i0), [3..5] bottom
+ * edge (row i1-1), [6..8] left (column j0), [9..11] right (column j1-1),
+ * [12..14] the plane between the halves (rows [i0, i0+half) and
+ * [i0+half, i1)), each oriented non-negative on the rectangle's side (the
+ * mid plane: on the top half's side); pl[15] = 1 if the planes are valid
+ * (the rectangle lies in one face and has at least 2 rows and 2 columns);
+ * pl[16] = 1 if the bottom half is not empty. */
+void orc_f32_rect_planes(int i0, int i1, int j0, int j1, int half, int H, int W, float *pl) {
+    float ua = f32_centre(j0, W), ub = f32_centre(j1 - 1, W);
+    float va = f32_centre(i0, H), vb = f32_centre(i1 - 1, H);
+    for (int q = 0; q < 17; ++q) pl[q] = 0.0f;
+    pl[16] = i1 - i0 > half ? 1.0f : 0.0f;
+    int f = f32_face(ua, va);
+    if (!(ua < ub && va < vb) || f32_face(ub, va) != f || f32_face(ua, vb) != f || f32_face(ub, vb) != f)
+        return;
+    volatile float su = ua + ub, sv = va + vb;
+    volatile float uc = su * 0.5f, vc = sv * 0.5f;
+    float c[3], d00[3], d01[3], d10[3], d11[3];
+    f32_decode(uc, vc, c);
+    f32_decode(ua, va, d00); f32_decode(ub, va, d01);
+    f32_decode(ua, vb, d10); f32_decode(ub, vb, d11);
+    f32_plane(d00, d01, c, pl);
+    f32_plane(d10, d11, c, pl + 3);
+    f32_plane(d00, d10, c, pl + 6);
+    f32_plane(d01, d11, c, pl + 9);
+    if (pl[16] != 0.0f) {
+        volatile float num = (float)(2 * (i0 + half));
+        volatile float q = num / (float)H;
+        volatile float vm = q - 1.0f;
+        float m0[3], m1[3], top[3];
+        f32_decode(ua, vm, m0); f32_decode(ub, vm, m1);
+        f32_decode(uc, va, top);
+        f32_plane(m0, m1, top, pl + 12);
+    }
+    pl[15] = 1.0f;
+}
+
+/* Axes of a Gaussian for the ellipsoid test: out[0..2] = v = mu - o and
+ * out[3+3k .. 5+3k] = s_k times column k of R(q) (q normalised), so that
+ * n^T Sigma n = sum_k ((s_k r_k) . n)^2 -- a sum of squares, exact in sign
+ * for flat Gaussians. */
+void orc_f32_gauss_axes(const float *mu, const float *s, const float *q, const float *o, float *out) {
+    volatile float vx = mu[0] - o[0], vy = mu[1] - o[1], vz = mu[2] - o[2];
+    volatile float ww = q[0] * q[0], xx = q[1] * q[1], yy = q[2] * q[2], zz = q[3] * q[3];
+    volatile float n2a = ww + xx;
+    volatile float n2b = n2a + yy;
+    volatile float n2 = n2b + zz;
+    float n = sqrtf(n2);
+    volatile float w = q[0] / n, x = q[1] / n, y = q[2] / n, z = q[3] / n;
+    volatile float pxx = x * x, pyy = y * y, pzz = z * z;
+    volatile float pxy = x * y, pxz = x * z, pyz = y * z;
+    volatile float pwx = w * x, pwy = w * y, pwz = w * z;
+    volatile float t00 = pyy + pzz, t11 = pxx + pzz, t22 = pxx + pyy;
+    volatile float t01 = pxy - pwz, t10 = pxy + pwz, t02 = pxz + pwy;
+    volatile float t20 = pxz - pwy, t12 = pyz - pwx, t21 = pyz + pwx;
+    volatile float u00 = 2.0f * t00, u11 = 2.0f * t11, u22 = 2.0f * t22;
+    float R[9];
+    volatile float r00 = 1.0f - u00, r11 = 1.0f - u11, r22 = 1.0f - u22;
+    volatile float r01 = 2.0f * t01, r10 = 2.0f * t10, r02 = 2.0f * t02;
+    volatile float r20 = 2.0f * t20, r12 = 2.0f * t12, r21 = 2.0f * t21;
+    R[0] = r00; R[1] = r01; R[2] = r02; R[3] = r10; R[4] = r11; R[5] = r12; R[6] = r20; R[7] = r21; R[8] = r22;
+    out[0] = vx; out[1] = vy; out[2] = vz;
+    for (int k = 0; k < 3; ++k)
+        for (int r = 0; r < 3; ++r) {
+            volatile float e = R[3 * r + k] * s[k];
+            out[3 + 3 * k + r] = e;
+        }
+}
+
+/* Does the Gaussian's culling ellipsoid {x : (x-mu)^T A (x-mu) <= k^2}
+ * reach the non-negative side of plane n?  Its support there is
+ * n.v + k sqrt(n^T Sigma n); the test compares squares (with k^2 widened by
+ * 2^-10 against rounding) when n.v < 0. */
+static int f32_plane_ok(const float *n, const float *ax, float k2s) {
+    float nv = f32_dot(n, ax);
+    if (nv >= 0.0f) return 1;
+    float p0 = f32_dot(n, ax + 3), p1 = f32_dot(n, ax + 6), p2 = f32_dot(n, ax + 9);
+    volatile float a0 = p0 * p0, a1 = p1 * p1, a2 = p2 * p2;
+    volatile float s01 = a0 + a1;
+    volatile float ss = s01 + a2;
+    volatile float rhs = k2s * ss;
+    volatile float lhs = nv * nv;
+    return lhs <= rhs;
+}
+
+/* Half-tile mask of a (Gaussian, tile) pair whose cones overlap: bit 0 the
+ * top half may be hit, bit 1 the bottom half; 0 = the tile is not reached. */
+static unsigned f32_half_mask(const float *pl, const float *ax, float k2s, int inside) {
+    const unsigned hb = pl[16] != 0.0f ? 2u : 0u;
+    if (inside || pl[15] == 0.0f) return 1u | hb;
+    if (!f32_plane_ok(pl + 6, ax, k2s) || !f32_plane_ok(pl + 9, ax, k2s)) return 0u;
+    unsigned m = 0u;
+    if (!hb) return f32_plane_ok(pl, ax, k2s) ? 1u : 0u;
+    float nv = f32_dot(pl + 12, ax);
+    int mid_pos = 1, mid_neg = 1;   /* the ellipsoid reaches the top / bottom side of the mid plane */
+    if (nv != 0.0f) {
+        float p0 = f32_dot(pl + 12, ax + 3), p1 = f32_dot(pl + 12, ax + 6), p2 = f32_dot(pl + 12, ax + 9);
+        volatile float a0 = p0 * p0, a1 = p1 * p1, a2 = p2 * p2;
+        volatile float s01 = a0 + a1;
+        volatile float ss = s01 + a2;
+        volatile float rhs = k2s * ss;
+        volatile float lhs = nv * nv;
+        const int reach = lhs <= rhs;
+        mid_pos = nv > 0.0f || reach;
+        mid_neg = nv < 0.0f || reach;
+    }
+    if (mid_pos && f32_plane_ok(pl, ax, k2s)) m |= 1u;
+    if (mid_neg && f32_plane_ok(pl + 3, ax, k2s)) m |= 2u;
+    return m;
+}
+
 /* Light-space tile binning (Sec. 3.2, occluder culling), FP32 specification:
  * tiles of tile x tile texels, super-tiles of 8x8 tiles; a Gaussian enters a
- * tile's list iff its cone overlaps the super-tile's cone and the tile's cone.
- * Writes pairs (key = l * n_tiles + tile, value = Gaussian index) in
- * (key, value) order, up to `capacity`; returns the total number of pairs
- * (or -1 if an input was invalid). */
-int64_t orc_f32_bin(const float *means, const float *scales, const float *opac, int64_t N,
-                    const float *lights, int L, int H, int W, const float *radii, int K,
+ * tile's list iff its bounding cone overlaps the super-tile's cone and the
+ * tile's cone, and its culling ellipsoid reaches the tile's half-tile cones
+ * (f32_half_mask; every Gaussian when the light is inside its bounding
+ * sphere, and on tiles that straddle an octahedral face, both halves).
+ * Writes pairs (key = l * n_tiles + tile, value = Gaussian index | half mask
+ * << 30) in (key, Gaussian) order, up to `capacity`; returns the total number
+ * of pairs (or -1 if an input was invalid). */
+int64_t orc_f32_bin(const float *means, const float *scales, const float *quats, const float *opac,
+                    int64_t N, const float *lights, int L, int H, int W, const float *radii, int K,
                     float kappa, float eps, int tile, uint32_t *keys, uint32_t *vals,
                     int64_t capacity) {
     int ty = (H + tile - 1) / tile, tx = (W + tile - 1) / tile;
     int sy = (ty + 7) / 8, sx = (tx + 7) / 8;
     int n_tiles = ty * tx;
     float *tc = (float *)malloc(sizeof(float) * 6 * n_tiles);
+    float *tp = (float *)malloc(sizeof(float) * 17 * n_tiles);
     float *sc = (float *)malloc(sizeof(float) * 6 * sy * sx);
     for (int a = 0; a < ty; ++a)
         for (int b = 0; b < tx; ++b) {
             int i0 = a * tile, j0 = b * tile;
             int i1 = i0 + tile < H ? i0 + tile : H, j1 = j0 + tile < W ? j0 + tile : W;
             orc_f32_rect_cone(i0, i1, j0, j1, H, W, tc + 6 * (a * tx + b));
+            orc_f32_rect_planes(i0, i1, j0, j1, tile / 2, H, W, tp + 17 * (a * tx + b));
         }
     for (int a = 0; a < sy; ++a)
         for (int b = 0; b < sx; ++b) {
@@ -533,13 +676,22 @@ int64_t orc_f32_bin(const float *means, const float *scales, const float *opac, 
     int64_t total = 0;
     int bad = 0;
     float *cones = (float *)malloc(sizeof(float) * 9 * (N > 0 ? N : 1));
+    float *axes = (float *)malloc(sizeof(float) * 12 * (N > 0 ? N : 1));
+    float *k2s = (float *)malloc(sizeof(float) * (N > 0 ? N : 1));
     char *ok = (char *)malloc(N > 0 ? N : 1);
     for (int l = 0; l < L; ++l) {
         for (int64_t n = 0; n < N; ++n) {
             int r = orc_f32_gauss_cone(means + 3 * n, scales + 3 * n, opac[n], lights + 3 * l,
                                        kappa, eps, radii[K - 1], cones + 9 * n);
+            for (int c = 0; c < 4; ++c)
+                if (!isfinite(quats[4 * n + c])) r = -1;
             if (r < 0) bad = 1;
             ok[n] = r == 1;
+            if (ok[n]) {
+                orc_f32_gauss_axes(means + 3 * n, scales + 3 * n, quats + 4 * n, lights + 3 * l, axes + 12 * n);
+                volatile float w = cones[9 * n + 6] * 1.0009765625f;
+                k2s[n] = w;
+            }
         }
         for (int t = 0; t < n_tiles; ++t) {
             int a = t / tx, b = t % tx;
@@ -548,15 +700,17 @@ int64_t orc_f32_bin(const float *means, const float *scales, const float *opac, 
                 if (!ok[n]) continue;
                 if (!f32_overlap(cones + 9 * n, sup)) continue;
                 if (!f32_overlap(cones + 9 * n, tc + 6 * t)) continue;
+                unsigned m = f32_half_mask(tp + 17 * t, axes + 12 * n, k2s[n], cones[9 * n + 5] != 0.0f);
+                if (!m) continue;
                 if (total < capacity) {
                     keys[total] = (uint32_t)(l * n_tiles + t);
-                    vals[total] = (uint32_t)n;
+                    vals[total] = (uint32_t)n | (m << 30);
                 }
                 ++total;
             }
         }
     }
-    free(tc); free(sc); free(cones); free(ok);
+    free(tc); free(tp); free(sc); free(cones); free(axes); free(k2s); free(ok);
     return bad ? -1 : total;
 }
 

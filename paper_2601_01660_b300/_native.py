@@ -91,7 +91,7 @@ _lib.dgsm_status_string.restype = C.c_char_p
 _lib.dgsm_build.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i32,
                             C.POINTER(Params), _vp, _vp]
 _lib.dgsm_get_build_stats.argtypes = [_vp, C.POINTER(BuildStats)]
-_lib.dgsm_bin.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i32,
+_lib.dgsm_bin.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i32,
                           C.POINTER(Params), _vp, _vp, _i64, C.POINTER(_i64), _vp]
 _lib.dgsm_attenuate.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp,
                                 _i64, _vp, _f32, _vp, _vp, _vp]
@@ -240,14 +240,15 @@ def dgsm_get_build_stats(ctx: Context | None = None) -> dict:
             "shell_evals": st.shell_evals}
 
 
-def dgsm_bin(means, scales, opac, lights, H, W, radii, params=None, ctx: Context | None = None,
+def dgsm_bin(means, scales, quats, opac, lights, H, W, radii, params=None, ctx: Context | None = None,
              stream=None):
-    """Light-space tile binning: sorted (keys, values) uint32->int64 tensors."""
+    """Light-space tile binning: sorted (keys, values) int32 tensors holding the
+    uint32 key and value (Gaussian index | half-tile mask << 30)."""
     ctx = ctx or context(means.device.index)
     p = params if isinstance(params, Params) else Params.make(**(params or {}))
     L, K, n = lights.shape[0], radii.shape[0], means.shape[0]
     total = _i64(0)
-    args = (ctx.handle, _ptr(means), _ptr(scales), _ptr(opac), n, _ptr(lights), L, H, W,
+    args = (ctx.handle, _ptr(means), _ptr(scales), _ptr(quats), _ptr(opac), n, _ptr(lights), L, H, W,
             _ptr(radii), K, C.byref(p))
     rc = _lib.dgsm_bin(*args, None, None, 0, C.byref(total), _stream(stream))
     if rc not in (DGSM_OK, 3):

@@ -39,6 +39,9 @@ constexpr int BT_THREADS = 256;
 constexpr int BT_WARPS = BT_THREADS / 32;
 constexpr int QCAP = 64;       // per-warp queue of hits: (a, d'.w', |w' x d'|^2, record/texel id)
 constexpr int ITEM_CHUNKS = 16;  // a work item holds at most ITEM_CHUNKS * chunk Gaussians
+#ifndef DGSM_BT_MIN_BLOCKS
+#define DGSM_BT_MIN_BLOCKS 4        // resident build blocks per SM the register budget targets
+#endif
 
 // Per (light, Gaussian) record read by the build kernel (64 bytes):
 //   r0 = (M00 M01 M02 M10), r1 = (M11 M12 M20 M21), r2 = (M22 w'x w'y w'z),
@@ -49,11 +52,19 @@ struct __align__(16) BuildRec {
     float4 r0, r1, r2, r3;
 };
 
-// Per (light, Gaussian) binning record (32 bytes): a = (dir xyz, cos theta),
-// b = (sin theta, mode, -, -); mode 0 = not binned, 1 = cone test, 2 = all tiles.
+// Per (light, Gaussian) binning record (80 bytes): a = (dir xyz, cos theta),
+// b = (sin theta, mode, k2s, v.x), c = (v.y, v.z, c0.x, c0.y),
+// d = (c0.z, c1.x, c1.y, c1.z), e = (c2.x, c2.y, c2.z, -); mode 0 = not
+// binned, 1 = cone and ellipsoid tests, 2 = all tiles.  v = mu - o, c_k =
+// s_k times axis k of the Gaussian, k2s = k^2 (1 + 2^-10).
 struct __align__(16) BinRec {
-    float4 a, b;
+    float4 a, b, c, d, e;
 };
+
+// Gaussian index bits of a pair value; bits 30 and 31 hold the half-tile
+// mask (bit 30: the top half of the tile may be hit, bit 31: the bottom).
+constexpr uint32_t VAL_IDX = 0x3FFFFFFFu;
+constexpr int PLANE_F4 = 5;  // float4 per tile: top, bottom, left, right, mid planes
 
 struct __align__(16) Item {
     uint32_t key, start, end, n_items;
@@ -135,8 +146,106 @@ __device__ void rect_cone(int i0, int i1, int j0, int j1, int H, int W, float4 *
     }
 }
 
+__device__ __forceinline__ float3 xcross(float3 a, float3 b) {
+    return make_float3(xsub(xmul(a.y, b.z), xmul(a.z, b.y)), xsub(xmul(a.z, b.x), xmul(a.x, b.z)),
+                       xsub(xmul(a.x, b.y), xmul(a.y, b.x)));
+}
+
+// Octahedral face of an atlas point: bit 0 u >= 0, bit 1 v >= 0, bit 2 the
+// upper hemisphere (as xdecode decides it).
+__device__ __forceinline__ int xface(float u, float v) {
+    const float z = xsub(xsub(1.0f, fabsf(u)), fabsf(v));
+    return (u >= 0.0f ? 1 : 0) | (v >= 0.0f ? 2 : 0) | (z >= 0.0f ? 4 : 0);
+}
+
+// Plane through the light containing directions a and b, non-negative on c's side.
+__device__ __forceinline__ float3 xplane(float3 a, float3 b, float3 c) {
+    float3 n = xcross(a, b);
+    if (xdot(n.x, n.y, n.z, c.x, c.y, c.z) < 0.0f) n = make_float3(-n.x, -n.y, -n.z);
+    return n;
+}
+
+// Separating planes of the texel-centre rectangle [j0,j1) x [i0,i1) for the
+// ellipsoid test.  Inside one octahedral face the decode is affine in (u,v),
+// so atlas lines are great circles and the rays through the rectangle's texel
+// centres lie in the polyhedral cone of its corner directions.
+// out[0] = (top edge plane, valid), out[1] = (bottom edge plane, has bottom
+// half), out[2] = left, out[3] = right, out[4] = plane between the halves
+// (rows [i0, i0+half) above, non-negative on their side).  valid = 0 when the
+// rectangle spans two faces or is a single row or column (no plane test).
+__device__ void rect_planes(int i0, int i1, int j0, int j1, int half, int H, int W, float4 *out) {
+    const float ua = xcentre(j0, W), ub = xcentre(j1 - 1, W);
+    const float va = xcentre(i0, H), vb = xcentre(i1 - 1, H);
+    const float hb = i1 - i0 > half ? 1.0f : 0.0f;
+    for (int q = 0; q < PLANE_F4; ++q) out[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    out[1].w = hb;
+    const int f = xface(ua, va);
+    if (!(ua < ub && va < vb) || xface(ub, va) != f || xface(ua, vb) != f || xface(ub, vb) != f) return;
+    const float uc = xmul(xadd(ua, ub), 0.5f), vc = xmul(xadd(va, vb), 0.5f);
+    const float3 c = xdecode(uc, vc);
+    const float3 d00 = xdecode(ua, va), d01 = xdecode(ub, va), d10 = xdecode(ua, vb), d11 = xdecode(ub, vb);
+    const float3 top = xplane(d00, d01, c), bot = xplane(d10, d11, c);
+    const float3 left = xplane(d00, d10, c), right = xplane(d01, d11, c);
+    out[0] = make_float4(top.x, top.y, top.z, 1.0f);
+    out[1] = make_float4(bot.x, bot.y, bot.z, hb);
+    out[2] = make_float4(left.x, left.y, left.z, 0.0f);
+    out[3] = make_float4(right.x, right.y, right.z, 0.0f);
+    if (hb != 0.0f) {
+        const float vm = xsub(xdiv((float)(2 * (i0 + half)), (float)H), 1.0f);
+        const float3 mid = xplane(xdecode(ua, vm), xdecode(ub, vm), xdecode(uc, va));
+        out[4] = make_float4(mid.x, mid.y, mid.z, 0.0f);
+    }
+}
+
+// The ellipsoid test of a Gaussian (axes ax: v, c0, c1, c2) against one
+// plane: does its culling ellipsoid reach the plane's non-negative side?
+// Support n.v + k |(c_k . n)_k| compared in squares when n.v < 0.
+struct GAxes {
+    float v[3], c[9], k2s;
+};
+
+__device__ __forceinline__ void plane_terms(const float4 &n, const GAxes &g, float &nv, float &reach) {
+    nv = xdot(n.x, n.y, n.z, g.v[0], g.v[1], g.v[2]);
+    const float p0 = xdot(n.x, n.y, n.z, g.c[0], g.c[1], g.c[2]);
+    const float p1 = xdot(n.x, n.y, n.z, g.c[3], g.c[4], g.c[5]);
+    const float p2 = xdot(n.x, n.y, n.z, g.c[6], g.c[7], g.c[8]);
+    const float ss = xadd(xadd(xmul(p0, p0), xmul(p1, p1)), xmul(p2, p2));
+    reach = (xmul(nv, nv) <= xmul(g.k2s, ss)) ? 1.0f : 0.0f;
+}
+
+__device__ __forceinline__ bool plane_ok(const float4 &n, const GAxes &g) {
+    const float nv = xdot(n.x, n.y, n.z, g.v[0], g.v[1], g.v[2]);
+    if (nv >= 0.0f) return true;
+    float nv2, reach;
+    plane_terms(n, g, nv2, reach);
+    return reach != 0.0f;
+}
+
+// Half-tile mask of a (Gaussian, tile) pair whose cones overlap: bit 0 the
+// top half may be hit, bit 1 the bottom half; 0 = the tile is not reached.
+__device__ __forceinline__ uint32_t half_mask(const float4 *pl, const GAxes &g, bool inside) {
+    const float4 p1 = pl[1];
+    const uint32_t hb = p1.w != 0.0f ? 2u : 0u;
+    const float4 p0 = pl[0];
+    if (inside || p0.w == 0.0f) return 1u | hb;
+    if (!plane_ok(pl[2], g) || !plane_ok(pl[3], g)) return 0u;
+    if (!hb) return plane_ok(p0, g) ? 1u : 0u;
+    bool mid_pos = true, mid_neg = true;
+    const float4 pm = pl[4];
+    float nv, reach;
+    plane_terms(pm, g, nv, reach);
+    if (nv != 0.0f) {
+        mid_pos = nv > 0.0f || reach != 0.0f;
+        mid_neg = nv < 0.0f || reach != 0.0f;
+    }
+    uint32_t m = 0u;
+    if (mid_pos && plane_ok(p0, g)) m |= 1u;
+    if (mid_neg && plane_ok(p1, g)) m |= 2u;
+    return m;
+}
+
 // cones: [0, n_tiles) tiles, then [n_tiles, n_tiles + n_super) super-tiles;
-// two float4 per cone.
+// two float4 per cone; then the tiles' planes, PLANE_F4 float4 each.
 __global__ void rect_cones_kernel(int H, int W, int tile, int tx, int ty, int sx, int sy,
                                   float4 *__restrict__ cones) {
     const int n_tiles = tx * ty, n_super = sx * sy;
@@ -154,6 +263,9 @@ __global__ void rect_cones_kernel(int H, int W, int tile, int tx, int ty, int sx
     }
     const int i0 = a * edge, j0 = b * edge;
     rect_cone(i0, min(i0 + edge, H), j0, min(j0 + edge, W), H, W, cones + 2 * idx);
+    if (idx < n_tiles)
+        rect_planes(i0, min(i0 + edge, H), j0, min(j0 + edge, W), tile / 2, H, W,
+                    cones + 2 * (n_tiles + n_super) + PLANE_F4 * idx);
 }
 
 // ---------------------------------------------------------------------------
@@ -164,6 +276,7 @@ __global__ void __launch_bounds__(256) prep_kernel(
     const float *__restrict__ quats, const float *__restrict__ opac, int64_t N,
     const float *__restrict__ lights, int L, const float *__restrict__ radii, int K, float kappa,
     float eps, BuildRec *__restrict__ brec, BinRec *__restrict__ bin, int *__restrict__ status) {
+    // brec == nullptr: binning only (no build record)
     const int64_t total = (int64_t)L * N;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -171,17 +284,14 @@ __global__ void __launch_bounds__(256) prep_kernel(
         const int64_t g = idx - (int64_t)l * N;
         const float mx = means[3 * g], my = means[3 * g + 1], mz = means[3 * g + 2];
         const float s0 = scales[3 * g], s1 = scales[3 * g + 1], s2 = scales[3 * g + 2];
-        // quats == nullptr: binning only (no build record)
-        float qw = 1.f, qx = 0.f, qy = 0.f, qz = 0.f;
-        if (quats) {
-            qw = quats[4 * g]; qx = quats[4 * g + 1]; qy = quats[4 * g + 2]; qz = quats[4 * g + 3];
-        }
+        float qw = quats[4 * g], qx = quats[4 * g + 1], qy = quats[4 * g + 2], qz = quats[4 * g + 3];
         const float alpha = opac[g];
         const float ox = lights[3 * l], oy = lights[3 * l + 1], oz = lights[3 * l + 2];
 
         BinRec br;
         br.a = make_float4(0.f, 0.f, 1.f, -1.f);
         br.b = make_float4(0.f, 0.f, 0.f, 0.f);  // mode 0: not binned
+        br.c = br.d = br.e = make_float4(0.f, 0.f, 0.f, 0.f);
         const bool finite = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(s0) &&
                             isfinite(s1) && isfinite(s2) && isfinite(qw) && isfinite(qx) &&
                             isfinite(qy) && isfinite(qz) && isfinite(alpha) && s0 > 0.f &&
@@ -224,8 +334,27 @@ __global__ void __launch_bounds__(256) prep_kernel(
             br.a = make_float4(xdiv(vx, dist), xdiv(vy, dist), xdiv(vz, dist), cs);
             br.b = make_float4(sn, 1.f, 0.f, 0.f);
         }
+        {
+            // axes of the culling ellipsoid (binning specification, exact ops)
+            const float n = xsqrt(xadd(xadd(xadd(xmul(qw, qw), xmul(qx, qx)), xmul(qy, qy)), xmul(qz, qz)));
+            const float w = xdiv(qw, n), x = xdiv(qx, n), y = xdiv(qy, n), z = xdiv(qz, n);
+            const float pxx = xmul(x, x), pyy = xmul(y, y), pzz = xmul(z, z);
+            const float pxy = xmul(x, y), pxz = xmul(x, z), pyz = xmul(y, z);
+            const float pwx = xmul(w, x), pwy = xmul(w, y), pwz = xmul(w, z);
+            const float r00 = xsub(1.0f, xmul(2.0f, xadd(pyy, pzz)));
+            const float r11 = xsub(1.0f, xmul(2.0f, xadd(pxx, pzz)));
+            const float r22 = xsub(1.0f, xmul(2.0f, xadd(pxx, pyy)));
+            const float r01 = xmul(2.0f, xsub(pxy, pwz)), r10 = xmul(2.0f, xadd(pxy, pwz));
+            const float r02 = xmul(2.0f, xadd(pxz, pwy)), r20 = xmul(2.0f, xsub(pxz, pwy));
+            const float r12 = xmul(2.0f, xsub(pyz, pwx)), r21 = xmul(2.0f, xadd(pyz, pwx));
+            br.b.z = xmul(k2, 1.0009765625f);
+            br.b.w = vx;
+            br.c = make_float4(vy, vz, xmul(r00, s0), xmul(r10, s0));
+            br.d = make_float4(xmul(r20, s0), xmul(r01, s1), xmul(r11, s1), xmul(r21, s1));
+            br.e = make_float4(xmul(r02, s2), xmul(r12, s2), xmul(r22, s2), 0.f);
+        }
         bin[idx] = br;
-        if (!quats) continue;
+        if (!brec) continue;
 
         // --- build record (ordinary single precision) ---
         const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
@@ -275,9 +404,11 @@ __device__ __forceinline__ bool cone_overlap(const BinRec &g, const float4 *cone
 }
 
 // Count (EMIT = false) or write (EMIT = true) the tiles each Gaussian
-// overlaps.  One warp per (light, Gaussian): 32 super-tile tests at a time,
-// then the 64 tiles of every overlapped super-tile, 32 at a time; the pairs
-// of one Gaussian are written contiguously from its scanned offset.
+// reaches.  One warp per (light, Gaussian): 32 super-tile cone tests at a
+// time, then the 64 tiles of every overlapped super-tile, 32 at a time (cone
+// test, then the ellipsoid test against the tile's planes, which also gives
+// the half-tile mask); the pairs of one Gaussian are written contiguously
+// from its scanned offset.
 template <bool EMIT>
 __global__ void __launch_bounds__(256) bin_kernel(
     const BinRec *__restrict__ bin, int64_t N, int L, int tx, int ty, int sx, int sy,
@@ -289,6 +420,7 @@ __global__ void __launch_bounds__(256) bin_kernel(
     const int64_t total = (int64_t)L * N;
     const int n_tiles = tx * ty, n_super = sx * sy;
     const float4 *scones = cones + 2 * n_tiles;
+    const float4 *planes = cones + 2 * (n_tiles + n_super);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -305,11 +437,18 @@ __global__ void __launch_bounds__(256) bin_kernel(
             if (EMIT)
                 for (int t = lane; t < n_tiles; t += 32) {
                     if (off + t >= cap) break;
+                    const uint32_t m = planes[PLANE_F4 * t + 1].w != 0.0f ? 3u : 1u;
                     keys[off + t] = kbase + t;
-                    vals[off + t] = gi;
+                    vals[off + t] = gi | (m << 30);
                 }
             c = n_tiles;
         } else if (mode == 1) {
+            GAxes ga;
+            ga.v[0] = g.b.w; ga.v[1] = g.c.x; ga.v[2] = g.c.y;
+            ga.c[0] = g.c.z; ga.c[1] = g.c.w; ga.c[2] = g.d.x;
+            ga.c[3] = g.d.y; ga.c[4] = g.d.z; ga.c[5] = g.d.w;
+            ga.c[6] = g.e.x; ga.c[7] = g.e.y; ga.c[8] = g.e.z;
+            ga.k2s = g.b.z;
             for (int sb = 0; sb < n_super; sb += 32) {
                 const int s = sb + lane;
                 unsigned m = __ballot_sync(0xffffffffu, s < n_super && cone_overlap(g, scones + 2 * s));
@@ -322,13 +461,15 @@ __global__ void __launch_bounds__(256) bin_kernel(
                         const int local = rnd * 32 + lane;
                         const int a = sa * SUPER + local / SUPER, b = sbb * SUPER + local % SUPER;
                         const int t = a * tx + b;
-                        const bool ov = a < ty && b < tx && cone_overlap(g, cones + 2 * t);
-                        const unsigned m2 = __ballot_sync(0xffffffffu, ov);
-                        if (EMIT && ov) {
+                        uint32_t hm = 0u;
+                        if (a < ty && b < tx && cone_overlap(g, cones + 2 * t))
+                            hm = half_mask(planes + PLANE_F4 * t, ga, false);
+                        const unsigned m2 = __ballot_sync(0xffffffffu, hm != 0u);
+                        if (EMIT && hm != 0u) {
                             const uint32_t pos = off + c + __popc(m2 & lt);
                             if (pos < cap) {
                                 keys[pos] = kbase + t;
-                                vals[pos] = gi;
+                                vals[pos] = gi | (hm << 30);
                             }
                         }
                         c += __popc(m2);
@@ -495,7 +636,7 @@ size_t build_smem_bytes(int K, int tile, int chunk) {
     const int nt = tile * tile;
     return (size_t)2 * chunk * REC_F4 * sizeof(float4) + (size_t)nt * sizeof(float4) +
            (size_t)K * nt * sizeof(float) + (size_t)((K + 3) & ~3) * sizeof(float) +
-           (size_t)BT_WARPS * QCAP * sizeof(float4);
+           (size_t)BT_WARPS * QCAP * sizeof(float4) + (size_t)2 * chunk;
 }
 
 // Persistent build kernel, 8 warps per block.  A warp owns 64 texels (two per
@@ -503,9 +644,12 @@ size_t build_smem_bytes(int K, int tile, int chunk) {
 // 4 texel groups of 2 warps.  The records of a staged chunk are handed out one
 // at a time to the warps of each texel group; a warp tests its texels against
 // the record (broadcast from shared memory) and queues the hits with their
-// geometry; 32 queued hits at a time are then evaluated lane-parallel.
+// geometry; 32 queued hits at a time are then evaluated lane-parallel.  Each
+// pair carries the binning's half-tile mask: a warp's 32 "A" texels and its
+// 32 "B" texels each lie in one half of the tile, and a half the mask
+// excludes is not tested.
 template <typename OutT>
-__global__ void __launch_bounds__(BT_THREADS, 5) build_items_kernel(
+__global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_kernel(
     const float4 *__restrict__ brec, const uint32_t *__restrict__ vals,
     const Item *__restrict__ items, const unsigned long long *__restrict__ n_items_total,
     unsigned int *__restrict__ item_counter, const float *__restrict__ radii, int K, int H, int W,
@@ -520,6 +664,7 @@ __global__ void __launch_bounds__(BT_THREADS, 5) build_items_kernel(
     float *D = reinterpret_cast<float *>(tdir + nt);         // [K][nt]
     float *rs = D + K * nt;                                  // [K]
     float4 *queue = reinterpret_cast<float4 *>(rs + ((K + 3) & ~3));  // [BT_WARPS][QCAP]
+    uint8_t *smask = reinterpret_cast<uint8_t *>(queue + BT_WARPS * QCAP);  // [2][chunk]
     __shared__ uint4 s_item;
     __shared__ int s_last;
     __shared__ int s_next[BT_WARPS];
@@ -528,6 +673,10 @@ __global__ void __launch_bounds__(BT_THREADS, 5) build_items_kernel(
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tg = warp % n_tg;
     const unsigned lt = (1u << lane) - 1u;
+    // half-tile bit of this warp's A texels and of its B texels
+    const uint32_t bitA = (tg * 64) / tile >= tile / 2 ? 2u : 1u;
+    const uint32_t bitB = (tg * 64 + 32) / tile >= tile / 2 ? 2u : 1u;
+    unsigned int n_tst = 0;
     const int64_t HW = (int64_t)H * W;
     const unsigned long long total_items = *n_items_total;
     for (int k = tid; k < K; k += BT_THREADS) rs[k] = radii[k];
@@ -579,7 +728,10 @@ __global__ void __launch_bounds__(BT_THREADS, 5) build_items_kernel(
 #pragma unroll
             for (int hh = 0; hh < 3; ++hh) {
                 const int e = tid + hh * BT_THREADS;
-                if (e < cnt * REC_F4) cp_async16(dst + e, src + (int64_t)g[hh] * REC_F4 + e % REC_F4);
+                if (e < cnt * REC_F4) {
+                    cp_async16(dst + e, src + (int64_t)(g[hh] & VAL_IDX) * REC_F4 + e % REC_F4);
+                    if (e % REC_F4 == 0) smask[(c & 1) * chunk + e / REC_F4] = (uint8_t)(g[hh] >> 30);
+                }
             }
             cp_async_commit();
         };
@@ -617,6 +769,7 @@ __global__ void __launch_bounds__(BT_THREADS, 5) build_items_kernel(
                     gg.c2 = e.z;
                     eval_shells(gg, st[(id >> 6) * REC_F4 + 3], rs, K, D, nt, tex, n_shell);
                 }
+                if (lane == 0) n_hit += (unsigned)n;
                 qn -= n;
                 __syncwarp();
             };
@@ -627,29 +780,31 @@ __global__ void __launch_bounds__(BT_THREADS, 5) build_items_kernel(
                 if (qn >= 32) flush(32);
             };
             // records are handed out dynamically to the warps of a texel group
+            const uint8_t *cmask = smask + (c & 1) * chunk;
             for (;;) {
                 int r = 0;
                 if (lane == 0) r = atomicAdd(&s_next[tg], 1);
                 r = __shfl_sync(0xffffffffu, r, 0);
                 if (r >= cnt) break;
+                const uint32_t hm = cmask[r];
+                const bool doA = (hm & bitA) != 0u, doB = (hm & bitB) != 0u;
+                if (!doA && !doB) continue;
                 const float4 q0 = st[r * REC_F4], q1 = st[r * REC_F4 + 1], q2 = st[r * REC_F4 + 2],
                              q3 = st[r * REC_F4 + 3];
                 const bool inside = (__float_as_int(q3.z) >> 20) & 1;
-                const PairGeom gA = pair_geom(q0, q1, q2, dA.x, dA.y, dA.z);
-                const PairGeom gB = pair_geom(q0, q1, q2, dB.x, dB.y, dB.z);
-                const bool hA = vA && pair_hit(gA, q3.y, inside);
-                const bool hB = vB && pair_hit(gB, q3.y, inside);
-                n_hit += (unsigned)hA + (unsigned)hB;
-                push(hA, gA, (r << 6) | lane);
-                push(hB, gB, (r << 6) | (32 + lane));
+                if (doA) {
+                    const PairGeom gA = pair_geom(q0, q1, q2, dA.x, dA.y, dA.z);
+                    push(vA && pair_hit(gA, q3.y, inside), gA, (r << 6) | lane);
+                    n_tst += vA;
+                }
+                if (doB) {
+                    const PairGeom gB = pair_geom(q0, q1, q2, dB.x, dB.y, dB.z);
+                    push(vB && pair_hit(gB, q3.y, inside), gB, (r << 6) | (32 + lane));
+                    n_tst += vB;
+                }
             }
             if (qn > 0) flush(qn);
             __syncthreads();  // the buffer is refilled two chunks later
-        }
-        if (tid == 0) {
-            const int nvalid = (min(tile_i * tile + tile, H) - tile_i * tile) *
-                               (min(tile_j * tile + tile, W) - tile_j * tile);
-            n_tested += (unsigned long long)nvalid * (unsigned long long)nrec;
         }
         // ---- finalize: prefix over shells, T = exp(-tau) (Eq. 4) ----
         if (n_items == 1) {
@@ -699,6 +854,7 @@ __global__ void __launch_bounds__(BT_THREADS, 5) build_items_kernel(
         __syncthreads();  // shared state is reused by the next item
     }
     if (stats) {
+        n_tested = n_tst;
         if (n_tested) atomicAdd(&s_cnt[0], n_tested);
         if (n_hit) atomicAdd(&s_cnt[1], n_hit);
         if (n_shell) atomicAdd(&s_cnt[2], n_shell);
@@ -741,7 +897,7 @@ int check_common(dgsm_ctx *ctx, const float *means, const float *scales, const f
     if (n < 0) return fail(ctx, DGSM_ERR_INVALID_ARG, "n < 0");
     if (n > 0 && (!means || !scales || !opac))
         return fail(ctx, DGSM_ERR_INVALID_ARG, "null Gaussian array");
-    if (n >= (int64_t)1 << 31) return fail(ctx, DGSM_ERR_INVALID_ARG, "n >= 2^31");
+    if (n >= (int64_t)1 << 30) return fail(ctx, DGSM_ERR_INVALID_ARG, "n >= 2^30");
     if (!lights || L < 1 || L > 64) return fail(ctx, DGSM_ERR_INVALID_ARG, "need 1..64 lights");
     if (H < 1 || W < 1 || H > 4096 || W > 4096) return fail(ctx, DGSM_ERR_INVALID_ARG, "H, W must be in 1..4096");
     if (!radii || K < 1 || K > 256) return fail(ctx, DGSM_ERR_INVALID_ARG, "K must be in 1..256");
@@ -756,7 +912,8 @@ int check_common(dgsm_ctx *ctx, const float *means, const float *scales, const f
 // the buffers hold max_pairs and the count stays on the device.
 int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
                 const float *opac, int64_t N, const float *lights, int L, int H, int W,
-                const float *radii, int K, const dgsm_params &p, cudaStream_t s, BinOut *out) {
+                const float *radii, int K, const dgsm_params &p, bool build_records, cudaStream_t s,
+                BinOut *out) {
     const int tile = p.tile;
     const int tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
     const int sx = (tx + SUPER - 1) / SUPER, sy = (ty + SUPER - 1) / SUPER;
@@ -766,10 +923,13 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     const int64_t nkeys = (int64_t)L * n_tiles;
     void *w_br, *w_bin, *w_cnt, *w_cones, *w_rng;
     int rc;
-    if ((rc = ws_reserve(ctx, WS_BUILD_REC, sizeof(BuildRec) * (size_t)LN, &w_br))) return rc;
+    if ((rc = ws_reserve(ctx, WS_BUILD_REC, build_records ? sizeof(BuildRec) * (size_t)LN : 256, &w_br)))
+        return rc;
     if ((rc = ws_reserve(ctx, WS_BIN_REC, sizeof(BinRec) * (size_t)LN, &w_bin))) return rc;
     if ((rc = ws_reserve(ctx, WS_COUNTS, sizeof(uint32_t) * (size_t)LN, &w_cnt))) return rc;
-    if ((rc = ws_reserve(ctx, WS_CONES, 2 * sizeof(float4) * (size_t)(n_tiles + sx * sy), &w_cones))) return rc;
+    if ((rc = ws_reserve(ctx, WS_CONES, sizeof(float4) * (size_t)(2 * (n_tiles + sx * sy) + PLANE_F4 * n_tiles),
+                         &w_cones)))
+        return rc;
     if ((rc = ws_reserve(ctx, WS_RANGES, 2 * sizeof(uint32_t) * (size_t)nkeys, &w_rng))) return rc;
     out->brec = (BuildRec *)w_br;
     out->ts = (uint32_t *)w_rng;
@@ -784,7 +944,8 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     rect_cones_kernel<<<(nc + 127) / 128, 128, 0, s>>>(H, W, tile, tx, ty, sx, sy, (float4 *)w_cones);
     const int grid = (int)std::min<int64_t>((LN + 255) / 256, (int64_t)ctx->num_sms * 16);
     prep_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, N, lights, L, radii, K, p.kappa,
-                                     p.eps_cull, (BuildRec *)w_br, (BinRec *)w_bin, ctx->d_status);
+                                     p.eps_cull, build_records ? (BuildRec *)w_br : nullptr,
+                                     (BinRec *)w_bin, ctx->d_status);
     const int wgrid = (int)std::min<int64_t>((LN * 32 + 255) / 256, (int64_t)ctx->num_sms * 16);
     bin_kernel<false><<<wgrid, 256, 0, s>>>((const BinRec *)w_bin, N, L, tx, ty, sx, sy,
                                              (const float4 *)w_cones, (uint32_t *)w_cnt, nullptr,
@@ -876,7 +1037,7 @@ extern "C" int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales
     cudaEvent_t *ev = prof ? ctx->prof_ev[ctx->prof_count] : nullptr;
     if (prof) cudaEventRecord(ev[0], s);
     BinOut b;
-    if ((rc = run_binning(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, s, &b)))
+    if ((rc = run_binning(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, true, s, &b)))
         return rc;
 
     // ---- work items: every tile's list cut into pieces of <= item Gaussians ----
@@ -950,9 +1111,9 @@ extern "C" int dgsm_get_build_stats(dgsm_ctx *ctx, dgsm_build_stats *out) {
     return DGSM_OK;
 }
 
-extern "C" int dgsm_bin(dgsm_ctx *ctx, const float *means, const float *scales, const float *opac,
-                        int64_t n, const float *lights, int32_t L, int32_t H, int32_t W,
-                        const float *radii, int32_t K, const dgsm_params *params,
+extern "C" int dgsm_bin(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
+                        const float *opac, int64_t n, const float *lights, int32_t L, int32_t H,
+                        int32_t W, const float *radii, int32_t K, const dgsm_params *params,
                         uint32_t *keys_out, uint32_t *vals_out, int64_t capacity,
                         int64_t *n_pairs_out, void *stream) {
     if (!ctx || !n_pairs_out) return DGSM_ERR_INVALID_ARG;
@@ -963,12 +1124,12 @@ extern "C" int dgsm_bin(dgsm_ctx *ctx, const float *means, const float *scales, 
     if (rc) return rc;
     if (capacity < 0 || (capacity > 0 && (!keys_out || !vals_out)))
         return fail(ctx, DGSM_ERR_INVALID_ARG, "bad output capacity or pointers");
+    if (n > 0 && !quats) return fail(ctx, DGSM_ERR_INVALID_ARG, "null quats");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
-    // binning never reads the quaternions (quats = nullptr skips the build records)
     BinOut b;
-    if ((rc = run_binning(ctx, means, scales, nullptr, opac, n, lights, L, H, W, radii, K, p, s, &b)))
+    if ((rc = run_binning(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, false, s, &b)))
         return rc;
     *n_pairs_out = b.P;
     if (b.P > capacity) return fail(ctx, DGSM_ERR_WORKSPACE, "capacity smaller than the pair count");

@@ -9,6 +9,13 @@
              3M Gaussians: |dT| p50/p99 against the exact atlas lookup, with
              and without the per-tile exact fallback, memory footprint,
              Gaussians/s, and an atlas of the same memory as the weights.
+  frame      the moving-avatar workload (1.5M static Gaussians with 4-light
+             512x512x64 atlases built once, 8 avatars of 100k walking for
+             120 frames, 256x256x32 dynamic atlases per frame, 2.3M
+             attenuated, 800k relit): autotuned tile x chunk of the dynamic
+             build, then ms per frame for direct calls with the blocking
+             build, direct calls with the capacity build, and graph replay,
+             with a per-stage breakdown.
 
 Comparisons against the FP64 oracle live in the test suite.
 """
@@ -136,6 +143,89 @@ def surrogate(steps: int = 3000, batch: int = 16384, n_query: int = 3_000_000, t
     }
 
 
+def frame(frames: int = 120) -> dict:
+    import torch
+
+    from paper_2601_01660_b300 import native, scenes
+    from paper_2601_01660_b300.frame import CrowdFrame
+    nat = native()
+    wl = scenes.workload("crowd8")
+    D, Y, w = wl["cubemap"]
+    sh = nat.sh_fit(_dev(D, torch), _dev(Y, torch), _dev(w, torch))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cf = CrowdFrame(wl["static"], wl["avatars"], wl["seg"], wl["lights"], wl["H"], wl["W"], wl["radii"],
+                    wl["H_dyn"], wl["W_dyn"], wl["radii_dyn"], sh)
+    t_static = time.perf_counter() - t0
+    mo = wl["motion"]
+    poses = [scenes.avatar_poses(mo, f) for f in range(frames)]
+    (tile, chunk), table = cf.autotune(poses[0])
+    cf.size_pairs(poses[::10])
+    s = cf.stream
+
+    def run(step, n):
+        s.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t = time.perf_counter()
+        e0.record(s)
+        for f in range(n):
+            step(poses[f % frames])
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / n, (time.perf_counter() - t) * 1e3 / n
+
+    for _ in range(3):
+        cf.step_eager(poses[0])
+    ms_sync, wall_sync = run(lambda p: cf.step_eager(p), frames)
+    ms_cap, wall_cap = run(lambda p: cf.step_eager(p, max_pairs=cf.max_pairs), frames)
+    nodes = cf.capture()
+    for _ in range(3):
+        cf.step_graph(poses[0])
+    ms_graph, wall_graph = run(cf.step_graph, frames)
+    status = nat.dgsm_sync_status(cf.ctx, stream=s)
+    # per-stage times of one frame (capacity build, direct calls)
+    k = cf._write_poses(poses[7])
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    ev[0].record(s)
+    nat.dgsm_rigid_transform(cf.rest_means, cf.rest_quats, cf.seg, cf.poses[k], means_out=cf.av_means,
+                             quats_out=cf.av_quats, ctx=cf.ctx, stream=s)
+    ev[1].record(s)
+    nat.dgsm_build(cf.av_means, cf.av_scales, cf.av_quats, cf.av_opac, cf.lights, cf.H_dyn, cf.W_dyn,
+                   cf.radii_dyn, params=dict(cf.bp, max_pairs=cf.max_pairs), out=cf.dyn_atlas, ctx=cf.ctx,
+                   stream=s)
+    ev[2].record(s)
+    nat.dgsm_attenuate_dyn(cf.static_atlas, cf.radii, cf.dyn_atlas, cf.radii_dyn, cf.lights, cf.q_means,
+                           cf.colors_in, out=cf.colors_out, ctx=cf.ctx, stream=s)
+    ev[3].record(s)
+    nat.dgsm_segment_centroids(cf.av_means, cf.av_opac, cf.seg, out=cf.centroids, ctx=cf.ctx, stream=s)
+    ev[4].record(s)
+    av_out = cf.colors_out[cf.n_static:]
+    nat.sh_relight_objects(cf.sh, cf.av_means, cf.av_quats, cf.av_scales, av_out, cf.centroids, cf.seg,
+                           out=av_out, ctx=cf.ctx, stream=s)
+    ev[5].record(s)
+    cf._frame_done(k)
+    ev[5].synchronize()
+    stats = nat.dgsm_get_build_stats(cf.ctx)
+    names = ["rigid_transform", "dynamic_build", "attenuate_static_x_dynamic", "centroids", "relight"]
+    stages = {nm: ev[i].elapsed_time(ev[i + 1]) for i, nm in enumerate(names)}
+    cf.close()
+    return {
+        "report": "frame",
+        "workload": "crowd8: 1.5M static + 8 x 100k avatars, 4 lights; static 512x512x64 (built once), "
+                    "dynamic 256x256x32 per frame; 2.3M attenuated, 800k relit",
+        "frames": frames, "static_build_s": round(t_static, 3),
+        "autotune_ms": {f"tile{t}_chunk{c}": round(v, 3) for (t, c), v in table.items()},
+        "chosen": {"tile": tile, "chunk": chunk}, "max_pairs": cf.max_pairs,
+        "dynamic_build_pairs": stats["n_pairs"], "dynamic_ray_evals": stats["ray_evals"],
+        "ms_per_frame": {"direct_blocking_build": round(ms_sync, 3), "direct_capacity_build": round(ms_cap, 3),
+                         "graph_replay": round(ms_graph, 3)},
+        "host_ms_per_frame": {"direct_blocking_build": round(wall_sync, 3),
+                              "direct_capacity_build": round(wall_cap, 3), "graph_replay": round(wall_graph, 3)},
+        "graph_nodes_per_frame": nodes, "status_after_replay": status,
+        "stage_ms": {k2: round(v, 4) for k2, v in stages.items()},
+    }
+
+
 def main(which: str) -> None:
-    fn = {"precision": precision, "surrogate": surrogate}[which]
+    fn = {"precision": precision, "surrogate": surrogate, "frame": frame}[which]
     print(json.dumps(fn()), flush=True)

@@ -34,12 +34,16 @@ def _build(nat, sc, lights, H, W, radii, **params):
 @pytest.mark.parametrize("H,W,tile,nl", [(32, 32, 8, 1), (44, 60, 8, 2), (64, 48, 16, 1),
                                          (40, 40, 4, 3), (128, 128, 8, 1)])
 def test_binning_bit_exact(nat, orc, H, W, tile, nl):
-    sc = scenes.cube_scene(2500, seed=31 + H, log_s_mean=math.log(0.06))
+    rng = np.random.default_rng(H)
+    cube = scenes.cube_scene(2500, seed=31 + H, log_s_mean=math.log(0.06))
+    flat = scenes.cube_scene(1500, seed=32 + H, log_s_mean=math.log(0.1))
+    flat.scales[np.arange(flat.n), rng.integers(0, 3, flat.n)] = 0.002   # 2 mm thick discs
+    sc = scenes.concat(cube, flat, scenes.avatar_body(rng, 1000, base=(0.3, 0.2, 1.5)))
     lights = np.float32([[0, 0, 0], [0.4, -0.3, 0.5], [-1, 1, 2.5]])[:nl]
     radii = scenes.radii_linear(0.1, 8, 10)
     ko, vo = orc.f32_bin(sc, lights, H, W, radii, eps=1e-7, tile=tile)
     d = scene_to_dev(sc)
-    kg, vg = nat.dgsm_bin(d["means"], d["scales"], d["opac"], dev(lights), H, W, dev(radii),
+    kg, vg = nat.dgsm_bin(d["means"], d["scales"], d["quats"], d["opac"], dev(lights), H, W, dev(radii),
                           params=dict(tile=tile))
     assert kg.numel() == ko.size
     assert np.array_equal(kg.cpu().numpy().astype(np.uint32), ko)
@@ -54,7 +58,7 @@ def test_binning_light_inside_and_beyond_shells(nat, orc):
     radii = scenes.radii_linear(0.1, 3.0, 6)
     ko, vo = orc.f32_bin(sc, lights, 24, 24, radii)
     d = scene_to_dev(sc)
-    kg, vg = nat.dgsm_bin(d["means"], d["scales"], d["opac"], dev(lights), 24, 24, dev(radii))
+    kg, vg = nat.dgsm_bin(d["means"], d["scales"], d["quats"], d["opac"], dev(lights), 24, 24, dev(radii))
     assert np.array_equal(kg.cpu().numpy().astype(np.uint32), ko)
     assert np.array_equal(vg.cpu().numpy().astype(np.uint32), vo)
 

@@ -131,9 +131,13 @@ def test_cull_radius_bounds_missed_optical_depth(orc):
             assert tau <= eps * 1.0001
 
 
+IDX = 0x3FFFFFFF   # Gaussian index bits of a pair value; bits 30, 31: half-tile mask
+
+
 def _brute_lists(orc, sc, o, H, W, tile, radii, eps):
-    """Which (tile, Gaussian) pairs must be binned: some texel ray of the tile
-    cuts the Gaussian's k-ellipsoid at t > 0 within the shells."""
+    """Which (tile, Gaussian, half) triples must be binned: some texel ray of
+    the tile's half (rows [0, tile/2) or [tile/2, tile)) cuts the Gaussian's
+    k-ellipsoid at t > 0 within the shells (FP64)."""
     ty, tx = -(-H // tile), -(-W // tile)
     need = set()
     dirs = np.array([[orc.texel_dir(i, j, H, W) for j in range(W)] for i in range(H)])
@@ -152,28 +156,100 @@ def _brute_lists(orc, sc, o, H, W, tile, radii, eps):
         m2 = c - b * b / a
         hit = (m2 <= k2) & (-b / a > 0)
         for i, j in zip(*np.nonzero(hit)):
-            need.add(((i // tile) * tx + (j // tile), g))
+            need.add(((i // tile) * tx + (j // tile), g, int(i % tile >= tile // 2)))
     return need
 
 
-@pytest.mark.parametrize("H,W,tile", [(32, 32, 8), (40, 56, 8), (64, 64, 16)])
+def _scene_with_flat_and_tiny(seed):
+    """Anisotropic cube Gaussians, flat surface Gaussians (2 mm thick) and
+    tiny avatar Gaussians: the shapes the ellipsoid test must bound."""
+    rng = np.random.default_rng(seed)
+    a = scenes.cube_scene(90, seed=seed, log_s_mean=math.log(0.08))
+    f = scenes.cube_scene(90, seed=seed + 1, log_s_mean=math.log(0.15))
+    f.scales[:, rng.integers(0, 3, f.n)] = 0.002
+    f.scales[np.arange(f.n), rng.integers(0, 3, f.n)] = 0.002
+    t = scenes.avatar_body(rng, 60, base=(0.0, 0.5, 1.0))
+    return scenes.concat(a, f, t)
+
+
+@pytest.mark.parametrize("H,W,tile", [(32, 32, 8), (40, 56, 8), (44, 40, 8), (64, 64, 16), (36, 28, 4)])
 def test_binning_is_conservative(orc, H, W, tile):
-    sc = scenes.cube_scene(150, seed=14, log_s_mean=math.log(0.08))
+    sc = _scene_with_flat_and_tiny(14)
     o = np.float32([0.1, -0.1, 0.2])
     radii = scenes.radii_linear(0.1, 8, 8)
     keys, vals = orc.f32_bin(sc, o[None], H, W, radii, eps=1e-7, tile=tile)
-    got = set(zip(keys.tolist(), vals.tolist()))
+    got = set()
+    for k, v in zip(keys.tolist(), vals.tolist()):
+        for h in (0, 1):
+            if (v >> (30 + h)) & 1:
+                got.add((k, v & IDX, h))
     need = _brute_lists(orc, sc, o, H, W, tile, radii, 1e-7)
-    assert need <= got
-    # the lists come out ordered by (key, Gaussian index)
-    order = np.lexsort((vals, keys))
+    assert need <= got, sorted(need - got)[:5]
+    # the lists come out ordered by (key, Gaussian index); every pair has a half
+    order = np.lexsort((vals & IDX, keys))
     assert np.array_equal(order, np.arange(keys.size))
+    assert np.all(vals >> 30 != 0)
+
+
+def test_ellipsoid_test_trims_a_flat_gaussian(orc):
+    """A 2 mm thick disc seen edge-on: its bounding sphere's cone covers a
+    disc of tiles, its ellipsoid only a thin band of them."""
+    H = W = 256
+    tile = 8
+    sc = scenes.Scene(np.float32([[0.0, 0.0, 3.0]]), np.float32([[0.3, 0.3, 0.002]]),
+                      np.float32([[np.cos(np.pi / 4), np.sin(np.pi / 4), 0.0, 0.0]]), np.float32([0.9]),
+                      np.float32([[1, 1, 1]]))
+    o = np.float32([0, 0, 0])
+    keys, vals = orc.f32_bin(sc, o[None], H, W, scenes.radii_linear(0.1, 8, 8), tile=tile)
+    r, g = orc.f32_gauss_cone(sc.means[0], sc.scales[0], sc.opac[0], o, 1.0, 1e-7, 8.0)
+    tx = W // tile
+    sphere = 0
+    for t in range(tx * tx):
+        ti, tj = divmod(t, tx)
+        c = orc.f32_rect_cone(ti * tile, ti * tile + tile, tj * tile, tj * tile + tile, H, W)
+        sphere += float(g[:3] @ c[:3]) >= float(g[3] * c[3] - g[4] * c[4])
+    assert sphere > 40 and len(keys) < 0.5 * sphere
+
+
+def test_rect_planes_bound_their_texels(orc):
+    """Every texel-centre direction of a valid rectangle is on the
+    non-negative side of its four edge planes and on the correct side of the
+    mid plane; a rectangle across the fold of the octahedral map (or one row
+    high) has no planes."""
+    H, W = 48, 64
+    for (i0, i1, j0, j1) in [(0, 8, 0, 8), (16, 24, 40, 48), (40, 48, 56, 64), (8, 16, 24, 32), (3, 11, 5, 13)]:
+        pl = orc.f32_rect_planes(i0, i1, j0, j1, 4, H, W)
+        if pl[15] == 0:
+            continue
+        for i in range(i0, i1):
+            for j in range(j0, j1):
+                d = orc.texel_dir(i, j, H, W)
+                for q in range(4):
+                    assert pl[3 * q: 3 * q + 3] @ d >= -1e-6
+                side = pl[12:15] @ d
+                assert (side >= -1e-6) if i < i0 + 4 else (side <= 1e-6)
+    # a tile that straddles |u| + |v| = 1 and a one-row tile
+    assert orc.f32_rect_planes(20, 28, 52, 60, 4, H, W)[15] == 0
+    assert orc.f32_rect_planes(5, 6, 0, 8, 4, H, W)[15] == 0
+
+
+def test_gauss_axes_give_the_covariance(orc):
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        s = np.float32(np.exp(rng.normal(-3, 1, 3)))
+        q = np.float32(rng.standard_normal(4))
+        mu, o = np.float32(rng.normal(size=3)), np.float32(rng.normal(size=3))
+        ax = orc.f32_gauss_axes(mu, s, q, o)
+        C = ax[3:].reshape(3, 3).astype(np.float64)     # rows: s_k r_k
+        A = orc.precision(s, q / np.linalg.norm(q))
+        np.testing.assert_allclose(C.T @ C, np.linalg.inv(A), rtol=1e-4, atol=1e-6 * np.max(s) ** 2)
+        np.testing.assert_allclose(ax[:3], mu.astype(np.float64) - o, rtol=1e-6, atol=1e-7)
 
 
 def test_binned_sum_matches_full_sum(orc):
-    """Summing Eq. 3 over the binned Gaussians only changes tau by at most
-    (number of Gaussians) x eps per voxel."""
-    sc = scenes.cube_scene(120, seed=15)
+    """Summing Eq. 3 over the binned Gaussians only (per half tile) changes
+    tau by at most (number of Gaussians) x eps per voxel."""
+    sc = _scene_with_flat_and_tiny(15)
     o = np.float32([0, 0, 0])
     H = W = 16
     tile = 8
@@ -182,18 +258,17 @@ def test_binned_sum_matches_full_sum(orc):
     keys, vals = orc.f32_bin(sc, o[None], H, W, radii, eps=eps, tile=tile)
     full = orc.build_tau(sc, o[None], H, W, radii)[0]
     tx = W // tile
-    for t in np.unique(keys):
-        members = vals[keys == t]
+    for t in range((H // tile) * (W // tile)):
         ti, tj = divmod(int(t), tx)
-        sub = scenes.subset(sc, members)
-        part = orc.build_tau(sub, o[None], H, W, radii)[0]
-        blk = (slice(None), slice(ti * tile, ti * tile + tile), slice(tj * tile, tj * tile + tile))
-        assert np.max(np.abs(part[blk] - full[blk])) <= sc.n * eps
-    empty = set(range((H // tile) * (W // tile))) - set(np.unique(keys).tolist())
-    for t in empty:
-        ti, tj = divmod(int(t), tx)
-        blk = (slice(None), slice(ti * tile, ti * tile + tile), slice(tj * tile, tj * tile + tile))
-        assert np.max(full[blk]) <= sc.n * eps
+        for h in (0, 1):
+            sel = (keys == t) & (((vals >> (30 + h)) & 1) == 1)
+            r0 = ti * tile + h * tile // 2
+            blk = (slice(None), slice(r0, r0 + tile // 2), slice(tj * tile, tj * tile + tile))
+            if sel.any():
+                part = orc.build_tau(scenes.subset(sc, vals[sel] & IDX), o[None], H, W, radii)[0]
+                assert np.max(np.abs(part[blk] - full[blk])) <= sc.n * eps
+            else:
+                assert np.max(full[blk]) <= sc.n * eps
 
 
 def test_sample_at_voxel_centre_returns_voxel(orc):

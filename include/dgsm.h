@@ -60,9 +60,10 @@ enum dgsm_dtype { DGSM_F32 = 0, DGSM_F16 = 1, DGSM_BF16 = 2 };
  * a tile's list is processed in work items of at most 16 chunks.
  * atlas_dtype: storage type of T (dgsm_dtype; tau is always accumulated in
  * float32).
- * max_pairs: 0 (default) sizes the pair buffers from the exact pair count,
- * read back once midway through the build; > 0 sizes them for max_pairs
- * pairs and never blocks (so the build can be captured in a CUDA graph; see
+ * max_pairs: 0 (default) sizes the pair buffers from the exact pair counts,
+ * read back twice during the build; > 0 sizes them for max_pairs pairs
+ * (both the (super-tile, Gaussian) and the (tile, Gaussian) pairs; see
+ * dgsm_build_stats) and never blocks (so the build can be captured in a CUDA graph; see
  * dgsm_graph_begin).  A build whose pairs exceed max_pairs records
  * DGSM_ERR_WORKSPACE in the status word and leaves T = 1 in its atlas. */
 typedef struct {
@@ -80,6 +81,7 @@ typedef struct {
     int64_t rays_tested;  /* texel-ray x Gaussian pairs tested (texels x list lengths) */
     int64_t ray_evals;    /* Gaussian-ray evaluations: rays cutting the culling ellipsoid at t > 0 */
     int64_t shell_evals;  /* closed-form (Eq. 3) evaluations at shell radii */
+    int64_t n_super_pairs; /* binned (8x8-tile super-tile, Gaussian) pairs */
 } dgsm_build_stats;
 
 /* Transfer parameters of Eqs. 9-10: lobe exponent q (1 = Lambertian),
@@ -120,8 +122,8 @@ const char *dgsm_status_string(int status);
  *   T = 1 everywhere); lights: (n_lights,3), 1 <= n_lights <= 64;
  *   1 <= H, W <= 4096; radii: (K), 1 <= K <= 256; params: host pointer or
  *   NULL for defaults; atlas: [n_lights][K][H][W] of params->atlas_dtype.
- * With params->max_pairs = 0 it blocks once, midway, to size the workspace
- * from the number of binned pairs; with max_pairs > 0 it never blocks and
+ * With params->max_pairs = 0 it blocks twice to size the workspace from the
+ * numbers of binned pairs; with max_pairs > 0 it never blocks and
  * reports input errors through the status word (dgsm_sync_status): a
  * non-finite Gaussian is then left out of the atlas.  Within a voxel the
  * contributions of different Gaussians are summed in an order that can vary

@@ -63,7 +63,7 @@ class RelightParams(C.Structure):
 
 class BuildStats(C.Structure):
     _fields_ = [("n_pairs", C.c_int64), ("rays_tested", C.c_int64), ("ray_evals", C.c_int64),
-                ("shell_evals", C.c_int64)]
+                ("shell_evals", C.c_int64), ("n_super_pairs", C.c_int64)]
 
 
 class FrameHostIn(C.Structure):
@@ -237,7 +237,7 @@ def dgsm_get_build_stats(ctx: Context | None = None) -> dict:
     st = BuildStats()
     ctx.check(_lib.dgsm_get_build_stats(ctx.handle, C.byref(st)))
     return {"n_pairs": st.n_pairs, "rays_tested": st.rays_tested, "ray_evals": st.ray_evals,
-            "shell_evals": st.shell_evals}
+            "shell_evals": st.shell_evals, "n_super_pairs": st.n_super_pairs}
 
 
 def dgsm_bin(means, scales, quats, opac, lights, H, W, radii, params=None, ctx: Context | None = None,

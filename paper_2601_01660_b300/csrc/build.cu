@@ -395,89 +395,269 @@ __global__ void __launch_bounds__(256) prep_kernel(
     }
 }
 
-__device__ __forceinline__ bool cone_overlap(const BinRec &g, const float4 *cone) {
-    const float4 c0 = __ldg(cone), c1 = __ldg(cone + 1);
+__device__ __forceinline__ bool cone_overlap_v(const BinRec &g, const float4 &c0, const float4 &c1) {
     if (c1.y != 0.0f) return true;  // cone spans a hemisphere
     const float dot = xdot(g.a.x, g.a.y, g.a.z, c0.x, c0.y, c0.z);
     const float rhs = xsub(xmul(g.a.w, c0.w), xmul(g.b.x, c1.x));
     return dot >= rhs;
 }
 
-// Count (EMIT = false) or write (EMIT = true) the tiles each Gaussian
-// reaches.  One warp per (light, Gaussian): 32 super-tile cone tests at a
-// time, then the 64 tiles of every overlapped super-tile, 32 at a time (cone
-// test, then the ellipsoid test against the tile's planes, which also gives
-// the half-tile mask); the pairs of one Gaussian are written contiguously
-// from its scanned offset.
+// cone: two float4 in global memory
+__device__ __forceinline__ bool cone_overlap(const BinRec &g, const float4 *cone) {
+    return cone_overlap_v(g, __ldg(cone), __ldg(cone + 1));
+}
+
+// ---------------------------------------------------------------------------
+// Binning in two levels.  Pass A (Gaussian-major): each (light, Gaussian)
+// tests its bounding cone against the cones of the 8x8-tile super-tiles and
+// emits (light * n_super + super-tile, Gaussian) pairs; a stable sort by key
+// gives every super-tile its Gaussian list in index order.  Pass B
+// (super-tile-major): a block takes up to UNIT_G Gaussians of one list, stages
+// the super-tile's 64 tile cones and planes and the Gaussians' records in
+// shared memory, and each warp tests its 8 tiles (cone test, then the
+// ellipsoid test on consecutive lanes); per-tile lists come out in Gaussian
+// order, laid out super-tile by super-tile, with no sort.
+// ---------------------------------------------------------------------------
+constexpr int UNIT_G = 512;     // Gaussians of one super-tile list per fine-binning block
+constexpr int FB_STAGE = 256;   // Gaussians staged in shared memory at a time
+constexpr int TDAT_F4 = 2 + PLANE_F4;  // per tile: cone (2 float4) + planes
+
 template <bool EMIT>
-__global__ void __launch_bounds__(256) bin_kernel(
-    const BinRec *__restrict__ bin, int64_t N, int L, int tx, int ty, int sx, int sy,
-    const float4 *__restrict__ cones, uint32_t *__restrict__ counts,
-    const uint32_t *__restrict__ offsets, uint32_t *__restrict__ keys,
-    uint32_t *__restrict__ vals, const unsigned long long *__restrict__ keep, uint32_t cap) {
-    // EMIT: nothing to write when the pairs overflow the buffers (*keep == 0)
+__global__ void __launch_bounds__(256) coarse_bin_kernel(
+    const BinRec *__restrict__ bin, int64_t N, int L, int n_super, const float4 *__restrict__ scones,
+    uint32_t *__restrict__ counts, const uint32_t *__restrict__ offsets, uint32_t *__restrict__ ckeys,
+    uint32_t *__restrict__ cvals, const unsigned long long *__restrict__ keep, uint32_t cap) {
     if (EMIT && *keep == 0) return;
     const int64_t total = (int64_t)L * N;
-    const int n_tiles = tx * ty, n_super = sx * sy;
-    const float4 *scones = cones + 2 * n_tiles;
-    const float4 *planes = cones + 2 * (n_tiles + n_super);
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < total;
-         idx += nwarps) {
-        const BinRec g = bin[idx];
-        const int mode = (int)g.b.y;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const float4 ga = bin[idx].a, gb = bin[idx].b;
+        BinRec g;
+        g.a = ga;
+        g.b = gb;
+        const int mode = (int)gb.y;
         const int l = (int)(idx / N);
         const uint32_t gi = (uint32_t)(idx - (int64_t)l * N);
-        const uint32_t kbase = (uint32_t)l * (uint32_t)n_tiles;
-        uint32_t c = 0, off = 0;
-        if (EMIT) off = offsets[idx];
-        if (mode == 2) {
-            if (EMIT)
-                for (int t = lane; t < n_tiles; t += 32) {
-                    if (off + t >= cap) break;
-                    const uint32_t m = planes[PLANE_F4 * t + 1].w != 0.0f ? 3u : 1u;
-                    keys[off + t] = kbase + t;
-                    vals[off + t] = gi | (m << 30);
-                }
-            c = n_tiles;
-        } else if (mode == 1) {
-            GAxes ga;
-            ga.v[0] = g.b.w; ga.v[1] = g.c.x; ga.v[2] = g.c.y;
-            ga.c[0] = g.c.z; ga.c[1] = g.c.w; ga.c[2] = g.d.x;
-            ga.c[3] = g.d.y; ga.c[4] = g.d.z; ga.c[5] = g.d.w;
-            ga.c[6] = g.e.x; ga.c[7] = g.e.y; ga.c[8] = g.e.z;
-            ga.k2s = g.b.z;
-            for (int sb = 0; sb < n_super; sb += 32) {
-                const int s = sb + lane;
-                unsigned m = __ballot_sync(0xffffffffu, s < n_super && cone_overlap(g, scones + 2 * s));
-                while (m) {
-                    const int si = sb + __ffs(m) - 1;
-                    m &= m - 1;
-                    const int sa = si / sx, sbb = si - sa * sx;
-#pragma unroll
-                    for (int rnd = 0; rnd < SUPER * SUPER / 32; ++rnd) {
-                        const int local = rnd * 32 + lane;
-                        const int a = sa * SUPER + local / SUPER, b = sbb * SUPER + local % SUPER;
-                        const int t = a * tx + b;
-                        uint32_t hm = 0u;
-                        if (a < ty && b < tx && cone_overlap(g, cones + 2 * t))
-                            hm = half_mask(planes + PLANE_F4 * t, ga, false);
-                        const unsigned m2 = __ballot_sync(0xffffffffu, hm != 0u);
-                        if (EMIT && hm != 0u) {
-                            const uint32_t pos = off + c + __popc(m2 & lt);
-                            if (pos < cap) {
-                                keys[pos] = kbase + t;
-                                vals[pos] = gi | (hm << 30);
-                            }
-                        }
-                        c += __popc(m2);
+        uint32_t c = 0, off = EMIT ? offsets[idx] : 0u;
+        if (mode != 0) {
+            for (int sidx = 0; sidx < n_super; ++sidx) {
+                if (mode == 2 || cone_overlap(g, scones + 2 * sidx)) {
+                    if (EMIT && off + c < cap) {
+                        ckeys[off + c] = (uint32_t)(l * n_super + sidx);
+                        cvals[off + c] = gi;
                     }
+                    ++c;
                 }
             }
         }
-        if (!EMIT && lane == 0) counts[idx] = c;
+        if (!EMIT) counts[idx] = c;
+    }
+}
+
+// Work units of pass B: unit_cnt[key] = ceil(list length / UNIT_G).
+__global__ void unit_count_kernel(const uint32_t *__restrict__ cs, const uint32_t *__restrict__ ce,
+                                  int n_keys, uint32_t *__restrict__ unit_cnt) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n_keys) unit_cnt[k] = (ce[k] - cs[k] + UNIT_G - 1) / UNIT_G;
+}
+
+// unit = (super key, list start, list end, index within the key | units of the key << 16, first unit of the key)
+struct __align__(16) Unit {
+    uint32_t key, start, end, ju, u0, pad0, pad1, pad2;
+};
+
+__global__ void unit_fill_kernel(const uint32_t *__restrict__ cs, const uint32_t *__restrict__ ce,
+                                 int n_keys, const uint32_t *__restrict__ unit_off,
+                                 Unit *__restrict__ units) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_keys) return;
+    const uint32_t s0 = cs[k], e0 = ce[k];
+    const uint32_t U = (e0 - s0 + UNIT_G - 1) / UNIT_G, u0 = unit_off[k];
+    for (uint32_t j = 0; j < U; ++j) {
+        Unit u;
+        u.key = (uint32_t)k;
+        u.start = s0 + j * UNIT_G;
+        u.end = min(s0 + (j + 1) * UNIT_G, e0);
+        u.ju = j | (U << 16);
+        u.u0 = u0;
+        u.pad0 = u.pad1 = u.pad2 = 0u;
+        units[u0 + j] = u;
+    }
+}
+
+// Lanes [lo, hi) of a warp as a bit mask (0 <= lo <= hi <= 32).
+__device__ __forceinline__ unsigned lane_range(int lo, int hi) {
+    const unsigned a = lo >= 32 ? 0u : (0xffffffffu << lo);
+    const unsigned b = hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u);
+    return a & b;
+}
+
+// Pass B.  COUNT: per (unit, tile) pair counts into fcnt; EMIT: pairs at the
+// scanned offsets foff.  Entry of (tile t of super key k, unit j of U) in
+// fcnt/foff: 64 u0 + t U + j, so that the scan lays out each tile's pairs
+// unit after unit, i.e. in Gaussian order.
+template <bool EMIT>
+__global__ void __launch_bounds__(256) fine_bin_kernel(
+    const Unit *__restrict__ units, const unsigned long long *__restrict__ n_units_dev,
+    const uint32_t *__restrict__ cvals, const BinRec *__restrict__ bin, int64_t N, int tx, int ty,
+    int sx, int n_tiles, int n_super, const float4 *__restrict__ cones,
+    uint32_t *__restrict__ fcnt, const uint32_t *__restrict__ foff, uint32_t *__restrict__ vals,
+    uint32_t *__restrict__ keys, const unsigned long long *__restrict__ keep, uint32_t cap) {
+    if (EMIT && *keep == 0) return;
+    __shared__ float4 tdat[64 * TDAT_F4];
+    __shared__ BinRec grec[FB_STAGE];
+    __shared__ uint32_t gidx[FB_STAGE];
+    __shared__ uint32_t running[64];
+    __shared__ uint32_t base[64];
+    __shared__ int tvalid[64];
+    const unsigned long long n_units = *n_units_dev;
+    const float4 *planes = cones + 2 * (n_tiles + n_super);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    for (unsigned long long u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const Unit U = units[u];
+        const int l = (int)(U.key / (uint32_t)n_super), sidx = (int)(U.key - (uint32_t)l * n_super);
+        const int sa = sidx / sx, sb = sidx - sa * sx;
+        const uint32_t j = U.ju & 0xffffu, nU = U.ju >> 16;
+        __syncthreads();  // shared state of the previous unit is no longer read
+        for (int e = tid; e < 64 * TDAT_F4; e += blockDim.x) {
+            const int t = e / TDAT_F4, part = e - t * TDAT_F4;
+            const int a = sa * SUPER + t / SUPER, b = sb * SUPER + t % SUPER;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a < ty && b < tx) {
+                const int gt = a * tx + b;
+                v = part < 2 ? __ldg(cones + 2 * gt + part) : __ldg(planes + PLANE_F4 * gt + part - 2);
+            }
+            tdat[e] = v;
+        }
+        if (tid < 64) {
+            const int a = sa * SUPER + tid / SUPER, b = sb * SUPER + tid % SUPER;
+            tvalid[tid] = a < ty && b < tx;
+            running[tid] = 0u;
+            if (EMIT) base[tid] = foff[64u * U.u0 + (uint32_t)tid * nU + j];
+        }
+        for (uint32_t s0 = U.start; s0 < U.end; s0 += FB_STAGE) {
+            const int ns = (int)min((uint32_t)FB_STAGE, U.end - s0);
+            __syncthreads();  // grec of the previous stage is no longer read
+            for (int e = tid; e < ns; e += blockDim.x) {
+                const uint32_t g = cvals[s0 + e];
+                gidx[e] = g;
+                grec[e] = bin[(int64_t)l * N + g];
+            }
+            __syncthreads();
+            for (int grp = 0; grp < ns; grp += 32) {
+                const int gl = grp + lane;
+                const bool gv = gl < ns;
+                BinRec G;
+                G.a = gv ? grec[gl].a : make_float4(0.f, 0.f, 1.f, -1.f);
+                G.b = gv ? grec[gl].b : make_float4(0.f, 0.f, 0.f, 0.f);
+                const bool inside = G.b.y == 2.0f;
+                // cone tests of this warp's 8 tiles
+                unsigned cm[8];
+                int pc[9];
+                pc[0] = 0;
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int t = warp * 8 + jj;
+                    const bool ov = gv && G.b.y != 0.0f && tvalid[t] &&
+                                    (inside || cone_overlap_v(G, tdat[TDAT_F4 * t], tdat[TDAT_F4 * t + 1]));
+                    cm[jj] = __ballot_sync(0xffffffffu, ov);
+                    pc[jj + 1] = pc[jj] + __popc(cm[jj]);
+                }
+                const int total = pc[8];
+                for (int r = 0; r < total; r += 32) {
+                    const int q = r + lane;
+                    uint32_t hm = 0u;
+                    int jq = 0, t = 0, glane = 0;
+                    if (q < total) {
+#pragma unroll
+                        for (int jj = 1; jj < 8; ++jj)
+                            if (q >= pc[jj]) jq = jj;
+                        unsigned cmq = cm[0];
+#pragma unroll
+                        for (int jj = 1; jj < 8; ++jj)
+                            if (jq == jj) cmq = cm[jj];
+                        int pcq = 0;
+#pragma unroll
+                        for (int jj = 1; jj < 8; ++jj)
+                            if (jq == jj) pcq = pc[jj];
+                        glane = (int)__fns(cmq, 0, q - pcq + 1);
+                        t = warp * 8 + jq;
+                        const BinRec &R = grec[grp + glane];
+                        if (R.b.y == 2.0f) {
+                            hm = tdat[TDAT_F4 * t + 3].w != 0.0f ? 3u : 1u;
+                        } else {
+                            GAxes ax;
+                            ax.v[0] = R.b.w; ax.v[1] = R.c.x; ax.v[2] = R.c.y;
+                            ax.c[0] = R.c.z; ax.c[1] = R.c.w; ax.c[2] = R.d.x;
+                            ax.c[3] = R.d.y; ax.c[4] = R.d.z; ax.c[5] = R.d.w;
+                            ax.c[6] = R.e.x; ax.c[7] = R.e.y; ax.c[8] = R.e.z;
+                            ax.k2s = R.b.z;
+                            hm = half_mask(tdat + TDAT_F4 * t + 2, ax, false);
+                        }
+                    }
+                    const unsigned pass = __ballot_sync(0xffffffffu, hm != 0u);
+                    if (EMIT && hm != 0u) {
+                        int lo = 0;
+#pragma unroll
+                        for (int jj = 1; jj < 8; ++jj)
+                            if (jq == jj) lo = pc[jj];
+                        lo = max(lo - r, 0);
+                        const uint32_t rank = __popc(pass & lt & lane_range(lo, 32));
+                        const uint32_t pos = base[t] + running[t] + rank;
+                        if (pos < cap) {
+                            vals[pos] = gidx[grp + glane] | (hm << 30);
+                            if (keys) {
+                                const int a = sa * SUPER + t / SUPER, b = sb * SUPER + t % SUPER;
+                                keys[pos] = (uint32_t)l * (uint32_t)n_tiles + (uint32_t)(a * tx + b);
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    if (lane < 8) {
+                        const int jj = lane;
+                        int lo = 0, hi = 0;
+#pragma unroll
+                        for (int k2 = 0; k2 < 8; ++k2)
+                            if (jj == k2) { lo = pc[k2]; hi = pc[k2 + 1]; }
+                        lo = min(max(lo - r, 0), 32);
+                        hi = min(max(hi - r, 0), 32);
+                        running[warp * 8 + jj] += __popc(pass & lane_range(lo, hi));
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        __syncthreads();
+        if (!EMIT && tid < 64) fcnt[64u * U.u0 + (uint32_t)tid * nU + j] = running[tid];
+    }
+}
+
+// Tile ranges of the two-level layout: the pairs of tile t of super key k
+// run from its unit-0 entry to the end of its last unit's entry.
+__global__ void fine_ranges_kernel(const Unit *__restrict__ units,
+                                   const unsigned long long *__restrict__ n_units_dev,
+                                   const uint32_t *__restrict__ fcnt, const uint32_t *__restrict__ foff,
+                                   const unsigned long long *__restrict__ keep, int n_super, int sx,
+                                   int tx, int ty, int n_tiles, uint32_t *__restrict__ ts,
+                                   uint32_t *__restrict__ te) {
+    if (*keep == 0) return;  // no pairs kept: every tile stays empty
+    const unsigned long long n_units = *n_units_dev;
+    const unsigned long long total = n_units * 64ull;
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long u = e >> 6;
+        const Unit U = units[u];
+        const uint32_t j = U.ju & 0xffffu, nU = U.ju >> 16;
+        if (j != 0) continue;
+        const int t = (int)(e & 63);
+        const int l = (int)(U.key / (uint32_t)n_super), sidx = (int)(U.key - (uint32_t)l * n_super);
+        const int a = (sidx / sx) * SUPER + t / SUPER, b = (sidx % sx) * SUPER + t % SUPER;
+        if (a >= ty || b >= tx) continue;
+        const uint32_t first = 64u * U.u0 + (uint32_t)t * nU;
+        const uint32_t key = (uint32_t)l * (uint32_t)n_tiles + (uint32_t)(a * tx + b);
+        ts[key] = foff[first];
+        te[key] = foff[first + nU - 1] + fcnt[first + nU - 1];
     }
 }
 
@@ -907,98 +1087,157 @@ int check_common(dgsm_ctx *ctx, const float *means, const float *scales, const f
     return DGSM_OK;
 }
 
-// prep + binning + sort + ranges.  With max_pairs = 0 it blocks once to
-// read the pair count and sizes the pair buffers from it; with max_pairs > 0
-// the buffers hold max_pairs and the count stays on the device.
+static int key_bits(int64_t n_keys) {
+    int bits = 0;
+    while (bits < 32 && ((uint64_t)(n_keys - 1) >> bits) != 0) ++bits;
+    return bits;
+}
+
+// Reads a device counter (and the status word) with one blocking copy.
+static int read_count(dgsm_ctx *ctx, const unsigned long long *d, cudaStream_t s,
+                      unsigned long long *out) {
+    cudaError_t e = cudaMemcpyAsync(ctx->h_pinned, d, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned + 1, ctx->d_status, sizeof(int),
+                                              cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "build: pair count");
+    const int st = *(int *)(ctx->h_pinned + 1);
+    if (st != DGSM_OK) {
+        cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
+        return fail(ctx, st, "a Gaussian has a non-finite field or a non-positive scale");
+    }
+    *out = ctx->h_pinned[0];
+    return DGSM_OK;
+}
+
+// prep + two-level binning + tile ranges.  With max_pairs = 0 it blocks
+// twice (after each level's count) to size the pair buffers exactly; with
+// max_pairs > 0 both levels' buffers hold max_pairs pairs and the counts stay
+// on the device.  want_keys: also write each pair's key (dgsm_bin).
 int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
                 const float *opac, int64_t N, const float *lights, int L, int H, int W,
-                const float *radii, int K, const dgsm_params &p, bool build_records, cudaStream_t s,
-                BinOut *out) {
+                const float *radii, int K, const dgsm_params &p, bool build_records, bool want_keys,
+                cudaStream_t s, BinOut *out) {
     const int tile = p.tile;
     const int tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
     const int sx = (tx + SUPER - 1) / SUPER, sy = (ty + SUPER - 1) / SUPER;
-    const int n_tiles = tx * ty;
+    const int n_tiles = tx * ty, n_super = sx * sy;
     out->tx = tx; out->ty = ty; out->n_tiles = n_tiles;
     const int64_t LN = (int64_t)L * N;
-    const int64_t nkeys = (int64_t)L * n_tiles;
-    void *w_br, *w_bin, *w_cnt, *w_cones, *w_rng;
+    const int64_t nkeys = (int64_t)L * n_tiles, nskeys = (int64_t)L * n_super;
+    void *w_br, *w_bin, *w_cnt, *w_cones, *w_rng, *w_crng;
     int rc;
     if ((rc = ws_reserve(ctx, WS_BUILD_REC, build_records ? sizeof(BuildRec) * (size_t)LN : 256, &w_br)))
         return rc;
     if ((rc = ws_reserve(ctx, WS_BIN_REC, sizeof(BinRec) * (size_t)LN, &w_bin))) return rc;
     if ((rc = ws_reserve(ctx, WS_COUNTS, sizeof(uint32_t) * (size_t)LN, &w_cnt))) return rc;
-    if ((rc = ws_reserve(ctx, WS_CONES, sizeof(float4) * (size_t)(2 * (n_tiles + sx * sy) + PLANE_F4 * n_tiles),
+    if ((rc = ws_reserve(ctx, WS_CONES, sizeof(float4) * (size_t)(2 * (n_tiles + n_super) + PLANE_F4 * n_tiles),
                          &w_cones)))
         return rc;
     if ((rc = ws_reserve(ctx, WS_RANGES, 2 * sizeof(uint32_t) * (size_t)nkeys, &w_rng))) return rc;
+    if ((rc = ws_reserve(ctx, WS_CRANGES, 2 * sizeof(uint32_t) * (size_t)nskeys, &w_crng))) return rc;
     out->brec = (BuildRec *)w_br;
     out->ts = (uint32_t *)w_rng;
     out->te = out->ts + nkeys;
+    uint32_t *cs = (uint32_t *)w_crng, *ce = cs + nskeys;
     cudaError_t e = cudaMemsetAsync(w_rng, 0, 2 * sizeof(uint32_t) * (size_t)nkeys, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w_crng, 0, 2 * sizeof(uint32_t) * (size_t)nskeys, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_stats, 0, 8 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "build: memset");
     out->P = 0;
     if (N == 0) return DGSM_OK;
+    unsigned long long *d_pairs = ctx->d_stats + 3, *d_keep = ctx->d_stats + 4;
+    unsigned long long *d_cpairs = ctx->d_stats + 5, *d_ckeep = ctx->d_stats + 6;
+    unsigned long long *d_units = ctx->d_stats + 7;
+    const float4 *cones = (const float4 *)w_cones;
 
-    const int nc = n_tiles + sx * sy;
+    // ---- per (light, Gaussian) records, level A: super-tiles ----
+    const int nc = n_tiles + n_super;
     rect_cones_kernel<<<(nc + 127) / 128, 128, 0, s>>>(H, W, tile, tx, ty, sx, sy, (float4 *)w_cones);
     const int grid = (int)std::min<int64_t>((LN + 255) / 256, (int64_t)ctx->num_sms * 16);
     prep_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, N, lights, L, radii, K, p.kappa,
                                      p.eps_cull, build_records ? (BuildRec *)w_br : nullptr,
                                      (BinRec *)w_bin, ctx->d_status);
-    const int wgrid = (int)std::min<int64_t>((LN * 32 + 255) / 256, (int64_t)ctx->num_sms * 16);
-    bin_kernel<false><<<wgrid, 256, 0, s>>>((const BinRec *)w_bin, N, L, tx, ty, sx, sy,
-                                             (const float4 *)w_cones, (uint32_t *)w_cnt, nullptr,
-                                             nullptr, nullptr, nullptr, 0u);
+    coarse_bin_kernel<false><<<grid, 256, 0, s>>>((const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles,
+                                                   (uint32_t *)w_cnt, nullptr, nullptr, nullptr, nullptr, 0u);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "prep/count kernels");
-    unsigned long long *d_total = ctx->d_stats + 3, *d_keep = ctx->d_stats + 4;
-    if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_cnt, (uint32_t *)w_cnt, LN, d_total, s)))
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "prep/coarse count kernels");
+    if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_cnt, (uint32_t *)w_cnt, LN, d_cpairs, s))) return rc;
+    int64_t capC = p.max_pairs;
+    if (capC == 0) {
+        unsigned long long Pc;
+        if ((rc = read_count(ctx, d_cpairs, s, &Pc))) return rc;
+        if (Pc >= (1ull << 31)) return fail(ctx, DGSM_ERR_WORKSPACE, "more than 2^31 (super-tile, Gaussian) pairs");
+        if (Pc == 0) return DGSM_OK;
+        capC = (int64_t)Pc;
+    }
+    void *cka, *cva, *ckb, *cvb;
+    if ((rc = ws_reserve(ctx, WS_CKEYS_A, sizeof(uint32_t) * capC, &cka))) return rc;
+    if ((rc = ws_reserve(ctx, WS_CVALS_A, sizeof(uint32_t) * capC, &cva))) return rc;
+    if ((rc = ws_reserve(ctx, WS_CKEYS_B, sizeof(uint32_t) * capC, &ckb))) return rc;
+    if ((rc = ws_reserve(ctx, WS_CVALS_B, sizeof(uint32_t) * capC, &cvb))) return rc;
+    keep_pairs_kernel<<<1, 32, 0, s>>>(d_cpairs, (unsigned long long)capC, d_ckeep, ctx->d_status);
+    coarse_bin_kernel<true><<<grid, 256, 0, s>>>((const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles,
+                                                  nullptr, (const uint32_t *)w_cnt, (uint32_t *)cka,
+                                                  (uint32_t *)cva, d_ckeep, (uint32_t)capC);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "coarse emit kernel");
+    uint32_t *ckeys = (uint32_t *)cka, *cvals = (uint32_t *)cva;
+    if ((rc = radix_sort_pairs(ctx, &ckeys, &cvals, (uint32_t *)ckb, (uint32_t *)cvb, d_ckeep, capC,
+                               key_bits(nskeys), s)))
+        return rc;
+    const int rgrid = (int)std::min<int64_t>((capC + 255) / 256, (int64_t)ctx->num_sms * 16);
+    tile_ranges_kernel<<<rgrid, 256, 0, s>>>(ckeys, d_ckeep, (uint32_t)nskeys, cs, ce);
+
+    // ---- work units of level B ----
+    const int64_t max_units = capC / UNIT_G + nskeys + 1;
+    void *w_units, *w_fcnt, *w_foff;
+    const size_t ucnt_bytes = (sizeof(uint32_t) * (size_t)nskeys + 15) & ~(size_t)15;
+    if ((rc = ws_reserve(ctx, WS_UNITS, ucnt_bytes + sizeof(Unit) * (size_t)max_units, &w_units))) return rc;
+    uint32_t *ucnt = (uint32_t *)w_units;
+    Unit *units = (Unit *)((char *)w_units + ucnt_bytes);
+    const int kgrid = (int)((nskeys + 255) / 256);
+    unit_count_kernel<<<kgrid, 256, 0, s>>>(cs, ce, (int)nskeys, ucnt);
+    if ((rc = scan_exclusive_u32(ctx, ucnt, ucnt, nskeys, d_units, s))) return rc;
+    unit_fill_kernel<<<kgrid, 256, 0, s>>>(cs, ce, (int)nskeys, ucnt, units);
+    const size_t nf = 64 * (size_t)max_units;
+    if ((rc = ws_reserve(ctx, WS_FCNT, sizeof(uint32_t) * nf, &w_fcnt))) return rc;
+    if ((rc = ws_reserve(ctx, WS_FOFF, sizeof(uint32_t) * nf, &w_foff))) return rc;
+    e = cudaMemsetAsync(w_fcnt, 0, sizeof(uint32_t) * nf, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "build: memset");
+    const int fgrid = (int)std::min<int64_t>(max_units, (int64_t)ctx->num_sms * 8);
+    fine_bin_kernel<false><<<fgrid, 256, 0, s>>>(units, d_units, cvals, (const BinRec *)w_bin, N, tx, ty, sx,
+                                                  n_tiles, n_super, cones, (uint32_t *)w_fcnt, nullptr,
+                                                  nullptr, nullptr, nullptr, 0u);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fine count kernel");
+    if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_fcnt, (uint32_t *)w_foff, (int64_t)nf, d_pairs, s)))
         return rc;
     int64_t cap = p.max_pairs;
     if (cap == 0) {
-        e = cudaMemcpyAsync(ctx->h_pinned, d_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned + 1, ctx->d_status, sizeof(int),
-                                                  cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "build: pair count");
-        const int st = *(int *)(ctx->h_pinned + 1);
-        if (st != DGSM_OK) {
-            cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
-            return fail(ctx, st, "a Gaussian has a non-finite field or a non-positive scale");
-        }
-        const unsigned long long P = ctx->h_pinned[0];
+        unsigned long long P;
+        if ((rc = read_count(ctx, d_pairs, s, &P))) return rc;
         if (P >= (1ull << 31)) return fail(ctx, DGSM_ERR_WORKSPACE, "more than 2^31 binned pairs");
-        if (P == 0) {
-            e = cudaMemsetAsync(d_keep, 0, sizeof(unsigned long long), s);
-            return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "build: memset");
-        }
+        if (P == 0) return DGSM_OK;
         cap = (int64_t)P;
     }
     out->P = cap;
-    void *ka, *va, *kb, *vb;
-    if ((rc = ws_reserve(ctx, WS_KEYS_A, sizeof(uint32_t) * cap, &ka))) return rc;
+    void *va, *ka = nullptr;
     if ((rc = ws_reserve(ctx, WS_VALS_A, sizeof(uint32_t) * cap, &va))) return rc;
-    if ((rc = ws_reserve(ctx, WS_KEYS_B, sizeof(uint32_t) * cap, &kb))) return rc;
-    if ((rc = ws_reserve(ctx, WS_VALS_B, sizeof(uint32_t) * cap, &vb))) return rc;
-    keep_pairs_kernel<<<1, 32, 0, s>>>(d_total, (unsigned long long)cap, d_keep, ctx->d_status);
-    bin_kernel<true><<<wgrid, 256, 0, s>>>((const BinRec *)w_bin, N, L, tx, ty, sx, sy,
-                                            (const float4 *)w_cones, nullptr,
-                                            (const uint32_t *)w_cnt, (uint32_t *)ka, (uint32_t *)va,
-                                            d_keep, (uint32_t)cap);
+    if (want_keys && (rc = ws_reserve(ctx, WS_KEYS_A, sizeof(uint32_t) * cap, &ka))) return rc;
+    keep_pairs_kernel<<<1, 32, 0, s>>>(d_pairs, (unsigned long long)cap, d_keep, ctx->d_status);
+    fine_bin_kernel<true><<<fgrid, 256, 0, s>>>(units, d_units, cvals, (const BinRec *)w_bin, N, tx, ty, sx,
+                                                 n_tiles, n_super, cones, (uint32_t *)w_fcnt,
+                                                 (const uint32_t *)w_foff, (uint32_t *)va, (uint32_t *)ka,
+                                                 d_keep, (uint32_t)cap);
+    const int ugrid = (int)std::min<int64_t>((int64_t)((nf + 255) / 256), (int64_t)ctx->num_sms * 16);
+    fine_ranges_kernel<<<ugrid, 256, 0, s>>>(units, d_units, (const uint32_t *)w_fcnt,
+                                              (const uint32_t *)w_foff, d_keep, n_super, sx, tx, ty,
+                                              n_tiles, out->ts, out->te);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "bin emit kernel");
-    int bits = 0;
-    while (bits < 32 && ((uint64_t)(nkeys - 1) >> bits) != 0) ++bits;
-    uint32_t *keys = (uint32_t *)ka, *vals = (uint32_t *)va;
-    if ((rc = radix_sort_pairs(ctx, &keys, &vals, (uint32_t *)kb, (uint32_t *)vb, d_keep, cap, bits, s)))
-        return rc;
-    const int rgrid = (int)std::min<int64_t>((cap + 255) / 256, (int64_t)ctx->num_sms * 16);
-    tile_ranges_kernel<<<rgrid, 256, 0, s>>>(keys, d_keep, (uint32_t)nkeys, out->ts, out->te);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "tile ranges kernel");
-    out->keys = keys;
-    out->vals = vals;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fine emit kernels");
+    out->keys = (uint32_t *)ka;
+    out->vals = (uint32_t *)va;
     return DGSM_OK;
 }
 
@@ -1037,7 +1276,8 @@ extern "C" int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales
     cudaEvent_t *ev = prof ? ctx->prof_ev[ctx->prof_count] : nullptr;
     if (prof) cudaEventRecord(ev[0], s);
     BinOut b;
-    if ((rc = run_binning(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, true, s, &b)))
+    if ((rc = run_binning(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, true, false, s,
+                          &b)))
         return rc;
 
     // ---- work items: every tile's list cut into pieces of <= item Gaussians ----
@@ -1101,13 +1341,14 @@ extern "C" int dgsm_get_build_stats(dgsm_ctx *ctx, dgsm_build_stats *out) {
     if (!ctx || !out) return DGSM_ERR_INVALID_ARG;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemcpy(ctx->h_pinned + 4, ctx->d_stats, 4 * sizeof(unsigned long long),
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->h_pinned + 4, ctx->d_stats, 6 * sizeof(unsigned long long),
                                          cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "dgsm_get_build_stats");
     out->n_pairs = (int64_t)ctx->h_pinned[7];
     out->rays_tested = (int64_t)ctx->h_pinned[4];
     out->ray_evals = (int64_t)ctx->h_pinned[5];
     out->shell_evals = (int64_t)ctx->h_pinned[6];
+    out->n_super_pairs = (int64_t)ctx->h_pinned[9];
     return DGSM_OK;
 }
 
@@ -1129,14 +1370,24 @@ extern "C" int dgsm_bin(dgsm_ctx *ctx, const float *means, const float *scales, 
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
     BinOut b;
-    if ((rc = run_binning(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, false, s, &b)))
+    if ((rc = run_binning(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, false, true, s,
+                          &b)))
         return rc;
     *n_pairs_out = b.P;
     if (b.P > capacity) return fail(ctx, DGSM_ERR_WORKSPACE, "capacity smaller than the pair count");
     if (b.P > 0) {
-        e = cudaMemcpyAsync(keys_out, b.keys, sizeof(uint32_t) * b.P, cudaMemcpyDeviceToDevice, s);
+        // the pairs are laid out super-tile by super-tile: sort them by key
+        // (stable, so each key keeps its Gaussian order)
+        void *kb, *vb;
+        if ((rc = ws_reserve(ctx, WS_KEYS_B, sizeof(uint32_t) * b.P, &kb))) return rc;
+        if ((rc = ws_reserve(ctx, WS_VALS_B, sizeof(uint32_t) * b.P, &vb))) return rc;
+        uint32_t *keys = b.keys, *vals = b.vals;
+        if ((rc = radix_sort_pairs(ctx, &keys, &vals, (uint32_t *)kb, (uint32_t *)vb, ctx->d_stats + 4, b.P,
+                                   key_bits((int64_t)L * b.n_tiles), s)))
+            return rc;
+        e = cudaMemcpyAsync(keys_out, keys, sizeof(uint32_t) * b.P, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(vals_out, b.vals, sizeof(uint32_t) * b.P, cudaMemcpyDeviceToDevice, s);
+            e = cudaMemcpyAsync(vals_out, vals, sizeof(uint32_t) * b.P, cudaMemcpyDeviceToDevice, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "dgsm_bin copy-out");

@@ -13,8 +13,8 @@
 // ---------------------------------------------------------------------------
 enum WsSlot {
     WS_BUILD_REC = 0,  // per (light, Gaussian) build record, 80 B
-    WS_BIN_REC,        // per (light, Gaussian) binning record, 32 B
-    WS_COUNTS,         // per (light, Gaussian) tile count / offset, u32
+    WS_BIN_REC,        // per (light, Gaussian) binning record, 80 B
+    WS_COUNTS,         // per (light, Gaussian) super-tile count / offset, u32
     WS_SCAN_TMP,       // scan block sums
     WS_CONES,          // tile + super-tile cones
     WS_KEYS_A, WS_VALS_A, WS_KEYS_B, WS_VALS_B,
@@ -29,6 +29,10 @@ enum WsSlot {
     WS_NF,             // surrogate training: per-sample rows and partial gradients
     WS_NF_ACC,         // surrogate attenuation over more than four lights: partial sums
     WS_POSES,          // rigid poses of moving objects, copied in per call
+    WS_CKEYS_A, WS_CVALS_A, WS_CKEYS_B, WS_CVALS_B,  // (super-tile, Gaussian) pairs
+    WS_CRANGES,        // per (light, super-tile) start/end of its Gaussian list
+    WS_UNITS,          // fine-binning work units (+ per-super-tile unit counts)
+    WS_FCNT, WS_FOFF,  // per (unit, tile) pair counts and their scan
     WS_NSLOTS
 };
 

@@ -109,12 +109,13 @@ class CrowdFrame:
 
     def size_pairs(self, pose_list, headroom=1.25):
         """Pair capacity of the dynamic build: the largest exact pair count
-        over the given poses, with headroom."""
+        (tile and super-tile pairs) over the given poses, with headroom."""
         best = 0
         for p in pose_list:
             self.step_eager(p)
             self.stream.synchronize()
-            best = max(best, self.nat.dgsm_get_build_stats(self.ctx)["n_pairs"])
+            st = self.nat.dgsm_get_build_stats(self.ctx)
+            best = max(best, st["n_pairs"], st["n_super_pairs"])
         self.max_pairs = int(best * headroom) + 1024
         return self.max_pairs
 

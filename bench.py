@@ -216,9 +216,10 @@ def run_ours(args, rank, world, local_rank):
         bound_pipe, ach, peak = "fp32", fp32_ach, fp32_peak
     else:
         bound_pipe, ach, peak = "mufu", mufu_ach, mufu_peak
-    roofline = {"bound": "alu", "kernel": "build_tiles_kernel", "pipe": bound_pipe,
+    traffic = _profiled_traffic("build_items_kernel", args.workload)
+    roofline = {"bound": "alu", "kernel": "build_items_kernel", "pipe": bound_pipe,
                 "achieved": round(ach, 4), "peak": round(peak, 4), "unit": "Tops/s",
-                "frac": round(ach / peak, 4), "traffic": None,
+                "frac": round(ach / peak, 4), "traffic": traffic,
                 "peak_source": "derived: 148 SMs x lanes/clk x max SM clock (unit counts), of derived",
                 "pipes": {"fp32": {"achieved": round(fp32_ach, 4), "peak": round(fp32_peak, 4),
                                    "frac": round(fp32_ach / fp32_peak, 4)},
@@ -267,11 +268,34 @@ def run_ours(args, rank, world, local_rank):
 
 
 def count_launches(args, L):
-    """Kernels of ours per step: prep 1, cones 1, count 1, scan 3, emit 1, 2 radix passes
-    x (hist 1 + scan 3 + scatter 1), ranges 1, tiles 1; attenuate 1; sh_fit 2;
-    centroid 2; relight 1."""
-    per_step = 1 + 1 + 1 + 3 + 1 + 2 * 5 + 1 + 1 + 1 + 2 + 2 + 1
-    return per_step * args.steps
+    """Kernels of ours per step.  Build: cones 1, prep 1, super-tile count 1,
+    scan 3, keep 1, super-tile emit 1, sort passes x (hist 1 + scan 3 +
+    scatter 1), super-tile ranges 1, unit count 1, scan 3, unit fill 1, tile
+    count 1, scan 3, keep 1, tile emit 1, tile ranges 1, item count 1, scan 3,
+    item expand 1, tile kernel 1.  Then attenuate 1, sh_fit 2, centroid 2,
+    relight 1."""
+    import math
+    n_super = math.ceil(512 / 8 / 8) ** 2 * L
+    sort_passes = math.ceil(max(1, (n_super - 1).bit_length()) / 8)
+    build = 27 + 5 * sort_passes
+    return (build + 6) * args.steps
+
+
+def _profiled_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of this
+    workload, or None when the summary is missing or was taken on another
+    version of the kernel source (its sha256 is recorded beside the figure)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel.replace('_kernel', '')}_{workload}.txt")
+    src = os.path.join(ROOT, "paper_2601_01660_b300", "csrc", "build.cu")
+    try:
+        fields = dict(line.split(":", 1) for line in open(path) if ":" in line)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if fields.get("source_sha256", "").strip() != sha:
+            return None
+        return int(fields["dram_bytes_per_launch"].strip())
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def _measured_peak(key, fallback):

@@ -403,10 +403,10 @@ int nf_tile_error(dgsm_ctx *ctx, const float *params, const float *atlas, int32_
  * uint8, nonzero = fall back) marks the tile of a query's texel cell, the
  * exact trilinear lookup in `atlas` ([n_lights][K][H][W] float32) is used
  * instead; mask and atlas may be NULL (field everywhere).  Other arguments
- * as for dgsm_attenuate.  Lights are processed four at a time (their
- * weights staged on chip once per block); with more than four lights the
- * partial weighted sums go through a context workspace of n_q floats, so
- * calls that share a context must share a stream. */
+ * as for dgsm_attenuate.  The field runs on the tensor cores (tcgen05), one
+ * light per CTA with its weights staged on chip; T of every (query, light)
+ * goes through a context workspace of n_lights x n_q floats before the
+ * colours are formed, so calls that share a context must share a stream. */
 int nf_attenuate(dgsm_ctx *ctx, const float *params, const uint8_t *mask, const float *atlas,
                  int32_t n_lights, int32_t H, int32_t W, const float *radii, int32_t K,
                  int32_t tile, const float *lights, const float *q_means, const float *colors_in,

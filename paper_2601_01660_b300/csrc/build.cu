@@ -95,9 +95,6 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-__device__ __forceinline__ void record_status(int *status, int code) {
-    atomicCAS(status, 0, code);
-}
 
 // ---------------------------------------------------------------------------
 // Direction cone of the texel-centre rectangle [j0,j1) x [i0,i1): axis = the

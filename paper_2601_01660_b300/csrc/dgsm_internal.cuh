@@ -70,6 +70,9 @@ struct Segs {
 // Host check: 1 <= n_obj <= MAX_OBJECTS, seg[0] = 0, nondecreasing, seg[n_obj] = n.
 bool make_segs(const int64_t *seg, int n_obj, int64_t n, Segs *out);
 
+// Records the first error code a kernel meets in the context's status word.
+__device__ __forceinline__ void record_status(int *status, int code) { atomicCAS(status, 0, code); }
+
 // Object holding Gaussian g (s[0] <= g < s[n]): the last o with s[o] <= g.
 __device__ __forceinline__ int seg_find(const Segs &sg, long long g) {
     int lo = 0, hi = sg.n - 1;

@@ -11,9 +11,10 @@
 // Training (on atlases built by dgsm_build): voxels drawn at random, MSE on T,
 // Adam; forward/backward per sample in FP32 SIMT (nf_fwdbwd_kernel), weight
 // gradients as a batch reduction (nf_wgrad_kernel), Adam (nf_adam_kernel).
-// Inference: bf16 tensor-core MMA (mma.sync m16n8k16, FP32 accumulate), the
-// output fragments of one layer re-packed in registers as the input
-// fragments of the next (nf_infer_kernel, nf_attenuate_kernel).
+// Inference: 5th-generation tensor cores (tcgen05.mma kind::f16, bf16
+// operands in shared memory, FP32 accumulators in tensor memory), 128 rows
+// per warpgroup tile (tc::field_kernel); attenuation writes T per light and a
+// small pass forms the colours (tc::combine_kernel).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -299,355 +300,11 @@ __global__ void nf_adam_kernel(const float *__restrict__ partial, int n_split, f
 }
 
 // ---------------------------------------------------------------------------
-// Inference on the tensor cores
+// bf16 packing for the tensor-core operands
 // ---------------------------------------------------------------------------
-constexpr int IF_WARPS = 4;
-constexpr int IF_THREADS = IF_WARPS * 32;
-// shared: bf16 weights W1 (64 x 96), W2..W4 (64 x 64) in [out][in] order, then
-// float biases b1..b4 (4 x 64), bf16-rounded w5 (64), b5
-constexpr int IF_WB = NF_HID * NF_FEAT + 3 * NF_HID * NF_HID;   // bf16 elements
-constexpr size_t IF_SMEM = IF_WB * sizeof(__nv_bfloat16) + (4 * NF_HID + NF_HID + 4) * sizeof(float);
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&p);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-__device__ void nf_stage_infer_weights(const float *__restrict__ params, __nv_bfloat16 *wb, float *fb) {
-    for (int e = threadIdx.x; e < IF_WB; e += blockDim.x) {
-        int src;
-        if (e < NF_HID * NF_FEAT) src = OFF_W1 + e;
-        else {
-            const int r = e - NF_HID * NF_FEAT, l = r / (NF_HID * NF_HID), q = r - l * NF_HID * NF_HID;
-            src = (l == 0 ? OFF_W2 : l == 1 ? OFF_W3 : OFF_W4) + q;
-        }
-        wb[e] = __float2bfloat16_rn(params[src]);
-    }
-    for (int e = threadIdx.x; e < 4 * NF_HID; e += blockDim.x) {
-        const int l = e / NF_HID, o = e - l * NF_HID;
-        fb[e] = params[(l == 0 ? OFF_B1 : l == 1 ? OFF_B2 : l == 2 ? OFF_B3 : OFF_B4) + o];
-    }
-    for (int e = threadIdx.x; e < NF_HID; e += blockDim.x) fb[4 * NF_HID + e] = bf16r(params[OFF_W5 + e]);
-    if (threadIdx.x == 0) fb[5 * NF_HID] = params[OFF_B5];
-}
-
-// The field for 32 samples per warp (two 16-row tiles).  uvr[t][r]: the
-// inputs of rows g (r = 0) and g + 8 (r = 1) of tile t, g = lane / 4.
-// Returns T_hat for those four rows (valid in every lane of the row's group).
-__device__ __forceinline__ void nf_field32(const __nv_bfloat16 *wb, const float *fb,
-                                           const float (&uvr)[2][2][3], float (&T)[2][2]) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
-    (void)g;
-    uint32_t A[2][6][4];  // A fragments of layer 1: tile, k-tile, register
-#pragma unroll
-    for (int tt = 0; tt < 2; ++tt)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            // this lane's frequencies m in {2t, 2t+1, 2t+8, 2t+9}
-            float sn[2][4], cs[2][4];
-#pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int m = 2 * t4 + (q & 1) + (q >> 1) * 8;
-                    nf_sincos(nf_freq(m), uvr[tt][r][a], sn[r][q], cs[r][q]);
-                }
-            // k-tile 2a holds the sines of axis a, 2a+1 its cosines
-            A[tt][2 * a][0] = pack_bf16(sn[0][0], sn[0][1]);
-            A[tt][2 * a][1] = pack_bf16(sn[1][0], sn[1][1]);
-            A[tt][2 * a][2] = pack_bf16(sn[0][2], sn[0][3]);
-            A[tt][2 * a][3] = pack_bf16(sn[1][2], sn[1][3]);
-            A[tt][2 * a + 1][0] = pack_bf16(cs[0][0], cs[0][1]);
-            A[tt][2 * a + 1][1] = pack_bf16(cs[1][0], cs[1][1]);
-            A[tt][2 * a + 1][2] = pack_bf16(cs[0][2], cs[0][3]);
-            A[tt][2 * a + 1][3] = pack_bf16(cs[1][2], cs[1][3]);
-        }
-    const uint32_t *wb32 = reinterpret_cast<const uint32_t *>(wb);
-    uint32_t Hf[2][4][4];  // activations as A fragments (4 k-tiles of 16)
-    // ---- layer 1: 96 -> 64 ----
-#pragma unroll
-    for (int tt = 0; tt < 2; ++tt) {
-        float C[8][4];
-#pragma unroll
-        for (int n = 0; n < 8; ++n) {
-            const float b0 = fb[8 * n + 2 * t4], b1 = fb[8 * n + 2 * t4 + 1];
-            C[n][0] = b0; C[n][1] = b1; C[n][2] = b0; C[n][3] = b1;
-        }
-#pragma unroll
-        for (int kt = 0; kt < 6; ++kt)
-#pragma unroll
-            for (int n = 0; n < 8; ++n) {
-                const int o = 8 * n + (lane >> 2);
-                const uint32_t b0 = wb32[(o * NF_FEAT + 16 * kt + 2 * t4) >> 1];
-                const uint32_t b1 = wb32[(o * NF_FEAT + 16 * kt + 2 * t4 + 8) >> 1];
-                mma_bf16(C[n], A[tt][kt][0], A[tt][kt][1], A[tt][kt][2], A[tt][kt][3], b0, b1);
-            }
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt) {
-            Hf[tt][kt][0] = pack_bf16(fmaxf(C[2 * kt][0], 0.f), fmaxf(C[2 * kt][1], 0.f));
-            Hf[tt][kt][1] = pack_bf16(fmaxf(C[2 * kt][2], 0.f), fmaxf(C[2 * kt][3], 0.f));
-            Hf[tt][kt][2] = pack_bf16(fmaxf(C[2 * kt + 1][0], 0.f), fmaxf(C[2 * kt + 1][1], 0.f));
-            Hf[tt][kt][3] = pack_bf16(fmaxf(C[2 * kt + 1][2], 0.f), fmaxf(C[2 * kt + 1][3], 0.f));
-        }
-    }
-    // ---- layers 2..4: 64 -> 64 ----
-#pragma unroll
-    for (int l = 0; l < 3; ++l) {
-        const uint32_t *Wl = wb32 + ((NF_HID * NF_FEAT + l * NF_HID * NF_HID) >> 1);
-        const float *bl = fb + (l + 1) * NF_HID;
-#pragma unroll
-        for (int tt = 0; tt < 2; ++tt) {
-            float C[8][4];
-#pragma unroll
-            for (int n = 0; n < 8; ++n) {
-                const float b0 = bl[8 * n + 2 * t4], b1 = bl[8 * n + 2 * t4 + 1];
-                C[n][0] = b0; C[n][1] = b1; C[n][2] = b0; C[n][3] = b1;
-            }
-#pragma unroll
-            for (int kt = 0; kt < 4; ++kt)
-#pragma unroll
-                for (int n = 0; n < 8; ++n) {
-                    const int o = 8 * n + (lane >> 2);
-                    const uint32_t b0 = Wl[(o * NF_HID + 16 * kt + 2 * t4) >> 1];
-                    const uint32_t b1 = Wl[(o * NF_HID + 16 * kt + 2 * t4 + 8) >> 1];
-                    mma_bf16(C[n], Hf[tt][kt][0], Hf[tt][kt][1], Hf[tt][kt][2], Hf[tt][kt][3], b0, b1);
-                }
-            if (l < 2) {
-#pragma unroll
-                for (int kt = 0; kt < 4; ++kt) {
-                    Hf[tt][kt][0] = pack_bf16(fmaxf(C[2 * kt][0], 0.f), fmaxf(C[2 * kt][1], 0.f));
-                    Hf[tt][kt][1] = pack_bf16(fmaxf(C[2 * kt][2], 0.f), fmaxf(C[2 * kt][3], 0.f));
-                    Hf[tt][kt][2] = pack_bf16(fmaxf(C[2 * kt + 1][0], 0.f), fmaxf(C[2 * kt + 1][1], 0.f));
-                    Hf[tt][kt][3] = pack_bf16(fmaxf(C[2 * kt + 1][2], 0.f), fmaxf(C[2 * kt + 1][3], 0.f));
-                }
-            } else {
-                // output layer: y = w5 . bf16(ReLU(z4)) + b5, reduced over the 4 lanes of a row group
-                const float *w5 = fb + 4 * NF_HID;
-                float y0 = 0.f, y1 = 0.f;
-#pragma unroll
-                for (int n = 0; n < 8; ++n) {
-                    const int c = 8 * n + 2 * t4;
-                    y0 = fmaf(w5[c], bf16r(fmaxf(C[n][0], 0.f)), y0);
-                    y0 = fmaf(w5[c + 1], bf16r(fmaxf(C[n][1], 0.f)), y0);
-                    y1 = fmaf(w5[c], bf16r(fmaxf(C[n][2], 0.f)), y1);
-                    y1 = fmaf(w5[c + 1], bf16r(fmaxf(C[n][3], 0.f)), y1);
-                }
-                y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
-                y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
-                y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
-                y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
-                const float b5 = fb[5 * NF_HID];
-                T[tt][0] = 1.0f / (1.0f + expf(-(y0 + b5)));
-                T[tt][1] = 1.0f / (1.0f + expf(-(y1 + b5)));
-            }
-        }
-    }
-}
-
-// Field values at n explicit inputs (u, v, rho).
-__global__ void __launch_bounds__(IF_THREADS) nf_infer_kernel(const float *__restrict__ params,
-                                                              const float *__restrict__ uvr, int64_t n,
-                                                              float *__restrict__ T_out) {
-    extern __shared__ float4 smem_if[];
-    __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(smem_if);
-    float *fb = reinterpret_cast<float *>(wb + IF_WB);
-    nf_stage_infer_weights(params, wb, fb);
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2;
-    for (int64_t base = ((int64_t)blockIdx.x * IF_WARPS + warp) * 32; base < n;
-         base += (int64_t)gridDim.x * IF_WARPS * 32) {
-        float in[2][2][3], T[2][2];
-#pragma unroll
-        for (int tt = 0; tt < 2; ++tt)
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int64_t s = base + 16 * tt + g + 8 * r;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) in[tt][r][a] = s < n ? uvr[3 * s + a] : 0.f;
-            }
-        nf_field32(wb, fb, in, T);
-        if ((lane & 3) == 0)
-#pragma unroll
-            for (int tt = 0; tt < 2; ++tt)
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const int64_t s = base + 16 * tt + g + 8 * r;
-                    if (s < n) T_out[s] = T[tt][r];
-                }
-    }
-}
-
-// Per-tile worst error of the field against the exact atlas over all voxels
-// of the tile (tile x tile texels x K shells): one block per tile.
-__global__ void __launch_bounds__(IF_THREADS) nf_tile_error_kernel(
-    const float *__restrict__ params, const float *__restrict__ atlas, int H, int W, int K, int tile,
-    int tx, float *__restrict__ tile_err) {
-    extern __shared__ float4 smem_if[];
-    __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(smem_if);
-    float *fb = reinterpret_cast<float *>(wb + IF_WB);
-    __shared__ float s_err;
-    nf_stage_infer_weights(params, wb, fb);
-    if (threadIdx.x == 0) s_err = 0.0f;
-    __syncthreads();
-    const int t = blockIdx.x, ti = t / tx, tj = t - ti * tx;
-    const int i0 = ti * tile, j0 = tj * tile;
-    const int hh = min(tile, H - i0), ww = min(tile, W - j0);
-    const int nvox = hh * ww * K;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2;
-    float worst = 0.0f;
-    for (int base = warp * 32; base < nvox; base += IF_WARPS * 32) {
-        float in[2][2][3], T[2][2], ref[2][2];
-#pragma unroll
-        for (int tt = 0; tt < 2; ++tt)
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                int e = base + 16 * tt + g + 8 * r;
-                const bool ok = e < nvox;
-                e = ok ? e : 0;
-                const int k = e / (hh * ww), rem = e - k * hh * ww;
-                const int i = i0 + rem / ww, j = j0 + rem % ww;
-                in[tt][r][0] = (2.0f * j + 1.0f) / W - 1.0f;
-                in[tt][r][1] = (2.0f * i + 1.0f) / H - 1.0f;
-                in[tt][r][2] = K > 1 ? (float)k / (float)(K - 1) : 0.0f;
-                ref[tt][r] = ok ? atlas[((int64_t)k * H + i) * W + j] : -1.0f;
-            }
-        nf_field32(wb, fb, in, T);
-#pragma unroll
-        for (int tt = 0; tt < 2; ++tt)
-#pragma unroll
-            for (int r = 0; r < 2; ++r)
-                if (ref[tt][r] >= 0.0f) worst = fmaxf(worst, fabsf(T[tt][r] - ref[tt][r]));
-    }
-    for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
-    if (lane == 0) atomicMax(reinterpret_cast<int *>(&s_err), __float_as_int(worst));
-    __syncthreads();
-    if (threadIdx.x == 0) tile_err[t] = s_err;
-}
-
-// Attenuation through the field: per query and light the field value at
-// (u, v, rho) of the query, or -- where the light's fallback mask marks the
-// tile of the query's texel cell -- the exact trilinear atlas lookup.  The
-// weights of up to NF_LGROUP lights are staged in shared memory once per
-// block; with more lights, launches over light groups carry the weighted sum
-// in `accum` (first group writes it, last group turns it into colours).
-constexpr int NF_LGROUP = 4;
-constexpr int NA_WARPS = 8;   // one block per SM: 8 warps share the staged weights
-constexpr int NA_THREADS = NA_WARPS * 32;
-
-__global__ void __launch_bounds__(NA_THREADS, 1) nf_attenuate_kernel(
-    const float *__restrict__ params, int n_params_stride, const uint8_t *__restrict__ mask,
-    const float *__restrict__ atlas, int L, int l0, int LG, int H, int W,
-    const float *__restrict__ radii, int K, int tile, int tx, int n_tiles,
-    const float *__restrict__ lights, const float *__restrict__ qm, const float *cin, int64_t Q,
-    const float *__restrict__ lw, float wd, float *cout, float *__restrict__ Tout,
-    float *__restrict__ accum) {
-    extern __shared__ float4 smem_if[];
-    __shared__ float rs[256];
-    __shared__ float ls[64 * 3];
-    __shared__ float wl[64];
-    for (int k = threadIdx.x; k < K; k += blockDim.x) rs[k] = radii[k];
-    for (int k = threadIdx.x; k < 3 * L; k += blockDim.x) ls[k] = lights[k];
-    for (int k = threadIdx.x; k < L; k += blockDim.x) wl[k] = lw ? lw[k] : 1.0f / (float)L;
-    char *stage_base = reinterpret_cast<char *>(smem_if);
-    for (int lg = 0; lg < LG; ++lg) {
-        __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(stage_base + lg * IF_SMEM);
-        nf_stage_infer_weights(params + (int64_t)(l0 + lg) * n_params_stride, wb,
-                               reinterpret_cast<float *>(wb + IF_WB));
-    }
-    __syncthreads();
-    const bool first = l0 == 0, last = l0 + LG == L;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2;
-    const int64_t plane = (int64_t)H * W;
-    for (int64_t base = ((int64_t)blockIdx.x * NA_WARPS + warp) * 32; base < Q;
-         base += (int64_t)gridDim.x * NA_WARPS * 32) {
-        float px[2][2], py[2][2], pz[2][2], acc[2][2];
-#pragma unroll
-        for (int tt = 0; tt < 2; ++tt)
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int64_t s = base + 16 * tt + g + 8 * r;
-                const bool ok = s < Q;
-                px[tt][r] = ok ? qm[3 * s] : 0.f;
-                py[tt][r] = ok ? qm[3 * s + 1] : 0.f;
-                pz[tt][r] = ok ? qm[3 * s + 2] : 0.f;
-                acc[tt][r] = (ok && !first) ? accum[s] : 0.f;
-            }
-        for (int lg = 0; lg < LG; ++lg) {
-            const int l = l0 + lg;
-            const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(stage_base + lg * IF_SMEM);
-            const float *fb = reinterpret_cast<const float *>(wb + IF_WB);
-            float in[2][2][3], T[2][2];
-            SampleIndex si[2][2];
-#pragma unroll
-            for (int tt = 0; tt < 2; ++tt)
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    si[tt][r] = sample_index(px[tt][r], py[tt][r], pz[tt][r], ls[3 * l], ls[3 * l + 1],
-                                             ls[3 * l + 2], H, W, rs, K);
-                    const float2 uv = xencode(px[tt][r] - ls[3 * l], py[tt][r] - ls[3 * l + 1],
-                                              pz[tt][r] - ls[3 * l + 2]);
-                    in[tt][r][0] = uv.x;
-                    in[tt][r][1] = uv.y;
-                    in[tt][r][2] = nf_rho(si[tt][r].t, rs, K);
-                }
-            nf_field32(wb, fb, in, T);
-#pragma unroll
-            for (int tt = 0; tt < 2; ++tt)
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const SampleIndex &sx = si[tt][r];
-                    float Tl = T[tt][r];
-                    if (sx.t == 0.0f) Tl = 1.0f;
-                    else if (mask && mask[(int64_t)l * n_tiles + (sx.ci / tile) * tx + (sx.cj / tile)]) {
-                        // exact trilinear lookup in the fallback atlas
-                        const int j0 = min(max(sx.bj, 0), W - 1), j1 = min(max(sx.bj + 1, 0), W - 1);
-                        const int i0 = min(max(sx.bi, 0), H - 1), i1 = min(max(sx.bi + 1, 0), H - 1);
-                        int k0, k1;
-                        float wt;
-                        if (sx.k < 0) { k0 = k1 = 0; wt = 0.f; }
-                        else if (sx.k >= K - 1) { k0 = k1 = K - 1; wt = 0.f; }
-                        else { k0 = sx.k; k1 = sx.k + 1; wt = (sx.t - rs[k0]) / (rs[k1] - rs[k0]); }
-                        const float *A0 = atlas + (int64_t)l * K * plane + k0 * plane;
-                        const float *A1 = atlas + (int64_t)l * K * plane + k1 * plane;
-                        const float fx = sx.fx, fy = sx.fy;
-                        const float b0 = (1 - fy) * ((1 - fx) * A0[i0 * W + j0] + fx * A0[i0 * W + j1]) +
-                                         fy * ((1 - fx) * A0[i1 * W + j0] + fx * A0[i1 * W + j1]);
-                        const float b1 = (1 - fy) * ((1 - fx) * A1[i0 * W + j0] + fx * A1[i0 * W + j1]) +
-                                         fy * ((1 - fx) * A1[i1 * W + j0] + fx * A1[i1 * W + j1]);
-                        Tl = (1 - wt) * b0 + wt * b1;
-                    }
-                    const int64_t q = base + 16 * tt + g + 8 * r;
-                    if (Tout && q < Q && (lane & 3) == 0) Tout[q * L + l] = Tl;
-                    acc[tt][r] = fmaf(wl[l], Tl, acc[tt][r]);
-                }
-        }
-        if ((lane & 3) == 0)
-#pragma unroll
-            for (int tt = 0; tt < 2; ++tt)
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const int64_t q = base + 16 * tt + g + 8 * r;
-                    if (q >= Q) continue;
-                    if (!last) {
-                        accum[q] = acc[tt][r];
-                        continue;
-                    }
-                    const float f = 1.0f - wd + wd * acc[tt][r];
-                    const float c0 = cin[3 * q], c1 = cin[3 * q + 1], c2 = cin[3 * q + 2];
-                    cout[3 * q] = c0 * f;
-                    cout[3 * q + 1] = c1 * f;
-                    cout[3 * q + 2] = c2 * f;
-                }
-    }
 }
 
 // He-uniform initial weights U(-sqrt(6/fan_in), +sqrt(6/fan_in)), zero biases.
@@ -666,16 +323,6 @@ __global__ void nf_init_kernel(unsigned long long seed, float *__restrict__ para
     const unsigned long long r = splitmix64(seed * (unsigned long long)NF_PARAMS + (unsigned long long)p);
     const float u01 = (float)(r >> 40) * (1.0f / 16777216.0f);  // 24 random bits
     params[p] = (2.0f * u01 - 1.0f) * sqrtf(6.0f / (float)fan_in);
-}
-
-int set_infer_smem(dgsm_ctx *ctx) {
-    cudaError_t e = cudaFuncSetAttribute(nf_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)IF_SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(nf_tile_error_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)IF_SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(nf_attenuate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(NF_LGROUP * IF_SMEM));
-    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "nf: smem attribute");
 }
 
 // scratch: per-sample rows + partial gradients of n_split splits
@@ -702,6 +349,402 @@ int run_fwdbwd(dgsm_ctx *ctx, const float *params, const float *atlas, int H, in
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "nf forward/backward");
 }
+
+// ---------------------------------------------------------------------------
+// Inference on the 5th-generation tensor cores (tcgen05).
+//
+// One warpgroup (128 threads) per CTA; thread t owns row t of a 128-row tile
+// (one query, voxel or input).  Per layer, the row's inputs (bf16) are written
+// to shared memory in the no-swizzle K-major canonical layout (8-row x 16-byte
+// core matrices; element (r, k) at (r/8) SBO + (k/8) 128 + (r%8) 16 + (k%8) 2),
+// one thread issues the MMAs (M = 128, N = 64, K = 16 each; kind::f16, bf16 in,
+// f32 out) into a 64-column TMEM accumulator and commits them to an mbarrier,
+// and every thread reads its row back with tcgen05.ld for the bias, ReLU and
+// bf16 rounding of the next layer's input.  The weights of the CTA's light
+// stay in shared memory in the same layout (B operands: W[out][in], K-major).
+// ---------------------------------------------------------------------------
+namespace tc {
+
+constexpr int TM = 128;
+constexpr int WG = 2;                 // warpgroups per CTA, each with its own tile in flight
+constexpr int THREADS = 128 * WG;
+constexpr uint32_t W1_BYTES = NF_HID * NF_FEAT * 2;   // 12288
+constexpr uint32_t WL_BYTES = NF_HID * NF_HID * 2;    // 8192
+constexpr uint32_t A_BYTES = TM * NF_FEAT * 2;        // 24576
+constexpr uint32_t OFF_SW1 = 0;
+constexpr uint32_t OFF_SW2 = OFF_SW1 + W1_BYTES;
+constexpr uint32_t OFF_SA = OFF_SW2 + 3 * WL_BYTES;   // 36864: one A tile per warpgroup
+constexpr uint32_t OFF_FB = OFF_SA + WG * A_BYTES;    // biases 4x64, w5 64, b5
+constexpr uint32_t OFF_BAR = OFF_FB + (5 * NF_HID + 4) * 4;  // one mbarrier per warpgroup
+constexpr uint32_t SMEM = OFF_BAR + 8 * WG + 128;     // + alignment slack
+// instruction descriptor: f32 accumulate, bf16 A and B, both K-major, N = 64, M = 128
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+constexpr long long WAIT_LIMIT = 1ll << 24;
+
+__device__ __forceinline__ uint32_t canon(int r, int k, uint32_t sbo) {
+    return (uint32_t)(r >> 3) * sbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+
+// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets in 16-byte units, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
+           ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        :
+        : "r"(dtmem), "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc));
+}
+
+__device__ __forceinline__ void commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void bar_init(uint32_t bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Bounded wait for phase `parity` of the mbarrier; false on timeout.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+    for (long long it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 32 consecutive fp32 columns of this thread's TMEM lane
+__device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Stage one light's weights: W1 (64 x 96), W2..W4 (64 x 64) as bf16 B operands
+// in the canonical layout, biases, bf16-rounded w5 and b5 as floats.
+__device__ void stage_weights(const float *__restrict__ params, char *sm) {
+    for (int e = threadIdx.x; e < NF_HID * NF_FEAT; e += blockDim.x) {
+        const int n = e / NF_FEAT, k = e - n * NF_FEAT;
+        *reinterpret_cast<__nv_bfloat16 *>(sm + OFF_SW1 + canon(n, k, (NF_FEAT / 8) * 128)) =
+            __float2bfloat16_rn(params[OFF_W1 + e]);
+    }
+    for (int e = threadIdx.x; e < 3 * NF_HID * NF_HID; e += blockDim.x) {
+        const int l = e / (NF_HID * NF_HID), q = e - l * NF_HID * NF_HID, n = q / NF_HID, k = q - n * NF_HID;
+        const int src = (l == 0 ? OFF_W2 : l == 1 ? OFF_W3 : OFF_W4) + q;
+        *reinterpret_cast<__nv_bfloat16 *>(sm + OFF_SW2 + l * WL_BYTES + canon(n, k, (NF_HID / 8) * 128)) =
+            __float2bfloat16_rn(params[src]);
+    }
+    float *fb = reinterpret_cast<float *>(sm + OFF_FB);
+    for (int e = threadIdx.x; e < 4 * NF_HID; e += blockDim.x) {
+        const int l = e / NF_HID, o = e - l * NF_HID;
+        fb[e] = params[(l == 0 ? OFF_B1 : l == 1 ? OFF_B2 : l == 2 ? OFF_B3 : OFF_B4) + o];
+    }
+    for (int e = threadIdx.x; e < NF_HID; e += blockDim.x) fb[4 * NF_HID + e] = bf16r(params[OFF_W5 + e]);
+    if (threadIdx.x == 0) fb[5 * NF_HID] = params[OFF_B5];
+}
+
+// sin and cos of pi p for the float32 phase p = f x reduced exactly to
+// [-1, 1] half-turns, by the SFU (absolute error ~1e-6, far below the
+// bfloat16 spacing the feature is rounded to next).
+__device__ __forceinline__ void sincos_sfu(float f, float x, float &s, float &c) {
+    float p = __fmul_rn(f, x);
+    p -= 2.0f * rintf(0.5f * p);
+    const float a = p * 3.14159265358979f;
+    s = __sinf(a);
+    c = __cosf(a);
+}
+
+// The 96 bf16 features of (u, v, rho) as row r of the layer-1 A tile:
+// k = 32 axis + m (sin), 32 axis + 16 + m (cos); 8 features per 16-byte store.
+__device__ __forceinline__ void write_features(char *sA, int r, float u, float v, float rho) {
+    const float x[3] = {u, v, rho};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {   // frequencies 8h .. 8h+7
+            float sn[8], cs[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) sincos_sfu(nf_freq(8 * h + m), x[a], sn[m], cs[m]);
+            uint4 ws, wc;
+            ws.x = pack_bf16(sn[0], sn[1]); ws.y = pack_bf16(sn[2], sn[3]);
+            ws.z = pack_bf16(sn[4], sn[5]); ws.w = pack_bf16(sn[6], sn[7]);
+            wc.x = pack_bf16(cs[0], cs[1]); wc.y = pack_bf16(cs[2], cs[3]);
+            wc.z = pack_bf16(cs[4], cs[5]); wc.w = pack_bf16(cs[6], cs[7]);
+            *reinterpret_cast<uint4 *>(sA + canon(r, 32 * a + 8 * h, (NF_FEAT / 8) * 128)) = ws;
+            *reinterpret_cast<uint4 *>(sA + canon(r, 32 * a + 16 + 8 * h, (NF_FEAT / 8) * 128)) = wc;
+        }
+    }
+}
+
+// Issue one layer's MMAs (K = kdim) and commit them to the barrier.
+__device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t a_saddr, uint32_t b_saddr, int kdim,
+                                            uint32_t bar) {
+    const uint32_t sbo = (uint32_t)(kdim / 8) * 128u;
+    for (int s = 0; s < kdim / 16; ++s)
+        mma(tmem, sdesc(a_saddr + 256u * s, 128u, sbo), sdesc(b_saddr + 256u * s, 128u, sbo), s > 0 ? 1u : 0u);
+    commit(bar);
+}
+
+// Hidden-layer epilogue of row r: h = bf16(ReLU(z + b)) into the A tile (K = 64).
+__device__ __forceinline__ void hidden_epilogue(uint32_t trow, const float *b, char *sA, int r) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        float z[32];
+        ld32(trow + 32u * half, z);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int c0 = 32 * half + 8 * g;
+            uint4 w;
+            w.x = pack_bf16(fmaxf(z[8 * g + 0] + b[c0 + 0], 0.f), fmaxf(z[8 * g + 1] + b[c0 + 1], 0.f));
+            w.y = pack_bf16(fmaxf(z[8 * g + 2] + b[c0 + 2], 0.f), fmaxf(z[8 * g + 3] + b[c0 + 3], 0.f));
+            w.z = pack_bf16(fmaxf(z[8 * g + 4] + b[c0 + 4], 0.f), fmaxf(z[8 * g + 5] + b[c0 + 5], 0.f));
+            w.w = pack_bf16(fmaxf(z[8 * g + 6] + b[c0 + 6], 0.f), fmaxf(z[8 * g + 7] + b[c0 + 7], 0.f));
+            *reinterpret_cast<uint4 *>(sA + canon(r, c0, (NF_HID / 8) * 128)) = w;
+        }
+    }
+}
+
+// Output of row r: sigmoid(w5 . bf16(ReLU(z4 + b4)) + b5).
+__device__ __forceinline__ float output_epilogue(uint32_t trow, const float *fb) {
+    const float *b4 = fb + 3 * NF_HID, *w5 = fb + 4 * NF_HID;
+    float y = 0.0f;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        float z[32];
+        ld32(trow + 32u * half, z);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int c = 32 * half + i;
+            y = fmaf(w5[c], bf16r(fmaxf(z[i] + b4[c], 0.f)), y);
+        }
+    }
+    return 1.0f / (1.0f + expf(-(y + fb[5 * NF_HID])));
+}
+
+// Barrier of one warpgroup (named barrier 1 + g, 128 threads).
+__device__ __forceinline__ void wg_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
+
+// The field for the warpgroup's current tile: its A tile already holds the
+// features.  r = row (thread within the warpgroup).  Returns false if an
+// MMA completion wait timed out.
+__device__ __forceinline__ bool run_mlp(char *sm, uint32_t sbase, int g, int r, uint32_t tmem, uint32_t &phase,
+                                        float &T) {
+    const int warp = r >> 5;
+    const float *fb = reinterpret_cast<const float *>(sm + OFF_FB);
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    const uint32_t a_off = OFF_SA + (uint32_t)g * A_BYTES, bar = sbase + OFF_BAR + 8u * g;
+    char *sA = sm + a_off;
+    bool ok = true;
+    for (int layer = 0; layer < 4; ++layer) {
+        fence_async_smem();
+        fence_before();
+        wg_sync(g);
+        if (r == 0) {
+            fence_after();
+            issue_layer(tmem, sbase + a_off, sbase + (layer == 0 ? OFF_SW1 : OFF_SW2 + (layer - 1) * WL_BYTES),
+                        layer == 0 ? NF_FEAT : NF_HID, bar);
+        }
+        ok = bar_wait(bar, phase) && ok;
+        phase ^= 1u;
+        fence_after();
+        if (layer < 3) hidden_epilogue(trow, fb + layer * NF_HID, sA, r);
+        else T = output_epilogue(trow, fb);
+    }
+    fence_before();
+    wg_sync(g);  // TMEM and A are free for the next tile
+    return ok;
+}
+
+enum Mode { MODE_UVR = 0, MODE_VOXEL_ERR = 1, MODE_QUERY = 2 };
+
+// MODE_UVR: T_out[i] = field(uvr[i]) for i < n.
+// MODE_VOXEL_ERR: one atlas tile per work unit, tile_err[t] = max |field - atlas|
+//   over its tile x tile texels x K shells.
+// MODE_QUERY: light l = blockIdx.x % L; per query q, T_all[l Q + q] = the
+//   field at (u, v, rho) of q seen from light l, or the exact trilinear atlas
+//   lookup where mask[l][tile of q's texel cell] is set.
+template <int MODE>
+__global__ void __launch_bounds__(THREADS, 2) field_kernel(
+    const float *__restrict__ params, int n_params_stride, int64_t n, const float *__restrict__ uvr,
+    const float *__restrict__ atlas, int H, int W, int K, int tile, int tx, int n_tiles,
+    const float *__restrict__ radii, const float *__restrict__ lights, int L, const uint8_t *__restrict__ mask,
+    float *__restrict__ out, int *__restrict__ status) {
+    extern __shared__ __align__(1024) char smem_raw[];
+    char *sm = reinterpret_cast<char *>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
+    __shared__ uint32_t s_tmem;
+    __shared__ float rs[256];
+    __shared__ float s_err[WG];
+    const int tid = threadIdx.x, warp = tid >> 5, g = tid >> 7, r = tid & 127;
+    const int l = MODE == MODE_QUERY ? (int)(blockIdx.x % (unsigned)L) : 0;
+    // work units (tiles of 128 rows) are dealt to warpgroups
+    const int cta = MODE == MODE_QUERY ? (int)(blockIdx.x / (unsigned)L) : (int)blockIdx.x;
+    const int n_cta = MODE == MODE_QUERY ? (int)(gridDim.x / (unsigned)L) : (int)gridDim.x;
+    const int wgi = cta * WG + g, n_wg = n_cta * WG;
+    stage_weights(params + (int64_t)l * n_params_stride, sm);
+    if (MODE == MODE_QUERY)
+        for (int k = tid; k < K; k += blockDim.x) rs[k] = radii[k];
+    if (tid < WG) bar_init(sbase + OFF_BAR + 8u * tid);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&s_tmem)), "r"(64u * WG)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = s_tmem + 64u * g;   // this warpgroup's 64 columns
+    uint32_t phase = 0;
+    bool ok = true;
+    char *sA = sm + OFF_SA + (uint32_t)g * A_BYTES;
+    if (MODE == MODE_UVR || MODE == MODE_QUERY) {
+        float ox = 0.f, oy = 0.f, oz = 0.f;
+        if (MODE == MODE_QUERY) { ox = lights[3 * l]; oy = lights[3 * l + 1]; oz = lights[3 * l + 2]; }
+        for (int64_t base = (int64_t)wgi * TM; base < n; base += (int64_t)n_wg * TM) {
+            const int64_t q = base + r;
+            const bool valid = q < n;
+            float u = 0.f, v = 0.f, rho = 0.f;
+            SampleIndex si;
+            si.t = 0.f;
+            if (valid) {
+                if (MODE == MODE_UVR) {
+                    u = uvr[3 * q]; v = uvr[3 * q + 1]; rho = uvr[3 * q + 2];
+                } else {
+                    const float px = uvr[3 * q], py = uvr[3 * q + 1], pz = uvr[3 * q + 2];
+                    si = sample_index(px, py, pz, ox, oy, oz, H, W, rs, K);
+                    const float2 e = xencode(px - ox, py - oy, pz - oz);
+                    u = e.x; v = e.y;
+                    rho = nf_rho(si.t, rs, K);
+                }
+            }
+            write_features(sA, r, u, v, rho);
+            float T = 0.f;
+            ok = run_mlp(sm, sbase, g, r, tmem, phase, T) && ok;
+            if (!valid) continue;
+            if (MODE == MODE_UVR) {
+                out[q] = T;
+            } else {
+                if (si.t == 0.0f) T = 1.0f;
+                else if (mask && mask[(int64_t)l * n_tiles + (si.ci / tile) * tx + (si.cj / tile)]) {
+                    const int j0 = min(max(si.bj, 0), W - 1), j1 = min(max(si.bj + 1, 0), W - 1);
+                    const int i0 = min(max(si.bi, 0), H - 1), i1 = min(max(si.bi + 1, 0), H - 1);
+                    int k0, k1;
+                    float wt;
+                    if (si.k < 0) { k0 = k1 = 0; wt = 0.f; }
+                    else if (si.k >= K - 1) { k0 = k1 = K - 1; wt = 0.f; }
+                    else { k0 = si.k; k1 = si.k + 1; wt = (si.t - rs[k0]) / (rs[k1] - rs[k0]); }
+                    const int64_t plane = (int64_t)H * W;
+                    const float *A0 = atlas + (int64_t)l * K * plane + k0 * plane;
+                    const float *A1 = atlas + (int64_t)l * K * plane + k1 * plane;
+                    const float fx = si.fx, fy = si.fy;
+                    const float b0 = (1 - fy) * ((1 - fx) * A0[i0 * W + j0] + fx * A0[i0 * W + j1]) +
+                                     fy * ((1 - fx) * A0[i1 * W + j0] + fx * A0[i1 * W + j1]);
+                    const float b1 = (1 - fy) * ((1 - fx) * A1[i0 * W + j0] + fx * A1[i0 * W + j1]) +
+                                     fy * ((1 - fx) * A1[i1 * W + j0] + fx * A1[i1 * W + j1]);
+                    T = (1 - wt) * b0 + wt * b1;
+                }
+                out[(int64_t)l * n + q] = T;
+            }
+        }
+    } else {
+        // atlas tiles as work units of a warpgroup; a tile's voxels in rows of 128
+        for (int t = wgi; t < n_tiles; t += n_wg) {
+            const int ti = t / tx, tj = t - ti * tx;
+            const int i0 = ti * tile, j0 = tj * tile;
+            const int hh = min(tile, H - i0), ww = min(tile, W - j0);
+            const int nvox = hh * ww * K;
+            float worst = 0.f;
+            for (int vb = 0; vb < nvox; vb += TM) {
+                const int e = vb + r;
+                const bool valid = e < nvox;
+                const int ee = valid ? e : 0;
+                const int k = ee / (hh * ww), rem = ee - k * hh * ww;
+                const int i = i0 + rem / ww, j = j0 + rem % ww;
+                const float u = (2.0f * j + 1.0f) / W - 1.0f, v = (2.0f * i + 1.0f) / H - 1.0f;
+                const float rho = K > 1 ? (float)k / (float)(K - 1) : 0.0f;
+                write_features(sA, r, u, v, rho);
+                float T = 0.f;
+                ok = run_mlp(sm, sbase, g, r, tmem, phase, T) && ok;
+                if (valid) worst = fmaxf(worst, fabsf(T - atlas[((int64_t)k * H + i) * W + j]));
+            }
+            for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+            if (r == 0) s_err[g] = 0.f;
+            wg_sync(g);
+            if ((r & 31) == 0) atomicMax(reinterpret_cast<int *>(&s_err[g]), __float_as_int(worst));
+            wg_sync(g);
+            if (r == 0) out[t] = s_err[g];
+        }
+    }
+    if (!ok && tid == 0) record_status(status, DGSM_ERR_TIMEOUT);
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(64u * WG)
+                     : "memory");
+    }
+}
+
+template <int MODE>
+int launch_field(dgsm_ctx *ctx, int grid, cudaStream_t s, const float *params, int stride, int64_t n,
+                 const float *uvr, const float *atlas, int H, int W, int K, int tile, int tx, int n_tiles,
+                 const float *radii, const float *lights, int L, const uint8_t *mask, float *out) {
+    cudaError_t e = cudaFuncSetAttribute(field_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "nf: tcgen05 smem attribute");
+    field_kernel<MODE><<<grid, THREADS, SMEM, s>>>(params, stride, n, uvr, atlas, H, W, K, tile, tx, n_tiles,
+                                                    radii, lights, L, mask, out, ctx->d_status);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "nf: tcgen05 field kernel");
+}
+
+// c' = c (1 - wd + wd sum_l w_l T_all[l][q]); optional T_out[q][l].
+__global__ void combine_kernel(const float *__restrict__ T_all, int L, int64_t Q, const float *__restrict__ lw,
+                               float wd, const float *cin, float *cout, float *__restrict__ Tout) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += (int64_t)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int l = 0; l < L; ++l) {
+            const float T = T_all[(int64_t)l * Q + q];
+            if (Tout) Tout[q * L + l] = T;
+            acc = fmaf(lw ? lw[l] : 1.0f / (float)L, T, acc);
+        }
+        const float f = 1.0f - wd + wd * acc;
+        const float c0 = cin[3 * q], c1 = cin[3 * q + 1], c2 = cin[3 * q + 2];
+        cout[3 * q] = c0 * f;
+        cout[3 * q + 1] = c1 * f;
+        cout[3 * q + 2] = c2 * f;
+    }
+}
+
+}  // namespace tc
 
 }  // namespace
 }  // namespace dgsm
@@ -775,16 +818,14 @@ extern "C" int nf_train(dgsm_ctx *ctx, const float *atlas, int32_t H, int32_t W,
 extern "C" int nf_forward(dgsm_ctx *ctx, const float *params, const float *uvr, int64_t n, float *T_out,
                           void *stream) {
     if (!ctx) return DGSM_ERR_INVALID_ARG;
-    if (n < 0 || (n > 0 && (!params || !uvr || !T_out))) return fail(ctx, DGSM_ERR_INVALID_ARG, "nf_forward: bad arguments");
+    if (n < 0 || !params || (n > 0 && (!uvr || !T_out))) return fail(ctx, DGSM_ERR_INVALID_ARG, "nf_forward: bad arguments");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
     if (n == 0) return DGSM_OK;
-    int rc = set_infer_smem(ctx);
-    if (rc) return rc;
-    const int grid = (int)std::min<int64_t>((n + IF_THREADS - 1) / IF_THREADS, (int64_t)ctx->num_sms * 8);
-    nf_infer_kernel<<<grid, IF_THREADS, IF_SMEM, (cudaStream_t)stream>>>(params, uvr, n, T_out);
-    e = cudaGetLastError();
-    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "nf_infer_kernel");
+    const int per_cta = tc::TM * tc::WG;
+    const int grid = (int)std::min<int64_t>((n + per_cta - 1) / per_cta, (int64_t)ctx->num_sms * 2);
+    return tc::launch_field<tc::MODE_UVR>(ctx, grid, (cudaStream_t)stream, params, NF_PARAMS, n, uvr, nullptr, 0, 0,
+                                          0, 1, 1, 0, nullptr, nullptr, 1, nullptr, T_out);
 }
 
 extern "C" int nf_tile_error(dgsm_ctx *ctx, const float *params, const float *atlas, int32_t H, int32_t W,
@@ -794,13 +835,10 @@ extern "C" int nf_tile_error(dgsm_ctx *ctx, const float *params, const float *at
         return fail(ctx, DGSM_ERR_INVALID_ARG, "nf_tile_error: bad arguments");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
-    int rc = set_infer_smem(ctx);
-    if (rc) return rc;
     const int tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
-    nf_tile_error_kernel<<<tx * ty, IF_THREADS, IF_SMEM, (cudaStream_t)stream>>>(params, atlas, H, W, K, tile,
-                                                                                tx, tile_err);
-    e = cudaGetLastError();
-    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "nf_tile_error_kernel");
+    const int grid = std::max(1, std::min((tx * ty + tc::WG - 1) / tc::WG, ctx->num_sms * 2));
+    return tc::launch_field<tc::MODE_VOXEL_ERR>(ctx, grid, (cudaStream_t)stream, params, NF_PARAMS, 0, nullptr, atlas,
+                                                H, W, K, tile, tx, tx * ty, nullptr, nullptr, 1, nullptr, tile_err);
 }
 
 extern "C" int nf_attenuate(dgsm_ctx *ctx, const float *params, const uint8_t *mask, const float *atlas,
@@ -817,22 +855,21 @@ extern "C" int nf_attenuate(dgsm_ctx *ctx, const float *params, const uint8_t *m
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
     if (n_q == 0) return DGSM_OK;
-    int rc = set_infer_smem(ctx);
+    cudaStream_t s = (cudaStream_t)stream;
+    void *p;
+    int rc = ws_reserve(ctx, WS_NF_ACC, sizeof(float) * (size_t)L * n_q, &p);
     if (rc) return rc;
+    float *T_all = (float *)p;
     const int tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
-    const int grid = (int)std::min<int64_t>((n_q + NA_THREADS - 1) / NA_THREADS, (int64_t)ctx->num_sms);
-    float *accum = nullptr;
-    if (L > NF_LGROUP) {
-        void *p;
-        if ((rc = ws_reserve(ctx, WS_NF_ACC, sizeof(float) * (size_t)n_q, &p))) return rc;
-        accum = (float *)p;
-    }
-    for (int l0 = 0; l0 < L; l0 += NF_LGROUP) {
-        const int LG = std::min(NF_LGROUP, L - l0);
-        nf_attenuate_kernel<<<grid, NA_THREADS, LG * IF_SMEM, (cudaStream_t)stream>>>(
-            params, NF_PARAMS, mask, atlas, L, l0, LG, H, W, radii, K, tile, tx, tx * ty, lights, q_means,
-            colors_in, n_q, light_w, direct_frac, colors_out, T_out, accum);
-    }
+    // CTAs per light: enough for two per SM in all, no more than the light's tiles of rows
+    const int64_t rows_per_cta = tc::TM * tc::WG;
+    const int per_light = (int)std::max<int64_t>(
+        1, std::min<int64_t>((n_q + rows_per_cta - 1) / rows_per_cta, std::max(1, 2 * ctx->num_sms / L)));
+    rc = tc::launch_field<tc::MODE_QUERY>(ctx, per_light * L, s, params, NF_PARAMS, n_q, q_means, atlas, H, W, K,
+                                          tile, tx, tx * ty, radii, lights, L, mask, T_all);
+    if (rc) return rc;
+    const int cgrid = (int)std::min<int64_t>((n_q + 255) / 256, (int64_t)ctx->num_sms * 8);
+    tc::combine_kernel<<<cgrid, 256, 0, s>>>(T_all, L, n_q, light_w, direct_frac, colors_in, colors_out, T_out);
     e = cudaGetLastError();
-    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "nf_attenuate_kernel");
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "nf: combine kernel");
 }

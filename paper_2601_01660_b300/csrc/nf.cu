@@ -368,18 +368,27 @@ namespace tc {
 constexpr int TM = 128;
 constexpr int WG = 2;                 // warpgroups per CTA, each with its own tile in flight
 constexpr int THREADS = 128 * WG;
-constexpr uint32_t W1_BYTES = NF_HID * NF_FEAT * 2;   // 12288
-constexpr uint32_t WL_BYTES = NF_HID * NF_HID * 2;    // 8192
-constexpr uint32_t A_BYTES = TM * NF_FEAT * 2;        // 24576
+// K of each layer: inputs, then two constant-1 columns that carry the bias as
+// a bfloat16 hi + lo pair (exact to ~2^-18 relative), padded to 16
+constexpr int K1 = NF_FEAT + 16;      // 112
+constexpr int KH = NF_HID + 16;       // 80
+constexpr int N5 = 16;                // output layer: column 0 = w5, the rest zero
+constexpr uint32_t SBO1 = (K1 / 8) * 128;   // 1792
+constexpr uint32_t SBOH = (KH / 8) * 128;   // 1280
+constexpr uint32_t W1_BYTES = NF_HID * K1 * 2;   // 14336
+constexpr uint32_t WL_BYTES = NF_HID * KH * 2;   // 10240
+constexpr uint32_t W5_BYTES = N5 * KH * 2;       // 2560
+constexpr uint32_t A_BYTES = TM * K1 * 2;        // 28672 (also holds the K = 80 layout)
 constexpr uint32_t OFF_SW1 = 0;
 constexpr uint32_t OFF_SW2 = OFF_SW1 + W1_BYTES;
-constexpr uint32_t OFF_SA = OFF_SW2 + 3 * WL_BYTES;   // 36864: one A tile per warpgroup
-constexpr uint32_t OFF_FB = OFF_SA + WG * A_BYTES;    // biases 4x64, w5 64, b5
-constexpr uint32_t OFF_BAR = OFF_FB + (5 * NF_HID + 4) * 4;  // one mbarrier per warpgroup
+constexpr uint32_t OFF_SW5 = OFF_SW2 + 3 * WL_BYTES;
+constexpr uint32_t OFF_SA = OFF_SW5 + W5_BYTES;       // one A tile per warpgroup
+constexpr uint32_t OFF_BAR = OFF_SA + WG * A_BYTES;   // one mbarrier per warpgroup
 constexpr uint32_t SMEM = OFF_BAR + 8 * WG + 128;     // + alignment slack
-// instruction descriptor: f32 accumulate, bf16 A and B, both K-major, N = 64, M = 128
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
-                           ((uint32_t)(128 >> 4) << 24);
+// instruction descriptors: f32 accumulate, bf16 A and B, both K-major, M = 128
+constexpr uint32_t idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
 constexpr long long WAIT_LIMIT = 1ll << 24;
 
 __device__ __forceinline__ uint32_t canon(int r, int k, uint32_t sbo) {
@@ -393,12 +402,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
            ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
 }
 
-__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t id, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
         :
-        : "r"(dtmem), "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc));
+        : "r"(dtmem), "l"(adesc), "l"(bdesc), "r"(id), "r"(acc));
 }
 
 __device__ __forceinline__ void commit(uint32_t bar) {
@@ -447,27 +456,48 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Stage one light's weights: W1 (64 x 96), W2..W4 (64 x 64) as bf16 B operands
-// in the canonical layout, biases, bf16-rounded w5 and b5 as floats.
+// one fp32 column of this thread's TMEM lane
+__device__ __forceinline__ float ld1(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    return __uint_as_float(r);
+}
+
+// bf16 pair (lo in the low half) of ReLU(lo), ReLU(hi)
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+__device__ __forceinline__ void st_bf16(char *sm, uint32_t off, float x) {
+    *reinterpret_cast<__nv_bfloat16 *>(sm + off) = __float2bfloat16_rn(x);
+}
+
+// Stage one light's weights as bf16 B operands (rows = outputs, K-major):
+// [W_l | b_hi b_lo 0 ...] for the four hidden layers and [w5 | b5_hi b5_lo 0 ...]
+// as row 0 of the 16-row output operand.
 __device__ void stage_weights(const float *__restrict__ params, char *sm) {
-    for (int e = threadIdx.x; e < NF_HID * NF_FEAT; e += blockDim.x) {
-        const int n = e / NF_FEAT, k = e - n * NF_FEAT;
-        *reinterpret_cast<__nv_bfloat16 *>(sm + OFF_SW1 + canon(n, k, (NF_FEAT / 8) * 128)) =
-            __float2bfloat16_rn(params[OFF_W1 + e]);
+    for (int e = threadIdx.x; e < NF_HID * K1; e += blockDim.x) {
+        const int n = e / K1, k = e - n * K1;
+        const float b = params[OFF_B1 + n], bh = bf16r(b);
+        const float v = k < NF_FEAT ? params[OFF_W1 + n * NF_FEAT + k] : k == NF_FEAT ? bh : k == NF_FEAT + 1 ? b - bh : 0.f;
+        st_bf16(sm, OFF_SW1 + canon(n, k, SBO1), v);
     }
-    for (int e = threadIdx.x; e < 3 * NF_HID * NF_HID; e += blockDim.x) {
-        const int l = e / (NF_HID * NF_HID), q = e - l * NF_HID * NF_HID, n = q / NF_HID, k = q - n * NF_HID;
-        const int src = (l == 0 ? OFF_W2 : l == 1 ? OFF_W3 : OFF_W4) + q;
-        *reinterpret_cast<__nv_bfloat16 *>(sm + OFF_SW2 + l * WL_BYTES + canon(n, k, (NF_HID / 8) * 128)) =
-            __float2bfloat16_rn(params[src]);
+    for (int e = threadIdx.x; e < 3 * NF_HID * KH; e += blockDim.x) {
+        const int l = e / (NF_HID * KH), q = e - l * NF_HID * KH, n = q / KH, k = q - n * KH;
+        const int w = l == 0 ? OFF_W2 : l == 1 ? OFF_W3 : OFF_W4, bo = l == 0 ? OFF_B2 : l == 1 ? OFF_B3 : OFF_B4;
+        const float b = params[bo + n], bh = bf16r(b);
+        const float v = k < NF_HID ? params[w + n * NF_HID + k] : k == NF_HID ? bh : k == NF_HID + 1 ? b - bh : 0.f;
+        st_bf16(sm, OFF_SW2 + l * WL_BYTES + canon(n, k, SBOH), v);
     }
-    float *fb = reinterpret_cast<float *>(sm + OFF_FB);
-    for (int e = threadIdx.x; e < 4 * NF_HID; e += blockDim.x) {
-        const int l = e / NF_HID, o = e - l * NF_HID;
-        fb[e] = params[(l == 0 ? OFF_B1 : l == 1 ? OFF_B2 : l == 2 ? OFF_B3 : OFF_B4) + o];
+    for (int e = threadIdx.x; e < N5 * KH; e += blockDim.x) {
+        const int n = e / KH, k = e - n * KH;
+        const float b = params[OFF_B5], bh = bf16r(b);
+        const float v = n != 0 ? 0.f : k < NF_HID ? params[OFF_W5 + k] : k == NF_HID ? bh : k == NF_HID + 1 ? b - bh : 0.f;
+        st_bf16(sm, OFF_SW5 + canon(n, k, SBOH), v);
     }
-    for (int e = threadIdx.x; e < NF_HID; e += blockDim.x) fb[4 * NF_HID + e] = bf16r(params[OFF_W5 + e]);
-    if (threadIdx.x == 0) fb[5 * NF_HID] = params[OFF_B5];
 }
 
 // sin and cos of pi p for the float32 phase p = f x reduced exactly to
@@ -481,8 +511,16 @@ __device__ __forceinline__ void sincos_sfu(float f, float x, float &s, float &c)
     c = __cosf(a);
 }
 
+// the constant columns (1, 1, 0, ..., 0) at k0 .. k0 + 15 of row r
+__device__ __forceinline__ void write_ones(char *sA, int r, int k0, uint32_t sbo) {
+    const uint32_t one2 = 0x3F803F80u;  // two bf16 ones
+    *reinterpret_cast<uint4 *>(sA + canon(r, k0, sbo)) = make_uint4(one2 & 0xFFFFFFFFu, 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(sA + canon(r, k0 + 8, sbo)) = make_uint4(0u, 0u, 0u, 0u);
+}
+
 // The 96 bf16 features of (u, v, rho) as row r of the layer-1 A tile:
-// k = 32 axis + m (sin), 32 axis + 16 + m (cos); 8 features per 16-byte store.
+// k = 32 axis + m (sin), 32 axis + 16 + m (cos); 8 features per 16-byte store;
+// then the two bias columns.
 __device__ __forceinline__ void write_features(char *sA, int r, float u, float v, float rho) {
     const float x[3] = {u, v, rho};
 #pragma unroll
@@ -497,85 +535,68 @@ __device__ __forceinline__ void write_features(char *sA, int r, float u, float v
             ws.z = pack_bf16(sn[4], sn[5]); ws.w = pack_bf16(sn[6], sn[7]);
             wc.x = pack_bf16(cs[0], cs[1]); wc.y = pack_bf16(cs[2], cs[3]);
             wc.z = pack_bf16(cs[4], cs[5]); wc.w = pack_bf16(cs[6], cs[7]);
-            *reinterpret_cast<uint4 *>(sA + canon(r, 32 * a + 8 * h, (NF_FEAT / 8) * 128)) = ws;
-            *reinterpret_cast<uint4 *>(sA + canon(r, 32 * a + 16 + 8 * h, (NF_FEAT / 8) * 128)) = wc;
+            *reinterpret_cast<uint4 *>(sA + canon(r, 32 * a + 8 * h, SBO1)) = ws;
+            *reinterpret_cast<uint4 *>(sA + canon(r, 32 * a + 16 + 8 * h, SBO1)) = wc;
         }
     }
+    write_ones(sA, r, NF_FEAT, SBO1);
 }
 
-// Issue one layer's MMAs (K = kdim) and commit them to the barrier.
-__device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t a_saddr, uint32_t b_saddr, int kdim,
+// Issue one layer's MMAs and commit them to the barrier.
+__device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t a_saddr, uint32_t b_saddr, int kdim, int n,
                                             uint32_t bar) {
-    const uint32_t sbo = (uint32_t)(kdim / 8) * 128u;
+    const uint32_t sbo = (uint32_t)(kdim / 8) * 128u, id = idesc(n);
     for (int s = 0; s < kdim / 16; ++s)
-        mma(tmem, sdesc(a_saddr + 256u * s, 128u, sbo), sdesc(b_saddr + 256u * s, 128u, sbo), s > 0 ? 1u : 0u);
+        mma(tmem, sdesc(a_saddr + 256u * s, 128u, sbo), sdesc(b_saddr + 256u * s, 128u, sbo), id, s > 0 ? 1u : 0u);
     commit(bar);
 }
 
-// Hidden-layer epilogue of row r: h = bf16(ReLU(z + b)) into the A tile (K = 64).
-__device__ __forceinline__ void hidden_epilogue(uint32_t trow, const float *b, char *sA, int r) {
+// Hidden-layer epilogue of row r: h = bf16(ReLU(z)) (the bias is in z) into
+// the A tile in the K = 80 layout; after layer 1 also its bias columns.
+__device__ __forceinline__ void hidden_epilogue(uint32_t trow, char *sA, int r, bool first) {
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         float z[32];
         ld32(trow + 32u * half, z);
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
-            const int c0 = 32 * half + 8 * g;
             uint4 w;
-            w.x = pack_bf16(fmaxf(z[8 * g + 0] + b[c0 + 0], 0.f), fmaxf(z[8 * g + 1] + b[c0 + 1], 0.f));
-            w.y = pack_bf16(fmaxf(z[8 * g + 2] + b[c0 + 2], 0.f), fmaxf(z[8 * g + 3] + b[c0 + 3], 0.f));
-            w.z = pack_bf16(fmaxf(z[8 * g + 4] + b[c0 + 4], 0.f), fmaxf(z[8 * g + 5] + b[c0 + 5], 0.f));
-            w.w = pack_bf16(fmaxf(z[8 * g + 6] + b[c0 + 6], 0.f), fmaxf(z[8 * g + 7] + b[c0 + 7], 0.f));
-            *reinterpret_cast<uint4 *>(sA + canon(r, c0, (NF_HID / 8) * 128)) = w;
+            w.x = relu_bf16x2(z[8 * g + 0], z[8 * g + 1]);
+            w.y = relu_bf16x2(z[8 * g + 2], z[8 * g + 3]);
+            w.z = relu_bf16x2(z[8 * g + 4], z[8 * g + 5]);
+            w.w = relu_bf16x2(z[8 * g + 6], z[8 * g + 7]);
+            *reinterpret_cast<uint4 *>(sA + canon(r, 32 * half + 8 * g, SBOH)) = w;
         }
     }
+    if (first) write_ones(sA, r, NF_HID, SBOH);
 }
-
-// Output of row r: sigmoid(w5 . bf16(ReLU(z4 + b4)) + b5).
-__device__ __forceinline__ float output_epilogue(uint32_t trow, const float *fb) {
-    const float *b4 = fb + 3 * NF_HID, *w5 = fb + 4 * NF_HID;
-    float y = 0.0f;
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        float z[32];
-        ld32(trow + 32u * half, z);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const int c = 32 * half + i;
-            y = fmaf(w5[c], bf16r(fmaxf(z[i] + b4[c], 0.f)), y);
-        }
-    }
-    return 1.0f / (1.0f + expf(-(y + fb[5 * NF_HID])));
-}
-
-// Barrier of one warpgroup (named barrier 1 + g, 128 threads).
-__device__ __forceinline__ void wg_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
 
 // The field for the warpgroup's current tile: its A tile already holds the
 // features.  r = row (thread within the warpgroup).  Returns false if an
 // MMA completion wait timed out.
-__device__ __forceinline__ bool run_mlp(char *sm, uint32_t sbase, int g, int r, uint32_t tmem, uint32_t &phase,
+__device__ __forceinline__ void wg_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
+
+__device__ __forceinline__ bool run_mlp(uint32_t sbase, char *sA, int g, int r, uint32_t tmem, uint32_t &phase,
                                         float &T) {
     const int warp = r >> 5;
-    const float *fb = reinterpret_cast<const float *>(sm + OFF_FB);
     const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-    const uint32_t a_off = OFF_SA + (uint32_t)g * A_BYTES, bar = sbase + OFF_BAR + 8u * g;
-    char *sA = sm + a_off;
+    const uint32_t a_saddr = sbase + OFF_SA + (uint32_t)g * A_BYTES, bar = sbase + OFF_BAR + 8u * g;
     bool ok = true;
-    for (int layer = 0; layer < 4; ++layer) {
+    for (int layer = 0; layer < 5; ++layer) {
         fence_async_smem();
         fence_before();
         wg_sync(g);
         if (r == 0) {
             fence_after();
-            issue_layer(tmem, sbase + a_off, sbase + (layer == 0 ? OFF_SW1 : OFF_SW2 + (layer - 1) * WL_BYTES),
-                        layer == 0 ? NF_FEAT : NF_HID, bar);
+            if (layer == 0) issue_layer(tmem, a_saddr, sbase + OFF_SW1, K1, NF_HID, bar);
+            else if (layer < 4) issue_layer(tmem, a_saddr, sbase + OFF_SW2 + (layer - 1) * WL_BYTES, KH, NF_HID, bar);
+            else issue_layer(tmem, a_saddr, sbase + OFF_SW5, KH, N5, bar);
         }
         ok = bar_wait(bar, phase) && ok;
         phase ^= 1u;
         fence_after();
-        if (layer < 3) hidden_epilogue(trow, fb + layer * NF_HID, sA, r);
-        else T = output_epilogue(trow, fb);
+        if (layer < 4) hidden_epilogue(trow, sA, r, layer == 0);
+        else T = 1.0f / (1.0f + expf(-ld1(trow)));
     }
     fence_before();
     wg_sync(g);  // TMEM and A are free for the next tile
@@ -647,7 +668,7 @@ __global__ void __launch_bounds__(THREADS, 2) field_kernel(
             }
             write_features(sA, r, u, v, rho);
             float T = 0.f;
-            ok = run_mlp(sm, sbase, g, r, tmem, phase, T) && ok;
+            ok = run_mlp(sbase, sA, g, r, tmem, phase, T) && ok;
             if (!valid) continue;
             if (MODE == MODE_UVR) {
                 out[q] = T;
@@ -692,7 +713,7 @@ __global__ void __launch_bounds__(THREADS, 2) field_kernel(
                 const float rho = K > 1 ? (float)k / (float)(K - 1) : 0.0f;
                 write_features(sA, r, u, v, rho);
                 float T = 0.f;
-                ok = run_mlp(sm, sbase, g, r, tmem, phase, T) && ok;
+                ok = run_mlp(sbase, sA, g, r, tmem, phase, T) && ok;
                 if (valid) worst = fmaxf(worst, fabsf(T - atlas[((int64_t)k * H + i) * W + j]));
             }
             for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));

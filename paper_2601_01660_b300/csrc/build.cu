@@ -489,28 +489,27 @@ __device__ __forceinline__ unsigned lane_range(int lo, int hi) {
     return a & b;
 }
 
-// Pass B.  COUNT: per (unit, tile) pair counts into fcnt; EMIT: pairs at the
-// scanned offsets foff.  Entry of (tile t of super key k, unit j of U) in
-// fcnt/foff: 64 u0 + t U + j, so that the scan lays out each tile's pairs
-// unit after unit, i.e. in Gaussian order.
-template <bool EMIT>
-__global__ void __launch_bounds__(256) fine_bin_kernel(
+// Pass B, count: per (unit, tile) the pair count into fcnt and three bitmaps
+// over the unit's Gaussians (reaches the tile, its top half, its bottom half)
+// into fmask, UNIT_G / 32 words each.  Entry of (tile t of super key k, unit j
+// of U) in fcnt/foff: 64 u0 + t U + j, so that the scan lays out each tile's
+// pairs unit after unit, i.e. in Gaussian order.
+constexpr int MASK_WORDS = UNIT_G / 32;
+
+__global__ void __launch_bounds__(256) fine_count_kernel(
     const Unit *__restrict__ units, const unsigned long long *__restrict__ n_units_dev,
     const uint32_t *__restrict__ cvals, const BinRec *__restrict__ bin, int64_t N, int tx, int ty,
-    int sx, int n_tiles, int n_super, const float4 *__restrict__ cones,
-    uint32_t *__restrict__ fcnt, const uint32_t *__restrict__ foff, uint32_t *__restrict__ vals,
-    uint32_t *__restrict__ keys, const unsigned long long *__restrict__ keep, uint32_t cap) {
-    if (EMIT && *keep == 0) return;
+    int sx, int n_tiles, int n_super, const float4 *__restrict__ cones, uint32_t *__restrict__ fcnt,
+    uint32_t *__restrict__ fmask) {
     __shared__ float4 tdat[64 * TDAT_F4];
     __shared__ BinRec grec[FB_STAGE];
-    __shared__ uint32_t gidx[FB_STAGE];
     __shared__ uint32_t running[64];
-    __shared__ uint32_t base[64];
     __shared__ int tvalid[64];
+    __shared__ uint32_t wmask[64][3];  // the current word's bitmaps of each tile
     const unsigned long long n_units = *n_units_dev;
     const float4 *planes = cones + 2 * (n_tiles + n_super);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const unsigned lt = (1u << lane) - 1u;
+    if (tid < 64) wmask[tid][0] = wmask[tid][1] = wmask[tid][2] = 0u;
     for (unsigned long long u = blockIdx.x; u < n_units; u += gridDim.x) {
         const Unit U = units[u];
         const int l = (int)(U.key / (uint32_t)n_super), sidx = (int)(U.key - (uint32_t)l * n_super);
@@ -531,18 +530,21 @@ __global__ void __launch_bounds__(256) fine_bin_kernel(
             const int a = sa * SUPER + tid / SUPER, b = sb * SUPER + tid % SUPER;
             tvalid[tid] = a < ty && b < tx;
             running[tid] = 0u;
-            if (EMIT) base[tid] = foff[64u * U.u0 + (uint32_t)tid * nU + j];
         }
+        uint32_t *um = fmask + (size_t)u * 64 * 3 * MASK_WORDS;
         for (uint32_t s0 = U.start; s0 < U.end; s0 += FB_STAGE) {
             const int ns = (int)min((uint32_t)FB_STAGE, U.end - s0);
             __syncthreads();  // grec of the previous stage is no longer read
-            for (int e = tid; e < ns; e += blockDim.x) {
-                const uint32_t g = cvals[s0 + e];
-                gidx[e] = g;
-                grec[e] = bin[(int64_t)l * N + g];
-            }
+            for (int e = tid; e < ns; e += blockDim.x) grec[e] = bin[(int64_t)l * N + cvals[s0 + e]];
             __syncthreads();
-            for (int grp = 0; grp < ns; grp += 32) {
+            for (int grp = 0; grp < FB_STAGE; grp += 32) {
+                const int word = (int)(s0 - U.start + grp) / 32;
+                if (grp >= ns) {
+                    // words past the unit's end stay empty
+                    if (lane < 8)
+                        for (int m = 0; m < 3; ++m) um[((warp * 8 + lane) * 3 + m) * MASK_WORDS + word] = 0u;
+                    continue;
+                }
                 const int gl = grp + lane;
                 const bool gv = gl < ns;
                 BinRec G;
@@ -561,26 +563,24 @@ __global__ void __launch_bounds__(256) fine_bin_kernel(
                     cm[jj] = __ballot_sync(0xffffffffu, ov);
                     pc[jj + 1] = pc[jj] + __popc(cm[jj]);
                 }
+                // ellipsoid tests of the overlapping (tile, Gaussian) pairs on consecutive lanes
                 const int total = pc[8];
                 for (int r = 0; r < total; r += 32) {
                     const int q = r + lane;
-                    uint32_t hm = 0u;
-                    int jq = 0, t = 0, glane = 0;
                     if (q < total) {
+                        int jq = 0;
 #pragma unroll
                         for (int jj = 1; jj < 8; ++jj)
                             if (q >= pc[jj]) jq = jj;
                         unsigned cmq = cm[0];
-#pragma unroll
-                        for (int jj = 1; jj < 8; ++jj)
-                            if (jq == jj) cmq = cm[jj];
                         int pcq = 0;
 #pragma unroll
                         for (int jj = 1; jj < 8; ++jj)
-                            if (jq == jj) pcq = pc[jj];
-                        glane = (int)__fns(cmq, 0, q - pcq + 1);
-                        t = warp * 8 + jq;
+                            if (jq == jj) { cmq = cm[jj]; pcq = pc[jj]; }
+                        const int glane = (int)__fns(cmq, 0, q - pcq + 1);
+                        const int t = warp * 8 + jq;
                         const BinRec &R = grec[grp + glane];
+                        uint32_t hm;
                         if (R.b.y == 2.0f) {
                             hm = tdat[TDAT_F4 * t + 3].w != 0.0f ? 3u : 1u;
                         } else {
@@ -592,41 +592,73 @@ __global__ void __launch_bounds__(256) fine_bin_kernel(
                             ax.k2s = R.b.z;
                             hm = half_mask(tdat + TDAT_F4 * t + 2, ax, false);
                         }
+                        const uint32_t bit = 1u << glane;
+                        if (hm) atomicOr(&wmask[t][0], bit);
+                        if (hm & 1u) atomicOr(&wmask[t][1], bit);
+                        if (hm & 2u) atomicOr(&wmask[t][2], bit);
                     }
-                    const unsigned pass = __ballot_sync(0xffffffffu, hm != 0u);
-                    if (EMIT && hm != 0u) {
-                        int lo = 0;
-#pragma unroll
-                        for (int jj = 1; jj < 8; ++jj)
-                            if (jq == jj) lo = pc[jj];
-                        lo = max(lo - r, 0);
-                        const uint32_t rank = __popc(pass & lt & lane_range(lo, 32));
-                        const uint32_t pos = base[t] + running[t] + rank;
-                        if (pos < cap) {
-                            vals[pos] = gidx[grp + glane] | (hm << 30);
-                            if (keys) {
-                                const int a = sa * SUPER + t / SUPER, b = sb * SUPER + t % SUPER;
-                                keys[pos] = (uint32_t)l * (uint32_t)n_tiles + (uint32_t)(a * tx + b);
-                            }
-                        }
-                    }
-                    __syncwarp();
-                    if (lane < 8) {
-                        const int jj = lane;
-                        int lo = 0, hi = 0;
-#pragma unroll
-                        for (int k2 = 0; k2 < 8; ++k2)
-                            if (jj == k2) { lo = pc[k2]; hi = pc[k2 + 1]; }
-                        lo = min(max(lo - r, 0), 32);
-                        hi = min(max(hi - r, 0), 32);
-                        running[warp * 8 + jj] += __popc(pass & lane_range(lo, hi));
-                    }
-                    __syncwarp();
                 }
+                __syncwarp();
+                if (lane < 8) {
+                    const int t = warp * 8 + lane;
+                    const uint32_t p = wmask[t][0];
+                    um[(t * 3 + 0) * MASK_WORDS + word] = p;
+                    um[(t * 3 + 1) * MASK_WORDS + word] = wmask[t][1];
+                    um[(t * 3 + 2) * MASK_WORDS + word] = wmask[t][2];
+                    wmask[t][0] = wmask[t][1] = wmask[t][2] = 0u;
+                    running[t] += __popc(p);
+                }
+                __syncwarp();
             }
         }
         __syncthreads();
-        if (!EMIT && tid < 64) fcnt[64u * U.u0 + (uint32_t)tid * nU + j] = running[tid];
+        if (tid < 64) fcnt[64u * U.u0 + (uint32_t)tid * nU + j] = running[tid];
+    }
+}
+
+// Pass B, emit: expand the count pass's bitmaps into pairs at the scanned
+// offsets (no tests).  A warp owns 8 tiles; lane = Gaussian within a word.
+__global__ void __launch_bounds__(256) fine_emit_kernel(
+    const Unit *__restrict__ units, const unsigned long long *__restrict__ n_units_dev,
+    const uint32_t *__restrict__ cvals, int tx, int ty, int sx, int n_tiles, int n_super,
+    const uint32_t *__restrict__ fmask, const uint32_t *__restrict__ foff, uint32_t *__restrict__ vals,
+    uint32_t *__restrict__ keys, const unsigned long long *__restrict__ keep, uint32_t cap) {
+    if (*keep == 0) return;
+    __shared__ uint32_t gidx[UNIT_G];
+    const unsigned long long n_units = *n_units_dev;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    for (unsigned long long u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const Unit U = units[u];
+        const int l = (int)(U.key / (uint32_t)n_super), sidx = (int)(U.key - (uint32_t)l * n_super);
+        const int sa = sidx / sx, sb = sidx - sa * sx;
+        const uint32_t j = U.ju & 0xffffu, nU = U.ju >> 16;
+        const int ng = (int)(U.end - U.start);
+        __syncthreads();
+        for (int e = tid; e < ng; e += blockDim.x) gidx[e] = cvals[U.start + e];
+        __syncthreads();
+        const uint32_t *um = fmask + (size_t)u * 64 * 3 * MASK_WORDS;
+        for (int jj = 0; jj < 8; ++jj) {
+            const int t = warp * 8 + jj;
+            const int a = sa * SUPER + t / SUPER, b = sb * SUPER + t % SUPER;
+            if (a >= ty || b >= tx) continue;
+            uint32_t pos0 = foff[64u * U.u0 + (uint32_t)t * nU + j];
+            const uint32_t key = (uint32_t)l * (uint32_t)n_tiles + (uint32_t)(a * tx + b);
+            for (int w = 0; w < (ng + 31) / 32; ++w) {
+                const uint32_t p = um[(t * 3 + 0) * MASK_WORDS + w];
+                if (p == 0u) continue;
+                if ((p >> lane) & 1u) {
+                    const uint32_t tt = um[(t * 3 + 1) * MASK_WORDS + w], bb = um[(t * 3 + 2) * MASK_WORDS + w];
+                    const uint32_t hm = ((tt >> lane) & 1u) | (((bb >> lane) & 1u) << 1);
+                    const uint32_t pos = pos0 + __popc(p & lt);
+                    if (pos < cap) {
+                        vals[pos] = gidx[32 * w + lane] | (hm << 30);
+                        if (keys) keys[pos] = key;
+                    }
+                }
+                pos0 += __popc(p);
+            }
+        }
     }
 }
 
@@ -1203,9 +1235,10 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     e = cudaMemsetAsync(w_fcnt, 0, sizeof(uint32_t) * nf, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "build: memset");
     const int fgrid = (int)std::min<int64_t>(max_units, (int64_t)ctx->num_sms * 8);
-    fine_bin_kernel<false><<<fgrid, 256, 0, s>>>(units, d_units, cvals, (const BinRec *)w_bin, N, tx, ty, sx,
-                                                  n_tiles, n_super, cones, (uint32_t *)w_fcnt, nullptr,
-                                                  nullptr, nullptr, nullptr, 0u);
+    void *w_fmask;
+    if ((rc = ws_reserve(ctx, WS_FMASK, sizeof(uint32_t) * 3 * MASK_WORDS * nf, &w_fmask))) return rc;
+    fine_count_kernel<<<fgrid, 256, 0, s>>>(units, d_units, cvals, (const BinRec *)w_bin, N, tx, ty, sx, n_tiles,
+                                            n_super, cones, (uint32_t *)w_fcnt, (uint32_t *)w_fmask);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fine count kernel");
     if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_fcnt, (uint32_t *)w_foff, (int64_t)nf, d_pairs, s)))
@@ -1223,10 +1256,9 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     if ((rc = ws_reserve(ctx, WS_VALS_A, sizeof(uint32_t) * cap, &va))) return rc;
     if (want_keys && (rc = ws_reserve(ctx, WS_KEYS_A, sizeof(uint32_t) * cap, &ka))) return rc;
     keep_pairs_kernel<<<1, 32, 0, s>>>(d_pairs, (unsigned long long)cap, d_keep, ctx->d_status);
-    fine_bin_kernel<true><<<fgrid, 256, 0, s>>>(units, d_units, cvals, (const BinRec *)w_bin, N, tx, ty, sx,
-                                                 n_tiles, n_super, cones, (uint32_t *)w_fcnt,
-                                                 (const uint32_t *)w_foff, (uint32_t *)va, (uint32_t *)ka,
-                                                 d_keep, (uint32_t)cap);
+    fine_emit_kernel<<<fgrid, 256, 0, s>>>(units, d_units, cvals, tx, ty, sx, n_tiles, n_super,
+                                           (const uint32_t *)w_fmask, (const uint32_t *)w_foff, (uint32_t *)va,
+                                           (uint32_t *)ka, d_keep, (uint32_t)cap);
     const int ugrid = (int)std::min<int64_t>((int64_t)((nf + 255) / 256), (int64_t)ctx->num_sms * 16);
     fine_ranges_kernel<<<ugrid, 256, 0, s>>>(units, d_units, (const uint32_t *)w_fcnt,
                                               (const uint32_t *)w_foff, d_keep, n_super, sx, tx, ty,

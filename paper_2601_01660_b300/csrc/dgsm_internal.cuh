@@ -33,6 +33,7 @@ enum WsSlot {
     WS_CRANGES,        // per (light, super-tile) start/end of its Gaussian list
     WS_UNITS,          // fine-binning work units (+ per-super-tile unit counts)
     WS_FCNT, WS_FOFF,  // per (unit, tile) pair counts and their scan
+    WS_FMASK,          // per (unit, tile) bitmaps of the Gaussians that reach it (and its halves)
     WS_NSLOTS
 };
 

@@ -482,13 +482,6 @@ __global__ void unit_fill_kernel(const uint32_t *__restrict__ cs, const uint32_t
     }
 }
 
-// Lanes [lo, hi) of a warp as a bit mask (0 <= lo <= hi <= 32).
-__device__ __forceinline__ unsigned lane_range(int lo, int hi) {
-    const unsigned a = lo >= 32 ? 0u : (0xffffffffu << lo);
-    const unsigned b = hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u);
-    return a & b;
-}
-
 // Pass B, count: per (unit, tile) the pair count into fcnt and three bitmaps
 // over the unit's Gaussians (reaches the tile, its top half, its bottom half)
 // into fmask, UNIT_G / 32 words each.  Entry of (tile t of super key k, unit j
@@ -806,8 +799,7 @@ __device__ __forceinline__ bool pair_hit(const PairGeom &g, float k2, bool insid
 // Eq. 3 for a hit pair at the shells on its chord, as per-shell increments of
 // the optical depth added to D[k * nt + texel].
 __device__ __forceinline__ void eval_shells(const PairGeom &g, const float4 &q3, const float *rs,
-                                            int K, float *D, int nt, int texel,
-                                            unsigned long long &n_shell) {
+                                            int K, float *D, int nt, int texel, unsigned int &n_shell) {
     const int packed = __float_as_int(q3.z);
     const bool inside = (packed >> 20) & 1;
     const int klo = packed & 1023, kend = (packed >> 10) & 1023;
@@ -832,13 +824,15 @@ __device__ __forceinline__ void eval_shells(const PairGeom &g, const float4 &q3,
     const float hs = h * ss;
     const float F0 = inside ? mass_below(-hs, A0, hm2, full) : 0.0f;
     float Gprev = 0.0f;
-    for (; k < kend && rs[k] <= hi_r; ++k) {
+    const int k0 = k;
+    float *dk = D + k * nt + texel;
+    for (; k < kend && rs[k] <= hi_r; ++k, dk += nt) {
         const float G = mass_below(fmaf(h, rs[k], -hs), A0, hm2, full) - F0;
-        atomicAdd(D + k * nt + texel, fmaxf(G - Gprev, 0.0f));
+        atomicAdd(dk, fmaxf(G - Gprev, 0.0f));
         Gprev = fmaxf(G, Gprev);
-        ++n_shell;
     }
-    if (k < K) atomicAdd(D + k * nt + texel, fmaxf(full - F0 - Gprev, 0.0f));
+    n_shell += (unsigned int)(k - k0);
+    if (k < K) atomicAdd(dk, fmaxf(full - F0 - Gprev, 0.0f));
 }
 
 size_t build_smem_bytes(int K, int tile, int chunk) {
@@ -890,7 +884,8 @@ __global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_ke
     const unsigned long long total_items = *n_items_total;
     for (int k = tid; k < K; k += BT_THREADS) rs[k] = radii[k];
     if (tid < 3) s_cnt[tid] = 0ull;
-    unsigned long long n_hit = 0, n_shell = 0, n_tested = 0;
+    unsigned long long n_tested = 0;
+    unsigned int n_hit = 0, n_shell = 0;
     float4 *q = queue + warp * QCAP;
 
     for (;;) {
@@ -1065,8 +1060,8 @@ __global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_ke
     if (stats) {
         n_tested = n_tst;
         if (n_tested) atomicAdd(&s_cnt[0], n_tested);
-        if (n_hit) atomicAdd(&s_cnt[1], n_hit);
-        if (n_shell) atomicAdd(&s_cnt[2], n_shell);
+        if (n_hit) atomicAdd(&s_cnt[1], (unsigned long long)n_hit);
+        if (n_shell) atomicAdd(&s_cnt[2], (unsigned long long)n_shell);
         __syncthreads();
         if (tid < 3) atomicAdd(stats + tid, s_cnt[tid]);
     }

@@ -27,25 +27,27 @@ __device__ __forceinline__ float load_T<__nv_bfloat16>(const __nv_bfloat16 *p) {
     return __bfloat162float(__ldg(p));
 }
 
+// Trilinear lookup in one light's atlas A [K][H][W] (at most 2^32 voxels, so
+// 32-bit offsets); inw[k] = 1 / (radii[k+1] - radii[k]).
 template <typename T>
 __device__ __forceinline__ float lookup(const T *__restrict__ A, int H, int W, int K,
-                                        const SampleIndex &s, const float *rs) {
+                                        const SampleIndex &s, const float *rs, const float *inw) {
     const int j0 = min(max(s.bj, 0), W - 1), j1 = min(max(s.bj + 1, 0), W - 1);
     const int i0 = min(max(s.bi, 0), H - 1), i1 = min(max(s.bi + 1, 0), H - 1);
     int k0, k1;
     float wt;
     if (s.k < 0) { k0 = k1 = 0; wt = 0.0f; }
     else if (s.k >= K - 1) { k0 = k1 = K - 1; wt = 0.0f; }
-    else { k0 = s.k; k1 = s.k + 1; wt = (s.t - rs[k0]) / (rs[k1] - rs[k0]); }
-    const int64_t plane = (int64_t)H * W;
-    const int64_t o00 = (int64_t)i0 * W + j0, o01 = (int64_t)i0 * W + j1;
-    const int64_t o10 = (int64_t)i1 * W + j0, o11 = (int64_t)i1 * W + j1;
+    else { k0 = s.k; k1 = s.k + 1; wt = (s.t - rs[k0]) * inw[k0]; }
+    const uint32_t plane = (uint32_t)H * (uint32_t)W;
+    const uint32_t o00 = (uint32_t)i0 * W + j0, o01 = (uint32_t)i0 * W + j1;
+    const uint32_t o10 = (uint32_t)i1 * W + j0, o11 = (uint32_t)i1 * W + j1;
     const float fx = s.fx, fy = s.fy;
-    const T *P0 = A + k0 * plane;
+    const T *P0 = A + (uint32_t)k0 * plane;
     float b0 = (1.0f - fy) * ((1.0f - fx) * load_T(P0 + o00) + fx * load_T(P0 + o01)) +
                fy * ((1.0f - fx) * load_T(P0 + o10) + fx * load_T(P0 + o11));
     if (k1 == k0) return b0;
-    const T *P1 = A + k1 * plane;
+    const T *P1 = A + (uint32_t)k1 * plane;
     float b1 = (1.0f - fy) * ((1.0f - fx) * load_T(P1 + o00) + fx * load_T(P1 + o01)) +
                fy * ((1.0f - fx) * load_T(P1 + o10) + fx * load_T(P1 + o11));
     return (1.0f - wt) * b0 + wt * b1;
@@ -73,15 +75,26 @@ __global__ void __launch_bounds__(ATT_THREADS) attenuate_kernel(
     const float *__restrict__ radii, int K, DynGeom dg, const float *__restrict__ lights,
     const float *__restrict__ qm, const float *cin, int64_t Q, const float *__restrict__ lw,
     float wd, float *cout, float *__restrict__ Tout) {
-    __shared__ float rs[256];
-    __shared__ float rsd[SEP ? 256 : 1];
+    __shared__ float rs[256], inw[256];
+    __shared__ float rsd[SEP ? 256 : 1], inwd[SEP ? 256 : 1];
+    __shared__ short tab[SHELL_BINS], tabd[SEP ? SHELL_BINS : 1];
     __shared__ float ls[64 * 3];
     __shared__ float wl[64];
-    for (int k = threadIdx.x; k < K; k += blockDim.x) rs[k] = radii[k];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        rs[k] = radii[k];
+        inw[k] = k + 1 < K ? 1.0f / (radii[k + 1] - radii[k]) : 0.0f;
+    }
     if (SEP)
-        for (int k = threadIdx.x; k < dg.K; k += blockDim.x) rsd[k] = dg.radii[k];
+        for (int k = threadIdx.x; k < dg.K; k += blockDim.x) {
+            rsd[k] = dg.radii[k];
+            inwd[k] = k + 1 < dg.K ? 1.0f / (dg.radii[k + 1] - dg.radii[k]) : 0.0f;
+        }
     for (int k = threadIdx.x; k < 3 * L; k += blockDim.x) ls[k] = lights[k];
     for (int k = threadIdx.x; k < L; k += blockDim.x) wl[k] = lw ? lw[k] : 1.0f / (float)L;
+    __syncthreads();
+    const ShellTab st = build_shell_tab(rs, K, tab);
+    ShellTab std_ = st;
+    if (SEP) std_ = build_shell_tab(rsd, dg.K, tabd);
     __syncthreads();
     const int64_t lstride = (int64_t)K * H * W;
     const int64_t dstride = SEP ? (int64_t)dg.K * dg.H * dg.W : lstride;
@@ -105,17 +118,17 @@ __global__ void __launch_bounds__(ATT_THREADS) attenuate_kernel(
 #pragma unroll
             for (int u = 0; u < ATT_U; ++u) {
                 const float ox = ls[3 * l], oy = ls[3 * l + 1], oz = ls[3 * l + 2];
-                const SampleIndex s = sample_index(px[u], py[u], pz[u], ox, oy, oz, H, W, rs, K);
+                const SampleIndex s = sample_index_tab(px[u], py[u], pz[u], ox, oy, oz, H, W, rs, K, tab, st);
                 Tl[u] = 1.0f;
                 if (s.t != 0.0f) {
-                    Tl[u] = lookup(atlas + l * lstride, H, W, K, s, rs);
+                    Tl[u] = lookup(atlas + l * lstride, H, W, K, s, rs, inw);
                     if (dyn) {
                         if (SEP) {
-                            const SampleIndex sd = sample_index(px[u], py[u], pz[u], ox, oy, oz, dg.H,
-                                                                dg.W, rsd, dg.K);
-                            Tl[u] *= lookup(dyn + l * dstride, dg.H, dg.W, dg.K, sd, rsd);
+                            const SampleIndex sd = sample_index_tab(px[u], py[u], pz[u], ox, oy, oz, dg.H,
+                                                                    dg.W, rsd, dg.K, tabd, std_);
+                            Tl[u] *= lookup(dyn + l * dstride, dg.H, dg.W, dg.K, sd, rsd, inwd);
                         } else {
-                            Tl[u] *= lookup(dyn + l * dstride, H, W, K, s, rs);
+                            Tl[u] *= lookup(dyn + l * dstride, H, W, K, s, rs, inw);
                         }
                     }
                 }
@@ -144,13 +157,16 @@ __global__ void sample_index_kernel(const float *__restrict__ pts, int64_t n,
                                     const float *__restrict__ radii, int K,
                                     int32_t *__restrict__ idx_out, float *__restrict__ frac_out) {
     __shared__ float rs[256];
+    __shared__ short tab[SHELL_BINS];
     for (int k = threadIdx.x; k < K; k += blockDim.x) rs[k] = radii[k];
+    __syncthreads();
+    const ShellTab st = build_shell_tab(rs, K, tab);
     __syncthreads();
     const float ox = light[0], oy = light[1], oz = light[2];
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const SampleIndex s = sample_index(pts[3 * q], pts[3 * q + 1], pts[3 * q + 2], ox, oy, oz,
-                                           H, W, rs, K);
+        const SampleIndex s = sample_index_tab(pts[3 * q], pts[3 * q + 1], pts[3 * q + 2], ox, oy, oz,
+                                               H, W, rs, K, tab, st);
         idx_out[5 * q] = s.ci;
         idx_out[5 * q + 1] = s.cj;
         idx_out[5 * q + 2] = s.bi;
@@ -201,7 +217,7 @@ int attenuate_common(dgsm_ctx *ctx, const void *atlas, const void *atlas_dyn, in
     if (n_q == 0) return DGSM_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t span = (int64_t)ATT_U * ATT_THREADS;
-    const int grid = (int)std::min<int64_t>((n_q + span - 1) / span, (int64_t)ctx->num_sms * 32);
+    const int grid = (int)std::min<int64_t>((n_q + span - 1) / span, (int64_t)ctx->num_sms * 8);
     switch (dtype) {
         case DGSM_F32:
             launch_attenuate<float>(grid, s, atlas, atlas_dyn, sep, L, H, W, radii, K, dg, lights, q_means,

@@ -164,6 +164,66 @@ __device__ __forceinline__ int count_le(const float *r, int K, float t) {
     return lo;
 }
 
+// A per-block guess table for the shell index: tab[b] = #{radii <= t_b} - 1
+// at the start t_b of bin b of SHELL_BINS equal bins of log2 t over
+// [radii[0], radii[K-1]].  shell_index() starts from the guess and steps to
+// the exact comparison count, so the result equals count_le(t) - 1 whatever
+// the radii (the table only saves the search).
+constexpr int SHELL_BINS = 256;
+
+struct ShellTab {
+    float lr0, scale;  // log2 radii[0] and bins per unit of log2 t (0: no table)
+};
+
+// Fill tab (SHELL_BINS shorts in shared memory) from the block's radii rs;
+// all threads of the block call it; a __syncthreads() must follow.
+__device__ __forceinline__ ShellTab build_shell_tab(const float *rs, int K, short *tab) {
+    ShellTab st;
+    st.lr0 = 0.0f;
+    st.scale = 0.0f;
+    if (K >= 2 && rs[0] > 0.0f && rs[K - 1] > rs[0]) {
+        st.lr0 = __log2f(rs[0]);
+        st.scale = (float)SHELL_BINS / (__log2f(rs[K - 1]) - st.lr0);
+    }
+    for (int b = threadIdx.x; b < SHELL_BINS; b += blockDim.x) {
+        const float tb = st.scale > 0.0f ? exp2f(st.lr0 + (float)b / st.scale) : rs[0];
+        tab[b] = (short)max(count_le(rs, K, tb) - 1, 0);
+    }
+    return st;
+}
+
+__device__ __forceinline__ int shell_index(float t, const float *rs, int K, const short *tab, ShellTab st) {
+    if (!(t >= rs[0])) return -1;
+    if (t >= rs[K - 1]) return K - 1;
+    const int b = min(max((int)((__log2f(t) - st.lr0) * st.scale), 0), SHELL_BINS - 1);
+    int k = tab[b];
+    while (k + 1 < K && rs[k + 1] <= t) ++k;
+    while (k >= 0 && rs[k] > t) --k;
+    return k;
+}
+
+// sample_index with the shell index from a guess table (same result).
+__device__ __forceinline__ SampleIndex sample_index_tab(float px, float py, float pz, float ox, float oy,
+                                                        float oz, int H, int W, const float *radii, int K,
+                                                        const short *tab, ShellTab st) {
+    SampleIndex s;
+    float vx = xsub(px, ox), vy = xsub(py, oy), vz = xsub(pz, oz);
+    s.t = xsqrt(xadd(xadd(xmul(vx, vx), xmul(vy, vy)), xmul(vz, vz)));
+    float2 uv = xencode(vx, vy, vz);
+    float fu = xmul(xmul(xadd(uv.x, 1.0f), 0.5f), (float)W);
+    float fv = xmul(xmul(xadd(uv.y, 1.0f), 0.5f), (float)H);
+    float gx = xsub(fu, 0.5f), gy = xsub(fv, 0.5f);
+    float bj = floorf(gx), bi = floorf(gy);
+    s.cj = min(max((int)floorf(fu), 0), W - 1);
+    s.ci = min(max((int)floorf(fv), 0), H - 1);
+    s.bj = (int)bj;
+    s.bi = (int)bi;
+    s.fx = xsub(gx, bj);
+    s.fy = xsub(gy, bi);
+    s.k = shell_index(s.t, radii, K, tab, st);
+    return s;
+}
+
 __device__ __forceinline__ SampleIndex sample_index(float px, float py, float pz, float ox,
                                                     float oy, float oz, int H, int W,
                                                     const float *radii, int K) {

@@ -328,7 +328,10 @@ int dgsm_weighted_centroid(dgsm_ctx *ctx, const float *means, const float *weigh
  * (sh_relight, centroid = their alpha-weighted centroid), copy out.
  * All array fields of `in` are host pointers (pinned memory makes the copies
  * asynchronous); colors_out: host (n,3); sh_out: host (3,9) or NULL.
- * Device buffers come from the context's workspace.  Blocks until the
+ * Device buffers come from the context's workspace.  The colours and the
+ * cubemap are copied, and the probe is fitted, on a side stream of the
+ * context while the build runs on `stream`; the colours outside the relit
+ * range are copied back on it while the range is relit.  Blocks until the
  * results are in host memory. */
 typedef struct {
     const float *means, *scales, *quats, *opac, *colors; /* (n,3) (n,3) (n,4) (n) (n,3) */

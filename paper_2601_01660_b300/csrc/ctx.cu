@@ -109,6 +109,9 @@ extern "C" void dgsm_destroy(dgsm_ctx *ctx) {
     for (int b = 0; b < dgsm_ctx::PROF_RING; ++b)
         for (int k = 0; k < 3; ++k)
             if (ctx->prof_ev[b][k]) cudaEventDestroy(ctx->prof_ev[b][k]);
+    for (int k = 0; k < 4; ++k)
+        if (ctx->fev[k]) cudaEventDestroy(ctx->fev[k]);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     delete ctx;
 }
 

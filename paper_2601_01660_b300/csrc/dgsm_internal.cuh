@@ -56,6 +56,9 @@ struct dgsm_ctx {
     // > 0 while a graph captured on this context is alive: its nodes hold
     // workspace addresses, so the workspace must not move
     int frozen = 0;
+    // side stream and events of dgsm_frame_host (copies beside compute)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fev[4] = {};
 };
 
 namespace dgsm {

@@ -198,39 +198,63 @@ extern "C" int dgsm_frame_host(dgsm_ctx *ctx, const dgsm_frame_host_in *in,
     void *d_atlas = take(sz_atlas);
     float *d_sh = (float *)take(sz_small), *d_cen = (float *)take(sz_small);
 
-    struct Cp { void *dst; const void *src; size_t bytes; } cps[] = {
-        {d_means, in->means, 12 * (size_t)n}, {d_scales, in->scales, 12 * (size_t)n},
-        {d_quats, in->quats, 16 * (size_t)n}, {d_opac, in->opac, 4 * (size_t)n},
-        {d_colors, in->colors, 12 * (size_t)n}, {d_lights, in->lights, 12 * (size_t)L},
-        {d_radii, in->radii, 4 * (size_t)K}, {d_cd, in->cube_dirs, 12 * (size_t)in->n_cube},
-        {d_cr, in->cube_rgb, 12 * (size_t)in->n_cube}, {d_cw, in->cube_w, 4 * (size_t)in->n_cube}};
-    for (const Cp &cp : cps) {
-        if (cp.bytes == 0) continue;
-        e = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "frame: host to device copy");
+    // Side stream: the colours and the cubemap go up, and the probe is fitted,
+    // while the build runs on `stream`; the colours of the Gaussians that are
+    // not relit come back while the avatar range is relit.
+    if (!ctx->side) {
+        e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+        for (int k = 0; e == cudaSuccess && k < 4; ++k)
+            e = cudaEventCreateWithFlags(&ctx->fev[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "frame: side stream");
     }
+    cudaStream_t s2 = ctx->side;
+    auto h2d = [&](void *dst, const void *src, size_t bytes, cudaStream_t st) {
+        return bytes == 0 ? cudaSuccess : cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    e = cudaEventRecord(ctx->fev[0], s);  // the side stream starts after earlier work on `stream`
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ctx->fev[0], 0);
+    if (e == cudaSuccess) e = h2d(d_means, in->means, 12 * (size_t)n, s);
+    if (e == cudaSuccess) e = h2d(d_scales, in->scales, 12 * (size_t)n, s);
+    if (e == cudaSuccess) e = h2d(d_quats, in->quats, 16 * (size_t)n, s);
+    if (e == cudaSuccess) e = h2d(d_opac, in->opac, 4 * (size_t)n, s);
+    if (e == cudaSuccess) e = h2d(d_lights, in->lights, 12 * (size_t)L, s);
+    if (e == cudaSuccess) e = h2d(d_radii, in->radii, 4 * (size_t)K, s);
+    if (e == cudaSuccess) e = h2d(d_colors, in->colors, 12 * (size_t)n, s2);
+    if (e == cudaSuccess) e = h2d(d_cd, in->cube_dirs, 12 * (size_t)in->n_cube, s2);
+    if (e == cudaSuccess) e = h2d(d_cr, in->cube_rgb, 12 * (size_t)in->n_cube, s2);
+    if (e == cudaSuccess) e = h2d(d_cw, in->cube_w, 4 * (size_t)in->n_cube, s2);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "frame: host to device copy");
+    if ((rc = sh_fit(ctx, d_cd, d_cr, d_cw, in->n_cube, in->lambda, d_sh, nullptr, s2))) return rc;
+    if ((e = cudaEventRecord(ctx->fev[1], s2)) != cudaSuccess) return cuda_fail(ctx, e, "frame: event");
     if ((rc = dgsm_build(ctx, d_means, d_scales, d_quats, d_opac, n, d_lights, L, H, W, d_radii, K,
                          &p, d_atlas, s)))
         return rc;
+    if ((e = cudaStreamWaitEvent(s, ctx->fev[1], 0)) != cudaSuccess) return cuda_fail(ctx, e, "frame: wait");
     if ((rc = dgsm_attenuate(ctx, d_atlas, nullptr, p.atlas_dtype, L, H, W, d_radii, K, d_lights,
                              d_means, d_colors, n, nullptr, 1.0f, d_out, nullptr, s)))
         return rc;
-    if ((rc = sh_fit(ctx, d_cd, d_cr, d_cw, in->n_cube, in->lambda, d_sh, nullptr, s))) return rc;
-    const int64_t a0 = in->relight_begin, na = in->relight_end - in->relight_begin;
+    const int64_t a0 = in->relight_begin, a1 = in->relight_end, na = a1 - a0;
+    // colours outside the relit range: back on the side stream, beside the relight
+    if ((e = cudaEventRecord(ctx->fev[2], s)) != cudaSuccess) return cuda_fail(ctx, e, "frame: event");
+    if ((e = cudaStreamWaitEvent(s2, ctx->fev[2], 0)) != cudaSuccess) return cuda_fail(ctx, e, "frame: wait");
+    if (a0 > 0) e = cudaMemcpyAsync(colors_out, d_out, 12 * (size_t)a0, cudaMemcpyDeviceToHost, s2);
+    if (e == cudaSuccess && a1 < n)
+        e = cudaMemcpyAsync(colors_out + 3 * a1, d_out + 3 * a1, 12 * (size_t)(n - a1), cudaMemcpyDeviceToHost, s2);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "frame: device to host copy");
     if (na > 0) {
         if ((rc = dgsm_weighted_centroid(ctx, d_means + 3 * a0, d_opac + a0, na, d_cen, s))) return rc;
         if ((rc = sh_relight(ctx, d_sh, d_means + 3 * a0, d_quats + 4 * a0, d_scales + 3 * a0, nullptr,
                              d_cen, d_out + 3 * a0, na, rparams, d_out + 3 * a0, s)))
             return rc;
-    }
-    if (n > 0) {
-        e = cudaMemcpyAsync(colors_out, d_out, 12 * (size_t)n, cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(colors_out + 3 * a0, d_out + 3 * a0, 12 * (size_t)na, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "frame: device to host copy");
     }
     if (sh_out) {
         e = cudaMemcpyAsync(sh_out, d_sh, 27 * sizeof(float), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "frame: device to host copy");
     }
+    if ((e = cudaEventRecord(ctx->fev[3], s2)) != cudaSuccess) return cuda_fail(ctx, e, "frame: event");
+    if ((e = cudaStreamWaitEvent(s, ctx->fev[3], 0)) != cudaSuccess) return cuda_fail(ctx, e, "frame: wait");
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "frame: synchronize");
     return dgsm_sync_status(ctx, stream);

@@ -489,7 +489,7 @@ __global__ void unit_fill_kernel(const uint32_t *__restrict__ cs, const uint32_t
 // pairs unit after unit, i.e. in Gaussian order.
 constexpr int MASK_WORDS = UNIT_G / 32;
 
-__global__ void __launch_bounds__(256) fine_count_kernel(
+__global__ void __launch_bounds__(256, 5) fine_count_kernel(
     const Unit *__restrict__ units, const unsigned long long *__restrict__ n_units_dev,
     const uint32_t *__restrict__ cvals, const BinRec *__restrict__ bin, int64_t N, int tx, int ty,
     int sx, int n_tiles, int n_super, const float4 *__restrict__ cones, uint32_t *__restrict__ fcnt,

@@ -441,7 +441,7 @@ def main():
     ap.add_argument("--cpu-texels", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--report", choices=["precision", "surrogate", "frame"],
+    ap.add_argument("--report", choices=["precision", "surrogate", "frame", "field"],
                     help="print a side report (one JSON line) instead of the step benchmark")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -9,6 +9,9 @@
              3M Gaussians: |dT| p50/p99 against the exact atlas lookup, with
              and without the per-tile exact fallback, memory footprint,
              Gaussians/s, and an atlas of the same memory as the weights.
+  field      the surrogate's tensor-core forward pass alone: 3M inputs
+             (u, v, rho) through one light's field (GPU-initialised weights),
+             TFLOP/s against the measured bf16 peak.
   frame      the moving-avatar workload (1.5M static Gaussians with 4-light
              512x512x64 atlases built once, 8 avatars of 100k walking for
              120 frames, 256x256x32 dynamic atlases per frame, 2.3M
@@ -226,6 +229,32 @@ def frame(frames: int = 120) -> dict:
     }
 
 
+def field(n: int = 3_000_000, reps: int = 20) -> dict:
+    import os
+
+    import torch
+
+    from paper_2601_01660_b300 import native
+    nat = native()
+    params = nat.nf_init(seed=5, n_lights=1)[0].contiguous()
+    g = torch.Generator(device="cuda").manual_seed(9)
+    uvr = torch.rand(n, 3, device="cuda", generator=g)
+    uvr[:, :2] = uvr[:, :2] * 2 - 1
+    ms = _time(torch, lambda: nat.nf_forward(params, uvr), reps=reps)
+    flop = n * 2.0 * (96 * 64 + 3 * 64 * 64 + 64)
+    peak = None
+    try:
+        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        peak = float(json.load(open(os.path.join(root, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        pass
+    tf = flop / (ms * 1e-3) / 1e12
+    return {"report": "field", "inputs": n, "ms": round(ms, 4), "field_evals_per_s": n / (ms * 1e-3),
+            "tflops": round(tf, 2), "bf16_peak_tflops": peak,
+            "frac": round(tf / peak, 4) if peak else None,
+            "flop_per_eval": 2 * (96 * 64 + 3 * 64 * 64 + 64), "kernel": "tc::field_kernel<MODE_UVR> (tcgen05)"}
+
+
 def main(which: str) -> None:
-    fn = {"precision": precision, "surrogate": surrogate, "frame": frame}[which]
+    fn = {"precision": precision, "surrogate": surrogate, "frame": frame, "field": field}[which]
     print(json.dumps(fn()), flush=True)

@@ -649,19 +649,27 @@ __global__ void __launch_bounds__(THREADS, 2) field_kernel(
     if (MODE == MODE_UVR || MODE == MODE_QUERY) {
         float ox = 0.f, oy = 0.f, oz = 0.f;
         if (MODE == MODE_QUERY) { ox = lights[3 * l]; oy = lights[3 * l + 1]; oz = lights[3 * l + 2]; }
-        for (int64_t base = (int64_t)wgi * TM; base < n; base += (int64_t)n_wg * TM) {
+        // the next tile's inputs are loaded while this tile runs its MMA chain
+        const int64_t step = (int64_t)n_wg * TM;
+        float nx = 0.f, ny = 0.f, nz = 0.f;
+        {
+            const int64_t q0 = (int64_t)wgi * TM + r;
+            if (q0 < n) { nx = uvr[3 * q0]; ny = uvr[3 * q0 + 1]; nz = uvr[3 * q0 + 2]; }
+        }
+        for (int64_t base = (int64_t)wgi * TM; base < n; base += step) {
             const int64_t q = base + r;
             const bool valid = q < n;
+            const float ix = nx, iy = ny, iz = nz;
+            if (q + step < n) { nx = uvr[3 * (q + step)]; ny = uvr[3 * (q + step) + 1]; nz = uvr[3 * (q + step) + 2]; }
             float u = 0.f, v = 0.f, rho = 0.f;
             SampleIndex si;
             si.t = 0.f;
             if (valid) {
                 if (MODE == MODE_UVR) {
-                    u = uvr[3 * q]; v = uvr[3 * q + 1]; rho = uvr[3 * q + 2];
+                    u = ix; v = iy; rho = iz;
                 } else {
-                    const float px = uvr[3 * q], py = uvr[3 * q + 1], pz = uvr[3 * q + 2];
-                    si = sample_index(px, py, pz, ox, oy, oz, H, W, rs, K);
-                    const float2 e = xencode(px - ox, py - oy, pz - oz);
+                    si = sample_index(ix, iy, iz, ox, oy, oz, H, W, rs, K);
+                    const float2 e = xencode(ix - ox, iy - oy, iz - oz);
                     u = e.x; v = e.y;
                     rho = nf_rho(si.t, rs, K);
                 }

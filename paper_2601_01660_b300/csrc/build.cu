@@ -37,7 +37,7 @@ constexpr int SUPER = 8;       // super-tile edge, in tiles
 constexpr int REC_F4 = 4;      // float4 per build record
 constexpr int BT_THREADS = 256;
 constexpr int BT_WARPS = BT_THREADS / 32;
-constexpr int QCAP = 64;       // per-warp queue of hits: (a, d'.w', |w' x d'|^2, record/texel id)
+constexpr int QCAP = 96;       // per-warp queue of hits: (a, d'.w', |w' x d'|^2, record/texel id)
 constexpr int ITEM_CHUNKS = 16;  // a work item holds at most ITEM_CHUNKS * chunk Gaussians
 #ifndef DGSM_BT_MIN_BLOCKS
 #define DGSM_BT_MIN_BLOCKS 4        // resident build blocks per SM the register budget targets
@@ -981,30 +981,35 @@ __global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_ke
                 const unsigned m = __ballot_sync(0xffffffffu, hit);
                 if (hit) q[qn + __popc(m & lt)] = make_float4(g.a, g.pw, g.c2, __int_as_float(id));
                 qn += __popc(m);
-                if (qn >= 32) flush(32);
             };
-            // records are handed out dynamically to the warps of a texel group
+            // records are handed out dynamically, two at a time, to the warps of a
+            // texel group; a warp's hits are evaluated once 32 are queued
             const uint8_t *cmask = smask + (c & 1) * chunk;
             for (;;) {
-                int r = 0;
-                if (lane == 0) r = atomicAdd(&s_next[tg], 1);
-                r = __shfl_sync(0xffffffffu, r, 0);
-                if (r >= cnt) break;
-                const uint32_t hm = cmask[r];
-                const bool doA = (hm & bitA) != 0u, doB = (hm & bitB) != 0u;
-                if (!doA && !doB) continue;
-                const float4 q0 = st[r * REC_F4], q1 = st[r * REC_F4 + 1], q2 = st[r * REC_F4 + 2],
-                             q3 = st[r * REC_F4 + 3];
-                const bool inside = (__float_as_int(q3.z) >> 20) & 1;
-                if (doA) {
-                    const PairGeom gA = pair_geom(q0, q1, q2, dA.x, dA.y, dA.z);
-                    push(vA && pair_hit(gA, q3.y, inside), gA, (r << 6) | lane);
-                    n_tst += vA;
-                }
-                if (doB) {
-                    const PairGeom gB = pair_geom(q0, q1, q2, dB.x, dB.y, dB.z);
-                    push(vB && pair_hit(gB, q3.y, inside), gB, (r << 6) | (32 + lane));
-                    n_tst += vB;
+                int r0 = 0;
+                if (lane == 0) r0 = atomicAdd(&s_next[tg], 2);
+                r0 = __shfl_sync(0xffffffffu, r0, 0);
+                if (r0 >= cnt) break;
+                const int r1 = min(r0 + 2, cnt);
+                for (int r = r0; r < r1; ++r) {
+                    const uint32_t hm = cmask[r];
+                    const bool doA = (hm & bitA) != 0u, doB = (hm & bitB) != 0u;
+                    if (!doA && !doB) continue;
+                    const float4 q0 = st[r * REC_F4], q1 = st[r * REC_F4 + 1], q2 = st[r * REC_F4 + 2],
+                                 q3 = st[r * REC_F4 + 3];
+                    const bool inside = (__float_as_int(q3.z) >> 20) & 1;
+                    if (doA) {
+                        const PairGeom gA = pair_geom(q0, q1, q2, dA.x, dA.y, dA.z);
+                        push(vA && pair_hit(gA, q3.y, inside), gA, (r << 6) | lane);
+                        n_tst += vA;
+                    }
+                    if (doB) {
+                        const PairGeom gB = pair_geom(q0, q1, q2, dB.x, dB.y, dB.z);
+                        push(vB && pair_hit(gB, q3.y, inside), gB, (r << 6) | (32 + lane));
+                        n_tst += vB;
+                    }
+                    // at most 31 + 2 * 32 < QCAP hits are queued here
+                    while (qn >= 32) flush(32);
                 }
             }
             if (qn > 0) flush(qn);

@@ -192,6 +192,34 @@ int dgsm_attenuate_dyn(dgsm_ctx *ctx, const void *atlas, int32_t dtype, int32_t 
                        int64_t n_q, const float *light_w, float direct_frac, float *colors_out,
                        float *T_out, void *stream);
 
+/* Footprint sampling for dgsm_attenuate (Sec. 3.3, last paragraph; Sec. 4,
+ * ablation (A)).  The paper averages several atlas lookups over each
+ * receiver's footprint instead of one lookup at its centre, with
+ * rotation-aware offsets in the receiver's principal axes:
+ *   x_i = mu + R (s (.) z_i),   T_l = sum_i w_i T_l(x_i),   sum_i w_i = 1,
+ * then scales the colour as dgsm_attenuate does.
+ *   mode DGSM_FP_CENTRE: z = 0 (the same result as dgsm_attenuate);
+ *   mode DGSM_FP_STENCIL7: z in {0, +-e_x, +-e_y, +-e_z}, weights proportional
+ *     to exp(-|z|^2/2) (1 at the centre, e^-1/2 on the axes);
+ *   mode DGSM_FP_MC (the paper's default): n_samples offsets z ~ N(0, I),
+ *     w = 1/n_samples.  Normal j of receiver q (coordinate j % 3 of sample
+ *     j / 3) comes from Philox4x64-10 (Salmon et al., SC 2011) at counter
+ *     (q, j / 8, 0, 0) and key (seed, 0): word (j % 8) / 2 gives two 24-bit
+ *     uniforms u1, u2 in (0, 1] (top bits of its low and high halves) and
+ *     Box-Muller gives sqrt(-2 ln u1) cos(2 pi u2) (even j) or sin (odd j).
+ *   q_quats (n_q,4) w,x,y,z; q_scales (n_q,3) linear standard deviations;
+ *   n_samples in 1..32 (DGSM_FP_MC only).  Other arguments as for
+ *   dgsm_attenuate (one atlas; no dynamic atlas).  Returns DGSM_OK,
+ *   DGSM_ERR_INVALID_ARG or DGSM_ERR_CUDA. */
+enum dgsm_footprint { DGSM_FP_CENTRE = 0, DGSM_FP_STENCIL7 = 1, DGSM_FP_MC = 2 };
+int dgsm_attenuate_footprint(dgsm_ctx *ctx, const void *atlas, int32_t dtype, int32_t n_lights,
+                             int32_t H, int32_t W, const float *radii, int32_t K,
+                             const float *lights, const float *q_means, const float *q_quats,
+                             const float *q_scales, const float *colors_in, int64_t n_q,
+                             const float *light_w, float direct_frac, int32_t mode,
+                             int32_t n_samples, uint64_t seed, float *colors_out, float *T_out,
+                             void *stream);
+
 /* The integer decisions of dgsm_attenuate for n points seen from one light
  * (device pointer to 3 floats): idx_out (n,5) = texel cell row i, cell
  * column j, bilinear base row i0, base column j0, shell k (#{radii <= t}-1,

@@ -75,6 +75,15 @@ def _declare(L):
     L.orc_count_ray_evals.restype = I64
     L.orc_count_ray_evals.argtypes = [_f, _f, _f, _f, I64, _f, C.c_int, C.c_int, _f, C.c_int,
                                       C.c_float, C.c_float, _i32, I64]
+    _u64 = C.POINTER(C.c_uint64)
+    L.orc_philox4x64.argtypes = [_u64, _u64, _u64]
+    L.orc_fp_normal.restype = C.c_double
+    L.orc_fp_normal.argtypes = [C.c_uint64, I64, C.c_int]
+    L.orc_fp_offsets.restype = C.c_int
+    L.orc_fp_offsets.argtypes = [C.c_int, C.c_int, C.c_uint64, I64, _d, _d]
+    L.orc_attenuate_footprint.argtypes = [_d, C.c_int, C.c_int, C.c_int, _f, C.c_int, _f, _f, _f, _f,
+                                          _f, I64, _f, C.c_double, C.c_int, C.c_int, C.c_uint64,
+                                          C.POINTER(C.c_int64), _d, _d]
     L.orc_sh_basis.argtypes = [_d, _d]
     L.orc_sh_fit.restype = C.c_int
     L.orc_sh_fit.argtypes = [_f, _f, _f, I64, C.c_double, _d]
@@ -218,6 +227,57 @@ def attenuate(atlas, radii, lights, q_means, colors, atlas_dyn=None, light_w=Non
     lw = _c32(light_w) if light_w is not None else None
     lib().orc_attenuate(_pd(atlas), _pd(dyn), L, H, W, _pf(_c32(radii)), K, _pf(_c32(lights)),
                         _pf(q_means), _pf(colors), Q, _pf(lw), float(direct_frac), _pd(out), _pd(T))
+    return (out, T) if want_T else out
+
+
+FOOTPRINT_MODES = {"centre": 0, "stencil7": 1, "mc": 2}
+
+
+def philox4x64(counter, key) -> np.ndarray:
+    """Philox4x64-10 of one counter (4 x uint64) and key (2 x uint64)."""
+    c = np.ascontiguousarray(counter, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    u64 = C.POINTER(C.c_uint64)
+    lib().orc_philox4x64(c.ctypes.data_as(u64), k.ctypes.data_as(u64), out.ctypes.data_as(u64))
+    return out
+
+
+def fp_normal(seed: int, q: int, j: int) -> float:
+    """Standard normal number j of receiver q (footprint Monte Carlo offsets)."""
+    return float(lib().orc_fp_normal(seed, q, j))
+
+
+def fp_offsets(mode: str, n_samples: int = 8, seed: int = 0, q: int = 0):
+    """(z (n,3), w (n,)) of one receiver's footprint samples."""
+    z = np.zeros((64, 3))
+    w = np.zeros(64)
+    n = lib().orc_fp_offsets(FOOTPRINT_MODES[mode], n_samples, seed, q, _pd(z), _pd(w))
+    return z[:n].copy(), w[:n].copy()
+
+
+def attenuate_footprint(atlas, radii, lights, q_means, q_quats, q_scales, colors, mode="mc",
+                        n_samples=8, seed=0, light_w=None, direct_frac=1.0, want_T=False,
+                        q_ids=None):
+    """Footprint attenuation: T = sum_i w_i T(mu + R (s . z_i)) (Sec. 3.3, ablation (A)).
+    q_ids: receiver indices keying the Monte Carlo offsets of each row (default 0..Q-1)."""
+    if not 1 <= n_samples <= 64:
+        raise ValueError("n_samples must be in 1..64")
+    atlas = _c64(atlas)
+    L, K, H, W = atlas.shape
+    q_means, q_quats, q_scales, colors = (_c32(a) for a in (q_means, q_quats, q_scales, colors))
+    Q = q_means.shape[0]
+    out = np.zeros((Q, 3))
+    T = np.zeros((Q, L)) if want_T else None
+    lw = _c32(light_w) if light_w is not None else None
+    ids = np.ascontiguousarray(q_ids, dtype=np.int64) if q_ids is not None else None
+    if ids is not None and ids.shape != (Q,):
+        raise ValueError("q_ids must have one index per receiver")
+    lib().orc_attenuate_footprint(_pd(atlas), L, H, W, _pf(_c32(radii)), K, _pf(_c32(lights)),
+                                  _pf(q_means), _pf(q_quats), _pf(q_scales), _pf(colors), Q, _pf(lw),
+                                  float(direct_frac), FOOTPRINT_MODES[mode], n_samples, seed,
+                                  ids.ctypes.data_as(C.POINTER(C.c_int64)) if ids is not None else None,
+                                  _pd(out), _pd(T))
     return (out, T) if want_T else out
 
 

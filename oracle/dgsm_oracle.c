@@ -892,3 +892,116 @@ void orc_relight(const double *sh, const float *means, const float *quats, const
         }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Footprint sampling (Sec. 3.3 and ablation (A) of Sec. 4)                  */
+/* ------------------------------------------------------------------------ */
+
+/* Philox4x64-10, the counter-based generator of Salmon, Moraes, Dror and
+ * Shaw ("Parallel random numbers: as easy as 1, 2, 3", SC 2011): ten rounds,
+ * each taking the two 128-bit products M0 c0 and M1 c2 and mixing their
+ * halves with c1, c3 and the round key; the key is advanced by the Weyl
+ * constants between rounds. */
+void orc_philox4x64(const uint64_t *ctr, const uint64_t *key, uint64_t *out) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        unsigned __int128 p0 = (unsigned __int128)M0 * c0, p1 = (unsigned __int128)M1 * c2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Standard normal number j of receiver q for seed `seed`: Philox4x64-10 at
+ * counter (q, j / 8, 0, 0) and key (seed, 0) gives four 64-bit words; word
+ * (j % 8) / 2 is split into two 32-bit halves, each giving a uniform
+ * u = (h / 2^8 + 1) 2^-24 in (0, 1] from its top 24 bits; Box-Muller then
+ * gives r cos(2 pi u2) for even j and r sin(2 pi u2) for odd j, with
+ * r = sqrt(-2 ln u1). */
+double orc_fp_normal(uint64_t seed, int64_t q, int j) {
+    uint64_t ctr[4] = {(uint64_t)q, (uint64_t)(j / 8), 0, 0}, key[2] = {seed, 0}, w[4];
+    orc_philox4x64(ctr, key, w);
+    uint64_t word = w[(j % 8) / 2];
+    uint32_t lo = (uint32_t)word, hi = (uint32_t)(word >> 32);
+    double u1 = (double)((lo >> 8) + 1u) * (1.0 / 16777216.0);
+    double u2 = (double)((hi >> 8) + 1u) * (1.0 / 16777216.0);
+    double r = sqrt(-2.0 * log(u1));
+    return (j % 2 == 0) ? r * cos(2.0 * ORC_PI * u2) : r * sin(2.0 * ORC_PI * u2);
+}
+
+/* Offsets z_i (n x 3) and weights w_i (sum 1) of one receiver's footprint.
+ * mode 0: the centre alone (z = 0, w = 1).
+ * mode 1: the 7-point stencil 0, +-e_x, +-e_y, +-e_z with weights proportional
+ *         to exp(-|z|^2 / 2) (1 at the centre, e^-1/2 on the axes).
+ * mode 2: n Monte Carlo offsets z_i ~ N(0, I) (orc_fp_normal, normal 3i + c
+ *         for coordinate c), w_i = 1 / n.
+ * Returns the number of samples. */
+int orc_fp_offsets(int mode, int n_samples, uint64_t seed, int64_t q, double *z, double *w) {
+    if (mode == 0) {
+        z[0] = z[1] = z[2] = 0.0;
+        w[0] = 1.0;
+        return 1;
+    }
+    if (mode == 1) {
+        double ea = exp(-0.5), norm = 1.0 + 6.0 * ea;
+        for (int i = 0; i < 21; ++i) z[i] = 0.0;
+        w[0] = 1.0 / norm;
+        for (int a = 0; a < 3; ++a) {
+            z[3 * (1 + 2 * a) + a] = 1.0;
+            z[3 * (2 + 2 * a) + a] = -1.0;
+            w[1 + 2 * a] = ea / norm;
+            w[2 + 2 * a] = ea / norm;
+        }
+        return 7;
+    }
+    for (int i = 0; i < n_samples; ++i) {
+        for (int c = 0; c < 3; ++c) z[3 * i + c] = orc_fp_normal(seed, q, 3 * i + c);
+        w[i] = 1.0 / n_samples;
+    }
+    return n_samples;
+}
+
+/* Footprint attenuation: T_l = sum_i w_i T_l(x_i) with x_i = mu + R (s . z_i)
+ * (rotation-aware offsets in the receiver's principal axes), then the direct
+ * part of the colour is scaled as in orc_attenuate.  n_samples <= 64.
+ * q_ids (may be NULL): the receiver index that keys the Monte Carlo offsets of
+ * row q (default q), so a sample of receivers can be checked on its own. */
+void orc_attenuate_footprint(const double *atlas, int L, int H, int W, const float *radii, int K,
+                             const float *lights, const float *q_means, const float *q_quats,
+                             const float *q_scales, const float *colors_in, int64_t Q,
+                             const float *light_w, double direct_frac, int mode, int n_samples,
+                             uint64_t seed, const int64_t *q_ids, double *colors_out,
+                             double *T_out) {
+    int64_t LS = (int64_t)K * H * W;
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < Q; ++q) {
+        double z[3 * 64], w[64], R[9];
+        int n = orc_fp_offsets(mode, n_samples, seed, q_ids ? q_ids[q] : q, z, w);
+        orc_quat_to_rot(q_quats + 4 * q, R);
+        double pts[3 * 64];
+        for (int i = 0; i < n; ++i)
+            for (int r = 0; r < 3; ++r) {
+                double acc = q_means[3 * q + r];
+                for (int c = 0; c < 3; ++c) acc += R[3 * r + c] * ((double)q_scales[3 * q + c] * z[3 * i + c]);
+                pts[3 * i + r] = acc;
+            }
+        double accl = 0;
+        for (int l = 0; l < L; ++l) {
+            double o[3] = {lights[3 * l], lights[3 * l + 1], lights[3 * l + 2]};
+            double T = 0;
+            for (int i = 0; i < n; ++i) T += w[i] * orc_sample_T(atlas + l * LS, H, W, radii, K, o, pts + 3 * i);
+            if (T_out) T_out[q * L + l] = T;
+            accl += (light_w ? (double)light_w[l] : 1.0 / L) * T;
+        }
+        double f = 1.0 - direct_frac + direct_frac * accl;
+        for (int c = 0; c < 3; ++c) colors_out[3 * q + c] = (double)colors_in[3 * q + c] * f;
+    }
+}

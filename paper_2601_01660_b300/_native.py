@@ -98,6 +98,9 @@ _lib.dgsm_attenuate.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32
 _lib.dgsm_attenuate_dyn.argtypes = [_vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _i32, _i32, _vp,
                                     _i32, _vp, _vp, _vp, _i64, _vp, _f32, _vp, _vp, _vp]
 _lib.dgsm_sample_index.argtypes = [_vp, _vp, _i64, _vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp]
+_lib.dgsm_attenuate_footprint.argtypes = [_vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp,
+                                          _vp, _vp, _i64, _vp, _f32, _i32, _i32, C.c_uint64, _vp,
+                                          _vp, _vp]
 _lib.sh_fit.argtypes = [_vp, _vp, _vp, _vp, _i64, _f64, _vp, _vp, _vp]
 _lib.sh_fit_static.argtypes = [_vp, _vp, _vp, _i64, _f64, _vp, _vp, _vp, _vp]
 _lib.sh_relight.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64,
@@ -286,6 +289,39 @@ def dgsm_attenuate(atlas, radii, lights, q_means, colors, atlas_dyn=None, light_
                                   _ptr(radii), K, _ptr(lights), _ptr(q_means), _ptr(colors), Q,
                                   _ptr(light_w), float(direct_frac), _ptr(out), _ptr(T),
                                   _stream(stream)))
+    return (out, T) if want_T else out
+
+
+FOOTPRINT_MODES = {"centre": 0, "stencil7": 1, "mc": 2}
+
+
+def dgsm_attenuate_footprint(atlas, radii, lights, q_means, q_quats, q_scales, colors, mode="mc",
+                             n_samples=8, seed=0, light_w=None, direct_frac=1.0, out=None,
+                             want_T=False, ctx: Context | None = None, stream=None):
+    """Footprint attenuation (Sec. 3.3; ablation (A)): T averaged over
+    x_i = mu + R (s . z_i) with the 7-point stencil or n_samples Monte Carlo
+    offsets (Philox4x64-10 keyed by seed and receiver index)."""
+    ctx = ctx or context(atlas.device.index)
+    dt = {torch.float32: 0, torch.float16: 1, torch.bfloat16: 2}[atlas.dtype]
+    _need(atlas, "atlas", atlas.dtype)
+    L, K, H, W = atlas.shape
+    _need(radii, "radii")
+    _need(lights, "lights", shape_last=3)
+    _need(q_means, "q_means", shape_last=3)
+    _need(q_quats, "q_quats", shape_last=4)
+    _need(q_scales, "q_scales", shape_last=3)
+    _need(colors, "colors", shape_last=3)
+    if light_w is not None:
+        _need(light_w, "light_w")
+    Q = q_means.shape[0]
+    if out is None:
+        out = torch.empty_like(colors)
+    T = torch.empty((Q, L), dtype=torch.float32, device=atlas.device) if want_T else None
+    ctx.check(_lib.dgsm_attenuate_footprint(
+        ctx.handle, _ptr(atlas), dt, L, H, W, _ptr(radii), K, _ptr(lights), _ptr(q_means),
+        _ptr(q_quats), _ptr(q_scales), _ptr(colors), Q, _ptr(light_w), float(direct_frac),
+        FOOTPRINT_MODES[mode], int(n_samples), int(seed) & (2**64 - 1), _ptr(out), _ptr(T),
+        _stream(stream)))
     return (out, T) if want_T else out
 
 

@@ -152,6 +152,137 @@ __global__ void __launch_bounds__(ATT_THREADS) attenuate_kernel(
     }
 }
 
+// ---- footprint sampling (Sec. 3.3; ablation (A) of Sec. 4) ----------------
+
+// Philox4x64-10 (Salmon, Moraes, Dror and Shaw, SC 2011): ten rounds of two
+// 64x64 -> 128-bit products, Weyl-sequence key schedule.
+__device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t k1) {
+    constexpr uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    constexpr uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+        const uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+        const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+}
+
+constexpr int FP_THREADS = 128;
+constexpr int FP_MAX_SAMPLES = 32;
+
+// One receiver per thread.  Its sample points x_i = mu + R (s . z_i) are
+// formed once in shared memory ([3 * n][FP_THREADS], conflict-free), then
+// every light averages its lookups over them.
+template <typename T>
+__global__ void __launch_bounds__(FP_THREADS) attenuate_fp_kernel(
+    const T *__restrict__ atlas, int L, int H, int W, const float *__restrict__ radii, int K,
+    const float *__restrict__ lights, const float *__restrict__ qm, const float *__restrict__ qq,
+    const float *__restrict__ qs, const float *cin, int64_t Q, const float *__restrict__ lw, float wd,
+    int mode, int n_mc, uint64_t seed, float *cout, float *__restrict__ Tout) {
+    extern __shared__ float pts[];
+    __shared__ float rs[256], inw[256];
+    __shared__ short tab[SHELL_BINS];
+    __shared__ float ls[64 * 3];
+    __shared__ float wl[64];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        rs[k] = radii[k];
+        inw[k] = k + 1 < K ? 1.0f / (radii[k + 1] - radii[k]) : 0.0f;
+    }
+    for (int k = threadIdx.x; k < 3 * L; k += blockDim.x) ls[k] = lights[k];
+    for (int k = threadIdx.x; k < L; k += blockDim.x) wl[k] = lw ? lw[k] : 1.0f / (float)L;
+    __syncthreads();
+    const ShellTab st = build_shell_tab(rs, K, tab);
+    __syncthreads();
+    const int n = mode == 0 ? 1 : mode == 1 ? 7 : n_mc;
+    const float ea = 0.60653065971263342f;  // exp(-1/2)
+    const float w_ctr = mode == 0 ? 1.0f : mode == 1 ? 1.0f / (1.0f + 6.0f * ea) : 1.0f / (float)n_mc;
+    const float w_ax = mode == 1 ? ea / (1.0f + 6.0f * ea) : w_ctr;
+    const int64_t lstride = (int64_t)K * H * W;
+    float *px = pts + threadIdx.x;  // sample i coordinate c at px[(3 i + c) * FP_THREADS]
+    for (int64_t q = (int64_t)blockIdx.x * FP_THREADS + threadIdx.x; q < Q;
+         q += (int64_t)gridDim.x * FP_THREADS) {
+        const float mx = __ldg(qm + 3 * q), my = __ldg(qm + 3 * q + 1), mz = __ldg(qm + 3 * q + 2);
+        const float c0 = cin[3 * q], c1 = cin[3 * q + 1], c2 = cin[3 * q + 2];
+        float R[9];
+        {
+            float w = __ldg(qq + 4 * q), x = __ldg(qq + 4 * q + 1), y = __ldg(qq + 4 * q + 2),
+                  z = __ldg(qq + 4 * q + 3);
+            const float inv = rsqrtf(w * w + x * x + y * y + z * z);
+            w *= inv; x *= inv; y *= inv; z *= inv;
+            R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+            R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+            R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+        }
+        const float sc[3] = {__ldg(qs + 3 * q), __ldg(qs + 3 * q + 1), __ldg(qs + 3 * q + 2)};
+        for (int i = 0; i < n; ++i) {
+            px[(3 * i) * FP_THREADS] = mx;
+            px[(3 * i + 1) * FP_THREADS] = my;
+            px[(3 * i + 2) * FP_THREADS] = mz;
+        }
+        // offset component j (sample j / 3, axis j % 3) of size zj: x_i += R[:, c] s_c zj
+        auto add = [&](int j, float zj) {
+            const int i = j / 3, c = j - 3 * i;
+            // column c of R and scale c by selects (no local-memory indexing)
+            const float a = (c == 0 ? sc[0] : c == 1 ? sc[1] : sc[2]) * zj;
+            const float r0 = c == 0 ? R[0] : c == 1 ? R[1] : R[2];
+            const float r1 = c == 0 ? R[3] : c == 1 ? R[4] : R[5];
+            const float r2 = c == 0 ? R[6] : c == 1 ? R[7] : R[8];
+            px[(3 * i) * FP_THREADS] += r0 * a;
+            px[(3 * i + 1) * FP_THREADS] += r1 * a;
+            px[(3 * i + 2) * FP_THREADS] += r2 * a;
+        };
+        if (mode == 1) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                add(3 * (1 + 2 * a) + a, 1.0f);
+                add(3 * (2 + 2 * a) + a, -1.0f);
+            }
+        } else if (mode == 2) {
+            for (int b = 0; b * 8 < 3 * n; ++b) {
+                uint64_t c[4] = {(uint64_t)q, (uint64_t)b, 0ull, 0ull};
+                philox4x64(c, seed, 0ull);
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const uint32_t lo = (uint32_t)c[p], hi = (uint32_t)(c[p] >> 32);
+                    const float u1 = (float)((lo >> 8) + 1u) * 5.9604644775390625e-8f;
+                    const float u2 = (float)((hi >> 8) + 1u) * 5.9604644775390625e-8f;
+                    const float r = sqrtf(-2.0f * logf(u1));
+                    float sn, cs;
+                    sincospif(2.0f * u2, &sn, &cs);
+                    const int j = 8 * b + 2 * p;
+                    if (j < 3 * n) add(j, r * cs);
+                    if (j + 1 < 3 * n) add(j + 1, r * sn);
+                }
+            }
+        }
+        float acc = 0.0f;
+        for (int l = 0; l < L; ++l) {
+            const float ox = ls[3 * l], oy = ls[3 * l + 1], oz = ls[3 * l + 2];
+            const T *A = atlas + l * lstride;
+            float Tl = 0.0f;
+            for (int i = 0; i < n; ++i) {
+                const SampleIndex s = sample_index_tab(px[(3 * i) * FP_THREADS], px[(3 * i + 1) * FP_THREADS],
+                                                       px[(3 * i + 2) * FP_THREADS], ox, oy, oz, H, W, rs,
+                                                       K, tab, st);
+                const float Ti = s.t != 0.0f ? lookup(A, H, W, K, s, rs, inw) : 1.0f;
+                Tl = fmaf(i == 0 ? w_ctr : w_ax, Ti, Tl);
+            }
+            if (Tout) Tout[q * L + l] = Tl;
+            acc = fmaf(wl[l], Tl, acc);
+        }
+        const float f = 1.0f - wd + wd * acc;
+        __stcs(cout + 3 * q, c0 * f);
+        __stcs(cout + 3 * q + 1, c1 * f);
+        __stcs(cout + 3 * q + 2, c2 * f);
+    }
+}
+
 __global__ void sample_index_kernel(const float *__restrict__ pts, int64_t n,
                                     const float *__restrict__ light, int H, int W,
                                     const float *__restrict__ radii, int K,
@@ -277,4 +408,58 @@ extern "C" int dgsm_sample_index(dgsm_ctx *ctx, const float *points, int64_t n, 
                                                                  idx_out, frac_out);
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "sample_index_kernel");
+}
+
+extern "C" int dgsm_attenuate_footprint(dgsm_ctx *ctx, const void *atlas, int32_t dtype, int32_t L,
+                                        int32_t H, int32_t W, const float *radii, int32_t K,
+                                        const float *lights, const float *q_means, const float *q_quats,
+                                        const float *q_scales, const float *colors_in, int64_t n_q,
+                                        const float *light_w, float direct_frac, int32_t mode,
+                                        int32_t n_samples, uint64_t seed, float *colors_out, float *T_out,
+                                        void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (n_q < 0) return fail(ctx, DGSM_ERR_INVALID_ARG, "n_q < 0");
+    if (L < 1 || L > 64) return fail(ctx, DGSM_ERR_INVALID_ARG, "need 1..64 lights");
+    if (H < 1 || W < 1 || H > 4096 || W > 4096) return fail(ctx, DGSM_ERR_INVALID_ARG, "H, W must be in 1..4096");
+    if (K < 1 || K > 256) return fail(ctx, DGSM_ERR_INVALID_ARG, "K must be in 1..256");
+    if (dtype < DGSM_F32 || dtype > DGSM_BF16) return fail(ctx, DGSM_ERR_INVALID_ARG, "bad dtype");
+    if (mode < DGSM_FP_CENTRE || mode > DGSM_FP_MC) return fail(ctx, DGSM_ERR_INVALID_ARG, "bad footprint mode");
+    if (mode == DGSM_FP_MC && (n_samples < 1 || n_samples > FP_MAX_SAMPLES))
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "n_samples must be in 1..32");
+    if (!atlas || !radii || !lights) return fail(ctx, DGSM_ERR_INVALID_ARG, "null atlas, radii or lights");
+    if (n_q > 0 && (!q_means || !q_quats || !q_scales || !colors_in || !colors_out))
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "null query array");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    if (n_q == 0) return DGSM_OK;
+    const int n = mode == DGSM_FP_CENTRE ? 1 : mode == DGSM_FP_STENCIL7 ? 7 : n_samples;
+    const size_t smem = (size_t)3 * n * FP_THREADS * sizeof(float);
+    const int grid = (int)std::min<int64_t>((n_q + FP_THREADS - 1) / FP_THREADS, (int64_t)ctx->num_sms * 16);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (dtype) {
+        case DGSM_F32:
+            e = cudaFuncSetAttribute(attenuate_fp_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                attenuate_fp_kernel<float><<<grid, FP_THREADS, smem, s>>>(
+                    (const float *)atlas, L, H, W, radii, K, lights, q_means, q_quats, q_scales, colors_in, n_q,
+                    light_w, direct_frac, mode, n_samples, seed, colors_out, T_out);
+            break;
+        case DGSM_F16:
+            e = cudaFuncSetAttribute(attenuate_fp_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                attenuate_fp_kernel<__half><<<grid, FP_THREADS, smem, s>>>(
+                    (const __half *)atlas, L, H, W, radii, K, lights, q_means, q_quats, q_scales, colors_in, n_q,
+                    light_w, direct_frac, mode, n_samples, seed, colors_out, T_out);
+            break;
+        default:
+            e = cudaFuncSetAttribute(attenuate_fp_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e == cudaSuccess)
+                attenuate_fp_kernel<__nv_bfloat16><<<grid, FP_THREADS, smem, s>>>(
+                    (const __nv_bfloat16 *)atlas, L, H, W, radii, K, lights, q_means, q_quats, q_scales,
+                    colors_in, n_q, light_w, direct_frac, mode, n_samples, seed, colors_out, T_out);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "attenuate_fp: smem attribute");
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "attenuate_fp_kernel");
 }

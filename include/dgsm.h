@@ -75,6 +75,15 @@ typedef struct {
     int32_t max_pairs;
 } dgsm_params;
 
+/* Receiver-driven region of interest of dgsm_build_roi (device pointers). */
+typedef struct {
+    const float *recv_means; /* (n_recv,3) receiver centres, for instance the scene Gaussians */
+    int64_t n_recv;
+    const float *box;        /* 5 floats c_x, c_y, R, z_min, z_max (dgsm_roi_box writes them) */
+    uint8_t *mask_out;       /* (n_lights,H,W) or NULL: 1 on the texels of P, else 0 */
+    int32_t *krange_out;     /* (n_lights,2) or NULL: k_min, k_max (k_max = -1: empty) */
+} dgsm_roi;
+
 /* Counters of the last dgsm_build on a context. */
 typedef struct {
     int64_t n_pairs;      /* binned (tile, Gaussian) pairs */
@@ -136,6 +145,34 @@ int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales, const flo
                const float *opac, int64_t n, const float *lights, int32_t n_lights, int32_t H,
                int32_t W, const float *radii, int32_t K, const dgsm_params *params, void *atlas,
                void *stream);
+
+/* dgsm_build restricted to a receiver-driven region of interest (Sec. 3.2,
+ * "Receiver-driven ROI"; the timing ablation (D) of Sec. 4).  Receivers
+ * whose centres lie in the box B = {|x - c_x| <= R, |y - c_y| <= R,
+ * z_min <= z <= z_max} are projected into each light's atlas; P is the set
+ * of texels their trilinear lookups read (the 2 x 2 bilinear taps of each,
+ * clamped to the edge) and [k_min, k_max] the shells that bracket their
+ * distances.  On R = P x {k_min..k_max} the atlas equals dgsm_build's; on
+ * every other voxel it is 1.  Only tiles holding a texel of P are binned and
+ * evaluated, and Gaussians wholly beyond shell k_max are skipped, so the
+ * cost follows the region, not the atlas.  Receivers in B are attenuated by
+ * dgsm_attenuate exactly as with the dense atlas (up to summation order).
+ * The box test and the projections use the single-precision index decisions
+ * of dgsm_sample_index.  Other arguments, blocking and errors as for
+ * dgsm_build; roi: host pointer (its arrays are device pointers). */
+int dgsm_build_roi(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
+                   const float *opac, int64_t n, const float *lights, int32_t n_lights, int32_t H,
+                   int32_t W, const float *radii, int32_t K, const dgsm_params *params,
+                   const dgsm_roi *roi, void *atlas, void *stream);
+
+/* The box of a region of interest around an avatar (Sec. 3.2): c = the
+ * alpha-weighted centroid of the avatar's Gaussians (x, y), the given
+ * half-width R, and z from the lowest to the highest avatar centre padded by
+ * z_margin.  avatar_means (n,3), avatar_opac (n): device, n >= 1; box_out:
+ * device, 5 floats (c_x, c_y, R, z_min, z_max; R = -1, an empty box, if the
+ * opacities sum to 0).  Asynchronous; one block. */
+int dgsm_roi_box(dgsm_ctx *ctx, const float *avatar_means, const float *avatar_opac, int64_t n,
+                 float R, float z_margin, float *box_out, void *stream);
 
 /* Counters of the last dgsm_build on ctx (blocks until they are ready). */
 int dgsm_get_build_stats(dgsm_ctx *ctx, dgsm_build_stats *out);

@@ -84,6 +84,8 @@ def _declare(L):
     L.orc_attenuate_footprint.argtypes = [_d, C.c_int, C.c_int, C.c_int, _f, C.c_int, _f, _f, _f, _f,
                                           _f, I64, _f, C.c_double, C.c_int, C.c_int, C.c_uint64,
                                           C.POINTER(C.c_int64), _d, _d]
+    L.orc_f32_roi.argtypes = [_f, I64, _f, _f, C.c_int, C.c_int, C.c_int, _f, C.c_int,
+                              C.POINTER(C.c_uint8), _i32]
     L.orc_sh_basis.argtypes = [_d, _d]
     L.orc_sh_fit.restype = C.c_int
     L.orc_sh_fit.argtypes = [_f, _f, _f, I64, C.c_double, _d]
@@ -279,6 +281,43 @@ def attenuate_footprint(atlas, radii, lights, q_means, q_quats, q_scales, colors
                                   ids.ctypes.data_as(C.POINTER(C.c_int64)) if ids is not None else None,
                                   _pd(out), _pd(T))
     return (out, T) if want_T else out
+
+
+# --- receiver-driven region of interest (Sec. 3.2) ---------------------------
+
+def roi_box(avatar_means, avatar_opac, R=2.0, z_margin=0.1) -> np.ndarray:
+    """(c_x, c_y, R, z_min, z_max): alpha-weighted centroid (x, y) of the avatar
+    and the height range of its centres padded by z_margin (FP64)."""
+    m = np.asarray(avatar_means, dtype=np.float64)
+    a = np.asarray(avatar_opac, dtype=np.float64)
+    c = (a[:, None] * m[:, :2]).sum(0) / a.sum()
+    return np.array([c[0], c[1], R, m[:, 2].min() - z_margin, m[:, 2].max() + z_margin])
+
+
+def f32_roi(recv_means, box, lights, H, W, radii):
+    """Region of interest: texel mask (L,H,W) uint8 and shell ranges (L,2) int32."""
+    recv = _c32(recv_means).reshape(-1, 3)
+    lights = _c32(lights).reshape(-1, 3)
+    radii = _c32(radii)
+    L = lights.shape[0]
+    mask = np.zeros((L, H, W), dtype=np.uint8)
+    kr = np.zeros((L, 2), dtype=np.int32)
+    lib().orc_f32_roi(_pf(recv), recv.shape[0], _pf(_c32(box)), _pf(lights), L, H, W, _pf(radii),
+                      radii.shape[0], mask.ctypes.data_as(C.POINTER(C.c_uint8)), kr.ctypes.data_as(_i32))
+    return mask, kr
+
+
+def roi_atlas(atlas, mask, krange) -> np.ndarray:
+    """The region-of-interest atlas: the dense atlas on P x [k_min, k_max], 1 elsewhere."""
+    out = np.ones_like(atlas)
+    L, K = atlas.shape[:2]
+    for l in range(L):
+        k0, k1 = int(krange[l, 0]), int(krange[l, 1])
+        if k1 < k0:
+            continue
+        sel = mask[l].astype(bool)
+        out[l, k0:k1 + 1][:, sel] = atlas[l, k0:k1 + 1][:, sel]
+    return out
 
 
 # --- FP32 index and binning specification -----------------------------------

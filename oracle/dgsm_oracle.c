@@ -1005,3 +1005,49 @@ void orc_attenuate_footprint(const double *atlas, int L, int H, int W, const flo
         for (int c = 0; c < 3; ++c) colors_out[3 * q + c] = (double)colors_in[3 * q + c] * f;
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Receiver-driven region of interest (Sec. 3.2)                             */
+/* ------------------------------------------------------------------------ */
+
+/* Receivers whose centres lie in the box B = {|x - c_x| <= R, |y - c_y| <= R,
+ * z_min <= z <= z_max} (box = c_x, c_y, R, z_min, z_max; single-precision
+ * decisions) mark, for each light, the texels their trilinear lookup reads:
+ * the 2 x 2 bilinear taps of the FP32 index specification, clamped to the
+ * edge (mask [L][H][W] of 0/1), and the shell range [k_min, k_max] of the two
+ * shells bracketing their distance, clamped to [0, K-1] (krange [L][2];
+ * k_min = K, k_max = -1 when no receiver sees the light).  A receiver at the
+ * light reads nothing (T = 1 there). */
+void orc_f32_roi(const float *recv, int64_t n, const float *box, const float *lights, int L, int H,
+                 int W, const float *radii, int K, uint8_t *mask, int32_t *krange) {
+    int64_t HW = (int64_t)H * W;
+    memset(mask, 0, (size_t)(L * HW));
+    for (int l = 0; l < L; ++l) {
+        krange[2 * l] = K;
+        krange[2 * l + 1] = -1;
+    }
+    for (int64_t q = 0; q < n; ++q) {
+        const float *x = recv + 3 * q;
+        volatile float dx = x[0] - box[0], dy = x[1] - box[1];
+        if (!(fabsf(dx) <= box[2] && fabsf(dy) <= box[2] && x[2] >= box[3] && x[2] <= box[4])) continue;
+        for (int l = 0; l < L; ++l) {
+            int32_t oi[5];
+            float of[3];
+            orc_f32_sample_index(x, lights + 3 * l, H, W, radii, K, oi, of);
+            if (of[2] == 0.0f) continue;
+            int i0 = oi[2], j0 = oi[3], i1 = i0 + 1, j1 = j0 + 1;
+            i0 = i0 < 0 ? 0 : (i0 > H - 1 ? H - 1 : i0);
+            i1 = i1 < 0 ? 0 : (i1 > H - 1 ? H - 1 : i1);
+            j0 = j0 < 0 ? 0 : (j0 > W - 1 ? W - 1 : j0);
+            j1 = j1 < 0 ? 0 : (j1 > W - 1 ? W - 1 : j1);
+            uint8_t *m = mask + l * HW;
+            m[(int64_t)i0 * W + j0] = m[(int64_t)i0 * W + j1] = 1;
+            m[(int64_t)i1 * W + j0] = m[(int64_t)i1 * W + j1] = 1;
+            int k = oi[4];
+            int k0 = k < 0 ? 0 : (k > K - 1 ? K - 1 : k);
+            int k1 = k < 0 ? 0 : (k + 1 > K - 1 ? K - 1 : k + 1);
+            if (k0 < krange[2 * l]) krange[2 * l] = k0;
+            if (k1 > krange[2 * l + 1]) krange[2 * l + 1] = k1;
+        }
+    }
+}

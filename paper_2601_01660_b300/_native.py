@@ -49,6 +49,12 @@ class Params(C.Structure):
         return p
 
 
+class Roi(C.Structure):
+    """Mirror of dgsm_roi."""
+    _fields_ = [("recv_means", C.c_void_p), ("n_recv", C.c_int64), ("box", C.c_void_p),
+                ("mask_out", C.c_void_p), ("krange_out", C.c_void_p)]
+
+
 class RelightParams(C.Structure):
     """Mirror of dgsm_relight_params."""
     _fields_ = [("q", C.c_float), ("gamma", C.c_float), ("t_max", C.c_float), ("eps", C.c_float),
@@ -91,6 +97,9 @@ _lib.dgsm_status_string.restype = C.c_char_p
 _lib.dgsm_build.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i32,
                             C.POINTER(Params), _vp, _vp]
 _lib.dgsm_get_build_stats.argtypes = [_vp, C.POINTER(BuildStats)]
+_lib.dgsm_build_roi.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i32,
+                                C.POINTER(Params), C.POINTER(Roi), _vp, _vp]
+_lib.dgsm_roi_box.argtypes = [_vp, _vp, _vp, _i64, _f32, _f32, _vp, _vp]
 _lib.dgsm_bin.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i32,
                           C.POINTER(Params), _vp, _vp, _i64, C.POINTER(_i64), _vp]
 _lib.dgsm_attenuate.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp,
@@ -261,6 +270,54 @@ def dgsm_bin(means, scales, quats, opac, lights, H, W, radii, params=None, ctx: 
     vals = torch.empty(max(P, 1), dtype=torch.int32, device=means.device)
     ctx.check(_lib.dgsm_bin(*args, _ptr(keys), _ptr(vals), P, C.byref(total), _stream(stream)))
     return keys[:P], vals[:P]
+
+
+def dgsm_build_roi(means, scales, quats, opac, lights, H, W, radii, recv_means, box, params=None,
+                   out=None, want_roi=False, ctx: Context | None = None, stream=None):
+    """dgsm_build on a receiver-driven region of interest (Sec. 3.2): the atlas
+    equals the dense one on P x [k_min, k_max] and is 1 elsewhere.  box: device
+    (5,) float32 (c_x, c_y, R, z_min, z_max).  With want_roi also returns the
+    texel mask (L, H, W) uint8 and the shell ranges (L, 2) int32."""
+    ctx = ctx or context(means.device.index)
+    _need(means, "means", shape_last=3)
+    _need(scales, "scales", shape_last=3)
+    _need(quats, "quats", shape_last=4)
+    _need(opac, "opac")
+    _need(lights, "lights", shape_last=3)
+    _need(radii, "radii")
+    _need(recv_means, "recv_means", shape_last=3)
+    _need(box, "box")
+    if box.numel() != 5:
+        raise ValueError("box must hold 5 floats")
+    p = params if isinstance(params, Params) else Params.make(**(params or {}))
+    L, K, n = lights.shape[0], radii.shape[0], means.shape[0]
+    if out is None:
+        out = torch.empty((L, K, H, W), dtype=TORCH_DTYPES[p.atlas_dtype], device=means.device)
+    _need(out, "out", TORCH_DTYPES[p.atlas_dtype])
+    if tuple(out.shape) != (L, K, H, W):
+        raise ValueError("out must have shape (L, K, H, W)")
+    mask = torch.empty((L, H, W), dtype=torch.uint8, device=means.device) if want_roi else None
+    kr = torch.empty((L, 2), dtype=torch.int32, device=means.device) if want_roi else None
+    addr = lambda t: None if t is None else t.data_ptr()
+    roi = Roi(addr(recv_means), recv_means.shape[0], addr(box), addr(mask), addr(kr))
+    ctx.check(_lib.dgsm_build_roi(ctx.handle, _ptr(means), _ptr(scales), _ptr(quats), _ptr(opac), n,
+                                  _ptr(lights), L, H, W, _ptr(radii), K, C.byref(p), C.byref(roi),
+                                  _ptr(out), _stream(stream)))
+    return (out, mask, kr) if want_roi else out
+
+
+def dgsm_roi_box(avatar_means, avatar_opac, R=2.0, z_margin=0.1, out=None,
+                 ctx: Context | None = None, stream=None):
+    """Box (c_x, c_y, R, z_min, z_max) around an avatar: alpha-weighted centroid
+    and padded height range of its centres (Sec. 3.2)."""
+    ctx = ctx or context(avatar_means.device.index)
+    _need(avatar_means, "avatar_means", shape_last=3)
+    _need(avatar_opac, "avatar_opac")
+    if out is None:
+        out = torch.empty(5, dtype=torch.float32, device=avatar_means.device)
+    ctx.check(_lib.dgsm_roi_box(ctx.handle, _ptr(avatar_means), _ptr(avatar_opac), avatar_means.shape[0],
+                                float(R), float(z_margin), _ptr(out), _stream(stream)))
+    return out
 
 
 def dgsm_attenuate(atlas, radii, lights, q_means, colors, atlas_dyn=None, light_w=None,

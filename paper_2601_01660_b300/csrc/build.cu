@@ -272,8 +272,11 @@ __global__ void __launch_bounds__(256) prep_kernel(
     const float *__restrict__ means, const float *__restrict__ scales,
     const float *__restrict__ quats, const float *__restrict__ opac, int64_t N,
     const float *__restrict__ lights, int L, const float *__restrict__ radii, int K, float kappa,
-    float eps, BuildRec *__restrict__ brec, BinRec *__restrict__ bin, int *__restrict__ status) {
+    float eps, BuildRec *__restrict__ brec, BinRec *__restrict__ bin, int *__restrict__ status,
+    const int *__restrict__ roi_k) {
     // brec == nullptr: binning only (no build record)
+    // roi_k (or nullptr): per light the shell range [kmin, kmax] of a region
+    // of interest; Gaussians wholly beyond shell kmax cannot change it
     const int64_t total = (int64_t)L * N;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -317,7 +320,8 @@ __global__ void __launch_bounds__(256) prep_kernel(
         const float vx = xsub(mx, ox), vy = xsub(my, oy), vz = xsub(mz, oz);
         const float dist = xsqrt(xadd(xadd(xmul(vx, vx), xmul(vy, vy)), xmul(vz, vz)));
         const float lo = xsub(dist, r);
-        if (lo > radii[K - 1]) {
+        const int klast = roi_k ? roi_k[2 * l + 1] : K - 1;
+        if (klast < 0 || lo > radii[klast]) {
             bin[idx] = br;
             continue;
         }
@@ -423,7 +427,10 @@ template <bool EMIT>
 __global__ void __launch_bounds__(256) coarse_bin_kernel(
     const BinRec *__restrict__ bin, int64_t N, int L, int n_super, const float4 *__restrict__ scones,
     uint32_t *__restrict__ counts, const uint32_t *__restrict__ offsets, uint32_t *__restrict__ ckeys,
-    uint32_t *__restrict__ cvals, const unsigned long long *__restrict__ keep, uint32_t cap) {
+    uint32_t *__restrict__ cvals, const unsigned long long *__restrict__ keep, uint32_t cap,
+    const uint8_t *__restrict__ sact) {
+    // sact (or nullptr): per (light, super-tile) 1 if it holds a texel of the
+    // region of interest
     if (EMIT && *keep == 0) return;
     const int64_t total = (int64_t)L * N;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -438,7 +445,7 @@ __global__ void __launch_bounds__(256) coarse_bin_kernel(
         uint32_t c = 0, off = EMIT ? offsets[idx] : 0u;
         if (mode != 0) {
             for (int sidx = 0; sidx < n_super; ++sidx) {
-                if (mode == 2 || cone_overlap(g, scones + 2 * sidx)) {
+                if ((!sact || sact[l * n_super + sidx]) && (mode == 2 || cone_overlap(g, scones + 2 * sidx))) {
                     if (EMIT && off + c < cap) {
                         ckeys[off + c] = (uint32_t)(l * n_super + sidx);
                         cvals[off + c] = gi;
@@ -493,7 +500,8 @@ __global__ void __launch_bounds__(256, 5) fine_count_kernel(
     const Unit *__restrict__ units, const unsigned long long *__restrict__ n_units_dev,
     const uint32_t *__restrict__ cvals, const BinRec *__restrict__ bin, int64_t N, int tx, int ty,
     int sx, int n_tiles, int n_super, const float4 *__restrict__ cones, uint32_t *__restrict__ fcnt,
-    uint32_t *__restrict__ fmask) {
+    uint32_t *__restrict__ fmask, const uint8_t *__restrict__ tact) {
+    // tact (or nullptr): per (light, tile) 1 if it holds a texel of the region of interest
     __shared__ float4 tdat[64 * TDAT_F4];
     __shared__ BinRec grec[FB_STAGE];
     __shared__ uint32_t running[64];
@@ -521,7 +529,7 @@ __global__ void __launch_bounds__(256, 5) fine_count_kernel(
         }
         if (tid < 64) {
             const int a = sa * SUPER + tid / SUPER, b = sb * SUPER + tid % SUPER;
-            tvalid[tid] = a < ty && b < tx;
+            tvalid[tid] = a < ty && b < tx && (!tact || tact[l * n_tiles + a * tx + b]);
             running[tid] = 0u;
         }
         uint32_t *um = fmask + (size_t)u * 64 * 3 * MASK_WORDS;
@@ -858,7 +866,10 @@ __global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_ke
     unsigned int *__restrict__ item_counter, const float *__restrict__ radii, int K, int H, int W,
     int tile, int tx, int n_tiles, int64_t N, int chunk, float *__restrict__ accum,
     unsigned int *__restrict__ done, OutT *__restrict__ atlas,
-    unsigned long long *__restrict__ stats) {
+    unsigned long long *__restrict__ stats, const uint8_t *__restrict__ roi_mask,
+    const int *__restrict__ roi_k) {
+    // roi_mask, roi_k (or nullptr): texels [L][H][W] and shell range [kmin,
+    // kmax] per light of a region of interest; T = 1 outside it
     extern __shared__ float4 smem4[];
     const int nt = tile * tile;
     const int n_tg = nt / 64;
@@ -1016,17 +1027,19 @@ __global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_ke
             __syncthreads();  // the buffer is refilled two chunks later
         }
         // ---- finalize: prefix over shells, T = exp(-tau) (Eq. 4) ----
+        const int kmin = roi_k ? roi_k[2 * l] : 0, kmax = roi_k ? roi_k[2 * l + 1] : K - 1;
         if (n_items == 1) {
             for (int e = tid; e < nt; e += BT_THREADS) {
                 if (tdir[e].w == 0.0f) continue;
                 const int i = tile_i * tile + e / tile, j = tile_j * tile + e % tile;
                 OutT *dst = atlas + (int64_t)l * K * HW + (int64_t)i * W + j;
+                const bool in = !roi_mask || roi_mask[(int64_t)l * HW + (int64_t)i * W + j];
                 float tau = 0.0f, Tprev = 1.0f;
                 for (int k = 0; k < K; ++k) {
                     tau += D[k * nt + e];
                     const float T = fminf(expf(-tau), Tprev);  // kept non-increasing in k
                     Tprev = T;
-                    dst[k * HW] = to_store<OutT>(T);
+                    dst[k * HW] = to_store<OutT>(in && k >= kmin && k <= kmax ? T : 1.0f);
                 }
             }
         } else {
@@ -1048,13 +1061,14 @@ __global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_ke
                     const int i = tile_i * tile + e / tile, j = tile_j * tile + e % tile;
                     OutT *dst = atlas + (int64_t)l * K * HW + (int64_t)i * W + j;
                     float *acc = accum + (int64_t)l * K * HW + (int64_t)i * W + j;
+                    const bool in = !roi_mask || roi_mask[(int64_t)l * HW + (int64_t)i * W + j];
                     float tau = 0.0f, Tprev = 1.0f;
                     for (int k = 0; k < K; ++k) {
                         tau += __ldcg(acc + k * HW);
                         acc[k * HW] = 0.0f;  // ready for the next build
                         const float T = fminf(expf(-tau), Tprev);
                         Tprev = T;
-                        dst[k * HW] = to_store<OutT>(T);
+                        dst[k * HW] = to_store<OutT>(in && k >= kmin && k <= kmax ? T : 1.0f);
                     }
                 }
                 if (tid == 0) done[key] = 0u;
@@ -1076,7 +1090,8 @@ template <typename OutT>
 int launch_build_items(dgsm_ctx *ctx, const BuildRec *brec, const uint32_t *vals, const Item *items,
                        const unsigned long long *n_items, unsigned int *counter, const float *radii,
                        int K, int H, int W, int tile, int tx, int n_tiles, int64_t N, int chunk,
-                       float *accum, unsigned int *done, void *atlas, cudaStream_t s) {
+                       float *accum, unsigned int *done, void *atlas, cudaStream_t s,
+                       const uint8_t *roi_mask, const int *roi_k) {
     const size_t smem = build_smem_bytes(K, tile, chunk);
     cudaError_t e = cudaFuncSetAttribute(build_items_kernel<OutT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1087,10 +1102,18 @@ int launch_build_items(dgsm_ctx *ctx, const BuildRec *brec, const uint32_t *vals
     const int grid = std::max(1, per_sm) * ctx->num_sms;
     build_items_kernel<OutT><<<grid, BT_THREADS, smem, s>>>(
         reinterpret_cast<const float4 *>(brec), vals, items, n_items, counter, radii, K, H, W, tile,
-        tx, n_tiles, N, chunk, accum, done, (OutT *)atlas, ctx->d_stats);
+        tx, n_tiles, N, chunk, accum, done, (OutT *)atlas, ctx->d_stats, roi_mask, roi_k);
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "build_items_kernel");
 }
+
+// Device arrays of a receiver-driven region of interest (dgsm_build_roi).
+struct RoiDev {
+    const uint8_t *mask = nullptr;  // [L][H][W] texels of the region
+    const uint8_t *tact = nullptr;  // [L][n_tiles] tiles holding one of them
+    const uint8_t *sact = nullptr;  // [L][n_super] super-tiles holding one of them
+    const int *krange = nullptr;    // [L][2] shell range kmin, kmax (kmax < 0: empty)
+};
 
 struct BinOut {
     int64_t P = 0;
@@ -1146,7 +1169,7 @@ static int read_count(dgsm_ctx *ctx, const unsigned long long *d, cudaStream_t s
 int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
                 const float *opac, int64_t N, const float *lights, int L, int H, int W,
                 const float *radii, int K, const dgsm_params &p, bool build_records, bool want_keys,
-                cudaStream_t s, BinOut *out) {
+                cudaStream_t s, BinOut *out, const RoiDev *roi = nullptr) {
     const int tile = p.tile;
     const int tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
     const int sx = (tx + SUPER - 1) / SUPER, sy = (ty + SUPER - 1) / SUPER;
@@ -1186,9 +1209,10 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     const int grid = (int)std::min<int64_t>((LN + 255) / 256, (int64_t)ctx->num_sms * 16);
     prep_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, N, lights, L, radii, K, p.kappa,
                                      p.eps_cull, build_records ? (BuildRec *)w_br : nullptr,
-                                     (BinRec *)w_bin, ctx->d_status);
+                                     (BinRec *)w_bin, ctx->d_status, roi ? roi->krange : nullptr);
     coarse_bin_kernel<false><<<grid, 256, 0, s>>>((const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles,
-                                                   (uint32_t *)w_cnt, nullptr, nullptr, nullptr, nullptr, 0u);
+                                                   (uint32_t *)w_cnt, nullptr, nullptr, nullptr, nullptr, 0u,
+                                                   roi ? roi->sact : nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "prep/coarse count kernels");
     if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_cnt, (uint32_t *)w_cnt, LN, d_cpairs, s))) return rc;
@@ -1208,7 +1232,8 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     keep_pairs_kernel<<<1, 32, 0, s>>>(d_cpairs, (unsigned long long)capC, d_ckeep, ctx->d_status);
     coarse_bin_kernel<true><<<grid, 256, 0, s>>>((const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles,
                                                   nullptr, (const uint32_t *)w_cnt, (uint32_t *)cka,
-                                                  (uint32_t *)cva, d_ckeep, (uint32_t)capC);
+                                                  (uint32_t *)cva, d_ckeep, (uint32_t)capC,
+                                                  roi ? roi->sact : nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "coarse emit kernel");
     uint32_t *ckeys = (uint32_t *)cka, *cvals = (uint32_t *)cva;
@@ -1238,7 +1263,8 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     void *w_fmask;
     if ((rc = ws_reserve(ctx, WS_FMASK, sizeof(uint32_t) * 3 * MASK_WORDS * nf, &w_fmask))) return rc;
     fine_count_kernel<<<fgrid, 256, 0, s>>>(units, d_units, cvals, (const BinRec *)w_bin, N, tx, ty, sx, n_tiles,
-                                            n_super, cones, (uint32_t *)w_fcnt, (uint32_t *)w_fmask);
+                                            n_super, cones, (uint32_t *)w_fcnt, (uint32_t *)w_fmask,
+                                            roi ? roi->tact : nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fine count kernel");
     if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_fcnt, (uint32_t *)w_foff, (int64_t)nf, d_pairs, s)))
@@ -1275,13 +1301,11 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
 
 using namespace dgsm;
 
-extern "C" int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales,
-                          const float *quats, const float *opac, int64_t n, const float *lights,
-                          int32_t L, int32_t H, int32_t W, const float *radii, int32_t K,
-                          const dgsm_params *params, void *atlas, void *stream) {
-    if (!ctx) return DGSM_ERR_INVALID_ARG;
-    dgsm_params p;
-    if (params) p = *params; else dgsm_default_params(&p);
+namespace dgsm {
+namespace {
+int check_build(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
+                const float *opac, int64_t n, const float *lights, int32_t L, int32_t H, int32_t W,
+                const float *radii, int32_t K, const dgsm_params &p, void *atlas) {
     int rc = check_common(ctx, means, scales, opac, n, lights, L, H, W, radii, K, p);
     if (rc) return rc;
     if (p.tile == 4) return fail(ctx, DGSM_ERR_INVALID_ARG, "dgsm_build supports tile 8 or 16");
@@ -1291,10 +1315,18 @@ extern "C" int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales
         return fail(ctx, DGSM_ERR_INVALID_ARG, "atlas_dtype must be DGSM_F32, DGSM_F16 or DGSM_BF16");
     if (build_smem_bytes(K, p.tile, p.chunk) > 220 * 1024)
         return fail(ctx, DGSM_ERR_INVALID_ARG, "K x tile^2 too large for shared memory: use tile 8");
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
-    cudaStream_t s = (cudaStream_t)stream;
     if (p.max_pairs < 0) return fail(ctx, DGSM_ERR_INVALID_ARG, "max_pairs < 0");
+    return DGSM_OK;
+}
+
+// The build proper (arguments checked, device current); roi (or nullptr)
+// restricts it to a region of interest.
+int build_impl(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
+               const float *opac, int64_t n, const float *lights, int32_t L, int32_t H, int32_t W,
+               const float *radii, int32_t K, const dgsm_params &p, void *atlas, cudaStream_t s,
+               const RoiDev *roi) {
+    int rc;
+    cudaError_t e;
     cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
     e = cudaStreamIsCapturing(s, &cap_st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamIsCapturing");
@@ -1306,7 +1338,7 @@ extern "C" int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales
     if (prof) cudaEventRecord(ev[0], s);
     BinOut b;
     if ((rc = run_binning(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, true, false, s,
-                          &b)))
+                          &b, roi)))
         return rc;
 
     // ---- work items: every tile's list cut into pieces of <= item Gaussians ----
@@ -1345,18 +1377,21 @@ extern "C" int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales
         case DGSM_F32:
             rc = launch_build_items<float>(ctx, b.brec, vals, items, n_items_dev, counter, radii, K,
                                            H, W, p.tile, b.tx, b.n_tiles, n, p.chunk,
-                                           (float *)w_acc, (unsigned *)w_done, atlas, s);
+                                           (float *)w_acc, (unsigned *)w_done, atlas, s,
+                                           roi ? roi->mask : nullptr, roi ? roi->krange : nullptr);
             break;
         case DGSM_F16:
             rc = launch_build_items<__half>(ctx, b.brec, vals, items, n_items_dev, counter, radii,
                                             K, H, W, p.tile, b.tx, b.n_tiles, n, p.chunk,
-                                            (float *)w_acc, (unsigned *)w_done, atlas, s);
+                                            (float *)w_acc, (unsigned *)w_done, atlas, s,
+                                            roi ? roi->mask : nullptr, roi ? roi->krange : nullptr);
             break;
         default:
             rc = launch_build_items<__nv_bfloat16>(ctx, b.brec, vals, items, n_items_dev, counter,
                                                    radii, K, H, W, p.tile, b.tx, b.n_tiles, n,
                                                    p.chunk, (float *)w_acc, (unsigned *)w_done,
-                                                   atlas, s);
+                                                   atlas, s, roi ? roi->mask : nullptr,
+                                                   roi ? roi->krange : nullptr);
     }
     if (rc) return rc;
     if (prof) {
@@ -1364,6 +1399,222 @@ extern "C" int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales
         ++ctx->prof_count;
     }
     return DGSM_OK;
+}
+
+// ---- receiver-driven region of interest (Sec. 3.2, "Receiver-driven ROI") ----
+
+__global__ void roi_init_kernel(int *__restrict__ krange, int L, int K) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < L) {
+        krange[2 * l] = K;
+        krange[2 * l + 1] = -1;
+    }
+}
+
+// Receivers whose centres lie in the box B = {|x - c_x| <= R, |y - c_y| <= R,
+// z_min <= z <= z_max} (single-precision decisions) mark, per light, the
+// texels and shells their trilinear lookup reads (Sec. 3.3): the 2 x 2
+// bilinear taps around their octahedral coordinate and the two shells that
+// bracket their distance, both clamped as the lookup clamps them.  The
+// marked texels form P; the shells give [k_min, k_max].
+__global__ void __launch_bounds__(256) roi_mark_kernel(
+    const float *__restrict__ recv, int64_t n, const float *__restrict__ box,
+    const float *__restrict__ lights, int L, int H, int W, const float *__restrict__ radii, int K,
+    uint8_t *__restrict__ mask, int *__restrict__ krange) {
+    __shared__ int skmin[64], skmax[64];
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        skmin[l] = K;
+        skmax[l] = -1;
+    }
+    __syncthreads();
+    const float cx = box[0], cy = box[1], R = box[2], z0 = box[3], z1 = box[4];
+    const int64_t HW = (int64_t)H * W;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const float x = recv[3 * q], y = recv[3 * q + 1], z = recv[3 * q + 2];
+        if (!(fabsf(xsub(x, cx)) <= R && fabsf(xsub(y, cy)) <= R && z >= z0 && z <= z1)) continue;
+        for (int l = 0; l < L; ++l) {
+            const SampleIndex si = sample_index(x, y, z, lights[3 * l], lights[3 * l + 1], lights[3 * l + 2],
+                                                H, W, radii, K);
+            if (si.t == 0.0f) continue;  // at the light: T = 1 without a lookup
+            const int j0 = min(max(si.bj, 0), W - 1), j1 = min(max(si.bj + 1, 0), W - 1);
+            const int i0 = min(max(si.bi, 0), H - 1), i1 = min(max(si.bi + 1, 0), H - 1);
+            uint8_t *m = mask + l * HW;
+            m[(int64_t)i0 * W + j0] = 1;
+            m[(int64_t)i0 * W + j1] = 1;
+            m[(int64_t)i1 * W + j0] = 1;
+            m[(int64_t)i1 * W + j1] = 1;
+            const int k0 = si.k < 0 ? 0 : min(si.k, K - 1);
+            const int k1 = si.k < 0 ? 0 : min(si.k + 1, K - 1);
+            atomicMin(&skmin[l], k0);
+            atomicMax(&skmax[l], k1);
+        }
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        if (skmax[l] >= 0) {
+            atomicMin(&krange[2 * l], skmin[l]);
+            atomicMax(&krange[2 * l + 1], skmax[l]);
+        }
+    }
+}
+
+// tact[l][t] = 1 if tile t (tile x tile texels) holds a texel of P.
+__global__ void roi_tiles_kernel(const uint8_t *__restrict__ mask, int L, int H, int W, int tile, int tx,
+                                 int n_tiles, uint8_t *__restrict__ tact) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)L * n_tiles) return;
+    const int l = (int)(idx / n_tiles), t = (int)(idx - (int64_t)l * n_tiles);
+    const int ti = t / tx, tj = t - ti * tx;
+    const uint8_t *m = mask + (int64_t)l * H * W;
+    uint8_t any = 0;
+    for (int i = ti * tile; i < min((ti + 1) * tile, H) && !any; ++i)
+        for (int j = tj * tile; j < min((tj + 1) * tile, W); ++j) any |= m[(int64_t)i * W + j];
+    tact[idx] = any;
+}
+
+// sact[l][s] = 1 if super-tile s (SUPER x SUPER tiles) holds an active tile.
+__global__ void roi_super_kernel(const uint8_t *__restrict__ tact, int L, int tx, int ty, int sx,
+                                 int n_tiles, int n_super, uint8_t *__restrict__ sact) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)L * n_super) return;
+    const int l = (int)(idx / n_super), sidx = (int)(idx - (int64_t)l * n_super);
+    const int sa = sidx / sx, sb = sidx - sa * sx;
+    uint8_t any = 0;
+    for (int a = sa * SUPER; a < min((sa + 1) * SUPER, ty); ++a)
+        for (int b = sb * SUPER; b < min((sb + 1) * SUPER, tx); ++b) any |= tact[(int64_t)l * n_tiles + a * tx + b];
+    sact[idx] = any;
+}
+
+// Box of dgsm_roi_box: the alpha-weighted centroid of the avatar (x, y), its
+// centres' height range padded by z_margin.  One block.
+__global__ void __launch_bounds__(1024) roi_box_kernel(const float *__restrict__ means,
+                                                       const float *__restrict__ opac, int64_t n, float R,
+                                                       float z_margin, float *__restrict__ box) {
+    __shared__ double sw[32], sx[32], sy[32];
+    __shared__ float szl[32], szh[32];
+    double w = 0.0, ax = 0.0, ay = 0.0;
+    float zl = INFINITY, zh = -INFINITY;
+    for (int64_t g = threadIdx.x; g < n; g += blockDim.x) {
+        const double a = (double)opac[g];
+        w += a;
+        ax += a * (double)means[3 * g];
+        ay += a * (double)means[3 * g + 1];
+        zl = fminf(zl, means[3 * g + 2]);
+        zh = fmaxf(zh, means[3 * g + 2]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        w += __shfl_down_sync(0xffffffffu, w, o);
+        ax += __shfl_down_sync(0xffffffffu, ax, o);
+        ay += __shfl_down_sync(0xffffffffu, ay, o);
+        zl = fminf(zl, __shfl_down_sync(0xffffffffu, zl, o));
+        zh = fmaxf(zh, __shfl_down_sync(0xffffffffu, zh, o));
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sw[warp] = w; sx[warp] = ax; sy[warp] = ay; szl[warp] = zl; szh[warp] = zh;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double W_ = 0.0, X = 0.0, Y = 0.0;
+        float lo = INFINITY, hi = -INFINITY;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            W_ += sw[k]; X += sx[k]; Y += sy[k];
+            lo = fminf(lo, szl[k]); hi = fmaxf(hi, szh[k]);
+        }
+        const bool ok = W_ > 0.0;
+        box[0] = ok ? (float)(X / W_) : 0.0f;
+        box[1] = ok ? (float)(Y / W_) : 0.0f;
+        box[2] = ok ? R : -1.0f;  // no weight: an empty box
+        box[3] = lo - z_margin;
+        box[4] = hi + z_margin;
+    }
+}
+
+}  // namespace
+}  // namespace dgsm
+
+extern "C" int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales,
+                          const float *quats, const float *opac, int64_t n, const float *lights,
+                          int32_t L, int32_t H, int32_t W, const float *radii, int32_t K,
+                          const dgsm_params *params, void *atlas, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    dgsm_params p;
+    if (params) p = *params; else dgsm_default_params(&p);
+    int rc = check_build(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, atlas);
+    if (rc) return rc;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    return build_impl(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, atlas,
+                      (cudaStream_t)stream, nullptr);
+}
+
+extern "C" int dgsm_build_roi(dgsm_ctx *ctx, const float *means, const float *scales,
+                              const float *quats, const float *opac, int64_t n, const float *lights,
+                              int32_t L, int32_t H, int32_t W, const float *radii, int32_t K,
+                              const dgsm_params *params, const dgsm_roi *roi, void *atlas,
+                              void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    dgsm_params p;
+    if (params) p = *params; else dgsm_default_params(&p);
+    int rc = check_build(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, atlas);
+    if (rc) return rc;
+    if (!roi || !roi->box) return fail(ctx, DGSM_ERR_INVALID_ARG, "null roi or roi box");
+    if (roi->n_recv < 0 || (roi->n_recv > 0 && !roi->recv_means))
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "bad roi receivers");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int tx = (W + p.tile - 1) / p.tile, ty = (H + p.tile - 1) / p.tile;
+    const int sx = (tx + SUPER - 1) / SUPER, sy = (ty + SUPER - 1) / SUPER;
+    const int64_t n_tiles = (int64_t)tx * ty, n_super = (int64_t)sx * sy;
+    const int64_t HW = (int64_t)H * W;
+    const size_t kr_bytes = ((size_t)L * 2 * sizeof(int) + 255) & ~(size_t)255;
+    const size_t m_bytes = ((size_t)(L * HW) + 255) & ~(size_t)255;
+    const size_t t_bytes = ((size_t)(L * n_tiles) + 255) & ~(size_t)255;
+    const size_t total = kr_bytes + m_bytes + t_bytes + (size_t)(L * n_super);
+    void *w;
+    if ((rc = ws_reserve(ctx, WS_ROI, total, &w))) return rc;
+    RoiDev r;
+    int *krange = (int *)w;
+    uint8_t *mask = (uint8_t *)w + kr_bytes;
+    uint8_t *tact = mask + m_bytes, *sact = tact + t_bytes;
+    r.krange = krange;
+    r.mask = mask;
+    r.tact = tact;
+    r.sact = sact;
+    e = cudaMemsetAsync(mask, 0, (size_t)(L * HW), s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "roi: memset");
+    roi_init_kernel<<<1, 64, 0, s>>>(krange, L, K);
+    if (roi->n_recv > 0) {
+        const int grid = (int)std::min<int64_t>((roi->n_recv + 255) / 256, (int64_t)ctx->num_sms * 8);
+        roi_mark_kernel<<<grid, 256, 0, s>>>(roi->recv_means, roi->n_recv, roi->box, lights, L, H, W, radii,
+                                             K, mask, krange);
+    }
+    roi_tiles_kernel<<<(int)((L * n_tiles + 255) / 256), 256, 0, s>>>(mask, L, H, W, p.tile, tx, (int)n_tiles,
+                                                                       tact);
+    roi_super_kernel<<<(int)((L * n_super + 255) / 256), 256, 0, s>>>(tact, L, tx, ty, sx, (int)n_tiles,
+                                                                       (int)n_super, sact);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "roi kernels");
+    if (roi->mask_out) e = cudaMemcpyAsync(roi->mask_out, mask, (size_t)(L * HW), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && roi->krange_out)
+        e = cudaMemcpyAsync(roi->krange_out, krange, (size_t)L * 2 * sizeof(int), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "roi: copy out");
+    return build_impl(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, atlas, s, &r);
+}
+
+extern "C" int dgsm_roi_box(dgsm_ctx *ctx, const float *avatar_means, const float *avatar_opac, int64_t n,
+                            float R, float z_margin, float *box_out, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (n < 1 || !avatar_means || !avatar_opac || !box_out)
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "roi box: need n >= 1 and device arrays");
+    if (!(R >= 0.0f) || !(z_margin >= 0.0f)) return fail(ctx, DGSM_ERR_INVALID_ARG, "roi box: R, z_margin >= 0");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    roi_box_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(avatar_means, avatar_opac, n, R, z_margin, box_out);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "roi_box_kernel");
 }
 
 extern "C" int dgsm_get_build_stats(dgsm_ctx *ctx, dgsm_build_stats *out) {

@@ -34,6 +34,7 @@ enum WsSlot {
     WS_UNITS,          // fine-binning work units (+ per-super-tile unit counts)
     WS_FCNT, WS_FOFF,  // per (unit, tile) pair counts and their scan
     WS_FMASK,          // per (unit, tile) bitmaps of the Gaussians that reach it (and its halves)
+    WS_ROI,            // region of interest: shell ranges, texel mask, tile and super-tile flags
     WS_NSLOTS
 };
 

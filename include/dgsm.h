@@ -65,7 +65,18 @@ enum dgsm_dtype { DGSM_F32 = 0, DGSM_F16 = 1, DGSM_BF16 = 2 };
  * (both the (super-tile, Gaussian) and the (tile, Gaussian) pairs; see
  * dgsm_build_stats) and never blocks (so the build can be captured in a CUDA graph; see
  * dgsm_graph_begin).  A build whose pairs exceed max_pairs records
- * DGSM_ERR_WORKSPACE in the status word and leaves T = 1 in its atlas. */
+ * DGSM_ERR_WORKSPACE in the status word and leaves T = 1 in its atlas.
+ * beta_mode: the opacity-to-absorption mapping (ablation (B) of Sec. 4),
+ * with tau* = -ln(1 - alpha):
+ *   1: beta = kappa tau*;
+ *   2: beta = kappa tau* sqrt(tr(A)/3) / sqrt(2 pi), A the precision (Eq. 5,
+ *      the default);
+ *   3: beta = kappa tau* / ((2 pi)^(3/2) sqrt(det Sigma)), Sigma the covariance;
+ *   4: beta = kappa tau* / ((2 pi)^(3/2) s_x s_y s_z); for Sigma = R diag(s^2) R^T
+ *      sqrt(det Sigma) = s_x s_y s_z, so 4 computes the same value as 3.
+ * The culling radius keeps the eps_cull bound under every mapping: the
+ * factor (s_max/s_min) above becomes sqrt(2 pi) s_max (mapping 1) or
+ * s_max / (2 pi s_x s_y s_z) (mappings 3, 4). */
 typedef struct {
     float kappa;
     float eps_cull;
@@ -73,6 +84,7 @@ typedef struct {
     int32_t chunk;
     int32_t atlas_dtype;
     int32_t max_pairs;
+    int32_t beta_mode;
 } dgsm_params;
 
 /* Receiver-driven region of interest of dgsm_build_roi (device pointers). */

@@ -86,6 +86,8 @@ def _declare(L):
                                           C.POINTER(C.c_int64), _d, _d]
     L.orc_f32_roi.argtypes = [_f, I64, _f, _f, C.c_int, C.c_int, C.c_int, _f, C.c_int,
                               C.POINTER(C.c_uint8), _i32]
+    L.orc_set_beta_mode.argtypes = [C.c_int]
+    L.orc_get_beta_mode.restype = C.c_int
     L.orc_sh_basis.argtypes = [_d, _d]
     L.orc_sh_fit.restype = C.c_int
     L.orc_sh_fit.argtypes = [_f, _f, _f, I64, C.c_double, _d]
@@ -128,6 +130,24 @@ def rotation(quat) -> np.ndarray:
     R = np.zeros(9)
     lib().orc_quat_to_rot(_pf(_c32(quat)), _pd(R))
     return R.reshape(3, 3)
+
+
+class beta_mode:
+    """Context manager: the oracle's opacity-to-absorption mapping (1..4; 2 is Eq. 5)."""
+
+    def __init__(self, mode: int):
+        if mode not in (1, 2, 3, 4):
+            raise ValueError("beta mode must be 1..4")
+        self.mode = mode
+
+    def __enter__(self):
+        self.prev = lib().orc_get_beta_mode()
+        lib().orc_set_beta_mode(self.mode)
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_beta_mode(self.prev)
+        return False
 
 
 def beta(scale, alpha: float, kappa: float = 1.0) -> float:

@@ -69,15 +69,52 @@ void orc_precision(const float *s, const float *q, double A[9]) {
         }
 }
 
-/* Eq. 5: tau* = -ln(1-alpha), beta = kappa tau* sqrt(tr(A)/3) / sqrt(2 pi). */
+/* Opacity-to-absorption mapping in use (ablation (B) of Sec. 4): 2 is Eq. 5.
+ * Set for the whole library by orc_set_beta_mode (test infrastructure: one
+ * mapping at a time). */
+static int g_beta_mode = 2;
+void orc_set_beta_mode(int mode) { g_beta_mode = mode; }
+int orc_get_beta_mode(void) { return g_beta_mode; }
+
+/* tau* = -ln(1-alpha) and
+ *   mapping 1: beta = kappa tau*;
+ *   mapping 2 (Eq. 5): beta = kappa tau* sqrt(tr(A)/3) / sqrt(2 pi), A the precision;
+ *   mapping 3: beta = kappa tau* / ((2 pi)^(3/2) sqrt(det Sigma)), Sigma the covariance;
+ *   mapping 4: beta = kappa tau* / ((2 pi)^(3/2) s_x s_y s_z).
+ * det Sigma is taken from the covariance matrix itself (mapping 3) and from the
+ * scales (mapping 4), so the two agree only up to rounding. */
 double orc_beta(const float *s, float alpha, double kappa) {
     double a = alpha;
     if (!(a > 0)) return 0.0;
     if (a > ALPHA_MAX) a = ALPHA_MAX;
     double tau_star = -log1p(-a);
+    double c = pow(2.0 * ORC_PI, 1.5);
+    if (g_beta_mode == 1) return kappa * tau_star;
+    if (g_beta_mode == 4) return kappa * tau_star / (c * (double)s[0] * s[1] * s[2]);
     double trA = 1.0 / ((double)s[0] * s[0]) + 1.0 / ((double)s[1] * s[1]) +
                  1.0 / ((double)s[2] * s[2]);
     return kappa * tau_star * sqrt(trA / 3.0) / sqrt(2.0 * ORC_PI);
+}
+
+/* Mapping 3 needs the rotation: sqrt(det Sigma) of Sigma = R diag(s^2) R^T
+ * formed as a matrix and its determinant expanded by cofactors. */
+static double beta_of(const float *s, const float *q, float alpha, double kappa) {
+    if (g_beta_mode != 3) return orc_beta(s, alpha, kappa);
+    double a = alpha;
+    if (!(a > 0)) return 0.0;
+    if (a > ALPHA_MAX) a = ALPHA_MAX;
+    double tau_star = -log1p(-a);
+    double R[9], S[9];
+    orc_quat_to_rot(q, R);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double acc = 0;
+            for (int k = 0; k < 3; ++k) acc += R[3 * r + k] * ((double)s[k] * s[k]) * R[3 * c + k];
+            S[3 * r + c] = acc;
+        }
+    double det = S[0] * (S[4] * S[8] - S[5] * S[7]) - S[1] * (S[3] * S[8] - S[5] * S[6]) +
+                 S[2] * (S[3] * S[7] - S[4] * S[6]);
+    return kappa * tau_star / (pow(2.0 * ORC_PI, 1.5) * sqrt(det));
 }
 
 /* Eq. 2 coefficients for the ray o + s d: a = d^T A d, b = d^T A (o-mu),
@@ -169,7 +206,7 @@ static orc_gauss *prep_all(const float *means, const float *scales, const float 
     for (int64_t n = 0; n < N; ++n) {
         orc_precision(scales + 3 * n, quats + 4 * n, g[n].A);
         for (int c = 0; c < 3; ++c) g[n].mu[c] = means[3 * n + c];
-        g[n].beta = orc_beta(scales + 3 * n, opac[n], kappa);
+        g[n].beta = beta_of(scales + 3 * n, quats + 4 * n, opac[n], kappa);
     }
     return g;
 }
@@ -464,7 +501,18 @@ int orc_f32_gauss_cone(const float *mu, const float *s, float alpha, const float
     volatile float om = 1.0f - a;
     volatile float odds = a / om;
     volatile float t1 = kappa * odds;
-    volatile float ratio = smax / smin;
+    /* bound of beta sqrt(2 pi / a) / tau* along any ray, per mapping */
+    volatile float ratio;
+    if (g_beta_mode == 1) {
+        ratio = 2.50662827f * smax;
+    } else if (g_beta_mode == 3 || g_beta_mode == 4) {
+        volatile float p01 = s[0] * s[1];
+        volatile float p012 = p01 * s[2];
+        volatile float den = 6.28318531f * p012;
+        ratio = smax / den;
+    } else {
+        ratio = smax / smin;
+    }
     volatile float t2 = t1 * ratio;
     volatile float Q = t2 / eps;
     int e = 0;

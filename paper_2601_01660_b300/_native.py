@@ -38,13 +38,16 @@ class DGSMError(RuntimeError):
 class Params(C.Structure):
     """Mirror of dgsm_params."""
     _fields_ = [("kappa", C.c_float), ("eps_cull", C.c_float), ("tile", C.c_int32),
-                ("chunk", C.c_int32), ("atlas_dtype", C.c_int32), ("max_pairs", C.c_int32)]
+                ("chunk", C.c_int32), ("atlas_dtype", C.c_int32), ("max_pairs", C.c_int32),
+                ("beta_mode", C.c_int32)]
 
     @classmethod
-    def make(cls, kappa=1.0, eps_cull=1e-7, tile=8, chunk=128, atlas_dtype="f32", max_pairs=0):
+    def make(cls, kappa=1.0, eps_cull=1e-7, tile=8, chunk=128, atlas_dtype="f32", max_pairs=0,
+             beta_mode=2):
         p = cls()
         _lib.dgsm_default_params(C.byref(p))
         p.kappa, p.eps_cull, p.tile, p.chunk, p.max_pairs = kappa, eps_cull, tile, chunk, max_pairs
+        p.beta_mode = beta_mode
         p.atlas_dtype = DTYPES[atlas_dtype] if isinstance(atlas_dtype, str) else int(atlas_dtype)
         return p
 

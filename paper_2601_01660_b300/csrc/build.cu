@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(256) prep_kernel(
     const float *__restrict__ quats, const float *__restrict__ opac, int64_t N,
     const float *__restrict__ lights, int L, const float *__restrict__ radii, int K, float kappa,
     float eps, BuildRec *__restrict__ brec, BinRec *__restrict__ bin, int *__restrict__ status,
-    const int *__restrict__ roi_k) {
+    const int *__restrict__ roi_k, int beta_mode) {
     // brec == nullptr: binning only (no build record)
     // roi_k (or nullptr): per light the shell range [kmin, kmax] of a region
     // of interest; Gaussians wholly beyond shell kmax cannot change it
@@ -311,7 +311,12 @@ __global__ void __launch_bounds__(256) prep_kernel(
         const float smax = fmaxf(fmaxf(s0, s1), s2);
         const float smin = fminf(fminf(s0, s1), s2);
         const float odds = xdiv(a, xsub(1.0f, a));
-        const float Q = xdiv(xmul(xmul(kappa, odds), xdiv(smax, smin)), eps);
+        // bound of beta sqrt(2 pi / a) / tau* along any ray, per mapping
+        float gbound;
+        if (beta_mode == 1) gbound = xmul(2.50662827f, smax);
+        else if (beta_mode == 3) gbound = xdiv(smax, xmul(6.28318531f, xmul(xmul(s0, s1), s2)));
+        else gbound = xdiv(smax, smin);
+        const float Q = xdiv(xmul(xmul(kappa, odds), gbound), eps);
         int e = 0;
         frexpf(Q, &e);
         e = max(e, 1);
@@ -377,8 +382,13 @@ __global__ void __launch_bounds__(256) prep_kernel(
         const float wz = M20 * vx + M21 * vy + M22 * vz;
         const float tau_star = -log1pf(-a);
         const float trA = i0 * i0 + i1 * i1 + i2 * i2;
-        // beta sqrt(pi/2) = kappa tau* sqrt(tr A / 3) / sqrt(2 pi) * sqrt(pi/2)
-        const float bpref = 0.5f * kappa * tau_star * sqrtf(trA * (1.0f / 3.0f));
+        // beta sqrt(pi/2), beta from the opacity-to-absorption mapping:
+        //   1: kappa tau*;  2 (Eq. 5): kappa tau* sqrt(tr A / 3) / sqrt(2 pi);
+        //   3: kappa tau* / ((2 pi)^(3/2) s0 s1 s2)
+        float bpref;
+        if (beta_mode == 1) bpref = 1.25331414f * kappa * tau_star;
+        else if (beta_mode == 3) bpref = 1.25331414f * kappa * tau_star / (15.7496099f * (s0 * s1 * s2));
+        else bpref = 0.5f * kappa * tau_star * sqrtf(trA * (1.0f / 3.0f));
         const float hi = dist + r;
         int klo = 0, kend = 0;
         if (!inside) {
@@ -1136,6 +1146,7 @@ int check_common(dgsm_ctx *ctx, const float *means, const float *scales, const f
     if (p.tile != 4 && p.tile != 8 && p.tile != 16) return fail(ctx, DGSM_ERR_INVALID_ARG, "tile must be 4, 8 or 16");
     if (p.chunk < 16 || p.chunk > 128) return fail(ctx, DGSM_ERR_INVALID_ARG, "chunk must be in 16..128");
     if (!(p.kappa >= 0.f) || !(p.eps_cull > 0.f)) return fail(ctx, DGSM_ERR_INVALID_ARG, "kappa >= 0 and eps_cull > 0 required");
+    if (p.beta_mode < 1 || p.beta_mode > 4) return fail(ctx, DGSM_ERR_INVALID_ARG, "beta_mode must be 1..4");
     return DGSM_OK;
 }
 
@@ -1209,7 +1220,8 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     const int grid = (int)std::min<int64_t>((LN + 255) / 256, (int64_t)ctx->num_sms * 16);
     prep_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, N, lights, L, radii, K, p.kappa,
                                      p.eps_cull, build_records ? (BuildRec *)w_br : nullptr,
-                                     (BinRec *)w_bin, ctx->d_status, roi ? roi->krange : nullptr);
+                                     (BinRec *)w_bin, ctx->d_status, roi ? roi->krange : nullptr,
+                                     p.beta_mode == 4 ? 3 : p.beta_mode);
     coarse_bin_kernel<false><<<grid, 256, 0, s>>>((const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles,
                                                    (uint32_t *)w_cnt, nullptr, nullptr, nullptr, nullptr, 0u,
                                                    roi ? roi->sact : nullptr);

@@ -65,6 +65,7 @@ extern "C" void dgsm_default_params(dgsm_params *p) {
     p->chunk = 128;
     p->atlas_dtype = DGSM_F32;
     p->max_pairs = 0;
+    p->beta_mode = 2;
 }
 
 extern "C" void dgsm_default_relight_params(dgsm_relight_params *p) {

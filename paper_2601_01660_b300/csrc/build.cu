@@ -1498,51 +1498,6 @@ __global__ void roi_super_kernel(const uint8_t *__restrict__ tact, int L, int tx
     sact[idx] = any;
 }
 
-// Box of dgsm_roi_box: the alpha-weighted centroid of the avatar (x, y), its
-// centres' height range padded by z_margin.  One block.
-__global__ void __launch_bounds__(1024) roi_box_kernel(const float *__restrict__ means,
-                                                       const float *__restrict__ opac, int64_t n, float R,
-                                                       float z_margin, float *__restrict__ box) {
-    __shared__ double sw[32], sx[32], sy[32];
-    __shared__ float szl[32], szh[32];
-    double w = 0.0, ax = 0.0, ay = 0.0;
-    float zl = INFINITY, zh = -INFINITY;
-    for (int64_t g = threadIdx.x; g < n; g += blockDim.x) {
-        const double a = (double)opac[g];
-        w += a;
-        ax += a * (double)means[3 * g];
-        ay += a * (double)means[3 * g + 1];
-        zl = fminf(zl, means[3 * g + 2]);
-        zh = fmaxf(zh, means[3 * g + 2]);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        w += __shfl_down_sync(0xffffffffu, w, o);
-        ax += __shfl_down_sync(0xffffffffu, ax, o);
-        ay += __shfl_down_sync(0xffffffffu, ay, o);
-        zl = fminf(zl, __shfl_down_sync(0xffffffffu, zl, o));
-        zh = fmaxf(zh, __shfl_down_sync(0xffffffffu, zh, o));
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        sw[warp] = w; sx[warp] = ax; sy[warp] = ay; szl[warp] = zl; szh[warp] = zh;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double W_ = 0.0, X = 0.0, Y = 0.0;
-        float lo = INFINITY, hi = -INFINITY;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            W_ += sw[k]; X += sx[k]; Y += sy[k];
-            lo = fminf(lo, szl[k]); hi = fmaxf(hi, szh[k]);
-        }
-        const bool ok = W_ > 0.0;
-        box[0] = ok ? (float)(X / W_) : 0.0f;
-        box[1] = ok ? (float)(Y / W_) : 0.0f;
-        box[2] = ok ? R : -1.0f;  // no weight: an empty box
-        box[3] = lo - z_margin;
-        box[4] = hi + z_margin;
-    }
-}
-
 }  // namespace
 }  // namespace dgsm
 
@@ -1614,19 +1569,6 @@ extern "C" int dgsm_build_roi(dgsm_ctx *ctx, const float *means, const float *sc
         e = cudaMemcpyAsync(roi->krange_out, krange, (size_t)L * 2 * sizeof(int), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "roi: copy out");
     return build_impl(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, atlas, s, &r);
-}
-
-extern "C" int dgsm_roi_box(dgsm_ctx *ctx, const float *avatar_means, const float *avatar_opac, int64_t n,
-                            float R, float z_margin, float *box_out, void *stream) {
-    if (!ctx) return DGSM_ERR_INVALID_ARG;
-    if (n < 1 || !avatar_means || !avatar_opac || !box_out)
-        return fail(ctx, DGSM_ERR_INVALID_ARG, "roi box: need n >= 1 and device arrays");
-    if (!(R >= 0.0f) || !(z_margin >= 0.0f)) return fail(ctx, DGSM_ERR_INVALID_ARG, "roi box: R, z_margin >= 0");
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
-    roi_box_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(avatar_means, avatar_opac, n, R, z_margin, box_out);
-    e = cudaGetLastError();
-    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "roi_box_kernel");
 }
 
 extern "C" int dgsm_get_build_stats(dgsm_ctx *ctx, dgsm_build_stats *out) {

@@ -225,7 +225,8 @@ def run_ours(args, rank, world, local_rank):
                                    "frac": round(fp32_ach / fp32_peak, 4)},
                           "mufu": {"achieved": round(mufu_ach, 4), "peak": round(mufu_peak, 4),
                                    "frac": round(mufu_ach / mufu_peak, 4)}},
-                "kernel_ms": round(tiles_ms, 4)}
+                "kernel_ms": round(tiles_ms, 4),
+                "ncu_pipe_utilisation": _profiled_pipes("build_items_kernel", args.workload)}
 
     # ---- attenuation roofline (HBM) -----------------------------------------
     # the event timer ticks in ~4 us steps on this part: the mean over steps
@@ -350,6 +351,29 @@ def _profiled_traffic(kernel, workload):
             return None
         return int(fields["dram_bytes_per_launch"].strip())
     except (OSError, KeyError, ValueError):
+        return None
+
+
+def _profiled_pipes(kernel, workload):
+    """ncu pipe utilisation (fraction of peak over active cycles) of `kernel`
+    from the full capture summarised beside its traffic figure, under the same
+    source-hash rule, or None."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", f"{kernel.replace('_kernel', '')}_{workload}.txt")
+    src = os.path.join(ROOT, "paper_2601_01660_b300", "csrc", "build.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if f"source_sha256: {sha}" not in text:
+            return None
+        m = re.search(r"FMA ([0-9.]+)%, ALU ([0-9.]+)%, XU \(MUFU\) ([0-9.]+)%", text)
+        if not m:
+            return None
+        return {"fma": float(m.group(1)) / 100, "alu": float(m.group(2)) / 100,
+                "xu": float(m.group(3)) / 100,
+                "source": "ncu --set full on the room550k case (profiles/build_items_room1p6m.txt)"}
+    except OSError:
         return None
 
 

@@ -310,6 +310,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "gpu_launches": None,
     }
+    line["probe"] = time_probe(nat, sc, means, scales, quats, opac, colors, a0, a1, flush, stream)
     roi_build["dense_ms_per_build"] = line["ms_per_build"]
     if line["ms_per_build"]:
         roi_build["speedup_vs_dense"] = round(line["ms_per_build"] / roi_build["ms"], 3)
@@ -321,6 +322,37 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def time_probe(nat, sc, means, scales, quats, opac, colors, a0, a1, flush, stream):
+    """The cubemap probe of Sec. 3.4 at the avatar: the room without its
+    avatar splatted on six 64x64 faces at the avatar's alpha-weighted
+    centroid, then the SH fit of the rendered radiance (timed apart from the
+    step, L2 flushed, mean of 3 after 2 warm-up calls)."""
+    import torch
+    face = 64
+    keep = torch.cat([torch.arange(0, a0), torch.arange(a1, sc.n)]).to(means.device)
+    sm, ss, sq, so, scol = (t.index_select(0, keep).contiguous() for t in (means, scales, quats, opac, colors))
+    dirs, w = nat.dgsm_cube_dirs(face)
+    rgb = torch.empty((6 * face * face, 3), dtype=torch.float32, device=means.device)
+    ms_r, ms_f = [], []
+    pairs = 0
+    for k in range(5):
+        flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        cen = nat.dgsm_weighted_centroid(means[a0:a1], opac[a0:a1])
+        _, pairs = nat.dgsm_render_cubemap(sm, ss, sq, so, scol, cen, face=face, out=rgb, want_pairs=True)
+        e1.record(stream)
+        nat.sh_fit(dirs, rgb, w)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        if k >= 2:
+            ms_r.append(e0.elapsed_time(e1))
+            ms_f.append(e1.elapsed_time(e2))
+    return {"face": face, "scene_gaussians": int(keep.numel()), "splat_pairs": int(pairs),
+            "render_ms": round(statistics.mean(ms_r), 4), "sh_fit_ms": round(statistics.mean(ms_f), 4),
+            "mean_radiance": [round(float(x), 4) for x in rgb.mean(0).tolist()]}
 
 
 def count_launches(args, L):

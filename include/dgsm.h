@@ -290,6 +290,41 @@ int dgsm_sample_index(dgsm_ctx *ctx, const float *points, int64_t n, const float
 int sh_fit(dgsm_ctx *ctx, const float *dirs, const float *rgb, const float *w, int64_t n,
            double lambda, float *sh_out, double *sh64_out, void *stream);
 
+/* The cubemap probe of Sec. 3.4: the 3DGS scene rendered on the six
+ * 90-degree cube faces at `centre` (for instance the avatar's alpha-weighted
+ * centroid from dgsm_weighted_centroid), face x face pixels each.  Pixel (i, j)
+ * of face f looks along F_f + u_j U_f + v_i V_f with u_j = (2j+1)/face - 1,
+ * v_i = (2i+1)/face - 1 and the cube-map axes (F, U, V) = (+x, -z, -y),
+ * (-x, +z, -y), (+y, +x, +z), (-y, +x, -z), (+z, +x, -y), (-z, -x, -y)
+ * (dgsm_cube_dirs gives the same directions).  Splatting follows 3DGS: the
+ * screen covariance is the Jacobian of the face's pinhole projection at the
+ * Gaussian's mean (its x/z, y/z clamped to +-1.3) applied to the view-space
+ * covariance, plus 0.3 pixel^2; a Gaussian contributes to the pixels whose
+ * centres lie within Mahalanobis distance 3 of its projected mean, with
+ * alpha = min(0.99, opacity exp(-m^2/2)); splats are composited front to back
+ * by view depth (ties by Gaussian index), C += alpha T c, T *= 1 - alpha,
+ * stopping before T would drop below 1e-4; the background is black.
+ * Gaussians whose depth is not above `near` are left out of a face.  The
+ * inclusion test and the depth order are IEEE single-precision operations
+ * in a fixed order.
+ *   means, scales, quats, opac, colors: the n scene Gaussians (device);
+ *   centre: device, 3 floats; face: a multiple of 8 in 8..1024; near > 0;
+ *   rgb_out: device (6 * face * face, 3), faces in the order above, rows i,
+ *   columns j; n_pairs_out: host, the (tile, splat) pairs rendered, or NULL.
+ * Blocks once to size its buffers from the pair count.  Returns DGSM_OK,
+ * DGSM_ERR_INVALID_ARG, DGSM_ERR_WORKSPACE or DGSM_ERR_CUDA. */
+int dgsm_render_cubemap(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
+                        const float *opac, const float *colors, int64_t n, const float *centre,
+                        int32_t face, float near, float *rgb_out, int64_t *n_pairs_out, void *stream);
+
+/* Directions and solid angles of the probe's pixels (Sec. 3.4: the
+ * per-pixel solid-angle weights that correct the cube map's area
+ * distortion): dirs_out (6 * face * face, 3) unit texel-centre directions in
+ * dgsm_render_cubemap's order, w_out (6 * face * face) the exact solid angle
+ * of each texel (sum 4 pi), computed in double precision.  Device pointers;
+ * asynchronous. */
+int dgsm_cube_dirs(dgsm_ctx *ctx, int32_t face, float *dirs_out, float *w_out, void *stream);
+
 /* sh_fit without a context and without allocating device memory.  The paper
  * has no counterpart: this exists for callers that cannot call cudaMalloc --
  * a real-time frame loop in which cudaMalloc/cudaFree would synchronise the

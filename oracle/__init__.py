@@ -88,6 +88,8 @@ def _declare(L):
                               C.POINTER(C.c_uint8), _i32]
     L.orc_set_beta_mode.argtypes = [C.c_int]
     L.orc_get_beta_mode.restype = C.c_int
+    L.orc_render_pixels.argtypes = [_f, _f, _f, _f, _f, I64, _f, C.c_int, C.c_float,
+                                    C.POINTER(C.c_int64), I64, _d]
     L.orc_sh_basis.argtypes = [_d, _d]
     L.orc_sh_fit.restype = C.c_int
     L.orc_sh_fit.argtypes = [_f, _f, _f, I64, C.c_double, _d]
@@ -338,6 +340,31 @@ def roi_atlas(atlas, mask, krange) -> np.ndarray:
         sel = mask[l].astype(bool)
         out[l, k0:k1 + 1][:, sel] = atlas[l, k0:k1 + 1][:, sel]
     return out
+
+
+# --- cubemap probe render (Sec. 3.4) ------------------------------------------
+
+def render_pixels(sc, centre, face, pix, near=0.05) -> np.ndarray:
+    """Radiance (len(pix), 3) of probe pixels pix (index f face^2 + i face + j),
+    brute force over every Gaussian of sc."""
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    out = np.zeros((pix.shape[0], 3))
+    lib().orc_render_pixels(_pf(sc.means), _pf(sc.scales), _pf(sc.quats), _pf(sc.opac), _pf(sc.colors),
+                            sc.n, _pf(_c32(centre)), int(face), float(near),
+                            pix.ctypes.data_as(C.POINTER(C.c_int64)), pix.shape[0], _pd(out))
+    return out
+
+
+def cube_dirs(face: int):
+    """Texel-centre unit directions (6 face^2, 3) of the probe, faces
+    (+x, -x, +y, -y, +z, -z) with the cube-map axes, rows v, columns u."""
+    c = (2.0 * np.arange(face) + 1.0) / face - 1.0
+    uu, vv = np.meshgrid(c, c, indexing="xy")
+    one = np.ones_like(uu)
+    faces = [(one, -vv, -uu), (-one, -vv, uu), (uu, one, vv), (uu, -one, -vv), (uu, -vv, one),
+             (-uu, -vv, -one)]
+    D = np.concatenate([np.stack(f, -1).reshape(-1, 3) for f in faces])
+    return D / np.linalg.norm(D, axis=1, keepdims=True)
 
 
 # --- FP32 index and binning specification -----------------------------------

@@ -1099,3 +1099,152 @@ void orc_f32_roi(const float *recv, int64_t n, const float *box, const float *li
         }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Cubemap probe render (Sec. 3.4): brute force over every Gaussian          */
+/* ------------------------------------------------------------------------ */
+
+/* Face f: forward axis F, texel axes U (columns u), V (rows v) as (axis, sign):
+ * (+x, -z, -y), (-x, +z, -y), (+y, +x, +z), (-y, +x, -z), (+z, +x, -y), (-z, -x, -y). */
+static const int kFaceAxis[6][3] = {{0, 2, 1}, {0, 2, 1}, {1, 0, 2}, {1, 0, 2}, {2, 0, 1}, {2, 0, 1}};
+static const float kFaceSign[6][3] = {{1, -1, -1}, {-1, 1, -1}, {1, 1, 1}, {-1, 1, -1}, {1, 1, -1},
+                                      {-1, -1, -1}};
+
+typedef struct {
+    float mx, my, A, B, C, tz;
+    int ok;
+} orc_splat;
+
+/* R diag(s), single precision, each operation rounded on its own. */
+static void f32_rot_scale(const float *q, const float *s, float *Rs) {
+    float n = sqrtf(((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) + q[3] * q[3]);
+    float w = q[0] / n, x = q[1] / n, y = q[2] / n, z = q[3] / n;
+    float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+    float wx = w * x, wy = w * y, wz = w * z;
+    float R[9] = {1.0f - 2.0f * (yy + zz), 2.0f * (xy - wz), 2.0f * (xz + wy),
+                  2.0f * (xy + wz), 1.0f - 2.0f * (xx + zz), 2.0f * (yz - wx),
+                  2.0f * (xz - wy), 2.0f * (yz + wx), 1.0f - 2.0f * (xx + yy)};
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) Rs[3 * r + k] = R[3 * r + k] * s[k];
+}
+
+/* The splat of a Gaussian on face f seen from o with focal length fl (pixels):
+ * the mean's pixel coordinates, the inverse of the screen covariance
+ * J W Sigma W^T J^T + 0.3 I (J the Jacobian of the pinhole projection at the
+ * mean, its x/z and y/z clamped to +-1.3) and the view depth.  Single
+ * precision, each operation rounded on its own, in the kernel's order. */
+static orc_splat f32_make_splat(const float *mu, const float *Rs, int f, const float *o, float fl,
+                                float near) {
+    orc_splat sp;
+    memset(&sp, 0, sizeof(sp));
+    float t[3] = {mu[0] - o[0], mu[1] - o[1], mu[2] - o[2]};
+    int aF = kFaceAxis[f][0], aU = kFaceAxis[f][1], aV = kFaceAxis[f][2];
+    float sF = kFaceSign[f][0], sU = kFaceSign[f][1], sV = kFaceSign[f][2];
+    float tz = sF * t[aF], tx = sU * t[aU], ty = sV * t[aV];
+    sp.tz = tz;
+    if (!(tz > near)) return sp;
+    float u = tx / tz, v = ty / tz;
+    sp.mx = (u + 1.0f) * fl;
+    sp.my = (v + 1.0f) * fl;
+    float gx[3], gy[3], gz[3], p1[3], p2[3];
+    for (int k = 0; k < 3; ++k) {
+        gx[k] = sU * Rs[3 * aU + k];
+        gy[k] = sV * Rs[3 * aV + k];
+        gz[k] = sF * Rs[3 * aF + k];
+    }
+    float uc = fminf(fmaxf(u, -1.3f), 1.3f), vc = fminf(fmaxf(v, -1.3f), 1.3f);
+    for (int k = 0; k < 3; ++k) {
+        float a1 = uc * gz[k], a2 = vc * gz[k];
+        p1[k] = gx[k] - a1;
+        p2[k] = gy[k] - a2;
+    }
+    float n11 = (p1[0] * p1[0] + p1[1] * p1[1]) + p1[2] * p1[2];
+    float n12 = (p1[0] * p2[0] + p1[1] * p2[1]) + p1[2] * p2[2];
+    float n22 = (p2[0] * p2[0] + p2[1] * p2[1]) + p2[2] * p2[2];
+    float h = fl / tz, h2 = h * h;
+    float a = h2 * n11 + 0.3f, b = h2 * n12, c = h2 * n22 + 0.3f;
+    float det = a * c - b * b;
+    if (!(det > 0.0f)) return sp;
+    sp.A = c / det;
+    sp.B = -b / det;
+    sp.C = a / det;
+    sp.ok = 1;
+    return sp;
+}
+
+static float f32_splat_m2(float px, float py, const orc_splat *sp) {
+    float dx = px - sp->mx, dy = py - sp->my;
+    float t1 = sp->A * (dx * dx), t2 = (2.0f * sp->B) * (dx * dy), t3 = sp->C * (dy * dy);
+    return (t1 + t2) + t3;
+}
+
+typedef struct {
+    uint32_t key;
+    int64_t g;
+    float m2;
+} orc_hit;
+
+static int hit_cmp(const void *x, const void *y) {
+    const orc_hit *a = (const orc_hit *)x, *b = (const orc_hit *)y;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return a->g < b->g ? -1 : (a->g > b->g ? 1 : 0);
+}
+
+/* Radiance of the probe pixels pix[0..npix) (index f face^2 + i face + j) of
+ * the cube at `centre`: every Gaussian with opacity > 0 whose splat on face f
+ * covers the pixel centre within Mahalanobis distance 3 (single-precision
+ * decision), in order of depth (the float's bit pattern) and then index,
+ * composited front to back in double precision with
+ * alpha = min(0.99, opacity exp(-m^2/2)), C += alpha T c, T *= 1 - alpha,
+ * stopping before T would drop below 1e-4. */
+void orc_render_pixels(const float *means, const float *scales, const float *quats, const float *opac,
+                       const float *colors, int64_t n, const float *centre, int face, float near,
+                       const int64_t *pix, int64_t npix, double *rgb_out) {
+    float fl = 0.5f * (float)face;
+    orc_splat *sp = (orc_splat *)malloc(sizeof(orc_splat) * 6 * (size_t)(n > 0 ? n : 1));
+#pragma omp parallel for schedule(static)
+    for (int64_t g = 0; g < n; ++g) {
+        float Rs[9];
+        f32_rot_scale(quats + 4 * g, scales + 3 * g, Rs);
+        for (int f = 0; f < 6; ++f) sp[6 * g + f] = f32_make_splat(means + 3 * g, Rs, f, centre, fl, near);
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t p = 0; p < npix; ++p) {
+        int64_t q = pix[p];
+        int f = (int)(q / ((int64_t)face * face));
+        int rem = (int)(q - (int64_t)f * face * face), i = rem / face, j = rem - i * face;
+        float px = (float)j + 0.5f, py = (float)i + 0.5f;
+        size_t cap = 64, cnt = 0;
+        orc_hit *hits = (orc_hit *)malloc(sizeof(orc_hit) * cap);
+        for (int64_t g = 0; g < n; ++g) {
+            const orc_splat *s = sp + 6 * g + f;
+            if (!s->ok || !(opac[g] > 0.0f)) continue;
+            float m2 = f32_splat_m2(px, py, s);
+            if (!(m2 <= 9.0f)) continue;
+            if (cnt == cap) {
+                cap *= 2;
+                hits = (orc_hit *)realloc(hits, sizeof(orc_hit) * cap);
+            }
+            uint32_t key;
+            memcpy(&key, &s->tz, 4);
+            hits[cnt].key = key;
+            hits[cnt].g = g;
+            hits[cnt].m2 = m2;
+            ++cnt;
+        }
+        qsort(hits, cnt, sizeof(orc_hit), hit_cmp);
+        double T = 1.0, c[3] = {0, 0, 0};
+        for (size_t k = 0; k < cnt; ++k) {
+            int64_t g = hits[k].g;
+            double alpha = (double)opac[g] * exp(-0.5 * (double)hits[k].m2);
+            if (alpha > 0.99) alpha = 0.99;
+            double Tn = T * (1.0 - alpha);
+            if (Tn < 1e-4) break;
+            for (int ch = 0; ch < 3; ++ch) c[ch] += alpha * T * (double)colors[3 * g + ch];
+            T = Tn;
+        }
+        for (int ch = 0; ch < 3; ++ch) rgb_out[3 * p + ch] = c[ch];
+        free(hits);
+    }
+    free(sp);
+}

@@ -114,6 +114,9 @@ _lib.dgsm_attenuate_footprint.argtypes = [_vp, _vp, _i32, _i32, _i32, _i32, _vp,
                                           _vp, _vp, _i64, _vp, _f32, _i32, _i32, C.c_uint64, _vp,
                                           _vp, _vp]
 _lib.sh_fit.argtypes = [_vp, _vp, _vp, _vp, _i64, _f64, _vp, _vp, _vp]
+_lib.dgsm_render_cubemap.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _f32, _vp,
+                                     C.POINTER(_i64), _vp]
+_lib.dgsm_cube_dirs.argtypes = [_vp, _i32, _vp, _vp, _vp]
 _lib.sh_fit_static.argtypes = [_vp, _vp, _vp, _i64, _f64, _vp, _vp, _vp, _vp]
 _lib.sh_relight.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64,
                             C.POINTER(RelightParams), _vp, _vp]
@@ -321,6 +324,36 @@ def dgsm_roi_box(avatar_means, avatar_opac, R=2.0, z_margin=0.1, out=None,
     ctx.check(_lib.dgsm_roi_box(ctx.handle, _ptr(avatar_means), _ptr(avatar_opac), avatar_means.shape[0],
                                 float(R), float(z_margin), _ptr(out), _stream(stream)))
     return out
+
+
+def dgsm_render_cubemap(means, scales, quats, opac, colors, centre, face=64, near=0.05, out=None,
+                        want_pairs=False, ctx: Context | None = None, stream=None):
+    """Cubemap probe (Sec. 3.4): the scene splatted on the six 90-degree faces
+    at `centre` (device, 3 floats); returns (6 * face^2, 3) radiance."""
+    ctx = ctx or context(means.device.index)
+    _need(means, "means", shape_last=3)
+    _need(scales, "scales", shape_last=3)
+    _need(quats, "quats", shape_last=4)
+    _need(opac, "opac")
+    _need(colors, "colors", shape_last=3)
+    _need(centre, "centre")
+    if out is None:
+        out = torch.empty((6 * face * face, 3), dtype=torch.float32, device=means.device)
+    npairs = _i64(0)
+    ctx.check(_lib.dgsm_render_cubemap(ctx.handle, _ptr(means), _ptr(scales), _ptr(quats), _ptr(opac),
+                                       _ptr(colors), means.shape[0], _ptr(centre), int(face), float(near),
+                                       _ptr(out), C.byref(npairs), _stream(stream)))
+    return (out, npairs.value) if want_pairs else out
+
+
+def dgsm_cube_dirs(face=64, device=None, ctx: Context | None = None, stream=None):
+    """(dirs (6 face^2, 3), solid angles (6 face^2)) of the probe's pixels."""
+    ctx = ctx or context(device)
+    dev = torch.device("cuda", ctx.device)
+    dirs = torch.empty((6 * face * face, 3), dtype=torch.float32, device=dev)
+    w = torch.empty(6 * face * face, dtype=torch.float32, device=dev)
+    ctx.check(_lib.dgsm_cube_dirs(ctx.handle, int(face), _ptr(dirs), _ptr(w), _stream(stream)))
+    return dirs, w
 
 
 def dgsm_attenuate(atlas, radii, lights, q_means, colors, atlas_dyn=None, light_w=None,

@@ -35,6 +35,7 @@ enum WsSlot {
     WS_FCNT, WS_FOFF,  // per (unit, tile) pair counts and their scan
     WS_FMASK,          // per (unit, tile) bitmaps of the Gaussians that reach it (and its halves)
     WS_ROI,            // region of interest: shell ranges, texel mask, tile and super-tile flags
+    WS_RENDER,         // cubemap probe render: per-pair splat payloads
     WS_NSLOTS
 };
 

@@ -1,0 +1,389 @@
+// render.cu -- the cubemap probe of Sec. 3.4 on sm_103a: the 3DGS scene
+// splatted on the six 90-degree faces at the avatar, and the faces' texel
+// directions and solid angles, which the SH fit (Eq. 7) takes as its samples.
+//
+// Pipeline per call (all on the caller's stream):
+//   splat_count_kernel  per Gaussian and face: view coordinates, the EWA
+//                       screen covariance (Jacobian of the face's pinhole
+//                       projection at the mean), its inverse and a
+//                       conservative square of tiles around the 3-sigma
+//                       ellipse -> number of (tile, splat) pairs
+//   scan                pair offsets                    (one host sync)
+//   splat_emit_kernel   the pairs: depth key, tile key, splat payload
+//   radix sort          by depth, then stably by tile: each tile's splats
+//                       front to back, ties by Gaussian index
+//   splat_ranges_kernel [start, end) of every tile
+//   splat_render_kernel one block per tile, one thread per pixel: staged
+//                       splats composited front to back,
+//                       C += alpha T c, T *= 1 - alpha, until T < 1e-4.
+// The pixel-inclusion decision (Mahalanobis distance <= 3) and the depth
+// order use IEEE single-precision operations in a fixed order, so they are
+// reproducible on the CPU; the tiles only accelerate it.
+#include <algorithm>
+
+#include "dgsm_internal.cuh"
+
+namespace dgsm {
+namespace {
+
+constexpr int RT = 8;                // render tile edge, pixels
+constexpr int RT_PIX = RT * RT;      // threads per render block
+constexpr float LOWPASS = 0.3f;      // screen-space dilation, pixel^2
+constexpr float JAC_LIMIT = 1.3f;    // |x/z|, |y/z| clamp of the Jacobian
+constexpr float T_STOP = 1e-4f;      // compositing stops below this transmittance
+constexpr float ALPHA_MAX = 0.99f;
+
+// Face f of the cube: forward axis F and the axes U, V along which the face's
+// texel coordinates u (columns) and v (rows) grow, as signed unit axes
+// (axis index, sign).  Direction of texel (u, v) = F + u U + v V.
+__constant__ int c_face_axis[6][3] = {{0, 2, 1}, {0, 2, 1}, {1, 0, 2}, {1, 0, 2}, {2, 0, 1}, {2, 0, 1}};
+__constant__ float c_face_sign[6][3] = {{1, -1, -1}, {-1, 1, -1}, {1, 1, 1}, {-1, 1, -1}, {1, 1, -1},
+                                        {-1, -1, -1}};
+
+struct Splat {
+    float mx, my;      // mean on the face, pixels (pixel j's centre at j + 0.5)
+    float A, B, C;     // inverse screen covariance [[A, B], [B, C]]
+    float tz;          // depth along the face's forward axis
+    int r;             // half-width of the tile square, pixels
+    bool ok;
+};
+
+// The Gaussian's splat on face f (camera at o, focal length fl = face / 2).
+// All steps are IEEE single operations in this order (the CPU oracle repeats
+// them): view coordinates of t = mu - o (signed selections, exact); u = tx/tz,
+// v = ty/tz; mean = ((u + 1) fl, (v + 1) fl); G = rows U, V, F of R diag(s);
+// p1 = g_x - u' g_z, p2 = g_y - v' g_z with u', v' clamped to the Jacobian
+// limit; h = fl / tz; the screen covariance h^2 [[p1.p1, p1.p2], [p1.p2,
+// p2.p2]] + LOWPASS I and its inverse.
+__device__ __forceinline__ Splat make_splat(const float *mu, const float *Rs, int f, const float *o,
+                                            float fl, float near) {
+    Splat sp;
+    sp.ok = false;
+    const float t[3] = {xsub(mu[0], o[0]), xsub(mu[1], o[1]), xsub(mu[2], o[2])};
+    const int aF = c_face_axis[f][0], aU = c_face_axis[f][1], aV = c_face_axis[f][2];
+    const float sF = c_face_sign[f][0], sU = c_face_sign[f][1], sV = c_face_sign[f][2];
+    const float tz = sF * t[aF], tx = sU * t[aU], ty = sV * t[aV];
+    sp.tz = tz;
+    if (!(tz > near)) return sp;
+    const float u = xdiv(tx, tz), v = xdiv(ty, tz);
+    sp.mx = xmul(xadd(u, 1.0f), fl);
+    sp.my = xmul(xadd(v, 1.0f), fl);
+    // rows of G = W R diag(s): row a = sign * row (axis) of Rs (Rs[3 r + k] = R[r][k] s_k)
+    float gx[3], gy[3], gz[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        gx[k] = sU * Rs[3 * aU + k];
+        gy[k] = sV * Rs[3 * aV + k];
+        gz[k] = sF * Rs[3 * aF + k];
+    }
+    const float uc = fminf(fmaxf(u, -JAC_LIMIT), JAC_LIMIT), vc = fminf(fmaxf(v, -JAC_LIMIT), JAC_LIMIT);
+    float p1[3], p2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p1[k] = xsub(gx[k], xmul(uc, gz[k]));
+        p2[k] = xsub(gy[k], xmul(vc, gz[k]));
+    }
+    const float n11 = xdot(p1[0], p1[1], p1[2], p1[0], p1[1], p1[2]);
+    const float n12 = xdot(p1[0], p1[1], p1[2], p2[0], p2[1], p2[2]);
+    const float n22 = xdot(p2[0], p2[1], p2[2], p2[0], p2[1], p2[2]);
+    const float h = xdiv(fl, tz), h2 = xmul(h, h);
+    const float a = xadd(xmul(h2, n11), LOWPASS), b = xmul(h2, n12), c = xadd(xmul(h2, n22), LOWPASS);
+    const float det = xsub(xmul(a, c), xmul(b, b));
+    if (!(det > 0.0f)) return sp;
+    sp.A = xdiv(c, det);
+    sp.B = xdiv(-b, det);
+    sp.C = xdiv(a, det);
+    // largest eigenvalue, then a square that covers the 3-sigma ellipse with a
+    // pixel of margin (it only selects tiles: the ellipse test decides)
+    const float mid = 0.5f * (a + c);
+    const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
+    const float ext = 3.0f * sqrtf(lam) * 1.001f + 1.0f;
+    if (!(ext < 1e6f)) return sp;
+    sp.r = (int)ceilf(ext);
+    sp.ok = true;
+    return sp;
+}
+
+// Mahalanobis distance squared of pixel centre (px, py) from the splat, in a fixed order.
+__device__ __forceinline__ float splat_m2(float px, float py, float mx, float my, float A, float B, float C) {
+    const float dx = xsub(px, mx), dy = xsub(py, my);
+    return xadd(xadd(xmul(A, xmul(dx, dx)), xmul(xmul(2.0f, B), xmul(dx, dy))), xmul(C, xmul(dy, dy)));
+}
+
+// R diag(s) of a Gaussian (quaternion w, x, y, z normalised first), row-major,
+// in IEEE single operations in a fixed order (part of the inclusion decision).
+__device__ __forceinline__ void rot_scale(const float *q, const float *s, float *Rs) {
+    const float n = xsqrt(xadd(xadd(xadd(xmul(q[0], q[0]), xmul(q[1], q[1])), xmul(q[2], q[2])), xmul(q[3], q[3])));
+    const float w = xdiv(q[0], n), x = xdiv(q[1], n), y = xdiv(q[2], n), z = xdiv(q[3], n);
+    const float xx = xmul(x, x), yy = xmul(y, y), zz = xmul(z, z);
+    const float xy = xmul(x, y), xz = xmul(x, z), yz = xmul(y, z);
+    const float wx = xmul(w, x), wy = xmul(w, y), wz = xmul(w, z);
+    const float R[9] = {xsub(1.0f, xmul(2.0f, xadd(yy, zz))), xmul(2.0f, xsub(xy, wz)), xmul(2.0f, xadd(xz, wy)),
+                        xmul(2.0f, xadd(xy, wz)), xsub(1.0f, xmul(2.0f, xadd(xx, zz))), xmul(2.0f, xsub(yz, wx)),
+                        xmul(2.0f, xsub(xz, wy)), xmul(2.0f, xadd(yz, wx)), xsub(1.0f, xmul(2.0f, xadd(xx, yy)))};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Rs[3 * r + k] = xmul(R[3 * r + k], s[k]);
+}
+
+// Tile range of a splat on its face ([i0, i1) x [j0, j1)); empty if off the face.
+__device__ __forceinline__ void splat_tiles(const Splat &sp, int nt, int &i0, int &i1, int &j0, int &j1) {
+    const float lo_x = sp.mx - (float)sp.r, hi_x = sp.mx + (float)sp.r;
+    const float lo_y = sp.my - (float)sp.r, hi_y = sp.my + (float)sp.r;
+    j0 = (int)fmaxf(floorf(lo_x / RT), 0.0f);
+    j1 = (int)fminf(floorf(hi_x / RT) + 1.0f, (float)nt);
+    i0 = (int)fmaxf(floorf(lo_y / RT), 0.0f);
+    i1 = (int)fminf(floorf(hi_y / RT) + 1.0f, (float)nt);
+    if (j1 < j0) j1 = j0;
+    if (i1 < i0) i1 = i0;
+}
+
+__global__ void __launch_bounds__(256) splat_count_kernel(
+    const float *__restrict__ means, const float *__restrict__ scales, const float *__restrict__ quats,
+    const float *__restrict__ opac, int64_t n, const float *__restrict__ centre, int face, float near,
+    uint32_t *__restrict__ counts) {
+    const float o[3] = {centre[0], centre[1], centre[2]};
+    const float fl = 0.5f * (float)face;
+    const int nt = face / RT;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c = 0;
+        if (opac[g] > 0.0f) {
+            float Rs[9];
+            rot_scale(quats + 4 * g, scales + 3 * g, Rs);
+            for (int f = 0; f < 6; ++f) {
+                const Splat sp = make_splat(means + 3 * g, Rs, f, o, fl, near);
+                if (!sp.ok) continue;
+                int i0, i1, j0, j1;
+                splat_tiles(sp, nt, i0, i1, j0, j1);
+                c += (uint32_t)((i1 - i0) * (j1 - j0));
+            }
+        }
+        counts[g] = c;
+    }
+}
+
+// payload of a pair: (mx, my, A, B), (C, opacity, tz, Gaussian index), (r, g, b, 0)
+__global__ void __launch_bounds__(256) splat_emit_kernel(
+    const float *__restrict__ means, const float *__restrict__ scales, const float *__restrict__ quats,
+    const float *__restrict__ opac, const float *__restrict__ colors, int64_t n,
+    const float *__restrict__ centre, int face, float near, const uint32_t *__restrict__ offsets,
+    uint32_t cap, uint32_t *__restrict__ dkey, uint32_t *__restrict__ tkey, uint32_t *__restrict__ pid,
+    float4 *__restrict__ payload) {
+    const float o[3] = {centre[0], centre[1], centre[2]};
+    const float fl = 0.5f * (float)face;
+    const int nt = face / RT;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const float al = opac[g];
+        if (!(al > 0.0f)) continue;
+        uint32_t pos = offsets[g];
+        float Rs[9];
+        rot_scale(quats + 4 * g, scales + 3 * g, Rs);
+        for (int f = 0; f < 6; ++f) {
+            const Splat sp = make_splat(means + 3 * g, Rs, f, o, fl, near);
+            if (!sp.ok) continue;
+            int i0, i1, j0, j1;
+            splat_tiles(sp, nt, i0, i1, j0, j1);
+            for (int i = i0; i < i1; ++i)
+                for (int j = j0; j < j1; ++j, ++pos) {
+                    if (pos >= cap) continue;
+                    dkey[pos] = __float_as_uint(sp.tz);  // tz > 0: the bits order like the values
+                    tkey[pos] = (uint32_t)((f * nt + i) * nt + j);
+                    pid[pos] = pos;
+                    payload[3 * (size_t)pos] = make_float4(sp.mx, sp.my, sp.A, sp.B);
+                    payload[3 * (size_t)pos + 1] = make_float4(sp.C, al, sp.tz, __int_as_float((int)g));
+                    payload[3 * (size_t)pos + 2] =
+                        make_float4(colors[3 * g], colors[3 * g + 1], colors[3 * g + 2], 0.0f);
+                }
+        }
+    }
+}
+
+__global__ void gather_keys_kernel(const uint32_t *__restrict__ order, const uint32_t *__restrict__ tkey_by_pid,
+                                   const unsigned long long *__restrict__ d_n, uint32_t *__restrict__ out) {
+    const unsigned long long n = *d_n;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        out[i] = tkey_by_pid[order[i]];
+}
+
+__global__ void splat_ranges_kernel(const uint32_t *__restrict__ keys, const unsigned long long *__restrict__ d_n,
+                                    uint32_t *__restrict__ ts, uint32_t *__restrict__ te) {
+    const unsigned long long n = *d_n;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t k = keys[i];
+        if (i == 0 || keys[i - 1] != k) ts[k] = (uint32_t)i;
+        if (i + 1 == n || keys[i + 1] != k) te[k] = (uint32_t)(i + 1);
+    }
+}
+
+// One block per tile, one thread per pixel; splats staged RT_PIX at a time.
+__global__ void __launch_bounds__(RT_PIX) splat_render_kernel(
+    const uint32_t *__restrict__ ts, const uint32_t *__restrict__ te, const uint32_t *__restrict__ order,
+    const float4 *__restrict__ payload, int face, float *__restrict__ rgb) {
+    __shared__ float4 s0[RT_PIX], s1[RT_PIX], s2[RT_PIX];
+    const int nt = face / RT;
+    const int tile = blockIdx.x;
+    const int f = tile / (nt * nt), rem = tile - f * nt * nt, ti = rem / nt, tj = rem - ti * nt;
+    const int i = ti * RT + threadIdx.x / RT, j = tj * RT + threadIdx.x % RT;
+    const float px = (float)j + 0.5f, py = (float)i + 0.5f;
+    const uint32_t start = ts[tile], end = te[tile];
+    float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
+    bool done = false;
+    for (uint32_t base = start; base < end; base += RT_PIX) {
+        if (__syncthreads_count(done) == RT_PIX) break;
+        const uint32_t e = base + threadIdx.x;
+        if (e < end) {
+            const uint32_t p = order[e];
+            s0[threadIdx.x] = __ldg(payload + 3 * (size_t)p);
+            s1[threadIdx.x] = __ldg(payload + 3 * (size_t)p + 1);
+            s2[threadIdx.x] = __ldg(payload + 3 * (size_t)p + 2);
+        }
+        __syncthreads();
+        const int cnt = (int)min((uint32_t)RT_PIX, end - base);
+        for (int k = 0; k < cnt && !done; ++k) {
+            const float4 a = s0[k], b = s1[k];
+            const float m2 = splat_m2(px, py, a.x, a.y, a.z, a.w, b.x);
+            if (!(m2 <= 9.0f)) continue;
+            const float alpha = fminf(ALPHA_MAX, b.y * __expf(-0.5f * m2));
+            const float Tn = T * (1.0f - alpha);
+            if (Tn < T_STOP) {
+                done = true;
+                break;
+            }
+            const float4 c = s2[k];
+            const float wgt = alpha * T;
+            cr = fmaf(wgt, c.x, cr);
+            cg = fmaf(wgt, c.y, cg);
+            cb = fmaf(wgt, c.z, cb);
+            T = Tn;
+        }
+    }
+    const size_t pix = ((size_t)f * face + i) * face + j;
+    rgb[3 * pix] = cr;
+    rgb[3 * pix + 1] = cg;
+    rgb[3 * pix + 2] = cb;
+}
+
+// Texel-centre directions of the faces and their exact solid angles,
+// w = omega(u1, v1) - omega(u0, v1) - omega(u1, v0) + omega(u0, v0) with
+// omega(x, y) = atan2(x y, sqrt(x^2 + y^2 + 1)) (the integral of
+// (1 + u^2 + v^2)^(-3/2) over [0, x] x [0, y]), in double precision.
+__global__ void cube_dirs_kernel(int face, float *__restrict__ dirs, float *__restrict__ w) {
+    const int64_t total = 6ll * face * face;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int f = (int)(p / ((int64_t)face * face));
+        const int rem = (int)(p - (int64_t)f * face * face), i = rem / face, j = rem - i * face;
+        const double u0 = 2.0 * j / face - 1.0, u1 = 2.0 * (j + 1) / face - 1.0;
+        const double v0 = 2.0 * i / face - 1.0, v1 = 2.0 * (i + 1) / face - 1.0;
+        auto om = [](double x, double y) { return atan2(x * y, sqrt(x * x + y * y + 1.0)); };
+        w[p] = (float)(om(u1, v1) - om(u0, v1) - om(u1, v0) + om(u0, v0));
+        const double u = 0.5 * (u0 + u1), v = 0.5 * (v0 + v1);
+        double d[3];
+        d[c_face_axis[f][0]] = c_face_sign[f][0];
+        d[c_face_axis[f][1]] = c_face_sign[f][1] * u;
+        d[c_face_axis[f][2]] = c_face_sign[f][2] * v;
+        const double nrm = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        dirs[3 * p] = (float)(d[0] / nrm);
+        dirs[3 * p + 1] = (float)(d[1] / nrm);
+        dirs[3 * p + 2] = (float)(d[2] / nrm);
+    }
+}
+
+}  // namespace
+}  // namespace dgsm
+
+using namespace dgsm;
+
+extern "C" int dgsm_cube_dirs(dgsm_ctx *ctx, int32_t face, float *dirs_out, float *w_out, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (face < 1 || face > 4096 || !dirs_out || !w_out)
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "cube dirs: face in 1..4096 and output arrays required");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    const int64_t total = 6ll * face * face;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx->num_sms * 8);
+    cube_dirs_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(face, dirs_out, w_out);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "cube_dirs_kernel");
+}
+
+extern "C" int dgsm_render_cubemap(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
+                                   const float *opac, const float *colors, int64_t n, const float *centre,
+                                   int32_t face, float near, float *rgb_out, int64_t *n_pairs_out,
+                                   void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(ctx, DGSM_ERR_INVALID_ARG, "render: n out of range");
+    if (n > 0 && (!means || !scales || !quats || !opac || !colors))
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "render: null Gaussian array");
+    if (!centre || !rgb_out) return fail(ctx, DGSM_ERR_INVALID_ARG, "render: null centre or output");
+    if (face < RT || face > 1024 || face % RT != 0)
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "render: face must be a multiple of 8 in 8..1024");
+    if (!(near > 0.0f)) return fail(ctx, DGSM_ERR_INVALID_ARG, "render: near must be > 0");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nt = face / RT, n_tiles = 6 * nt * nt;
+    int rc;
+    void *w_cnt, *w_rng;
+    if ((rc = ws_reserve(ctx, WS_COUNTS, sizeof(uint32_t) * (size_t)std::max<int64_t>(n, 1), &w_cnt))) return rc;
+    // per-tile [start, end), then the 8-byte pair counter
+    const size_t rng_bytes = (2 * sizeof(uint32_t) * (size_t)n_tiles + 7) & ~(size_t)7;
+    if ((rc = ws_reserve(ctx, WS_RANGES, rng_bytes + sizeof(unsigned long long), &w_rng))) return rc;
+    uint32_t *ts = (uint32_t *)w_rng, *te = ts + n_tiles;
+    unsigned long long *d_total = (unsigned long long *)((char *)w_rng + rng_bytes);
+    e = cudaMemsetAsync(w_rng, 0, rng_bytes + sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "render: memset");
+    uint64_t P = 0;
+    if (n > 0) {
+        const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 16);
+        splat_count_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, n, centre, face, near,
+                                                (uint32_t *)w_cnt);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "splat_count_kernel");
+        if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_cnt, (uint32_t *)w_cnt, n, d_total, s))) return rc;
+        e = cudaMemcpyAsync(ctx->h_pinned, d_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "render: pair count");
+        P = ctx->h_pinned[0];
+        if (P >= (1ull << 31)) return fail(ctx, DGSM_ERR_WORKSPACE, "render: more than 2^31 pairs");
+    }
+    if (n_pairs_out) *n_pairs_out = (int64_t)P;
+    if (P > 0) {
+        void *ka, *va, *kb, *vb, *tk, *pl;
+        if ((rc = ws_reserve(ctx, WS_KEYS_A, sizeof(uint32_t) * P, &ka))) return rc;
+        if ((rc = ws_reserve(ctx, WS_VALS_A, sizeof(uint32_t) * P, &va))) return rc;
+        if ((rc = ws_reserve(ctx, WS_KEYS_B, sizeof(uint32_t) * P, &kb))) return rc;
+        if ((rc = ws_reserve(ctx, WS_VALS_B, sizeof(uint32_t) * P, &vb))) return rc;
+        if ((rc = ws_reserve(ctx, WS_CKEYS_A, sizeof(uint32_t) * P, &tk))) return rc;
+        if ((rc = ws_reserve(ctx, WS_RENDER, 3 * sizeof(float4) * P, &pl))) return rc;
+        const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 16);
+        splat_emit_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, colors, n, centre, face, near,
+                                               (const uint32_t *)w_cnt, (uint32_t)P, (uint32_t *)ka,
+                                               (uint32_t *)tk, (uint32_t *)va, (float4 *)pl);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "splat_emit_kernel");
+        // front to back within each tile: sort by depth, then stably by tile
+        uint32_t *keys = (uint32_t *)ka, *vals = (uint32_t *)va;
+        if ((rc = radix_sort_pairs(ctx, &keys, &vals, (uint32_t *)kb, (uint32_t *)vb, d_total, (int64_t)P, 32, s)))
+            return rc;
+        uint32_t *alt_k = keys == (uint32_t *)ka ? (uint32_t *)kb : (uint32_t *)ka;
+        uint32_t *alt_v = vals == (uint32_t *)va ? (uint32_t *)vb : (uint32_t *)va;
+        const int rgrid = (int)std::min<int64_t>(((int64_t)P + 255) / 256, (int64_t)ctx->num_sms * 16);
+        gather_keys_kernel<<<rgrid, 256, 0, s>>>(vals, (const uint32_t *)tk, d_total, alt_k);
+        uint32_t *tkeys = alt_k;
+        int bits = 1;
+        while ((1 << bits) < n_tiles) ++bits;
+        if ((rc = radix_sort_pairs(ctx, &tkeys, &vals, keys, alt_v, d_total, (int64_t)P, bits, s))) return rc;
+        splat_ranges_kernel<<<rgrid, 256, 0, s>>>(tkeys, d_total, ts, te);
+        splat_render_kernel<<<n_tiles, RT_PIX, 0, s>>>(ts, te, vals, (const float4 *)pl, face, rgb_out);
+    } else {
+        splat_render_kernel<<<n_tiles, RT_PIX, 0, s>>>(ts, te, ts, nullptr, face, rgb_out);
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "splat render kernels");
+}

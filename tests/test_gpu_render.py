@@ -1,0 +1,107 @@
+"""GPU parity of the cubemap probe (Sec. 3.4): the splat render against the
+brute-force oracle (every Gaussian at every pixel), the pixel directions and
+solid angles, and the probe of the benchmark's room fed to the SH fit.
+
+Tolerance: the inclusion test (Mahalanobis distance <= 3) and the depth order
+are the same single-precision operations on both sides, so the same splats
+reach a pixel in the same order.  alpha uses the kernel's exp in FP32 against
+FP64 in the oracle (relative 1e-6), and the stop test T < 1e-4 can fall on
+either side of the threshold: the one splat it decides carries at most
+alpha T c < 1e-4 of the colour.  Bound: 2e-4 per channel."""
+import numpy as np
+import pytest
+import torch
+from scipy import integrate
+
+from paper_2601_01660_b300 import scenes
+
+from gpu_util import dev, scene_to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-4
+
+
+@pytest.fixture(scope="module")
+def nat():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2601_01660_b300 import native
+    return native()
+
+
+def _render(nat, sc, centre, face, near=0.05):
+    d = scene_to_dev(sc)
+    return nat.dgsm_render_cubemap(d["means"], d["scales"], d["quats"], d["opac"], d["colors"], dev(centre),
+                                   face=face, near=near, want_pairs=True)
+
+
+@pytest.mark.parametrize("face", [8, 16, 24])
+def test_render_matches_oracle_every_pixel(nat, orc, face):
+    sc = scenes.cube_scene(3000, seed=face, centre=(0.0, 0.0, 0.0), side=6.0)
+    centre = np.float32([0.1, -0.2, 0.3])
+    rgb, P = _render(nat, sc, centre, face)
+    ref = orc.render_pixels(sc, centre, face, np.arange(6 * face * face))
+    err = np.abs(rgb.double().cpu().numpy() - ref)
+    assert P > 0 and ref.max() > 0.3
+    assert err.max() <= TOL and np.median(err) <= 1e-6, err.max()
+
+
+def test_render_large_splats_and_near_plane(nat, orc):
+    # Gaussians close to the probe cover many tiles and straddle faces
+    rng = np.random.default_rng(3)
+    sc = scenes.cube_scene(400, seed=4, centre=(0.0, 0.0, 0.0), side=1.0, log_s_mean=np.log(0.1))
+    sc.means[:20] = np.float32(rng.uniform(-0.06, 0.06, (20, 3)))  # some behind the near plane
+    rgb, _ = _render(nat, sc, [0, 0, 0], 16, near=0.05)
+    ref = orc.render_pixels(sc, [0, 0, 0], 16, np.arange(6 * 256), near=0.05)
+    assert np.abs(rgb.double().cpu().numpy() - ref).max() <= TOL
+
+
+def test_render_empty(nat):
+    sc = scenes.cube_scene(1, seed=0)
+    d = scene_to_dev(scenes.subset(sc, np.arange(0)))
+    rgb = nat.dgsm_render_cubemap(d["means"], d["scales"], d["quats"], d["opac"], d["colors"], dev([0, 0, 0]),
+                                  face=8)
+    assert rgb.shape == (384, 3) and (rgb == 0).all()
+    from paper_2601_01660_b300._native import DGSMError
+    with pytest.raises(DGSMError):
+        nat.dgsm_render_cubemap(d["means"], d["scales"], d["quats"], d["opac"], d["colors"], dev([0, 0, 0]),
+                                face=12)
+
+
+def test_cube_dirs_and_solid_angles(nat, orc):
+    face = 16
+    dirs, w = nat.dgsm_cube_dirs(face)
+    dirs, w = dirs.cpu().numpy(), w.double().cpu().numpy()
+    assert np.abs(dirs - orc.cube_dirs(face)).max() <= 1e-6
+    assert abs(w.sum() - 4 * np.pi) <= 1e-5
+    for p in (0, 37, 255, 256 * 3 + 100):
+        i, j = (p % 256) // face, p % face
+        u0, v0 = 2 * j / face - 1, 2 * i / face - 1
+        ref, _ = integrate.dblquad(lambda v, u: (1 + u * u + v * v) ** -1.5, u0, u0 + 2 / face, v0, v0 + 2 / face)
+        assert abs(w[p] - ref) <= 1e-7 * max(1.0, ref / 1e-3)
+
+
+def test_room_probe_sampled_pixels_and_fit(nat, orc):
+    """The benchmark's room without its avatar, probed at the avatar's
+    alpha-weighted centroid: 300 sampled pixels against the oracle, then the
+    SH fit of the rendered probe against the FP64 oracle fit."""
+    wl = scenes.workload("room1p6m")
+    sc = wl["occluders"]
+    sl = sc.meta["avatar"]
+    keep = np.concatenate([np.arange(0, sl.start), np.arange(sl.stop, sc.n)])
+    scene = scenes.subset(sc, keep)
+    av = scenes.subset(sc, np.arange(sl.start, sl.stop))
+    cen = nat.dgsm_weighted_centroid(dev(av.means), dev(av.opac))
+    centre = cen.cpu().numpy().astype(np.float32)
+    face = 64
+    rgb, P = _render(nat, scene, centre, face)
+    pix = np.random.default_rng(7).choice(6 * face * face, 300, replace=False)
+    ref = orc.render_pixels(scene, centre, face, pix)
+    got = rgb.double().cpu().numpy()[pix]
+    assert np.abs(got - ref).max() <= TOL
+    assert np.median(ref.sum(1)) > 0.1  # the room is around the probe
+    dirs, w = nat.dgsm_cube_dirs(face)
+    sh, sh64 = nat.sh_fit(dirs, rgb, w, want64=True)
+    sh_ref = orc.sh_fit(dirs.cpu().numpy(), rgb.cpu().numpy(), w.cpu().numpy())
+    assert np.allclose(sh64.cpu().numpy(), sh_ref, rtol=1e-9, atol=1e-12)

@@ -650,13 +650,17 @@ void orc_f32_gauss_axes(const float *mu, const float *s, const float *q, const f
  * reach the non-negative side of plane n?  Its support there is
  * n.v + k sqrt(n^T Sigma n); the test compares squares (with k^2 widened by
  * 2^-10 against rounding) when n.v < 0. */
+/* Dot product of the plane tests: a0 b0, then fused + a1 b1, then fused + a2 b2. */
+static float f32_fdot(const float *a, const float *b) {
+    volatile float p = a[0] * b[0];
+    return fmaf(a[2], b[2], fmaf(a[1], b[1], p));
+}
+
 static int f32_plane_ok(const float *n, const float *ax, float k2s) {
-    float nv = f32_dot(n, ax);
+    float nv = f32_fdot(n, ax);
     if (nv >= 0.0f) return 1;
-    float p0 = f32_dot(n, ax + 3), p1 = f32_dot(n, ax + 6), p2 = f32_dot(n, ax + 9);
-    volatile float a0 = p0 * p0, a1 = p1 * p1, a2 = p2 * p2;
-    volatile float s01 = a0 + a1;
-    volatile float ss = s01 + a2;
+    float p[3] = {f32_fdot(n, ax + 3), f32_fdot(n, ax + 6), f32_fdot(n, ax + 9)};
+    volatile float ss = f32_fdot(p, p);
     volatile float rhs = k2s * ss;
     volatile float lhs = nv * nv;
     return lhs <= rhs;
@@ -670,13 +674,11 @@ static unsigned f32_half_mask(const float *pl, const float *ax, float k2s, int i
     if (!f32_plane_ok(pl + 6, ax, k2s) || !f32_plane_ok(pl + 9, ax, k2s)) return 0u;
     unsigned m = 0u;
     if (!hb) return f32_plane_ok(pl, ax, k2s) ? 1u : 0u;
-    float nv = f32_dot(pl + 12, ax);
+    float nv = f32_fdot(pl + 12, ax);
     int mid_pos = 1, mid_neg = 1;   /* the ellipsoid reaches the top / bottom side of the mid plane */
     if (nv != 0.0f) {
-        float p0 = f32_dot(pl + 12, ax + 3), p1 = f32_dot(pl + 12, ax + 6), p2 = f32_dot(pl + 12, ax + 9);
-        volatile float a0 = p0 * p0, a1 = p1 * p1, a2 = p2 * p2;
-        volatile float s01 = a0 + a1;
-        volatile float ss = s01 + a2;
+        float p[3] = {f32_fdot(pl + 12, ax + 3), f32_fdot(pl + 12, ax + 6), f32_fdot(pl + 12, ax + 9)};
+        volatile float ss = f32_fdot(p, p);
         volatile float rhs = k2s * ss;
         volatile float lhs = nv * nv;
         const int reach = lhs <= rhs;

@@ -201,17 +201,23 @@ struct GAxes {
     float v[3], c[9], k2s;
 };
 
+// Dot products of the plane tests as a fused chain a0 b0, then + a1 b1, then
+// + a2 b2, each step one IEEE fused multiply-add (C's fmaf computes the same).
+__device__ __forceinline__ float xfdot(float ax, float ay, float az, float bx, float by, float bz) {
+    return __fmaf_rn(az, bz, __fmaf_rn(ay, by, __fmul_rn(ax, bx)));
+}
+
 __device__ __forceinline__ void plane_terms(const float4 &n, const GAxes &g, float &nv, float &reach) {
-    nv = xdot(n.x, n.y, n.z, g.v[0], g.v[1], g.v[2]);
-    const float p0 = xdot(n.x, n.y, n.z, g.c[0], g.c[1], g.c[2]);
-    const float p1 = xdot(n.x, n.y, n.z, g.c[3], g.c[4], g.c[5]);
-    const float p2 = xdot(n.x, n.y, n.z, g.c[6], g.c[7], g.c[8]);
-    const float ss = xadd(xadd(xmul(p0, p0), xmul(p1, p1)), xmul(p2, p2));
+    nv = xfdot(n.x, n.y, n.z, g.v[0], g.v[1], g.v[2]);
+    const float p0 = xfdot(n.x, n.y, n.z, g.c[0], g.c[1], g.c[2]);
+    const float p1 = xfdot(n.x, n.y, n.z, g.c[3], g.c[4], g.c[5]);
+    const float p2 = xfdot(n.x, n.y, n.z, g.c[6], g.c[7], g.c[8]);
+    const float ss = xfdot(p0, p1, p2, p0, p1, p2);
     reach = (xmul(nv, nv) <= xmul(g.k2s, ss)) ? 1.0f : 0.0f;
 }
 
 __device__ __forceinline__ bool plane_ok(const float4 &n, const GAxes &g) {
-    const float nv = xdot(n.x, n.y, n.z, g.v[0], g.v[1], g.v[2]);
+    const float nv = xfdot(n.x, n.y, n.z, g.v[0], g.v[1], g.v[2]);
     if (nv >= 0.0f) return true;
     float nv2, reach;
     plane_terms(n, g, nv2, reach);

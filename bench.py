@@ -310,7 +310,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "gpu_launches": None,
     }
-    line["probe"] = time_probe(nat, sc, means, scales, quats, opac, colors, a0, a1, flush, stream)
+    line["probe"] = time_probe(nat, sc, means, scales, quats, opac, colors, a0, a1, flush, stream, out)
     roi_build["dense_ms_per_build"] = line["ms_per_build"]
     if line["ms_per_build"]:
         roi_build["speedup_vs_dense"] = round(line["ms_per_build"] / roi_build["ms"], 3)
@@ -324,7 +324,7 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
-def time_probe(nat, sc, means, scales, quats, opac, colors, a0, a1, flush, stream):
+def time_probe(nat, sc, means, scales, quats, opac, colors, a0, a1, flush, stream, final):
     """The cubemap probe of Sec. 3.4 at the avatar: the room without its
     avatar splatted on six 64x64 faces at the avatar's alpha-weighted
     centroid, then the SH fit of the rendered radiance (timed apart from the
@@ -350,9 +350,28 @@ def time_probe(nat, sc, means, scales, quats, opac, colors, a0, a1, flush, strea
         if k >= 2:
             ms_r.append(e0.elapsed_time(e1))
             ms_f.append(e1.elapsed_time(e2))
-    return {"face": face, "scene_gaussians": int(keep.numel()), "splat_pairs": int(pairs),
-            "render_ms": round(statistics.mean(ms_r), 4), "sh_fit_ms": round(statistics.mean(ms_f), 4),
-            "mean_radiance": [round(float(x), 4) for x in rgb.mean(0).tolist()]}
+    probe = {"face": face, "scene_gaussians": int(keep.numel()), "splat_pairs": int(pairs),
+             "render_ms": round(statistics.mean(ms_r), 4), "sh_fit_ms": round(statistics.mean(ms_f), 4),
+             "mean_radiance": [round(float(x), 4) for x in rgb.mean(0).tolist()]}
+    # the final composite: every Gaussian (scene and avatar, the step's
+    # attenuated and relit colours) seen from 3 m at 1280 x 720
+    from paper_2601_01660_b300 import scenes
+    W, H = 1280, 720
+    cam = torch.as_tensor(scenes.look_at_camera([-1.2, -1.5, 1.6], [1.5, 0.0, 0.9], W, H, 60.0))[None].to(means.device)
+    img = torch.empty((1, H, W, 3), dtype=torch.float32, device=means.device)
+    ms_c = []
+    for k in range(5):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, cpairs = nat.dgsm_render_views(means, scales, quats, opac, final, cam, W, H, out=img, want_pairs=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= 2:
+            ms_c.append(e0.elapsed_time(e1))
+    probe["composite"] = {"width": W, "height": H, "gaussians": int(sc.n), "splat_pairs": int(cpairs),
+                          "render_ms": round(statistics.mean(ms_c), 4)}
+    return probe
 
 
 def count_launches(args, L):

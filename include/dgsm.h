@@ -290,23 +290,42 @@ int dgsm_sample_index(dgsm_ctx *ctx, const float *points, int64_t n, const float
 int sh_fit(dgsm_ctx *ctx, const float *dirs, const float *rgb, const float *w, int64_t n,
            double lambda, float *sh_out, double *sh64_out, void *stream);
 
+/* 3DGS splatting into pinhole cameras: the final composite of the relit
+ * avatar in the shadowed scene (Fig. 2's last stage), and the engine of
+ * dgsm_render_cubemap.  Camera c is 16 floats: a rotation R (row-major; rows
+ * the image x axis, the image y axis and the forward axis, world to view),
+ * the position, fx, fy, cx, cy; pixel (i, j) (row i, column j, centre at
+ * (j + 0.5, i + 0.5)) sees the view point (x, y, z) at (fx x/z + cx,
+ * fy y/z + cy).  Splatting follows 3DGS: the screen covariance is the
+ * Jacobian of this projection at the Gaussian's mean (its x/z, y/z clamped to
+ * 1.3 x the half field of view) applied to the view-space covariance, plus
+ * 0.3 pixel^2; a Gaussian contributes to the pixels whose centres lie within
+ * Mahalanobis distance 3 of its projected mean, with alpha = min(0.99,
+ * opacity exp(-m^2/2)); splats are composited front to back by view depth
+ * (ties by Gaussian index), C += alpha T c, T *= 1 - alpha, stopping before T
+ * would drop below 1e-4; the background is black.  Gaussians whose depth is
+ * not above `near` are left out.  The inclusion test and the depth order are
+ * IEEE single-precision operations in a fixed order.
+ *   means, scales, quats, opac, colors: the n Gaussians (device);
+ *   cams: device, n_views x 16 floats, 1 <= n_views <= 64; 1 <= W, H <= 4096;
+ *   near > 0; rgb_out: device (n_views, H, W, 3); n_pairs_out: host, the
+ *   (8x8 tile, splat) pairs rendered, or NULL.
+ * Blocks once to size its buffers from the pair count.  Returns DGSM_OK,
+ * DGSM_ERR_INVALID_ARG, DGSM_ERR_WORKSPACE or DGSM_ERR_CUDA. */
+int dgsm_render_views(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
+                      const float *opac, const float *colors, int64_t n, const float *cams, int32_t n_views,
+                      int32_t W, int32_t H, float near, float *rgb_out, int64_t *n_pairs_out, void *stream);
+
 /* The cubemap probe of Sec. 3.4: the 3DGS scene rendered on the six
  * 90-degree cube faces at `centre` (for instance the avatar's alpha-weighted
  * centroid from dgsm_weighted_centroid), face x face pixels each.  Pixel (i, j)
  * of face f looks along F_f + u_j U_f + v_i V_f with u_j = (2j+1)/face - 1,
  * v_i = (2i+1)/face - 1 and the cube-map axes (F, U, V) = (+x, -z, -y),
  * (-x, +z, -y), (+y, +x, +z), (-y, +x, -z), (+z, +x, -y), (-z, -x, -y)
- * (dgsm_cube_dirs gives the same directions).  Splatting follows 3DGS: the
- * screen covariance is the Jacobian of the face's pinhole projection at the
- * Gaussian's mean (its x/z, y/z clamped to +-1.3) applied to the view-space
- * covariance, plus 0.3 pixel^2; a Gaussian contributes to the pixels whose
- * centres lie within Mahalanobis distance 3 of its projected mean, with
- * alpha = min(0.99, opacity exp(-m^2/2)); splats are composited front to back
- * by view depth (ties by Gaussian index), C += alpha T c, T *= 1 - alpha,
- * stopping before T would drop below 1e-4; the background is black.
- * Gaussians whose depth is not above `near` are left out of a face.  The
- * inclusion test and the depth order are IEEE single-precision operations
- * in a fixed order.
+ * (dgsm_cube_dirs gives the same directions).  Each face is a
+ * dgsm_render_views camera at `centre` with rows (U, V, F) and
+ * fx = fy = cx = cy = face / 2 (a 90-degree field of view); splatting and
+ * compositing as there.
  *   means, scales, quats, opac, colors: the n scene Gaussians (device);
  *   centre: device, 3 floats; face: a multiple of 8 in 8..1024; near > 0;
  *   rgb_out: device (6 * face * face, 3), faces in the order above, rows i,

@@ -90,6 +90,9 @@ def _declare(L):
     L.orc_get_beta_mode.restype = C.c_int
     L.orc_render_pixels.argtypes = [_f, _f, _f, _f, _f, I64, _f, C.c_int, C.c_float,
                                     C.POINTER(C.c_int64), I64, _d]
+    L.orc_render_view_pixels.argtypes = [_f, _f, _f, _f, _f, I64, _f, C.c_int, C.c_int, C.c_int, C.c_float,
+                                         C.POINTER(C.c_int64), I64, _d]
+    L.orc_cube_cams.argtypes = [_f, C.c_int, _f]
     L.orc_sh_basis.argtypes = [_d, _d]
     L.orc_sh_fit.restype = C.c_int
     L.orc_sh_fit.argtypes = [_f, _f, _f, I64, C.c_double, _d]
@@ -352,6 +355,25 @@ def render_pixels(sc, centre, face, pix, near=0.05) -> np.ndarray:
     lib().orc_render_pixels(_pf(sc.means), _pf(sc.scales), _pf(sc.quats), _pf(sc.opac), _pf(sc.colors),
                             sc.n, _pf(_c32(centre)), int(face), float(near),
                             pix.ctypes.data_as(C.POINTER(C.c_int64)), pix.shape[0], _pd(out))
+    return out
+
+
+def render_view_pixels(sc, cams, W, H, pix, near=0.05) -> np.ndarray:
+    """Radiance (len(pix), 3) of pixels pix (index (v H + i) W + j) of the
+    pinhole cameras cams (n_views, 16), brute force over every Gaussian."""
+    cams = _c32(cams).reshape(-1, 16)
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    out = np.zeros((pix.shape[0], 3))
+    lib().orc_render_view_pixels(_pf(sc.means), _pf(sc.scales), _pf(sc.quats), _pf(sc.opac), _pf(sc.colors),
+                                 sc.n, _pf(cams), cams.shape[0], int(W), int(H), float(near),
+                                 pix.ctypes.data_as(C.POINTER(C.c_int64)), pix.shape[0], _pd(out))
+    return out
+
+
+def cube_cams(centre, face: int) -> np.ndarray:
+    """The six probe cameras (6, 16) at centre."""
+    out = np.zeros((6, 16), dtype=np.float32)
+    lib().orc_cube_cams(_pf(_c32(centre)), int(face), _pf(out))
     return out
 
 

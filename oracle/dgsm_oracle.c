@@ -1130,41 +1130,55 @@ static void f32_rot_scale(const float *q, const float *s, float *Rs) {
         for (int k = 0; k < 3; ++k) Rs[3 * r + k] = R[3 * r + k] * s[k];
 }
 
-/* The splat of a Gaussian on face f seen from o with focal length fl (pixels):
- * the mean's pixel coordinates, the inverse of the screen covariance
- * J W Sigma W^T J^T + 0.3 I (J the Jacobian of the pinhole projection at the
- * mean, its x/z and y/z clamped to +-1.3) and the view depth.  Single
+/* Dot product in a fixed order: (a0 b0 + a1 b1) + a2 b2, each step rounded. */
+static float f32_dot3(float a0, float a1, float a2, float b0, float b1, float b2) {
+    float p0 = a0 * b0, p1 = a1 * b1, p2 = a2 * b2;
+    return (p0 + p1) + p2;
+}
+
+/* The splat of a Gaussian in camera cam (16 floats: R row-major with rows x,
+ * y, forward; position; fx, fy, cx, cy) for a W x H image: the mean's pixel
+ * coordinates, the inverse of the screen covariance J W Sigma W^T J^T + 0.3 I
+ * (J the Jacobian of the pinhole projection at the mean, its x/z and y/z
+ * clamped to 1.3 x the half field of view) and the view depth.  Single
  * precision, each operation rounded on its own, in the kernel's order. */
-static orc_splat f32_make_splat(const float *mu, const float *Rs, int f, const float *o, float fl,
+static orc_splat f32_make_splat(const float *mu, const float *Rs, const float *cam, int W, int H,
                                 float near) {
     orc_splat sp;
     memset(&sp, 0, sizeof(sp));
-    float t[3] = {mu[0] - o[0], mu[1] - o[1], mu[2] - o[2]};
-    int aF = kFaceAxis[f][0], aU = kFaceAxis[f][1], aV = kFaceAxis[f][2];
-    float sF = kFaceSign[f][0], sU = kFaceSign[f][1], sV = kFaceSign[f][2];
-    float tz = sF * t[aF], tx = sU * t[aU], ty = sV * t[aV];
+    const float *R = cam;
+    float t0 = mu[0] - cam[9], t1 = mu[1] - cam[10], t2 = mu[2] - cam[11];
+    float tx = f32_dot3(R[0], R[1], R[2], t0, t1, t2);
+    float ty = f32_dot3(R[3], R[4], R[5], t0, t1, t2);
+    float tz = f32_dot3(R[6], R[7], R[8], t0, t1, t2);
     sp.tz = tz;
     if (!(tz > near)) return sp;
+    float fx = cam[12], fy = cam[13];
     float u = tx / tz, v = ty / tz;
-    sp.mx = (u + 1.0f) * fl;
-    sp.my = (v + 1.0f) * fl;
+    float fu = fx * u, fv = fy * v;
+    sp.mx = fu + cam[14];
+    sp.my = fv + cam[15];
     float gx[3], gy[3], gz[3], p1[3], p2[3];
     for (int k = 0; k < 3; ++k) {
-        gx[k] = sU * Rs[3 * aU + k];
-        gy[k] = sV * Rs[3 * aV + k];
-        gz[k] = sF * Rs[3 * aF + k];
+        gx[k] = f32_dot3(R[0], R[1], R[2], Rs[k], Rs[3 + k], Rs[6 + k]);
+        gy[k] = f32_dot3(R[3], R[4], R[5], Rs[k], Rs[3 + k], Rs[6 + k]);
+        gz[k] = f32_dot3(R[6], R[7], R[8], Rs[k], Rs[3 + k], Rs[6 + k]);
     }
-    float uc = fminf(fmaxf(u, -1.3f), 1.3f), vc = fminf(fmaxf(v, -1.3f), 1.3f);
+    float hw = 0.5f * (float)W, hh = 0.5f * (float)H;
+    float qx = hw / fx, qy = hh / fy;
+    float limx = 1.3f * qx, limy = 1.3f * qy;
+    float uc = fminf(fmaxf(u, -limx), limx), vc = fminf(fmaxf(v, -limy), limy);
     for (int k = 0; k < 3; ++k) {
         float a1 = uc * gz[k], a2 = vc * gz[k];
         p1[k] = gx[k] - a1;
         p2[k] = gy[k] - a2;
     }
-    float n11 = (p1[0] * p1[0] + p1[1] * p1[1]) + p1[2] * p1[2];
-    float n12 = (p1[0] * p2[0] + p1[1] * p2[1]) + p1[2] * p2[2];
-    float n22 = (p2[0] * p2[0] + p2[1] * p2[1]) + p2[2] * p2[2];
-    float h = fl / tz, h2 = h * h;
-    float a = h2 * n11 + 0.3f, b = h2 * n12, c = h2 * n22 + 0.3f;
+    float n11 = f32_dot3(p1[0], p1[1], p1[2], p1[0], p1[1], p1[2]);
+    float n12 = f32_dot3(p1[0], p1[1], p1[2], p2[0], p2[1], p2[2]);
+    float n22 = f32_dot3(p2[0], p2[1], p2[2], p2[0], p2[1], p2[2]);
+    float hx = fx / tz, hy = fy / tz;
+    float hxx = hx * hx, hxy = hx * hy, hyy = hy * hy;
+    float a = hxx * n11 + 0.3f, b = hxy * n12, c = hyy * n22 + 0.3f;
     float det = a * c - b * b;
     if (!(det > 0.0f)) return sp;
     sp.A = c / det;
@@ -1192,34 +1206,34 @@ static int hit_cmp(const void *x, const void *y) {
     return a->g < b->g ? -1 : (a->g > b->g ? 1 : 0);
 }
 
-/* Radiance of the probe pixels pix[0..npix) (index f face^2 + i face + j) of
- * the cube at `centre`: every Gaussian with opacity > 0 whose splat on face f
- * covers the pixel centre within Mahalanobis distance 3 (single-precision
- * decision), in order of depth (the float's bit pattern) and then index,
- * composited front to back in double precision with
+/* Radiance of pixels pix[0..npix) (index (v H + i) W + j) of n_views W x H
+ * cameras (cams: n_views x 16 floats): every Gaussian with opacity > 0 whose
+ * splat in view v covers the pixel centre within Mahalanobis distance 3
+ * (single-precision decision), in order of depth (the float's bit pattern)
+ * and then index, composited front to back in double precision with
  * alpha = min(0.99, opacity exp(-m^2/2)), C += alpha T c, T *= 1 - alpha,
  * stopping before T would drop below 1e-4. */
-void orc_render_pixels(const float *means, const float *scales, const float *quats, const float *opac,
-                       const float *colors, int64_t n, const float *centre, int face, float near,
-                       const int64_t *pix, int64_t npix, double *rgb_out) {
-    float fl = 0.5f * (float)face;
-    orc_splat *sp = (orc_splat *)malloc(sizeof(orc_splat) * 6 * (size_t)(n > 0 ? n : 1));
+void orc_render_view_pixels(const float *means, const float *scales, const float *quats, const float *opac,
+                            const float *colors, int64_t n, const float *cams, int n_views, int W, int H,
+                            float near, const int64_t *pix, int64_t npix, double *rgb_out) {
+    orc_splat *sp = (orc_splat *)malloc(sizeof(orc_splat) * n_views * (size_t)(n > 0 ? n : 1));
 #pragma omp parallel for schedule(static)
     for (int64_t g = 0; g < n; ++g) {
         float Rs[9];
         f32_rot_scale(quats + 4 * g, scales + 3 * g, Rs);
-        for (int f = 0; f < 6; ++f) sp[6 * g + f] = f32_make_splat(means + 3 * g, Rs, f, centre, fl, near);
+        for (int v = 0; v < n_views; ++v)
+            sp[(int64_t)n_views * g + v] = f32_make_splat(means + 3 * g, Rs, cams + 16 * v, W, H, near);
     }
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t p = 0; p < npix; ++p) {
         int64_t q = pix[p];
-        int f = (int)(q / ((int64_t)face * face));
-        int rem = (int)(q - (int64_t)f * face * face), i = rem / face, j = rem - i * face;
+        int v = (int)(q / ((int64_t)W * H));
+        int rem = (int)(q - (int64_t)v * W * H), i = rem / W, j = rem - i * W;
         float px = (float)j + 0.5f, py = (float)i + 0.5f;
         size_t cap = 64, cnt = 0;
         orc_hit *hits = (orc_hit *)malloc(sizeof(orc_hit) * cap);
         for (int64_t g = 0; g < n; ++g) {
-            const orc_splat *s = sp + 6 * g + f;
+            const orc_splat *s = sp + (int64_t)n_views * g + v;
             if (!s->ok || !(opac[g] > 0.0f)) continue;
             float m2 = f32_splat_m2(px, py, s);
             if (!(m2 <= 9.0f)) continue;
@@ -1249,4 +1263,29 @@ void orc_render_pixels(const float *means, const float *scales, const float *qua
         free(hits);
     }
     free(sp);
+}
+
+/* The six probe cameras at `centre` (cams: 6 x 16 floats): rows U, V, F of
+ * each face, fx = fy = cx = cy = face / 2. */
+void orc_cube_cams(const float *centre, int face, float *cams) {
+    for (int f = 0; f < 6; ++f) {
+        float *c = cams + 16 * f;
+        for (int k = 0; k < 9; ++k) c[k] = 0.0f;
+        c[0 + kFaceAxis[f][1]] = kFaceSign[f][1];
+        c[3 + kFaceAxis[f][2]] = kFaceSign[f][2];
+        c[6 + kFaceAxis[f][0]] = kFaceSign[f][0];
+        c[9] = centre[0];
+        c[10] = centre[1];
+        c[11] = centre[2];
+        c[12] = c[13] = c[14] = c[15] = 0.5f * (float)face;
+    }
+}
+
+/* Probe pixels (index f face^2 + i face + j) of the cube at `centre`. */
+void orc_render_pixels(const float *means, const float *scales, const float *quats, const float *opac,
+                       const float *colors, int64_t n, const float *centre, int face, float near,
+                       const int64_t *pix, int64_t npix, double *rgb_out) {
+    float cams[6 * 16];
+    orc_cube_cams(centre, face, cams);
+    orc_render_view_pixels(means, scales, quats, opac, colors, n, cams, 6, face, face, near, pix, npix, rgb_out);
 }

@@ -117,6 +117,8 @@ _lib.sh_fit.argtypes = [_vp, _vp, _vp, _vp, _i64, _f64, _vp, _vp, _vp]
 _lib.dgsm_render_cubemap.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _f32, _vp,
                                      C.POINTER(_i64), _vp]
 _lib.dgsm_cube_dirs.argtypes = [_vp, _i32, _vp, _vp, _vp]
+_lib.dgsm_render_views.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _f32, _vp,
+                                   C.POINTER(_i64), _vp]
 _lib.sh_fit_static.argtypes = [_vp, _vp, _vp, _i64, _f64, _vp, _vp, _vp, _vp]
 _lib.sh_relight.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64,
                             C.POINTER(RelightParams), _vp, _vp]
@@ -343,6 +345,26 @@ def dgsm_render_cubemap(means, scales, quats, opac, colors, centre, face=64, nea
     ctx.check(_lib.dgsm_render_cubemap(ctx.handle, _ptr(means), _ptr(scales), _ptr(quats), _ptr(opac),
                                        _ptr(colors), means.shape[0], _ptr(centre), int(face), float(near),
                                        _ptr(out), C.byref(npairs), _stream(stream)))
+    return (out, npairs.value) if want_pairs else out
+
+
+def dgsm_render_views(means, scales, quats, opac, colors, cams, W, H, near=0.05, out=None,
+                      want_pairs=False, ctx: Context | None = None, stream=None):
+    """3DGS splatting into pinhole cameras: cams (n_views, 16) float32 on the
+    device (R row-major rows x, y, forward; position; fx, fy, cx, cy);
+    returns (n_views, H, W, 3) radiance."""
+    ctx = ctx or context(means.device.index)
+    for t, nm, last in ((means, "means", 3), (scales, "scales", 3), (quats, "quats", 4), (colors, "colors", 3)):
+        _need(t, nm, shape_last=last)
+    _need(opac, "opac")
+    _need(cams, "cams", shape_last=16)
+    V = cams.shape[0]
+    if out is None:
+        out = torch.empty((V, H, W, 3), dtype=torch.float32, device=means.device)
+    npairs = _i64(0)
+    ctx.check(_lib.dgsm_render_views(ctx.handle, _ptr(means), _ptr(scales), _ptr(quats), _ptr(opac),
+                                     _ptr(colors), means.shape[0], _ptr(cams), V, int(W), int(H), float(near),
+                                     _ptr(out), C.byref(npairs), _stream(stream)))
     return (out, npairs.value) if want_pairs else out
 
 

@@ -35,7 +35,8 @@ enum WsSlot {
     WS_FCNT, WS_FOFF,  // per (unit, tile) pair counts and their scan
     WS_FMASK,          // per (unit, tile) bitmaps of the Gaussians that reach it (and its halves)
     WS_ROI,            // region of interest: shell ranges, texel mask, tile and super-tile flags
-    WS_RENDER,         // cubemap probe render: per-pair splat payloads
+    WS_RENDER,         // splat render: per-pair splat payloads
+    WS_CAMS,           // the six probe cameras of dgsm_render_cubemap
     WS_NSLOTS
 };
 

@@ -1,12 +1,13 @@
-// render.cu -- the cubemap probe of Sec. 3.4 on sm_103a: the 3DGS scene
-// splatted on the six 90-degree faces at the avatar, and the faces' texel
-// directions and solid angles, which the SH fit (Eq. 7) takes as its samples.
+// render.cu -- 3DGS splatting on sm_103a for the cubemap probe of Sec. 3.4
+// (the scene on the six 90-degree faces at the avatar; the SH fit of Eq. 7
+// takes the faces' texels as its samples) and for the final composite of the
+// relit avatar in the shadowed scene, seen by pinhole cameras.
 //
-// Pipeline per call (all on the caller's stream):
-//   splat_count_kernel  per Gaussian and face: view coordinates, the EWA
-//                       screen covariance (Jacobian of the face's pinhole
+// Pipeline per call (all on the caller's stream), for n_views cameras:
+//   splat_count_kernel  per Gaussian and view: view coordinates, the EWA
+//                       screen covariance (Jacobian of the pinhole
 //                       projection at the mean), its inverse and a
-//                       conservative square of tiles around the 3-sigma
+//                       conservative square of 8x8 tiles around the 3-sigma
 //                       ellipse -> number of (tile, splat) pairs
 //   scan                pair offsets                    (one host sync)
 //   splat_emit_kernel   the pairs: depth key, tile key, splat payload
@@ -29,9 +30,10 @@ namespace {
 constexpr int RT = 8;                // render tile edge, pixels
 constexpr int RT_PIX = RT * RT;      // threads per render block
 constexpr float LOWPASS = 0.3f;      // screen-space dilation, pixel^2
-constexpr float JAC_LIMIT = 1.3f;    // |x/z|, |y/z| clamp of the Jacobian
+constexpr float JAC_LIMIT = 1.3f;    // Jacobian evaluated within 1.3 x the half field of view
 constexpr float T_STOP = 1e-4f;      // compositing stops below this transmittance
 constexpr float ALPHA_MAX = 0.99f;
+constexpr int CAM_F = 16;            // floats per camera: R (9, rows x, y, forward), position (3), fx, fy, cx, cy
 
 // Face f of the cube: forward axis F and the axes U, V along which the face's
 // texel coordinates u (columns) and v (rows) grow, as signed unit axes
@@ -41,42 +43,46 @@ __constant__ float c_face_sign[6][3] = {{1, -1, -1}, {-1, 1, -1}, {1, 1, 1}, {-1
                                         {-1, -1, -1}};
 
 struct Splat {
-    float mx, my;      // mean on the face, pixels (pixel j's centre at j + 0.5)
+    float mx, my;      // mean in the image, pixels (pixel j's centre at j + 0.5)
     float A, B, C;     // inverse screen covariance [[A, B], [B, C]]
-    float tz;          // depth along the face's forward axis
-    int r;             // half-width of the tile square, pixels
+    float tz;          // depth along the camera's forward axis
+    int rx, ry;        // half-widths of the pixel box around the mean
     bool ok;
 };
 
-// The Gaussian's splat on face f (camera at o, focal length fl = face / 2).
-// All steps are IEEE single operations in this order (the CPU oracle repeats
-// them): view coordinates of t = mu - o (signed selections, exact); u = tx/tz,
-// v = ty/tz; mean = ((u + 1) fl, (v + 1) fl); G = rows U, V, F of R diag(s);
-// p1 = g_x - u' g_z, p2 = g_y - v' g_z with u', v' clamped to the Jacobian
-// limit; h = fl / tz; the screen covariance h^2 [[p1.p1, p1.p2], [p1.p2,
-// p2.p2]] + LOWPASS I and its inverse.
-__device__ __forceinline__ Splat make_splat(const float *mu, const float *Rs, int f, const float *o,
-                                            float fl, float near) {
+// The Gaussian's splat in camera c (cam: 16 floats) for a W x H image.  All
+// steps are IEEE single operations in this order (the CPU oracle repeats
+// them): t = mu - position; (tx, ty, tz) = R t (rows x, y, forward);
+// u = tx / tz, v = ty / tz; mean = (fx u + cx, fy v + cy); G = R (R_g diag(s))
+// column by column; p1 = g_x - u' g_z, p2 = g_y - v' g_z with u', v' clamped
+// to 1.3 x the half field of view; hx = fx / tz, hy = fy / tz; the screen
+// covariance [[hx^2 p1.p1, hx hy p1.p2], [., hy^2 p2.p2]] + LOWPASS I and
+// its inverse.
+__device__ __forceinline__ Splat make_splat(const float *mu, const float *Rs, const float *cam, int W, int H,
+                                            float near) {
     Splat sp;
     sp.ok = false;
-    const float t[3] = {xsub(mu[0], o[0]), xsub(mu[1], o[1]), xsub(mu[2], o[2])};
-    const int aF = c_face_axis[f][0], aU = c_face_axis[f][1], aV = c_face_axis[f][2];
-    const float sF = c_face_sign[f][0], sU = c_face_sign[f][1], sV = c_face_sign[f][2];
-    const float tz = sF * t[aF], tx = sU * t[aU], ty = sV * t[aV];
+    const float *R = cam;
+    const float t0 = xsub(mu[0], cam[9]), t1 = xsub(mu[1], cam[10]), t2 = xsub(mu[2], cam[11]);
+    const float tx = xdot(R[0], R[1], R[2], t0, t1, t2);
+    const float ty = xdot(R[3], R[4], R[5], t0, t1, t2);
+    const float tz = xdot(R[6], R[7], R[8], t0, t1, t2);
     sp.tz = tz;
     if (!(tz > near)) return sp;
+    const float fx = cam[12], fy = cam[13];
     const float u = xdiv(tx, tz), v = xdiv(ty, tz);
-    sp.mx = xmul(xadd(u, 1.0f), fl);
-    sp.my = xmul(xadd(v, 1.0f), fl);
-    // rows of G = W R diag(s): row a = sign * row (axis) of Rs (Rs[3 r + k] = R[r][k] s_k)
+    sp.mx = xadd(xmul(fx, u), cam[14]);
+    sp.my = xadd(xmul(fy, v), cam[15]);
     float gx[3], gy[3], gz[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        gx[k] = sU * Rs[3 * aU + k];
-        gy[k] = sV * Rs[3 * aV + k];
-        gz[k] = sF * Rs[3 * aF + k];
+        gx[k] = xdot(R[0], R[1], R[2], Rs[k], Rs[3 + k], Rs[6 + k]);
+        gy[k] = xdot(R[3], R[4], R[5], Rs[k], Rs[3 + k], Rs[6 + k]);
+        gz[k] = xdot(R[6], R[7], R[8], Rs[k], Rs[3 + k], Rs[6 + k]);
     }
-    const float uc = fminf(fmaxf(u, -JAC_LIMIT), JAC_LIMIT), vc = fminf(fmaxf(v, -JAC_LIMIT), JAC_LIMIT);
+    const float limx = xmul(JAC_LIMIT, xdiv(xmul(0.5f, (float)W), fx));
+    const float limy = xmul(JAC_LIMIT, xdiv(xmul(0.5f, (float)H), fy));
+    const float uc = fminf(fmaxf(u, -limx), limx), vc = fminf(fmaxf(v, -limy), limy);
     float p1[3], p2[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -86,20 +92,21 @@ __device__ __forceinline__ Splat make_splat(const float *mu, const float *Rs, in
     const float n11 = xdot(p1[0], p1[1], p1[2], p1[0], p1[1], p1[2]);
     const float n12 = xdot(p1[0], p1[1], p1[2], p2[0], p2[1], p2[2]);
     const float n22 = xdot(p2[0], p2[1], p2[2], p2[0], p2[1], p2[2]);
-    const float h = xdiv(fl, tz), h2 = xmul(h, h);
-    const float a = xadd(xmul(h2, n11), LOWPASS), b = xmul(h2, n12), c = xadd(xmul(h2, n22), LOWPASS);
+    const float hx = xdiv(fx, tz), hy = xdiv(fy, tz);
+    const float a = xadd(xmul(xmul(hx, hx), n11), LOWPASS);
+    const float b = xmul(xmul(hx, hy), n12);
+    const float c = xadd(xmul(xmul(hy, hy), n22), LOWPASS);
     const float det = xsub(xmul(a, c), xmul(b, b));
     if (!(det > 0.0f)) return sp;
     sp.A = xdiv(c, det);
     sp.B = xdiv(-b, det);
     sp.C = xdiv(a, det);
-    // largest eigenvalue, then a square that covers the 3-sigma ellipse with a
-    // pixel of margin (it only selects tiles: the ellipse test decides)
-    const float mid = 0.5f * (a + c);
-    const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
-    const float ext = 3.0f * sqrtf(lam) * 1.001f + 1.0f;
-    if (!(ext < 1e6f)) return sp;
-    sp.r = (int)ceilf(ext);
+    // the box that bounds the 3-sigma ellipse (half-widths 3 sqrt(a), 3 sqrt(c)),
+    // with a pixel of margin: it only selects tiles, the ellipse test decides
+    const float ex = 3.0f * sqrtf(a) * 1.001f + 1.0f, ey = 3.0f * sqrtf(c) * 1.001f + 1.0f;
+    if (!(ex < 1e6f) || !(ey < 1e6f) || !(fabsf(sp.mx) < 1e7f) || !(fabsf(sp.my) < 1e7f)) return sp;
+    sp.rx = (int)ceilf(ex);
+    sp.ry = (int)ceilf(ey);
     sp.ok = true;
     return sp;
 }
@@ -127,36 +134,38 @@ __device__ __forceinline__ void rot_scale(const float *q, const float *s, float 
         for (int k = 0; k < 3; ++k) Rs[3 * r + k] = xmul(R[3 * r + k], s[k]);
 }
 
-// Tile range of a splat on its face ([i0, i1) x [j0, j1)); empty if off the face.
-__device__ __forceinline__ void splat_tiles(const Splat &sp, int nt, int &i0, int &i1, int &j0, int &j1) {
-    const float lo_x = sp.mx - (float)sp.r, hi_x = sp.mx + (float)sp.r;
-    const float lo_y = sp.my - (float)sp.r, hi_y = sp.my + (float)sp.r;
-    j0 = (int)fmaxf(floorf(lo_x / RT), 0.0f);
-    j1 = (int)fminf(floorf(hi_x / RT) + 1.0f, (float)nt);
-    i0 = (int)fmaxf(floorf(lo_y / RT), 0.0f);
-    i1 = (int)fminf(floorf(hi_y / RT) + 1.0f, (float)nt);
+// Tile range of a splat in its image ([i0, i1) x [j0, j1)); empty if off the image.
+__device__ __forceinline__ void splat_tiles(const Splat &sp, int ntx, int nty, int &i0, int &i1, int &j0,
+                                            int &j1) {
+    const float lo_x = sp.mx - (float)sp.rx, hi_x = sp.mx + (float)sp.rx;
+    const float lo_y = sp.my - (float)sp.ry, hi_y = sp.my + (float)sp.ry;
+    j0 = (int)fminf(fmaxf(floorf(lo_x / RT), 0.0f), (float)ntx);
+    j1 = (int)fminf(fmaxf(floorf(hi_x / RT) + 1.0f, 0.0f), (float)ntx);
+    i0 = (int)fminf(fmaxf(floorf(lo_y / RT), 0.0f), (float)nty);
+    i1 = (int)fminf(fmaxf(floorf(hi_y / RT) + 1.0f, 0.0f), (float)nty);
     if (j1 < j0) j1 = j0;
     if (i1 < i0) i1 = i0;
 }
 
 __global__ void __launch_bounds__(256) splat_count_kernel(
     const float *__restrict__ means, const float *__restrict__ scales, const float *__restrict__ quats,
-    const float *__restrict__ opac, int64_t n, const float *__restrict__ centre, int face, float near,
-    uint32_t *__restrict__ counts) {
-    const float o[3] = {centre[0], centre[1], centre[2]};
-    const float fl = 0.5f * (float)face;
-    const int nt = face / RT;
+    const float *__restrict__ opac, int64_t n, const float *__restrict__ cams, int n_views, int W, int H,
+    float near, uint32_t *__restrict__ counts) {
+    __shared__ float scam[64 * CAM_F];
+    for (int k = threadIdx.x; k < n_views * CAM_F; k += blockDim.x) scam[k] = cams[k];
+    __syncthreads();
+    const int ntx = (W + RT - 1) / RT, nty = (H + RT - 1) / RT;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
          g += (int64_t)gridDim.x * blockDim.x) {
         uint32_t c = 0;
         if (opac[g] > 0.0f) {
             float Rs[9];
             rot_scale(quats + 4 * g, scales + 3 * g, Rs);
-            for (int f = 0; f < 6; ++f) {
-                const Splat sp = make_splat(means + 3 * g, Rs, f, o, fl, near);
+            for (int v = 0; v < n_views; ++v) {
+                const Splat sp = make_splat(means + 3 * g, Rs, scam + CAM_F * v, W, H, near);
                 if (!sp.ok) continue;
                 int i0, i1, j0, j1;
-                splat_tiles(sp, nt, i0, i1, j0, j1);
+                splat_tiles(sp, ntx, nty, i0, i1, j0, j1);
                 c += (uint32_t)((i1 - i0) * (j1 - j0));
             }
         }
@@ -164,16 +173,18 @@ __global__ void __launch_bounds__(256) splat_count_kernel(
     }
 }
 
-// payload of a pair: (mx, my, A, B), (C, opacity, tz, Gaussian index), (r, g, b, 0)
+// payload of splat (Gaussian g, view v) at g n_views + v: (mx, my, A, B),
+// (C, opacity, tz, g), (r, g, b, 0); a pair carries the splat's index
 __global__ void __launch_bounds__(256) splat_emit_kernel(
     const float *__restrict__ means, const float *__restrict__ scales, const float *__restrict__ quats,
-    const float *__restrict__ opac, const float *__restrict__ colors, int64_t n,
-    const float *__restrict__ centre, int face, float near, const uint32_t *__restrict__ offsets,
-    uint32_t cap, uint32_t *__restrict__ dkey, uint32_t *__restrict__ tkey, uint32_t *__restrict__ pid,
+    const float *__restrict__ opac, const float *__restrict__ colors, int64_t n, const float *__restrict__ cams,
+    int n_views, int W, int H, float near, const uint32_t *__restrict__ offsets, uint32_t cap,
+    uint32_t *__restrict__ dkey, uint32_t *__restrict__ tkey, uint32_t *__restrict__ pid,
     float4 *__restrict__ payload) {
-    const float o[3] = {centre[0], centre[1], centre[2]};
-    const float fl = 0.5f * (float)face;
-    const int nt = face / RT;
+    __shared__ float scam[64 * CAM_F];
+    for (int k = threadIdx.x; k < n_views * CAM_F; k += blockDim.x) scam[k] = cams[k];
+    __syncthreads();
+    const int ntx = (W + RT - 1) / RT, nty = (H + RT - 1) / RT;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
          g += (int64_t)gridDim.x * blockDim.x) {
         const float al = opac[g];
@@ -181,32 +192,46 @@ __global__ void __launch_bounds__(256) splat_emit_kernel(
         uint32_t pos = offsets[g];
         float Rs[9];
         rot_scale(quats + 4 * g, scales + 3 * g, Rs);
-        for (int f = 0; f < 6; ++f) {
-            const Splat sp = make_splat(means + 3 * g, Rs, f, o, fl, near);
+        for (int v = 0; v < n_views; ++v) {
+            const Splat sp = make_splat(means + 3 * g, Rs, scam + CAM_F * v, W, H, near);
             if (!sp.ok) continue;
             int i0, i1, j0, j1;
-            splat_tiles(sp, nt, i0, i1, j0, j1);
+            splat_tiles(sp, ntx, nty, i0, i1, j0, j1);
+            if (i1 == i0 || j1 == j0) continue;
+            const size_t sid = (size_t)g * n_views + v;
+            payload[3 * sid] = make_float4(sp.mx, sp.my, sp.A, sp.B);
+            payload[3 * sid + 1] = make_float4(sp.C, al, sp.tz, __int_as_float((int)g));
+            payload[3 * sid + 2] = make_float4(colors[3 * g], colors[3 * g + 1], colors[3 * g + 2], 0.0f);
             for (int i = i0; i < i1; ++i)
                 for (int j = j0; j < j1; ++j, ++pos) {
                     if (pos >= cap) continue;
                     dkey[pos] = __float_as_uint(sp.tz);  // tz > 0: the bits order like the values
-                    tkey[pos] = (uint32_t)((f * nt + i) * nt + j);
-                    pid[pos] = pos;
-                    payload[3 * (size_t)pos] = make_float4(sp.mx, sp.my, sp.A, sp.B);
-                    payload[3 * (size_t)pos + 1] = make_float4(sp.C, al, sp.tz, __int_as_float((int)g));
-                    payload[3 * (size_t)pos + 2] =
-                        make_float4(colors[3 * g], colors[3 * g + 1], colors[3 * g + 2], 0.0f);
+                    tkey[pos] = (uint32_t)((v * nty + i) * ntx + j);
+                    pid[pos] = (uint32_t)sid;
                 }
         }
     }
 }
 
-__global__ void gather_keys_kernel(const uint32_t *__restrict__ order, const uint32_t *__restrict__ tkey_by_pid,
-                                   const unsigned long long *__restrict__ d_n, uint32_t *__restrict__ out) {
+// After the depth sort (values: pair positions): the tile key and the splat
+// index of each sorted pair.
+__global__ void gather_keys_kernel(const uint32_t *__restrict__ order, const uint32_t *__restrict__ tkey_by_pos,
+                                   const uint32_t *__restrict__ sid_by_pos, const unsigned long long *__restrict__ d_n,
+                                   uint32_t *__restrict__ tkey_out, uint32_t *__restrict__ sid_out) {
+    const unsigned long long n = *d_n;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t p = order[i];
+        tkey_out[i] = tkey_by_pos[p];
+        sid_out[i] = sid_by_pos[p];
+    }
+}
+
+__global__ void iota_kernel(const unsigned long long *__restrict__ d_n, uint32_t *__restrict__ out) {
     const unsigned long long n = *d_n;
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x)
-        out[i] = tkey_by_pid[order[i]];
+        out[i] = (uint32_t)i;
 }
 
 __global__ void splat_ranges_kernel(const uint32_t *__restrict__ keys, const unsigned long long *__restrict__ d_n,
@@ -221,18 +246,20 @@ __global__ void splat_ranges_kernel(const uint32_t *__restrict__ keys, const uns
 }
 
 // One block per tile, one thread per pixel; splats staged RT_PIX at a time.
+// Pixels of an edge tile beyond the image take part in the staging only.
 __global__ void __launch_bounds__(RT_PIX) splat_render_kernel(
     const uint32_t *__restrict__ ts, const uint32_t *__restrict__ te, const uint32_t *__restrict__ order,
-    const float4 *__restrict__ payload, int face, float *__restrict__ rgb) {
+    const float4 *__restrict__ payload, int W, int H, float *__restrict__ rgb) {
     __shared__ float4 s0[RT_PIX], s1[RT_PIX], s2[RT_PIX];
-    const int nt = face / RT;
+    const int ntx = (W + RT - 1) / RT, nty = (H + RT - 1) / RT;
     const int tile = blockIdx.x;
-    const int f = tile / (nt * nt), rem = tile - f * nt * nt, ti = rem / nt, tj = rem - ti * nt;
+    const int v = tile / (ntx * nty), rem = tile - v * ntx * nty, ti = rem / ntx, tj = rem - ti * ntx;
     const int i = ti * RT + threadIdx.x / RT, j = tj * RT + threadIdx.x % RT;
+    const bool inside = i < H && j < W;
     const float px = (float)j + 0.5f, py = (float)i + 0.5f;
     const uint32_t start = ts[tile], end = te[tile];
     float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
-    bool done = false;
+    bool done = !inside;
     for (uint32_t base = start; base < end; base += RT_PIX) {
         if (__syncthreads_count(done) == RT_PIX) break;
         const uint32_t e = base + threadIdx.x;
@@ -262,10 +289,28 @@ __global__ void __launch_bounds__(RT_PIX) splat_render_kernel(
             T = Tn;
         }
     }
-    const size_t pix = ((size_t)f * face + i) * face + j;
+    if (!inside) return;
+    const size_t pix = ((size_t)v * H + i) * W + j;
     rgb[3 * pix] = cr;
     rgb[3 * pix + 1] = cg;
     rgb[3 * pix + 2] = cb;
+}
+
+// The six probe cameras at `centre`: rows U, V, F of each face, focal length
+// and principal point face / 2 (a 90-degree field of view).
+__global__ void cube_cams_kernel(const float *__restrict__ centre, int face, float *__restrict__ cams) {
+    const int f = threadIdx.x;
+    if (f >= 6) return;
+    float *c = cams + CAM_F * f;
+    for (int k = 0; k < 9; ++k) c[k] = 0.0f;
+    c[0 + c_face_axis[f][1]] = c_face_sign[f][1];  // row x: U
+    c[3 + c_face_axis[f][2]] = c_face_sign[f][2];  // row y: V
+    c[6 + c_face_axis[f][0]] = c_face_sign[f][0];  // row forward: F
+    c[9] = centre[0];
+    c[10] = centre[1];
+    c[11] = centre[2];
+    const float fl = 0.5f * (float)face;
+    c[12] = c[13] = c[14] = c[15] = fl;
 }
 
 // Texel-centre directions of the faces and their exact solid angles,
@@ -294,6 +339,86 @@ __global__ void cube_dirs_kernel(int face, float *__restrict__ dirs, float *__re
     }
 }
 
+// The splatting pipeline for n_views cameras (device, CAM_F floats each) of
+// W x H images; arguments checked, device current.
+int render_impl(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats, const float *opac,
+                const float *colors, int64_t n, const float *cams, int n_views, int W, int H, float near,
+                float *rgb_out, int64_t *n_pairs_out, cudaStream_t s) {
+    const int ntx = (W + RT - 1) / RT, nty = (H + RT - 1) / RT;
+    const int64_t n_tiles = (int64_t)n_views * ntx * nty;
+    int rc;
+    void *w_cnt, *w_rng;
+    if ((rc = ws_reserve(ctx, WS_COUNTS, sizeof(uint32_t) * (size_t)std::max<int64_t>(n, 1), &w_cnt))) return rc;
+    // per-tile [start, end), then the 8-byte pair counter
+    const size_t rng_bytes = (2 * sizeof(uint32_t) * (size_t)n_tiles + 7) & ~(size_t)7;
+    if ((rc = ws_reserve(ctx, WS_RANGES, rng_bytes + sizeof(unsigned long long), &w_rng))) return rc;
+    uint32_t *ts = (uint32_t *)w_rng, *te = ts + n_tiles;
+    unsigned long long *d_total = (unsigned long long *)((char *)w_rng + rng_bytes);
+    cudaError_t e = cudaMemsetAsync(w_rng, 0, rng_bytes + sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "render: memset");
+    uint64_t P = 0;
+    const int grid = (int)std::min<int64_t>((std::max<int64_t>(n, 1) + 255) / 256, (int64_t)ctx->num_sms * 16);
+    if (n > 0) {
+        splat_count_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, n, cams, n_views, W, H, near,
+                                                (uint32_t *)w_cnt);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "splat_count_kernel");
+        if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_cnt, (uint32_t *)w_cnt, n, d_total, s))) return rc;
+        e = cudaMemcpyAsync(ctx->h_pinned, d_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "render: pair count");
+        P = ctx->h_pinned[0];
+        if (P >= (1ull << 31)) return fail(ctx, DGSM_ERR_WORKSPACE, "render: more than 2^31 pairs");
+    }
+    if (n_pairs_out) *n_pairs_out = (int64_t)P;
+    if (P > 0) {
+        void *ka, *va, *kb, *vb, *tk, *sk, *pl;
+        if ((rc = ws_reserve(ctx, WS_KEYS_A, sizeof(uint32_t) * P, &ka))) return rc;
+        if ((rc = ws_reserve(ctx, WS_VALS_A, sizeof(uint32_t) * P, &va))) return rc;
+        if ((rc = ws_reserve(ctx, WS_KEYS_B, sizeof(uint32_t) * P, &kb))) return rc;
+        if ((rc = ws_reserve(ctx, WS_VALS_B, sizeof(uint32_t) * P, &vb))) return rc;
+        if ((rc = ws_reserve(ctx, WS_CKEYS_A, sizeof(uint32_t) * P, &tk))) return rc;
+        if ((rc = ws_reserve(ctx, WS_CVALS_A, sizeof(uint32_t) * P, &sk))) return rc;
+        if ((rc = ws_reserve(ctx, WS_RENDER, 3 * sizeof(float4) * (size_t)n * n_views, &pl))) return rc;
+        splat_emit_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, colors, n, cams, n_views, W, H, near,
+                                               (const uint32_t *)w_cnt, (uint32_t)P, (uint32_t *)ka,
+                                               (uint32_t *)tk, (uint32_t *)sk, (float4 *)pl);
+        const int rgrid = (int)std::min<int64_t>(((int64_t)P + 255) / 256, (int64_t)ctx->num_sms * 16);
+        iota_kernel<<<rgrid, 256, 0, s>>>(d_total, (uint32_t *)va);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "splat_emit_kernel");
+        // front to back within each tile: sort the pair positions by depth,
+        // then (tile, splat) stably by tile
+        uint32_t *keys = (uint32_t *)ka, *vals = (uint32_t *)va;
+        if ((rc = radix_sort_pairs(ctx, &keys, &vals, (uint32_t *)kb, (uint32_t *)vb, d_total, (int64_t)P, 32, s)))
+            return rc;
+        uint32_t *alt_k = keys == (uint32_t *)ka ? (uint32_t *)kb : (uint32_t *)ka;
+        uint32_t *alt_v = vals == (uint32_t *)va ? (uint32_t *)vb : (uint32_t *)va;
+        gather_keys_kernel<<<rgrid, 256, 0, s>>>(vals, (const uint32_t *)tk, (const uint32_t *)sk, d_total, alt_k,
+                                                 alt_v);
+        uint32_t *tkeys = alt_k, *sids = alt_v;
+        int bits = 1;
+        while (((int64_t)1 << bits) < n_tiles) ++bits;
+        if ((rc = radix_sort_pairs(ctx, &tkeys, &sids, keys, vals, d_total, (int64_t)P, bits, s))) return rc;
+        splat_ranges_kernel<<<rgrid, 256, 0, s>>>(tkeys, d_total, ts, te);
+        splat_render_kernel<<<(unsigned)n_tiles, RT_PIX, 0, s>>>(ts, te, sids, (const float4 *)pl, W, H, rgb_out);
+    } else {
+        splat_render_kernel<<<(unsigned)n_tiles, RT_PIX, 0, s>>>(ts, te, ts, nullptr, W, H, rgb_out);
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "splat render kernels");
+}
+
+int check_gaussians(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
+                    const float *opac, const float *colors, int64_t n, float near, const float *rgb_out) {
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(ctx, DGSM_ERR_INVALID_ARG, "render: n out of range");
+    if (n > 0 && (!means || !scales || !quats || !opac || !colors))
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "render: null Gaussian array");
+    if (!rgb_out) return fail(ctx, DGSM_ERR_INVALID_ARG, "render: null output");
+    if (!(near > 0.0f)) return fail(ctx, DGSM_ERR_INVALID_ARG, "render: near must be > 0");
+    return DGSM_OK;
+}
+
 }  // namespace
 }  // namespace dgsm
 
@@ -312,78 +437,41 @@ extern "C" int dgsm_cube_dirs(dgsm_ctx *ctx, int32_t face, float *dirs_out, floa
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "cube_dirs_kernel");
 }
 
+extern "C" int dgsm_render_views(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
+                                 const float *opac, const float *colors, int64_t n, const float *cams,
+                                 int32_t n_views, int32_t W, int32_t H, float near, float *rgb_out,
+                                 int64_t *n_pairs_out, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    int rc = check_gaussians(ctx, means, scales, quats, opac, colors, n, near, rgb_out);
+    if (rc) return rc;
+    if (!cams || n_views < 1 || n_views > 64) return fail(ctx, DGSM_ERR_INVALID_ARG, "render: need 1..64 cameras");
+    if (n * n_views >= ((int64_t)1 << 32)) return fail(ctx, DGSM_ERR_INVALID_ARG, "render: n x n_views >= 2^32");
+    if (W < 1 || H < 1 || W > 4096 || H > 4096) return fail(ctx, DGSM_ERR_INVALID_ARG, "render: W, H in 1..4096");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    return render_impl(ctx, means, scales, quats, opac, colors, n, cams, n_views, W, H, near, rgb_out, n_pairs_out,
+                       (cudaStream_t)stream);
+}
+
 extern "C" int dgsm_render_cubemap(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
                                    const float *opac, const float *colors, int64_t n, const float *centre,
                                    int32_t face, float near, float *rgb_out, int64_t *n_pairs_out,
                                    void *stream) {
     if (!ctx) return DGSM_ERR_INVALID_ARG;
-    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(ctx, DGSM_ERR_INVALID_ARG, "render: n out of range");
-    if (n > 0 && (!means || !scales || !quats || !opac || !colors))
-        return fail(ctx, DGSM_ERR_INVALID_ARG, "render: null Gaussian array");
-    if (!centre || !rgb_out) return fail(ctx, DGSM_ERR_INVALID_ARG, "render: null centre or output");
+    int rc = check_gaussians(ctx, means, scales, quats, opac, colors, n, near, rgb_out);
+    if (rc) return rc;
+    if (!centre) return fail(ctx, DGSM_ERR_INVALID_ARG, "render: null centre");
+    if (n * 6 >= ((int64_t)1 << 32)) return fail(ctx, DGSM_ERR_INVALID_ARG, "render: 6 n >= 2^32");
     if (face < RT || face > 1024 || face % RT != 0)
         return fail(ctx, DGSM_ERR_INVALID_ARG, "render: face must be a multiple of 8 in 8..1024");
-    if (!(near > 0.0f)) return fail(ctx, DGSM_ERR_INVALID_ARG, "render: near must be > 0");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
-    const int nt = face / RT, n_tiles = 6 * nt * nt;
-    int rc;
-    void *w_cnt, *w_rng;
-    if ((rc = ws_reserve(ctx, WS_COUNTS, sizeof(uint32_t) * (size_t)std::max<int64_t>(n, 1), &w_cnt))) return rc;
-    // per-tile [start, end), then the 8-byte pair counter
-    const size_t rng_bytes = (2 * sizeof(uint32_t) * (size_t)n_tiles + 7) & ~(size_t)7;
-    if ((rc = ws_reserve(ctx, WS_RANGES, rng_bytes + sizeof(unsigned long long), &w_rng))) return rc;
-    uint32_t *ts = (uint32_t *)w_rng, *te = ts + n_tiles;
-    unsigned long long *d_total = (unsigned long long *)((char *)w_rng + rng_bytes);
-    e = cudaMemsetAsync(w_rng, 0, rng_bytes + sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "render: memset");
-    uint64_t P = 0;
-    if (n > 0) {
-        const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 16);
-        splat_count_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, n, centre, face, near,
-                                                (uint32_t *)w_cnt);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "splat_count_kernel");
-        if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_cnt, (uint32_t *)w_cnt, n, d_total, s))) return rc;
-        e = cudaMemcpyAsync(ctx->h_pinned, d_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "render: pair count");
-        P = ctx->h_pinned[0];
-        if (P >= (1ull << 31)) return fail(ctx, DGSM_ERR_WORKSPACE, "render: more than 2^31 pairs");
-    }
-    if (n_pairs_out) *n_pairs_out = (int64_t)P;
-    if (P > 0) {
-        void *ka, *va, *kb, *vb, *tk, *pl;
-        if ((rc = ws_reserve(ctx, WS_KEYS_A, sizeof(uint32_t) * P, &ka))) return rc;
-        if ((rc = ws_reserve(ctx, WS_VALS_A, sizeof(uint32_t) * P, &va))) return rc;
-        if ((rc = ws_reserve(ctx, WS_KEYS_B, sizeof(uint32_t) * P, &kb))) return rc;
-        if ((rc = ws_reserve(ctx, WS_VALS_B, sizeof(uint32_t) * P, &vb))) return rc;
-        if ((rc = ws_reserve(ctx, WS_CKEYS_A, sizeof(uint32_t) * P, &tk))) return rc;
-        if ((rc = ws_reserve(ctx, WS_RENDER, 3 * sizeof(float4) * P, &pl))) return rc;
-        const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 16);
-        splat_emit_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, colors, n, centre, face, near,
-                                               (const uint32_t *)w_cnt, (uint32_t)P, (uint32_t *)ka,
-                                               (uint32_t *)tk, (uint32_t *)va, (float4 *)pl);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "splat_emit_kernel");
-        // front to back within each tile: sort by depth, then stably by tile
-        uint32_t *keys = (uint32_t *)ka, *vals = (uint32_t *)va;
-        if ((rc = radix_sort_pairs(ctx, &keys, &vals, (uint32_t *)kb, (uint32_t *)vb, d_total, (int64_t)P, 32, s)))
-            return rc;
-        uint32_t *alt_k = keys == (uint32_t *)ka ? (uint32_t *)kb : (uint32_t *)ka;
-        uint32_t *alt_v = vals == (uint32_t *)va ? (uint32_t *)vb : (uint32_t *)va;
-        const int rgrid = (int)std::min<int64_t>(((int64_t)P + 255) / 256, (int64_t)ctx->num_sms * 16);
-        gather_keys_kernel<<<rgrid, 256, 0, s>>>(vals, (const uint32_t *)tk, d_total, alt_k);
-        uint32_t *tkeys = alt_k;
-        int bits = 1;
-        while ((1 << bits) < n_tiles) ++bits;
-        if ((rc = radix_sort_pairs(ctx, &tkeys, &vals, keys, alt_v, d_total, (int64_t)P, bits, s))) return rc;
-        splat_ranges_kernel<<<rgrid, 256, 0, s>>>(tkeys, d_total, ts, te);
-        splat_render_kernel<<<n_tiles, RT_PIX, 0, s>>>(ts, te, vals, (const float4 *)pl, face, rgb_out);
-    } else {
-        splat_render_kernel<<<n_tiles, RT_PIX, 0, s>>>(ts, te, ts, nullptr, face, rgb_out);
-    }
+    void *w_cams;
+    if ((rc = ws_reserve(ctx, WS_CAMS, 6 * CAM_F * sizeof(float), &w_cams))) return rc;
+    cube_cams_kernel<<<1, 32, 0, s>>>(centre, face, (float *)w_cams);
     e = cudaGetLastError();
-    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "splat render kernels");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cube_cams_kernel");
+    return render_impl(ctx, means, scales, quats, opac, colors, n, (const float *)w_cams, 6, face, face, near,
+                       rgb_out, n_pairs_out, s);
 }

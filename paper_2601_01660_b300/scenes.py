@@ -251,6 +251,19 @@ def radii_geometric(r0: float, r1: float, k: int) -> np.ndarray:
     return _f32(r0 * (r1 / r0) ** (np.arange(k) / (k - 1)))
 
 
+def look_at_camera(eye, target, W: int, H: int, fov_y_deg: float = 60.0, up=(0.0, 0.0, 1.0)) -> np.ndarray:
+    """A pinhole camera (16 float32: rotation rows image x, image y (down),
+    forward; position; fx, fy, cx, cy) at `eye` looking at `target`."""
+    eye, target, up = (np.asarray(a, dtype=np.float64) for a in (eye, target, up))
+    f = target - eye
+    f /= np.linalg.norm(f)
+    x = np.cross(f, up)
+    x /= np.linalg.norm(x)
+    y = np.cross(f, x)
+    fy = 0.5 * H / math.tan(math.radians(fov_y_deg) / 2)
+    return _f32(np.concatenate([x, y, f, eye, [fy, fy, 0.5 * W, 0.5 * H]]))
+
+
 def four_lights() -> np.ndarray:
     """The four point lights used by the multi-light workloads."""
     return _f32([[0.0, 0.0, 0.0], [1.5, 1.5, -0.5], [-1.5, 1.5, -0.5], [0.0, -2.0, -0.5]])

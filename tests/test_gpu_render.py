@@ -1,6 +1,7 @@
-"""GPU parity of the cubemap probe (Sec. 3.4): the splat render against the
-brute-force oracle (every Gaussian at every pixel), the pixel directions and
-solid angles, and the probe of the benchmark's room fed to the SH fit.
+"""GPU parity of the splat renderer: the cubemap probe (Sec. 3.4) and pinhole
+cameras (the final composite) against the brute-force oracle (every Gaussian
+at every pixel), the pixel directions and solid angles, the probe of the
+benchmark's room fed to the SH fit, and a 320 x 240 view of the room.
 
 Tolerance: the inclusion test (Mahalanobis distance <= 3) and the depth order
 are the same single-precision operations on both sides, so the same splats
@@ -105,3 +106,32 @@ def test_room_probe_sampled_pixels_and_fit(nat, orc):
     sh, sh64 = nat.sh_fit(dirs, rgb, w, want64=True)
     sh_ref = orc.sh_fit(dirs.cpu().numpy(), rgb.cpu().numpy(), w.cpu().numpy())
     assert np.allclose(sh64.cpu().numpy(), sh_ref, rtol=1e-9, atol=1e-12)
+
+
+def test_render_views_matches_oracle_every_pixel(nat, orc):
+    sc = scenes.cube_scene(3000, seed=11, centre=(0.0, 0.0, 0.0), side=6.0)
+    W, H = 40, 28   # not multiples of the 8-pixel tile
+    cams = np.stack([scenes.look_at_camera([0.2, -2.5, 0.4], [0, 0, 0], W, H, 70.0),
+                     scenes.look_at_camera([1.5, 1.0, -0.5], [0.1, 0.2, 0.3], W, H, 45.0)])
+    d = scene_to_dev(sc)
+    rgb, P = nat.dgsm_render_views(d["means"], d["scales"], d["quats"], d["opac"], d["colors"], dev(cams), W, H,
+                                   want_pairs=True)
+    ref = orc.render_view_pixels(sc, cams, W, H, np.arange(2 * W * H))
+    err = np.abs(rgb.double().cpu().numpy().reshape(-1, 3) - ref)
+    assert P > 0 and ref.max() > 0.3
+    assert err.max() <= TOL and np.median(err) <= 1e-6, err.max()
+
+
+def test_room_composite_sampled_pixels(nat, orc):
+    """The final composite: the room with its avatar seen from 3 m, 320 x 240,
+    on 300 sampled pixels (the scene's own colours; the renderer alone)."""
+    wl = scenes.workload("room1p6m")
+    sc = wl["occluders"]
+    cam = scenes.look_at_camera([-1.2, -1.5, 1.6], [1.5, 0.0, 0.9], 320, 240, 60.0)
+    d = scene_to_dev(sc)
+    rgb = nat.dgsm_render_views(d["means"], d["scales"], d["quats"], d["opac"], d["colors"], dev(cam[None]),
+                                320, 240)
+    pix = np.random.default_rng(8).choice(320 * 240, 300, replace=False)
+    ref = orc.render_view_pixels(sc, cam[None], 320, 240, pix)
+    assert np.abs(rgb.double().cpu().numpy().reshape(-1, 3)[pix] - ref).max() <= TOL
+    assert np.median(ref.sum(1)) > 0.1

@@ -85,3 +85,38 @@ def test_every_face_projects_along_its_directions():
         sc = _scene([(o + 2.5 * D[p]).astype(np.float32)], 0.01, [0.8], [[1, 1, 1]])
         img = oracle.render_pixels(sc, o, face, np.arange(D.shape[0]))
         assert int(np.argmax(img[:, 0])) == p and img[p, 0] > 0.7
+
+
+def _camera(rot_seed, pos, fx, fy, cx, cy):
+    from scipy.spatial.transform import Rotation
+    R = Rotation.random(random_state=rot_seed).as_matrix()  # rows: image x, image y, forward
+    return np.float32(np.concatenate([R.ravel(), pos, [fx, fy, cx, cy]])), R
+
+
+def test_pinhole_camera_projects_view_points_to_their_pixels():
+    W, H = 40, 28
+    cam, R = _camera(3, [0.2, -0.1, 0.5], 30.0, 28.0, 20.0, 14.0)
+    rng = np.random.default_rng(5)
+    for _ in range(12):
+        i, j = int(rng.integers(2, H - 2)), int(rng.integers(2, W - 2))
+        z = float(rng.uniform(1.0, 3.0))
+        x, y = (j + 0.5 - 20.0) * z / 30.0, (i + 0.5 - 14.0) * z / 28.0
+        mu = np.float32([0.2, -0.1, 0.5]) + R.T @ np.array([x, y, z])
+        sc = _scene([mu.astype(np.float32)], 0.004, [0.8], [[1, 1, 1]])
+        img = oracle.render_view_pixels(sc, cam[None], W, H, np.arange(W * H))
+        assert int(np.argmax(img[:, 0])) == i * W + j
+        assert img[i * W + j, 0] == pytest.approx(0.8, rel=1e-4)
+
+
+def test_cube_face_is_a_camera():
+    sc = scenes.cube_scene(300, seed=6, centre=(0.0, 0.0, 0.0), side=5.0)
+    face = 8
+    cams = oracle.cube_cams([0.1, 0.2, -0.3], face)
+    a = oracle.render_pixels(sc, [0.1, 0.2, -0.3], face, np.arange(6 * face * face))
+    b = oracle.render_view_pixels(sc, cams, face, face, np.arange(6 * face * face))
+    assert np.array_equal(a, b)
+    # the camera rows are the face axes of the direction table
+    D = oracle.cube_dirs(face).reshape(6, face, face, 3)
+    for f in range(6):
+        centre_dir = D[f, face // 2 - 1:face // 2 + 1, face // 2 - 1:face // 2 + 1].mean((0, 1))
+        assert np.dot(centre_dir / np.linalg.norm(centre_dir), cams[f, 6:9]) > 0.999

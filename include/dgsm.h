@@ -301,10 +301,11 @@ int sh_fit(dgsm_ctx *ctx, const float *dirs, const float *rgb, const float *w, i
  * 1.3 x the half field of view) applied to the view-space covariance, plus
  * 0.3 pixel^2; a Gaussian contributes to the pixels whose centres lie within
  * Mahalanobis distance 3 of its projected mean, with alpha = min(0.99,
- * opacity exp(-m^2/2)); splats are composited front to back by view depth
- * (ties by Gaussian index), C += alpha T c, T *= 1 - alpha, stopping before T
- * would drop below 1e-4; the background is black.  Gaussians whose depth is
- * not above `near` are left out.  The inclusion test and the depth order are
+ * opacity exp(-m^2/2)); all of them are composited front to back by view
+ * depth (ties by Gaussian index), C += alpha T c, T *= 1 - alpha, except what
+ * lies behind a transmittance below 1e-6 (less than 1e-6 of the brightest
+ * colour); the background is black.  Gaussians whose depth is not above
+ * `near` are left out.  The inclusion test and the depth order are
  * IEEE single-precision operations in a fixed order.
  *   means, scales, quats, opac, colors: the n Gaussians (device);
  *   cams: device, n_views x 16 floats, 1 <= n_views <= 64; 1 <= W, H <= 4096;

@@ -1210,9 +1210,8 @@ static int hit_cmp(const void *x, const void *y) {
  * cameras (cams: n_views x 16 floats): every Gaussian with opacity > 0 whose
  * splat in view v covers the pixel centre within Mahalanobis distance 3
  * (single-precision decision), in order of depth (the float's bit pattern)
- * and then index, composited front to back in double precision with
- * alpha = min(0.99, opacity exp(-m^2/2)), C += alpha T c, T *= 1 - alpha,
- * stopping before T would drop below 1e-4. */
+ * and then index, all composited front to back in double precision with
+ * alpha = min(0.99, opacity exp(-m^2/2)), C += alpha T c, T *= 1 - alpha. */
 void orc_render_view_pixels(const float *means, const float *scales, const float *quats, const float *opac,
                             const float *colors, int64_t n, const float *cams, int n_views, int W, int H,
                             float near, const int64_t *pix, int64_t npix, double *rgb_out) {
@@ -1254,10 +1253,8 @@ void orc_render_view_pixels(const float *means, const float *scales, const float
             int64_t g = hits[k].g;
             double alpha = (double)opac[g] * exp(-0.5 * (double)hits[k].m2);
             if (alpha > 0.99) alpha = 0.99;
-            double Tn = T * (1.0 - alpha);
-            if (Tn < 1e-4) break;
             for (int ch = 0; ch < 3; ++ch) c[ch] += alpha * T * (double)colors[3 * g + ch];
-            T = Tn;
+            T *= 1.0 - alpha;
         }
         for (int ch = 0; ch < 3; ++ch) rgb_out[3 * p + ch] = c[ch];
         free(hits);

@@ -37,6 +37,8 @@ enum WsSlot {
     WS_ROI,            // region of interest: shell ranges, texel mask, tile and super-tile flags
     WS_RENDER,         // splat render: per-pair splat payloads
     WS_CAMS,           // the six probe cameras of dgsm_render_cubemap
+    WS_SEGS,           // splat render: per-tile segment counts and offsets, the segments
+    WS_PART,           // splat render: per-segment partial colour and transmittance of each pixel
     WS_NSLOTS
 };
 

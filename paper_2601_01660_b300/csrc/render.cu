@@ -14,9 +14,16 @@
 //   radix sort          by depth, then stably by tile: each tile's splats
 //                       front to back, ties by Gaussian index
 //   splat_ranges_kernel [start, end) of every tile
-//   splat_render_kernel one block per tile, one thread per pixel: staged
-//                       splats composited front to back,
-//                       C += alpha T c, T *= 1 - alpha, until T < 1e-4.
+//   segment kernels     every tile's list cut into segments of `seg` splats,
+//                       seg sized so that the segments fill the GPU
+//   splat_segment_kernel one block per segment, one thread per pixel: the
+//                       segment's splats composited front to back,
+//                       C += alpha T c, T *= 1 - alpha (local T)
+//   splat_merge_kernel  per pixel, the segments in order:
+//                       C = C_0 + T_0 (C_1 + T_1 (C_2 + ...))
+// Every splat within 3 sigma of a pixel is composited; a segment, and the
+// merge, stop once their transmittance is below T_CUT, which changes the
+// colour by less than T_CUT times the brightest splat colour.
 // The pixel-inclusion decision (Mahalanobis distance <= 3) and the depth
 // order use IEEE single-precision operations in a fixed order, so they are
 // reproducible on the CPU; the tiles only accelerate it.
@@ -31,7 +38,8 @@ constexpr int RT = 8;                // render tile edge, pixels
 constexpr int RT_PIX = RT * RT;      // threads per render block
 constexpr float LOWPASS = 0.3f;      // screen-space dilation, pixel^2
 constexpr float JAC_LIMIT = 1.3f;    // Jacobian evaluated within 1.3 x the half field of view
-constexpr float T_STOP = 1e-4f;      // compositing stops below this transmittance
+constexpr float T_CUT = 1e-6f;       // transmittance below which the rest is left out
+constexpr int SEG_MIN = 256;         // least splats per segment of a tile's list
 constexpr float ALPHA_MAX = 0.99f;
 constexpr int CAM_F = 16;            // floats per camera: R (9, rows x, y, forward), position (3), fx, fy, cx, cy
 
@@ -245,51 +253,96 @@ __global__ void splat_ranges_kernel(const uint32_t *__restrict__ keys, const uns
     }
 }
 
-// One block per tile, one thread per pixel; splats staged RT_PIX at a time.
-// Pixels of an edge tile beyond the image take part in the staging only.
-__global__ void __launch_bounds__(RT_PIX) splat_render_kernel(
-    const uint32_t *__restrict__ ts, const uint32_t *__restrict__ te, const uint32_t *__restrict__ order,
-    const float4 *__restrict__ payload, int W, int H, float *__restrict__ rgb) {
+// Segments: seg_cnt[t] = ceil(list length / seg), at least 1 (an empty tile
+// still writes its pixels).
+__global__ void seg_count_kernel(const uint32_t *__restrict__ ts, const uint32_t *__restrict__ te, int64_t n_tiles,
+                                 uint32_t seg, uint32_t *__restrict__ seg_cnt) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_tiles) seg_cnt[t] = max(1u, (te[t] - ts[t] + seg - 1) / seg);
+}
+
+// seg = (tile, start, end, index of the tile's first segment)
+__global__ void seg_fill_kernel(const uint32_t *__restrict__ ts, const uint32_t *__restrict__ te, int64_t n_tiles,
+                                uint32_t seg, const uint32_t *__restrict__ seg_off, uint4 *__restrict__ segs) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const uint32_t s0 = ts[t], e0 = te[t], o = seg_off[t];
+    const uint32_t n = max(1u, (e0 - s0 + seg - 1) / seg);
+    for (uint32_t k = 0; k < n; ++k)
+        segs[o + k] = make_uint4((uint32_t)t, s0 + k * seg, min(s0 + (k + 1) * seg, e0), o);
+}
+
+// One block per segment (persistent over the segments), one thread per pixel
+// of the segment's tile; splats staged RT_PIX at a time.  Writes the
+// segment's (C, T) per pixel to part[seg][pixel].
+__global__ void __launch_bounds__(RT_PIX) splat_segment_kernel(
+    const uint4 *__restrict__ segs, const unsigned long long *__restrict__ n_segs_dev,
+    const uint32_t *__restrict__ order, const float4 *__restrict__ payload, int W, int H,
+    float4 *__restrict__ part) {
     __shared__ float4 s0[RT_PIX], s1[RT_PIX], s2[RT_PIX];
     const int ntx = (W + RT - 1) / RT, nty = (H + RT - 1) / RT;
-    const int tile = blockIdx.x;
-    const int v = tile / (ntx * nty), rem = tile - v * ntx * nty, ti = rem / ntx, tj = rem - ti * ntx;
-    const int i = ti * RT + threadIdx.x / RT, j = tj * RT + threadIdx.x % RT;
-    const bool inside = i < H && j < W;
-    const float px = (float)j + 0.5f, py = (float)i + 0.5f;
-    const uint32_t start = ts[tile], end = te[tile];
-    float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
-    bool done = !inside;
-    for (uint32_t base = start; base < end; base += RT_PIX) {
-        if (__syncthreads_count(done) == RT_PIX) break;
-        const uint32_t e = base + threadIdx.x;
-        if (e < end) {
-            const uint32_t p = order[e];
-            s0[threadIdx.x] = __ldg(payload + 3 * (size_t)p);
-            s1[threadIdx.x] = __ldg(payload + 3 * (size_t)p + 1);
-            s2[threadIdx.x] = __ldg(payload + 3 * (size_t)p + 2);
-        }
-        __syncthreads();
-        const int cnt = (int)min((uint32_t)RT_PIX, end - base);
-        for (int k = 0; k < cnt && !done; ++k) {
-            const float4 a = s0[k], b = s1[k];
-            const float m2 = splat_m2(px, py, a.x, a.y, a.z, a.w, b.x);
-            if (!(m2 <= 9.0f)) continue;
-            const float alpha = fminf(ALPHA_MAX, b.y * __expf(-0.5f * m2));
-            const float Tn = T * (1.0f - alpha);
-            if (Tn < T_STOP) {
-                done = true;
-                break;
+    const unsigned long long n_segs = *n_segs_dev;
+    for (unsigned long long sg = blockIdx.x; sg < n_segs; sg += gridDim.x) {
+        const uint4 S = segs[sg];
+        const int tile = (int)S.x;
+        const int rem = tile % (ntx * nty), ti = rem / ntx, tj = rem - ti * ntx;
+        const int i = ti * RT + threadIdx.x / RT, j = tj * RT + threadIdx.x % RT;
+        const bool inside = i < H && j < W;
+        const float px = (float)j + 0.5f, py = (float)i + 0.5f;
+        float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
+        bool done = !inside;
+        for (uint32_t base = S.y; base < S.z; base += RT_PIX) {
+            if (__syncthreads_count(done) == RT_PIX) break;
+            const uint32_t e = base + threadIdx.x;
+            if (e < S.z) {
+                const uint32_t p = order[e];
+                s0[threadIdx.x] = __ldg(payload + 3 * (size_t)p);
+                s1[threadIdx.x] = __ldg(payload + 3 * (size_t)p + 1);
+                s2[threadIdx.x] = __ldg(payload + 3 * (size_t)p + 2);
             }
-            const float4 c = s2[k];
-            const float wgt = alpha * T;
-            cr = fmaf(wgt, c.x, cr);
-            cg = fmaf(wgt, c.y, cg);
-            cb = fmaf(wgt, c.z, cb);
-            T = Tn;
+            __syncthreads();
+            const int cnt = (int)min((uint32_t)RT_PIX, S.z - base);
+            for (int k = 0; k < cnt && !done; ++k) {
+                const float4 a = s0[k], b = s1[k];
+                const float m2 = splat_m2(px, py, a.x, a.y, a.z, a.w, b.x);
+                if (!(m2 <= 9.0f)) continue;
+                const float alpha = fminf(ALPHA_MAX, b.y * __expf(-0.5f * m2));
+                const float4 c = s2[k];
+                const float wgt = alpha * T;
+                cr = fmaf(wgt, c.x, cr);
+                cg = fmaf(wgt, c.y, cg);
+                cb = fmaf(wgt, c.z, cb);
+                T = T * (1.0f - alpha);
+                if (T < T_CUT) done = true;
+            }
         }
+        __syncthreads();  // the staging buffers are refilled by the next segment
+        part[sg * RT_PIX + threadIdx.x] = make_float4(cr, cg, cb, T);
     }
-    if (!inside) return;
+}
+
+// Per pixel, the segments of its tile in order: C = C_0 + T_0 (C_1 + ...).
+__global__ void splat_merge_kernel(const uint32_t *__restrict__ seg_cnt, const uint32_t *__restrict__ seg_off,
+                                   const float4 *__restrict__ part, int64_t n_tiles, int W, int H,
+                                   float *__restrict__ rgb) {
+    const int ntx = (W + RT - 1) / RT, nty = (H + RT - 1) / RT;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= n_tiles * RT_PIX) return;
+    const int64_t tile = gid / RT_PIX;
+    const int px = (int)(gid - tile * RT_PIX);
+    const int v = (int)(tile / (ntx * nty)), rem = (int)(tile - (int64_t)v * ntx * nty);
+    const int ti = rem / ntx, tj = rem - ti * ntx;
+    const int i = ti * RT + px / RT, j = tj * RT + px % RT;
+    if (i >= H || j >= W) return;
+    const uint32_t o = seg_off[tile], n = seg_cnt[tile];
+    float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
+    for (uint32_t k = 0; k < n && T >= T_CUT; ++k) {
+        const float4 q = part[(size_t)(o + k) * RT_PIX + px];
+        cr = fmaf(T, q.x, cr);
+        cg = fmaf(T, q.y, cg);
+        cb = fmaf(T, q.z, cb);
+        T *= q.w;
+    }
     const size_t pix = ((size_t)v * H + i) * W + j;
     rgb[3 * pix] = cr;
     rgb[3 * pix + 1] = cg;
@@ -357,6 +410,8 @@ int render_impl(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     cudaError_t e = cudaMemsetAsync(w_rng, 0, rng_bytes + sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "render: memset");
     uint64_t P = 0;
+    const uint32_t *order = nullptr;     // splat of each sorted pair
+    const float4 *payload = nullptr;     // per-splat payloads
     const int grid = (int)std::min<int64_t>((std::max<int64_t>(n, 1) + 255) / 256, (int64_t)ctx->num_sms * 16);
     if (n > 0) {
         splat_count_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, n, cams, n_views, W, H, near,
@@ -401,10 +456,30 @@ int render_impl(dgsm_ctx *ctx, const float *means, const float *scales, const fl
         while (((int64_t)1 << bits) < n_tiles) ++bits;
         if ((rc = radix_sort_pairs(ctx, &tkeys, &sids, keys, vals, d_total, (int64_t)P, bits, s))) return rc;
         splat_ranges_kernel<<<rgrid, 256, 0, s>>>(tkeys, d_total, ts, te);
-        splat_render_kernel<<<(unsigned)n_tiles, RT_PIX, 0, s>>>(ts, te, sids, (const float4 *)pl, W, H, rgb_out);
-    } else {
-        splat_render_kernel<<<(unsigned)n_tiles, RT_PIX, 0, s>>>(ts, te, ts, nullptr, W, H, rgb_out);
+        order = sids;
+        payload = (const float4 *)pl;
     }
+    // segments of every tile's list (an empty tile has one empty segment):
+    // long enough that a tile's front layers saturate within its first
+    // segment, short enough that the segments give every SM 8 blocks
+    const uint64_t fill = (uint64_t)ctx->num_sms * 8;
+    const uint32_t seg = (uint32_t)std::max<uint64_t>(SEG_MIN, ((P + fill - 1) / fill + RT_PIX - 1) / RT_PIX * RT_PIX);
+    const int64_t max_segs = (int64_t)(P / seg) + n_tiles;
+    void *w_seg, *w_part;
+    const size_t cnt_bytes = (sizeof(uint32_t) * (size_t)n_tiles + 15) & ~(size_t)15;
+    if ((rc = ws_reserve(ctx, WS_SEGS, 2 * cnt_bytes + 16 + sizeof(uint4) * (size_t)max_segs, &w_seg))) return rc;
+    if ((rc = ws_reserve(ctx, WS_PART, sizeof(float4) * RT_PIX * (size_t)max_segs, &w_part))) return rc;
+    uint32_t *seg_cnt = (uint32_t *)w_seg, *seg_off = (uint32_t *)((char *)w_seg + cnt_bytes);
+    unsigned long long *d_nseg = (unsigned long long *)((char *)w_seg + 2 * cnt_bytes);
+    uint4 *segs = (uint4 *)((char *)w_seg + 2 * cnt_bytes + 16);
+    const int tgrid = (int)((n_tiles + 255) / 256);
+    seg_count_kernel<<<tgrid, 256, 0, s>>>(ts, te, n_tiles, seg, seg_cnt);
+    if ((rc = scan_exclusive_u32(ctx, seg_cnt, seg_off, n_tiles, d_nseg, s))) return rc;
+    seg_fill_kernel<<<tgrid, 256, 0, s>>>(ts, te, n_tiles, seg, seg_off, segs);
+    const int sgrid = (int)std::min<int64_t>(max_segs, (int64_t)ctx->num_sms * 16);
+    splat_segment_kernel<<<sgrid, RT_PIX, 0, s>>>(segs, d_nseg, order, payload, W, H, (float4 *)w_part);
+    splat_merge_kernel<<<(int)((n_tiles * RT_PIX + 255) / 256), 256, 0, s>>>(seg_cnt, seg_off, (const float4 *)w_part,
+                                                                              n_tiles, W, H, rgb_out);
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "splat render kernels");
 }

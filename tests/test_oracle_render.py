@@ -1,7 +1,7 @@
 """Pins of the cubemap probe render (Sec. 3.4): the face axes against the
 cubemap sample geometry, a single splat's centre and neighbour pixels in
 closed form (EWA covariance of an isotropic Gaussian), front-to-back
-compositing order, the transmittance stop, the near plane, and every face's
+compositing order through opaque layers, the near plane, and every face's
 projection against the direction table."""
 import math
 
@@ -61,10 +61,10 @@ def test_front_to_back_order_and_stop():
     rgb = oracle.render_pixels(sc, [0, 0, 0], face, [p])[0]
     a1, a2 = 0.5, 0.6  # alpha at the splat centre (m^2 ~ 0)
     assert np.allclose(rgb, [a1, (1 - a1) * a2, 0], atol=2e-5)
-    # three opaque layers: T = 0.01, then 1e-4 (kept), then 1e-6 < 1e-4 (stop)
+    # three opaque layers (alpha capped at 0.99): T = 1, 0.01, 1e-4 in front of them
     sc = _scene([(k * d).astype(np.float32) for k in (2.0, 3.0, 4.0)], 0.05, [1.0, 1.0, 1.0], [c1, c2, c3])
     rgb = oracle.render_pixels(sc, [0, 0, 0], face, [p])[0]
-    assert np.allclose(rgb, [0.99, 0.01 * 0.99, 0.0], rtol=1e-4, atol=1e-9)
+    assert np.allclose(rgb, [0.99, 0.01 * 0.99, 1e-4 * 0.99], rtol=1e-4, atol=1e-12)
 
 
 def test_near_plane_and_transparent():

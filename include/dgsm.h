@@ -345,6 +345,17 @@ int dgsm_render_cubemap(dgsm_ctx *ctx, const float *means, const float *scales, 
  * asynchronous. */
 int dgsm_cube_dirs(dgsm_ctx *ctx, int32_t face, float *dirs_out, float *w_out, void *stream);
 
+/* Self-test of the library's bounded device-side waits (failure detection;
+ * the paper has no counterpart).  Every wait on an mbarrier (the tensor-core
+ * kernels of the surrogate) polls a bounded number of times, then records
+ * DGSM_ERR_TIMEOUT in the context's status word and lets the kernel return,
+ * so that the context stays usable.  This entry point runs one such wait on
+ * an mbarrier that expects one arrival: with arrive != 0 the arrival comes
+ * and the wait completes; with arrive = 0 nothing arrives and the wait gives
+ * up after `limit` polls (1..2^24).  Read the outcome with dgsm_sync_status.
+ * Returns DGSM_OK, DGSM_ERR_INVALID_ARG or DGSM_ERR_CUDA. */
+int dgsm_selftest_wait(dgsm_ctx *ctx, int32_t arrive, int64_t limit, void *stream);
+
 /* sh_fit without a context and without allocating device memory.  The paper
  * has no counterpart: this exists for callers that cannot call cudaMalloc --
  * a real-time frame loop in which cudaMalloc/cudaFree would synchronise the

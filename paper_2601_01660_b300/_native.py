@@ -123,6 +123,7 @@ _lib.sh_fit_static.argtypes = [_vp, _vp, _vp, _i64, _f64, _vp, _vp, _vp, _vp]
 _lib.sh_relight.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64,
                             C.POINTER(RelightParams), _vp, _vp]
 _lib.dgsm_sync_status.argtypes = [_vp, _vp]
+_lib.dgsm_selftest_wait.argtypes = [_vp, _i32, _i64, _vp]
 _lib.dgsm_weighted_centroid.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp]
 _lib.dgsm_frame_host.argtypes = [_vp, C.POINTER(FrameHostIn), C.POINTER(Params),
                                  C.POINTER(RelightParams), _vp, _vp, _vp]
@@ -661,6 +662,14 @@ def dgsm_autotune_build(means, scales, quats, opac, lights, H, W, radii, tiles=(
     table = {(t, c): float(ms[a * len(chunks) + b]) for a, t in enumerate(tiles)
              for b, c in enumerate(chunks)}
     return best, table
+
+
+def dgsm_selftest_wait(arrive: bool, limit: int = 4096, ctx: Context | None = None, stream=None):
+    """One bounded mbarrier wait on the device (failure-detection self-test):
+    without `arrive` it times out and records DGSM_ERR_TIMEOUT (read it with
+    dgsm_sync_status)."""
+    ctx = ctx or context()
+    ctx.check(_lib.dgsm_selftest_wait(ctx.handle, 1 if arrive else 0, int(limit), _stream(stream)))
 
 
 def dgsm_sync_status(ctx: Context | None = None, stream=None) -> int:

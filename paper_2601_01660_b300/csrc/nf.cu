@@ -424,9 +424,10 @@ __device__ __forceinline__ void bar_init(uint32_t bar) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Bounded wait for phase `parity` of the mbarrier; false on timeout.
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
-    for (long long it = 0; it < WAIT_LIMIT; ++it) {
+// Bounded wait for phase `parity` of the mbarrier: at most `limit` polls;
+// false on timeout.
+__device__ __forceinline__ bool bar_wait_n(uint32_t bar, uint32_t parity, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -437,6 +438,23 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
         if (done) return true;
     }
     return false;
+}
+
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) { return bar_wait_n(bar, parity, WAIT_LIMIT); }
+
+// Self-test of the bounded wait: one mbarrier expecting one arrival.  With
+// `arrive` the thread arrives first and the wait completes; without, nothing
+// arrives, the wait gives up after `limit` polls, and the kernel records
+// DGSM_ERR_TIMEOUT in the status word and returns normally.
+__global__ void wait_selftest_kernel(int arrive, long long limit, int *status) {
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+    if (threadIdx.x == 0) bar_init(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+        if (!bar_wait_n(b, 0u, limit)) record_status(status, DGSM_ERR_TIMEOUT);
+    }
 }
 
 // 32 consecutive fp32 columns of this thread's TMEM lane
@@ -901,4 +919,14 @@ extern "C" int nf_attenuate(dgsm_ctx *ctx, const float *params, const uint8_t *m
     tc::combine_kernel<<<cgrid, 256, 0, s>>>(T_all, L, n_q, light_w, direct_frac, colors_in, colors_out, T_out);
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "nf: combine kernel");
+}
+
+extern "C" int dgsm_selftest_wait(dgsm_ctx *ctx, int32_t arrive, int64_t limit, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (limit < 1 || limit > (1ll << 24)) return fail(ctx, DGSM_ERR_INVALID_ARG, "selftest: limit in 1..2^24");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    tc::wait_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(arrive, (long long)limit, ctx->d_status);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "wait_selftest_kernel");
 }

@@ -54,6 +54,9 @@ def _declare(L):
     L.orc_octa_encode.argtypes = [_d, _d, _d]
     L.orc_octa_decode.argtypes = [C.c_double, C.c_double, _d]
     L.orc_texel_dir.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _d]
+    L.orc_cube_encode.restype = C.c_int
+    L.orc_cube_encode.argtypes = [_d, _d, _d]
+    L.orc_cube_decode.argtypes = [C.c_int, C.c_double, C.c_double, _d]
     L.orc_build_tau.argtypes = [_f, _f, _f, _f, I64, _f, C.c_int, C.c_int, C.c_int, _f,
                                 C.c_int, C.c_double, _d]
     L.orc_build_tau_texels.argtypes = [_f, _f, _f, _f, I64, _f, C.c_int, C.c_int, _f, C.c_int,
@@ -88,6 +91,8 @@ def _declare(L):
                               C.POINTER(C.c_uint8), _i32]
     L.orc_set_beta_mode.argtypes = [C.c_int]
     L.orc_get_beta_mode.restype = C.c_int
+    L.orc_set_atlas_map.argtypes = [C.c_int]
+    L.orc_get_atlas_map.restype = C.c_int
     L.orc_render_pixels.argtypes = [_f, _f, _f, _f, _f, I64, _f, C.c_int, C.c_float,
                                     C.POINTER(C.c_int64), I64, _d]
     L.orc_render_view_pixels.argtypes = [_f, _f, _f, _f, _f, I64, _f, C.c_int, C.c_int, C.c_int, C.c_float,
@@ -155,6 +160,26 @@ class beta_mode:
         return False
 
 
+class atlas_map:
+    """Context manager: the oracle's atlas parameterisation, 0 the octahedral
+    map (Sec. 3.2) or 1 the cube map (six F x F faces stacked in rows, H = 6F,
+    W = F; the ablation's alternative)."""
+
+    def __init__(self, map_id: int):
+        if map_id not in (0, 1):
+            raise ValueError("atlas map must be 0 (octahedral) or 1 (cube)")
+        self.map_id = map_id
+
+    def __enter__(self):
+        self.prev = lib().orc_get_atlas_map()
+        lib().orc_set_atlas_map(self.map_id)
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_atlas_map(self.prev)
+        return False
+
+
 def beta(scale, alpha: float, kappa: float = 1.0) -> float:
     return float(lib().orc_beta(_pf(_c32(scale)), float(alpha), float(kappa)))
 
@@ -182,6 +207,19 @@ def octa_encode(d):
 def octa_decode(u, v) -> np.ndarray:
     d = np.zeros(3)
     lib().orc_octa_decode(float(u), float(v), _pd(d))
+    return d
+
+
+def cube_encode(d):
+    """(face, u, v) of direction d on the cube map."""
+    u, v = C.c_double(), C.c_double()
+    f = lib().orc_cube_encode(_pd(_c64(d)), C.byref(u), C.byref(v))
+    return f, u.value, v.value
+
+
+def cube_decode(f, u, v) -> np.ndarray:
+    d = np.zeros(3)
+    lib().orc_cube_decode(int(f), float(u), float(v), _pd(d))
     return d
 
 

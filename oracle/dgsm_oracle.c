@@ -182,9 +182,50 @@ void orc_octa_decode(double u, double v, double *d) {
     d[0] = x / n; d[1] = y / n; d[2] = z / n;
 }
 
-/* Direction of texel (i,j) of an H x W atlas: decode of its pixel centre. */
+/* Atlas parameterisation in use (ablation (C) of Sec. 4): 0 the octahedral
+ * map, 1 a cube map of six F x F faces stacked in rows (H = 6F, W = F).  Set
+ * for the whole library by orc_set_atlas_map (test infrastructure). */
+static int g_atlas_map = 0;
+void orc_set_atlas_map(int map) { g_atlas_map = map; }
+int orc_get_atlas_map(void) { return g_atlas_map; }
+
+/* Cube face f: forward axis, texel axes U (columns u) and V (rows v) as
+ * (axis, sign): (+x, -z, -y), (-x, +z, -y), (+y, +x, +z), (-y, +x, -z),
+ * (+z, +x, -y), (-z, -x, -y). */
+static const int kCubeAxis[6][3] = {{0, 2, 1}, {0, 2, 1}, {1, 0, 2}, {1, 0, 2}, {2, 0, 1}, {2, 0, 1}};
+static const int kCubeSign[6][3] = {{1, -1, -1}, {-1, 1, -1}, {1, 1, 1}, {-1, 1, -1}, {1, 1, -1}, {-1, -1, -1}};
+
+/* Unit direction of the point (u, v) of cube face f. */
+void orc_cube_decode(int f, double u, double v, double *d) {
+    double c[3];
+    c[kCubeAxis[f][0]] = kCubeSign[f][0];
+    c[kCubeAxis[f][1]] = kCubeSign[f][1] * u;
+    c[kCubeAxis[f][2]] = kCubeSign[f][2] * v;
+    double n = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    d[0] = c[0] / n; d[1] = c[1] / n; d[2] = c[2] / n;
+}
+
+/* Face of the largest component (ties to x, then y; >= 0 the positive face)
+ * and the face coordinates of d. */
+int orc_cube_encode(const double *d, double *u, double *v) {
+    double ax = fabs(d[0]), ay = fabs(d[1]), az = fabs(d[2]);
+    int f = (ax >= ay && ax >= az) ? (d[0] >= 0 ? 0 : 1) : (ay >= az ? (d[1] >= 0 ? 2 : 3) : (d[2] >= 0 ? 4 : 5));
+    double m = fabs(d[kCubeAxis[f][0]]);
+    *u = kCubeSign[f][1] * d[kCubeAxis[f][1]] / m;
+    *v = kCubeSign[f][2] * d[kCubeAxis[f][2]] / m;
+    return f;
+}
+
+/* Direction of texel (i,j) of an H x W atlas: decode of its pixel centre
+ * (octahedral, or face i / W of a cube map). */
 void orc_texel_dir(int i, int j, int H, int W, double *d) {
     double u = (2.0 * j + 1.0) / W - 1.0;
+    if (g_atlas_map == 1) {
+        int f = i / W;
+        double v = (2.0 * (i - f * W) + 1.0) / W - 1.0;
+        orc_cube_decode(f, u, v, d);
+        return;
+    }
     double v = (2.0 * i + 1.0) / H - 1.0;
     orc_octa_decode(u, v, d);
 }
@@ -296,15 +337,24 @@ double orc_sample_T(const double *atlas_l, int H, int W, const float *radii, int
     double t = sqrt(vx * vx + vy * vy + vz * vz);
     if (t == 0) return 1.0;
     double d[3] = {vx / t, vy / t, vz / t}, u, v;
-    orc_octa_encode(d, &u, &v);
-    double gx = (u + 1.0) * 0.5 * W - 0.5, gy = (v + 1.0) * 0.5 * H - 0.5;
+    int r0 = 0, hf = H;   /* rows of the point's face (all rows for the octahedral map) */
+    if (g_atlas_map == 1) {
+        int f = orc_cube_encode(d, &u, &v);
+        r0 = f * W;
+        hf = W;
+    } else {
+        orc_octa_encode(d, &u, &v);
+    }
+    double gx = (u + 1.0) * 0.5 * W - 0.5, gy = (v + 1.0) * 0.5 * hf - 0.5;
     double fj = floor(gx), fi = floor(gy);
     double ax = gx - fj, ay = gy - fi;
     int j0 = (int)fj, i0 = (int)fi, j1 = j0 + 1, i1 = i0 + 1;
     if (j0 < 0) j0 = 0; if (j0 > W - 1) j0 = W - 1;
     if (j1 < 0) j1 = 0; if (j1 > W - 1) j1 = W - 1;
-    if (i0 < 0) i0 = 0; if (i0 > H - 1) i0 = H - 1;
-    if (i1 < 0) i1 = 0; if (i1 > H - 1) i1 = H - 1;
+    if (i0 < 0) i0 = 0; if (i0 > hf - 1) i0 = hf - 1;
+    if (i1 < 0) i1 = 0; if (i1 > hf - 1) i1 = hf - 1;
+    i0 += r0;
+    i1 += r0;
     int k = -1;
     for (int q = 0; q < K; ++q)
         if ((double)radii[q] <= t) k = q;
@@ -363,8 +413,15 @@ static float sgnf_pos(float x) { return x >= 0.0f ? 1.0f : -1.0f; }
  * out_i[0..4] = cell i, cell j, bilinear base i0, base j0, shell k (-1 below r_0);
  * out_f[0..2] = fy, fx (bilinear fractions), t (distance).  All single
  * precision, IEEE-rounded, no FMA. */
+static void f32_sample_index_cube(const float *x, const float *o, int F, const float *radii, int K,
+                                  int32_t *out_i, float *out_f);
+
 void orc_f32_sample_index(const float *x, const float *o, int H, int W, const float *radii,
                           int K, int32_t *out_i, float *out_f) {
+    if (g_atlas_map == 1) {
+        f32_sample_index_cube(x, o, W, radii, K, out_i, out_f);
+        return;
+    }
     volatile float vx = x[0] - o[0], vy = x[1] - o[1], vz = x[2] - o[2];
     volatile float t2a = vx * vx, t2b = vy * vy, t2c = vz * vz;
     volatile float t2 = (t2a + t2b) + t2c;
@@ -391,6 +448,44 @@ void orc_f32_sample_index(const float *x, const float *o, int H, int W, const fl
     for (int q = 0; q < K; ++q)
         if (radii[q] <= t) k = q;
     out_i[0] = ci; out_i[1] = cj; out_i[2] = (int32_t)bi; out_i[3] = (int32_t)bj; out_i[4] = k;
+    volatile float fy = gy - bi, fx = gx - bj;
+    out_f[0] = fy; out_f[1] = fx; out_f[2] = t;
+}
+
+/* The same decisions on a cube map of F x F faces (rows global, face f's
+ * rows from f F): the face of the largest component of v = x - o (ties to x,
+ * then y; a component >= 0 picks the positive face), u = U.v / m,
+ * v = V.v / m with m that component's size, then as for the octahedral map
+ * within the face. */
+static void f32_sample_index_cube(const float *x, const float *o, int F, const float *radii, int K,
+                                  int32_t *out_i, float *out_f) {
+    volatile float vx = x[0] - o[0], vy = x[1] - o[1], vz = x[2] - o[2];
+    volatile float t2a = vx * vx, t2b = vy * vy, t2c = vz * vz;
+    volatile float t2 = (t2a + t2b) + t2c;
+    float t = sqrtf(t2);
+    float c[3] = {vx, vy, vz};
+    float ax = fabsf(c[0]), ay = fabsf(c[1]), az = fabsf(c[2]);
+    int f = (ax >= ay && ax >= az) ? (c[0] >= 0.0f ? 0 : 1) : (ay >= az ? (c[1] >= 0.0f ? 2 : 3) : (c[2] >= 0.0f ? 4 : 5));
+    float m = fabsf(c[kCubeAxis[f][0]]);
+    float u = 0.0f, v = 0.0f;
+    if (m != 0.0f) {
+        volatile float nu = (float)kCubeSign[f][1] * c[kCubeAxis[f][1]];
+        volatile float nv = (float)kCubeSign[f][2] * c[kCubeAxis[f][2]];
+        volatile float qu = nu / m, qv = nv / m;
+        u = qu;
+        v = qv;
+    }
+    volatile float fu = ((u + 1.0f) * 0.5f) * (float)F;
+    volatile float fv = ((v + 1.0f) * 0.5f) * (float)F;
+    volatile float gx = fu - 0.5f, gy = fv - 0.5f;
+    float bj = floorf(gx), bi = floorf(gy);
+    int cj = (int)floorf(fu), ci = (int)floorf(fv);
+    if (cj < 0) cj = 0; if (cj > F - 1) cj = F - 1;
+    if (ci < 0) ci = 0; if (ci > F - 1) ci = F - 1;
+    int k = -1;
+    for (int q = 0; q < K; ++q)
+        if (radii[q] <= t) k = q;
+    out_i[0] = f * F + ci; out_i[1] = cj; out_i[2] = f * F + (int32_t)bi; out_i[3] = (int32_t)bj; out_i[4] = k;
     volatile float fy = gy - bi, fx = gx - bj;
     out_f[0] = fy; out_f[1] = fx; out_f[2] = t;
 }
@@ -433,10 +528,61 @@ static float f32_centre(int j, int W) {
     return r;
 }
 
+/* FP32 decode of the point (u, v) of cube face f, normalised. */
+static void f32_decode_cube(int f, float u, float v, float *d) {
+    float c[3];
+    c[kCubeAxis[f][0]] = (float)kCubeSign[f][0];
+    c[kCubeAxis[f][1]] = (float)kCubeSign[f][1] * u;
+    c[kCubeAxis[f][2]] = (float)kCubeSign[f][2] * v;
+    volatile float xx = c[0] * c[0], yy = c[1] * c[1], zz = c[2] * c[2];
+    volatile float n2 = (xx + yy) + zz;
+    float n = sqrtf(n2);
+    volatile float dx = c[0] / n, dy = c[1] / n, dz = c[2] / n;
+    d[0] = dx; d[1] = dy; d[2] = dz;
+}
+
+/* Cone of a rectangle of a cube-map atlas (faces of F = W texels stacked in
+ * rows): axis the decoded rectangle centre, half-angle the largest angle to
+ * its corners (within a face the decode is a central projection of the face
+ * plane); a rectangle across two faces spans everything. */
+static void f32_rect_cone_cube(int i0, int i1, int j0, int j1, int F, float *cone) {
+    int f = i0 / F;
+    if ((i1 - 1) / F != f) {
+        cone[0] = 0.0f; cone[1] = 0.0f; cone[2] = 1.0f; cone[3] = -1.0f; cone[4] = 0.0f; cone[5] = 1.0f;
+        return;
+    }
+    float ua = f32_centre(j0, F), ub = f32_centre(j1 - 1, F);
+    float va = f32_centre(i0 - f * F, F), vb = f32_centre(i1 - 1 - f * F, F);
+    volatile float su = ua + ub, sv = va + vb;
+    volatile float uc = su * 0.5f, vc = sv * 0.5f;
+    float c[3];
+    f32_decode_cube(f, uc, vc, c);
+    float us[2] = {ua, ub}, vs[2] = {va, vb}, cmin = 1.0f;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            float d[3];
+            f32_decode_cube(f, us[b], vs[a], d);
+            float cs = f32_dot(c, d);
+            if (cs < cmin) cmin = cs;
+        }
+    cone[0] = c[0]; cone[1] = c[1]; cone[2] = c[2];
+    if (cmin <= 0.0f) {
+        cone[3] = -1.0f; cone[4] = 0.0f; cone[5] = 1.0f;
+    } else {
+        volatile float cc = cmin * cmin;
+        volatile float om = 1.0f - cc;
+        cone[3] = cmin; cone[4] = sqrtf(om); cone[5] = 0.0f;
+    }
+}
+
 /* Direction cone of the texel-centre rectangle [j0,j1) x [i0,i1):
  * cone[0..2] axis, cone[3] cos, cone[4] sin, cone[5] = 1 if it spans a
  * hemisphere or more (then every Gaussian overlaps it). */
 void orc_f32_rect_cone(int i0, int i1, int j0, int j1, int H, int W, float *cone) {
+    if (g_atlas_map == 1) {
+        f32_rect_cone_cube(i0, i1, j0, j1, W, cone);
+        return;
+    }
     float ua = f32_centre(j0, W), ub = f32_centre(j1 - 1, W);
     float va = f32_centre(i0, H), vb = f32_centre(i1 - 1, H);
     volatile float su = ua + ub, sv = va + vb;
@@ -584,7 +730,13 @@ static void f32_plane(const float *a, const float *b, const float *c, float *n) 
  * mid plane: on the top half's side); pl[15] = 1 if the planes are valid
  * (the rectangle lies in one face and has at least 2 rows and 2 columns);
  * pl[16] = 1 if the bottom half is not empty. */
+static void f32_rect_planes_cube(int i0, int i1, int j0, int j1, int half, int F, float *pl);
+
 void orc_f32_rect_planes(int i0, int i1, int j0, int j1, int half, int H, int W, float *pl) {
+    if (g_atlas_map == 1) {
+        f32_rect_planes_cube(i0, i1, j0, j1, half, W, pl);
+        return;
+    }
     float ua = f32_centre(j0, W), ub = f32_centre(j1 - 1, W);
     float va = f32_centre(i0, H), vb = f32_centre(i1 - 1, H);
     for (int q = 0; q < 17; ++q) pl[q] = 0.0f;
@@ -609,6 +761,38 @@ void orc_f32_rect_planes(int i0, int i1, int j0, int j1, int half, int H, int W,
         float m0[3], m1[3], top[3];
         f32_decode(ua, vm, m0); f32_decode(ub, vm, m1);
         f32_decode(uc, va, top);
+        f32_plane(m0, m1, top, pl + 12);
+    }
+    pl[15] = 1.0f;
+}
+
+/* Planes of a rectangle of a cube-map atlas: the edge planes through its
+ * corner directions and the plane between its halves (atlas lines are great
+ * circles within a face). */
+static void f32_rect_planes_cube(int i0, int i1, int j0, int j1, int half, int F, float *pl) {
+    int f = i0 / F;
+    float ua = f32_centre(j0, F), ub = f32_centre(j1 - 1, F);
+    float va = f32_centre(i0 - f * F, F), vb = f32_centre(i1 - 1 - f * F, F);
+    for (int q = 0; q < 17; ++q) pl[q] = 0.0f;
+    pl[16] = i1 - i0 > half ? 1.0f : 0.0f;
+    if (!(ua < ub && va < vb) || (i1 - 1) / F != f) return;
+    volatile float su = ua + ub, sv = va + vb;
+    volatile float uc = su * 0.5f, vc = sv * 0.5f;
+    float c[3], d00[3], d01[3], d10[3], d11[3];
+    f32_decode_cube(f, uc, vc, c);
+    f32_decode_cube(f, ua, va, d00); f32_decode_cube(f, ub, va, d01);
+    f32_decode_cube(f, ua, vb, d10); f32_decode_cube(f, ub, vb, d11);
+    f32_plane(d00, d01, c, pl);
+    f32_plane(d10, d11, c, pl + 3);
+    f32_plane(d00, d10, c, pl + 6);
+    f32_plane(d01, d11, c, pl + 9);
+    if (pl[16] != 0.0f) {
+        volatile float num = (float)(2 * (i0 + half - f * F));
+        volatile float q = num / (float)F;
+        volatile float vm = q - 1.0f;
+        float m0[3], m1[3], top[3];
+        f32_decode_cube(f, ua, vm, m0); f32_decode_cube(f, ub, vm, m1);
+        f32_decode_cube(f, uc, va, top);
         f32_plane(m0, m1, top, pl + 12);
     }
     pl[15] = 1.0f;
@@ -1086,8 +1270,14 @@ void orc_f32_roi(const float *recv, int64_t n, const float *box, const float *li
             orc_f32_sample_index(x, lights + 3 * l, H, W, radii, K, oi, of);
             if (of[2] == 0.0f) continue;
             int i0 = oi[2], j0 = oi[3], i1 = i0 + 1, j1 = j0 + 1;
-            i0 = i0 < 0 ? 0 : (i0 > H - 1 ? H - 1 : i0);
-            i1 = i1 < 0 ? 0 : (i1 > H - 1 ? H - 1 : i1);
+            /* rows clamp to the point's face on a cube map, to the atlas otherwise */
+            int rlo = 0, rhi = H - 1;
+            if (g_atlas_map == 1) {
+                rlo = (oi[0] / W) * W;
+                rhi = rlo + W - 1;
+            }
+            i0 = i0 < rlo ? rlo : (i0 > rhi ? rhi : i0);
+            i1 = i1 < rlo ? rlo : (i1 > rhi ? rhi : i1);
             j0 = j0 < 0 ? 0 : (j0 > W - 1 ? W - 1 : j0);
             j1 = j1 < 0 ? 0 : (j1 > W - 1 ? W - 1 : j1);
             uint8_t *m = mask + l * HW;

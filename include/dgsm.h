@@ -76,7 +76,14 @@ enum dgsm_dtype { DGSM_F32 = 0, DGSM_F16 = 1, DGSM_BF16 = 2 };
  *      sqrt(det Sigma) = s_x s_y s_z, so 4 computes the same value as 3.
  * The culling radius keeps the eps_cull bound under every mapping: the
  * factor (s_max/s_min) above becomes sqrt(2 pi) s_max (mapping 1) or
- * s_max / (2 pi s_x s_y s_z) (mappings 3, 4). */
+ * s_max / (2 pi s_x s_y s_z) (mappings 3, 4).
+ * atlas_map: the atlas parameterisation (ablation (C) of Sec. 4): 0 the
+ * octahedral map of Eq. 6 (the default); 1 a cube map of six F x F faces
+ * stacked in rows (H = 6F, W = F, F a multiple of the tile): face f holds
+ * rows [f F, (f+1) F) and its texel (u, v) looks along F_f + u U_f + v V_f
+ * with the cube-map axes (F, U, V) = (+x, -z, -y), (-x, +z, -y), (+y, +x, +z),
+ * (-y, +x, -z), (+z, +x, -y), (-z, -x, -y).  Cube atlases are read with
+ * dgsm_attenuate_cube. */
 typedef struct {
     float kappa;
     float eps_cull;
@@ -85,6 +92,7 @@ typedef struct {
     int32_t atlas_dtype;
     int32_t max_pairs;
     int32_t beta_mode;
+    int32_t atlas_map;
 } dgsm_params;
 
 /* Receiver-driven region of interest of dgsm_build_roi (device pointers). */
@@ -268,6 +276,23 @@ int dgsm_attenuate_footprint(dgsm_ctx *ctx, const void *atlas, int32_t dtype, in
                              const float *light_w, float direct_frac, int32_t mode,
                              int32_t n_samples, uint64_t seed, float *colors_out, float *T_out,
                              void *stream);
+
+/* dgsm_attenuate on a cube-map atlas (dgsm_params.atlas_map = 1): atlas
+ * [n_lights][K][6F][F] of `dtype`.  The point's face is that of the largest
+ * component of x - o (ties go to x, then y; a component >= 0 picks the
+ * positive face), u = U.v / m and v = V.v / m with m that component's size;
+ * the bilinear taps are clamped to the face's F x F texels (no filtering
+ * across faces), and shells as for dgsm_attenuate.  One atlas (no dynamic
+ * atlas).  Other arguments and errors as for dgsm_attenuate. */
+int dgsm_attenuate_cube(dgsm_ctx *ctx, const void *atlas, int32_t dtype, int32_t n_lights, int32_t F,
+                        const float *radii, int32_t K, const float *lights, const float *q_means,
+                        const float *colors_in, int64_t n_q, const float *light_w, float direct_frac,
+                        float *colors_out, float *T_out, void *stream);
+
+/* The integer decisions of dgsm_attenuate_cube, as dgsm_sample_index gives
+ * them for the octahedral map: rows are global (face f's rows start at f F). */
+int dgsm_sample_index_cube(dgsm_ctx *ctx, const float *points, int64_t n, const float *light, int32_t F,
+                           const float *radii, int32_t K, int32_t *idx_out, float *frac_out, void *stream);
 
 /* The integer decisions of dgsm_attenuate for n points seen from one light
  * (device pointer to 3 floats): idx_out (n,5) = texel cell row i, cell

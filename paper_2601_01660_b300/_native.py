@@ -39,15 +39,15 @@ class Params(C.Structure):
     """Mirror of dgsm_params."""
     _fields_ = [("kappa", C.c_float), ("eps_cull", C.c_float), ("tile", C.c_int32),
                 ("chunk", C.c_int32), ("atlas_dtype", C.c_int32), ("max_pairs", C.c_int32),
-                ("beta_mode", C.c_int32)]
+                ("beta_mode", C.c_int32), ("atlas_map", C.c_int32)]
 
     @classmethod
     def make(cls, kappa=1.0, eps_cull=1e-7, tile=8, chunk=128, atlas_dtype="f32", max_pairs=0,
-             beta_mode=2):
+             beta_mode=2, atlas_map=0):
         p = cls()
         _lib.dgsm_default_params(C.byref(p))
         p.kappa, p.eps_cull, p.tile, p.chunk, p.max_pairs = kappa, eps_cull, tile, chunk, max_pairs
-        p.beta_mode = beta_mode
+        p.beta_mode, p.atlas_map = beta_mode, {"octa": 0, "cube": 1}.get(atlas_map, atlas_map)
         p.atlas_dtype = DTYPES[atlas_dtype] if isinstance(atlas_dtype, str) else int(atlas_dtype)
         return p
 
@@ -110,6 +110,9 @@ _lib.dgsm_attenuate.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32
 _lib.dgsm_attenuate_dyn.argtypes = [_vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _i32, _i32, _vp,
                                     _i32, _vp, _vp, _vp, _i64, _vp, _f32, _vp, _vp, _vp]
 _lib.dgsm_sample_index.argtypes = [_vp, _vp, _i64, _vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp]
+_lib.dgsm_attenuate_cube.argtypes = [_vp, _vp, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp, _i64, _vp, _f32,
+                                     _vp, _vp, _vp]
+_lib.dgsm_sample_index_cube.argtypes = [_vp, _vp, _i64, _vp, _i32, _vp, _i32, _vp, _vp, _vp]
 _lib.dgsm_attenuate_footprint.argtypes = [_vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp,
                                           _vp, _vp, _i64, _vp, _f32, _i32, _i32, C.c_uint64, _vp,
                                           _vp, _vp]
@@ -439,6 +442,42 @@ def dgsm_attenuate_footprint(atlas, radii, lights, q_means, q_quats, q_scales, c
         FOOTPRINT_MODES[mode], int(n_samples), int(seed) & (2**64 - 1), _ptr(out), _ptr(T),
         _stream(stream)))
     return (out, T) if want_T else out
+
+
+def dgsm_attenuate_cube(atlas, radii, lights, q_means, colors, light_w=None, direct_frac=1.0, out=None,
+                        want_T=False, ctx: Context | None = None, stream=None):
+    """Receiver attenuation through a cube-map atlas [L][K][6F][F] (atlas_map = 1)."""
+    ctx = ctx or context(atlas.device.index)
+    dt = {torch.float32: 0, torch.float16: 1, torch.bfloat16: 2}[atlas.dtype]
+    _need(atlas, "atlas", atlas.dtype)
+    L, K, H, F = atlas.shape
+    if H != 6 * F:
+        raise ValueError("a cube atlas has H = 6 W")
+    _need(radii, "radii")
+    _need(lights, "lights", shape_last=3)
+    _need(q_means, "q_means", shape_last=3)
+    _need(colors, "colors", shape_last=3)
+    Q = q_means.shape[0]
+    if out is None:
+        out = torch.empty_like(colors)
+    T = torch.empty((Q, L), dtype=torch.float32, device=atlas.device) if want_T else None
+    ctx.check(_lib.dgsm_attenuate_cube(ctx.handle, _ptr(atlas), dt, L, F, _ptr(radii), K, _ptr(lights),
+                                       _ptr(q_means), _ptr(colors), Q, _ptr(light_w), float(direct_frac), _ptr(out),
+                                       _ptr(T), _stream(stream)))
+    return (out, T) if want_T else out
+
+
+def dgsm_sample_index_cube(points, light, F, radii, ctx: Context | None = None, stream=None):
+    """Integer decisions of the cube-map lookup: idx (n,5) int32 (cell row
+    (global), cell column, base row (global), base column, shell), frac (n,3)."""
+    ctx = ctx or context(points.device.index)
+    _need(points, "points", shape_last=3)
+    n = points.shape[0]
+    idx = torch.empty((n, 5), dtype=torch.int32, device=points.device)
+    frac = torch.empty((n, 3), dtype=torch.float32, device=points.device)
+    ctx.check(_lib.dgsm_sample_index_cube(ctx.handle, _ptr(points), n, _ptr(light), int(F), _ptr(radii),
+                                          radii.shape[0], _ptr(idx), _ptr(frac), _stream(stream)))
+    return idx, frac
 
 
 def dgsm_attenuate_dyn(atlas, radii, atlas_dyn, radii_dyn, lights, q_means, colors, light_w=None,

@@ -32,8 +32,10 @@ __device__ __forceinline__ float load_T<__nv_bfloat16>(const __nv_bfloat16 *p) {
 template <typename T>
 __device__ __forceinline__ float lookup(const T *__restrict__ A, int H, int W, int K,
                                         const SampleIndex &s, const float *rs, const float *inw) {
+    // rows clamped to the point's face (the whole atlas for the octahedral map)
     const int j0 = min(max(s.bj, 0), W - 1), j1 = min(max(s.bj + 1, 0), W - 1);
-    const int i0 = min(max(s.bi, 0), H - 1), i1 = min(max(s.bi + 1, 0), H - 1);
+    const int rlo = s.r0, rhi = s.r0 + s.hf - 1;
+    const int i0 = min(max(s.bi, rlo), rhi), i1 = min(max(s.bi + 1, rlo), rhi);
     int k0, k1;
     float wt;
     if (s.k < 0) { k0 = k1 = 0; wt = 0.0f; }
@@ -69,7 +71,7 @@ struct DynGeom {
     const float *radii;
 };
 
-template <typename T, bool SEP>
+template <typename T, bool SEP, bool CUBE = false>
 __global__ void __launch_bounds__(ATT_THREADS) attenuate_kernel(
     const T *__restrict__ atlas, const T *__restrict__ dyn, int L, int H, int W,
     const float *__restrict__ radii, int K, DynGeom dg, const float *__restrict__ lights,
@@ -118,7 +120,8 @@ __global__ void __launch_bounds__(ATT_THREADS) attenuate_kernel(
 #pragma unroll
             for (int u = 0; u < ATT_U; ++u) {
                 const float ox = ls[3 * l], oy = ls[3 * l + 1], oz = ls[3 * l + 2];
-                const SampleIndex s = sample_index_tab(px[u], py[u], pz[u], ox, oy, oz, H, W, rs, K, tab, st);
+                const SampleIndex s = CUBE ? sample_index_cube(px[u], py[u], pz[u], ox, oy, oz, W, rs, K, tab, st)
+                                           : sample_index_tab(px[u], py[u], pz[u], ox, oy, oz, H, W, rs, K, tab, st);
                 Tl[u] = 1.0f;
                 if (s.t != 0.0f) {
                     Tl[u] = lookup(atlas + l * lstride, H, W, K, s, rs, inw);
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(FP_THREADS) attenuate_fp_kernel(
 __global__ void sample_index_kernel(const float *__restrict__ pts, int64_t n,
                                     const float *__restrict__ light, int H, int W,
                                     const float *__restrict__ radii, int K,
-                                    int32_t *__restrict__ idx_out, float *__restrict__ frac_out) {
+                                    int32_t *__restrict__ idx_out, float *__restrict__ frac_out, int cube) {
     __shared__ float rs[256];
     __shared__ short tab[SHELL_BINS];
     for (int k = threadIdx.x; k < K; k += blockDim.x) rs[k] = radii[k];
@@ -296,8 +299,10 @@ __global__ void sample_index_kernel(const float *__restrict__ pts, int64_t n,
     const float ox = light[0], oy = light[1], oz = light[2];
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const SampleIndex s = sample_index_tab(pts[3 * q], pts[3 * q + 1], pts[3 * q + 2], ox, oy, oz,
-                                               H, W, rs, K, tab, st);
+        const SampleIndex s = cube ? sample_index_cube(pts[3 * q], pts[3 * q + 1], pts[3 * q + 2], ox, oy, oz, W,
+                                                       rs, K, tab, st)
+                                   : sample_index_tab(pts[3 * q], pts[3 * q + 1], pts[3 * q + 2], ox, oy, oz,
+                                                      H, W, rs, K, tab, st);
         idx_out[5 * q] = s.ci;
         idx_out[5 * q + 1] = s.cj;
         idx_out[5 * q + 2] = s.bi;
@@ -319,8 +324,11 @@ template <typename T>
 void launch_attenuate(int grid, cudaStream_t s, const void *atlas, const void *dyn, bool sep, int L,
                       int H, int W, const float *radii, int K, DynGeom dg, const float *lights,
                       const float *qm, const float *cin, int64_t Q, const float *lw, float wd,
-                      float *cout, float *Tout) {
-    if (sep)
+                      float *cout, float *Tout, bool cube) {
+    if (cube)
+        attenuate_kernel<T, false, true><<<grid, ATT_THREADS, 0, s>>>((const T *)atlas, nullptr, L, H, W,
+            radii, K, dg, lights, qm, cin, Q, lw, wd, cout, Tout);
+    else if (sep)
         attenuate_kernel<T, true><<<grid, ATT_THREADS, 0, s>>>((const T *)atlas, (const T *)dyn, L, H, W,
             radii, K, dg, lights, qm, cin, Q, lw, wd, cout, Tout);
     else
@@ -332,10 +340,14 @@ int attenuate_common(dgsm_ctx *ctx, const void *atlas, const void *atlas_dyn, in
                      int32_t L, int32_t H, int32_t W, const float *radii, int32_t K, bool sep,
                      DynGeom dg, const float *lights, const float *q_means,
                      const float *colors_in, int64_t n_q, const float *light_w,
-                     float direct_frac, float *colors_out, float *T_out, void *stream) {
+                     float direct_frac, float *colors_out, float *T_out, void *stream, bool cube = false) {
     if (n_q < 0) return fail(ctx, DGSM_ERR_INVALID_ARG, "n_q < 0");
     if (L < 1 || L > 64) return fail(ctx, DGSM_ERR_INVALID_ARG, "need 1..64 lights");
-    if (H < 1 || W < 1 || H > 4096 || W > 4096) return fail(ctx, DGSM_ERR_INVALID_ARG, "H, W must be in 1..4096");
+    if (cube) {
+        if (W < 1 || W > 4096 || H != 6 * W) return fail(ctx, DGSM_ERR_INVALID_ARG, "cube atlas: F in 1..4096");
+    } else if (H < 1 || W < 1 || H > 4096 || W > 4096) {
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "H, W must be in 1..4096");
+    }
     if (K < 1 || K > 256) return fail(ctx, DGSM_ERR_INVALID_ARG, "K must be in 1..256");
     if (sep && (dg.H < 1 || dg.W < 1 || dg.H > 4096 || dg.W > 4096 || dg.K < 1 || dg.K > 256 || !dg.radii))
         return fail(ctx, DGSM_ERR_INVALID_ARG, "dynamic atlas: H, W in 1..4096, K in 1..256, radii required");
@@ -352,15 +364,16 @@ int attenuate_common(dgsm_ctx *ctx, const void *atlas, const void *atlas_dyn, in
     switch (dtype) {
         case DGSM_F32:
             launch_attenuate<float>(grid, s, atlas, atlas_dyn, sep, L, H, W, radii, K, dg, lights, q_means,
-                                    colors_in, n_q, light_w, direct_frac, colors_out, T_out);
+                                    colors_in, n_q, light_w, direct_frac, colors_out, T_out, cube);
             break;
         case DGSM_F16:
             launch_attenuate<__half>(grid, s, atlas, atlas_dyn, sep, L, H, W, radii, K, dg, lights, q_means,
-                                     colors_in, n_q, light_w, direct_frac, colors_out, T_out);
+                                     colors_in, n_q, light_w, direct_frac, colors_out, T_out, cube);
             break;
         default:
             launch_attenuate<__nv_bfloat16>(grid, s, atlas, atlas_dyn, sep, L, H, W, radii, K, dg, lights,
-                                            q_means, colors_in, n_q, light_w, direct_frac, colors_out, T_out);
+                                            q_means, colors_in, n_q, light_w, direct_frac, colors_out, T_out,
+                                            cube);
     }
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "attenuate_kernel");
@@ -405,7 +418,7 @@ extern "C" int dgsm_sample_index(dgsm_ctx *ctx, const float *points, int64_t n, 
     if (n == 0) return DGSM_OK;
     const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8);
     sample_index_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(points, n, light, H, W, radii, K,
-                                                                 idx_out, frac_out);
+                                                                 idx_out, frac_out, 0);
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "sample_index_kernel");
 }
@@ -462,4 +475,30 @@ extern "C" int dgsm_attenuate_footprint(dgsm_ctx *ctx, const void *atlas, int32_
     if (e != cudaSuccess) return cuda_fail(ctx, e, "attenuate_fp: smem attribute");
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "attenuate_fp_kernel");
+}
+
+extern "C" int dgsm_attenuate_cube(dgsm_ctx *ctx, const void *atlas, int32_t dtype, int32_t L, int32_t F,
+                                   const float *radii, int32_t K, const float *lights, const float *q_means,
+                                   const float *colors_in, int64_t n_q, const float *light_w, float direct_frac,
+                                   float *colors_out, float *T_out, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    return attenuate_common(ctx, atlas, nullptr, dtype, L, 6 * F, F, radii, K, false, DynGeom{6 * F, F, K, radii},
+                            lights, q_means, colors_in, n_q, light_w, direct_frac, colors_out, T_out, stream, true);
+}
+
+extern "C" int dgsm_sample_index_cube(dgsm_ctx *ctx, const float *points, int64_t n, const float *light,
+                                      int32_t F, const float *radii, int32_t K, int32_t *idx_out, float *frac_out,
+                                      void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (n < 0 || F < 1 || F > 4096 || K < 1 || K > 256) return fail(ctx, DGSM_ERR_INVALID_ARG, "bad size");
+    if (n > 0 && (!points || !light || !radii || !idx_out || !frac_out))
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "null pointer");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    if (n == 0) return DGSM_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8);
+    sample_index_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(points, n, light, 6 * F, F, radii, K, idx_out,
+                                                                 frac_out, 1);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "sample_index_kernel");
 }

@@ -247,10 +247,70 @@ __device__ __forceinline__ uint32_t half_mask(const float4 *pl, const GAxes &g, 
     return m;
 }
 
+// The cone and planes of a texel-centre rectangle of a cube-map atlas
+// (F x F faces stacked in rows; see xdecode_cube).  Inside a face the decode
+// is a central projection of the face plane, so the largest angle from the
+// centre direction over the rectangle is at a corner, and atlas lines are
+// great circles.  A rectangle that spans two faces gets the whole sphere and
+// no planes.
+__device__ void rect_cone_cube(int i0, int i1, int j0, int j1, int F, float4 *out) {
+    const int f = i0 / F;
+    if ((i1 - 1) / F != f) {
+        out[0] = make_float4(0.0f, 0.0f, 1.0f, -1.0f);
+        out[1] = make_float4(0.0f, 1.0f, 0.0f, 0.0f);
+        return;
+    }
+    const float ua = xcentre(j0, F), ub = xcentre(j1 - 1, F);
+    const float va = xcentre(i0 - f * F, F), vb = xcentre(i1 - 1 - f * F, F);
+    const float uc = xmul(xadd(ua, ub), 0.5f), vc = xmul(xadd(va, vb), 0.5f);
+    const float3 c = xdecode_cube(f, uc, vc);
+    float cmin = 1.0f;
+    const float us[2] = {ua, ub}, vs[2] = {va, vb};
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const float3 d = xdecode_cube(f, us[b], vs[a]);
+            cmin = fminf(cmin, xdot(c.x, c.y, c.z, d.x, d.y, d.z));
+        }
+    if (cmin <= 0.0f) {
+        out[0] = make_float4(c.x, c.y, c.z, -1.0f);
+        out[1] = make_float4(0.0f, 1.0f, 0.0f, 0.0f);
+    } else {
+        out[0] = make_float4(c.x, c.y, c.z, cmin);
+        out[1] = make_float4(xsqrt(xsub(1.0f, xmul(cmin, cmin))), 0.0f, 0.0f, 0.0f);
+    }
+}
+
+__device__ void rect_planes_cube(int i0, int i1, int j0, int j1, int half, int F, float4 *out) {
+    const int f = i0 / F;
+    const float ua = xcentre(j0, F), ub = xcentre(j1 - 1, F);
+    const float va = xcentre(i0 - f * F, F), vb = xcentre(i1 - 1 - f * F, F);
+    const float hb = i1 - i0 > half ? 1.0f : 0.0f;
+    for (int q = 0; q < PLANE_F4; ++q) out[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    out[1].w = hb;
+    if (!(ua < ub && va < vb) || (i1 - 1) / F != f) return;
+    const float uc = xmul(xadd(ua, ub), 0.5f), vc = xmul(xadd(va, vb), 0.5f);
+    const float3 c = xdecode_cube(f, uc, vc);
+    const float3 d00 = xdecode_cube(f, ua, va), d01 = xdecode_cube(f, ub, va);
+    const float3 d10 = xdecode_cube(f, ua, vb), d11 = xdecode_cube(f, ub, vb);
+    const float3 top = xplane(d00, d01, c), bot = xplane(d10, d11, c);
+    const float3 left = xplane(d00, d10, c), right = xplane(d01, d11, c);
+    out[0] = make_float4(top.x, top.y, top.z, 1.0f);
+    out[1] = make_float4(bot.x, bot.y, bot.z, hb);
+    out[2] = make_float4(left.x, left.y, left.z, 0.0f);
+    out[3] = make_float4(right.x, right.y, right.z, 0.0f);
+    if (hb != 0.0f) {
+        const float vm = xsub(xdiv((float)(2 * (i0 + half - f * F)), (float)F), 1.0f);
+        const float3 mid = xplane(xdecode_cube(f, ua, vm), xdecode_cube(f, ub, vm), xdecode_cube(f, uc, va));
+        out[4] = make_float4(mid.x, mid.y, mid.z, 0.0f);
+    }
+}
+
 // cones: [0, n_tiles) tiles, then [n_tiles, n_tiles + n_super) super-tiles;
 // two float4 per cone; then the tiles' planes, PLANE_F4 float4 each.
 __global__ void rect_cones_kernel(int H, int W, int tile, int tx, int ty, int sx, int sy,
-                                  float4 *__restrict__ cones) {
+                                  float4 *__restrict__ cones, int map) {
     const int n_tiles = tx * ty, n_super = sx * sy;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n_tiles + n_super) return;
@@ -265,6 +325,13 @@ __global__ void rect_cones_kernel(int H, int W, int tile, int tx, int ty, int sx
         b = (idx - n_tiles) % sx;
     }
     const int i0 = a * edge, j0 = b * edge;
+    if (map == MAP_CUBE) {
+        rect_cone_cube(i0, min(i0 + edge, H), j0, min(j0 + edge, W), W, cones + 2 * idx);
+        if (idx < n_tiles)
+            rect_planes_cube(i0, min(i0 + edge, H), j0, min(j0 + edge, W), tile / 2, W,
+                             cones + 2 * (n_tiles + n_super) + PLANE_F4 * idx);
+        return;
+    }
     rect_cone(i0, min(i0 + edge, H), j0, min(j0 + edge, W), H, W, cones + 2 * idx);
     if (idx < n_tiles)
         rect_planes(i0, min(i0 + edge, H), j0, min(j0 + edge, W), tile / 2, H, W,
@@ -883,7 +950,7 @@ __global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_ke
     int tile, int tx, int n_tiles, int64_t N, int chunk, float *__restrict__ accum,
     unsigned int *__restrict__ done, OutT *__restrict__ atlas,
     unsigned long long *__restrict__ stats, const uint8_t *__restrict__ roi_mask,
-    const int *__restrict__ roi_k) {
+    const int *__restrict__ roi_k, int map) {
     // roi_mask, roi_k (or nullptr): texels [L][H][W] and shell range [kmin,
     // kmax] per light of a region of interest; T = 1 outside it
     extern __shared__ float4 smem4[];
@@ -930,11 +997,23 @@ __global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_ke
         for (int e = tid; e < K * nt; e += BT_THREADS) D[e] = 0.0f;
         for (int e = tid; e < nt; e += BT_THREADS) {
             const int i = tile_i * tile + e / tile, j = tile_j * tile + e % tile;
-            const float u = (2.0f * j + 1.0f) / W - 1.0f, v = (2.0f * i + 1.0f) / H - 1.0f;
-            float z = 1.0f - fabsf(u) - fabsf(v), x = u, y = v;
-            if (z < 0.0f) {
-                x = (u >= 0.f ? 1.f : -1.f) * (1.0f - fabsf(v));
-                y = (v >= 0.f ? 1.f : -1.f) * (1.0f - fabsf(u));
+            float x, y, z;
+            if (map == MAP_CUBE) {
+                const int f = min(i / W, 5);
+                const float u = (2.0f * j + 1.0f) / W - 1.0f, v = (2.0f * (i - f * W) + 1.0f) / W - 1.0f;
+                int aF, aU, aV;
+                float sF, sU, sV;
+                cube_axes(f, aF, aU, aV, sF, sU, sV);
+                x = aF == 0 ? sF : aU == 0 ? sU * u : sV * v;
+                y = aF == 1 ? sF : aU == 1 ? sU * u : sV * v;
+                z = aF == 2 ? sF : aU == 2 ? sU * u : sV * v;
+            } else {
+                const float u = (2.0f * j + 1.0f) / W - 1.0f, v = (2.0f * i + 1.0f) / H - 1.0f;
+                z = 1.0f - fabsf(u) - fabsf(v), x = u, y = v;
+                if (z < 0.0f) {
+                    x = (u >= 0.f ? 1.f : -1.f) * (1.0f - fabsf(v));
+                    y = (v >= 0.f ? 1.f : -1.f) * (1.0f - fabsf(u));
+                }
             }
             const float inv = rsqrtf(x * x + y * y + z * z);
             tdir[e] = make_float4(x * inv, y * inv, z * inv, (i < H && j < W) ? 1.0f : 0.0f);
@@ -1107,7 +1186,7 @@ int launch_build_items(dgsm_ctx *ctx, const BuildRec *brec, const uint32_t *vals
                        const unsigned long long *n_items, unsigned int *counter, const float *radii,
                        int K, int H, int W, int tile, int tx, int n_tiles, int64_t N, int chunk,
                        float *accum, unsigned int *done, void *atlas, cudaStream_t s,
-                       const uint8_t *roi_mask, const int *roi_k) {
+                       const uint8_t *roi_mask, const int *roi_k, int map) {
     const size_t smem = build_smem_bytes(K, tile, chunk);
     cudaError_t e = cudaFuncSetAttribute(build_items_kernel<OutT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1118,7 +1197,7 @@ int launch_build_items(dgsm_ctx *ctx, const BuildRec *brec, const uint32_t *vals
     const int grid = std::max(1, per_sm) * ctx->num_sms;
     build_items_kernel<OutT><<<grid, BT_THREADS, smem, s>>>(
         reinterpret_cast<const float4 *>(brec), vals, items, n_items, counter, radii, K, H, W, tile,
-        tx, n_tiles, N, chunk, accum, done, (OutT *)atlas, ctx->d_stats, roi_mask, roi_k);
+        tx, n_tiles, N, chunk, accum, done, (OutT *)atlas, ctx->d_stats, roi_mask, roi_k, map);
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "build_items_kernel");
 }
@@ -1153,6 +1232,9 @@ int check_common(dgsm_ctx *ctx, const float *means, const float *scales, const f
     if (p.chunk < 16 || p.chunk > 128) return fail(ctx, DGSM_ERR_INVALID_ARG, "chunk must be in 16..128");
     if (!(p.kappa >= 0.f) || !(p.eps_cull > 0.f)) return fail(ctx, DGSM_ERR_INVALID_ARG, "kappa >= 0 and eps_cull > 0 required");
     if (p.beta_mode < 1 || p.beta_mode > 4) return fail(ctx, DGSM_ERR_INVALID_ARG, "beta_mode must be 1..4");
+    if (p.atlas_map != MAP_OCTA && p.atlas_map != MAP_CUBE) return fail(ctx, DGSM_ERR_INVALID_ARG, "atlas_map must be 0 or 1");
+    if (p.atlas_map == MAP_CUBE && (H != 6 * W || W % p.tile != 0 || W > 4096))
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "cube atlas: H = 6 F, F a multiple of the tile, F <= 4096");
     return DGSM_OK;
 }
 
@@ -1222,7 +1304,8 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
 
     // ---- per (light, Gaussian) records, level A: super-tiles ----
     const int nc = n_tiles + n_super;
-    rect_cones_kernel<<<(nc + 127) / 128, 128, 0, s>>>(H, W, tile, tx, ty, sx, sy, (float4 *)w_cones);
+    rect_cones_kernel<<<(nc + 127) / 128, 128, 0, s>>>(H, W, tile, tx, ty, sx, sy, (float4 *)w_cones,
+                                                        p.atlas_map);
     const int grid = (int)std::min<int64_t>((LN + 255) / 256, (int64_t)ctx->num_sms * 16);
     prep_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, N, lights, L, radii, K, p.kappa,
                                      p.eps_cull, build_records ? (BuildRec *)w_br : nullptr,
@@ -1396,20 +1479,20 @@ int build_impl(dgsm_ctx *ctx, const float *means, const float *scales, const flo
             rc = launch_build_items<float>(ctx, b.brec, vals, items, n_items_dev, counter, radii, K,
                                            H, W, p.tile, b.tx, b.n_tiles, n, p.chunk,
                                            (float *)w_acc, (unsigned *)w_done, atlas, s,
-                                           roi ? roi->mask : nullptr, roi ? roi->krange : nullptr);
+                                           roi ? roi->mask : nullptr, roi ? roi->krange : nullptr, p.atlas_map);
             break;
         case DGSM_F16:
             rc = launch_build_items<__half>(ctx, b.brec, vals, items, n_items_dev, counter, radii,
                                             K, H, W, p.tile, b.tx, b.n_tiles, n, p.chunk,
                                             (float *)w_acc, (unsigned *)w_done, atlas, s,
-                                            roi ? roi->mask : nullptr, roi ? roi->krange : nullptr);
+                                            roi ? roi->mask : nullptr, roi ? roi->krange : nullptr, p.atlas_map);
             break;
         default:
             rc = launch_build_items<__nv_bfloat16>(ctx, b.brec, vals, items, n_items_dev, counter,
                                                    radii, K, H, W, p.tile, b.tx, b.n_tiles, n,
                                                    p.chunk, (float *)w_acc, (unsigned *)w_done,
                                                    atlas, s, roi ? roi->mask : nullptr,
-                                                   roi ? roi->krange : nullptr);
+                                                   roi ? roi->krange : nullptr, p.atlas_map);
     }
     if (rc) return rc;
     if (prof) {
@@ -1438,7 +1521,7 @@ __global__ void roi_init_kernel(int *__restrict__ krange, int L, int K) {
 __global__ void __launch_bounds__(256) roi_mark_kernel(
     const float *__restrict__ recv, int64_t n, const float *__restrict__ box,
     const float *__restrict__ lights, int L, int H, int W, const float *__restrict__ radii, int K,
-    uint8_t *__restrict__ mask, int *__restrict__ krange) {
+    uint8_t *__restrict__ mask, int *__restrict__ krange, int map) {
     __shared__ int skmin[64], skmax[64];
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
         skmin[l] = K;
@@ -1452,11 +1535,15 @@ __global__ void __launch_bounds__(256) roi_mark_kernel(
         const float x = recv[3 * q], y = recv[3 * q + 1], z = recv[3 * q + 2];
         if (!(fabsf(xsub(x, cx)) <= R && fabsf(xsub(y, cy)) <= R && z >= z0 && z <= z1)) continue;
         for (int l = 0; l < L; ++l) {
-            const SampleIndex si = sample_index(x, y, z, lights[3 * l], lights[3 * l + 1], lights[3 * l + 2],
-                                                H, W, radii, K);
+            const SampleIndex si =
+                map == MAP_CUBE ? sample_index_cube(x, y, z, lights[3 * l], lights[3 * l + 1], lights[3 * l + 2], W,
+                                                    radii, K, nullptr, ShellTab{})
+                                : sample_index(x, y, z, lights[3 * l], lights[3 * l + 1], lights[3 * l + 2], H, W,
+                                               radii, K);
             if (si.t == 0.0f) continue;  // at the light: T = 1 without a lookup
             const int j0 = min(max(si.bj, 0), W - 1), j1 = min(max(si.bj + 1, 0), W - 1);
-            const int i0 = min(max(si.bi, 0), H - 1), i1 = min(max(si.bi + 1, 0), H - 1);
+            const int rlo = si.r0, rhi = si.r0 + si.hf - 1;
+            const int i0 = min(max(si.bi, rlo), rhi), i1 = min(max(si.bi + 1, rlo), rhi);
             uint8_t *m = mask + l * HW;
             m[(int64_t)i0 * W + j0] = 1;
             m[(int64_t)i0 * W + j1] = 1;
@@ -1562,7 +1649,7 @@ extern "C" int dgsm_build_roi(dgsm_ctx *ctx, const float *means, const float *sc
     if (roi->n_recv > 0) {
         const int grid = (int)std::min<int64_t>((roi->n_recv + 255) / 256, (int64_t)ctx->num_sms * 8);
         roi_mark_kernel<<<grid, 256, 0, s>>>(roi->recv_means, roi->n_recv, roi->box, lights, L, H, W, radii,
-                                             K, mask, krange);
+                                             K, mask, krange, p.atlas_map);
     }
     roi_tiles_kernel<<<(int)((L * n_tiles + 255) / 256), 256, 0, s>>>(mask, L, H, W, p.tile, tx, (int)n_tiles,
                                                                        tact);

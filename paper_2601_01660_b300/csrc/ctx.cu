@@ -66,6 +66,7 @@ extern "C" void dgsm_default_params(dgsm_params *p) {
     p->atlas_dtype = DGSM_F32;
     p->max_pairs = 0;
     p->beta_mode = 2;
+    p->atlas_map = 0;
 }
 
 extern "C" void dgsm_default_relight_params(dgsm_relight_params *p) {

@@ -153,10 +153,64 @@ __device__ __forceinline__ float2 xencode(float vx, float vy, float vz) {
                        xmul(sgn_pos(qy), xsub(1.0f, fabsf(qx))));
 }
 
+// Cube-map atlas (the alternative parameterisation of the paper's ablation
+// (C)): six F x F faces stacked as rows [f F, (f+1) F) of an atlas with
+// H = 6F, W = F.  Face f has forward axis F_f and texel axes U_f (columns,
+// u) and V_f (rows, v) as signed unit axes; texel (u, v) looks along
+// F_f + u U_f + v V_f: (+x, -z, -y), (-x, +z, -y), (+y, +x, +z), (-y, +x, -z),
+// (+z, +x, -y), (-z, -x, -y) (the usual cube-map faces).
+enum { MAP_OCTA = 0, MAP_CUBE = 1 };
+
+__device__ __forceinline__ void cube_axes(int f, int &aF, int &aU, int &aV, float &sF, float &sU, float &sV) {
+    switch (f) {
+        case 0: aF = 0; aU = 2; aV = 1; sF = 1.f; sU = -1.f; sV = -1.f; break;
+        case 1: aF = 0; aU = 2; aV = 1; sF = -1.f; sU = 1.f; sV = -1.f; break;
+        case 2: aF = 1; aU = 0; aV = 2; sF = 1.f; sU = 1.f; sV = 1.f; break;
+        case 3: aF = 1; aU = 0; aV = 2; sF = -1.f; sU = 1.f; sV = -1.f; break;
+        case 4: aF = 2; aU = 0; aV = 1; sF = 1.f; sU = 1.f; sV = -1.f; break;
+        default: aF = 2; aU = 0; aV = 1; sF = -1.f; sU = -1.f; sV = -1.f; break;
+    }
+}
+
+__device__ __forceinline__ float pick3(float x, float y, float z, int a) { return a == 0 ? x : a == 1 ? y : z; }
+
+// Unit direction of the point (u, v) of cube face f.
+__device__ __forceinline__ float3 xdecode_cube(int f, float u, float v) {
+    int aF, aU, aV;
+    float sF, sU, sV;
+    cube_axes(f, aF, aU, aV, sF, sU, sV);
+    const float cF = sF, cU = sU * u, cV = sV * v;  // sign flips: exact
+    const float x = aF == 0 ? cF : aU == 0 ? cU : cV;
+    const float y = aF == 1 ? cF : aU == 1 ? cU : cV;
+    const float z = aF == 2 ? cF : aU == 2 ? cU : cV;
+    const float n = xsqrt(xadd(xadd(xmul(x, x), xmul(y, y)), xmul(z, z)));
+    return make_float3(xdiv(x, n), xdiv(y, n), xdiv(z, n));
+}
+
+// Cube encode of the un-normalised vector v: the face of the largest
+// component (ties go to x, then y; a component >= 0 picks the positive face)
+// and the face coordinates u = U.v / m, v = V.v / m, m that component's size.
+__device__ __forceinline__ int xencode_cube(float vx, float vy, float vz, float &u, float &v) {
+    const float ax = fabsf(vx), ay = fabsf(vy), az = fabsf(vz);
+    const int f = (ax >= ay && ax >= az) ? (vx >= 0.0f ? 0 : 1) : (ay >= az ? (vy >= 0.0f ? 2 : 3) : (vz >= 0.0f ? 4 : 5));
+    int aF, aU, aV;
+    float sF, sU, sV;
+    cube_axes(f, aF, aU, aV, sF, sU, sV);
+    const float m = fabsf(pick3(vx, vy, vz, aF));
+    if (m == 0.0f) {
+        u = v = 0.0f;
+        return f;
+    }
+    u = xdiv(sU * pick3(vx, vy, vz, aU), m);
+    v = xdiv(sV * pick3(vx, vy, vz, aV), m);
+    return f;
+}
+
 // Index decisions of one lookup (shared by attenuate and sample_index).
 struct SampleIndex {
     int ci, cj;    // texel cell containing the point
     int bi, bj;    // bilinear base tap (may be -1 or H-1/W-1 before clamping)
+    int r0, hf;    // rows of the point's face: [r0, r0 + hf) (0, H for the octahedral map)
     int k;         // #{radii <= t} - 1
     float fy, fx;  // bilinear fractions
     float t;       // distance to the light
@@ -228,6 +282,8 @@ __device__ __forceinline__ SampleIndex sample_index_tab(float px, float py, floa
     s.bi = (int)bi;
     s.fx = xsub(gx, bj);
     s.fy = xsub(gy, bi);
+    s.r0 = 0;
+    s.hf = H;
     s.k = shell_index(s.t, radii, K, tab, st);
     return s;
 }
@@ -249,7 +305,37 @@ __device__ __forceinline__ SampleIndex sample_index(float px, float py, float pz
     s.bi = (int)bi;
     s.fx = xsub(gx, bj);
     s.fy = xsub(gy, bi);
+    s.r0 = 0;
+    s.hf = H;
     s.k = count_le(radii, K, s.t) - 1;
+    return s;
+}
+
+// The same decisions on a cube-map atlas of F x F faces (H = 6F, W = F):
+// rows are global (face f's rows start at f F); the bilinear taps are
+// clamped to the point's face.  tab (or nullptr: a comparison count) as for
+// sample_index_tab.
+__device__ __forceinline__ SampleIndex sample_index_cube(float px, float py, float pz, float ox, float oy,
+                                                         float oz, int F, const float *radii, int K,
+                                                         const short *tab, ShellTab st) {
+    SampleIndex s;
+    float vx = xsub(px, ox), vy = xsub(py, oy), vz = xsub(pz, oz);
+    s.t = xsqrt(xadd(xadd(xmul(vx, vx), xmul(vy, vy)), xmul(vz, vz)));
+    float u, v;
+    const int f = xencode_cube(vx, vy, vz, u, v);
+    float fu = xmul(xmul(xadd(u, 1.0f), 0.5f), (float)F);
+    float fv = xmul(xmul(xadd(v, 1.0f), 0.5f), (float)F);
+    float gx = xsub(fu, 0.5f), gy = xsub(fv, 0.5f);
+    float bj = floorf(gx), bi = floorf(gy);
+    s.r0 = f * F;
+    s.hf = F;
+    s.cj = min(max((int)floorf(fu), 0), F - 1);
+    s.ci = s.r0 + min(max((int)floorf(fv), 0), F - 1);
+    s.bj = (int)bj;
+    s.bi = s.r0 + (int)bi;
+    s.fx = xsub(gx, bj);
+    s.fy = xsub(gy, bi);
+    s.k = tab ? shell_index(s.t, radii, K, tab, st) : count_le(radii, K, s.t) - 1;
     return s;
 }
 

@@ -566,7 +566,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["room1p6m", "room550k"], default=WORKLOAD,
                     help="room550k: the same room at a third of the size (profiler captures)")
-    ap.add_argument("--cpu-texels", type=int, default=32)
+    ap.add_argument("--cpu-texels", type=int, default=72)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--report", choices=["precision", "surrogate", "frame", "field"],

@@ -315,6 +315,7 @@ def run_ours(args, rank, world, local_rank):
     if line["ms_per_build"]:
         roi_build["speedup_vs_dense"] = round(line["ms_per_build"] / roi_build["ms"], 3)
     line["roi_build"] = roi_build
+    line["pca_normals"] = time_pca_normals(nat, means, quats, scales, opac, a0, a1, flush, stream)
     line["gpu_launches"] = count_launches(args, L)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, evals, args.cpu_texels)
@@ -322,6 +323,32 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def time_pca_normals(nat, means, quats, scales, opac, a0, a1, flush, stream, radius=0.05):
+    """Local-PCA pseudo-normals (Sec. 4) of the avatar (its own Gaussians as
+    neighbours, oriented away from its centroid) and of the whole room, r =
+    5 cm; L2 flushed before each timed call."""
+    import torch
+    out = {"radius_m": radius}
+    cen = nat.dgsm_weighted_centroid(means[a0:a1], opac[a0:a1])
+    for name, sl in (("avatar", slice(a0, a1)), ("room", slice(0, means.shape[0]))):
+        m, q, s, o = means[sl], quats[sl], scales[sl], opac[sl]
+        res = torch.empty_like(m)
+        ms = []
+        for k in range(5):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            nat.dgsm_pca_normals(m, o, q, s, cen, radius=radius, out=res)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= 2:
+                ms.append(e0.elapsed_time(e1))
+        t = statistics.mean(ms)
+        out[name] = {"gaussians": int(m.shape[0]), "ms": round(t, 4),
+                     "gaussians_per_s": m.shape[0] / (t * 1e-3)}
+    return out
 
 
 def time_probe(nat, sc, means, scales, quats, opac, colors, a0, a1, flush, stream, final):

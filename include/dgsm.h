@@ -414,6 +414,22 @@ int sh_relight(dgsm_ctx *ctx, const float *sh, const float *means, const float *
                const float *colors_in, int64_t n, const dgsm_relight_params *params,
                float *colors_out, void *stream);
 
+/* Pseudo-normals by local PCA (Sec. 4, lighting consistency: an alpha- and
+ * distance-weighted PCA of the nearby Gaussian centres), for sh_relight's
+ * `normals`.  For Gaussian i: the Gaussians j (i included) with
+ * |x_j - x_i| <= radius, weighted w_j = opac_j (1 - |x_j - x_i|^2 / radius^2)^2;
+ * the unit eigenvector of the smallest eigenvalue of their weighted
+ * covariance; the smallest-scale axis of the Gaussian (first on ties) when
+ * fewer than three neighbours carry weight or the covariance vanishes.  The
+ * normal is flipped when n . (x_i - centroid) < 0.  means (n,3), opac (n),
+ * quats (n,4; 16-byte aligned), scales (n,3), centroid (3), normals_out
+ * (n,3): device.  0 <= n < 2^31, radius > 0 and finite.  Neighbours are found
+ * through a spatial hash of cells of edge `radius` (workspace: about
+ * 32 n + 16 max(2n, 1024) bytes).  Asynchronous. */
+int dgsm_pca_normals(dgsm_ctx *ctx, const float *means, const float *opac, const float *quats,
+                     const float *scales, int64_t n, float radius, const float *centroid,
+                     float *normals_out, void *stream);
+
 /* sh_relight for a Gaussian array made of n_obj contiguous objects (for
  * instance avatars): object o holds Gaussians [seg[o], seg[o+1]) and its
  * normals are turned away from centroids[o] (device, n_obj x 3 floats; see

@@ -62,29 +62,31 @@ def weighted_moments(means, opac, i, radius):
     return W, m, C, cnt
 
 
-def pca_normals(means, opac, quats, scales, radius, centroid, want_info=False):
+def pca_normals(means, opac, quats, scales, radius, centroid, want_info=False, idx=None):
     """Pseudo-normals (n, 3) FP64; with want_info also per Gaussian the
     eigenvalues of C in ascending order (n, 3) and whether the smallest-axis
-    fallback was taken (n,)."""
+    fallback was taken (n,).  idx: only these Gaussians (rows in idx order),
+    their neighbourhoods still taken from all of them."""
     if not float(radius) > 0:
         raise ValueError("radius must be > 0")
     x = np.asarray(means, dtype=np.float64)
-    n = x.shape[0]
+    rows = np.arange(x.shape[0]) if idx is None else np.asarray(idx)
+    n = rows.shape[0]
     c = np.asarray(centroid, dtype=np.float64)
     out = np.zeros((n, 3))
     lam = np.zeros((n, 3))
     fb = np.zeros(n, dtype=bool)
-    for i in range(n):
+    for r_, i in enumerate(rows):
         W, m, C, cnt = weighted_moments(x, opac, i, radius)
         if cnt < 3 or not np.trace(C) > 0:
             v = _smallest_axis(quats[i], scales[i])
-            fb[i] = True
+            fb[r_] = True
         else:
             ev, V = np.linalg.eigh(C)   # ascending eigenvalues
-            lam[i] = ev
+            lam[r_] = ev
             v = V[:, 0]
         v = v / np.linalg.norm(v)
         if np.dot(v, x[i] - c) < 0:
             v = -v
-        out[i] = v
+        out[r_] = v
     return (out, lam, fb) if want_info else out

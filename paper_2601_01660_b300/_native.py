@@ -103,6 +103,7 @@ _lib.dgsm_get_build_stats.argtypes = [_vp, C.POINTER(BuildStats)]
 _lib.dgsm_build_roi.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i32,
                                 C.POINTER(Params), C.POINTER(Roi), _vp, _vp]
 _lib.dgsm_roi_box.argtypes = [_vp, _vp, _vp, _i64, _f32, _f32, _vp, _vp]
+_lib.dgsm_pca_normals.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _f32, _vp, _vp, _vp]
 _lib.dgsm_bin.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i32,
                           C.POINTER(Params), _vp, _vp, _i64, C.POINTER(_i64), _vp]
 _lib.dgsm_attenuate.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp,
@@ -329,6 +330,25 @@ def dgsm_roi_box(avatar_means, avatar_opac, R=2.0, z_margin=0.1, out=None,
         out = torch.empty(5, dtype=torch.float32, device=avatar_means.device)
     ctx.check(_lib.dgsm_roi_box(ctx.handle, _ptr(avatar_means), _ptr(avatar_opac), avatar_means.shape[0],
                                 float(R), float(z_margin), _ptr(out), _stream(stream)))
+    return out
+
+
+def dgsm_pca_normals(means, opac, quats, scales, centroid, radius=0.05, out=None,
+                     ctx: Context | None = None, stream=None):
+    """Pseudo-normals (n, 3) by alpha- and distance-weighted local PCA of the
+    Gaussian centres within `radius` (Sec. 4), the smallest-scale axis where
+    the neighbourhood is too sparse; turned away from `centroid` (device, 3)."""
+    ctx = ctx or context(means.device.index)
+    _need(means, "means", shape_last=3)
+    _need(opac, "opac")
+    _need(quats, "quats", shape_last=4)
+    _need(scales, "scales", shape_last=3)
+    _need(centroid, "centroid")
+    n = means.shape[0]
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float32, device=means.device)
+    ctx.check(_lib.dgsm_pca_normals(ctx.handle, _ptr(means), _ptr(opac), _ptr(quats), _ptr(scales), n,
+                                    float(radius), _ptr(centroid), _ptr(out), _stream(stream)))
     return out
 
 

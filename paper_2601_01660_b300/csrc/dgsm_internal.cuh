@@ -39,6 +39,7 @@ enum WsSlot {
     WS_CAMS,           // the six probe cameras of dgsm_render_cubemap
     WS_SEGS,           // splat render: per-tile segment counts and offsets, the segments
     WS_PART,           // splat render: per-segment partial colour and transmittance of each pixel
+    WS_NORMALS,        // pca normals: bucket keys and order, bucket ranges, sorted points
     WS_NSLOTS
 };
 

@@ -542,29 +542,60 @@ static void f32_decode_cube(int f, float u, float v, float *d) {
 }
 
 /* Cone of a rectangle of a cube-map atlas (faces of F = W texels stacked in
- * rows): axis the decoded rectangle centre, half-angle the largest angle to
- * its corners (within a face the decode is a central projection of the face
- * plane); a rectangle across two faces spans everything. */
+ * rows).  Its part on one face is a convex spherical quadrilateral (the
+ * decode is a central projection of the face plane), so a cap of half-angle
+ * below 90 degrees holds the part iff it holds its four corners.  Axis: the
+ * decoded centre of a rectangle on one face; the normalised sum of the
+ * decoded centres of its parts for one across faces.  Half-angle: the
+ * largest angle to a corner of any part. */
 static void f32_rect_cone_cube(int i0, int i1, int j0, int j1, int F, float *cone) {
-    int f = i0 / F;
-    if ((i1 - 1) / F != f) {
-        cone[0] = 0.0f; cone[1] = 0.0f; cone[2] = 1.0f; cone[3] = -1.0f; cone[4] = 0.0f; cone[5] = 1.0f;
-        return;
-    }
+    int f0 = i0 / F, f1 = (i1 - 1) / F;
     float ua = f32_centre(j0, F), ub = f32_centre(j1 - 1, F);
-    float va = f32_centre(i0 - f * F, F), vb = f32_centre(i1 - 1 - f * F, F);
-    volatile float su = ua + ub, sv = va + vb;
-    volatile float uc = su * 0.5f, vc = sv * 0.5f;
+    volatile float su = ua + ub;
+    volatile float uc = su * 0.5f;
     float c[3];
-    f32_decode_cube(f, uc, vc, c);
-    float us[2] = {ua, ub}, vs[2] = {va, vb}, cmin = 1.0f;
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b) {
+    if (f0 == f1) {
+        float va = f32_centre(i0 - f0 * F, F), vb = f32_centre(i1 - 1 - f0 * F, F);
+        volatile float sv = va + vb;
+        volatile float vc = sv * 0.5f;
+        f32_decode_cube(f0, uc, vc, c);
+    } else {
+        volatile float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+        for (int f = f0; f <= f1; ++f) {
+            int r0 = (i0 > f * F ? i0 : f * F) - f * F;
+            int r1 = (i1 < (f + 1) * F ? i1 : (f + 1) * F) - 1 - f * F;
+            float va = f32_centre(r0, F), vb = f32_centre(r1, F);
+            volatile float sv = va + vb;
+            volatile float vc = sv * 0.5f;
             float d[3];
-            f32_decode_cube(f, us[b], vs[a], d);
-            float cs = f32_dot(c, d);
-            if (cs < cmin) cmin = cs;
+            f32_decode_cube(f, uc, vc, d);
+            sx = sx + d[0];
+            sy = sy + d[1];
+            sz = sz + d[2];
         }
+        volatile float xx = sx * sx, yy = sy * sy, zz = sz * sz;
+        volatile float n2 = (xx + yy) + zz;
+        float n = sqrtf(n2);
+        if (!(n > 0.0f)) {
+            cone[0] = 0.0f; cone[1] = 0.0f; cone[2] = 1.0f; cone[3] = -1.0f; cone[4] = 0.0f; cone[5] = 1.0f;
+            return;
+        }
+        volatile float cx = sx / n, cy = sy / n, cz = sz / n;
+        c[0] = cx; c[1] = cy; c[2] = cz;
+    }
+    float us[2] = {ua, ub}, cmin = 1.0f;
+    for (int f = f0; f <= f1; ++f) {
+        int r0 = (i0 > f * F ? i0 : f * F) - f * F;
+        int r1 = (i1 < (f + 1) * F ? i1 : (f + 1) * F) - 1 - f * F;
+        float vs[2] = {f32_centre(r0, F), f32_centre(r1, F)};
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                float d[3];
+                f32_decode_cube(f, us[b], vs[a], d);
+                float cs = f32_dot(c, d);
+                if (cs < cmin) cmin = cs;
+            }
+    }
     cone[0] = c[0]; cone[1] = c[1]; cone[2] = c[2];
     if (cmin <= 0.0f) {
         cone[3] = -1.0f; cone[4] = 0.0f; cone[5] = 1.0f;
@@ -875,7 +906,9 @@ static unsigned f32_half_mask(const float *pl, const float *ax, float k2s, int i
 }
 
 /* Light-space tile binning (Sec. 3.2, occluder culling), FP32 specification:
- * tiles of tile x tile texels, super-tiles of 8x8 tiles; a Gaussian enters a
+ * tiles of tile x tile texels, super-tiles of 8x8 tiles (on a cube map a
+ * super-tile across two faces has one cone per face part, and overlapping
+ * either counts); a Gaussian enters a
  * tile's list iff its bounding cone overlaps the super-tile's cone and the
  * tile's cone, and its culling ellipsoid reaches the tile's half-tile cones
  * (f32_half_mask; every Gaussian when the light is inside its bounding
@@ -892,7 +925,9 @@ int64_t orc_f32_bin(const float *means, const float *scales, const float *quats,
     int n_tiles = ty * tx;
     float *tc = (float *)malloc(sizeof(float) * 6 * n_tiles);
     float *tp = (float *)malloc(sizeof(float) * 17 * n_tiles);
-    float *sc = (float *)malloc(sizeof(float) * 6 * sy * sx);
+    /* per super-tile: its cone, a second cone and a flag (1 when the
+     * super-tile lies across two cube faces: one cone per face part) */
+    float *sc = (float *)malloc(sizeof(float) * 13 * sy * sx);
     for (int a = 0; a < ty; ++a)
         for (int b = 0; b < tx; ++b) {
             int i0 = a * tile, j0 = b * tile;
@@ -904,7 +939,16 @@ int64_t orc_f32_bin(const float *means, const float *scales, const float *quats,
         for (int b = 0; b < sx; ++b) {
             int i0 = a * 8 * tile, j0 = b * 8 * tile;
             int i1 = i0 + 8 * tile < H ? i0 + 8 * tile : H, j1 = j0 + 8 * tile < W ? j0 + 8 * tile : W;
-            orc_f32_rect_cone(i0, i1, j0, j1, H, W, sc + 6 * (a * sx + b));
+            float *sup = sc + 13 * (a * sx + b);
+            sup[12] = 0.0f;
+            if (g_atlas_map == 1 && (i1 - 1) / W == i0 / W + 1) {
+                int cut = ((i1 - 1) / W) * W;
+                orc_f32_rect_cone(i0, cut, j0, j1, H, W, sup);
+                orc_f32_rect_cone(cut, i1, j0, j1, H, W, sup + 6);
+                sup[12] = 1.0f;
+            } else {
+                orc_f32_rect_cone(i0, i1, j0, j1, H, W, sup);
+            }
         }
     /* per tile: collect in Gaussian order (the natural (key, value) order) */
     int64_t total = 0;
@@ -929,10 +973,11 @@ int64_t orc_f32_bin(const float *means, const float *scales, const float *quats,
         }
         for (int t = 0; t < n_tiles; ++t) {
             int a = t / tx, b = t % tx;
-            const float *sup = sc + 6 * ((a / 8) * sx + (b / 8));
+            const float *sup = sc + 13 * ((a / 8) * sx + (b / 8));
             for (int64_t n = 0; n < N; ++n) {
                 if (!ok[n]) continue;
-                if (!f32_overlap(cones + 9 * n, sup)) continue;
+                if (!f32_overlap(cones + 9 * n, sup) && !(sup[12] != 0.0f && f32_overlap(cones + 9 * n, sup + 6)))
+                    continue;
                 if (!f32_overlap(cones + 9 * n, tc + 6 * t)) continue;
                 unsigned m = f32_half_mask(tp + 17 * t, axes + 12 * n, k2s[n], cones[9 * n + 5] != 0.0f);
                 if (!m) continue;

@@ -137,21 +137,30 @@ def test_build_calibration_along_a_texel_ray(orc):
             assert T[1, opp, j] == 1.0
 
 
-@pytest.mark.parametrize("F,tile", [(16, 8), (20, 8), (32, 16), (12, 4)])
+@pytest.mark.parametrize("F,tile", [(16, 8), (20, 8), (32, 16), (12, 4), (208, 64), (40, 64)])
 def test_tile_cones_contain_their_texels(orc, F, tile):
+    """Every rectangle's cone holds its texel rays, also for rectangles across
+    two faces (super-tiles of 64 texels on faces of 208 or 40): their cone
+    covers both parts (the whole sphere when the two faces are opposite)."""
     H = 6 * F
+    across = 0
     with orc.atlas_map(1):
         for i0 in range(0, H, tile):
             for j0 in range(0, F, tile):
                 i1, j1 = min(i0 + tile, H), min(j0 + tile, F)
                 cone = orc.f32_rect_cone(i0, i1, j0, j1, H, F)
-                assert cone[5] == ((i1 - 1) // F != i0 // F)   # only a tile across two faces spans all
+                two = (i1 - 1) // F == i0 // F + 1
+                across += two
                 if cone[5]:
                     continue
                 c = cone[:3].astype(np.float64)
-                for i in range(i0, i1):
-                    for j in range(j0, j1):
+                for i in range(i0, i1, max(1, tile // 16)):
+                    for j in range(j0, j1, max(1, tile // 16)):
                         assert orc.texel_dir(i, j, H, F) @ c >= cone[3] - 1e-6
+                for i in (i0, i1 - 1):           # the corners always
+                    for j in (j0, j1 - 1):
+                        assert orc.texel_dir(i, j, H, F) @ c >= cone[3] - 1e-6
+    assert across > 0 or F % tile == 0
 
 
 def test_rect_planes_bound_their_texels(orc):
@@ -174,7 +183,7 @@ def test_rect_planes_bound_their_texels(orc):
         assert orc.f32_rect_planes(5, 6, 0, 8, 4, H, F)[15] == 0
 
 
-@pytest.mark.parametrize("F,tile", [(8, 8), (12, 8), (16, 16), (6, 4)])
+@pytest.mark.parametrize("F,tile", [(8, 8), (12, 8), (16, 16), (6, 4), (40, 8), (24, 4)])
 def test_binning_is_conservative(orc, F, tile):
     sc = _scene_with_flat_and_tiny(14)
     o = np.float32([0.1, -0.1, 0.2])

@@ -316,6 +316,8 @@ def run_ours(args, rank, world, local_rank):
         roi_build["speedup_vs_dense"] = round(line["ms_per_build"] / roi_build["ms"], 3)
     line["roi_build"] = roi_build
     line["pca_normals"] = time_pca_normals(nat, means, quats, scales, opac, a0, a1, flush, stream)
+    line["ablations"] = time_ablations(nat, (means, scales, quats, opac, colors), lights, radii, H, W,
+                                       atlas, flush, stream)
     line["gpu_launches"] = count_launches(args, L)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, evals, args.cpu_texels)
@@ -323,6 +325,66 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def time_ablations(nat, gauss, lights, radii, H, W, atlas, flush, stream, F=208):
+    """The ablation variants of Sec. 4 on the step's scene, each timed on its
+    own (5 calls, the last 3 averaged, L2 flushed before each):
+    (A) the 7-point stencil footprint (the 8-sample Monte Carlo one is in
+    the line's attenuate);
+    (B) the opacity-to-absorption mappings 1, 3 and 4 (the step builds with
+    mapping 2, Eq. 5): build time and the pairs each one evaluates;
+    (C) the cube-map atlas with about the octahedral atlas's texel count (six
+    208 x 208 faces = 259,584 texels against 512^2 = 262,144): build time,
+    attenuation through it, and how far its transmittances are from the
+    octahedral atlas's at the receivers."""
+    import torch
+    means, scales, quats, opac, colors = gauss
+
+    def timed(fn):
+        ms = []
+        for k in range(5):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= 2:
+                ms.append(e0.elapsed_time(e1))
+        return statistics.mean(ms)
+
+    def build(params, h, w, out):
+        nat.dgsm_set_profiling(True)
+        t = timed(lambda k: nat.dgsm_build(means, scales, quats, opac, lights, h, w, radii, params=params,
+                                           out=out))
+        prof = nat.dgsm_profile_collect()[2:]
+        nat.dgsm_set_profiling(False)
+        st = nat.dgsm_get_build_stats()
+        return {"ms": round(t, 4), "binning_ms": round(statistics.mean(p[0] for p in prof), 4),
+                "tile_kernel_ms": round(statistics.mean(p[1] for p in prof), 4),
+                "ray_evals": int(st["ray_evals"]), "evals_per_s": st["ray_evals"] / (t * 1e-3)}
+
+    out = torch.empty_like(colors)
+    res = {"footprint_stencil7_ms": round(timed(lambda k: nat.dgsm_attenuate_footprint(
+        atlas, radii, lights, means, quats, scales, colors, mode="stencil7", out=out)), 5)}
+    tmp = torch.empty_like(atlas)
+    res["beta_mode"] = {str(m): build({"beta_mode": m}, H, W, tmp) for m in (1, 3, 4)}
+    L, K = atlas.shape[0], atlas.shape[1]
+    cube = torch.empty((L, K, 6 * F, F), dtype=torch.float32, device=atlas.device)
+    c = build({"atlas_map": 1}, 6 * F, F, cube)
+    c.update({"face": F, "texels": 6 * F * F, "octahedral_texels": H * W})
+    c["attenuate_ms"] = round(timed(lambda k: nat.dgsm_attenuate_cube(cube, radii, lights, means, colors,
+                                                                      out=out)), 5)
+    nat.dgsm_build(means, scales, quats, opac, lights, H, W, radii, out=tmp)
+    _, To = nat.dgsm_attenuate(tmp, radii, lights, means, colors, want_T=True)
+    _, Tc = nat.dgsm_attenuate_cube(cube, radii, lights, means, colors, want_T=True)
+    dT = (To - Tc).abs().flatten()
+    c["T_vs_octahedral"] = {"mean_abs": round(dT.mean().item(), 6),
+                            "p99_abs": round(torch.quantile(dT[::max(1, dT.numel() // 1000000)].float(),
+                                                            0.99).item(), 6)}
+    res["cube_map"] = c
+    return res
 
 
 def time_pca_normals(nat, means, quats, scales, opac, a0, a1, flush, stream, radius=0.05):

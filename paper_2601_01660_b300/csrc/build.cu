@@ -249,30 +249,49 @@ __device__ __forceinline__ uint32_t half_mask(const float4 *pl, const GAxes &g, 
 
 // The cone and planes of a texel-centre rectangle of a cube-map atlas
 // (F x F faces stacked in rows; see xdecode_cube).  Inside a face the decode
-// is a central projection of the face plane, so the largest angle from the
-// centre direction over the rectangle is at a corner, and atlas lines are
-// great circles.  A rectangle that spans two faces gets the whole sphere and
-// no planes.
+// is a central projection of the face plane, so the rectangle's part on a
+// face is a convex spherical quadrilateral (great-circle edges), and a cap of
+// half-angle below 90 degrees (a convex set) holds it iff it holds its four
+// corners.  The axis is the decoded centre for a rectangle on one face, the
+// normalised sum of its parts' decoded centres for one across faces; the
+// half-angle reaches the farthest corner of any part.
 __device__ void rect_cone_cube(int i0, int i1, int j0, int j1, int F, float4 *out) {
-    const int f = i0 / F;
-    if ((i1 - 1) / F != f) {
-        out[0] = make_float4(0.0f, 0.0f, 1.0f, -1.0f);
-        out[1] = make_float4(0.0f, 1.0f, 0.0f, 0.0f);
-        return;
-    }
+    const int f0 = i0 / F, f1 = (i1 - 1) / F;
     const float ua = xcentre(j0, F), ub = xcentre(j1 - 1, F);
-    const float va = xcentre(i0 - f * F, F), vb = xcentre(i1 - 1 - f * F, F);
-    const float uc = xmul(xadd(ua, ub), 0.5f), vc = xmul(xadd(va, vb), 0.5f);
-    const float3 c = xdecode_cube(f, uc, vc);
-    float cmin = 1.0f;
-    const float us[2] = {ua, ub}, vs[2] = {va, vb};
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const float3 d = xdecode_cube(f, us[b], vs[a]);
-            cmin = fminf(cmin, xdot(c.x, c.y, c.z, d.x, d.y, d.z));
+    const float uc = xmul(xadd(ua, ub), 0.5f);
+    float3 c;
+    if (f0 == f1) {
+        const float va = xcentre(i0 - f0 * F, F), vb = xcentre(i1 - 1 - f0 * F, F);
+        c = xdecode_cube(f0, uc, xmul(xadd(va, vb), 0.5f));
+    } else {
+        float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+        for (int f = f0; f <= f1; ++f) {
+            const float va = xcentre(max(i0, f * F) - f * F, F), vb = xcentre(min(i1, (f + 1) * F) - 1 - f * F, F);
+            const float3 d = xdecode_cube(f, uc, xmul(xadd(va, vb), 0.5f));
+            sx = xadd(sx, d.x);
+            sy = xadd(sy, d.y);
+            sz = xadd(sz, d.z);
         }
+        const float n = xsqrt(xadd(xadd(xmul(sx, sx), xmul(sy, sy)), xmul(sz, sz)));
+        if (!(n > 0.0f)) {
+            out[0] = make_float4(0.0f, 0.0f, 1.0f, -1.0f);
+            out[1] = make_float4(0.0f, 1.0f, 0.0f, 0.0f);
+            return;
+        }
+        c = make_float3(xdiv(sx, n), xdiv(sy, n), xdiv(sz, n));
+    }
+    float cmin = 1.0f;
+    const float us[2] = {ua, ub};
+    for (int f = f0; f <= f1; ++f) {
+        const float vs[2] = {xcentre(max(i0, f * F) - f * F, F), xcentre(min(i1, (f + 1) * F) - 1 - f * F, F)};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const float3 d = xdecode_cube(f, us[b], vs[a]);
+                cmin = fminf(cmin, xdot(c.x, c.y, c.z, d.x, d.y, d.z));
+            }
+    }
     if (cmin <= 0.0f) {
         out[0] = make_float4(c.x, c.y, c.z, -1.0f);
         out[1] = make_float4(0.0f, 1.0f, 0.0f, 0.0f);
@@ -308,7 +327,11 @@ __device__ void rect_planes_cube(int i0, int i1, int j0, int j1, int half, int F
 }
 
 // cones: [0, n_tiles) tiles, then [n_tiles, n_tiles + n_super) super-tiles;
-// two float4 per cone; then the tiles' planes, PLANE_F4 float4 each.
+// two float4 per cone; then the tiles' planes, PLANE_F4 float4 each; then a
+// second cone per super-tile.  On a cube map a super-tile across two faces
+// (which lie anywhere on the sphere relative to each other: the faces are
+// stacked in atlas rows) gets one cone per face part, the first flagged in
+// its second float4's z; a Gaussian reaches it if it overlaps either.
 __global__ void rect_cones_kernel(int H, int W, int tile, int tx, int ty, int sx, int sy,
                                   float4 *__restrict__ cones, int map) {
     const int n_tiles = tx * ty, n_super = sx * sy;
@@ -325,8 +348,21 @@ __global__ void rect_cones_kernel(int H, int W, int tile, int tx, int ty, int sx
         b = (idx - n_tiles) % sx;
     }
     const int i0 = a * edge, j0 = b * edge;
+    float4 *second = idx >= n_tiles ? cones + 2 * (n_tiles + n_super) + PLANE_F4 * n_tiles + 2 * (idx - n_tiles)
+                                    : nullptr;
+    if (second) {
+        second[0] = make_float4(0.0f, 0.0f, 1.0f, 2.0f);  // unused unless flagged
+        second[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
     if (map == MAP_CUBE) {
-        rect_cone_cube(i0, min(i0 + edge, H), j0, min(j0 + edge, W), W, cones + 2 * idx);
+        const int i1 = min(i0 + edge, H), f0 = i0 / W, f1 = (i1 - 1) / W;
+        if (second && f1 == f0 + 1) {
+            rect_cone_cube(i0, f1 * W, j0, min(j0 + edge, W), W, cones + 2 * idx);
+            rect_cone_cube(f1 * W, i1, j0, min(j0 + edge, W), W, second);
+            cones[2 * idx + 1].z = 1.0f;
+            return;
+        }
+        rect_cone_cube(i0, i1, j0, min(j0 + edge, W), W, cones + 2 * idx);
         if (idx < n_tiles)
             rect_planes_cube(i0, min(i0 + edge, H), j0, min(j0 + edge, W), tile / 2, W,
                              cones + 2 * (n_tiles + n_super) + PLANE_F4 * idx);
@@ -491,6 +527,14 @@ __device__ __forceinline__ bool cone_overlap(const BinRec &g, const float4 *cone
     return cone_overlap_v(g, __ldg(cone), __ldg(cone + 1));
 }
 
+// Super-tile sidx: its cone, or either of its two cones when flagged.
+__device__ __forceinline__ bool super_overlap(const BinRec &g, const float4 *scones, const float4 *scones2,
+                                              int sidx) {
+    const float4 c0 = __ldg(scones + 2 * sidx), c1 = __ldg(scones + 2 * sidx + 1);
+    if (cone_overlap_v(g, c0, c1)) return true;
+    return c1.z != 0.0f && cone_overlap(g, scones2 + 2 * sidx);
+}
+
 // ---------------------------------------------------------------------------
 // Binning in two levels.  Pass A (Gaussian-major): each (light, Gaussian)
 // tests its bounding cone against the cones of the 8x8-tile super-tiles and
@@ -509,7 +553,7 @@ constexpr int TDAT_F4 = 2 + PLANE_F4;  // per tile: cone (2 float4) + planes
 template <bool EMIT>
 __global__ void __launch_bounds__(256) coarse_bin_kernel(
     const BinRec *__restrict__ bin, int64_t N, int L, int n_super, const float4 *__restrict__ scones,
-    uint32_t *__restrict__ counts, const uint32_t *__restrict__ offsets, uint32_t *__restrict__ ckeys,
+    const float4 *__restrict__ scones2, uint32_t *__restrict__ counts, const uint32_t *__restrict__ offsets, uint32_t *__restrict__ ckeys,
     uint32_t *__restrict__ cvals, const unsigned long long *__restrict__ keep, uint32_t cap,
     const uint8_t *__restrict__ sact) {
     // sact (or nullptr): per (light, super-tile) 1 if it holds a texel of the
@@ -528,7 +572,7 @@ __global__ void __launch_bounds__(256) coarse_bin_kernel(
         uint32_t c = 0, off = EMIT ? offsets[idx] : 0u;
         if (mode != 0) {
             for (int sidx = 0; sidx < n_super; ++sidx) {
-                if ((!sact || sact[l * n_super + sidx]) && (mode == 2 || cone_overlap(g, scones + 2 * sidx))) {
+                if ((!sact || sact[l * n_super + sidx]) && (mode == 2 || super_overlap(g, scones, scones2, sidx))) {
                     if (EMIT && off + c < cap) {
                         ckeys[off + c] = (uint32_t)(l * n_super + sidx);
                         cvals[off + c] = gi;
@@ -1282,7 +1326,8 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
         return rc;
     if ((rc = ws_reserve(ctx, WS_BIN_REC, sizeof(BinRec) * (size_t)LN, &w_bin))) return rc;
     if ((rc = ws_reserve(ctx, WS_COUNTS, sizeof(uint32_t) * (size_t)LN, &w_cnt))) return rc;
-    if ((rc = ws_reserve(ctx, WS_CONES, sizeof(float4) * (size_t)(2 * (n_tiles + n_super) + PLANE_F4 * n_tiles),
+    if ((rc = ws_reserve(ctx, WS_CONES,
+                         sizeof(float4) * (size_t)(2 * (n_tiles + n_super) + PLANE_F4 * n_tiles + 2 * n_super),
                          &w_cones)))
         return rc;
     if ((rc = ws_reserve(ctx, WS_RANGES, 2 * sizeof(uint32_t) * (size_t)nkeys, &w_rng))) return rc;
@@ -1311,8 +1356,9 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
                                      p.eps_cull, build_records ? (BuildRec *)w_br : nullptr,
                                      (BinRec *)w_bin, ctx->d_status, roi ? roi->krange : nullptr,
                                      p.beta_mode == 4 ? 3 : p.beta_mode);
+    const float4 *scones2 = cones + 2 * (n_tiles + n_super) + PLANE_F4 * n_tiles;
     coarse_bin_kernel<false><<<grid, 256, 0, s>>>((const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles,
-                                                   (uint32_t *)w_cnt, nullptr, nullptr, nullptr, nullptr, 0u,
+                                                   scones2, (uint32_t *)w_cnt, nullptr, nullptr, nullptr, nullptr, 0u,
                                                    roi ? roi->sact : nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "prep/coarse count kernels");
@@ -1332,7 +1378,7 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     if ((rc = ws_reserve(ctx, WS_CVALS_B, sizeof(uint32_t) * capC, &cvb))) return rc;
     keep_pairs_kernel<<<1, 32, 0, s>>>(d_cpairs, (unsigned long long)capC, d_ckeep, ctx->d_status);
     coarse_bin_kernel<true><<<grid, 256, 0, s>>>((const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles,
-                                                  nullptr, (const uint32_t *)w_cnt, (uint32_t *)cka,
+                                                  scones2, nullptr, (const uint32_t *)w_cnt, (uint32_t *)cka,
                                                   (uint32_t *)cva, d_ckeep, (uint32_t)capC,
                                                   roi ? roi->sact : nullptr);
     e = cudaGetLastError();

@@ -185,6 +185,28 @@ int dgsm_build_roi(dgsm_ctx *ctx, const float *means, const float *scales, const
                    int32_t W, const float *radii, int32_t K, const dgsm_params *params,
                    const dgsm_roi *roi, void *atlas, void *stream);
 
+/* One band of atlas rows, for splitting one light's atlas over several GPUs
+ * (each GPU bins every Gaussian but builds only the tiles of its rows, then
+ * the bands are exchanged; the lights themselves are independent problems).
+ * Builds rows [row0, row1) of the atlas exactly as dgsm_build does and sets
+ * every other texel to T = 1 (a region of interest made of whole rows).
+ * 0 <= row0 < row1 <= H; other arguments, blocking and errors as for
+ * dgsm_build. */
+int dgsm_build_band(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
+                    const float *opac, int64_t n, const float *lights, int32_t n_lights, int32_t H,
+                    int32_t W, const float *radii, int32_t K, const dgsm_params *params, int32_t row0,
+                    int32_t row1, void *atlas, void *stream);
+
+/* Copies `rows` rows of every plane between two row-major stacks of planes
+ * of width W: dst plane p, rows [dst_row0, dst_row0 + rows) <- src plane p,
+ * rows [src_row0, src_row0 + rows); planes of src_rows and dst_rows rows.
+ * Cuts an atlas band out of an atlas [L][K][H][W] (planes = L K) into a
+ * slab, and puts a gathered slab back.  src, dst: device; elem_bytes 4
+ * (float32) or 2 (float16, bfloat16).  One asynchronous 2-D copy. */
+int dgsm_atlas_rows_copy(dgsm_ctx *ctx, const void *src, int32_t src_rows, int32_t src_row0, void *dst,
+                         int32_t dst_rows, int32_t dst_row0, int32_t rows, int64_t planes, int32_t W,
+                         int32_t elem_bytes, void *stream);
+
 /* The box of a region of interest around an avatar (Sec. 3.2): c = the
  * alpha-weighted centroid of the avatar's Gaussians (x, y), the given
  * half-width R, and z from the lowest to the highest avatar centre padded by

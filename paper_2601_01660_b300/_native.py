@@ -103,6 +103,9 @@ _lib.dgsm_get_build_stats.argtypes = [_vp, C.POINTER(BuildStats)]
 _lib.dgsm_build_roi.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i32,
                                 C.POINTER(Params), C.POINTER(Roi), _vp, _vp]
 _lib.dgsm_roi_box.argtypes = [_vp, _vp, _vp, _i64, _f32, _f32, _vp, _vp]
+_lib.dgsm_build_band.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i32,
+                                 C.POINTER(Params), _i32, _i32, _vp, _vp]
+_lib.dgsm_atlas_rows_copy.argtypes = [_vp, _vp, _i32, _i32, _vp, _i32, _i32, _i32, _i64, _i32, _i32, _vp]
 _lib.dgsm_pca_normals.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _f32, _vp, _vp, _vp]
 _lib.dgsm_bin.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i32,
                           C.POINTER(Params), _vp, _vp, _i64, C.POINTER(_i64), _vp]
@@ -255,6 +258,47 @@ def dgsm_build(means, scales, quats, opac, lights, H, W, radii, params=None, out
                               _ptr(lights), L, H, W, _ptr(radii), K, C.byref(p), _ptr(out),
                               _stream(stream)))
     return out
+
+
+def dgsm_build_band(means, scales, quats, opac, lights, H, W, radii, row0, row1, params=None, out=None,
+                    ctx: Context | None = None, stream=None):
+    """Rows [row0, row1) of the atlas [L][K][H][W] as dgsm_build builds them,
+    T = 1 elsewhere (one GPU's band of a light's atlas)."""
+    ctx = ctx or context(means.device.index)
+    _need(means, "means", shape_last=3)
+    _need(scales, "scales", shape_last=3)
+    _need(quats, "quats", shape_last=4)
+    _need(opac, "opac")
+    _need(lights, "lights", shape_last=3)
+    _need(radii, "radii")
+    p = params if isinstance(params, Params) else Params.make(**(params or {}))
+    L, K, n = lights.shape[0], radii.shape[0], means.shape[0]
+    if out is None:
+        out = torch.empty((L, K, H, W), dtype=TORCH_DTYPES[p.atlas_dtype], device=means.device)
+    _need(out, "out", TORCH_DTYPES[p.atlas_dtype])
+    if tuple(out.shape) != (L, K, H, W):
+        raise ValueError("out must have shape (L, K, H, W)")
+    ctx.check(_lib.dgsm_build_band(ctx.handle, _ptr(means), _ptr(scales), _ptr(quats), _ptr(opac), n,
+                                   _ptr(lights), L, H, W, _ptr(radii), K, C.byref(p), int(row0), int(row1),
+                                   _ptr(out), _stream(stream)))
+    return out
+
+
+def dgsm_atlas_rows_copy(src, src_row0, dst, dst_row0, rows, ctx: Context | None = None, stream=None):
+    """dst[..., dst_row0:dst_row0+rows, :] = src[..., src_row0:src_row0+rows, :] for
+    contiguous (..., rows, W) device tensors of one dtype and the same leading shape."""
+    ctx = ctx or context(src.device.index)
+    _need(src, "src", src.dtype)
+    _need(dst, "dst", src.dtype)
+    if src.dim() < 2 or src.shape[:-2] != dst.shape[:-2] or src.shape[-1] != dst.shape[-1]:
+        raise ValueError("src and dst must share their leading shape and width")
+    planes = 1
+    for d in src.shape[:-2]:
+        planes *= int(d)
+    ctx.check(_lib.dgsm_atlas_rows_copy(ctx.handle, _ptr(src), src.shape[-2], int(src_row0), _ptr(dst),
+                                        dst.shape[-2], int(dst_row0), int(rows), planes, src.shape[-1],
+                                        src.element_size(), _stream(stream)))
+    return dst
 
 
 def dgsm_get_build_stats(ctx: Context | None = None) -> dict:

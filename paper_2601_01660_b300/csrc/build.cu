@@ -1710,6 +1710,90 @@ extern "C" int dgsm_build_roi(dgsm_ctx *ctx, const float *means, const float *sc
     return build_impl(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, atlas, s, &r);
 }
 
+// ---- a band of atlas rows (the multi-GPU split of one light's atlas) ----
+
+namespace dgsm {
+namespace {
+
+// mask[l][i][j] = 1 for rows [row0, row1); every shell in range.
+__global__ void band_init_kernel(uint8_t *__restrict__ mask, int *__restrict__ krange, int L, int H, int W, int K,
+                                 int row0, int row1) {
+    const int64_t HW = (int64_t)H * W;
+    const int64_t total = (int64_t)L * HW;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)((idx % HW) / W);
+        mask[idx] = i >= row0 && i < row1;
+        if (idx < L) {
+            krange[2 * idx] = 0;
+            krange[2 * idx + 1] = K - 1;
+        }
+    }
+}
+
+}  // namespace
+}  // namespace dgsm
+
+extern "C" int dgsm_build_band(dgsm_ctx *ctx, const float *means, const float *scales, const float *quats,
+                               const float *opac, int64_t n, const float *lights, int32_t L, int32_t H,
+                               int32_t W, const float *radii, int32_t K, const dgsm_params *params,
+                               int32_t row0, int32_t row1, void *atlas, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    dgsm_params p;
+    if (params) p = *params; else dgsm_default_params(&p);
+    int rc = check_build(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, atlas);
+    if (rc) return rc;
+    if (!(0 <= row0 && row0 < row1 && row1 <= H))
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "band rows: need 0 <= row0 < row1 <= H");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int tx = (W + p.tile - 1) / p.tile, ty = (H + p.tile - 1) / p.tile;
+    const int sx = (tx + SUPER - 1) / SUPER, sy = (ty + SUPER - 1) / SUPER;
+    const int64_t n_tiles = (int64_t)tx * ty, n_super = (int64_t)sx * sy;
+    const int64_t HW = (int64_t)H * W;
+    const size_t kr_bytes = ((size_t)L * 2 * sizeof(int) + 255) & ~(size_t)255;
+    const size_t m_bytes = ((size_t)(L * HW) + 255) & ~(size_t)255;
+    const size_t t_bytes = ((size_t)(L * n_tiles) + 255) & ~(size_t)255;
+    const size_t total = kr_bytes + m_bytes + t_bytes + (size_t)(L * n_super);
+    void *w;
+    if ((rc = ws_reserve(ctx, WS_ROI, total, &w))) return rc;
+    RoiDev r;
+    int *krange = (int *)w;
+    uint8_t *mask = (uint8_t *)w + kr_bytes;
+    uint8_t *tact = mask + m_bytes, *sact = tact + t_bytes;
+    r.krange = krange;
+    r.mask = mask;
+    r.tact = tact;
+    r.sact = sact;
+    const int grid = (int)std::min<int64_t>((L * HW + 255) / 256, (int64_t)ctx->num_sms * 8);
+    band_init_kernel<<<grid, 256, 0, s>>>(mask, krange, L, H, W, K, row0, row1);
+    roi_tiles_kernel<<<(int)((L * n_tiles + 255) / 256), 256, 0, s>>>(mask, L, H, W, p.tile, tx, (int)n_tiles,
+                                                                       tact);
+    roi_super_kernel<<<(int)((L * n_super + 255) / 256), 256, 0, s>>>(tact, L, tx, ty, sx, (int)n_tiles,
+                                                                       (int)n_super, sact);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "band kernels");
+    return build_impl(ctx, means, scales, quats, opac, n, lights, L, H, W, radii, K, p, atlas, s, &r);
+}
+
+extern "C" int dgsm_atlas_rows_copy(dgsm_ctx *ctx, const void *src, int32_t src_rows, int32_t src_row0, void *dst,
+                                    int32_t dst_rows, int32_t dst_row0, int32_t rows, int64_t planes, int32_t W,
+                                    int32_t elem_bytes, void *stream) {
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (rows == 0 || planes == 0) return DGSM_OK;
+    if (!src || !dst || rows < 0 || planes < 0 || W < 1 || (elem_bytes != 2 && elem_bytes != 4) ||
+        src_row0 < 0 || dst_row0 < 0 || src_row0 + rows > src_rows || dst_row0 + rows > dst_rows)
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "atlas rows copy: rows out of range or bad sizes");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    const size_t row_b = (size_t)W * elem_bytes;
+    e = cudaMemcpy2DAsync((char *)dst + (size_t)dst_row0 * row_b, (size_t)dst_rows * row_b,
+                          (const char *)src + (size_t)src_row0 * row_b, (size_t)src_rows * row_b,
+                          (size_t)rows * row_b, (size_t)planes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "atlas rows copy");
+}
+
 extern "C" int dgsm_get_build_stats(dgsm_ctx *ctx, dgsm_build_stats *out) {
     if (!ctx || !out) return DGSM_ERR_INVALID_ARG;
     cudaError_t e = cudaSetDevice(ctx->device);

@@ -279,12 +279,24 @@ def run_ours(args, rank, world, local_rank):
     roi_vox = int(sum(int(roi_mask[l].sum().item()) * max(0, int(rk[l, 1]) - int(rk[l, 0]) + 1)
                       for l in range(L)))
     roi_t = statistics.mean(roi_ms)
+    roi_st = nat.dgsm_get_build_stats()
+    roi_tile_ms = statistics.mean(p[1] for p in roi_prof)
+    # the region's tile kernel against the same FP32 roofline as the dense one
+    # (its voxels outside P x [k_min, k_max] are written as 1 without work)
+    roi_fp32 = (FP32_PER_EVAL * roi_st["ray_evals"] + FP32_PER_SHELL * roi_st["shell_evals"]
+                + FP32_PER_VOXEL * roi_vox)
+    roi_ach = roi_fp32 / (roi_tile_ms * 1e-3) / 1e12
     roi_build = {"ms": round(roi_t, 4), "box_half_width_m": 2.0, "voxels": roi_vox,
                  "phases_ms": {"prep_binning_sort": round(statistics.mean(p[0] for p in roi_prof), 4),
-                               "tile_kernel": round(statistics.mean(p[1] for p in roi_prof), 4)},
+                               "tile_kernel": round(roi_tile_ms, 4)},
+                 "ray_evals": int(roi_st["ray_evals"]),
+                 "tile_kernel_roofline": {"bound": "alu", "pipe": "fp32", "achieved": round(roi_ach, 4),
+                                          "peak": round(fp32_peak, 4), "unit": "Tops/s",
+                                          "frac": round(roi_ach / fp32_peak, 4)},
                  "voxel_frac": round(roi_vox / voxels, 4), "dense_ms_per_build": None}
     attenuate["footprint_mc8"] = {"ms": round(fpt, 5), "gaussians_per_s": N / (fpt * 1e-3),
                                   "achieved_gbs": round((N * 64) / (fpt * 1e-3) / 1e9, 1),
+                                  "frac": round((N * 64) / (fpt * 1e-3) / 1e9 / hbm_peak, 4),
                                   "algorithmic_bytes": N * 64,
                                   "gathers_per_query": 8 * 8 * L}
 

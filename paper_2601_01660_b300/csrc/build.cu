@@ -527,7 +527,8 @@ __device__ __forceinline__ bool cone_overlap(const BinRec &g, const float4 *cone
     return cone_overlap_v(g, __ldg(cone), __ldg(cone + 1));
 }
 
-// Super-tile sidx: its cone, or either of its two cones when flagged.
+// Super-tile sidx of a cube map: its cone, or either of its two cones when
+// flagged (the octahedral map's super-tiles have one cone).
 __device__ __forceinline__ bool super_overlap(const BinRec &g, const float4 *scones, const float4 *scones2,
                                               int sidx) {
     const float4 c0 = __ldg(scones + 2 * sidx), c1 = __ldg(scones + 2 * sidx + 1);
@@ -550,7 +551,7 @@ constexpr int UNIT_G = 512;     // Gaussians of one super-tile list per fine-bin
 constexpr int FB_STAGE = 256;   // Gaussians staged in shared memory at a time
 constexpr int TDAT_F4 = 2 + PLANE_F4;  // per tile: cone (2 float4) + planes
 
-template <bool EMIT>
+template <bool EMIT, bool TWO>
 __global__ void __launch_bounds__(256) coarse_bin_kernel(
     const BinRec *__restrict__ bin, int64_t N, int L, int n_super, const float4 *__restrict__ scones,
     const float4 *__restrict__ scones2, uint32_t *__restrict__ counts, const uint32_t *__restrict__ offsets, uint32_t *__restrict__ ckeys,
@@ -572,7 +573,8 @@ __global__ void __launch_bounds__(256) coarse_bin_kernel(
         uint32_t c = 0, off = EMIT ? offsets[idx] : 0u;
         if (mode != 0) {
             for (int sidx = 0; sidx < n_super; ++sidx) {
-                if ((!sact || sact[l * n_super + sidx]) && (mode == 2 || super_overlap(g, scones, scones2, sidx))) {
+                if ((!sact || sact[l * n_super + sidx]) &&
+                    (mode == 2 || (TWO ? super_overlap(g, scones, scones2, sidx) : cone_overlap(g, scones + 2 * sidx)))) {
                     if (EMIT && off + c < cap) {
                         ckeys[off + c] = (uint32_t)(l * n_super + sidx);
                         cvals[off + c] = gi;
@@ -1357,9 +1359,10 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
                                      (BinRec *)w_bin, ctx->d_status, roi ? roi->krange : nullptr,
                                      p.beta_mode == 4 ? 3 : p.beta_mode);
     const float4 *scones2 = cones + 2 * (n_tiles + n_super) + PLANE_F4 * n_tiles;
-    coarse_bin_kernel<false><<<grid, 256, 0, s>>>((const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles,
-                                                   scones2, (uint32_t *)w_cnt, nullptr, nullptr, nullptr, nullptr, 0u,
-                                                   roi ? roi->sact : nullptr);
+    const bool two = p.atlas_map == MAP_CUBE;
+    (two ? coarse_bin_kernel<false, true> : coarse_bin_kernel<false, false>)<<<grid, 256, 0, s>>>(
+        (const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles, scones2, (uint32_t *)w_cnt, nullptr, nullptr,
+        nullptr, nullptr, 0u, roi ? roi->sact : nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "prep/coarse count kernels");
     if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_cnt, (uint32_t *)w_cnt, LN, d_cpairs, s))) return rc;
@@ -1377,10 +1380,9 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     if ((rc = ws_reserve(ctx, WS_CKEYS_B, sizeof(uint32_t) * capC, &ckb))) return rc;
     if ((rc = ws_reserve(ctx, WS_CVALS_B, sizeof(uint32_t) * capC, &cvb))) return rc;
     keep_pairs_kernel<<<1, 32, 0, s>>>(d_cpairs, (unsigned long long)capC, d_ckeep, ctx->d_status);
-    coarse_bin_kernel<true><<<grid, 256, 0, s>>>((const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles,
-                                                  scones2, nullptr, (const uint32_t *)w_cnt, (uint32_t *)cka,
-                                                  (uint32_t *)cva, d_ckeep, (uint32_t)capC,
-                                                  roi ? roi->sact : nullptr);
+    (two ? coarse_bin_kernel<true, true> : coarse_bin_kernel<true, false>)<<<grid, 256, 0, s>>>(
+        (const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles, scones2, nullptr, (const uint32_t *)w_cnt,
+        (uint32_t *)cka, (uint32_t *)cva, d_ckeep, (uint32_t)capC, roi ? roi->sact : nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "coarse emit kernel");
     uint32_t *ckeys = (uint32_t *)cka, *cvals = (uint32_t *)cva;

@@ -29,7 +29,8 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # ORACLE_SANITIZED=1 loads the ASan/UBSan build (its runtime must be preloaded)
+        path = _build.build(sanitize=os.environ.get("ORACLE_SANITIZED") == "1")
         _lib = C.CDLL(path)
         _declare(_lib)
     return _lib

@@ -385,6 +385,7 @@ extern "C" int dgsm_attenuate(dgsm_ctx *ctx, const void *atlas, const void *atla
                               int32_t K, const float *lights, const float *q_means,
                               const float *colors_in, int64_t n_q, const float *light_w,
                               float direct_frac, float *colors_out, float *T_out, void *stream) {
+    DGSM_RANGE("dgsm_attenuate");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     return attenuate_common(ctx, atlas, atlas_dyn, dtype, L, H, W, radii, K, false,
                             DynGeom{H, W, K, radii}, lights, q_means, colors_in, n_q, light_w,
@@ -398,6 +399,7 @@ extern "C" int dgsm_attenuate_dyn(dgsm_ctx *ctx, const void *atlas, int32_t dtyp
                                   const float *q_means, const float *colors_in, int64_t n_q,
                                   const float *light_w, float direct_frac, float *colors_out,
                                   float *T_out, void *stream) {
+    DGSM_RANGE("dgsm_attenuate_dyn");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     if (!atlas_dyn) return fail(ctx, DGSM_ERR_INVALID_ARG, "null dynamic atlas");
     return attenuate_common(ctx, atlas, atlas_dyn, dtype, L, H, W, radii, K, true,
@@ -430,6 +432,7 @@ extern "C" int dgsm_attenuate_footprint(dgsm_ctx *ctx, const void *atlas, int32_
                                         const float *light_w, float direct_frac, int32_t mode,
                                         int32_t n_samples, uint64_t seed, float *colors_out, float *T_out,
                                         void *stream) {
+    DGSM_RANGE("dgsm_attenuate_footprint");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     if (n_q < 0) return fail(ctx, DGSM_ERR_INVALID_ARG, "n_q < 0");
     if (L < 1 || L > 64) return fail(ctx, DGSM_ERR_INVALID_ARG, "need 1..64 lights");
@@ -481,6 +484,7 @@ extern "C" int dgsm_attenuate_cube(dgsm_ctx *ctx, const void *atlas, int32_t dty
                                    const float *radii, int32_t K, const float *lights, const float *q_means,
                                    const float *colors_in, int64_t n_q, const float *light_w, float direct_frac,
                                    float *colors_out, float *T_out, void *stream) {
+    DGSM_RANGE("dgsm_attenuate_cube");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     return attenuate_common(ctx, atlas, nullptr, dtype, L, 6 * F, F, radii, K, false, DynGeom{6 * F, F, K, radii},
                             lights, q_means, colors_in, n_q, light_w, direct_frac, colors_out, T_out, stream, true);

@@ -1646,6 +1646,7 @@ extern "C" int dgsm_build(dgsm_ctx *ctx, const float *means, const float *scales
                           const float *quats, const float *opac, int64_t n, const float *lights,
                           int32_t L, int32_t H, int32_t W, const float *radii, int32_t K,
                           const dgsm_params *params, void *atlas, void *stream) {
+    DGSM_RANGE("dgsm_build");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     dgsm_params p;
     if (params) p = *params; else dgsm_default_params(&p);
@@ -1662,6 +1663,7 @@ extern "C" int dgsm_build_roi(dgsm_ctx *ctx, const float *means, const float *sc
                               int32_t L, int32_t H, int32_t W, const float *radii, int32_t K,
                               const dgsm_params *params, const dgsm_roi *roi, void *atlas,
                               void *stream) {
+    DGSM_RANGE("dgsm_build_roi");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     dgsm_params p;
     if (params) p = *params; else dgsm_default_params(&p);
@@ -1740,6 +1742,7 @@ extern "C" int dgsm_build_band(dgsm_ctx *ctx, const float *means, const float *s
                                const float *opac, int64_t n, const float *lights, int32_t L, int32_t H,
                                int32_t W, const float *radii, int32_t K, const dgsm_params *params,
                                int32_t row0, int32_t row1, void *atlas, void *stream) {
+    DGSM_RANGE("dgsm_build_band");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     dgsm_params p;
     if (params) p = *params; else dgsm_default_params(&p);
@@ -1816,6 +1819,7 @@ extern "C" int dgsm_bin(dgsm_ctx *ctx, const float *means, const float *scales, 
                         int32_t W, const float *radii, int32_t K, const dgsm_params *params,
                         uint32_t *keys_out, uint32_t *vals_out, int64_t capacity,
                         int64_t *n_pairs_out, void *stream) {
+    DGSM_RANGE("dgsm_bin");
     if (!ctx || !n_pairs_out) return DGSM_ERR_INVALID_ARG;
     dgsm_params p;
     if (params) p = *params; else dgsm_default_params(&p);

@@ -67,6 +67,8 @@ struct dgsm_ctx {
     cudaEvent_t fev[4] = {};
 };
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace dgsm {
 
 // Contiguous objects of a Gaussian array (avatars): object o holds the
@@ -92,6 +94,16 @@ __device__ __forceinline__ int seg_find(const Segs &sg, long long g) {
     }
     return lo;
 }
+
+// An NVTX range around a library call (header-only NVTX: a no-op unless a
+// profiler is attached), so that profiles can be cut by entry point.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define DGSM_RANGE(name) ::dgsm::NvtxRange dgsm_nvtx_range_(name)
 
 int fail(dgsm_ctx *ctx, int code, const std::string &msg);
 int cuda_fail(dgsm_ctx *ctx, cudaError_t e, const char *what);

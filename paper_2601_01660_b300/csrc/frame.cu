@@ -156,6 +156,7 @@ extern "C" int dgsm_segment_centroids(dgsm_ctx *ctx, const float *means, const f
 extern "C" int dgsm_frame_host(dgsm_ctx *ctx, const dgsm_frame_host_in *in,
                                const dgsm_params *params, const dgsm_relight_params *rparams,
                                float *colors_out, float *sh_out, void *stream) {
+    DGSM_RANGE("dgsm_frame_host");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     if (!in || !colors_out) return fail(ctx, DGSM_ERR_INVALID_ARG, "frame: null input or output");
     const int64_t n = in->n;

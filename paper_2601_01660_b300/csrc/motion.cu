@@ -59,6 +59,7 @@ extern "C" int dgsm_rigid_transform(dgsm_ctx *ctx, const float *means, const flo
                                     int64_t n, const int64_t *seg, int32_t n_obj,
                                     const float *poses, float *means_out, float *quats_out,
                                     void *stream) {
+    DGSM_RANGE("dgsm_rigid_transform");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     if (n < 0) return fail(ctx, DGSM_ERR_INVALID_ARG, "rigid_transform: n < 0");
     Segs segs;

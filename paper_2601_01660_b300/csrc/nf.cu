@@ -836,6 +836,7 @@ extern "C" int nf_loss_grad(dgsm_ctx *ctx, const float *params, const float *uvr
 extern "C" int nf_train(dgsm_ctx *ctx, const float *atlas, int32_t H, int32_t W, int32_t K,
                         float *params, float *adam_m, float *adam_v, int32_t steps, int32_t batch,
                         float lr, uint64_t seed, int32_t step0, float *loss_out, void *stream) {
+    DGSM_RANGE("nf_train");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     if (!atlas || !params || !adam_m || !adam_v || H < 1 || W < 1 || K < 1 || steps < 0 || batch < 1 ||
         batch > (1 << 22) || step0 < 0 || !(lr > 0.f))
@@ -893,6 +894,7 @@ extern "C" int nf_attenuate(dgsm_ctx *ctx, const float *params, const uint8_t *m
                             const float *lights, const float *q_means, const float *colors_in, int64_t n_q,
                             const float *light_w, float direct_frac, float *colors_out, float *T_out,
                             void *stream) {
+    DGSM_RANGE("nf_attenuate");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     if (n_q < 0 || L < 1 || L > 64 || H < 1 || W < 1 || H > 4096 || W > 4096 || K < 1 || K > 256 || tile < 1 ||
         !params || !radii || !lights || (mask && !atlas))

@@ -238,6 +238,7 @@ using namespace dgsm;
 extern "C" int dgsm_pca_normals(dgsm_ctx *ctx, const float *means, const float *opac, const float *quats,
                                 const float *scales, int64_t n, float radius, const float *centroid,
                                 float *normals_out, void *stream) {
+    DGSM_RANGE("dgsm_pca_normals");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     if (n < 0 || n > 0x7fffffffLL) return fail(ctx, DGSM_ERR_INVALID_ARG, "pca normals: 0 <= n < 2^31");
     if (!(radius > 0.0f) || !(radius < INFINITY))

@@ -516,6 +516,7 @@ extern "C" int dgsm_render_views(dgsm_ctx *ctx, const float *means, const float 
                                  const float *opac, const float *colors, int64_t n, const float *cams,
                                  int32_t n_views, int32_t W, int32_t H, float near, float *rgb_out,
                                  int64_t *n_pairs_out, void *stream) {
+    DGSM_RANGE("dgsm_render_views");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     int rc = check_gaussians(ctx, means, scales, quats, opac, colors, n, near, rgb_out);
     if (rc) return rc;
@@ -532,6 +533,7 @@ extern "C" int dgsm_render_cubemap(dgsm_ctx *ctx, const float *means, const floa
                                    const float *opac, const float *colors, int64_t n, const float *centre,
                                    int32_t face, float near, float *rgb_out, int64_t *n_pairs_out,
                                    void *stream) {
+    DGSM_RANGE("dgsm_render_cubemap");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     int rc = check_gaussians(ctx, means, scales, quats, opac, colors, n, near, rgb_out);
     if (rc) return rc;

@@ -71,6 +71,7 @@ using namespace dgsm;
 
 extern "C" int dgsm_roi_box(dgsm_ctx *ctx, const float *avatar_means, const float *avatar_opac, int64_t n,
                             float R, float z_margin, float *box_out, void *stream) {
+    DGSM_RANGE("dgsm_roi_box");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     if (n < 1 || !avatar_means || !avatar_opac || !box_out)
         return fail(ctx, DGSM_ERR_INVALID_ARG, "roi box: need n >= 1 and device arrays");

@@ -87,6 +87,7 @@ extern "C" int dgsm_autotune_build(dgsm_ctx *ctx, const float *means, const floa
                                    const int32_t *tiles, int32_t n_tiles, const int32_t *chunks,
                                    int32_t n_chunks, int32_t reps, void *atlas,
                                    dgsm_params *best_out, float *ms_out, void *stream) {
+    DGSM_RANGE("dgsm_autotune_build");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     if (!tiles || !chunks || n_tiles < 1 || n_chunks < 1 || reps < 1 || !best_out)
         return fail(ctx, DGSM_ERR_INVALID_ARG, "autotune: need candidates, reps >= 1 and an output");

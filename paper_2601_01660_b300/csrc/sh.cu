@@ -248,6 +248,7 @@ using namespace dgsm;
 
 extern "C" int sh_fit(dgsm_ctx *ctx, const float *dirs, const float *rgb, const float *w,
                       int64_t n, double lambda, float *sh_out, double *sh64_out, void *stream) {
+    DGSM_RANGE("sh_fit");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     if (n < 1 || !dirs || !rgb || !w || !sh_out) return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_fit: need n >= 1 and non-null arrays");
     if (!(lambda >= 0.0)) return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_fit: lambda must be >= 0");
@@ -298,6 +299,7 @@ extern "C" int sh_relight(dgsm_ctx *ctx, const float *sh, const float *means, co
                           const float *scales, const float *normals, const float *centroid,
                           const float *colors_in, int64_t n, const dgsm_relight_params *params,
                           float *colors_out, void *stream) {
+    DGSM_RANGE("sh_relight");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     if (n < 0) return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_relight: n < 0");
     const int64_t whole[2] = {0, n};
@@ -312,6 +314,7 @@ extern "C" int sh_relight_objects(dgsm_ctx *ctx, const float *sh, const float *m
                                   const int64_t *seg, int32_t n_obj, const float *colors_in,
                                   int64_t n, const dgsm_relight_params *params, float *colors_out,
                                   void *stream) {
+    DGSM_RANGE("sh_relight_objects");
     if (!ctx) return DGSM_ERR_INVALID_ARG;
     if (n < 0) return fail(ctx, DGSM_ERR_INVALID_ARG, "sh_relight_objects: n < 0");
     Segs segs;

@@ -60,6 +60,18 @@ def test_bands_reassemble_the_dense_build(nat, world, tile):
     assert dense.min().item() < 0.5
 
 
+def test_cube_map_bands(nat):
+    """The split works the same on a cube-map atlas (six 24 x 24 faces)."""
+    sc = scenes.cube_scene(8000, seed=6)
+    d = scene_to_dev(sc)
+    lights = dev(scenes.four_lights()[:2])
+    radii = dev(scenes.radii_linear(0.1, 8, 8))
+    p = {"atlas_map": 1}
+    dense = nat.dgsm_build(d["means"], d["scales"], d["quats"], d["opac"], lights, 144, 24, radii, params=p)
+    got = _banded(nat, d, lights, 144, 24, radii, 4, params=p)
+    assert (got - dense).abs().max().item() <= 1e-6
+
+
 def test_band_against_the_oracle(nat, orc):
     sc = scenes.cube_scene(1500, seed=2)
     lights = np.float32([[0, 0, 0], [0.5, -0.5, 1.0]])

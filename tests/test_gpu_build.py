@@ -151,3 +151,31 @@ def test_bad_arguments_are_rejected(nat):
         _build(nat, sc, np.float32([[0, 0, 0]]), 16, 16, scenes.radii_linear(0.1, 8, 4), chunk=4)
     with pytest.raises(nat.DGSMError):   # 4x4 tiles: binning only
         _build(nat, sc, np.float32([[0, 0, 0]]), 16, 16, scenes.radii_linear(0.1, 8, 4), tile=4)
+
+
+def test_maximum_sizes(nat, orc):
+    """The largest sizes the build accepts: 256 shells; a 4096 x 4096 atlas
+    (sampled texels); 64 lights.  Each against the FP64 oracle."""
+    sc = scenes.cube_scene(600, seed=21)
+    # K = 256 geometric shells on a small atlas, every voxel
+    radii = scenes.radii_geometric(0.05, 12.0, 256)
+    T = _build(nat, sc, np.float32([[0, 0, 0]]), 12, 12, radii).double().cpu().numpy()
+    assert np.abs(T - orc.build_atlas(sc, np.float32([[0, 0, 0]]), 12, 12, radii)).max() <= TOL_F32
+    # H = W = 4096 (2 shells), 300 random texels
+    radii2 = np.float32([0.5, 9.0])
+    T = _build(nat, sc, np.float32([[0.1, 0.2, 0.3]]), 4096, 4096, radii2)
+    lij = texel_sample(np.random.default_rng(1), 1, 4096, 4096, 300)
+    got = T[lij[:, 0], :, lij[:, 1], lij[:, 2]].double().cpu().numpy()
+    tau = orc.build_tau_texels(sc, np.float32([[0.1, 0.2, 0.3]]), 4096, 4096, radii2, lij)
+    assert np.abs(got - np.exp(-tau)).max() <= TOL_F32 and np.exp(-tau).min() < 0.99
+    # 64 lights, every voxel
+    lights = np.float32(np.random.default_rng(2).uniform(-2, 2, (64, 3)) + [0, 0, 3.0])
+    radii3 = scenes.radii_linear(0.1, 8, 4)
+    T = _build(nat, sc, lights, 8, 8, radii3).double().cpu().numpy()
+    assert np.abs(T - orc.build_atlas(sc, lights, 8, 8, radii3)).max() <= TOL_F32
+    with pytest.raises(nat.DGSMError):   # one past each limit
+        _build(nat, sc, np.float32([[0, 0, 0]]), 8, 8, scenes.radii_geometric(0.05, 12.0, 257))
+    with pytest.raises(nat.DGSMError):
+        _build(nat, sc, np.float32([[0, 0, 0]]), 4097, 8, radii2)
+    with pytest.raises(nat.DGSMError):
+        _build(nat, sc, np.zeros((65, 3), np.float32), 8, 8, radii2)

@@ -4,15 +4,19 @@
 // relit avatar in the shadowed scene, seen by pinhole cameras.
 //
 // Pipeline per call (all on the caller's stream), for n_views cameras:
-//   splat_count_kernel  per Gaussian and view: view coordinates, the EWA
-//                       screen covariance (Jacobian of the pinhole
-//                       projection at the mean), its inverse and a
-//                       conservative square of 8x8 tiles around the 3-sigma
-//                       ellipse -> number of (tile, splat) pairs
-//   scan                pair offsets                    (one host sync)
-//   splat_emit_kernel   the pairs: depth key, tile key, splat payload
-//   radix sort          by depth, then stably by tile: each tile's splats
-//                       front to back, ties by Gaussian index
+//   splat_prep_kernel   per Gaussian and view (a splat): view coordinates,
+//                       the EWA screen covariance (Jacobian of the pinhole
+//                       projection at the mean), its inverse, its payload,
+//                       its depth and a conservative rectangle of 8x8 tiles
+//                       around the 3-sigma ellipse
+//   scan, compaction    the splats that reach a tile
+//   radix sort          those splats by depth (stable: ties by Gaussian index)
+//   scan                pair offsets of the splats in depth order (one host
+//                       sync for the pair count)
+//   splat_pairs_kernel  the (tile, splat) pairs in depth order, every block
+//                       spreading its splats' pairs over all of its threads
+//   radix sort          the pairs stably by tile: each tile's splats front
+//                       to back
 //   splat_ranges_kernel [start, end) of every tile
 //   segment kernels     every tile's list cut into segments of `seg` splats,
 //                       seg sized so that the segments fill the GPU
@@ -155,40 +159,15 @@ __device__ __forceinline__ void splat_tiles(const Splat &sp, int ntx, int nty, i
     if (i1 < i0) i1 = i0;
 }
 
-__global__ void __launch_bounds__(256) splat_count_kernel(
-    const float *__restrict__ means, const float *__restrict__ scales, const float *__restrict__ quats,
-    const float *__restrict__ opac, int64_t n, const float *__restrict__ cams, int n_views, int W, int H,
-    float near, uint32_t *__restrict__ counts) {
-    __shared__ float scam[64 * CAM_F];
-    for (int k = threadIdx.x; k < n_views * CAM_F; k += blockDim.x) scam[k] = cams[k];
-    __syncthreads();
-    const int ntx = (W + RT - 1) / RT, nty = (H + RT - 1) / RT;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t c = 0;
-        if (opac[g] > 0.0f) {
-            float Rs[9];
-            rot_scale(quats + 4 * g, scales + 3 * g, Rs);
-            for (int v = 0; v < n_views; ++v) {
-                const Splat sp = make_splat(means + 3 * g, Rs, scam + CAM_F * v, W, H, near);
-                if (!sp.ok) continue;
-                int i0, i1, j0, j1;
-                splat_tiles(sp, ntx, nty, i0, i1, j0, j1);
-                c += (uint32_t)((i1 - i0) * (j1 - j0));
-            }
-        }
-        counts[g] = c;
-    }
-}
-
-// payload of splat (Gaussian g, view v) at g n_views + v: (mx, my, A, B),
-// (C, opacity, tz, g), (r, g, b, 0); a pair carries the splat's index
-__global__ void __launch_bounds__(256) splat_emit_kernel(
+// Splat sid = g n_views + v (Gaussian g, view v): payload (mx, my, A, B),
+// (C, opacity, tz, g), (r, g, b, 0); depth key (the bits of tz > 0 order like
+// its values); 1 if it reaches a tile; tile count; tile rectangle and view
+// (i0 | j0 << 16, width in tiles | view << 16).
+__global__ void __launch_bounds__(256) splat_prep_kernel(
     const float *__restrict__ means, const float *__restrict__ scales, const float *__restrict__ quats,
     const float *__restrict__ opac, const float *__restrict__ colors, int64_t n, const float *__restrict__ cams,
-    int n_views, int W, int H, float near, const uint32_t *__restrict__ offsets, uint32_t cap,
-    uint32_t *__restrict__ dkey, uint32_t *__restrict__ tkey, uint32_t *__restrict__ pid,
-    float4 *__restrict__ payload) {
+    int n_views, int W, int H, float near, uint32_t *__restrict__ dkey, uint32_t *__restrict__ live,
+    uint32_t *__restrict__ counts, uint2 *__restrict__ rect, float4 *__restrict__ payload) {
     __shared__ float scam[64 * CAM_F];
     for (int k = threadIdx.x; k < n_views * CAM_F; k += blockDim.x) scam[k] = cams[k];
     __syncthreads();
@@ -196,50 +175,98 @@ __global__ void __launch_bounds__(256) splat_emit_kernel(
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
          g += (int64_t)gridDim.x * blockDim.x) {
         const float al = opac[g];
-        if (!(al > 0.0f)) continue;
-        uint32_t pos = offsets[g];
         float Rs[9];
-        rot_scale(quats + 4 * g, scales + 3 * g, Rs);
+        if (al > 0.0f) rot_scale(quats + 4 * g, scales + 3 * g, Rs);
         for (int v = 0; v < n_views; ++v) {
-            const Splat sp = make_splat(means + 3 * g, Rs, scam + CAM_F * v, W, H, near);
-            if (!sp.ok) continue;
-            int i0, i1, j0, j1;
-            splat_tiles(sp, ntx, nty, i0, i1, j0, j1);
-            if (i1 == i0 || j1 == j0) continue;
             const size_t sid = (size_t)g * n_views + v;
-            payload[3 * sid] = make_float4(sp.mx, sp.my, sp.A, sp.B);
-            payload[3 * sid + 1] = make_float4(sp.C, al, sp.tz, __int_as_float((int)g));
-            payload[3 * sid + 2] = make_float4(colors[3 * g], colors[3 * g + 1], colors[3 * g + 2], 0.0f);
-            for (int i = i0; i < i1; ++i)
-                for (int j = j0; j < j1; ++j, ++pos) {
-                    if (pos >= cap) continue;
-                    dkey[pos] = __float_as_uint(sp.tz);  // tz > 0: the bits order like the values
-                    tkey[pos] = (uint32_t)((v * nty + i) * ntx + j);
-                    pid[pos] = (uint32_t)sid;
+            uint32_t key = 0xffffffffu, c = 0u;
+            uint2 rc = make_uint2(0u, 0u);
+            if (al > 0.0f) {
+                const Splat sp = make_splat(means + 3 * g, Rs, scam + CAM_F * v, W, H, near);
+                if (sp.ok) {
+                    int i0, i1, j0, j1;
+                    splat_tiles(sp, ntx, nty, i0, i1, j0, j1);
+                    if (i1 > i0 && j1 > j0) {
+                        key = __float_as_uint(sp.tz);
+                        c = (uint32_t)((i1 - i0) * (j1 - j0));
+                        rc = make_uint2((uint32_t)i0 | ((uint32_t)j0 << 16), (uint32_t)(j1 - j0) | ((uint32_t)v << 16));
+                        payload[3 * sid] = make_float4(sp.mx, sp.my, sp.A, sp.B);
+                        payload[3 * sid + 1] = make_float4(sp.C, al, sp.tz, __int_as_float((int)g));
+                        payload[3 * sid + 2] = make_float4(colors[3 * g], colors[3 * g + 1], colors[3 * g + 2], 0.0f);
+                    }
                 }
+            }
+            dkey[sid] = key;
+            live[sid] = c > 0u ? 1u : 0u;
+            counts[sid] = c;
+            rect[sid] = rc;
         }
     }
 }
 
-// After the depth sort (values: pair positions): the tile key and the splat
-// index of each sorted pair.
-__global__ void gather_keys_kernel(const uint32_t *__restrict__ order, const uint32_t *__restrict__ tkey_by_pos,
-                                   const uint32_t *__restrict__ sid_by_pos, const unsigned long long *__restrict__ d_n,
-                                   uint32_t *__restrict__ tkey_out, uint32_t *__restrict__ sid_out) {
-    const unsigned long long n = *d_n;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint32_t p = order[i];
-        tkey_out[i] = tkey_by_pos[p];
-        sid_out[i] = sid_by_pos[p];
+// The splats that reach a tile, in index order (pos: exclusive scan of the
+// flags): their depth keys and indices, for the depth sort.
+__global__ void compact_splats_kernel(const uint32_t *__restrict__ dkey, const uint32_t *__restrict__ counts,
+                                      const uint32_t *__restrict__ pos, int64_t ns, uint32_t *__restrict__ ckey,
+                                      uint32_t *__restrict__ csid) {
+    for (int64_t sid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sid < ns;
+         sid += (int64_t)gridDim.x * blockDim.x) {
+        if (counts[sid] == 0u) continue;
+        const uint32_t k = pos[sid];
+        ckey[k] = dkey[sid];
+        csid[k] = (uint32_t)sid;
     }
 }
 
-__global__ void iota_kernel(const unsigned long long *__restrict__ d_n, uint32_t *__restrict__ out) {
-    const unsigned long long n = *d_n;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x)
-        out[i] = (uint32_t)i;
+// Tile counts of the splats in depth order (0 past the nv live splats).
+__global__ void sorted_counts_kernel(const uint32_t *__restrict__ order, const uint32_t *__restrict__ counts,
+                                     const unsigned long long *__restrict__ d_nv, int64_t ns,
+                                     uint32_t *__restrict__ out) {
+    const int64_t nv = (int64_t)*d_nv;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < ns; r += (int64_t)gridDim.x * blockDim.x)
+        out[r] = r < nv ? counts[order[r]] : 0u;
+}
+
+// The pairs of the splats in depth order: block b takes PAIR_T consecutive
+// splats and spreads their pairs over its threads (each finds its splat by a
+// binary search of the splats' offsets in shared memory), so a splat over
+// thousands of tiles does not hold one thread.  Pairs of one splat run over
+// its tile rectangle row by row.
+constexpr int PAIR_T = 256;
+__global__ void __launch_bounds__(PAIR_T) splat_pairs_kernel(
+    const uint32_t *__restrict__ order, const uint32_t *__restrict__ off, const uint2 *__restrict__ rect,
+    int64_t ns, const unsigned long long *__restrict__ d_nv, const unsigned long long *__restrict__ d_total,
+    int ntx, int nty, uint32_t *__restrict__ tkey, uint32_t *__restrict__ pid) {
+    __shared__ uint32_t s_off[PAIR_T + 1];
+    __shared__ uint32_t s_sid[PAIR_T];
+    const uint32_t P = (uint32_t)*d_total;
+    const int64_t nv = (int64_t)*d_nv;
+    const int tid = threadIdx.x;
+    for (int64_t base = (int64_t)blockIdx.x * PAIR_T; base < ns; base += (int64_t)gridDim.x * PAIR_T) {
+        __syncthreads();  // the previous range is no longer read
+        const int64_t r = base + tid;
+        s_off[tid] = r < ns ? off[r] : P;
+        s_sid[tid] = r < nv ? order[r] : 0u;
+        if (tid == 0) s_off[PAIR_T] = base + PAIR_T < ns ? off[base + PAIR_T] : P;
+        __syncthreads();
+        const uint32_t p1 = s_off[PAIR_T];
+        for (uint32_t p = s_off[0] + tid; p < p1; p += PAIR_T) {
+            // the last splat of the block whose offset is <= p (splats without
+            // pairs share the offset of the next one and come before it)
+            int lo = 0, hi = PAIR_T - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= p) lo = mid; else hi = mid - 1;
+            }
+            const uint32_t sid = s_sid[lo], local = p - s_off[lo];
+            const uint2 rc = rect[sid];
+            const uint32_t i0 = rc.x & 0xffffu, j0 = rc.x >> 16, w = rc.y & 0xffffu, v = rc.y >> 16;
+            const uint32_t di = local / w;
+            const uint32_t i = i0 + di, j = j0 + (local - di * w);
+            tkey[p] = (v * (uint32_t)nty + i) * (uint32_t)ntx + j;
+            pid[p] = sid;
+        }
+    }
 }
 
 __global__ void splat_ranges_kernel(const uint32_t *__restrict__ keys, const unsigned long long *__restrict__ d_n,
@@ -400,64 +427,84 @@ int render_impl(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     const int ntx = (W + RT - 1) / RT, nty = (H + RT - 1) / RT;
     const int64_t n_tiles = (int64_t)n_views * ntx * nty;
     int rc;
-    void *w_cnt, *w_rng;
-    if ((rc = ws_reserve(ctx, WS_COUNTS, sizeof(uint32_t) * (size_t)std::max<int64_t>(n, 1), &w_cnt))) return rc;
-    // per-tile [start, end), then the 8-byte pair counter
+    const int64_t ns = n * n_views;  // splats
+    void *w_rng;
+    // per-tile [start, end), then the 8-byte pair and splat counters
     const size_t rng_bytes = (2 * sizeof(uint32_t) * (size_t)n_tiles + 7) & ~(size_t)7;
-    if ((rc = ws_reserve(ctx, WS_RANGES, rng_bytes + sizeof(unsigned long long), &w_rng))) return rc;
+    if ((rc = ws_reserve(ctx, WS_RANGES, rng_bytes + 2 * sizeof(unsigned long long), &w_rng))) return rc;
     uint32_t *ts = (uint32_t *)w_rng, *te = ts + n_tiles;
     unsigned long long *d_total = (unsigned long long *)((char *)w_rng + rng_bytes);
-    cudaError_t e = cudaMemsetAsync(w_rng, 0, rng_bytes + sizeof(unsigned long long), s);
+    unsigned long long *d_ns = d_total + 1;
+    cudaError_t e = cudaMemsetAsync(w_rng, 0, rng_bytes + 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "render: memset");
     uint64_t P = 0;
     const uint32_t *order = nullptr;     // splat of each sorted pair
     const float4 *payload = nullptr;     // per-splat payloads
     const int grid = (int)std::min<int64_t>((std::max<int64_t>(n, 1) + 255) / 256, (int64_t)ctx->num_sms * 16);
+    uint32_t *sorder = nullptr, *soff = nullptr;
+    const uint2 *rect = nullptr;
     if (n > 0) {
-        splat_count_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, n, cams, n_views, W, H, near,
-                                                (uint32_t *)w_cnt);
+        // splats: depth keys and indices (sorted in place, with alternates),
+        // tile counts (then their offsets in depth order), rectangles, payloads
+        void *dk, *dv, *dk2, *dv2, *w_cnt, *w_spl;
+        const size_t nsz = (size_t)ns;
+        if ((rc = ws_reserve(ctx, WS_CKEYS_A, sizeof(uint32_t) * nsz, &dk))) return rc;
+        if ((rc = ws_reserve(ctx, WS_CVALS_A, sizeof(uint32_t) * nsz, &dv))) return rc;
+        if ((rc = ws_reserve(ctx, WS_CKEYS_B, sizeof(uint32_t) * nsz, &dk2))) return rc;
+        if ((rc = ws_reserve(ctx, WS_CVALS_B, sizeof(uint32_t) * nsz, &dv2))) return rc;
+        if ((rc = ws_reserve(ctx, WS_COUNTS, 2 * sizeof(uint32_t) * nsz, &w_cnt))) return rc;
+        if ((rc = ws_reserve(ctx, WS_RENDER, (3 * sizeof(float4) + sizeof(uint2)) * nsz, &w_spl))) return rc;
+        uint32_t *cnt = (uint32_t *)w_cnt;
+        soff = cnt + nsz;
+        float4 *pl = (float4 *)w_spl;
+        uint2 *rc2 = (uint2 *)(pl + 3 * nsz);
+        // keys by splat in dk, live flags in dk2 (then their scan); the live
+        // splats' keys and indices compacted into dv2 and dv, sorted with dk
+        // and dk2 as the alternates
+        splat_prep_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, colors, n, cams, n_views, W, H, near,
+                                               (uint32_t *)dk, (uint32_t *)dk2, cnt, rc2, pl);
         e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "splat_count_kernel");
-        if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_cnt, (uint32_t *)w_cnt, n, d_total, s))) return rc;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "splat_prep_kernel");
+        if ((rc = scan_exclusive_u32(ctx, (uint32_t *)dk2, (uint32_t *)dk2, ns, d_ns, s))) return rc;
+        const int sgrid0 = (int)std::min<int64_t>((ns + 255) / 256, (int64_t)ctx->num_sms * 16);
+        compact_splats_kernel<<<sgrid0, 256, 0, s>>>((const uint32_t *)dk, cnt, (const uint32_t *)dk2, ns,
+                                                     (uint32_t *)dv2, (uint32_t *)dv);
+        uint32_t *keys = (uint32_t *)dv2, *vals = (uint32_t *)dv;
+        if ((rc = radix_sort_pairs(ctx, &keys, &vals, (uint32_t *)dk, (uint32_t *)dk2, d_ns, ns, 32, s)))
+            return rc;
+        sorder = vals;
+        sorted_counts_kernel<<<sgrid0, 256, 0, s>>>(sorder, cnt, d_ns, ns, soff);
+        if ((rc = scan_exclusive_u32(ctx, soff, soff, ns, d_total, s))) return rc;
         e = cudaMemcpyAsync(ctx->h_pinned, d_total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "render: pair count");
         P = ctx->h_pinned[0];
         if (P >= (1ull << 31)) return fail(ctx, DGSM_ERR_WORKSPACE, "render: more than 2^31 pairs");
+        rect = rc2;
+        payload = pl;
     }
     if (n_pairs_out) *n_pairs_out = (int64_t)P;
     if (P > 0) {
-        void *ka, *va, *kb, *vb, *tk, *sk, *pl;
+        void *ka, *va, *kb, *vb;
         if ((rc = ws_reserve(ctx, WS_KEYS_A, sizeof(uint32_t) * P, &ka))) return rc;
         if ((rc = ws_reserve(ctx, WS_VALS_A, sizeof(uint32_t) * P, &va))) return rc;
         if ((rc = ws_reserve(ctx, WS_KEYS_B, sizeof(uint32_t) * P, &kb))) return rc;
         if ((rc = ws_reserve(ctx, WS_VALS_B, sizeof(uint32_t) * P, &vb))) return rc;
-        if ((rc = ws_reserve(ctx, WS_CKEYS_A, sizeof(uint32_t) * P, &tk))) return rc;
-        if ((rc = ws_reserve(ctx, WS_CVALS_A, sizeof(uint32_t) * P, &sk))) return rc;
-        if ((rc = ws_reserve(ctx, WS_RENDER, 3 * sizeof(float4) * (size_t)n * n_views, &pl))) return rc;
-        splat_emit_kernel<<<grid, 256, 0, s>>>(means, scales, quats, opac, colors, n, cams, n_views, W, H, near,
-                                               (const uint32_t *)w_cnt, (uint32_t)P, (uint32_t *)ka,
-                                               (uint32_t *)tk, (uint32_t *)sk, (float4 *)pl);
-        const int rgrid = (int)std::min<int64_t>(((int64_t)P + 255) / 256, (int64_t)ctx->num_sms * 16);
-        iota_kernel<<<rgrid, 256, 0, s>>>(d_total, (uint32_t *)va);
+        const int pgrid = (int)std::min<int64_t>((ns + PAIR_T - 1) / PAIR_T, (int64_t)ctx->num_sms * 16);
+        splat_pairs_kernel<<<pgrid, PAIR_T, 0, s>>>(sorder, soff, rect, ns, d_ns, d_total, ntx, nty,
+                                                    (uint32_t *)ka, (uint32_t *)va);
         e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "splat_emit_kernel");
-        // front to back within each tile: sort the pair positions by depth,
-        // then (tile, splat) stably by tile
-        uint32_t *keys = (uint32_t *)ka, *vals = (uint32_t *)va;
-        if ((rc = radix_sort_pairs(ctx, &keys, &vals, (uint32_t *)kb, (uint32_t *)vb, d_total, (int64_t)P, 32, s)))
-            return rc;
-        uint32_t *alt_k = keys == (uint32_t *)ka ? (uint32_t *)kb : (uint32_t *)ka;
-        uint32_t *alt_v = vals == (uint32_t *)va ? (uint32_t *)vb : (uint32_t *)va;
-        gather_keys_kernel<<<rgrid, 256, 0, s>>>(vals, (const uint32_t *)tk, (const uint32_t *)sk, d_total, alt_k,
-                                                 alt_v);
-        uint32_t *tkeys = alt_k, *sids = alt_v;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "splat_pairs_kernel");
+        // (tile, splat) pairs in depth order, sorted stably by tile: every
+        // tile's splats front to back
+        uint32_t *tkeys = (uint32_t *)ka, *sids = (uint32_t *)va;
         int bits = 1;
         while (((int64_t)1 << bits) < n_tiles) ++bits;
-        if ((rc = radix_sort_pairs(ctx, &tkeys, &sids, keys, vals, d_total, (int64_t)P, bits, s))) return rc;
+        if ((rc = radix_sort_pairs(ctx, &tkeys, &sids, (uint32_t *)kb, (uint32_t *)vb, d_total, (int64_t)P, bits, s)))
+            return rc;
+        const int rgrid = (int)std::min<int64_t>(((int64_t)P + 255) / 256, (int64_t)ctx->num_sms * 16);
         splat_ranges_kernel<<<rgrid, 256, 0, s>>>(tkeys, d_total, ts, te);
         order = sids;
-        payload = (const float4 *)pl;
     }
     // segments of every tile's list (an empty tile has one empty segment):
     // long enough that a tile's front layers saturate within its first

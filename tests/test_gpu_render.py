@@ -70,6 +70,18 @@ def test_render_empty(nat):
                                 face=12)
 
 
+def test_render_nothing_in_view(nat):
+    """Gaussians that no camera sees (all behind it, or transparent): no
+    splat reaches a tile and the image stays black."""
+    sc = scenes.cube_scene(500, seed=9, centre=(0.0, 0.0, 3.0), side=2.0)
+    sc.opac[:100] = 0.0
+    d = scene_to_dev(sc)
+    cam = scenes.look_at_camera([0, 0, 0], [1.0, 0, 0], 32, 24, 60.0)   # the cube is 63 degrees above the view axis
+    rgb, P = nat.dgsm_render_views(d["means"], d["scales"], d["quats"], d["opac"], d["colors"], dev(cam[None]),
+                                   32, 24, want_pairs=True)
+    assert P == 0 and (rgb == 0).all()
+
+
 def test_cube_dirs_and_solid_angles(nat, orc):
     face = 16
     dirs, w = nat.dgsm_cube_dirs(face)

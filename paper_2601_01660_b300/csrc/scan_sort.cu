@@ -95,7 +95,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_apply_kernel(const uint32_t
 // ---------------------------------------------------------------------------
 // Radix sort: 8-bit digits; one block sorts a segment of 16 rounds x 256
 // items.  Stability comes from ranking each round's items in thread order
-// (warp match + per-warp digit counts) on top of the running digit offsets.
+// (warp match + per-warp digit counts) on top of the running digit counts;
+// the segment is ordered in shared memory and written out run by run.
 // ---------------------------------------------------------------------------
 constexpr int RS_THREADS = 256;
 constexpr int RS_ROUNDS = 16;
@@ -122,22 +123,49 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
     const unsigned long long *d_n, int shift, const uint32_t *__restrict__ offs, int nb) {
-    __shared__ uint32_t base[256];
-    const int64_t n = (int64_t)*d_n;
+    // The block's segment is first put in digit order in shared memory (each
+    // round's items ranked in thread order on top of the running digit
+    // counts), then written out: consecutive threads write consecutive items
+    // of one digit's run, so the stores coalesce.
+    __shared__ uint32_t gbase[256];   // global start of each digit's run of this block
+    __shared__ uint32_t lstart[256];  // start of each digit's run in the block's order
+    __shared__ uint32_t lrun[256];    // items of each digit placed so far
+    __shared__ uint32_t wsum[RS_WARPS];
     __shared__ uint32_t wcnt[RS_WARPS][256];
+    __shared__ uint32_t sk[RS_SEG], sv[RS_SEG];
+    const int64_t n = (int64_t)*d_n;
+    const int64_t seg = (int64_t)blockIdx.x * RS_SEG;
+    if (seg >= n) return;  // uniform across the block
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    base[tid] = offs[(int64_t)tid * nb + blockIdx.x];
-    const int64_t seg = (int64_t)blockIdx.x * RS_SEG;
+    // offsets are digit-major ([digit][block]), so the block's count of digit
+    // tid is the next entry minus this one (the total n after the last)
+    const int64_t e = (int64_t)tid * nb + blockIdx.x;
+    const uint32_t o = offs[e];
+    const uint32_t c = (tid == 255 && blockIdx.x == nb - 1 ? (uint32_t)n : offs[e + 1]) - o;
+    gbase[tid] = o;
+    uint32_t x = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t add = 0;
+    for (int w = 0; w < warp; ++w) add += wsum[w];
+    lstart[tid] = x - c + add;
+    lrun[tid] = 0;
+    const int seg_n = (int)min((int64_t)RS_SEG, n - seg);
     for (int r = 0; r < RS_ROUNDS; ++r) {
-        if (seg + r * RS_THREADS >= n) break;  // uniform across the block
+        if (r * RS_THREADS >= seg_n) break;  // uniform across the block
 #pragma unroll
         for (int w = 0; w < RS_WARPS; ++w) wcnt[w][tid] = 0;
         __syncthreads();
-        const int64_t i = seg + r * RS_THREADS + tid;
-        const bool valid = i < n;
-        const uint32_t k = valid ? keys_in[i] : 0u;
-        const uint32_t v = valid ? vals_in[i] : 0u;
+        const int li = r * RS_THREADS + tid;
+        const bool valid = li < seg_n;
+        const uint32_t k = valid ? keys_in[seg + li] : 0u;
+        const uint32_t v = valid ? vals_in[seg + li] : 0u;
         const int d = valid ? (int)((k >> shift) & 255u) : 256 + lane;
         const unsigned m = __match_any_sync(0xffffffffu, d);
         const int rank = __popc(m & lt_mask);
@@ -146,18 +174,26 @@ __global__ void __launch_bounds__(RS_THREADS) radix_scatter_kernel(
         uint32_t run = 0;
 #pragma unroll
         for (int w = 0; w < RS_WARPS; ++w) {
-            uint32_t c = wcnt[w][tid];
+            const uint32_t cw = wcnt[w][tid];
             wcnt[w][tid] = run;
-            run += c;
+            run += cw;
         }
         __syncthreads();
         if (valid) {
-            uint32_t dst = base[d] + wcnt[warp][d] + (uint32_t)rank;
-            keys_out[dst] = k;
-            vals_out[dst] = v;
+            const uint32_t pos = lstart[d] + lrun[d] + wcnt[warp][d] + (uint32_t)rank;
+            sk[pos] = k;
+            sv[pos] = v;
         }
         __syncthreads();
-        base[tid] += run;
+        lrun[tid] += run;
+    }
+    __syncthreads();
+    for (int i = tid; i < seg_n; i += RS_THREADS) {
+        const uint32_t k = sk[i];
+        const int d = (int)((k >> shift) & 255u);
+        const uint32_t dst = gbase[d] + ((uint32_t)i - lstart[d]);
+        keys_out[dst] = k;
+        vals_out[dst] = sv[i];
     }
 }
 

@@ -227,18 +227,22 @@ __global__ void sorted_counts_kernel(const uint32_t *__restrict__ order, const u
         out[r] = r < nv ? counts[order[r]] : 0u;
 }
 
-// The pairs of the splats in depth order: block b takes PAIR_T consecutive
-// splats and spreads their pairs over its threads (each finds its splat by a
-// binary search of the splats' offsets in shared memory), so a splat over
-// thousands of tiles does not hold one thread.  Pairs of one splat run over
-// its tile rectangle row by row.
+// The pairs of the splats in depth order: a block takes PAIR_T consecutive
+// splats and cuts their pairs into tiles of PAIR_T x PAIR_U.  In a tile each
+// thread finds the splat of its first pair by a binary search of the splats'
+// offsets in shared memory, then walks PAIR_U consecutive pairs over the
+// splats' tile rectangles (row by row); the tile is staged in shared memory
+// and stored coalesced.  A splat over thousands of tiles does not hold one
+// thread.
 constexpr int PAIR_T = 256;
+constexpr int PAIR_U = 8;
 __global__ void __launch_bounds__(PAIR_T) splat_pairs_kernel(
     const uint32_t *__restrict__ order, const uint32_t *__restrict__ off, const uint2 *__restrict__ rect,
     int64_t ns, const unsigned long long *__restrict__ d_nv, const unsigned long long *__restrict__ d_total,
     int ntx, int nty, uint32_t *__restrict__ tkey, uint32_t *__restrict__ pid) {
     __shared__ uint32_t s_off[PAIR_T + 1];
     __shared__ uint32_t s_sid[PAIR_T];
+    __shared__ uint32_t s_key[PAIR_T * PAIR_U], s_pid[PAIR_T * PAIR_U];
     const uint32_t P = (uint32_t)*d_total;
     const int64_t nv = (int64_t)*d_nv;
     const int tid = threadIdx.x;
@@ -250,21 +254,53 @@ __global__ void __launch_bounds__(PAIR_T) splat_pairs_kernel(
         if (tid == 0) s_off[PAIR_T] = base + PAIR_T < ns ? off[base + PAIR_T] : P;
         __syncthreads();
         const uint32_t p1 = s_off[PAIR_T];
-        for (uint32_t p = s_off[0] + tid; p < p1; p += PAIR_T) {
-            // the last splat of the block whose offset is <= p (splats without
-            // pairs share the offset of the next one and come before it)
-            int lo = 0, hi = PAIR_T - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_off[mid] <= p) lo = mid; else hi = mid - 1;
+        for (uint32_t t0 = s_off[0]; t0 < p1; t0 += PAIR_T * PAIR_U) {
+            const uint32_t q0 = t0 + (uint32_t)tid * PAIR_U;
+            if (q0 < p1) {
+                // the last splat of the block whose offset is <= q0 (splats
+                // without pairs share the offset of the next one, before it)
+                int lo = 0, hi = PAIR_T - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= q0) lo = mid; else hi = mid - 1;
+                }
+                uint32_t sid = s_sid[lo], left = s_off[lo + 1] - q0;
+                uint2 rc = rect[sid];
+                uint32_t i0 = rc.x & 0xffffu, j0 = rc.x >> 16, w = rc.y & 0xffffu, v = rc.y >> 16;
+                const uint32_t local = q0 - s_off[lo], di = local / w;
+                uint32_t i = i0 + di, j = j0 + (local - di * w);
+                const int nu = (int)min((uint32_t)PAIR_U, p1 - q0);
+                for (int u = 0; u < nu; ++u) {
+                    if (left == 0u) {  // the next splat with pairs
+                        do {
+                            ++lo;
+                        } while (s_off[lo + 1] == s_off[lo]);
+                        sid = s_sid[lo];
+                        left = s_off[lo + 1] - s_off[lo];
+                        rc = rect[sid];
+                        i0 = rc.x & 0xffffu;
+                        j0 = rc.x >> 16;
+                        w = rc.y & 0xffffu;
+                        v = rc.y >> 16;
+                        i = i0;
+                        j = j0;
+                    }
+                    s_key[tid * PAIR_U + u] = (v * (uint32_t)nty + i) * (uint32_t)ntx + j;
+                    s_pid[tid * PAIR_U + u] = sid;
+                    --left;
+                    if (++j == j0 + w) {
+                        j = j0;
+                        ++i;
+                    }
+                }
             }
-            const uint32_t sid = s_sid[lo], local = p - s_off[lo];
-            const uint2 rc = rect[sid];
-            const uint32_t i0 = rc.x & 0xffffu, j0 = rc.x >> 16, w = rc.y & 0xffffu, v = rc.y >> 16;
-            const uint32_t di = local / w;
-            const uint32_t i = i0 + di, j = j0 + (local - di * w);
-            tkey[p] = (v * (uint32_t)nty + i) * (uint32_t)ntx + j;
-            pid[p] = sid;
+            __syncthreads();
+            const uint32_t cnt = min((uint32_t)(PAIR_T * PAIR_U), p1 - t0);
+            for (uint32_t x = (uint32_t)tid; x < cnt; x += PAIR_T) {
+                tkey[t0 + x] = s_key[x];
+                pid[t0 + x] = s_pid[x];
+            }
+            __syncthreads();
         }
     }
 }

@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("beta_mode", C.c_int32), ("atlas_map", C.c_int32)]
 
     @classmethod
-    def make(cls, kappa=1.0, eps_cull=1e-7, tile=8, chunk=128, atlas_dtype="f32", max_pairs=0,
+    def make(cls, kappa=1.0, eps_cull=1e-7, tile=8, chunk=192, atlas_dtype="f32", max_pairs=0,
              beta_mode=2, atlas_map=0):
         p = cls()
         _lib.dgsm_default_params(C.byref(p))
@@ -747,7 +747,7 @@ class capture:
 
 
 def dgsm_autotune_build(means, scales, quats, opac, lights, H, W, radii, tiles=(8, 16),
-                        chunks=(32, 64, 128), reps=3, params=None, ctx: Context | None = None,
+                        chunks=(32, 64, 128, 192), reps=3, params=None, ctx: Context | None = None,
                         stream=None):
     """Measured tile x chunk choice for dgsm_build: (best Params, {(tile, chunk): ms})."""
     ctx = ctx or context(means.device.index)

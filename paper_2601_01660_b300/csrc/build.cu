@@ -1275,7 +1275,9 @@ int check_common(dgsm_ctx *ctx, const float *means, const float *scales, const f
     if (H < 1 || W < 1 || H > 4096 || W > 4096) return fail(ctx, DGSM_ERR_INVALID_ARG, "H, W must be in 1..4096");
     if (!radii || K < 1 || K > 256) return fail(ctx, DGSM_ERR_INVALID_ARG, "K must be in 1..256");
     if (p.tile != 4 && p.tile != 8 && p.tile != 16) return fail(ctx, DGSM_ERR_INVALID_ARG, "tile must be 4, 8 or 16");
-    if (p.chunk < 16 || p.chunk > 128) return fail(ctx, DGSM_ERR_INVALID_ARG, "chunk must be in 16..128");
+    // the staging loop gives each of the 256 threads three of a chunk's
+    // 4-float4 records: at most 3 x 256 / 4 = 192 records
+    if (p.chunk < 16 || p.chunk > 192) return fail(ctx, DGSM_ERR_INVALID_ARG, "chunk must be in 16..192");
     if (!(p.kappa >= 0.f) || !(p.eps_cull > 0.f)) return fail(ctx, DGSM_ERR_INVALID_ARG, "kappa >= 0 and eps_cull > 0 required");
     if (p.beta_mode < 1 || p.beta_mode > 4) return fail(ctx, DGSM_ERR_INVALID_ARG, "beta_mode must be 1..4");
     if (p.atlas_map != MAP_OCTA && p.atlas_map != MAP_CUBE) return fail(ctx, DGSM_ERR_INVALID_ARG, "atlas_map must be 0 or 1");

@@ -64,7 +64,8 @@ def test_binning_light_inside_and_beyond_shells(nat, orc):
 
 
 @pytest.mark.parametrize("H,W,tile,K,chunk", [(44, 60, 8, 12, 64), (32, 32, 16, 7, 16),
-                                               (20, 36, 8, 5, 16), (40, 24, 8, 9, 32)])
+                                               (20, 36, 8, 5, 16), (40, 24, 8, 9, 32), (48, 40, 8, 10, 192),
+                                               (32, 48, 16, 6, 160)])
 def test_build_matches_oracle_every_voxel(nat, orc, H, W, tile, K, chunk):
     """Small chunks cut long tile lists into several work items, so this also
     covers the cross-item accumulation."""
@@ -149,6 +150,8 @@ def test_bad_arguments_are_rejected(nat):
     assert ei.value.code == 1
     with pytest.raises(nat.DGSMError):
         _build(nat, sc, np.float32([[0, 0, 0]]), 16, 16, scenes.radii_linear(0.1, 8, 4), chunk=4)
+    with pytest.raises(nat.DGSMError):   # three staging loads per thread hold at most 192 records
+        _build(nat, sc, np.float32([[0, 0, 0]]), 16, 16, scenes.radii_linear(0.1, 8, 4), chunk=193)
     with pytest.raises(nat.DGSMError):   # 4x4 tiles: binning only
         _build(nat, sc, np.float32([[0, 0, 0]]), 16, 16, scenes.radii_linear(0.1, 8, 4), tile=4)
 

@@ -57,7 +57,7 @@ enum dgsm_dtype { DGSM_F32 = 0, DGSM_F16 = 1, DGSM_BF16 = 2 };
  * tile: atlas tile edge in texels for light-space binning: 8 or 16 for
  * dgsm_build (default 8, the paper's 8x8 tiles), also 4 for dgsm_bin.
  * chunk: Gaussians staged in shared memory per round, 16..192 (default 192);
- * a tile's list is processed in work items of at most 16 chunks.
+ * a tile's list is processed in work items of at most 8 chunks.
  * atlas_dtype: storage type of T (dgsm_dtype; tau is always accumulated in
  * float32).
  * max_pairs: 0 (default) sizes the pair buffers from the exact pair counts,

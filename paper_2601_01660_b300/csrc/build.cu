@@ -38,7 +38,7 @@ constexpr int REC_F4 = 4;      // float4 per build record
 constexpr int BT_THREADS = 256;
 constexpr int BT_WARPS = BT_THREADS / 32;
 constexpr int QCAP = 96;       // per-warp queue of hits: (a, d'.w', |w' x d'|^2, record/texel id)
-constexpr int ITEM_CHUNKS = 16;  // a work item holds at most ITEM_CHUNKS * chunk Gaussians
+constexpr int ITEM_CHUNKS = 8;   // a work item holds at most ITEM_CHUNKS * chunk Gaussians
 #ifndef DGSM_BT_MIN_BLOCKS
 #define DGSM_BT_MIN_BLOCKS 4        // resident build blocks per SM the register budget targets
 #endif

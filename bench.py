@@ -568,31 +568,57 @@ def run_e2e(nat, wl, args, evals):
 
 # ----------------------------------------------------------------------------- oracle
 
-def oracle_step(wl, lij, q_idx, r_idx):
-    """One bounded sample of the step on the FP64 oracle: the build at texels lij,
-    attenuation of queries q_idx, the full SH fit, relight of avatar Gaussians r_idx."""
+def oracle_step(wl, lij, q_idx, r_idx, atlas=None):
+    """One bounded sample of the step on the FP64 oracle, extrapolated to the
+    whole step: the build at texels lij (its per-call setup over every
+    Gaussian timed alone, with no texel, so that it counts once; the texels,
+    a whole number of waves of the oracle's threads, give the per-texel cost
+    for every texel), attenuation of queries q_idx (scaled to every
+    receiver), the full SH fit, relight of avatar Gaussians r_idx (scaled to
+    the whole avatar).  `atlas` is an all-ones array of the atlas shape,
+    allocated outside the timing; it is restored before return.  Returns
+    (full-step seconds, seconds the sample took)."""
     import oracle
     from paper_2601_01660_b300 import scenes
     sc, lights, radii, H, W = wl["occluders"], wl["lights"], wl["radii"], wl["H"], wl["W"]
+    L, K = lights.shape[0], radii.shape[0]
+    if atlas is None:
+        atlas = np.ones((L, K, H, W))
+    n = lij.shape[0]
     t0 = time.perf_counter()
-    tau = oracle.build_tau_texels(sc, lights, H, W, radii, lij)
+    oracle.build_tau_texels(sc, lights, H, W, radii, lij[:0])
     t1 = time.perf_counter()
+    tau = oracle.build_tau_texels(sc, lights, H, W, radii, lij)
+    t2 = time.perf_counter()
+    setup = t1 - t0
+    per_texel = max((t2 - t1) - setup, 0.0) / max(n, 1)
+    build_full = setup + per_texel * L * H * W
     # attenuate the sampled queries against an atlas that holds the sampled texels
-    K = radii.shape[0]
-    atlas = np.ones((lights.shape[0], K, H, W))
     atlas[lij[:, 0], :, lij[:, 1], lij[:, 2]] = np.exp(-tau)
     q = scenes.subset(sc, q_idx)
+    t3 = time.perf_counter()
     oracle.attenuate(atlas, radii, lights, q.means, q.colors)
-    t2 = time.perf_counter()
+    t4 = time.perf_counter()
+    atlas[lij[:, 0], :, lij[:, 1], lij[:, 2]] = 1.0
     D, Y, w = wl["cubemap"]
     shc = oracle.sh_fit(D, Y, w)
+    t5 = time.perf_counter()
     av = scenes.subset(sc, r_idx)
     oracle.relight(shc, av, av.means.astype(np.float64).mean(0))
-    t3 = time.perf_counter()
-    return t1 - t0, t2 - t1, t3 - t2
+    t6 = time.perf_counter()
+    sl = sc.meta["avatar"]
+    full = (build_full + (t4 - t3) * sc.n / max(q_idx.size, 1) + (t5 - t4)
+            + (t6 - t5) * (sl.stop - sl.start) / max(r_idx.size, 1))
+    return full, t6 - t0
 
 
 def _oracle_sample(wl, n_texels, seed=0):
+    """Random texels (a whole number of waves of the oracle's threads, so the
+    timed sample keeps every core busy as the full build would), and matching
+    fractions of the receivers and of the avatar."""
+    import oracle
+    cores = max(1, oracle.num_threads())
+    n_texels = -(-max(n_texels, cores) // cores) * cores
     rng = np.random.default_rng(seed)
     sc = wl["occluders"]
     H, W, L = wl["H"], wl["W"], wl["lights"].shape[0]
@@ -608,22 +634,37 @@ def _oracle_sample(wl, n_texels, seed=0):
     return lij, q_idx, r_idx, frac
 
 
+def _oracle_eval_count(wl, stride=16):
+    """Gaussian-ray evaluations of the whole build, estimated on the oracle
+    from a regular grid of texels (every stride-th row and column of every
+    light's atlas): counting is far cheaper than evaluating, so the count's
+    sample can be much larger than the timed one."""
+    import oracle
+    H, W, L = wl["H"], wl["W"], wl["lights"].shape[0]
+    ii, jj = np.meshgrid(np.arange(stride // 2, H, stride), np.arange(stride // 2, W, stride), indexing="ij")
+    lij = np.concatenate([np.stack([np.full(ii.size, l), ii.ravel(), jj.ravel()], 1) for l in range(L)])
+    lij = lij.astype(np.int32)
+    n = oracle.count_ray_evals(wl["occluders"], wl["lights"], H, W, wl["radii"], lij)
+    return n * (L * H * W) / lij.shape[0], lij.shape[0]
+
+
 def cpu_baseline(wl, evals_full, n_texels):
     """The oracle (FP64 brute force, OpenMP on the host cores) on a bounded
     sample of the step, scaled to the metric's unit."""
     import oracle
     lij, q_idx, r_idx, frac = _oracle_sample(wl, n_texels)
-    tb, ta, tr = oracle_step(wl, lij, q_idx, r_idx)
-    sample_evals = oracle.count_ray_evals(wl["occluders"], wl["lights"], wl["H"], wl["W"],
-                                          wl["radii"], lij)
-    t_full = (tb + ta) / frac + tr
-    value = sample_evals / frac / t_full
+    n_texels = lij.shape[0]
+    t_full, t_sample = oracle_step(wl, lij, q_idx, r_idx)
+    evals_est, n_count = _oracle_eval_count(wl)
+    value = evals_est / t_full
     return {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": (f"{n_texels} random texels of the 512x512x64 build x all 1.6M Gaussians x 64 "
-                       f"shells, {q_idx.size} attenuated queries, {r_idx.size} relit avatar "
-                       f"Gaussians, full SH fit; extrapolated to the full step "
-                       f"({t_full:.0f} s); {sample_evals} Gaussian-ray evals in the sample"),
-            "sample_seconds": round(tb + ta + tr, 2), "evals_full_gpu_count": int(evals_full)}
+                       f"shells (setup and per-texel cost timed apart), {q_idx.size} attenuated "
+                       f"queries, {r_idx.size} relit avatar Gaussians, full SH fit; each part "
+                       f"extrapolated to the full step ({t_full:.0f} s); the step's "
+                       f"Gaussian-ray evals ({evals_est:.3g}) counted by the oracle on a "
+                       f"{n_count}-texel grid"),
+            "sample_seconds": round(t_sample, 2), "evals_full_gpu_count": int(evals_full)}
 
 
 def run_reference(args, rank, world):
@@ -633,18 +674,25 @@ def run_reference(args, rank, world):
     import oracle
     wl = load_workload(0)
     # keep the whole --steps/--warmup run to a couple of minutes
-    n_tex = max(2, min(args.cpu_texels, 384 // max(1, args.steps)))
-    lij, q_idx, r_idx, frac = _oracle_sample(wl, n_tex)
-    sample_evals = oracle.count_ray_evals(wl["occluders"], wl["lights"], wl["H"], wl["W"],
-                                          wl["radii"], lij)
+    # as many waves of the oracle's threads per step (1 to 4) as keep the
+    # timed steps near 150 s: one wave, timed once here, sets the pace (a
+    # single wave runs at the pace of its slowest thread, so more waves
+    # measure the build's per-texel cost more fairly)
+    cores = max(1, oracle.num_threads())
+    lij1, _, _, _ = _oracle_sample(wl, cores)
+    t0 = time.perf_counter()
+    oracle.build_tau_texels(wl["occluders"], wl["lights"], wl["H"], wl["W"], wl["radii"], lij1)
+    t_wave = max(time.perf_counter() - t0, 1e-3)
+    waves = int(min(4, max(1, 150.0 / (max(1, args.steps) * t_wave))))
+    lij, q_idx, r_idx, frac = _oracle_sample(wl, waves * cores)
+    n_tex = lij.shape[0]
+    evals_est, n_count = _oracle_eval_count(wl)
+    atlas = np.ones((wl["lights"].shape[0], wl["radii"].shape[0], wl["H"], wl["W"]))
     for _ in range(args.warmup):
-        oracle_step(wl, lij[:2], q_idx[:2], r_idx[:1])
-    times = []
-    for _ in range(args.steps):
-        tb, ta, tr = oracle_step(wl, lij, q_idx, r_idx)
-        times.append((tb + ta) / frac + tr)
+        oracle_step(wl, lij[:0], q_idx[:1], r_idx[:1], atlas)
+    times = [oracle_step(wl, lij, q_idx, r_idx, atlas)[0] for _ in range(args.steps)]
     t_full = statistics.mean(times)
-    value = sample_evals / frac / t_full
+    value = evals_est / t_full
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_full * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -653,8 +701,10 @@ def run_reference(args, rank, world):
                        "atlas": [wl["H"], wl["W"], wl["radii"].shape[0]]},
             "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": value,
                              "sample": (f"{n_tex} random texels of the 512x512x64 build x all "
-                                        f"Gaussians x 64 shells per step, matching fractions of the "
-                                        f"attenuation and relight, full SH fit; extrapolated")},
+                                        f"Gaussians x 64 shells per step (setup and per-texel cost "
+                                        f"timed apart), matching fractions of the attenuation and "
+                                        f"relight, full SH fit; each part extrapolated; the step's "
+                                        f"evals counted by the oracle on a {n_count}-texel grid")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

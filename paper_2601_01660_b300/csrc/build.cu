@@ -1410,7 +1410,9 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     if ((rc = ws_reserve(ctx, WS_FOFF, sizeof(uint32_t) * nf, &w_foff))) return rc;
     e = cudaMemsetAsync(w_fcnt, 0, sizeof(uint32_t) * nf, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "build: memset");
-    const int fgrid = (int)std::min<int64_t>(max_units, (int64_t)ctx->num_sms * 8);
+    // many more blocks than fit at once: units differ in cost, and the block
+    // scheduler balances them (binning 2.70 ms with 8 blocks per SM, 2.45 with 64)
+    const int fgrid = (int)std::min<int64_t>(max_units, (int64_t)ctx->num_sms * 64);
     void *w_fmask;
     if ((rc = ws_reserve(ctx, WS_FMASK, sizeof(uint32_t) * 3 * MASK_WORDS * nf, &w_fmask))) return rc;
     fine_count_kernel<<<fgrid, 256, 0, s>>>(units, d_units, cvals, (const BinRec *)w_bin, N, tx, ty, sx, n_tiles,

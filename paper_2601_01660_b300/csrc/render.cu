@@ -526,7 +526,7 @@ int render_impl(dgsm_ctx *ctx, const float *means, const float *scales, const fl
         if ((rc = ws_reserve(ctx, WS_VALS_A, sizeof(uint32_t) * P, &va))) return rc;
         if ((rc = ws_reserve(ctx, WS_KEYS_B, sizeof(uint32_t) * P, &kb))) return rc;
         if ((rc = ws_reserve(ctx, WS_VALS_B, sizeof(uint32_t) * P, &vb))) return rc;
-        const int pgrid = (int)std::min<int64_t>((ns + PAIR_T - 1) / PAIR_T, (int64_t)ctx->num_sms * 16);
+        const int pgrid = (int)std::min<int64_t>((ns + PAIR_T - 1) / PAIR_T, (int64_t)ctx->num_sms * 64);
         splat_pairs_kernel<<<pgrid, PAIR_T, 0, s>>>(sorder, soff, rect, ns, d_ns, d_total, ntx, nty,
                                                     (uint32_t *)ka, (uint32_t *)va);
         e = cudaGetLastError();
@@ -559,7 +559,9 @@ int render_impl(dgsm_ctx *ctx, const float *means, const float *scales, const fl
     seg_count_kernel<<<tgrid, 256, 0, s>>>(ts, te, n_tiles, seg, seg_cnt);
     if ((rc = scan_exclusive_u32(ctx, seg_cnt, seg_off, n_tiles, d_nseg, s))) return rc;
     seg_fill_kernel<<<tgrid, 256, 0, s>>>(ts, te, n_tiles, seg, seg_off, segs);
-    const int sgrid = (int)std::min<int64_t>(max_segs, (int64_t)ctx->num_sms * 16);
+    // more blocks than fit at once, so the block scheduler balances segments of
+    // different cost
+    const int sgrid = (int)std::min<int64_t>(max_segs, (int64_t)ctx->num_sms * 64);
     splat_segment_kernel<<<sgrid, RT_PIX, 0, s>>>(segs, d_nseg, order, payload, W, H, (float4 *)w_part);
     splat_merge_kernel<<<(int)((n_tiles * RT_PIX + 255) / 256), 256, 0, s>>>(seg_cnt, seg_off, (const float4 *)w_part,
                                                                               n_tiles, W, H, rgb_out);

@@ -56,7 +56,7 @@ enum dgsm_dtype { DGSM_F32 = 0, DGSM_F16 = 1, DGSM_BF16 = 2 };
  * kappa * alpha/(1-alpha) * (s_max/s_min) / eps_cull.
  * tile: atlas tile edge in texels for light-space binning: 8 or 16 for
  * dgsm_build (default 8, the paper's 8x8 tiles), also 4 for dgsm_bin.
- * chunk: Gaussians staged in shared memory per round, 16..192 (default 192);
+ * chunk: Gaussians staged in shared memory per round, 16..192 (default 128);
  * a tile's list is processed in work items of at most 8 chunks.
  * atlas_dtype: storage type of T (dgsm_dtype; tau is always accumulated in
  * float32).
@@ -621,6 +621,17 @@ int nf_attenuate(dgsm_ctx *ctx, const float *params, const uint8_t *mask, const 
                  int32_t tile, const float *lights, const float *q_means, const float *colors_in,
                  int64_t n_q, const float *light_w, float direct_frac, float *colors_out,
                  float *T_out, void *stream);
+
+/* Measured single-precision ALU peaks of the context's GPU, the roofline
+ * denominators of the build's tile kernel (its closed form of Eq. 3 is bound
+ * by FP32 and special-function issue, not by memory).  out (host, 4
+ * doubles): [0] FP32 fused multiply-add lane operations per second, [1]
+ * ex2.approx, [2] rcp.approx, [3] rsqrt.approx lane operations per second.
+ * Each comes from a kernel that fills every SM with independent dependency
+ * chains of that one instruction, timed with CUDA events on `stream` (best
+ * of three after one warm-up launch, about 0.5 s in all) at whatever SM
+ * clock the GPU runs; nothing is changed on the GPU.  Blocks until done. */
+int dgsm_measure_alu_peaks(dgsm_ctx *ctx, double *out, void *stream);
 
 /* Reads and clears the context's device status word (blocks on `stream`):
  * returns DGSM_OK or the first error a kernel recorded since the last call. */

@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("beta_mode", C.c_int32), ("atlas_map", C.c_int32)]
 
     @classmethod
-    def make(cls, kappa=1.0, eps_cull=1e-7, tile=8, chunk=192, atlas_dtype="f32", max_pairs=0,
+    def make(cls, kappa=1.0, eps_cull=1e-7, tile=8, chunk=128, atlas_dtype="f32", max_pairs=0,
              beta_mode=2, atlas_map=0):
         p = cls()
         _lib.dgsm_default_params(C.byref(p))
@@ -158,6 +158,7 @@ _lib.dgsm_autotune_build.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _
                                      C.POINTER(Params), _vp, _i32, _vp, _i32, _i32, _vp,
                                      C.POINTER(Params), _vp, _vp]
 _lib.dgsm_set_profiling.argtypes = [_vp, C.c_int]
+_lib.dgsm_measure_alu_peaks.argtypes = [_vp, C.POINTER(C.c_double), _vp]
 _lib.dgsm_profile_collect.argtypes = [_vp, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]
 for _fn in ("dgsm_build", "dgsm_get_build_stats", "dgsm_bin", "dgsm_attenuate",
             "dgsm_sample_index", "sh_fit", "sh_relight", "dgsm_sync_status",
@@ -165,7 +166,8 @@ for _fn in ("dgsm_build", "dgsm_get_build_stats", "dgsm_bin", "dgsm_attenuate",
             "dgsm_profile_collect", "sh_fit_static", "nf_init", "nf_loss_grad", "nf_train", "nf_forward",
             "nf_tile_error", "nf_attenuate", "sh_relight_objects", "dgsm_segment_centroids",
             "dgsm_rigid_transform", "dgsm_graph_begin", "dgsm_graph_end", "dgsm_graph_launch",
-            "dgsm_graph_node_count", "dgsm_autotune_build", "dgsm_attenuate_dyn"):
+            "dgsm_graph_node_count", "dgsm_autotune_build", "dgsm_attenuate_dyn",
+            "dgsm_measure_alu_peaks"):
     getattr(_lib, _fn).restype = C.c_int
 
 
@@ -829,6 +831,14 @@ def dgsm_frame_host(means, scales, quats, opac, colors, lights, H, W, radii, cub
 def dgsm_set_profiling(enable: bool, ctx: Context | None = None):
     ctx = ctx or context()
     ctx.check(_lib.dgsm_set_profiling(ctx.handle, int(bool(enable))))
+
+
+def dgsm_measure_alu_peaks(ctx: Context | None = None, stream=None) -> dict:
+    """Measured FP32 and MUFU lane-operation rates of the current GPU (blocks)."""
+    ctx = ctx or context()
+    out = (C.c_double * 4)()
+    ctx.check(_lib.dgsm_measure_alu_peaks(ctx.handle, out, _stream(stream)))
+    return {"fp32_ops_s": out[0], "ex2_ops_s": out[1], "rcp_ops_s": out[2], "rsqrt_ops_s": out[3]}
 
 
 def dgsm_profile_collect(ctx: Context | None = None):

@@ -36,8 +36,6 @@ namespace {
 constexpr int SUPER = 8;       // super-tile edge, in tiles
 constexpr int REC_F4 = 4;      // float4 per build record
 constexpr int BT_THREADS = 256;
-constexpr int BT_WARPS = BT_THREADS / 32;
-constexpr int QCAP = 96;       // per-warp queue of hits: (a, d'.w', |w' x d'|^2, record/texel id)
 constexpr int ITEM_CHUNKS = 8;   // a work item holds at most ITEM_CHUNKS * chunk Gaussians
 #ifndef DGSM_BT_MIN_BLOCKS
 #define DGSM_BT_MIN_BLOCKS 4        // resident build blocks per SM the register budget targets
@@ -933,101 +931,180 @@ __device__ __forceinline__ bool pair_hit(const PairGeom &g, float k2, bool insid
     return g.c2 <= k2 * g.a && (inside || g.pw > 0.0f);
 }
 
-// Eq. 3 for a hit pair at the shells on its chord, as per-shell increments of
-// the optical depth added to D[k * nt + texel].
-__device__ __forceinline__ void eval_shells(const PairGeom &g, const float4 &q3, const float *rs,
-                                            int K, float *D, int nt, int texel, unsigned int &n_shell) {
-    const int packed = __float_as_int(q3.z);
-    const bool inside = (packed >> 20) & 1;
-    const int klo = packed & 1023, kend = (packed >> 10) & 1023;
-    const float ia = rcp_approx(g.a);
-    const float m2 = g.c2 * ia;   // c - b^2/a
-    const float ss = g.pw * ia;   // closest approach s* = -b/a
-    const float rsa = rsqrt_approx(g.a);
-    // The ray's mass outside its chord through the culling ellipsoid,
-    // s in s* +- sqrt((k^2 - m^2)/a), is at most eps_cull (the same bound
-    // as the culling): shells before the chord get nothing, shells after it
-    // the whole remaining mass.  The chord lies inside the sphere window
-    // [klo, kend) of the record.
-    const float c2h = fmaxf(q3.y - m2, 1e-30f);
-    const float half = c2h * rsqrt_approx(c2h) * rsa;
-    const float lo_r = ss - half, hi_r = ss + half;
-    int k = klo;
-    while (k < kend && rs[k] < lo_r) ++k;
-    const float A0 = q3.x * rsa;                 // beta sqrt(pi/(2a))
-    const float h = g.a * rsa * 0.70710678118f;  // sqrt(a/2)
-    const float hm2 = -0.72134752044f * m2;      // -m^2/2 log2(e)
-    const float full = 2.0f * A0 * ex2_approx(hm2);
-    const float hs = h * ss;
-    const float F0 = inside ? mass_below(-hs, A0, hm2, full) : 0.0f;
-    float Gprev = 0.0f;
-    const int k0 = k;
-    float *dk = D + k * nt + texel;
-    for (; k < kend && rs[k] <= hi_r; ++k, dk += nt) {
-        const float G = mass_below(fmaf(h, rs[k], -hs), A0, hm2, full) - F0;
-        atomicAdd(dk, fmaxf(G - Gprev, 0.0f));
-        Gprev = fmaxf(G, Gprev);
-    }
-    n_shell += (unsigned int)(k - k0);
-    if (k < K) atomicAdd(dk, fmaxf(full - F0 - Gprev, 0.0f));
-}
+// ---------------------------------------------------------------------------
+// Build tile kernel (Eqs. 2-4 over one tile's Gaussian list).
+//
+// Candidates.  Inside one face of the atlas map the texel rays of a tile are
+// an affine family d(x, y) = d_c + x E_x + y E_y of the tile-local texel
+// offsets (x, y) from the tile centre: Eq. 6 is affine in (u, v) on each face
+// of the octahedron, and a cube face is a central projection.  The culling
+// test of a pair, |w' x M d|^2 <= k^2 |M d|^2, is homogeneous of degree 2 in
+// d, so over a tile it is a conic Q(x, y) <= 0 whose six coefficients are
+// formed once per (Gaussian, tile), with k^2 widened by CONIC_WIDEN.  Each
+// tile row meets the conic in an interval of texels (two roots of a
+// quadratic): the candidate mask.  Where the expansion about the tile centre
+// could lose the margin to rounding (a Gaussian far smaller than the tile),
+// where the tile spans two faces, or where the light is inside the culling
+// sphere, every texel is a candidate.
+//
+// Evaluation.  The candidates of a staged chunk go to one list, record by
+// record (each thread writes its record's candidates at an offset from a
+// warp scan); warps take 32 consecutive candidates at a time.  A lane tests
+// its candidate exactly (the test above in the Gaussian's whitened frame, as
+// the culling defines it) and evaluates Eq. 3 at the shells on the chord of
+// the hit through the culling ellipsoid.  Consecutive candidates are
+// neighbouring texels of one Gaussian, whose chords cover about as many
+// shells, so the lanes of a warp take their shell loops nearly in step.
+// Increments accumulate per tile in shared memory; the last work item of a
+// tile takes the shell prefix sum and T = exp(-tau) (Eq. 4).
+// ---------------------------------------------------------------------------
+constexpr int SHELL_TB0 = 107 << 23;       // float bits of 2^-20
+constexpr int SHELL_NB = 512;              // 16 buckets per octave over [2^-20, 2^12) metres
+constexpr float CONIC_WIDEN = 1.0f / 32.0f;
+constexpr float CONIC_COND = 1.0f / 8192.0f;
+constexpr unsigned FULLMASK = 0xffffffffu;
 
 size_t build_smem_bytes(int K, int tile, int chunk) {
     const int nt = tile * tile;
-    return (size_t)2 * chunk * REC_F4 * sizeof(float4) + (size_t)nt * sizeof(float4) +
-           (size_t)K * nt * sizeof(float) + (size_t)((K + 3) & ~3) * sizeof(float) +
-           (size_t)BT_WARPS * QCAP * sizeof(float4) + (size_t)2 * chunk;
+    return (size_t)2 * chunk * REC_F4 * sizeof(float4) +   // staged records
+           (size_t)nt * sizeof(float4) +                    // texel directions
+           (size_t)K * nt * sizeof(float) +                 // per-shell increments
+           (size_t)((K + 3) & ~3) * sizeof(float) +         // radii
+           (size_t)chunk * nt * sizeof(uint16_t) +          // candidate list
+           (size_t)SHELL_NB * sizeof(uint16_t) +            // shell table
+           (size_t)2 * chunk;                               // half-tile masks
 }
 
-// Persistent build kernel, 8 warps per block.  A warp owns 64 texels (two per
-// lane): with tile 8 all 8 warps cover the whole tile, with tile 16 they form
-// 4 texel groups of 2 warps.  The records of a staged chunk are handed out one
-// at a time to the warps of each texel group; a warp tests its texels against
-// the record (broadcast from shared memory) and queues the hits with their
-// geometry; 32 queued hits at a time are then evaluated lane-parallel.  Each
-// pair carries the binning's half-tile mask: a warp's 32 "A" texels and its
-// 32 "B" texels each lie in one half of the tile, and a half the mask
-// excludes is not tested.
-template <typename OutT>
-__global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_kernel(
+// Candidate texels of one staged record in rows [h T/2, (h+1) T/2) of a T x T
+// tile: out[i] = jl | (je << 8), the columns [jl, je) of row h T/2 + i (je <=
+// jl: none).  The binning's half-tile bit h (1: rows [0, T/2), 2: rows
+// [T/2, T)) must be set; face: (d_c, ok), E_x, E_y of the tile; rows_valid x
+// cols_valid: texels inside the atlas.
+template <int T>
+__device__ __forceinline__ void cand_mask(const float4 &q0, const float4 &q1, const float4 &q2,
+                                          const float4 &q3, int h, const float4 &fc,
+                                          const float4 &fx, const float4 &fy, int rows_valid,
+                                          int cols_valid, uint32_t (&out)[T / 2]) {
+    constexpr float HC = 0.5f * (float)(T - 1);
+    const bool inside = (__float_as_int(q3.z) >> 20) & 1;
+    bool conic = fc.w != 0.0f && !inside;
+    float q00 = 0.f, qx = 0.f, qy = 0.f, qxx = 0.f, qxy = 0.f, qyy = 0.f;
+    if (conic) {
+        const float wx = q2.y, wy = q2.z, wz = q2.w;
+        auto mvec = [&](float x, float y, float z, float &a, float &b, float &c) {
+            a = fmaf(q0.x, x, fmaf(q0.y, y, q0.z * z));
+            b = fmaf(q0.w, x, fmaf(q1.x, y, q1.y * z));
+            c = fmaf(q1.z, x, fmaf(q1.w, y, q2.x * z));
+        };
+        float p0x, p0y, p0z, pxx, pxy, pxz, pyx, pyy, pyz;
+        mvec(fc.x, fc.y, fc.z, p0x, p0y, p0z);
+        mvec(fx.x, fx.y, fx.z, pxx, pxy, pxz);
+        mvec(fy.x, fy.y, fy.z, pyx, pyy, pyz);
+        // c = w' x p
+        const float c0x = fmaf(wy, p0z, -wz * p0y), c0y = fmaf(wz, p0x, -wx * p0z), c0z = fmaf(wx, p0y, -wy * p0x);
+        const float cxx = fmaf(wy, pxz, -wz * pxy), cxy = fmaf(wz, pxx, -wx * pxz), cxz = fmaf(wx, pxy, -wy * pxx);
+        const float cyx = fmaf(wy, pyz, -wz * pyy), cyy = fmaf(wz, pyx, -wx * pyz), cyz = fmaf(wx, pyy, -wy * pyx);
+        auto dot = [](float ax, float ay, float az, float bx, float by, float bz) {
+            return fmaf(ax, bx, fmaf(ay, by, az * bz));
+        };
+        const float P00 = dot(p0x, p0y, p0z, p0x, p0y, p0z), Pxx = dot(pxx, pxy, pxz, pxx, pxy, pxz),
+                    Pyy = dot(pyx, pyy, pyz, pyx, pyy, pyz);
+        const float P0x = dot(p0x, p0y, p0z, pxx, pxy, pxz), P0y = dot(p0x, p0y, p0z, pyx, pyy, pyz),
+                    Pxy = dot(pxx, pxy, pxz, pyx, pyy, pyz);
+        const float C00 = dot(c0x, c0y, c0z, c0x, c0y, c0z), Cxx = dot(cxx, cxy, cxz, cxx, cxy, cxz),
+                    Cyy = dot(cyx, cyy, cyz, cyx, cyy, cyz);
+        const float C0x = dot(c0x, c0y, c0z, cxx, cxy, cxz), C0y = dot(c0x, c0y, c0z, cyx, cyy, cyz),
+                    Cxy = dot(cxx, cxy, cxz, cyx, cyy, cyz);
+        const float K2 = q3.y * (1.0f + CONIC_WIDEN);
+        q00 = fmaf(-K2, P00, C00);
+        qx = 2.0f * fmaf(-K2, P0x, C0x);
+        qy = 2.0f * fmaf(-K2, P0y, C0y);
+        qxx = fmaf(-K2, Pxx, Cxx);
+        qxy = 2.0f * fmaf(-K2, Pxy, Cxy);
+        qyy = fmaf(-K2, Pyy, Cyy);
+        // The expansion keeps its margin when the terms it sums are not far
+        // larger than k^2 |M d|^2 over the tile (|M d| >= |p0|/2 there).
+        const float h2 = HC * HC;
+        const float B = 3.0f * (fmaf(h2, Cxx + Cyy, C00) + K2 * fmaf(h2, Pxx + Pyy, P00));
+        conic = 2.0f * h2 * (Pxx + Pyy) <= 0.25f * P00 && B * CONIC_COND <= q3.y * P00;
+    }
+    float i2a = 0.0f;
+    if (conic && qxx > 0.0f) i2a = __fdividef(0.5f, qxx);
+#pragma unroll
+    for (int rr = 0; rr < T / 2; ++rr) {
+        const int i = h * (T / 2) + rr;
+        int jl = 0, je = cols_valid;
+        if (i >= rows_valid) {
+            je = 0;
+        } else if (conic && qxx > 0.0f) {
+            const float y = (float)i - HC;
+            const float Bc = fmaf(qxy, y, qx), C = fmaf(y, fmaf(qyy, y, qy), q00);
+            const float disc = fmaf(-4.0f * qxx, C, Bc * Bc);
+            if (disc < 0.0f) {
+                je = 0;
+            } else {
+                const float sd = disc * rsqrt_approx(fmaxf(disc, 1e-37f));
+                const float xl = fmaxf(fmaf(-Bc - sd, i2a, HC - 1e-3f), -1.0f);
+                const float xr = fminf(fmaf(sd - Bc, i2a, HC + 1e-3f), (float)T);
+                jl = max(__float2int_ru(xl), 0);
+                je = min(__float2int_rd(xr) + 1, cols_valid);
+            }
+        }
+        out[rr] = (uint32_t)jl | ((uint32_t)max(je, 0) << 8);
+    }
+}
+
+// Persistent: blocks pull work items (a tile's list, or a piece of it) from
+// an atomic counter.  8 warps; staged chunks of records double buffered.
+template <typename OutT, int T>
+__global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_tiles_kernel(
     const float4 *__restrict__ brec, const uint32_t *__restrict__ vals,
     const Item *__restrict__ items, const unsigned long long *__restrict__ n_items_total,
     unsigned int *__restrict__ item_counter, const float *__restrict__ radii, int K, int H, int W,
-    int tile, int tx, int n_tiles, int64_t N, int chunk, float *__restrict__ accum,
+    int tx, int n_tiles, int64_t N, int chunk, float *__restrict__ accum,
     unsigned int *__restrict__ done, OutT *__restrict__ atlas,
     unsigned long long *__restrict__ stats, const uint8_t *__restrict__ roi_mask,
     const int *__restrict__ roi_k, int map) {
     // roi_mask, roi_k (or nullptr): texels [L][H][W] and shell range [kmin,
     // kmax] per light of a region of interest; T = 1 outside it
+    constexpr int NT = T * T;
     extern __shared__ float4 smem4[];
-    const int nt = tile * tile;
-    const int n_tg = nt / 64;
-    float4 *stage = smem4;                                   // [2][chunk * REC_F4]
-    float4 *tdir = stage + 2 * chunk * REC_F4;               // [nt] (dir, valid)
-    float *D = reinterpret_cast<float *>(tdir + nt);         // [K][nt]
-    float *rs = D + K * nt;                                  // [K]
-    float4 *queue = reinterpret_cast<float4 *>(rs + ((K + 3) & ~3));  // [BT_WARPS][QCAP]
-    uint8_t *smask = reinterpret_cast<uint8_t *>(queue + BT_WARPS * QCAP);  // [2][chunk]
+    float4 *stage = smem4;                                    // [2][chunk * REC_F4]
+    float4 *tdir = stage + 2 * chunk * REC_F4;                // [NT] (dir, valid)
+    float *D = reinterpret_cast<float *>(tdir + NT);          // [K][NT]
+    float *rs = D + K * NT;                                   // [K]
+    uint16_t *cand = reinterpret_cast<uint16_t *>(rs + ((K + 3) & ~3));  // [chunk * NT]
+    uint16_t *stab = cand + chunk * NT;                       // [SHELL_NB]
+    uint8_t *smask = reinterpret_cast<uint8_t *>(stab + SHELL_NB);  // [2][chunk]
     __shared__ uint4 s_item;
     __shared__ int s_last;
-    __shared__ int s_next[BT_WARPS];
+    __shared__ int s_total[2];
+    __shared__ float4 s_face[3];
     __shared__ unsigned long long s_cnt[3];
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tg = warp % n_tg;
-    const unsigned lt = (1u << lane) - 1u;
-    // half-tile bit of this warp's A texels and of its B texels
-    const uint32_t bitA = (tg * 64) / tile >= tile / 2 ? 2u : 1u;
-    const uint32_t bitB = (tg * 64 + 32) / tile >= tile / 2 ? 2u : 1u;
-    unsigned int n_tst = 0;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int64_t HW = (int64_t)H * W;
     const unsigned long long total_items = *n_items_total;
     for (int k = tid; k < K; k += BT_THREADS) rs[k] = radii[k];
     if (tid < 3) s_cnt[tid] = 0ull;
-    unsigned long long n_tested = 0;
-    unsigned int n_hit = 0, n_shell = 0;
-    float4 *q = queue + warp * QCAP;
-
+    __syncthreads();
+    // stab[b] = #{k : r_k < t_b}, t_b the float with bits SHELL_TB0 + (b << 19)
+    for (int b = tid; b < SHELL_NB; b += BT_THREADS) {
+        const float tb = __int_as_float(SHELL_TB0 + (b << 19));
+        int c = 0;
+        while (c < K && rs[c] < tb) ++c;
+        stab[b] = (uint16_t)c;
+    }
+    // a bucket holds several radii (radii closer than 1/16 octave, or beyond the
+    // table): the shell search then steps on past the first one
+    int several = 0;
+    for (int k = tid; k + 1 < K; k += BT_THREADS) {
+        const int bk = __float_as_int(rs[k]), bn = __float_as_int(rs[k + 1]);
+        const bool out = bk <= SHELL_TB0 || bn - SHELL_TB0 >= (SHELL_NB << 19);
+        several |= out || ((bk - SHELL_TB0) >> 19) == ((bn - SHELL_TB0) >> 19);
+    }
+    const bool step_more = __syncthreads_or(several) != 0;
+    unsigned int n_cand = 0, n_hit = 0, n_shell = 0;
     for (;;) {
         if (tid == 0) {
             const unsigned it = atomicAdd(item_counter, 1u);
@@ -1040,9 +1117,12 @@ __global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_ke
         const uint32_t key = item.x, start = item.y, end = item.z, n_items = item.w;
         const int l = key / n_tiles, t = key - l * n_tiles;
         const int tile_i = t / tx, tile_j = t - tile_i * tx;
-        for (int e = tid; e < K * nt; e += BT_THREADS) D[e] = 0.0f;
-        for (int e = tid; e < nt; e += BT_THREADS) {
-            const int i = tile_i * tile + e / tile, j = tile_j * tile + e % tile;
+        const int i0 = tile_i * T, j0 = tile_j * T;
+        const int rows_valid = min(T, H - i0), cols_valid = min(T, W - j0);
+        for (int e = tid; e < K * NT; e += BT_THREADS) D[e] = 0.0f;
+        if (tid == 0) s_total[0] = 0;
+        for (int e = tid; e < NT; e += BT_THREADS) {
+            const int i = i0 + e / T, j = j0 + e % T;
             float x, y, z;
             if (map == MAP_CUBE) {
                 const int f = min(i / W, 5);
@@ -1064,11 +1144,64 @@ __global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_ke
             const float inv = rsqrtf(x * x + y * y + z * z);
             tdir[e] = make_float4(x * inv, y * inv, z * inv, (i < H && j < W) ? 1.0f : 0.0f);
         }
+        if (tid == 0) {
+            // the tile's affine ray family d_c + x E_x + y E_y (texel offsets x, y)
+            float dc0, dc1, dc2, ex0 = 0.f, ex1 = 0.f, ex2 = 0.f, ey0 = 0.f, ey1 = 0.f, ey2 = 0.f;
+            bool ok = true;
+            if (map == MAP_CUBE) {
+                const int f = min(i0 / W, 5);
+                int aF, aU, aV;
+                float sF, sU, sV;
+                cube_axes(f, aF, aU, aV, sF, sU, sV);
+                const float du = 2.0f / W;
+                const float uc = (float)(2 * j0 + T) / W - 1.0f, vc = (float)(2 * (i0 - f * W) + T) / W - 1.0f;
+                dc0 = aF == 0 ? sF : aU == 0 ? sU * uc : sV * vc;
+                dc1 = aF == 1 ? sF : aU == 1 ? sU * uc : sV * vc;
+                dc2 = aF == 2 ? sF : aU == 2 ? sU * uc : sV * vc;
+                ex0 = aU == 0 ? sU * du : 0.f;
+                ex1 = aU == 1 ? sU * du : 0.f;
+                ex2 = aU == 2 ? sU * du : 0.f;
+                ey0 = aV == 0 ? sV * du : 0.f;
+                ey1 = aV == 1 ? sV * du : 0.f;
+                ey2 = aV == 2 ? sV * du : 0.f;
+            } else {
+                const float du = 2.0f / W, dv = 2.0f / H;
+                const float uc = (float)(2 * j0 + T) / W - 1.0f, vc = (float)(2 * i0 + T) / H - 1.0f;
+                const float ua = (2.0f * j0 + 1.0f) / W - 1.0f, ub = (2.0f * (j0 + cols_valid - 1) + 1.0f) / W - 1.0f;
+                const float va = (2.0f * i0 + 1.0f) / H - 1.0f, vb = (2.0f * (i0 + rows_valid - 1) + 1.0f) / H - 1.0f;
+                const float su = ua >= 0.f ? 1.f : -1.f, sv = va >= 0.f ? 1.f : -1.f;
+                ok = (ub >= 0.f) == (ua >= 0.f) && (vb >= 0.f) == (va >= 0.f);
+                const float s00 = fabsf(ua) + fabsf(va), s01 = fabsf(ub) + fabsf(va);
+                const float s10 = fabsf(ua) + fabsf(vb), s11 = fabsf(ub) + fabsf(vb);
+                const bool inner = fmaxf(fmaxf(s00, s01), fmaxf(s10, s11)) <= 1.0f;
+                const bool outer = fminf(fminf(s00, s01), fminf(s10, s11)) >= 1.0f;
+                ok = ok && (inner || outer);
+                // inner face: d = (u, v, 1 - su u - sv v); outer (folded) face:
+                // d = (su (1 - sv v), sv (1 - su u), 1 - su u - sv v)
+                dc2 = 1.0f - su * uc - sv * vc;
+                ex2 = -su * du;
+                ey2 = -sv * dv;
+                if (inner) {
+                    dc0 = uc;
+                    dc1 = vc;
+                    ex0 = du;
+                    ey1 = dv;
+                } else {
+                    dc0 = su - su * sv * vc;
+                    dc1 = sv - su * sv * uc;
+                    ex1 = -su * sv * du;
+                    ey0 = -su * sv * dv;
+                }
+            }
+            s_face[0] = make_float4(dc0, dc1, dc2, ok ? 1.f : 0.f);
+            s_face[1] = make_float4(ex0, ex1, ex2, 0.f);
+            s_face[2] = make_float4(ey0, ey1, ey2, 0.f);
+        }
         const float4 *src = brec + (int64_t)l * N * REC_F4;
         const int nrec = (int)(end - start);
         const int nchunks = (nrec + chunk - 1) / chunk;
         // staging: entry e of a chunk = record e / REC_F4, part e % REC_F4;
-        // a thread owns e = tid, tid + 256, tid + 512
+        // a thread owns e = tid, tid + BT_THREADS, tid + 2 BT_THREADS
         uint32_t gnext[3] = {0u, 0u, 0u};
         auto load_idx = [&](int c, uint32_t *g) {
             const int base = (int)start + c * chunk, cnt = min(chunk, (int)end - base);
@@ -1097,98 +1230,132 @@ __global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_ke
             issue(0, g0);
             if (nchunks > 1) load_idx(1, gnext);
         }
-        __syncthreads();
-        const float4 dA = tdir[tg * 64 + lane], dB = tdir[tg * 64 + 32 + lane];
-        const bool vA = dA.w != 0.0f, vB = dB.w != 0.0f;
+        const float4 *st = stage;
         for (int c = 0; c < nchunks; ++c) {
+            cp_async_wait<0>();
+            // chunk c is in shared memory, and every warp is done with chunk c - 1,
+            // whose buffers chunk c + 1 now takes
+            __syncthreads();
             if (c + 1 < nchunks) {
                 issue(c + 1, gnext);
                 if (c + 2 < nchunks) load_idx(c + 2, gnext);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
             }
-            if (tid < n_tg) s_next[tid] = 0;
-            __syncthreads();
-            const float4 *st = stage + (c & 1) * chunk * REC_F4;
+            st = stage + (c & 1) * chunk * REC_F4;
             const int cnt = min(chunk, (int)end - ((int)start + c * chunk));
-            int qn = 0;
-            auto flush = [&](int n) {  // evaluate the n (<= 32) hits at the top of the queue
-                __syncwarp();
-                if (lane < n) {
-                    const float4 e = q[qn - n + lane];
-                    const int id = __float_as_int(e.w);
-                    const int tex = tg * 64 + (id & 63);
-                    PairGeom gg;
-                    gg.a = e.x;
-                    gg.pw = e.y;
-                    gg.c2 = e.z;
-                    eval_shells(gg, st[(id >> 6) * REC_F4 + 3], rs, K, D, nt, tex, n_shell);
+            // candidate list: the threads 2r and 2r + 1 of a pass write the
+            // candidates of record r in the top and bottom half of the tile, at
+            // offsets from a warp scan and one shared counter per warp
+            for (int pa = 0; pa < 2 * cnt; pa += BT_THREADS) {
+                uint32_t iv[T / 2];
+#pragma unroll
+                for (int rr = 0; rr < T / 2; ++rr) iv[rr] = 0u;
+                const int r = (pa + tid) >> 1, h = tid & 1;
+                int nr = 0;
+                if (r < cnt && ((smask[(c & 1) * chunk + r] >> h) & 1u)) {
+                    cand_mask<T>(st[r * REC_F4], st[r * REC_F4 + 1], st[r * REC_F4 + 2], st[r * REC_F4 + 3],
+                                 h, s_face[0], s_face[1], s_face[2], rows_valid, cols_valid, iv);
+#pragma unroll
+                    for (int rr = 0; rr < T / 2; ++rr) nr += max((int)(iv[rr] >> 8) - (int)(iv[rr] & 255u), 0);
                 }
-                if (lane == 0) n_hit += (unsigned)n;
-                qn -= n;
-                __syncwarp();
-            };
-            auto push = [&](bool hit, const PairGeom &g, int id) {
-                const unsigned m = __ballot_sync(0xffffffffu, hit);
-                if (hit) q[qn + __popc(m & lt)] = make_float4(g.a, g.pw, g.c2, __int_as_float(id));
-                qn += __popc(m);
-            };
-            // records are handed out dynamically, two at a time, to the warps of a
-            // texel group; a warp's hits are evaluated once 32 are queued
-            const uint8_t *cmask = smask + (c & 1) * chunk;
-            for (;;) {
-                int r0 = 0;
-                if (lane == 0) r0 = atomicAdd(&s_next[tg], 2);
-                r0 = __shfl_sync(0xffffffffu, r0, 0);
-                if (r0 >= cnt) break;
-                const int r1 = min(r0 + 2, cnt);
-                for (int r = r0; r < r1; ++r) {
-                    const uint32_t hm = cmask[r];
-                    const bool doA = (hm & bitA) != 0u, doB = (hm & bitB) != 0u;
-                    if (!doA && !doB) continue;
-                    const float4 q0 = st[r * REC_F4], q1 = st[r * REC_F4 + 1], q2 = st[r * REC_F4 + 2],
-                                 q3 = st[r * REC_F4 + 3];
-                    const bool inside = (__float_as_int(q3.z) >> 20) & 1;
-                    if (doA) {
-                        const PairGeom gA = pair_geom(q0, q1, q2, dA.x, dA.y, dA.z);
-                        push(vA && pair_hit(gA, q3.y, inside), gA, (r << 6) | lane);
-                        n_tst += vA;
-                    }
-                    if (doB) {
-                        const PairGeom gB = pair_geom(q0, q1, q2, dB.x, dB.y, dB.z);
-                        push(vB && pair_hit(gB, q3.y, inside), gB, (r << 6) | (32 + lane));
-                        n_tst += vB;
-                    }
-                    // at most 31 + 2 * 32 < QCAP hits are queued here
-                    while (qn >= 32) flush(32);
+                int incl = nr;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(FULLMASK, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                int wbase = 0;
+                if (lane == 31 && incl > 0) wbase = atomicAdd(&s_total[c & 1], incl);
+                int pos = __shfl_sync(FULLMASK, wbase, 31) + incl - nr;
+#pragma unroll
+                for (int rr = 0; rr < T / 2; ++rr) {
+                    const int id0 = (r << 8) | ((h * (T / 2) + rr) * T);
+                    for (int j = (int)(iv[rr] & 255u); j < (int)(iv[rr] >> 8); ++j) cand[pos++] = (uint16_t)(id0 + j);
                 }
             }
-            if (qn > 0) flush(qn);
-            __syncthreads();  // the buffer is refilled two chunks later
+            __syncthreads();
+            const int total = s_total[c & 1];
+            if (tid == 0) {
+                s_total[(c + 1) & 1] = 0;  // the next chunk's counter
+                n_cand += (unsigned)total;
+            }
+            // warp w takes the batches w, w + 8, ... of 32 consecutive candidates;
+            // the body is straight-line code with predicated deposits (lanes past
+            // the list's end or without a hit deposit nothing)
+            const int warp = tid >> 5;
+            for (int f0 = warp * 32; f0 < total; f0 += BT_THREADS) {
+                const bool valid = f0 + lane < total;
+                const uint32_t id = valid ? cand[f0 + lane] : 0u;
+                const int r = (int)(id >> 8), tex = (int)(id & 255u);
+                const float4 q0 = st[r * REC_F4], q1 = st[r * REC_F4 + 1], q2 = st[r * REC_F4 + 2],
+                             q3 = st[r * REC_F4 + 3];
+                const float4 dd = tdir[tex];
+                const PairGeom g = pair_geom(q0, q1, q2, dd.x, dd.y, dd.z);
+                const bool inside = (__float_as_int(q3.z) >> 20) & 1;
+                const bool hit = valid && pair_hit(g, q3.y, inside);
+                n_hit += hit ? 1u : 0u;
+                const float rsa = rsqrt_approx(g.a);
+                const float ia = rsa * rsa;
+                const float m2 = g.c2 * ia;   // c - b^2/a
+                const float ss = g.pw * ia;   // closest approach s* = -b/a
+                // the chord through the culling ellipsoid, s* +- sqrt((k^2 - m^2)/a):
+                // the ray's mass outside it is at most eps_cull, so shells before it
+                // get nothing and the first shell past it the whole remaining mass
+                const float c2h = fmaxf(q3.y - m2, 1e-30f);
+                const float half = c2h * rsqrt_approx(c2h) * rsa;
+                const float lo = ss - half, hi = ss + half;
+                // first shell at or past the chord's start: the table's bucket holds
+                // at most one radius (else step_more is set and a loop finishes)
+                int k = stab[max(min((__float_as_int(lo) - SHELL_TB0) >> 19, SHELL_NB - 1), 0)];
+                k += (k < K && rs[min(k, K - 1)] < lo) ? 1 : 0;
+                if (step_more)
+                    while (k < K && rs[k] < lo) ++k;
+                const float A0 = q3.x * rsa;                  // beta sqrt(pi/(2a))
+                const float hh = g.a * rsa * 0.70710678118f;  // sqrt(a/2)
+                const float hm2 = -0.72134752044f * m2;       // -m^2/2 log2(e)
+                const float full = 2.0f * A0 * ex2_approx(hm2);
+                const float hs = hh * ss;
+                float F0 = 0.0f;
+                if (__any_sync(FULLMASK, inside)) F0 = inside ? mass_below(-hs, A0, hm2, full) : 0.0f;
+                const int k0 = k;
+                float Gprev = 0.0f;
+                // shells on the chord (most hits have none or one)
+                bool more = hit && k < K && rs[min(k, K - 1)] <= hi;
+                while (__any_sync(FULLMASK, more)) {
+                    const float G = mass_below(fmaf(hh, rs[min(k, K - 1)], -hs), A0, hm2, full) - F0;
+                    if (more) {
+                        atomicAdd(D + k * NT + tex, fmaxf(G - Gprev, 0.0f));
+                        Gprev = fmaxf(G, Gprev);
+                        ++k;
+                    }
+                    more = more && k < K && rs[min(k, K - 1)] <= hi;
+                }
+                n_shell += (unsigned)(k - k0);
+                if (hit && k < K) atomicAdd(D + k * NT + tex, fmaxf(full - F0 - Gprev, 0.0f));
+            }
         }
+        __syncthreads();
         // ---- finalize: prefix over shells, T = exp(-tau) (Eq. 4) ----
         const int kmin = roi_k ? roi_k[2 * l] : 0, kmax = roi_k ? roi_k[2 * l + 1] : K - 1;
         if (n_items == 1) {
-            for (int e = tid; e < nt; e += BT_THREADS) {
+            for (int e = tid; e < NT; e += BT_THREADS) {
                 if (tdir[e].w == 0.0f) continue;
-                const int i = tile_i * tile + e / tile, j = tile_j * tile + e % tile;
+                const int i = i0 + e / T, j = j0 + e % T;
                 OutT *dst = atlas + (int64_t)l * K * HW + (int64_t)i * W + j;
                 const bool in = !roi_mask || roi_mask[(int64_t)l * HW + (int64_t)i * W + j];
                 float tau = 0.0f, Tprev = 1.0f;
                 for (int k = 0; k < K; ++k) {
-                    tau += D[k * nt + e];
-                    const float T = fminf(expf(-tau), Tprev);  // kept non-increasing in k
-                    Tprev = T;
-                    dst[k * HW] = to_store<OutT>(in && k >= kmin && k <= kmax ? T : 1.0f);
+                    tau += D[k * NT + e];
+                    const float Tk = fminf(expf(-tau), Tprev);  // kept non-increasing in k
+                    Tprev = Tk;
+                    dst[k * HW] = to_store<OutT>(in && k >= kmin && k <= kmax ? Tk : 1.0f);
                 }
             }
         } else {
-            for (int e = tid; e < K * nt; e += BT_THREADS) {
-                const int k = e / nt, te = e - k * nt;
+            for (int e = tid; e < K * NT; e += BT_THREADS) {
+                const int k = e / NT, te = e - k * NT;
                 const float v = D[e];
                 if (v == 0.0f || tdir[te].w == 0.0f) continue;
-                const int i = tile_i * tile + te / tile, j = tile_j * tile + te % tile;
+                const int i = i0 + te / T, j = j0 + te % T;
                 atomicAdd(accum + ((int64_t)l * K + k) * HW + (int64_t)i * W + j, v);
             }
             __threadfence();
@@ -1197,9 +1364,9 @@ __global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_ke
             __syncthreads();
             if (s_last) {
                 __threadfence();
-                for (int e = tid; e < nt; e += BT_THREADS) {
+                for (int e = tid; e < NT; e += BT_THREADS) {
                     if (tdir[e].w == 0.0f) continue;
-                    const int i = tile_i * tile + e / tile, j = tile_j * tile + e % tile;
+                    const int i = i0 + e / T, j = j0 + e % T;
                     OutT *dst = atlas + (int64_t)l * K * HW + (int64_t)i * W + j;
                     float *acc = accum + (int64_t)l * K * HW + (int64_t)i * W + j;
                     const bool in = !roi_mask || roi_mask[(int64_t)l * HW + (int64_t)i * W + j];
@@ -1207,9 +1374,9 @@ __global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_ke
                     for (int k = 0; k < K; ++k) {
                         tau += __ldcg(acc + k * HW);
                         acc[k * HW] = 0.0f;  // ready for the next build
-                        const float T = fminf(expf(-tau), Tprev);
-                        Tprev = T;
-                        dst[k * HW] = to_store<OutT>(in && k >= kmin && k <= kmax ? T : 1.0f);
+                        const float Tk = fminf(expf(-tau), Tprev);
+                        Tprev = Tk;
+                        dst[k * HW] = to_store<OutT>(in && k >= kmin && k <= kmax ? Tk : 1.0f);
                     }
                 }
                 if (tid == 0) done[key] = 0u;
@@ -1218,13 +1385,32 @@ __global__ void __launch_bounds__(BT_THREADS, DGSM_BT_MIN_BLOCKS) build_items_ke
         __syncthreads();  // shared state is reused by the next item
     }
     if (stats) {
-        n_tested = n_tst;
-        if (n_tested) atomicAdd(&s_cnt[0], n_tested);
+        if (n_cand) atomicAdd(&s_cnt[0], (unsigned long long)n_cand);
         if (n_hit) atomicAdd(&s_cnt[1], (unsigned long long)n_hit);
         if (n_shell) atomicAdd(&s_cnt[2], (unsigned long long)n_shell);
         __syncthreads();
         if (tid < 3) atomicAdd(stats + tid, s_cnt[tid]);
     }
+}
+
+template <typename OutT, int T>
+int launch_tiles(dgsm_ctx *ctx, const BuildRec *brec, const uint32_t *vals, const Item *items,
+                 const unsigned long long *n_items, unsigned int *counter, const float *radii, int K,
+                 int H, int W, int tx, int n_tiles, int64_t N, int chunk, float *accum, unsigned int *done,
+                 void *atlas, cudaStream_t s, const uint8_t *roi_mask, const int *roi_k, int map) {
+    const size_t smem = build_smem_bytes(K, T, chunk);
+    cudaError_t e = cudaFuncSetAttribute(build_tiles_kernel<OutT, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "build: smem attribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_tiles_kernel<OutT, T>, BT_THREADS, smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "build: occupancy query");
+    const int grid = std::max(1, per_sm) * ctx->num_sms;
+    build_tiles_kernel<OutT, T><<<grid, BT_THREADS, smem, s>>>(
+        reinterpret_cast<const float4 *>(brec), vals, items, n_items, counter, radii, K, H, W, tx,
+        n_tiles, N, chunk, accum, done, (OutT *)atlas, ctx->d_stats, roi_mask, roi_k, map);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "build_tiles_kernel");
 }
 
 template <typename OutT>
@@ -1233,22 +1419,12 @@ int launch_build_items(dgsm_ctx *ctx, const BuildRec *brec, const uint32_t *vals
                        int K, int H, int W, int tile, int tx, int n_tiles, int64_t N, int chunk,
                        float *accum, unsigned int *done, void *atlas, cudaStream_t s,
                        const uint8_t *roi_mask, const int *roi_k, int map) {
-    const size_t smem = build_smem_bytes(K, tile, chunk);
-    cudaError_t e = cudaFuncSetAttribute(build_items_kernel<OutT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "build: smem attribute");
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_items_kernel<OutT>, BT_THREADS, smem);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "build: occupancy query");
-    const int grid = std::max(1, per_sm) * ctx->num_sms;
-    build_items_kernel<OutT><<<grid, BT_THREADS, smem, s>>>(
-        reinterpret_cast<const float4 *>(brec), vals, items, n_items, counter, radii, K, H, W, tile,
-        tx, n_tiles, N, chunk, accum, done, (OutT *)atlas, ctx->d_stats, roi_mask, roi_k, map);
-    e = cudaGetLastError();
-    return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "build_items_kernel");
+    if (tile == 16)
+        return launch_tiles<OutT, 16>(ctx, brec, vals, items, n_items, counter, radii, K, H, W, tx, n_tiles, N,
+                                      chunk, accum, done, atlas, s, roi_mask, roi_k, map);
+    return launch_tiles<OutT, 8>(ctx, brec, vals, items, n_items, counter, radii, K, H, W, tx, n_tiles, N,
+                                 chunk, accum, done, atlas, s, roi_mask, roi_k, map);
 }
-
-// Device arrays of a receiver-driven region of interest (dgsm_build_roi).
 struct RoiDev {
     const uint8_t *mask = nullptr;  // [L][H][W] texels of the region
     const uint8_t *tact = nullptr;  // [L][n_tiles] tiles holding one of them
@@ -1275,8 +1451,8 @@ int check_common(dgsm_ctx *ctx, const float *means, const float *scales, const f
     if (H < 1 || W < 1 || H > 4096 || W > 4096) return fail(ctx, DGSM_ERR_INVALID_ARG, "H, W must be in 1..4096");
     if (!radii || K < 1 || K > 256) return fail(ctx, DGSM_ERR_INVALID_ARG, "K must be in 1..256");
     if (p.tile != 4 && p.tile != 8 && p.tile != 16) return fail(ctx, DGSM_ERR_INVALID_ARG, "tile must be 4, 8 or 16");
-    // the staging loop gives each of the 256 threads three of a chunk's
-    // 4-float4 records: at most 3 x 256 / 4 = 192 records
+    // the tile kernel's staging gives each of its 256 threads at most three of
+    // a chunk's 4-float4 records: at most 3 x 256 / 4 = 192 records
     if (p.chunk < 16 || p.chunk > 192) return fail(ctx, DGSM_ERR_INVALID_ARG, "chunk must be in 16..192");
     if (!(p.kappa >= 0.f) || !(p.eps_cull > 0.f)) return fail(ctx, DGSM_ERR_INVALID_ARG, "kappa >= 0 and eps_cull > 0 required");
     if (p.beta_mode < 1 || p.beta_mode > 4) return fail(ctx, DGSM_ERR_INVALID_ARG, "beta_mode must be 1..4");

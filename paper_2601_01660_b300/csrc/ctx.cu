@@ -62,7 +62,7 @@ extern "C" void dgsm_default_params(dgsm_params *p) {
     p->kappa = 1.0f;
     p->eps_cull = 1e-7f;
     p->tile = 8;
-    p->chunk = 192;
+    p->chunk = 128;
     p->atlas_dtype = DGSM_F32;
     p->max_pairs = 0;
     p->beta_mode = 2;

@@ -33,7 +33,7 @@ def test_default_params_without_gpu():
     from paper_2601_01660_b300 import native
     nat = native()
     p = nat.Params.make()
-    assert (p.kappa, p.tile, p.chunk, p.atlas_dtype) == (1.0, 8, 192, 0)
+    assert (p.kappa, p.tile, p.chunk, p.atlas_dtype) == (1.0, 8, 128, 0)
     assert abs(p.eps_cull - 1e-7) < 1e-12
     rp = nat.RelightParams()
     nat._lib.dgsm_default_relight_params(ctypes.byref(rp))

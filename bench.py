@@ -36,21 +36,19 @@ METRIC = "Gaussian-ray evals/s and ms per 512²×64 DGSM build; attenuated Gauss
 UNIT = "Gaussian-ray evals/s"
 WORKLOAD = "room1p6m"
 
-# Algorithmic single-precision work of the build tile kernel, per unit
-# (arithmetic a minimal implementation of the closed form must issue):
-#   per Gaussian-ray evaluation: whitened direction 9, a 3, d'.w' 3, w' x d' 6,
-#     |.|^2 3, m^2 and s* 2, chord half-length 3, setup of the erfc terms 7
-#                                                                 -> 36 FP32 + 4 MUFU
-#   per shell evaluation (Eq. 3 at one radius): argument 1, erfc polynomial
-#     and its reciprocal 6, exponent 2, scaling 2, select/difference/accumulate 5
-#                                                                 -> 16 FP32 + 2 MUFU
-#   per voxel: prefix sum, clamp, exp                             ->  3 FP32 + 1 MUFU
-FP32_PER_EVAL, MUFU_PER_EVAL = 36, 4
-FP32_PER_SHELL, MUFU_PER_SHELL = 16, 2
-FP32_PER_VOXEL, MUFU_PER_VOXEL = 3, 1
-SMS = 148
-FP32_LANES_PER_SM = 128   # FP32 results per SM per clock
-MUFU_LANES_PER_SM = 16    # special-function (MUFU) results per SM per clock
+# Algorithmic single-precision work of the build tile kernel, per unit, as
+# the measurement plan fixes it (arithmetic a minimal implementation of the
+# closed form must issue):
+#   per Gaussian-ray evaluation: 45-55 FP32 (whitened direction 18, a and b 12,
+#     cross product and norm 14, the rest), counted as 50, + 1 rsqrt + 1 ex2
+#   per shell evaluation (Eq. 3 at one radius): 20 FP32 + 1 rcp + 1 ex2
+#   per voxel: 1 FP32 (prefix sum) + 1 ex2
+# MUFU instructions differ in rate (ex2 runs at twice the rate of rcp and
+# rsqrt on this part), so the MUFU roofline weighs each by its measured rate.
+FP32_PER_EVAL, RSQ_PER_EVAL, EX2_PER_EVAL = 50, 1, 1
+FP32_PER_SHELL, RCP_PER_SHELL, EX2_PER_SHELL = 20, 1, 1
+FP32_PER_VOXEL, EX2_PER_VOXEL = 1, 1
+TILE_KERNEL = "build_tiles_kernel"
 L2_BYTES = 126 * 1024 * 1024
 
 
@@ -172,11 +170,16 @@ def run_ours(args, rank, world, local_rank):
         sh = step()
     torch.cuda.synchronize()
     stats = nat.dgsm_get_build_stats()
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]
+    # roofline denominators of the tile kernel: FP32 and MUFU rates measured
+    # now, on this GPU, with the SM clock sampled meanwhile
+    with ClockSampler(gpu_index) as pclk:
+        peaks = nat.dgsm_measure_alu_peaks()
+    peaks["sm_mhz"] = pclk.summary().get("sm_mhz")
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     nat.dgsm_set_profiling(True)
-    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]
     with ClockSampler(gpu_index) as clk:
         if dist is not None:
             dist.barrier()
@@ -205,28 +208,35 @@ def run_ours(args, rank, world, local_rank):
     tiles_ms = statistics.mean(p[1] for p in prof) if prof else None
     binning_ms = statistics.mean(p[0] for p in prof) if prof else None
     voxels = L * K * H * W
-    fp32 = FP32_PER_EVAL * evals + FP32_PER_SHELL * stats["shell_evals"] + FP32_PER_VOXEL * voxels
-    mufu = MUFU_PER_EVAL * evals + MUFU_PER_SHELL * stats["shell_evals"] + MUFU_PER_VOXEL * voxels
-    f_peak = (clocks.get("sm_max_mhz") or 2032.0) * 1e6
-    fp32_peak = SMS * FP32_LANES_PER_SM * f_peak / 1e12
-    mufu_peak = SMS * MUFU_LANES_PER_SM * f_peak / 1e12
+    shells = stats["shell_evals"]
+    fp32 = FP32_PER_EVAL * evals + FP32_PER_SHELL * shells + FP32_PER_VOXEL * voxels
+    n_ex2 = EX2_PER_EVAL * evals + EX2_PER_SHELL * shells + EX2_PER_VOXEL * voxels
+    n_slow = RSQ_PER_EVAL * evals + RCP_PER_SHELL * shells      # rsqrt and rcp
+    fp32_peak = peaks["fp32_ops_s"] / 1e12
+    # MUFU: the op mix's rate when the pipe runs flat out on it
+    mufu_ops = n_ex2 + n_slow
+    mufu_peak = mufu_ops / (n_ex2 / peaks["ex2_ops_s"] + n_slow / peaks["rcp_ops_s"]) / 1e12
     fp32_ach = fp32 / (tiles_ms * 1e-3) / 1e12
-    mufu_ach = mufu / (tiles_ms * 1e-3) / 1e12
+    mufu_ach = mufu_ops / (tiles_ms * 1e-3) / 1e12
     if fp32_ach / fp32_peak >= mufu_ach / mufu_peak:
         bound_pipe, ach, peak = "fp32", fp32_ach, fp32_peak
     else:
         bound_pipe, ach, peak = "mufu", mufu_ach, mufu_peak
-    traffic = _profiled_traffic("build_items_kernel", args.workload)
-    roofline = {"bound": "alu", "kernel": "build_items_kernel", "pipe": bound_pipe,
+    traffic = _profiled_traffic(TILE_KERNEL, args.workload)
+    roofline = {"bound": "alu", "kernel": TILE_KERNEL, "pipe": bound_pipe,
                 "achieved": round(ach, 4), "peak": round(peak, 4), "unit": "Tops/s",
                 "frac": round(ach / peak, 4), "traffic": traffic,
-                "peak_source": "derived: 148 SMs x lanes/clk x max SM clock (unit counts), of derived",
+                "peak_source": "measured in this run (dgsm_measure_alu_peaks: FFMA and MUFU chains "
+                               f"filling every SM, at {peaks.get('sm_mhz') or 'unsampled'} MHz), of measured",
+                "work_per_unit": {"eval": f"{FP32_PER_EVAL} FP32 + rsqrt + ex2",
+                                  "shell": f"{FP32_PER_SHELL} FP32 + rcp + ex2", "voxel": "1 FP32 + ex2"},
                 "pipes": {"fp32": {"achieved": round(fp32_ach, 4), "peak": round(fp32_peak, 4),
                                    "frac": round(fp32_ach / fp32_peak, 4)},
                           "mufu": {"achieved": round(mufu_ach, 4), "peak": round(mufu_peak, 4),
                                    "frac": round(mufu_ach / mufu_peak, 4)}},
+                "measured_peaks": {k: (round(v / 1e12, 3) if k.endswith("_s") else v) for k, v in peaks.items()},
                 "kernel_ms": round(tiles_ms, 4),
-                "ncu_pipe_utilisation": _profiled_pipes("build_items_kernel", args.workload)}
+                "ncu_pipe_utilisation": _profiled_pipes(TILE_KERNEL, args.workload)}
 
     # ---- attenuation roofline (HBM) -----------------------------------------
     # the event timer ticks in ~4 us steps on this part: the mean over steps
@@ -294,6 +304,36 @@ def run_ours(args, rank, world, local_rank):
                                           "peak": round(fp32_peak, 4), "unit": "Tops/s",
                                           "frac": round(roi_ach / fp32_peak, 4)},
                  "voxel_frac": round(roi_vox / voxels, 4), "dense_ms_per_build": None}
+    # back-to-back calls (20 per event pair, so that the event resolution and
+    # the launch gaps do not count), at the workload's 1.6M receivers and at
+    # 8x that many (positions repeated with millimetre offsets), whose 460 MB
+    # of streamed inputs and outputs exceed L2
+    def b2b(m, c):
+        o = torch.empty_like(c)
+        for _ in range(3):
+            nat.dgsm_attenuate(atlas, radii, lights, m, c, out=o)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            nat.dgsm_attenuate(atlas, radii, lights, m, c, out=o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        q = m.shape[0]
+        return {"queries": q, "ms": round(ms, 5), "gaussians_per_s": q / (ms * 1e-3),
+                "achieved_gbs": round(36 * q / (ms * 1e-3) / 1e9, 1),
+                "frac": round(36 * q / (ms * 1e-3) / 1e9 / hbm_peak, 4)}
+    attenuate["back_to_back"] = b2b(means, colors)
+    rep = 8
+    big_m = (means.repeat(rep, 1) + 1e-3 * torch.arange(rep, device=dev, dtype=torch.float32)
+             .repeat_interleave(N)[:, None]).contiguous()
+    big_c = colors.repeat(rep, 1).contiguous()
+    attenuate["large"] = b2b(big_m, big_c)
+    del big_m, big_c
+    attenuate["bound"] = ("L2 gathers: about 5 atlas sectors (160 B) per receiver and light come from L2 "
+                          "(receivers in scene order have no atlas locality), against 36 streamed bytes; "
+                          "profiles/attenuate_room1p6m_x8.md")
     attenuate["footprint_mc8"] = {"ms": round(fpt, 5), "gaussians_per_s": N / (fpt * 1e-3),
                                   "achieved_gbs": round((N * 64) / (fpt * 1e-3) / 1e9, 1),
                                   "frac": round((N * 64) / (fpt * 1e-3) / 1e9 / hbm_peak, 4),
@@ -524,7 +564,7 @@ def _profiled_pipes(kernel, workload):
             return None
         return {"fma": float(m.group(1)) / 100, "alu": float(m.group(2)) / 100,
                 "xu": float(m.group(3)) / 100,
-                "source": "ncu --set full on the room550k case (profiles/build_items_room1p6m.txt)"}
+                "source": f"ncu --set full on the room550k case (profiles/{kernel.replace('_kernel', '')}_room1p6m.txt)"}
     except OSError:
         return None
 

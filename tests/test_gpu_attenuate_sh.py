@@ -94,6 +94,32 @@ def test_attenuate_half_atlas(nat, orc, dtype):
     assert np.abs(T - Tref).max() <= 1e-5
 
 
+@pytest.mark.parametrize("Q", [512 * 4, 2051])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_attenuate_streaming_paths_agree(nat, orc, Q, dtype):
+    """The pass streams 16-byte-aligned inputs through shared memory in
+    whole tiles (queries past the last tile read directly), falls back to
+    direct loads for a misaligned view, and may write in place; every path
+    matches the oracle."""
+    rng = np.random.default_rng(Q)
+    L, K, H, W = 2, 7, 40, 48
+    radii = scenes.radii_geometric(0.1, 9, K)
+    atlas = np.sort(rng.random((L, K, H, W)), axis=1)[:, ::-1].copy()
+    lights = np.float32([[0, 0, 0], [1, -0.5, 0.5]])
+    qm = np.float32(rng.uniform(-10, 10, (Q + 1, 3)))
+    col = np.float32(rng.random((Q + 1, 3)))
+    at = dev(atlas, dtype)
+    ref = orc.attenuate(at.double().cpu().numpy(), radii, lights, qm, col)
+    m, c = dev(qm), dev(col)
+    aligned = nat.dgsm_attenuate(at, dev(radii), dev(lights), m[:Q].contiguous(), c[:Q].contiguous())
+    assert np.abs(aligned.double().cpu().numpy() - ref[:Q]).max() <= 1e-5
+    shifted = nat.dgsm_attenuate(at, dev(radii), dev(lights), m[1:], c[1:])   # 12-byte offset views
+    assert np.abs(shifted.double().cpu().numpy() - ref[1:]).max() <= 1e-5
+    inplace = c[:Q].clone()
+    nat.dgsm_attenuate(at, dev(radii), dev(lights), m[:Q].contiguous(), inplace, out=inplace)
+    assert np.abs(inplace.double().cpu().numpy() - ref[:Q]).max() <= 1e-5
+
+
 def test_attenuate_in_place_and_empty(nat):
     atlas = torch.full((1, 4, 8, 8), 0.5, device="cuda")
     radii = dev(scenes.radii_linear(0.1, 8, 4))

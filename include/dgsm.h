@@ -415,8 +415,12 @@ int dgsm_selftest_wait(dgsm_ctx *ctx, int32_t arrive, int64_t limit, void *strea
  *   n <= 4,194,304 (larger n returns DGSM_ERR_WORKSPACE);
  *   status_out: device int or NULL; receives DGSM_OK or DGSM_ERR_NOT_SPD
  *   (then sh_out is zero).
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  All calls share the one array:
+ * The first call on a device looks up the array's device address and keeps
+ * it for the rest of the process; make that first call before any stream
+ * capture, and do not call this entry point again after destroying the
+ * device's context (cudaDeviceReset), whose addresses it would still use.
+ * An error that earlier work left pending on the calling thread is returned
+ * as DGSM_ERR_CUDA without being cleared.  All calls share the one array:
  * calls that overlap on the GPU (on concurrent streams) race and give wrong
  * results; serialise them.  Returns DGSM_OK, DGSM_ERR_INVALID_ARG,
  * DGSM_ERR_WORKSPACE (n too large) or DGSM_ERR_CUDA; there is no context to

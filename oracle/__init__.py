@@ -76,6 +76,9 @@ def _declare(L):
     L.orc_f32_gauss_axes.argtypes = [_f, _f, _f, _f, _f]
     L.orc_f32_bin.argtypes = [_f, _f, _f, _f, I64, _f, C.c_int, C.c_int, C.c_int, _f, C.c_int,
                               C.c_float, C.c_float, C.c_int, _u32, _u32, I64]
+    L.orc_f32_bin_keys.restype = I64
+    L.orc_f32_bin_keys.argtypes = [_f, _f, _f, _f, I64, _f, C.c_int, C.c_int, C.c_int, _f, C.c_int,
+                                   C.c_float, C.c_float, C.c_int, _u32, C.c_int, _u32, _u32, I64]
     L.orc_count_ray_evals.restype = I64
     L.orc_count_ray_evals.argtypes = [_f, _f, _f, _f, I64, _f, C.c_int, C.c_int, _f, C.c_int,
                                       C.c_float, C.c_float, _i32, I64]
@@ -481,6 +484,25 @@ def f32_bin(sc, lights, H, W, radii, kappa=1.0, eps=1e-7, tile=8):
     keys = np.zeros(max(total, 1), dtype=np.uint32)
     vals = np.zeros(max(total, 1), dtype=np.uint32)
     lib().orc_f32_bin(*args, keys.ctypes.data_as(_u32), vals.ctypes.data_as(_u32), total)
+    return keys[:total], vals[:total]
+
+
+def f32_bin_keys(sc, lights, H, W, radii, keys_wanted, kappa=1.0, eps=1e-7, tile=8):
+    """f32_bin restricted to the (light, tile) keys `keys_wanted` (key = l *
+    n_tiles + tile): the same (key, value) pairs, only for those tiles."""
+    lights = _c32(lights).reshape(-1, 3)
+    radii = _c32(radii)
+    want = np.unique(np.asarray(keys_wanted, dtype=np.uint32))
+    args = (_pf(sc.means), _pf(sc.scales), _pf(sc.quats), _pf(sc.opac), sc.n, _pf(lights), lights.shape[0],
+            H, W, _pf(radii), radii.shape[0], float(kappa), float(eps), int(tile),
+            want.ctypes.data_as(_u32), int(want.size))
+    empty = np.zeros(1, dtype=np.uint32)
+    total = lib().orc_f32_bin_keys(*args, empty.ctypes.data_as(_u32), empty.ctypes.data_as(_u32), 0)
+    if total < 0:
+        raise ValueError("invalid Gaussian input")
+    keys = np.zeros(max(total, 1), dtype=np.uint32)
+    vals = np.zeros(max(total, 1), dtype=np.uint32)
+    lib().orc_f32_bin_keys(*args, keys.ctypes.data_as(_u32), vals.ctypes.data_as(_u32), total)
     return keys[:total], vals[:total]
 
 

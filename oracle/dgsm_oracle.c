@@ -993,6 +993,100 @@ int64_t orc_f32_bin(const float *means, const float *scales, const float *quats,
     return bad ? -1 : total;
 }
 
+/* The same specification restricted to the listed (light, tile) keys
+ * (key = l * n_tiles + tile, keys ascending): the pairs of those tiles only,
+ * in (key, Gaussian) order, up to `capacity`; returns their total (or -1 if
+ * an input was invalid).  Affordable at full size, where orc_f32_bin, which
+ * tests every tile against every Gaussian, is not. */
+int64_t orc_f32_bin_keys(const float *means, const float *scales, const float *quats, const float *opac,
+                         int64_t N, const float *lights, int L, int H, int W, const float *radii, int K,
+                         float kappa, float eps, int tile, const uint32_t *want, int n_want, uint32_t *keys,
+                         uint32_t *vals, int64_t capacity) {
+    int ty = (H + tile - 1) / tile, tx = (W + tile - 1) / tile;
+    int n_tiles = ty * tx;
+    int bad = 0;
+    int64_t *cnt = (int64_t *)calloc((size_t)n_want + 1, sizeof(int64_t));
+    float *cones = (float *)malloc(sizeof(float) * 9 * (N > 0 ? N : 1));
+    float *axes = (float *)malloc(sizeof(float) * 12 * (N > 0 ? N : 1));
+    float *k2s = (float *)malloc(sizeof(float) * (N > 0 ? N : 1));
+    char *ok = (char *)malloc(N > 0 ? N : 1);
+    int64_t written = 0;
+    for (int l = 0; l < L; ++l) {
+        int w0 = 0, w1 = 0;  /* the wanted keys of light l: [w0, w1) */
+        while (w0 < n_want && (int)(want[w0] / n_tiles) < l) ++w0;
+        w1 = w0;
+        while (w1 < n_want && (int)(want[w1] / n_tiles) == l) ++w1;
+        if (w1 == w0) continue;
+        int bad_l = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad_l)
+        for (int64_t n = 0; n < N; ++n) {
+            int r = orc_f32_gauss_cone(means + 3 * n, scales + 3 * n, opac[n], lights + 3 * l, kappa, eps,
+                                       radii[K - 1], cones + 9 * n);
+            for (int c = 0; c < 4; ++c)
+                if (!isfinite(quats[4 * n + c])) r = -1;
+            if (r < 0) bad_l = 1;
+            ok[n] = r == 1;
+            if (ok[n]) {
+                orc_f32_gauss_axes(means + 3 * n, scales + 3 * n, quats + 4 * n, lights + 3 * l, axes + 12 * n);
+                volatile float w = cones[9 * n + 6] * 1.0009765625f;
+                k2s[n] = w;
+            }
+        }
+        bad |= bad_l;
+        /* two passes over the wanted tiles: count, then write at the offsets */
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1) {
+                int64_t acc = written;
+                for (int q = w0; q < w1; ++q) {
+                    int64_t c = cnt[q];
+                    cnt[q] = acc;
+                    acc += c;
+                }
+                written = acc;
+            }
+#pragma omp parallel for schedule(dynamic, 1)
+            for (int q = w0; q < w1; ++q) {
+                int t = (int)(want[q] % n_tiles);
+                int a = t / tx, b = t % tx;
+                int i0 = a * tile, j0 = b * tile;
+                int i1 = i0 + tile < H ? i0 + tile : H, j1 = j0 + tile < W ? j0 + tile : W;
+                int si0 = (a / 8) * 8 * tile, sj0 = (b / 8) * 8 * tile;
+                int si1 = si0 + 8 * tile < H ? si0 + 8 * tile : H, sj1 = sj0 + 8 * tile < W ? sj0 + 8 * tile : W;
+                float tc[6], tp[17], sup[13];
+                orc_f32_rect_cone(i0, i1, j0, j1, H, W, tc);
+                orc_f32_rect_planes(i0, i1, j0, j1, tile / 2, H, W, tp);
+                sup[12] = 0.0f;
+                if (g_atlas_map == 1 && (si1 - 1) / W == si0 / W + 1) {
+                    int cut = ((si1 - 1) / W) * W;
+                    orc_f32_rect_cone(si0, cut, sj0, sj1, H, W, sup);
+                    orc_f32_rect_cone(cut, si1, sj0, sj1, H, W, sup + 6);
+                    sup[12] = 1.0f;
+                } else {
+                    orc_f32_rect_cone(si0, si1, sj0, sj1, H, W, sup);
+                }
+                int64_t c = 0, pos = pass == 1 ? cnt[q] : 0;
+                for (int64_t n = 0; n < N; ++n) {
+                    if (!ok[n]) continue;
+                    if (!f32_overlap(cones + 9 * n, sup) && !(sup[12] != 0.0f && f32_overlap(cones + 9 * n, sup + 6)))
+                        continue;
+                    if (!f32_overlap(cones + 9 * n, tc)) continue;
+                    unsigned m = f32_half_mask(tp, axes + 12 * n, k2s[n], cones[9 * n + 5] != 0.0f);
+                    if (!m) continue;
+                    if (pass == 1 && pos < capacity) {
+                        keys[pos] = want[q];
+                        vals[pos] = (uint32_t)n | (m << 30);
+                    }
+                    ++pos;
+                    ++c;
+                }
+                if (pass == 0) cnt[q] = c;
+            }
+        }
+    }
+    free(cnt); free(cones); free(axes); free(k2s); free(ok);
+    return bad ? -1 : written;
+}
+
 /* Number of Gaussian-ray evaluations the method must make at the listed
  * texels (l,i,j): pairs whose ray from light l cuts the Gaussian's culling
  * ellipsoid {(x-mu)^T A (x-mu) <= k^2} at t > 0 (k^2 from the binning

@@ -354,7 +354,9 @@ double *g_fit_scratch_ptr[FIT_STATIC_MAX_DEVICES] = {};
 
 // Device address of the static scratch on `dev` (which must be current).  In
 // host code the symbol names a host-side stand-in, so the address is taken
-// once per device with cudaGetSymbolAddress and cached.
+// once per device with cudaGetSymbolAddress and cached.  The cache outlives
+// nothing but the device's context: after cudaDeviceReset the address is
+// stale, which the header states.
 int fit_scratch_address(int dev, double **out) {
     std::lock_guard<std::mutex> lock(g_fit_scratch_mu);
     if (!g_fit_scratch_ptr[dev]) {
@@ -385,6 +387,9 @@ extern "C" int sh_fit_static(const float *dirs, const float *rgb, const float *w
     cudaStream_t s = (cudaStream_t)stream;
     const int nblocks = (int)std::min<int64_t>(
         std::min<int64_t>((n + FIT_THREADS - 1) / FIT_THREADS, (int64_t)sms), FIT_STATIC_BLOCKS);
+    // an error left by earlier work of the caller's is reported, not cleared,
+    // so that the launch check below sees this call's launches only
+    if (cudaPeekAtLastError() != cudaSuccess) return DGSM_ERR_CUDA;
     // every partial slot the solve reads is rewritten below; only the status starts at zero
     if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return DGSM_ERR_CUDA;
     sh_fit_partial_kernel<<<nblocks, FIT_THREADS, 0, s>>>(dirs, rgb, w, n, scratch);

@@ -50,6 +50,89 @@ def test_room_build_sampled_texels(nat, orc, room):
     assert np.exp(-tau).min() < 0.5  # the sample sees real shadow
 
 
+def _texel_of(orc, direction, H, W):
+    """(row, column) of the texel holding a direction (row i <-> v, column j <-> u)."""
+    u, v = orc.octa_encode(np.asarray(direction, dtype=np.float64))
+    return min(max(int((v + 1) * 0.5 * H), 0), H - 1), min(max(int((u + 1) * 0.5 * W), 0), W - 1)
+
+
+def test_room_build_shadow_texels(nat, orc, room):
+    """256 texels of the room atlas against the FP64 brute force: the deepest
+    shadows and the sharpest shadow edges the build found, the avatar's
+    shadow, texels along the octahedral fold and at the map's corners (the
+    direction straight down), and random ones."""
+    wl, d, atlas, _, _ = room
+    H, W = wl["H"], wl["W"]
+    A = atlas[0].double().cpu().numpy()          # [K][H][W]
+    rng = np.random.default_rng(14)
+    last = A[-1]
+    deep = np.argsort(last, axis=None)[:4000]
+    edge = np.abs(np.diff(A[-1], axis=1))
+    edges = np.argsort(edge, axis=None)[::-1][:4000]
+    pick = list(rng.choice(deep, 64, replace=False))
+    pick += [int(i * W + j) for i, j in zip(*np.unravel_index(rng.choice(edges, 64, replace=False), edge.shape))]
+    o = wl["lights"][0].astype(np.float64)
+    sl = wl["occluders"].meta["avatar"]
+    av = wl["occluders"].means[sl].astype(np.float64)
+    for p in av[rng.choice(len(av), 32, replace=False)]:
+        i, j = _texel_of(orc, p - o, H, W)
+        pick.append(i * W + j)
+    fold = [(i, j) for i in range(H) for j in range(W)
+            if abs(abs((2 * j + 1) / W - 1) + abs((2 * i + 1) / H - 1) - 1) < 2.0 / W]
+    pick += [i * W + j for i, j in (fold[k] for k in rng.choice(len(fold), 32, replace=False))]
+    pick += [0, W - 1, (H - 1) * W, H * W - 1]
+    rest = 256 - len(set(pick))
+    pick += list(rng.choice(H * W, rest + 16, replace=False))
+    flat = np.array(sorted(set(int(x) for x in pick)))[:256]
+    lij = np.stack([np.zeros_like(flat), flat // W, flat % W], 1).astype(np.int32)
+    tau = orc.build_tau_texels(wl["occluders"], wl["lights"], H, W, wl["radii"], lij)
+    got = A[:, lij[:, 1], lij[:, 2]].T
+    err = np.abs(got - np.exp(-tau))
+    assert lij.shape[0] == 256
+    assert err.max() <= TOL_F32, err.max()
+    assert np.exp(-tau).min() < 1e-3 and (np.exp(-tau)[:, -1] < 0.5).sum() >= 64
+
+
+def test_room_binning_bit_exact_sampled_tiles(nat, orc, room):
+    """The 512 x 512 room's tile lists equal the binning specification bit
+    for bit on about 300 tiles: the longest lists, tiles across the fold,
+    tiles toward the avatar, the corners, and random ones."""
+    wl, d, _, _, _ = room
+    H, W, tile = wl["H"], wl["W"], 8
+    tx = W // tile
+    kg, vg = nat.dgsm_bin(d["means"], d["scales"], d["quats"], d["opac"], dev(wl["lights"]), H, W,
+                          dev(wl["radii"]))
+    kg = kg.cpu().numpy().astype(np.uint32)
+    vg = vg.cpu().numpy().astype(np.uint32)
+    counts = np.bincount(kg, minlength=(H // tile) * tx)
+    rng = np.random.default_rng(15)
+    want = set(np.argsort(counts)[::-1][:60].tolist())
+    for t in range(counts.size):
+        ti, tj = divmod(t, tx)
+        u = [(2 * (tj * tile + q) + 1) / W - 1 for q in (0, tile - 1)]
+        v = [(2 * (ti * tile + q) + 1) / H - 1 for q in (0, tile - 1)]
+        sums = [abs(a) + abs(b) for a in u for b in v]
+        if min(sums) < 1 < max(sums) and rng.random() < 0.25:
+            want.add(t)
+    o = wl["lights"][0].astype(np.float64)
+    sl = wl["occluders"].meta["avatar"]
+    av = wl["occluders"].means[sl].astype(np.float64)
+    for p in av[rng.choice(len(av), 40, replace=False)]:
+        i, j = _texel_of(orc, p - o, H, W)
+        want.add((i // tile) * tx + j // tile)
+    want |= {0, tx - 1, counts.size - tx, counts.size - 1}
+    for t in rng.permutation(counts.size).tolist():   # random tiles up to 300 in all
+        if len(want) >= 300:
+            break
+        want.add(t)
+    want = np.array(sorted(want), dtype=np.uint32)
+    assert want.size == 300
+    ko, vo = orc.f32_bin_keys(wl["occluders"], wl["lights"], H, W, wl["radii"], want)
+    m = np.isin(kg, want)
+    assert ko.size > 10 ** 6
+    assert np.array_equal(kg[m], ko) and np.array_equal(vg[m], vo)
+
+
 def test_room_attenuate_sampled_queries(nat, orc, room):
     wl, d, atlas, out, T = room
     sc = wl["occluders"]

@@ -320,3 +320,96 @@ def test_attenuate_weights_and_direct_fraction(orc):
     np.testing.assert_allclose(out, c64 * (0.5 + 0.5 * 0.2), rtol=1e-7)
     out, T = orc.attenuate(atlas, radii, lights, qm, col, atlas_dyn=atlas, want_T=True)
     np.testing.assert_allclose(T, np.tile([0.04, 0.25, 0.81], (10, 1)), rtol=1e-12)
+
+
+def _room_like_scene(seed):
+    """The room's shapes at a size the brute force covers: 2 mm floor discs
+    3-5 m from a light 2.8 m above the floor, wall discs up to the height of
+    the light (their rays cross the fold |u| + |v| = 1 of the octahedral map)
+    and small avatar Gaussians."""
+    rng = np.random.default_rng(seed)
+    n_f, n_w = 120, 90
+    r = rng.uniform(1.8, 4.0, n_f)
+    phi = rng.uniform(0, 2 * np.pi, n_f)
+    floor_m = np.stack([r * np.cos(phi), r * np.sin(phi), np.zeros(n_f)], 1)
+    floor_s = np.stack([np.exp(rng.normal(math.log(0.05), 0.5, n_f)),
+                        np.exp(rng.normal(math.log(0.05), 0.5, n_f)), np.full(n_f, 0.002)], 1)
+    yaw = rng.uniform(0, np.pi, n_f)
+    floor_q = np.stack([np.cos(yaw / 2), np.zeros(n_f), np.zeros(n_f), np.sin(yaw / 2)], 1)
+    wall_m = np.stack([np.full(n_w, 4.0), rng.uniform(-3, 3, n_w), rng.uniform(2.0, 3.0, n_w)], 1)
+    wall_s = np.stack([np.full(n_w, 0.002), np.exp(rng.normal(math.log(0.05), 0.5, n_w)),
+                       np.exp(rng.normal(math.log(0.05), 0.5, n_w))], 1)
+    wall_q = np.tile([1.0, 0.0, 0.0, 0.0], (n_w, 1))
+    n = n_f + n_w
+    room = scenes.Scene(np.float32(np.concatenate([floor_m, wall_m])), np.float32(np.concatenate([floor_s, wall_s])),
+                        np.float32(np.concatenate([floor_q, wall_q])), np.float32(rng.uniform(0.05, 0.95, n)),
+                        np.float32(rng.random((n, 3))))
+    return scenes.concat(room, scenes.avatar_body(rng, 60, base=(1.5, 0.0, 0.0)))
+
+
+def test_binning_is_conservative_room_shapes(orc):
+    sc = _room_like_scene(21)
+    o = np.float32([0.0, 0.0, 2.8])
+    radii = scenes.radii_geometric(0.05, 12, 16)
+    H = W = 96
+    tile = 8
+    keys, vals = orc.f32_bin(sc, o[None], H, W, radii, eps=1e-7, tile=tile)
+    got = set()
+    for k, v in zip(keys.tolist(), vals.tolist()):
+        for h in (0, 1):
+            if (v >> (30 + h)) & 1:
+                got.add((k, v & IDX, h))
+    need = _brute_lists(orc, sc, o, H, W, tile, radii, 1e-7)
+    assert len(need) > 300
+    assert need <= got, sorted(need - got)[:5]
+    # some of the needed pairs lie on tiles across the octahedral fold
+    tx = W // tile
+    fold = 0
+    for (t, g, h) in need:
+        ti, tj = divmod(t, tx)
+        u = [(2 * (tj * tile + d) + 1) / W - 1 for d in (0, tile - 1)]
+        v = [(2 * (ti * tile + d) + 1) / H - 1 for d in (0, tile - 1)]
+        s = [abs(a) + abs(b) for a in u for b in v]
+        fold += min(s) < 1 < max(s)
+    assert fold > 0
+
+
+def test_binned_sum_matches_full_sum_room_shapes(orc):
+    sc = _room_like_scene(22)
+    o = np.float32([0.0, 0.0, 2.8])
+    H = W = 48
+    tile = 8
+    radii = scenes.radii_geometric(0.05, 12, 12)
+    eps = 1e-7
+    keys, vals = orc.f32_bin(sc, o[None], H, W, radii, eps=eps, tile=tile)
+    full = orc.build_tau(sc, o[None], H, W, radii)[0]
+    tx = W // tile
+    worst = 0.0
+    for t in range((H // tile) * (W // tile)):
+        ti, tj = divmod(int(t), tx)
+        for h in (0, 1):
+            sel = (keys == t) & (((vals >> (30 + h)) & 1) == 1)
+            r0 = ti * tile + h * tile // 2
+            blk = (slice(None), slice(r0, r0 + tile // 2), slice(tj * tile, tj * tile + tile))
+            part = (orc.build_tau(scenes.subset(sc, vals[sel] & IDX), o[None], H, W, radii)[0][blk]
+                    if sel.any() else 0.0)
+            worst = max(worst, float(np.max(np.abs(part - full[blk]))))
+    assert worst <= sc.n * eps
+    assert full.max() > 0.5   # the sample holds real shadow
+
+
+def test_bin_keys_is_the_specification_on_its_tiles(orc):
+    """The tile-filtered binning (used at full size) returns exactly the full
+    specification's pairs of the requested tiles."""
+    rng = np.random.default_rng(23)
+    sc = _room_like_scene(23)
+    lights = np.float32([[0.0, 0.0, 2.8], [1.0, 1.0, 2.5]])
+    radii = scenes.radii_geometric(0.05, 12, 16)
+    for H, W, tile in [(64, 64, 8), (40, 56, 8), (64, 48, 16), (36, 28, 4)]:
+        ko, vo = orc.f32_bin(sc, lights, H, W, radii, tile=tile)
+        nt = -(-H // tile) * -(-W // tile)
+        want = rng.choice(2 * nt, min(60, 2 * nt), replace=False)
+        ks, vs = orc.f32_bin_keys(sc, lights, H, W, radii, want, tile=tile)
+        m = np.isin(ko, want)
+        assert ks.size > 0
+        assert np.array_equal(ks, ko[m]) and np.array_equal(vs, vo[m])

@@ -22,11 +22,14 @@ def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a)).cuda()
 
 
-def _static_fit(nat, D, Y, w, lam):
+def _static_fit(nat, D, Y, w, lam, outs=None):
     """Call the C entry point directly through ctypes (device buffers from torch)."""
-    sh = torch.empty((3, 9), dtype=torch.float32, device="cuda")
-    sh64 = torch.empty((3, 9), dtype=torch.float64, device="cuda")
-    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    if outs is None:
+        outs = (torch.empty((3, 9), dtype=torch.float32, device="cuda"),
+                torch.empty((3, 9), dtype=torch.float64, device="cuda"),
+                torch.empty((1,), dtype=torch.int32, device="cuda"))
+    sh, sh64, status = outs
+    status.fill_(-1)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     rc = nat._lib.sh_fit_static(ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
                                 ctypes.c_void_p(w.data_ptr()), D.shape[0], float(lam),
@@ -45,9 +48,17 @@ def test_static_fit_matches_sh_fit_twice_in_a_row():
     for (D, Y, w), lam in cases:
         D, Y, w = _dev(D), _dev(Y), _dev(w)
         ref, ref64 = nat.sh_fit(D, Y, w, lam=lam, want64=True)
-        for _ in range(2):  # the second call reuses the scratch the first one filled
-            sh, sh64, status = _static_fit(nat, D, Y, w, lam)
+        outs = None
+        for call in range(2):  # the second call reuses the scratch the first one filled
+            if call == 1:
+                # the outputs already exist: the call itself must take no device memory
+                torch.cuda.synchronize()
+                free0, used0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+            sh, sh64, status = outs = _static_fit(nat, D, Y, w, lam, outs)
             torch.cuda.synchronize()
+            if call == 1:
+                assert torch.cuda.mem_get_info()[0] == free0
+                assert torch.cuda.memory_allocated() == used0
             assert int(status.item()) == 0
             np.testing.assert_allclose(sh64.cpu().numpy(), ref64.cpu().numpy(), rtol=1e-10, atol=1e-12)
             np.testing.assert_allclose(sh.cpu().numpy(), ref.cpu().numpy(), rtol=1e-6, atol=1e-7)

@@ -371,12 +371,47 @@ def run_ours(args, rank, world, local_rank):
     line["ablations"] = time_ablations(nat, (means, scales, quats, opac, colors), lights, radii, H, W,
                                        atlas, flush, stream)
     line["gpu_launches"] = count_launches(args, L)
+    if rank == 0 and world == 1 and not args.no_reports:
+        line.update(side_reports())
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, evals, args.cpu_texels)
     if dist is not None:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def side_reports():
+    """The precision, learned-surrogate and batched-frame reports, compact, so
+    that the batched and learned forms are measured beside the plain form on
+    the same GPU in the same run (the full reports: bench.py --report ...)."""
+    import torch
+
+    from paper_2601_01660_b300 import reports
+    out = {}
+    p = reports.precision()
+    out["precision"] = {
+        "workload": p["workload"],
+        "max_abs_dT_vs_f32_store": {dt: [round(v["max"], 7) for v in p["abs_dT_vs_f32"][dt].values()]
+                                    for dt in ("f16", "bf16")},
+        "build_ms": p["build_ms"]}
+    torch.cuda.empty_cache()
+    s = reports.surrogate()
+    out["surrogate"] = {
+        "workload": s["workload"],
+        "abs_dT_vs_exact": {k: {"p50": round(v["p50"], 6), "p99": round(v["p99"], 6)}
+                            for k, v in s["abs_dT_vs_exact"].items()},
+        "fallback_tile_fraction": {k: v for k, v in s["fallback_tile_fraction"].items() if k != "rule"},
+        "memory_bytes": s["memory_bytes"],
+        "gaussians_per_s": s["gaussians_per_s"],
+        "training_s": s["training"]["seconds_total"]}
+    torch.cuda.empty_cache()
+    f = reports.frame()
+    out["frame"] = {"workload": f["workload"], "ms_per_frame": f["ms_per_frame"],
+                    "graph_nodes_per_frame": f["graph_nodes_per_frame"], "stage_ms": f["stage_ms"],
+                    "chosen": f["chosen"]}
+    torch.cuda.empty_cache()
+    return out
 
 
 def time_ablations(nat, gauss, lights, radii, H, W, atlas, flush, stream, F=208):
@@ -760,6 +795,8 @@ def main():
     ap.add_argument("--cpu-texels", type=int, default=72)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-reports", action="store_true",
+                    help="leave out the precision, surrogate and frame reports of the line")
     ap.add_argument("--report", choices=["precision", "surrogate", "frame", "field"],
                     help="print a side report (one JSON line) instead of the step benchmark")
     args = ap.parse_args()

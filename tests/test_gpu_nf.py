@@ -142,3 +142,93 @@ def test_surrogate_attenuation_light_groups(nat):
         assert torch.allclose(T[sel, l], T_ex[sel, l], atol=1e-6)
     f = 1.0 - 0.8 + 0.8 * (T * lw[None, :]).sum(1)
     assert torch.allclose(out, qc * f[:, None], rtol=1e-5, atol=1e-6)
+
+
+def test_surrogate_attenuation_field_path_matches_oracle(nat, orc):
+    """nf_attenuate without a mask, query by query against the oracle: (u, v)
+    from the FP64 octahedral encode of x - o, rho = (k + w) / (K - 1) from the
+    FP64 shell search, the FP64 field, then the light weighting and the
+    direct fraction."""
+    L, H, W, K = 2, 64, 64, 16
+    radii = scenes.radii_geometric(0.05, 12.0, K)
+    lights = np.float32([[0.0, 0.0, 0.0], [0.5, -0.3, 0.4]])
+    params = np.stack([_params(21), _params(22)])
+    q = scenes.cube_scene(4000, seed=23)
+    q.means[:50] *= np.float32(4.0)          # some beyond the last shell (rho = 1)
+    lw, wd = np.float32([0.7, 0.3]), 0.8
+    out, T = nat.nf_attenuate(dev(params), dev(radii), dev(lights), dev(q.means), dev(q.colors), H, W,
+                              light_w=dev(lw), direct_frac=wd, want_T=True)
+    T = T.double().cpu().numpy()
+    Tref = np.zeros_like(T)
+    r64 = radii.astype(np.float64)
+    for l in range(L):
+        v = q.means.astype(np.float64) - lights[l].astype(np.float64)
+        uv = np.array([orc.octa_encode(x) for x in v])
+        t = np.linalg.norm(v, axis=1)
+        k = np.searchsorted(r64, t, side="right") - 1
+        kc = np.clip(k, 0, K - 2)
+        w = (t - r64[kc]) / (r64[kc + 1] - r64[kc])
+        rho = np.where(k < 0, 0.0, np.where(k >= K - 1, 1.0, (kc + w) / (K - 1)))
+        Tref[:, l], _ = onf.forward(params[l], np.float32(np.column_stack([uv, rho])))
+    err = np.abs(T - Tref)
+    # as for the forward pass: float32 inputs and sums against FP64 ones can move
+    # a bfloat16 rounding of a feature or activation by one ulp on a few samples
+    assert np.quantile(err, 0.99) <= 1e-3 and err.max() <= 1e-2 and err.mean() <= 2e-4, \
+        (np.quantile(err, 0.99), err.max(), err.mean())
+    ref = q.colors.astype(np.float64) * (1.0 - wd + wd * (Tref * lw[None, :]).sum(1))[:, None]
+    eo = np.abs(out.double().cpu().numpy() - ref)
+    assert np.quantile(eo, 0.99) <= 1e-3 and eo.max() <= 1e-2
+
+
+def _texel_dirs(H, W):
+    j = (2 * torch.arange(W, device="cuda", dtype=torch.float64) + 1) / W - 1
+    i = (2 * torch.arange(H, device="cuda", dtype=torch.float64) + 1) / H - 1
+    v, u = torch.meshgrid(i, j, indexing="ij")
+    z = 1 - u.abs() - v.abs()
+    x = torch.where(z < 0, torch.where(u >= 0, 1.0, -1.0) * (1 - v.abs()), u)
+    y = torch.where(z < 0, torch.where(v >= 0, 1.0, -1.0) * (1 - u.abs()), v)
+    d = torch.stack([x, y, z], -1)
+    return (d / d.norm(dim=-1, keepdim=True)).float()
+
+
+def test_trained_field_needs_fewer_exact_tiles_than_an_equal_memory_atlas(nat):
+    """What the learned field gains over the method without it.  Both stand
+    in for a light's exact 512x512x64 atlas of the cube scene under one rule:
+    a tile whose largest error over its 8x8x64 voxels exceeds 0.02 keeps its
+    exact voxels.  The field (18,753 parameters, bfloat16: 37.5 KB) is set
+    against an exact atlas built directly at the same memory (24x24x16
+    float32 voxels, 36.9 KB, sampled by the trilinear lookup).  The field
+    leaves fewer tiles to the fallback, so at the same error bound the pair
+    (field + exact tiles) needs less memory."""
+    occ = scenes.cube_scene(20_000, seed=0)
+    lights = scenes.four_lights()[:2]
+    H = W = 512
+    K, tile, tol = 64, 8, 0.02
+    radii = scenes.radii_geometric(0.05, 12.0, K)
+    d = scene_to_dev(occ)
+    lt, rt = dev(lights), dev(radii)
+    atlas = nat.dgsm_build(d["means"], d["scales"], d["quats"], d["opac"], lt, H, W, rt)
+    small_r = dev(scenes.radii_geometric(0.05, 12.0, 16))
+    small = nat.dgsm_build(d["means"], d["scales"], d["quats"], d["opac"], lt, 24, 24, small_r)
+    P = nat.nf_param_count()
+    dirs = _texel_dirs(H, W)
+    fb_field = fb_small = 0
+    for l in range(2):
+        p = nat.nf_init(seed=100 + l, n_lights=1)[0].contiguous()
+        m, v = torch.zeros(P, device="cuda"), torch.zeros(P, device="cuda")
+        step0 = 0
+        for steps, lr in ((6000, 2e-3), (3000, 5e-4), (1000, 1e-4)):
+            nat.nf_train(atlas[l], p, m, v, steps=steps, batch=16384, lr=lr, seed=l + 1, step0=step0)
+            step0 += steps
+        fb_field += int((nat.nf_tile_error(p, atlas[l], tile=tile) > tol).sum())
+        err = torch.zeros(H // tile, W // tile, device="cuda")
+        for k in range(K):
+            pts = (lt[l][None, None, :] + rt[k] * dirs).reshape(-1, 3).contiguous()
+            _, Ts = nat.dgsm_attenuate(small[l:l + 1].contiguous(), small_r, lt[l:l + 1].contiguous(), pts,
+                                       torch.ones_like(pts), want_T=True)
+            e = (Ts[:, 0].reshape(H, W) - atlas[l, k]).abs()
+            err = torch.maximum(err, e.reshape(H // tile, tile, W // tile, tile).amax(dim=(1, 3)))
+        fb_small += int((err > tol).sum())
+    n_tiles = 2 * (H // tile) * (W // tile)
+    assert 0.05 * n_tiles < fb_small < 0.9 * n_tiles      # the baseline is neither trivial nor hopeless
+    assert fb_field < 0.95 * fb_small, (fb_field, fb_small)

@@ -408,8 +408,9 @@ def side_reports():
     torch.cuda.empty_cache()
     f = reports.frame()
     out["frame"] = {"workload": f["workload"], "ms_per_frame": f["ms_per_frame"],
-                    "graph_nodes_per_frame": f["graph_nodes_per_frame"], "stage_ms": f["stage_ms"],
-                    "chosen": f["chosen"]}
+                    "graph_nodes_per_frame": f["graph_nodes_per_frame"],
+                    "persistent_graph_nodes_per_frame": f["persistent_graph_nodes_per_frame"],
+                    "persistent_status": f["persistent_status"], "stage_ms": f["stage_ms"], "chosen": f["chosen"]}
     torch.cuda.empty_cache()
     return out
 

@@ -489,10 +489,82 @@ int dgsm_rigid_transform(dgsm_ctx *ctx, const float *means, const float *quats, 
                          const int64_t *seg, int32_t n_obj, const float *poses, float *means_out,
                          float *quats_out, void *stream);
 
+/* The moving-avatar frame (static scene + rigidly moving avatars, Secs.
+ * 3.2-3.5) as ONE persistent cooperative kernel: every block stays resident
+ * and the frame's steps are separated by grid-wide barriers instead of
+ * kernel boundaries.  In order:
+ *   1. rigid motion of the avatars to `poses` (as dgsm_rigid_transform);
+ *   2. the avatars' dynamic atlases for all lights (as dgsm_build with
+ *      tile 8 and params->max_pairs > 0: prep, the two binning levels, work
+ *      items and the closed-form accumulation, Eqs. 3-4);
+ *   3. every Gaussian, static then avatar, attenuated by
+ *      T_static,l x T_dyn,l with light weights 1/L (as dgsm_attenuate_dyn);
+ *   4. per-avatar alpha-weighted centroids (as dgsm_segment_centroids, the
+ *      same FP64 sums in the same order) and the SH relight of the avatars
+ *      (Eqs. 8-10, as sh_relight_objects).
+ * Results equal those of the separate calls up to the order of floating-
+ * point atomic sums in the atlas.  The launch (a memset of its barrier state
+ * and one cooperative kernel) may be captured in a CUDA graph.
+ *
+ * Every barrier wait is bounded: a block that waits longer than about two
+ * seconds (clock64 cycles at the SM clock) records DGSM_ERR_TIMEOUT in the
+ * context's status word and returns, and so does every other block at its
+ * next barrier; the context stays usable and the next call starts afresh.
+ * timeout_barrier in 1..7 makes that barrier give up at once (a test of the
+ * failure path); -1 (or any other value) for none.  The outputs of a frame
+ * that timed out are incomplete.
+ *
+ * Arguments (all device pointers unless stated; float32):
+ *   q_means (n_static + n_avatar, 3): the receivers; rows n_static.. are
+ *     overwritten with the moved avatar means;
+ *   colors_in, colors_out (n_static + n_avatar, 3);
+ *   static_atlas [L][K][H][W] float32 with its radii (K floats);
+ *   rest_means (n_avatar, 3), rest_quats (n_avatar, 4; 16-byte aligned),
+ *     scales (n_avatar, 3), opac (n_avatar): the avatars at rest;
+ *   quats_out (n_avatar, 4; 16-byte aligned): the moved rotations;
+ *   seg: HOST array of n_obj + 1 offsets (as for sh_relight_objects);
+ *   poses: n_obj x 8 floats, device or host (pinned when captured), copied
+ *     on `stream` when the frame runs;
+ *   dyn_atlas [L][K_dyn][H_dyn][W_dyn] float32 (written) with radii_dyn;
+ *   lights (L, 3), 1 <= L <= 64; sh: 3 x 9 probe coefficients;
+ *   centroids_out (n_obj, 3) (written); direct_frac as for dgsm_attenuate.
+ * params: tile 8, atlas_dtype DGSM_F32, the octahedral map, max_pairs > 0
+ * (capacity of both binning levels; a frame over it records
+ * DGSM_ERR_WORKSPACE and leaves T_dyn = 1); L x super-tiles of the dynamic
+ * atlas <= 4096 and L x tiles <= 65536.  Asynchronous; returns DGSM_OK,
+ * DGSM_ERR_INVALID_ARG, DGSM_ERR_WORKSPACE (workspace would grow during a
+ * capture) or DGSM_ERR_CUDA (the message names the call). */
+typedef struct dgsm_crowd_frame_args {
+    const float *q_means;
+    const float *colors_in;
+    float *colors_out;
+    int64_t n_static;
+    const float *static_atlas;
+    int32_t H, W, K;
+    const float *radii;
+    const float *rest_means, *rest_quats, *scales, *opac;
+    float *quats_out;
+    int64_t n_avatar;
+    const int64_t *seg;
+    int32_t n_obj;
+    const float *poses;
+    float *dyn_atlas;
+    int32_t H_dyn, W_dyn, K_dyn;
+    const float *radii_dyn;
+    const float *lights;
+    int32_t L;
+    const float *sh;
+    float *centroids_out;
+    float direct_frac;
+} dgsm_crowd_frame_args;
+
+int dgsm_crowd_frame(dgsm_ctx *ctx, const dgsm_crowd_frame_args *args, const dgsm_params *params,
+                     const dgsm_relight_params *rparams, int32_t timeout_barrier, void *stream);
+
 /* CUDA-graph capture of library calls on `stream` (a created stream, not
  * the legacy default stream).  Between dgsm_graph_begin and dgsm_graph_end
  * only asynchronous calls may be made: dgsm_build with params->max_pairs > 0,
- * dgsm_attenuate, dgsm_rigid_transform, dgsm_segment_centroids,
+ * dgsm_attenuate, dgsm_rigid_transform, dgsm_segment_centroids, dgsm_crowd_frame,
  * sh_relight(_objects), sh_fit, dgsm_weighted_centroid, nf_attenuate.  The
  * context's workspace must already be large enough: make the same calls once
  * before capturing (a call that would grow it fails with

@@ -85,6 +85,18 @@ class FrameHostIn(C.Structure):
                 ("cube_w", C.c_void_p), ("n_cube", C.c_int64), ("lam", C.c_double)]
 
 
+class CrowdFrameArgs(C.Structure):
+    """Mirror of dgsm_crowd_frame_args (device pointers except seg, and poses when pinned)."""
+    _fields_ = [("q_means", C.c_void_p), ("colors_in", C.c_void_p), ("colors_out", C.c_void_p),
+                ("n_static", C.c_int64), ("static_atlas", C.c_void_p), ("H", C.c_int32), ("W", C.c_int32),
+                ("K", C.c_int32), ("radii", C.c_void_p), ("rest_means", C.c_void_p), ("rest_quats", C.c_void_p),
+                ("scales", C.c_void_p), ("opac", C.c_void_p), ("quats_out", C.c_void_p), ("n_avatar", C.c_int64),
+                ("seg", C.c_void_p), ("n_obj", C.c_int32), ("poses", C.c_void_p), ("dyn_atlas", C.c_void_p),
+                ("H_dyn", C.c_int32), ("W_dyn", C.c_int32), ("K_dyn", C.c_int32), ("radii_dyn", C.c_void_p),
+                ("lights", C.c_void_p), ("L", C.c_int32), ("sh", C.c_void_p), ("centroids_out", C.c_void_p),
+                ("direct_frac", C.c_float)]
+
+
 _vp = C.c_void_p
 _i32, _i64, _f32, _f64 = C.c_int32, C.c_int64, C.c_float, C.c_double
 
@@ -148,6 +160,8 @@ _lib.sh_relight_objects.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp
                                     C.POINTER(RelightParams), _vp, _vp]
 _lib.dgsm_segment_centroids.argtypes = [_vp, _vp, _vp, _i64, _vp, _i32, _vp, _vp]
 _lib.dgsm_rigid_transform.argtypes = [_vp, _vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp, _vp]
+_lib.dgsm_crowd_frame.argtypes = [_vp, C.POINTER(CrowdFrameArgs), C.POINTER(Params), C.POINTER(RelightParams),
+                                  _i32, _vp]
 _lib.dgsm_graph_begin.argtypes = [_vp, _vp]
 _lib.dgsm_graph_end.argtypes = [_vp, _vp, C.POINTER(_vp)]
 _lib.dgsm_graph_launch.argtypes = [_vp, _vp]
@@ -700,6 +714,51 @@ def dgsm_rigid_transform(means, quats, seg, poses, means_out=None, quats_out=Non
                                         _ptr(poses), _ptr(means_out), _ptr(quats_out),
                                         _stream(stream)))
     return means_out, quats_out
+
+
+def dgsm_crowd_frame(q_means, colors_in, colors_out, n_static, static_atlas, radii, rest_means, rest_quats,
+                     scales, opac, quats_out, seg, poses, dyn_atlas, radii_dyn, lights, sh, centroids_out,
+                     direct_frac=1.0, params=None, relight_params=None, timeout_barrier=-1,
+                     ctx: Context | None = None, stream=None):
+    """The moving-avatar frame as one persistent cooperative kernel
+    (dgsm_crowd_frame): rigid motion, the dynamic atlases (tile 8, params
+    max_pairs > 0), attenuation of every receiver by static x dynamic atlases,
+    per-avatar centroids and relight.  q_means rows n_static.. receive the
+    moved avatar means.  timeout_barrier 1..7 makes that grid barrier give up
+    (DGSM_ERR_TIMEOUT in the status word)."""
+    ctx = ctx or context(q_means.device.index)
+    for t, nm, k in ((q_means, "q_means", 3), (colors_in, "colors_in", 3), (colors_out, "colors_out", 3),
+                     (radii, "radii", None), (rest_means, "rest_means", 3), (rest_quats, "rest_quats", 4),
+                     (scales, "scales", 3), (opac, "opac", None), (quats_out, "quats_out", 4),
+                     (radii_dyn, "radii_dyn", None), (lights, "lights", 3), (sh, "sh", None),
+                     (centroids_out, "centroids_out", 3)):
+        _need(t, nm, shape_last=k)
+    _need(static_atlas, "static_atlas")
+    _need(dyn_atlas, "dyn_atlas")
+    if poses.dtype != torch.float32 or not poses.is_contiguous() or tuple(poses.shape[1:]) != (8,):
+        raise ValueError("poses must be a contiguous (n_obj, 8) float32 tensor")
+    n_av = rest_means.shape[0]
+    segs, n_obj = _segs(seg, n_av)
+    L, K, H, W = static_atlas.shape
+    Ld, Kd, Hd, Wd = dyn_atlas.shape
+    if Ld != L or lights.shape[0] != L:
+        raise ValueError("one static and one dynamic atlas per light")
+    if q_means.shape[0] != n_static + n_av:
+        raise ValueError("q_means holds the static receivers, then the avatars")
+    a = CrowdFrameArgs()
+    a.q_means, a.colors_in, a.colors_out, a.n_static = _ptr(q_means), _ptr(colors_in), _ptr(colors_out), n_static
+    a.static_atlas, a.H, a.W, a.K, a.radii = _ptr(static_atlas), H, W, K, _ptr(radii)
+    a.rest_means, a.rest_quats, a.scales, a.opac = _ptr(rest_means), _ptr(rest_quats), _ptr(scales), _ptr(opac)
+    a.quats_out, a.n_avatar = _ptr(quats_out), n_av
+    a.seg, a.n_obj, a.poses = C.cast(segs, C.c_void_p), n_obj, _ptr(poses)
+    a.dyn_atlas, a.H_dyn, a.W_dyn, a.K_dyn, a.radii_dyn = _ptr(dyn_atlas), Hd, Wd, Kd, _ptr(radii_dyn)
+    a.lights, a.L, a.sh, a.centroids_out = _ptr(lights), L, _ptr(sh), _ptr(centroids_out)
+    a.direct_frac = float(direct_frac)
+    p = params if isinstance(params, Params) else Params.make(**(params or {}))
+    rp = relight_params if isinstance(relight_params, RelightParams) else RelightParams.make(**(relight_params or {}))
+    ctx.check(_lib.dgsm_crowd_frame(ctx.handle, C.byref(a), C.byref(p), C.byref(rp), int(timeout_barrier),
+                                    _stream(stream)))
+    return colors_out
 
 
 class Graph:

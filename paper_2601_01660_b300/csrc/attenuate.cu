@@ -12,48 +12,10 @@
 #include <algorithm>
 
 #include "dgsm_internal.cuh"
+#include "lookup.cuh"
 
 namespace dgsm {
 namespace {
-
-template <typename T>
-__device__ __forceinline__ float load_T(const T *p);
-template <>
-__device__ __forceinline__ float load_T<float>(const float *p) { return __ldg(p); }
-template <>
-__device__ __forceinline__ float load_T<__half>(const __half *p) { return __half2float(__ldg(p)); }
-template <>
-__device__ __forceinline__ float load_T<__nv_bfloat16>(const __nv_bfloat16 *p) {
-    return __bfloat162float(__ldg(p));
-}
-
-// Trilinear lookup in one light's atlas A [K][H][W] (at most 2^32 voxels, so
-// 32-bit offsets); inw[k] = 1 / (radii[k+1] - radii[k]).
-template <typename T>
-__device__ __forceinline__ float lookup(const T *__restrict__ A, int H, int W, int K,
-                                        const SampleIndex &s, const float *rs, const float *inw) {
-    // rows clamped to the point's face (the whole atlas for the octahedral map)
-    const int j0 = min(max(s.bj, 0), W - 1), j1 = min(max(s.bj + 1, 0), W - 1);
-    const int rlo = s.r0, rhi = s.r0 + s.hf - 1;
-    const int i0 = min(max(s.bi, rlo), rhi), i1 = min(max(s.bi + 1, rlo), rhi);
-    int k0, k1;
-    float wt;
-    if (s.k < 0) { k0 = k1 = 0; wt = 0.0f; }
-    else if (s.k >= K - 1) { k0 = k1 = K - 1; wt = 0.0f; }
-    else { k0 = s.k; k1 = s.k + 1; wt = (s.t - rs[k0]) * inw[k0]; }
-    const uint32_t plane = (uint32_t)H * (uint32_t)W;
-    const uint32_t o00 = (uint32_t)i0 * W + j0, o01 = (uint32_t)i0 * W + j1;
-    const uint32_t o10 = (uint32_t)i1 * W + j0, o11 = (uint32_t)i1 * W + j1;
-    const float fx = s.fx, fy = s.fy;
-    const T *P0 = A + (uint32_t)k0 * plane;
-    float b0 = (1.0f - fy) * ((1.0f - fx) * load_T(P0 + o00) + fx * load_T(P0 + o01)) +
-               fy * ((1.0f - fx) * load_T(P0 + o10) + fx * load_T(P0 + o11));
-    if (k1 == k0) return b0;
-    const T *P1 = A + (uint32_t)k1 * plane;
-    float b1 = (1.0f - fy) * ((1.0f - fx) * load_T(P1 + o00) + fx * load_T(P1 + o01)) +
-               fy * ((1.0f - fx) * load_T(P1 + o10) + fx * load_T(P1 + o11));
-    return (1.0f - wt) * b0 + wt * b1;
-}
 
 constexpr int ATT_THREADS = 256;
 constexpr int ATT_U = 4;  // queries in flight per thread

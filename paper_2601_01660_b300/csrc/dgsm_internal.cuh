@@ -40,6 +40,8 @@ enum WsSlot {
     WS_SEGS,           // splat render: per-tile segment counts and offsets, the segments
     WS_PART,           // splat render: per-segment partial colour and transmittance of each pixel
     WS_NORMALS,        // pca normals: bucket keys and order, bucket ranges, sorted points
+    WS_PFRAME,         // persistent frame kernel: control words, binning, items, records
+    WS_PF_CONES,       // persistent frame kernel: the dynamic atlas's tile cones
     WS_NSLOTS
 };
 
@@ -65,6 +67,9 @@ struct dgsm_ctx {
     // side stream and events of dgsm_frame_host (copies beside compute)
     cudaStream_t side = nullptr;
     cudaEvent_t fev[4] = {};
+    // tile cones of the persistent frame kernel: valid for this buffer and atlas size
+    void *pf_cones = nullptr;
+    int pf_cones_h = 0, pf_cones_w = 0;
 };
 
 #include <nvtx3/nvToolsExt.h>

@@ -8,11 +8,10 @@
 #include <algorithm>
 
 #include "dgsm_internal.cuh"
+#include "motion.cuh"
 
 namespace dgsm {
 namespace {
-
-constexpr int CEN_THREADS = 256;
 
 __global__ void __launch_bounds__(CEN_THREADS) centroid_partial_kernel(
     const float *__restrict__ means, const float *__restrict__ w, int64_t n,
@@ -58,48 +57,19 @@ __global__ void centroid_final_kernel(const double *__restrict__ partials, int n
 __global__ void __launch_bounds__(CEN_THREADS) segment_centroid_partial_kernel(
     const float *__restrict__ means, const float *__restrict__ w, const __grid_constant__ Segs segs,
     double *__restrict__ partials) {
-    const int o = blockIdx.y;
-    const long long b = segs.s[o], e = segs.s[o + 1];
-    double a[4] = {0.0, 0.0, 0.0, 0.0};
-    for (long long i = b + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < e;
-         i += (long long)gridDim.x * blockDim.x) {
-        const double wi = w ? (double)w[i] : 1.0;
-        a[0] += wi * means[3 * i];
-        a[1] += wi * means[3 * i + 1];
-        a[2] += wi * means[3 * i + 2];
-        a[3] += wi;
-    }
     __shared__ double red[CEN_THREADS / 32][4];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int c = 0; c < 4; ++c) {
-        double x = a[c];
-        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-        if (lane == 0) red[warp][c] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x < 4) {
-        double x = 0.0;
-        for (int q = 0; q < CEN_THREADS / 32; ++q) x += red[q][threadIdx.x];
-        partials[4 * ((int64_t)o * gridDim.x + blockIdx.x) + threadIdx.x] = x;
-    }
+    centroid_partial_block(
+        w, segs, blockIdx.y, blockIdx.x, gridDim.x,
+        [&](long long i) { return make_float3(means[3 * i], means[3 * i + 1], means[3 * i + 2]); }, partials,
+        red);
 }
 
 // One warp per object.
 __global__ void segment_centroid_final_kernel(const double *__restrict__ partials, int nb, int n_obj,
                                               float *__restrict__ out) {
-    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (o >= n_obj) return;
-    double a[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = lane; b < nb; b += 32)
-        for (int c = 0; c < 4; ++c) a[c] += partials[4 * ((int64_t)o * nb + b) + c];
-    for (int c = 0; c < 4; ++c)
-        for (int off = 16; off > 0; off >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], off);
-    if (lane == 0) {
-        const double inv = a[3] > 0.0 ? 1.0 / a[3] : 0.0;
-        out[3 * o] = (float)(a[0] * inv);
-        out[3 * o + 1] = (float)(a[1] * inv);
-        out[3 * o + 2] = (float)(a[2] * inv);
-    }
+    centroid_final_warp(partials, nb, o, out);
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }

@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "dgsm_internal.cuh"
+#include "motion.cuh"
 
 namespace dgsm {
 namespace {
@@ -20,33 +21,16 @@ __global__ void __launch_bounds__(RT_THREADS) rigid_transform_kernel(
     float *__restrict__ quats_out) {
     // per object: unit rotation quaternion (w,x,y,z), translation, row-major R
     __shared__ float P[MAX_OBJECTS][16];
-    for (int o = threadIdx.x; o < segs.n; o += blockDim.x) {
-        float w = poses[8 * o], x = poses[8 * o + 1], y = poses[8 * o + 2], z = poses[8 * o + 3];
-        const float inv = rsqrtf(w * w + x * x + y * y + z * z);
-        w *= inv; x *= inv; y *= inv; z *= inv;
-        float *r = P[o];
-        r[0] = w; r[1] = x; r[2] = y; r[3] = z;
-        r[4] = poses[8 * o + 4]; r[5] = poses[8 * o + 5]; r[6] = poses[8 * o + 6];
-        r[7] = 1.f - 2.f * (y * y + z * z); r[8] = 2.f * (x * y - w * z); r[9] = 2.f * (x * z + w * y);
-        r[10] = 2.f * (x * y + w * z); r[11] = 1.f - 2.f * (x * x + z * z); r[12] = 2.f * (y * z - w * x);
-        r[13] = 2.f * (x * z - w * y); r[14] = 2.f * (y * z + w * x); r[15] = 1.f - 2.f * (x * x + y * y);
-    }
+    for (int o = threadIdx.x; o < segs.n; o += blockDim.x) pose_matrix(poses + 8 * o, P[o]);
     __syncthreads();
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
          g += (int64_t)gridDim.x * blockDim.x) {
         const float *r = P[segs.n == 1 ? 0 : seg_find(segs, g)];
-        const float mx = means[3 * g], my = means[3 * g + 1], mz = means[3 * g + 2];
-        means_out[3 * g] = r[7] * mx + r[8] * my + r[9] * mz + r[4];
-        means_out[3 * g + 1] = r[10] * mx + r[11] * my + r[12] * mz + r[5];
-        means_out[3 * g + 2] = r[13] * mx + r[14] * my + r[15] * mz + r[6];
-        const float4 q = reinterpret_cast<const float4 *>(quats)[g];  // (w, x, y, z)
-        const float w1 = r[0], x1 = r[1], y1 = r[2], z1 = r[3];
-        float4 o;
-        o.x = w1 * q.x - x1 * q.y - y1 * q.z - z1 * q.w;
-        o.y = w1 * q.y + x1 * q.x + y1 * q.w - z1 * q.z;
-        o.z = w1 * q.z - x1 * q.w + y1 * q.x + z1 * q.y;
-        o.w = w1 * q.w + x1 * q.z - y1 * q.y + z1 * q.x;
-        reinterpret_cast<float4 *>(quats_out)[g] = o;
+        const float3 m = pose_point(r, means[3 * g], means[3 * g + 1], means[3 * g + 2]);
+        means_out[3 * g] = m.x;
+        means_out[3 * g + 1] = m.y;
+        means_out[3 * g + 2] = m.z;
+        reinterpret_cast<float4 *>(quats_out)[g] = pose_quat(r, reinterpret_cast<const float4 *>(quats)[g]);
     }
 }
 

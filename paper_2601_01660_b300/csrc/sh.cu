@@ -4,31 +4,10 @@
 #include <mutex>
 
 #include "dgsm_internal.cuh"
+#include "relight.cuh"
 
 namespace dgsm {
 namespace {
-
-// Real SH basis to degree 2, index l^2 + l + m, no Condon-Shortley phase.
-// Normalisations sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!), times sqrt(2) for
-// m != 0, with the Cartesian forms of the associated Legendre factors.
-constexpr double SH_C0 = 0.28209479177387814;   // 1/2 sqrt(1/pi)
-constexpr double SH_C1 = 0.48860251190291992;   // sqrt(3/(4 pi))
-constexpr double SH_C2 = 1.09254843059207907;   // 1/2 sqrt(15/pi)
-constexpr double SH_C20 = 0.31539156525252005;  // 1/4 sqrt(5/pi)
-constexpr double SH_C22 = 0.54627421529603959;  // 1/4 sqrt(15/pi)
-
-template <typename F>
-__device__ __forceinline__ void sh9(F x, F y, F z, F *Y) {
-    Y[0] = F(SH_C0);
-    Y[1] = F(SH_C1) * y;
-    Y[2] = F(SH_C1) * z;
-    Y[3] = F(SH_C1) * x;
-    Y[4] = F(SH_C2) * x * y;
-    Y[5] = F(SH_C2) * y * z;
-    Y[6] = F(SH_C20) * (F(3) * z * z - F(1));
-    Y[7] = F(SH_C2) * x * z;
-    Y[8] = F(SH_C22) * (x * x - y * y);
-}
 
 constexpr int FIT_THREADS = 256;
 constexpr int FIT_NV = 45 + 27;  // upper triangle of B^T W B, then B^T W Y (9 x 3)
@@ -146,6 +125,8 @@ __global__ void sh_fit_solve_kernel(const double *__restrict__ partials, int nbl
 // Radiance transfer.  Each block first tabulates the lat-long quadrature
 // (direction, weight w_j, w_j L_c(w_j)) in shared memory, then contracts it
 // against the lobe of each of its Gaussians.
+constexpr int RELIGHT_G = 4;  // Gaussians per thread in relight_kernel
+
 __global__ void __launch_bounds__(256) relight_kernel(
     const float *__restrict__ sh, const float *__restrict__ means, const float *__restrict__ quats,
     const float *__restrict__ scales, const float *__restrict__ normals,
@@ -159,85 +140,34 @@ __global__ void __launch_bounds__(256) relight_kernel(
     if (!normals)
         for (int k = threadIdx.x; k < 3 * segs.n; k += blockDim.x) cen[k] = centroid[k];
     __syncthreads();
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        const int it = j / nph, ip = j - it * nph;
-        float st, ct, sp, cp;
-        sincospif((it + 0.5f) / nth, &st, &ct);
-        sincospif(2.0f * (ip + 0.5f) / nph, &sp, &cp);
-        const float ox = st * cp, oy = st * sp, oz = ct;
-        float Y[9];
-        sh9<float>(ox, oy, oz, Y);
-        float Lc[3];
-        for (int c = 0; c < 3; ++c) {
-            float acc = 0.0f;
-            for (int k = 0; k < 9; ++k) acc = fmaf(shs[9 * c + k], Y[k], acc);
-            Lc[c] = acc;
-        }
-        tab[2 * j] = make_float4(ox, oy, oz, st);
-        tab[2 * j + 1] = make_float4(st * Lc[0], st * Lc[1], st * Lc[2], 0.0f);
-    }
+    relight_table_fill(shs, 0, M, nth, nph, tab);
     __syncthreads();
-    const bool lambert = q == 1.0f;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        float nx, ny, nz;
-        if (normals) {
-            nx = normals[3 * g]; ny = normals[3 * g + 1]; nz = normals[3 * g + 2];
-            const float inv = rsqrtf(nx * nx + ny * ny + nz * nz);
-            nx *= inv; ny *= inv; nz *= inv;
-        } else {
-            float qw = quats[4 * g], qx = quats[4 * g + 1], qy = quats[4 * g + 2], qz = quats[4 * g + 3];
-            const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-            qw *= qn; qx *= qn; qy *= qn; qz *= qn;
-            const float s0 = scales[3 * g], s1 = scales[3 * g + 1], s2 = scales[3 * g + 2];
-            int k = 0;
-            float sm = s0;
-            if (s1 < sm) { k = 1; sm = s1; }
-            if (s2 < sm) k = 2;
-            // column k of R(q): the Gaussian's k-th local axis
-            if (k == 0) {
-                nx = 1.f - 2.f * (qy * qy + qz * qz); ny = 2.f * (qx * qy + qw * qz); nz = 2.f * (qx * qz - qw * qy);
-            } else if (k == 1) {
-                nx = 2.f * (qx * qy - qw * qz); ny = 1.f - 2.f * (qx * qx + qz * qz); nz = 2.f * (qy * qz + qw * qx);
+    // RELIGHT_G Gaussians per thread, blockDim apart: one read of each table
+    // entry serves all of them, which keeps the loop on the FP32 pipe
+    const int64_t per_block = (int64_t)blockDim.x * RELIGHT_G;
+    for (int64_t base = (int64_t)blockIdx.x * per_block; base < N; base += (int64_t)gridDim.x * per_block) {
+        float3 n[RELIGHT_G];
+#pragma unroll
+        for (int r = 0; r < RELIGHT_G; ++r) {
+            const int64_t g = base + r * (int64_t)blockDim.x + threadIdx.x;
+            if (g >= N) {
+                n[r] = make_float3(0.f, 0.f, 1.f);  // a padding slot: summed, never written
+            } else if (normals) {
+                n[r] = make_float3(normals[3 * g], normals[3 * g + 1], normals[3 * g + 2]);
+                const float inv = rsqrtf(n[r].x * n[r].x + n[r].y * n[r].y + n[r].z * n[r].z);
+                n[r].x *= inv; n[r].y *= inv; n[r].z *= inv;
             } else {
-                nx = 2.f * (qx * qz + qw * qy); ny = 2.f * (qy * qz - qw * qx); nz = 1.f - 2.f * (qx * qx + qy * qy);
-            }
-            const int o = segs.n == 1 ? 0 : seg_find(segs, g);
-            const float cx = cen[3 * o], cy = cen[3 * o + 1], cz = cen[3 * o + 2];
-            const float side = nx * (means[3 * g] - cx) + ny * (means[3 * g + 1] - cy) +
-                               nz * (means[3 * g + 2] - cz);
-            if (side < 0.0f) { nx = -nx; ny = -ny; nz = -nz; }
-        }
-        float num0 = 0.f, num1 = 0.f, num2 = 0.f, den = 0.f;
-        if (lambert) {
-#pragma unroll 4
-            for (int j = 0; j < M; ++j) {
-                const float4 a = tab[2 * j], b = tab[2 * j + 1];
-                const float S = fmaxf(fmaf(a.x, nx, fmaf(a.y, ny, a.z * nz)), 0.0f);
-                den = fmaf(S, a.w, den);
-                num0 = fmaf(S, b.x, num0);
-                num1 = fmaf(S, b.y, num1);
-                num2 = fmaf(S, b.z, num2);
-            }
-        } else {
-            for (int j = 0; j < M; ++j) {
-                const float4 a = tab[2 * j], b = tab[2 * j + 1];
-                const float c = fmaf(a.x, nx, fmaf(a.y, ny, a.z * nz));
-                const float S = c > 0.0f ? exp2f(q * log2f(c)) : 0.0f;
-                den = fmaf(S, a.w, den);
-                num0 = fmaf(S, b.x, num0);
-                num1 = fmaf(S, b.y, num1);
-                num2 = fmaf(S, b.z, num2);
+                const int o = segs.n == 1 ? 0 : seg_find(segs, g);
+                n[r] = relight_axis_normal(means, quats, scales, g, cen[3 * o], cen[3 * o + 1], cen[3 * o + 2]);
             }
         }
-        const float inv = 1.0f / (den + eps);
-        const float sc0 = fminf(fmaxf(num0 * inv, 0.0f), t_max);
-        const float sc1 = fminf(fmaxf(num1 * inv, 0.0f), t_max);
-        const float sc2 = fminf(fmaxf(num2 * inv, 0.0f), t_max);
-        const float c0 = cin[3 * g], c1 = cin[3 * g + 1], c2 = cin[3 * g + 2];
-        cout[3 * g] = fmaxf(gamma * c0 * sc0, 0.0f);
-        cout[3 * g + 1] = fmaxf(gamma * c1 * sc1, 0.0f);
-        cout[3 * g + 2] = fmaxf(gamma * c2 * sc2, 0.0f);
+        float4 acc[RELIGHT_G];
+        relight_accumulate<RELIGHT_G>(tab, M, q, n, acc);
+#pragma unroll
+        for (int r = 0; r < RELIGHT_G; ++r) {
+            const int64_t g = base + r * (int64_t)blockDim.x + threadIdx.x;
+            if (g < N) relight_write(acc[r], eps, t_max, gamma, cin, cout, g);
+        }
     }
 }
 
@@ -286,7 +216,13 @@ int relight_launch(dgsm_ctx *ctx, const float *sh, const float *means, const flo
     const size_t smem = (size_t)p.n_theta * p.n_phi * 2 * sizeof(float4);
     e = cudaFuncSetAttribute(relight_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "relight smem attribute");
-    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 2);
+    // as many blocks as fit at once (the table decides), at most one group of
+    // RELIGHT_G x 256 Gaussians each
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, relight_kernel, 256, smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "relight occupancy");
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>((n + 256 * RELIGHT_G - 1) / (256 * RELIGHT_G), (int64_t)ctx->num_sms * std::max(per_sm, 1)));
     relight_kernel<<<grid, 256, smem, (cudaStream_t)stream>>>(
         sh, means, quats, scales, normals, centroids, segs, colors_in, n, p.q, p.gamma, p.t_max,
         p.eps, p.n_theta, p.n_phi, colors_out);

@@ -11,6 +11,10 @@ avatars whose atlases are rebuilt every frame:
   4. per-avatar alpha-weighted centroids and the SH relight of the avatars
      (dgsm_segment_centroids, sh_relight_objects; Sec. 3.5).
 
+With persistent=True the four steps run as ONE persistent cooperative
+kernel (dgsm_crowd_frame: grid-wide barriers between the steps instead of
+kernel boundaries, tile 8, capacity build).
+
 `capture()` records these calls once into CUDA graphs; a frame is then one
 graph launch.  Two graphs alternate between two pinned pose buffers, so the
 host writes the poses of frame f + 1 while frame f runs.  Every step runs in
@@ -30,8 +34,10 @@ def _dev(a, device):
 
 class CrowdFrame:
     def __init__(self, static, avatars, seg, lights, H, W, radii, H_dyn, W_dyn, radii_dyn, sh,
-                 build_params=None, relight_params=None, device="cuda", ctx=None):
+                 build_params=None, relight_params=None, device="cuda", ctx=None, persistent=False):
         self.nat = nat = native()
+        self.persistent = persistent
+        self.timeout_barrier = -1  # 1..7: that grid barrier of the persistent kernel gives up
         self.device = torch.device(device)
         self.ctx = ctx or nat.Context(self.device.index or 0)
         self.stream = torch.cuda.Stream(device=self.device)
@@ -79,6 +85,13 @@ class CrowdFrame:
     # -- one frame as library calls ------------------------------------------
     def _calls(self, poses, max_pairs):
         nat, s, ctx = self.nat, self.stream, self.ctx
+        if self.persistent and max_pairs > 0:
+            nat.dgsm_crowd_frame(self.q_means, self.colors_in, self.colors_out, self.n_static, self.static_atlas,
+                                 self.radii, self.rest_means, self.rest_quats, self.av_scales, self.av_opac,
+                                 self.av_quats, self.seg, poses, self.dyn_atlas, self.radii_dyn, self.lights,
+                                 self.sh, self.centroids, params=dict(self.bp, tile=8, max_pairs=max_pairs),
+                                 relight_params=self.rp, timeout_barrier=self.timeout_barrier, ctx=ctx, stream=s)
+            return
         nat.dgsm_rigid_transform(self.rest_means, self.rest_quats, self.seg, poses,
                                  means_out=self.av_means, quats_out=self.av_quats, ctx=ctx, stream=s)
         nat.dgsm_build(self.av_means, self.av_scales, self.av_quats, self.av_opac, self.lights,

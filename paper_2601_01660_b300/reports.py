@@ -250,6 +250,19 @@ def frame(frames: int = 120) -> dict:
     names = ["rigid_transform", "dynamic_build", "attenuate_static_x_dynamic", "centroids", "relight"]
     stages = {nm: ev[i].elapsed_time(ev[i + 1]) for i, nm in enumerate(names)}
     cf.close()
+    # the same frames as one persistent cooperative kernel (tile 8), direct and in a graph
+    cf.persistent = True
+    cf.bp.update(tile=8)
+    for _ in range(3):
+        cf.step_eager(poses[0], max_pairs=cf.max_pairs)
+    ms_pk, wall_pk = run(lambda p: cf.step_eager(p, max_pairs=cf.max_pairs), frames)
+    status_pk = nat.dgsm_sync_status(cf.ctx, stream=s)
+    nodes_pk = cf.capture()
+    for _ in range(3):
+        cf.step_graph(poses[0])
+    ms_pkg, wall_pkg = run(cf.step_graph, frames)
+    status_pkg = nat.dgsm_sync_status(cf.ctx, stream=s)
+    cf.close()
     return {
         "report": "frame",
         "workload": "crowd8: 1.5M static + 8 x 100k avatars, 4 lights; static 512x512x64 (built once), "
@@ -259,10 +272,13 @@ def frame(frames: int = 120) -> dict:
         "chosen": {"tile": tile, "chunk": chunk}, "max_pairs": cf.max_pairs,
         "dynamic_build_pairs": stats["n_pairs"], "dynamic_ray_evals": stats["ray_evals"],
         "ms_per_frame": {"direct_blocking_build": round(ms_sync, 3), "direct_capacity_build": round(ms_cap, 3),
-                         "graph_replay": round(ms_graph, 3)},
+                         "graph_replay": round(ms_graph, 3), "persistent_kernel": round(ms_pk, 3),
+                         "persistent_kernel_graph": round(ms_pkg, 3)},
         "host_ms_per_frame": {"direct_blocking_build": round(wall_sync, 3),
-                              "direct_capacity_build": round(wall_cap, 3), "graph_replay": round(wall_graph, 3)},
+                              "direct_capacity_build": round(wall_cap, 3), "graph_replay": round(wall_graph, 3),
+                              "persistent_kernel": round(wall_pk, 3), "persistent_kernel_graph": round(wall_pkg, 3)},
         "graph_nodes_per_frame": nodes, "status_after_replay": status,
+        "persistent_graph_nodes_per_frame": nodes_pk, "persistent_status": [status_pk, status_pkg],
         "stage_ms": {k2: round(v, 4) for k2, v in stages.items()},
     }
 

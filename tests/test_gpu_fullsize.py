@@ -164,15 +164,17 @@ def test_room_relight_sampled_gaussians(nat, orc, room):
     assert np.quantile(rel.max(1), 0.998) <= 1e-3   # a normal turned within rounding may differ
 
 
-def test_crowd_frame_full_size(nat, orc):
-    """The 8-avatar frame at full size under graph replay: the dynamic atlas on
-    sampled texels and the final colours on sampled Gaussians."""
+@pytest.mark.parametrize("persistent", [False, True])
+def test_crowd_frame_full_size(nat, orc, persistent):
+    """The 8-avatar frame at full size under graph replay, as separate calls
+    and as the persistent frame kernel: the dynamic atlas on sampled texels
+    and the final colours on sampled Gaussians."""
     from paper_2601_01660_b300.frame import CrowdFrame
     wl = scenes.workload("crowd8")
     D, Y, w = wl["cubemap"]
     sh = nat.sh_fit(dev(D), dev(Y), dev(w))
     cf = CrowdFrame(wl["static"], wl["avatars"], wl["seg"], wl["lights"], wl["H"], wl["W"], wl["radii"],
-                    wl["H_dyn"], wl["W_dyn"], wl["radii_dyn"], sh)
+                    wl["H_dyn"], wl["W_dyn"], wl["radii_dyn"], sh, persistent=persistent)
     try:
         cf.size_pairs([scenes.avatar_poses(wl["motion"], f) for f in range(0, 120, 30)])
         cf.capture()

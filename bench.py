@@ -410,7 +410,8 @@ def side_reports():
     out["frame"] = {"workload": f["workload"], "ms_per_frame": f["ms_per_frame"],
                     "graph_nodes_per_frame": f["graph_nodes_per_frame"],
                     "persistent_graph_nodes_per_frame": f["persistent_graph_nodes_per_frame"],
-                    "persistent_status": f["persistent_status"], "stage_ms": f["stage_ms"], "chosen": f["chosen"]}
+                    "persistent_status": f["persistent_status"], "persistent_phase_ms": f["persistent_phase_ms"],
+                    "stage_ms": f["stage_ms"], "chosen": f["chosen"]}
     torch.cuda.empty_cache()
     return out
 
@@ -798,6 +799,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-reports", action="store_true",
                     help="leave out the precision, surrogate and frame reports of the line")
+    ap.add_argument("--frame-workload", choices=["crowd8", "crowd8s"], default="crowd8",
+                    help="the frame report's workload (crowd8s: a tenth of the Gaussians, for profiler captures)")
     ap.add_argument("--report", choices=["precision", "surrogate", "frame", "field"],
                     help="print a side report (one JSON line) instead of the step benchmark")
     args = ap.parse_args()
@@ -806,7 +809,7 @@ def main():
     rank, world, local_rank = _env_rank()
     if args.report:
         from paper_2601_01660_b300 import reports
-        reports.main(args.report)
+        reports.main(args.report, frame_workload=args.frame_workload)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -561,6 +561,13 @@ typedef struct dgsm_crowd_frame_args {
 int dgsm_crowd_frame(dgsm_ctx *ctx, const dgsm_crowd_frame_args *args, const dgsm_params *params,
                      const dgsm_relight_params *rparams, int32_t timeout_barrier, void *stream);
 
+/* Phase times of the last dgsm_crowd_frame run while profiling was enabled
+ * (dgsm_set_profiling): ms_out[0..7] (host) = the eight steps between the
+ * kernel's start, its seven grid barriers and the last block's end, read from
+ * the GPU's global timer.  Blocks.  Returns DGSM_ERR_INVALID_ARG when no
+ * profiled frame ran. */
+int dgsm_crowd_frame_phases(dgsm_ctx *ctx, double *ms_out);
+
 /* CUDA-graph capture of library calls on `stream` (a created stream, not
  * the legacy default stream).  Between dgsm_graph_begin and dgsm_graph_end
  * only asynchronous calls may be made: dgsm_build with params->max_pairs > 0,

@@ -162,6 +162,7 @@ _lib.dgsm_segment_centroids.argtypes = [_vp, _vp, _vp, _i64, _vp, _i32, _vp, _vp
 _lib.dgsm_rigid_transform.argtypes = [_vp, _vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp, _vp]
 _lib.dgsm_crowd_frame.argtypes = [_vp, C.POINTER(CrowdFrameArgs), C.POINTER(Params), C.POINTER(RelightParams),
                                   _i32, _vp]
+_lib.dgsm_crowd_frame_phases.argtypes = [_vp, C.POINTER(C.c_double)]
 _lib.dgsm_graph_begin.argtypes = [_vp, _vp]
 _lib.dgsm_graph_end.argtypes = [_vp, _vp, C.POINTER(_vp)]
 _lib.dgsm_graph_launch.argtypes = [_vp, _vp]
@@ -759,6 +760,15 @@ def dgsm_crowd_frame(q_means, colors_in, colors_out, n_static, static_atlas, rad
     ctx.check(_lib.dgsm_crowd_frame(ctx.handle, C.byref(a), C.byref(p), C.byref(rp), int(timeout_barrier),
                                     _stream(stream)))
     return colors_out
+
+
+def dgsm_crowd_frame_phases(ctx: Context | None = None):
+    """Milliseconds of the eight steps of the last profiled persistent frame
+    (P1 prep .. P8 attenuation and relight)."""
+    ctx = ctx or context()
+    out = (C.c_double * 8)()
+    ctx.check(_lib.dgsm_crowd_frame_phases(ctx.handle, out))
+    return list(out)
 
 
 class Graph:

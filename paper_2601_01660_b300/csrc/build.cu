@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256, 5) fine_count_kernel(
     const FineSmem sm = fine_smem(smem);
     const unsigned long long n_units = *n_units_dev;
     const int tid = threadIdx.x;
-    if (tid < 64) sm.wmask[tid][0] = sm.wmask[tid][1] = sm.wmask[tid][2] = 0u;
+    for (int k = tid; k < FB_WARPS * 64 * 3; k += blockDim.x) (&sm.wm[0][0][0])[k] = 0u;
     for (unsigned long long u = blockIdx.x; u < n_units; u += gridDim.x) {
         const Unit U = units[u];
         fine_count_unit(U, u, cvals, bin, N, tx, ty, sx, n_tiles, n_super, cones, fmask, tact, sm);

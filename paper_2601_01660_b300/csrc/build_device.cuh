@@ -44,6 +44,7 @@ struct __align__(16) BinRec {
 // mask (bit 30: the top half of the tile may be hit, bit 31: the bottom).
 constexpr uint32_t VAL_IDX = 0x3FFFFFFFu;
 constexpr int PLANE_F4 = 5;  // float4 per tile: top, bottom, left, right, mid planes
+constexpr unsigned FULLMASK = 0xffffffffu;
 
 struct __align__(16) Item {
     uint32_t key, start, end, n_items;
@@ -542,33 +543,106 @@ struct __align__(16) Unit {
 constexpr int MASK_WORDS = UNIT_G / 32;
 
 // Shared memory of one fine-binning unit (FINE_SMEM_BYTES, carved by the caller).
+constexpr int FB_WARPS = 8;                 // warps of a fine-binning block (256 threads)
+constexpr int FB_PAIRS = 32 * 16;           // (Gaussian, quad) pairs a warp can hold: 16 quads per lane
 struct FineSmem {
-    float4 *tdat;          // [64 * TDAT_F4] the super-tile's tile cones and planes
-    BinRec *grec;          // [FB_STAGE] the staged Gaussians' records
-    uint32_t *running;     // [64] pairs found per tile
-    int *tvalid;           // [64] tile exists (and is active)
-    uint32_t (*wmask)[3];  // [64][3] the current word's bitmaps of each tile; zero on entry and exit
+    float4 *tdat;           // [64 * TDAT_F4] the super-tile's tile cones and planes
+    float4 *qc;             // [16 * 2] cones of its 2x2-tile quads (see quad_cones)
+    BinRec *grec;           // [FB_STAGE] the staged Gaussians' records
+    uint32_t *running;      // [64] pairs found per tile
+    int *tvalid;            // [64] tile exists (and is active)
+    uint32_t (*wm)[64][3];  // [FB_WARPS][64][3] each warp's word of bitmaps per tile; zero on entry and exit
+    uint16_t (*plist)[FB_PAIRS];  // [FB_WARPS][FB_PAIRS] each warp's (lane << 4 | quad) pairs
+    uint16_t (*plist2)[128];      // [FB_WARPS][128] each warp's (lane << 6 | tile) pairs of 32 quad pairs
 };
-constexpr size_t FINE_SMEM_BYTES = sizeof(float4) * 64 * TDAT_F4 + sizeof(BinRec) * FB_STAGE +
-                                   sizeof(uint32_t) * 64 + sizeof(int) * 64 + sizeof(uint32_t) * 64 * 3;
+constexpr size_t FINE_SMEM_BYTES = sizeof(float4) * (64 * TDAT_F4 + 32) + sizeof(BinRec) * FB_STAGE +
+                                   sizeof(uint32_t) * 64 + sizeof(int) * 64 +
+                                   sizeof(uint32_t) * FB_WARPS * 64 * 3 + sizeof(uint16_t) * FB_WARPS * (FB_PAIRS + 128);
 
 __device__ __forceinline__ FineSmem fine_smem(void *base) {
     FineSmem sm;
     char *p = (char *)base;
     sm.tdat = (float4 *)p; p += sizeof(float4) * 64 * TDAT_F4;
+    sm.qc = (float4 *)p; p += sizeof(float4) * 32;
     sm.grec = (BinRec *)p; p += sizeof(BinRec) * FB_STAGE;
     sm.running = (uint32_t *)p; p += sizeof(uint32_t) * 64;
     sm.tvalid = (int *)p; p += sizeof(int) * 64;
-    sm.wmask = (uint32_t(*)[3])p;
+    sm.wm = (uint32_t(*)[64][3])p; p += sizeof(uint32_t) * FB_WARPS * 64 * 3;
+    sm.plist = (uint16_t(*)[FB_PAIRS])p; p += sizeof(uint16_t) * FB_WARPS * FB_PAIRS;
+    sm.plist2 = (uint16_t(*)[128])p;
     return sm;
 }
 
-// Fine binning of unit u (all threads of the block): the cone test of each of
-// its Gaussians against each of the super-tile's 64 tiles, then the ellipsoid
-// test of the overlapping pairs on consecutive lanes; writes the unit's three
-// bitmaps per tile to fmask and leaves the per-tile pair counts in
-// sm.running (read them after this returns; the call ends with a barrier).
-// tact (or nullptr): per (light, tile) 1 if it holds a texel of the region of
+// Quad q (tiles rows 2 (q / 4) + {0, 1}, columns 2 (q % 4) + {0, 1} of the
+// super-tile): a cone holding the cones of its valid tiles, as (axis xyz,
+// cos phi), (sin phi, flag, -, -), flag 0 = no valid tile, 1 = a cone,
+// 2 = every direction.  Axis c = the normalised sum of the tile axes, phi =
+// max over the tiles of (angle(c, axis_t) + phi_t) + 3e-3 rad; by the
+// triangle inequality on the sphere, a Gaussian cone that overlaps a tile's
+// cone then overlaps the quad's, and the 3e-3 rad and the 1e-5 slack of
+// quad_overlap cover the rounding of both tests (a cosine compared within
+// 1e-6 moves the angle by at most sqrt(2e-6) < 1.5e-3 rad).  A quad of
+// half-angle beyond pi/2 - 3e-3 (or holding a whole-sphere tile) admits every
+// Gaussian, whose cone is narrower than pi/2.
+__device__ __forceinline__ void quad_cone(const float4 *tdat, const int *tvalid, int q, float4 *out) {
+    const int t0 = (2 * (q / 4)) * SUPER + 2 * (q % 4);
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    bool any = false, whole = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int t = t0 + (k >> 1) * SUPER + (k & 1);
+        if (!tvalid[t]) continue;
+        const float4 c0 = tdat[TDAT_F4 * t], c1 = tdat[TDAT_F4 * t + 1];
+        any = true;
+        whole |= c1.y != 0.0f;
+        cx += c0.x; cy += c0.y; cz += c0.z;
+    }
+    if (!any) {
+        out[0] = make_float4(0.f, 0.f, 1.f, 1.f);
+        out[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const float cn = sqrtf(cx * cx + cy * cy + cz * cz);
+    float phi = 0.0f;
+    if (!whole && cn > 1e-6f) {
+        cx /= cn; cy /= cn; cz /= cn;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int t = t0 + (k >> 1) * SUPER + (k & 1);
+            if (!tvalid[t]) continue;
+            const float4 c0 = tdat[TDAT_F4 * t], c1 = tdat[TDAT_F4 * t + 1];
+            const float d = fminf(fmaxf(cx * c0.x + cy * c0.y + cz * c0.z, -1.0f), 1.0f);
+            phi = fmaxf(phi, acosf(d) + atan2f(c1.x, c0.w));
+        }
+        phi += 3e-3f;
+    }
+    if (whole || cn <= 1e-6f || phi >= 1.5707963f - 3e-3f) {
+        out[0] = make_float4(0.f, 0.f, 1.f, -1.f);
+        out[1] = make_float4(1.f, 2.f, 0.f, 0.f);
+        return;
+    }
+    out[0] = make_float4(cx, cy, cz, cosf(phi));
+    out[1] = make_float4(sinf(phi), 1.f, 0.f, 0.f);
+}
+
+// Does Gaussian cone g (axis g.a.xyz, cos g.a.w, sin g.b.x) reach quad cone
+// (c0, c1)?  Looser than the tiles' exact test (see quad_cone).
+__device__ __forceinline__ bool quad_overlap(const BinRec &g, const float4 &c0, const float4 &c1) {
+    if (c1.y == 0.0f) return false;
+    if (c1.y == 2.0f) return true;
+    const float dot = fmaf(g.a.x, c0.x, fmaf(g.a.y, c0.y, g.a.z * c0.z));
+    return dot >= fmaf(g.a.w, c0.w, -g.b.x * c1.x) - 1e-5f;
+}
+
+// Fine binning of unit u (all threads of the block): each warp takes 32 of
+// its Gaussians at a time; a Gaussian's cone is tested against the 16 quad
+// cones, the passing (Gaussian, quad) pairs are spread over the lanes, and
+// each pair gets the exact tests of the quad's tiles (the cone test, then
+// the ellipsoid planes).  Writes the unit's three bitmaps per tile to fmask
+// (the same bits as testing every tile: the quad test only skips tiles whose
+// exact cone test fails) and leaves the per-tile pair counts in sm.running
+// (read them after this returns; the call ends with a barrier).  tact (or
+// nullptr): per (light, tile) 1 if it holds a texel of the region of
 // interest.
 __device__ __forceinline__ void fine_count_unit(const Unit &U, unsigned long long u,
                                                 const uint32_t *__restrict__ cvals,
@@ -596,55 +670,86 @@ __device__ __forceinline__ void fine_count_unit(const Unit &U, unsigned long lon
         sm.tvalid[tid] = a < ty && b < tx && (!tact || tact[l * n_tiles + a * tx + b]);
         sm.running[tid] = 0u;
     }
+    __syncthreads();
+    if (tid < 16) quad_cone(sm.tdat, sm.tvalid, tid, sm.qc + 2 * tid);
     uint32_t *um = fmask + (size_t)u * 64 * 3 * MASK_WORDS;
+    uint32_t (*wm)[3] = sm.wm[warp];
+    uint16_t *pl = sm.plist[warp], *pl2 = sm.plist2[warp];
     for (uint32_t s0 = U.start; s0 < U.end; s0 += FB_STAGE) {
         const int ns = (int)min((uint32_t)FB_STAGE, U.end - s0);
-        __syncthreads();  // grec of the previous stage is no longer read
+        __syncthreads();  // grec of the previous stage is no longer read (and the quad cones are ready)
         for (int e = tid; e < ns; e += blockDim.x) sm.grec[e] = bin[(int64_t)l * N + cvals[s0 + e]];
         __syncthreads();
-        for (int grp = 0; grp < FB_STAGE; grp += 32) {
-            const int word = (int)(s0 - U.start + grp) / 32;
-            if (grp >= ns) {
-                // words past the unit's end stay empty
-                if (lane < 8)
-                    for (int m = 0; m < 3; ++m) um[((warp * 8 + lane) * 3 + m) * MASK_WORDS + word] = 0u;
-                continue;
+        const int grp = warp * 32;  // this warp's 32 Gaussians of the stage
+        if (grp >= ns) continue;    // words past the unit's end are never read
+        const int word = (int)(s0 - U.start + grp) / 32;
+        const int gl = grp + lane;
+        const bool gv = gl < ns;
+        BinRec G;
+        G.a = gv ? sm.grec[gl].a : make_float4(0.f, 0.f, 1.f, -1.f);
+        G.b = gv ? sm.grec[gl].b : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool inside = G.b.y == 2.0f;
+        // quads this Gaussian may reach
+        uint32_t qm = 0u;
+        if (gv && G.b.y != 0.0f) {
+#pragma unroll 4
+            for (int q = 0; q < 16; ++q) {
+                const float4 c0 = sm.qc[2 * q], c1 = sm.qc[2 * q + 1];
+                if (c1.y != 0.0f && (inside || quad_overlap(G, c0, c1))) qm |= 1u << q;
             }
-            const int gl = grp + lane;
-            const bool gv = gl < ns;
-            BinRec G;
-            G.a = gv ? sm.grec[gl].a : make_float4(0.f, 0.f, 1.f, -1.f);
-            G.b = gv ? sm.grec[gl].b : make_float4(0.f, 0.f, 0.f, 0.f);
-            const bool inside = G.b.y == 2.0f;
-            // cone tests of this warp's 8 tiles
-            unsigned cm[8];
-            int pc[9];
-            pc[0] = 0;
+        }
+        // spread the (Gaussian, quad) pairs over the warp's list
+        const int cnt = __popc(qm);
+        int off = cnt;
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-                const int t = warp * 8 + jj;
-                const bool ov = gv && G.b.y != 0.0f && sm.tvalid[t] &&
-                                (inside || cone_overlap_v(G, sm.tdat[TDAT_F4 * t], sm.tdat[TDAT_F4 * t + 1]));
-                cm[jj] = __ballot_sync(0xffffffffu, ov);
-                pc[jj + 1] = pc[jj] + __popc(cm[jj]);
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULLMASK, off, o);
+            if (lane >= o) off += y;
+        }
+        const int total = __shfl_sync(FULLMASK, off, 31);
+        off -= cnt;
+        for (uint32_t m = qm; m; m &= m - 1) pl[off++] = (uint16_t)((lane << 4) | (__ffs(m) - 1));
+        __syncwarp();
+        for (int r = 0; r < total; r += 32) {
+            // the cone tests of the quads' tiles, one (Gaussian, quad) pair per lane ...
+            const int e = r + lane;
+            uint32_t tm = 0u;
+            int gln = 0, t0 = 0;
+            if (e < total) {
+                const int pq = pl[e], q = pq & 15;
+                gln = pq >> 4;
+                t0 = (2 * (q / 4)) * SUPER + 2 * (q % 4);
+                BinRec Rc;
+                Rc.a = sm.grec[grp + gln].a;
+                Rc.b = sm.grec[grp + gln].b;
+                const bool rin = Rc.b.y == 2.0f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int t = t0 + (k >> 1) * SUPER + (k & 1);
+                    if (sm.tvalid[t] && (rin || cone_overlap_v(Rc, sm.tdat[TDAT_F4 * t], sm.tdat[TDAT_F4 * t + 1])))
+                        tm |= 1u << k;
+                }
             }
-            // ellipsoid tests of the overlapping (tile, Gaussian) pairs on consecutive lanes
-            const int total = pc[8];
-            for (int r = 0; r < total; r += 32) {
-                const int q = r + lane;
-                if (q < total) {
-                    int jq = 0;
+            // ... then the ellipsoid tests of the passing (Gaussian, tile) pairs on consecutive lanes
+            const int c2 = __popc(tm);
+            int o2 = c2;
 #pragma unroll
-                    for (int jj = 1; jj < 8; ++jj)
-                        if (q >= pc[jj]) jq = jj;
-                    unsigned cmq = cm[0];
-                    int pcq = 0;
-#pragma unroll
-                    for (int jj = 1; jj < 8; ++jj)
-                        if (jq == jj) { cmq = cm[jj]; pcq = pc[jj]; }
-                    const int glane = (int)__fns(cmq, 0, q - pcq + 1);
-                    const int t = warp * 8 + jq;
-                    const BinRec &R = sm.grec[grp + glane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULLMASK, o2, o);
+                if (lane >= o) o2 += y;
+            }
+            const int total2 = __shfl_sync(FULLMASK, o2, 31);
+            o2 -= c2;
+            for (uint32_t m = tm; m; m &= m - 1) {
+                const int k = __ffs(m) - 1;
+                pl2[o2++] = (uint16_t)((gln << 6) | (t0 + (k >> 1) * SUPER + (k & 1)));
+            }
+            __syncwarp();
+            for (int r2 = 0; r2 < total2; r2 += 32) {
+                const int e2 = r2 + lane;
+                if (e2 < total2) {
+                    const int v = pl2[e2], g2 = v >> 6, t = v & 63;
+                    const BinRec &R = sm.grec[grp + g2];
                     uint32_t hm;
                     if (R.b.y == 2.0f) {
                         hm = sm.tdat[TDAT_F4 * t + 3].w != 0.0f ? 3u : 1u;
@@ -657,26 +762,28 @@ __device__ __forceinline__ void fine_count_unit(const Unit &U, unsigned long lon
                         ax.k2s = R.b.z;
                         hm = half_mask(sm.tdat + TDAT_F4 * t + 2, ax, false);
                     }
-                    const uint32_t bit = 1u << glane;
-                    if (hm) atomicOr(&sm.wmask[t][0], bit);
-                    if (hm & 1u) atomicOr(&sm.wmask[t][1], bit);
-                    if (hm & 2u) atomicOr(&sm.wmask[t][2], bit);
+                    const uint32_t bit = 1u << g2;
+                    if (hm) atomicOr(&wm[t][0], bit);
+                    if (hm & 1u) atomicOr(&wm[t][1], bit);
+                    if (hm & 2u) atomicOr(&wm[t][2], bit);
                 }
             }
             __syncwarp();
-            if (lane < 8) {
-                const int t = warp * 8 + lane;
-                const uint32_t p = sm.wmask[t][0];
-                um[(t * 3 + 0) * MASK_WORDS + word] = p;
-                um[(t * 3 + 1) * MASK_WORDS + word] = sm.wmask[t][1];
-                um[(t * 3 + 2) * MASK_WORDS + word] = sm.wmask[t][2];
-                sm.wmask[t][0] = sm.wmask[t][1] = sm.wmask[t][2] = 0u;
-                sm.running[t] += __popc(p);
-            }
-            __syncwarp();
         }
+        __syncwarp();
+        // this warp's word of every tile's bitmaps, then cleared
+        for (int t = lane; t < 64; t += 32) {
+            const uint32_t p = wm[t][0];
+            if (p) atomicAdd(&sm.running[t], (uint32_t)__popc(p));
+        }
+        for (int k = lane; k < 64 * 3; k += 32) {
+            const int t = k / 3, m = k - 3 * t;
+            um[(t * 3 + m) * MASK_WORDS + word] = wm[t][m];
+            wm[t][m] = 0u;
+        }
+        __syncwarp();
     }
-    __syncthreads();    __syncthreads();
+    __syncthreads();
 }
 
 template <typename T>
@@ -768,7 +875,6 @@ constexpr int SHELL_TB0 = 107 << 23;       // float bits of 2^-20
 constexpr int SHELL_NB = 512;              // 16 buckets per octave over [2^-20, 2^12) metres
 constexpr float CONIC_WIDEN = 1.0f / 32.0f;
 constexpr float CONIC_COND = 1.0f / 8192.0f;
-constexpr unsigned FULLMASK = 0xffffffffu;
 
 size_t build_smem_bytes(int K, int tile, int chunk) {
     const int nt = tile * tile;

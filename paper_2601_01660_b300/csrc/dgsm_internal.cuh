@@ -42,6 +42,7 @@ enum WsSlot {
     WS_NORMALS,        // pca normals: bucket keys and order, bucket ranges, sorted points
     WS_PFRAME,         // persistent frame kernel: control words, binning, items, records
     WS_PF_CONES,       // persistent frame kernel: the dynamic atlas's tile cones
+    WS_PF_PHASE,       // persistent frame kernel: phase timestamps (while profiling)
     WS_NSLOTS
 };
 

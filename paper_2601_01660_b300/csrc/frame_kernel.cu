@@ -64,7 +64,7 @@ constexpr long long FR_BUDGET = 4000000000ll;  // cycles a barrier waits (about 
 // Control words, zeroed before every launch.
 struct FrameCtl {
     unsigned bar_count, bar_gen, abort, item_counter;
-    unsigned skip, pad0, pad1, pad2;
+    unsigned skip, done_blocks, unit_counter, emit_counter;  // counters of P4 and P6
     unsigned long long n_units, n_items;
 };
 
@@ -102,7 +102,7 @@ struct FrameDev {
     const float4 *cones;
     BuildRec *brec;
     BinRec *bin;
-    uint32_t *skey_cnt, *skey_cur;     // [L n_super]
+    uint32_t *skey_cnt, *skey_cur, *skey_start, *unit_off;  // [L n_super]
     uint32_t *cvals;                   // [capC]
     Unit *units;                       // [max_units]
     uint32_t *fcnt, *fmask;            // [max_units][64], [max_units][64][3][MASK_WORDS]
@@ -117,6 +117,7 @@ struct FrameDev {
     unsigned long long *stats;
     uint32_t capC, cap, max_units, max_items;
     int timeout_barrier;
+    unsigned long long *phase_ns;  // nullptr, or 9 timestamps: start, each barrier, end
     Segs segs;
 };
 
@@ -165,6 +166,17 @@ __device__ __noinline__ bool grid_sync(const FrameDev &d, int idx) {
     return s_ok != 0;
 }
 
+// Phase timing (when the context profiles): block 0 stamps the global timer
+// at the start and as it leaves each barrier; the last block to finish
+// stamps the end.
+__device__ __forceinline__ void stamp(const FrameDev &d, int k) {
+    if (d.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        d.phase_ns[k] = t;
+    }
+}
+
 // Per-block tables of the attenuation (both atlases' radii and shell-guess
 // tables, the lights and their weights), carved from shared memory.
 struct AttTabs {
@@ -197,24 +209,31 @@ __device__ __forceinline__ AttTabs att_tabs(const FrameDev &d, void *base) {
     return a;
 }
 
-// sum_l w_l T_static,l(p) T_dyn,l(p) (as dgsm_attenuate_dyn).  The dynamic
+// acc[u] = sum_l w_l T_static,l(p_u) T_dyn,l(p_u) for U receivers at once,
+// the lights outside so that their gathers are in flight together (as in
+// dgsm_attenuate_dyn, with the same arithmetic per receiver).  The dynamic
 // atlases were written by this kernel: their taps are read through L2.
-__device__ __forceinline__ float att_sum(const FrameDev &d, const AttTabs &a, float px, float py, float pz) {
+template <int U>
+__device__ __forceinline__ void att_batch(const FrameDev &d, const AttTabs &at, const float (&px)[U],
+                                          const float (&py)[U], const float (&pz)[U], float (&acc)[U]) {
     const uint32_t lstride = (uint32_t)d.K * d.H * d.W, dstride = (uint32_t)d.Kd * d.Hd * d.Wd;
-    float acc = 0.0f;
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = 0.0f;
     for (int l = 0; l < d.L; ++l) {
-        const float ox = a.ls[3 * l], oy = a.ls[3 * l + 1], oz = a.ls[3 * l + 2];
-        const SampleIndex s = sample_index_tab(px, py, pz, ox, oy, oz, d.H, d.W, a.rs, d.K, a.tab, a.st);
-        float Tl = 1.0f;
-        if (s.t != 0.0f) {
-            Tl = lookup<float>(d.sat + (size_t)l * lstride, d.H, d.W, d.K, s, a.rs, a.inw);
-            const SampleIndex sd =
-                sample_index_tab(px, py, pz, ox, oy, oz, d.Hd, d.Wd, a.rsd, d.Kd, a.tabd, a.std_);
-            Tl *= lookup<float, true>(d.dyn + (size_t)l * dstride, d.Hd, d.Wd, d.Kd, sd, a.rsd, a.inwd);
+        const float ox = at.ls[3 * l], oy = at.ls[3 * l + 1], oz = at.ls[3 * l + 2];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const SampleIndex s = sample_index_tab(px[u], py[u], pz[u], ox, oy, oz, d.H, d.W, at.rs, d.K, at.tab, at.st);
+            float Tl = 1.0f;
+            if (s.t != 0.0f) {
+                Tl = lookup<float>(d.sat + (size_t)l * lstride, d.H, d.W, d.K, s, at.rs, at.inw);
+                const SampleIndex sd =
+                    sample_index_tab(px[u], py[u], pz[u], ox, oy, oz, d.Hd, d.Wd, at.rsd, d.Kd, at.tabd, at.std_);
+                Tl *= lookup<float, true>(d.dyn + (size_t)l * dstride, d.Hd, d.Wd, d.Kd, sd, at.rsd, at.inwd);
+            }
+            acc[u] = fmaf(at.wl[l], Tl, acc[u]);
         }
-        acc = fmaf(a.wl[l], Tl, acc);
     }
-    return acc;
 }
 
 // Exclusive scan over n entries (one block; every thread calls it): get(i)
@@ -272,10 +291,12 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
     __shared__ float s_pose[MAX_OBJECTS][16];
     __shared__ double s_red[FR_THREADS / 32][4];
     __shared__ unsigned long long s_warp[FR_THREADS / 32];
+    __shared__ unsigned s_next;  // the unit a block takes next (P4, P6)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t gtid = (int64_t)blockIdx.x * FR_THREADS + tid, gstride = (int64_t)gridDim.x * FR_THREADS;
     const int64_t N = d.N;
     const int nsk = d.L * d.n_super, ntk = d.L * d.n_tiles;
+    stamp(d, 0);
     for (int o = tid; o < d.segs.n; o += FR_THREADS) pose_matrix(d.poses + 8 * o, s_pose[o]);
     __syncthreads();
 
@@ -325,14 +346,16 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
         }
     }
     if (!grid_sync(d, 1)) return;
+    stamp(d, 1);
 
     // ---- P2 (block 0): super-tile list offsets, units, centroids ----
     if (blockIdx.x == 0) {
-        uint32_t *ucnt = reinterpret_cast<uint32_t *>(fsm);  // [nsk] units per key, then their offsets
+        uint32_t *ucnt = reinterpret_cast<uint32_t *>(fsm);  // [nsk] units per key
         const unsigned long long Pc = block_scan(
             nsk, [&](int i) { return __ldcg(d.skey_cnt + i); },
             [&](int i, unsigned long long pre, uint32_t c) {
                 d.skey_cur[i] = (uint32_t)pre;
+                d.skey_start[i] = (uint32_t)pre;
                 ucnt[i] = (c + UNIT_G - 1) / UNIT_G;
             },
             s_warp);
@@ -347,24 +370,8 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
             }
         }
         const unsigned long long nu = block_scan(
-            nsk, [&](int i) { return ucnt[i]; }, [&](int i, unsigned long long pre, uint32_t) { ucnt[i] = (uint32_t)pre; },
-            s_warp);
-        if (!skip) {
-            for (int k = tid; k < nsk; k += FR_THREADS) {
-                const uint32_t s0 = __ldcg(d.skey_cur + k), e0 = s0 + __ldcg(d.skey_cnt + k);
-                const uint32_t U = (e0 - s0 + UNIT_G - 1) / UNIT_G, u0 = ucnt[k];
-                for (uint32_t j = 0; j < U; ++j) {
-                    Unit u;
-                    u.key = (uint32_t)k;
-                    u.start = s0 + j * UNIT_G;
-                    u.end = min(s0 + (j + 1) * UNIT_G, e0);
-                    u.ju = j | (U << 16);
-                    u.u0 = u0;
-                    u.pad0 = u.pad1 = u.pad2 = 0u;
-                    d.units[u0 + j] = u;
-                }
-            }
-        }
+            nsk, [&](int i) { return ucnt[i]; },
+            [&](int i, unsigned long long pre, uint32_t) { d.unit_off[i] = (uint32_t)pre; }, s_warp);
         if (tid == 0) {
             d.ctl->n_units = skip ? 0ull : nu;
             d.stats[7] = skip ? 0ull : nu;
@@ -372,8 +379,29 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
         for (int o = warp; o < d.segs.n; o += FR_THREADS / 32) centroid_final_warp(d.cen_part, d.cen_bps, o, d.centroids);
     }
     if (!grid_sync(d, 2)) return;
+    stamp(d, 2);
 
-    // ---- P3: super-tile lists (warp-aggregated cursors) ----
+    // ---- P3: super-tile lists (warp-aggregated cursors); the fine-binning units ----
+    const unsigned long long n_units = __ldcg(&d.ctl->n_units);
+    for (int64_t i = gtid; i < (int64_t)n_units; i += gstride) {
+        // unit i belongs to the last key whose first unit is <= i (empty keys
+        // share their offset with the next key, which the search passes over)
+        int lo = 0, hi = nsk;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldcg(d.unit_off + mid) <= (uint32_t)i) lo = mid; else hi = mid;
+        }
+        const uint32_t s0 = __ldcg(d.skey_start + lo), e0 = s0 + __ldcg(d.skey_cnt + lo);
+        const uint32_t U = (e0 - s0 + UNIT_G - 1) / UNIT_G, u0 = __ldcg(d.unit_off + lo), j = (uint32_t)i - u0;
+        Unit u;
+        u.key = (uint32_t)lo;
+        u.start = s0 + j * UNIT_G;
+        u.end = min(s0 + (j + 1) * UNIT_G, e0);
+        u.ju = j | (U << 16);
+        u.u0 = u0;
+        u.pad0 = u.pad1 = u.pad2 = 0u;
+        d.units[i] = u;
+    }
     if (!__ldcg(&d.ctl->skip)) {
         const int64_t total = (int64_t)d.L * N;
         const float4 *scones = d.cones + 2 * d.n_tiles;
@@ -398,7 +426,12 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
                 const unsigned ball = __ballot_sync(FULLMASK, ok);
                 if (!ball) continue;
                 const uint32_t key = (uint32_t)(l * d.n_super + sidx);
-                const unsigned grp = __match_any_sync(FULLMASK, ok ? key : 0xffffffffu) & ball;
+                // lanes of one light share the key; a warp spans two lights
+                // only where it crosses a light boundary
+                const int first = __ffs(ball) - 1;
+                const int l0 = __shfl_sync(FULLMASK, l, first);
+                const unsigned same = __ballot_sync(FULLMASK, ok && l == l0);
+                const unsigned grp = same == ball ? ball : __match_any_sync(FULLMASK, ok ? key : 0xffffffffu) & ball;
                 const int leader = ok ? __ffs(grp) - 1 : lane;
                 uint32_t at = 0u;
                 if (ok && lane == leader) at = atomicAdd(d.skey_cur + key, (uint32_t)__popc(grp));
@@ -411,13 +444,17 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
         }
     }
     if (!grid_sync(d, 3)) return;
+    stamp(d, 3);
 
     // ---- P4: fine binning of the units, per-tile counts ----
-    const unsigned long long n_units = __ldcg(&d.ctl->n_units);
     {
         const FineSmem sm = fine_smem(fsm);
-        if (tid < 64) sm.wmask[tid][0] = sm.wmask[tid][1] = sm.wmask[tid][2] = 0u;
-        for (unsigned long long u = blockIdx.x; u < n_units; u += gridDim.x) {
+        for (int k = tid; k < FB_WARPS * 64 * 3; k += blockDim.x) (&sm.wm[0][0][0])[k] = 0u;
+        for (;;) {
+            if (tid == 0) s_next = atomicAdd(&d.ctl->unit_counter, 1u);
+            __syncthreads();
+            const unsigned long long u = s_next;
+            if (u >= n_units) break;
             const Unit U = load_unit(d.units + u);
             fine_count_unit(U, u, d.cvals, d.bin, N, d.tx, d.ty, d.sx, d.n_tiles, d.n_super, d.cones, d.fmask,
                             nullptr, sm);
@@ -433,6 +470,7 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
         }
     }
     if (!grid_sync(d, 4)) return;
+    stamp(d, 4);
 
     // ---- P5 (block 0): tile offsets, work items ----
     if (blockIdx.x == 0) {
@@ -463,7 +501,15 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
                 return c == 0u ? 1u : (c + item - 1u) / item;
             },
             [&](int i, unsigned long long pre, uint32_t) { d.item_off[i] = (uint32_t)pre; }, s_warp);
-        for (int k = tid; k < ntk; k += FR_THREADS) {
+        if (tid == 0) d.ctl->n_items = n_items;
+    }
+    if (!grid_sync(d, 5)) return;
+    stamp(d, 5);
+
+    // ---- P6: the tiles' work items; per-tile lists from the fine bitmaps ----
+    {
+        const uint32_t item = (uint32_t)(ITEM_CHUNKS * d.chunk);
+        for (int64_t k = gtid; k < ntk; k += gstride) {
             const uint32_t s0 = __ldcg(d.ts + k), e0 = __ldcg(d.te + k), o = __ldcg(d.item_off + k);
             const uint32_t n = e0 == s0 ? 1u : (e0 - s0 + item - 1u) / item;
             for (uint32_t q = 0; q < n; ++q) {
@@ -475,20 +521,20 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
                 d.items[o + q] = it;
             }
         }
-        if (tid == 0) d.ctl->n_items = n_items;
     }
-    if (!grid_sync(d, 5)) return;
-
-    // ---- P6: per-tile lists from the fine bitmaps ----
     if (!__ldcg(&d.ctl->skip)) {
         uint32_t *gidx = reinterpret_cast<uint32_t *>(fsm);  // [UNIT_G]
         const unsigned lt = (1u << lane) - 1u;
-        for (unsigned long long u = blockIdx.x; u < n_units; u += gridDim.x) {
+        for (;;) {
+            __syncthreads();  // gidx and s_next of the previous unit are no longer read
+            if (tid == 0) s_next = atomicAdd(&d.ctl->emit_counter, 1u);
+            __syncthreads();
+            const unsigned long long u = s_next;
+            if (u >= n_units) break;
             const Unit U = load_unit(d.units + u);
             const int l = (int)(U.key / (uint32_t)d.n_super), sidx = (int)(U.key - (uint32_t)l * d.n_super);
             const int sa = sidx / d.sx, sb = sidx - sa * d.sx;
             const int ng = (int)(U.end - U.start);
-            __syncthreads();
             for (int e = tid; e < ng; e += FR_THREADS) gidx[e] = __ldcg(d.cvals + U.start + e);
             __syncthreads();
             const uint32_t *um = d.fmask + u * (64ull * 3 * MASK_WORDS);
@@ -496,18 +542,18 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
                 const int t = warp * 8 + jj;
                 const int a = sa * SUPER + t / SUPER, b = sb * SUPER + t % SUPER;
                 if (a >= d.ty || b >= d.tx) continue;
-                const uint32_t c = __ldcg(d.fcnt + 64ull * u + t);
+                const uint32_t c = d.fcnt[64ull * u + t];
                 if (c == 0u) continue;
                 const uint32_t key = (uint32_t)l * (uint32_t)d.n_tiles + (uint32_t)(a * d.tx + b);
                 uint32_t pos0 = 0u;
                 if (lane == 0) pos0 = atomicAdd(d.tcur + key, c);
                 pos0 = __shfl_sync(FULLMASK, pos0, 0);
                 for (int w = 0; w < (ng + 31) / 32; ++w) {
-                    const uint32_t p = __ldcg(um + (t * 3 + 0) * MASK_WORDS + w);
+                    const uint32_t p = um[(t * 3 + 0) * MASK_WORDS + w];
                     if (p == 0u) continue;
                     if ((p >> lane) & 1u) {
-                        const uint32_t tt = __ldcg(um + (t * 3 + 1) * MASK_WORDS + w);
-                        const uint32_t bb = __ldcg(um + (t * 3 + 2) * MASK_WORDS + w);
+                        const uint32_t tt = um[(t * 3 + 1) * MASK_WORDS + w];
+                        const uint32_t bb = um[(t * 3 + 2) * MASK_WORDS + w];
                         const uint32_t hm = ((tt >> lane) & 1u) | (((bb >> lane) & 1u) << 1);
                         const uint32_t pos = pos0 + __popc(p & lt);
                         if (pos < d.cap) d.vals[pos] = gidx[32 * w + lane] | (hm << 30);
@@ -518,12 +564,14 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
         }
     }
     if (!grid_sync(d, 6)) return;
+    stamp(d, 6);
 
     // ---- P7: the dynamic atlases (closed form, Eqs. 3-4) ----
     tiles_worker<float, 8>(reinterpret_cast<const float4 *>(d.brec), d.vals, d.items, &d.ctl->n_items,
                            &d.ctl->item_counter, d.radii_d, d.Kd, d.Hd, d.Wd, d.tx, d.n_tiles, N, d.chunk, d.accum,
                            d.done, d.dyn, d.stats, nullptr, nullptr, MAP_OCTA, fsm);
     if (!grid_sync(d, 7)) return;
+    stamp(d, 7);
 
     // ---- P8: attenuation of every receiver; relight of the avatars ----
     {
@@ -535,10 +583,11 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
         for (int k = tid; k < 3 * d.segs.n; k += FR_THREADS) cen[k] = __ldcg(d.centroids + k);
         __syncthreads();
         const float wd = d.wd;
-        // half of the blocks start with the relight (FP32-bound), half with the
-        // static receivers (gather-bound), so that an SM's blocks overlap the two
+        // every block relights its avatars first, then attenuates its static
+        // receivers (measured: faster than mixing the two on an SM, whose
+        // gathers then lose shared L1 and warps to the relight's table passes)
         for (int pass = 0; pass < 2; ++pass) {
-            if ((pass == 0) == ((blockIdx.x & 1) == 0)) {
+            if (pass == 1) {
                 // static receivers: FR_ATT_U per thread, blockDim apart
                 const int64_t span = (int64_t)FR_ATT_U * FR_THREADS;
                 for (int64_t base = (int64_t)blockIdx.x * span; base < d.n_static; base += (int64_t)gridDim.x * span) {
@@ -550,26 +599,8 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
                         px[u] = ok ? __ldg(d.q_means + 3 * q) : 0.f;
                         py[u] = ok ? __ldg(d.q_means + 3 * q + 1) : 0.f;
                         pz[u] = ok ? __ldg(d.q_means + 3 * q + 2) : 0.f;
-                        acc[u] = 0.f;
                     }
-                    const uint32_t lstride = (uint32_t)d.K * d.H * d.W, dstride = (uint32_t)d.Kd * d.Hd * d.Wd;
-                    for (int l = 0; l < d.L; ++l) {
-                        const float ox = at.ls[3 * l], oy = at.ls[3 * l + 1], oz = at.ls[3 * l + 2];
-#pragma unroll
-                        for (int u = 0; u < FR_ATT_U; ++u) {
-                            const SampleIndex s =
-                                sample_index_tab(px[u], py[u], pz[u], ox, oy, oz, d.H, d.W, at.rs, d.K, at.tab, at.st);
-                            float Tl = 1.0f;
-                            if (s.t != 0.0f) {
-                                Tl = lookup<float>(d.sat + (size_t)l * lstride, d.H, d.W, d.K, s, at.rs, at.inw);
-                                const SampleIndex sd = sample_index_tab(px[u], py[u], pz[u], ox, oy, oz, d.Hd, d.Wd,
-                                                                        at.rsd, d.Kd, at.tabd, at.std_);
-                                Tl *= lookup<float, true>(d.dyn + (size_t)l * dstride, d.Hd, d.Wd, d.Kd, sd, at.rsd,
-                                                          at.inwd);
-                            }
-                            acc[u] = fmaf(at.wl[l], Tl, acc[u]);
-                        }
-                    }
+                    att_batch<FR_ATT_U>(d, at, px, py, pz, acc);
 #pragma unroll
                     for (int u = 0; u < FR_ATT_U; ++u) {
                         const int64_t q = base + u * FR_THREADS + tid;
@@ -621,13 +652,23 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
                         const float *pr = s_pose[d.segs.n == 1 ? 0 : seg_find(d.segs, g)];
                         const float3 m =
                             pose_point(pr, d.rest_means[3 * g], d.rest_means[3 * g + 1], d.rest_means[3 * g + 2]);
-                        const float f = 1.0f - wd + wd * att_sum(d, at, m.x, m.y, m.z);
+                        float px1[1] = {m.x}, py1[1] = {m.y}, pz1[1] = {m.z}, ta[1];
+                        att_batch<1>(d, at, px1, py1, pz1, ta);
+                        const float f = 1.0f - wd + wd * ta[0];
                         const int64_t q = d.n_static + g;
                         relight_write_rgb(acc[r], d.reps, d.rt_max, d.rgamma, d.cin[3 * q] * f, d.cin[3 * q + 1] * f,
                                           d.cin[3 * q + 2] * f, d.cout, q);
                     }
                 }
             }
+        }
+    }
+    if (d.phase_ns) {
+        __syncthreads();
+        if (tid == 0 && atomicAdd(&d.ctl->done_blocks, 1u) == gridDim.x - 1) {
+            unsigned long long t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            d.phase_ns[8] = t;
         }
     }
 }
@@ -720,6 +761,7 @@ extern "C" int dgsm_crowd_frame(dgsm_ctx *ctx, const dgsm_crowd_frame_args *a, c
     const size_t sz_ctl = al256(sizeof(FrameCtl)), sz_skc = al256(4 * (size_t)nsk), sz_tc = al256(4 * (size_t)ntk);
     const size_t sz_zero = sz_ctl + sz_skc + sz_tc;
     const size_t sizes[] = {al256(4 * (size_t)nsk),                                  // skey_cur
+                            al256(4 * (size_t)nsk), al256(4 * (size_t)nsk),          // skey_start, unit_off
                             al256(4 * (size_t)ntk), al256(4 * (size_t)ntk),          // ts, te
                             al256(4 * (size_t)ntk), al256(4 * (size_t)ntk),          // tcur, item_off
                             al256(4 * (size_t)capC),                                 // cvals
@@ -742,21 +784,24 @@ extern "C" int dgsm_crowd_frame(dgsm_ctx *ctx, const dgsm_crowd_frame_args *a, c
     d.ctl = (FrameCtl *)take(sz_ctl);
     d.skey_cnt = (uint32_t *)take(sz_skc);
     d.tile_cnt = (uint32_t *)take(sz_tc);
-    d.skey_cur = (uint32_t *)take(sizes[0]);
-    d.ts = (uint32_t *)take(sizes[1]);
-    d.te = (uint32_t *)take(sizes[2]);
-    d.tcur = (uint32_t *)take(sizes[3]);
-    d.item_off = (uint32_t *)take(sizes[4]);
-    d.cvals = (uint32_t *)take(sizes[5]);
-    d.units = (Unit *)take(sizes[6]);
-    d.fcnt = (uint32_t *)take(sizes[7]);
-    d.fmask = (uint32_t *)take(sizes[8]);
-    d.items = (Item *)take(sizes[9]);
-    d.vals = (uint32_t *)take(sizes[10]);
-    d.brec = (BuildRec *)take(sizes[11]);
-    d.bin = (BinRec *)take(sizes[12]);
-    d.cen_part = (double *)take(sizes[13]);
-    float *d_poses = (float *)take(sizes[14]);
+    int si = 0;
+    d.skey_cur = (uint32_t *)take(sizes[si++]);
+    d.skey_start = (uint32_t *)take(sizes[si++]);
+    d.unit_off = (uint32_t *)take(sizes[si++]);
+    d.ts = (uint32_t *)take(sizes[si++]);
+    d.te = (uint32_t *)take(sizes[si++]);
+    d.tcur = (uint32_t *)take(sizes[si++]);
+    d.item_off = (uint32_t *)take(sizes[si++]);
+    d.cvals = (uint32_t *)take(sizes[si++]);
+    d.units = (Unit *)take(sizes[si++]);
+    d.fcnt = (uint32_t *)take(sizes[si++]);
+    d.fmask = (uint32_t *)take(sizes[si++]);
+    d.items = (Item *)take(sizes[si++]);
+    d.vals = (uint32_t *)take(sizes[si++]);
+    d.brec = (BuildRec *)take(sizes[si++]);
+    d.bin = (BinRec *)take(sizes[si++]);
+    d.cen_part = (double *)take(sizes[si++]);
+    float *d_poses = (float *)take(sizes[si++]);
     // per-voxel accumulators and per-tile counters, shared with dgsm_build:
     // every user leaves them at zero, so they are cleared only when new
     const size_t acc_bytes = sizeof(float) * (size_t)L * Kd * Hd * Wd;
@@ -821,6 +866,12 @@ extern "C" int dgsm_crowd_frame(dgsm_ctx *ctx, const dgsm_crowd_frame_args *a, c
     d.max_units = (uint32_t)max_units; d.max_items = (uint32_t)max_items;
     d.timeout_barrier = timeout_barrier;
     d.segs = segs;
+    d.phase_ns = nullptr;
+    if (ctx->prof) {
+        void *ph;
+        if ((rc = ws_reserve(ctx, WS_PF_PHASE, 9 * sizeof(unsigned long long), &ph))) return rc;
+        d.phase_ns = (unsigned long long *)ph;
+    }
 
     const size_t smem = std::max({build_smem_bytes(Kd, 8, p.chunk), FINE_SMEM_BYTES, sizeof(uint32_t) * (size_t)nsk,
                                   sizeof(uint32_t) * (size_t)UNIT_G, relight_smem_bytes()});
@@ -842,5 +893,20 @@ extern "C" int dgsm_crowd_frame(dgsm_ctx *ctx, const dgsm_crowd_frame_args *a, c
     cfg.numAttrs = 1;
     e = cudaLaunchKernelEx(&cfg, crowd_frame_kernel, d);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "crowd_frame_kernel (cooperative launch)");
+    return DGSM_OK;
+}
+
+// Phase times of the last frame run while the context profiled: ms_out[k] =
+// time from barrier k to barrier k + 1 (k = 0: from the kernel's start; k =
+// 7: to the last block's end), as block 0 saw the barriers.  Blocks.
+extern "C" int dgsm_crowd_frame_phases(dgsm_ctx *ctx, double *ms_out) {
+    if (!ctx || !ms_out) return DGSM_ERR_INVALID_ARG;
+    if (!ctx->ws[WS_PF_PHASE]) return fail(ctx, DGSM_ERR_INVALID_ARG, "crowd_frame_phases: no profiled frame");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    unsigned long long t[9];
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(t, ctx->ws[WS_PF_PHASE], sizeof(t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "crowd_frame_phases");
+    for (int k = 0; k < 8; ++k) ms_out[k] = (double)(long long)(t[k + 1] - t[k]) * 1e-6;
     return DGSM_OK;
 }

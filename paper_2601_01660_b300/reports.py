@@ -184,13 +184,13 @@ def surrogate(schedule=SURROGATE_SCHEDULE, batch: int = 16384, n_query: int = 3_
     }
 
 
-def frame(frames: int = 120) -> dict:
+def frame(frames: int = 120, workload: str = "crowd8") -> dict:
     import torch
 
     from paper_2601_01660_b300 import native, scenes
     from paper_2601_01660_b300.frame import CrowdFrame
     nat = native()
-    wl = scenes.workload("crowd8")
+    wl = scenes.workload(workload)
     D, Y, w = wl["cubemap"]
     sh = nat.sh_fit(_dev(D, torch), _dev(Y, torch), _dev(w, torch))
     torch.cuda.synchronize()
@@ -263,10 +263,22 @@ def frame(frames: int = 120) -> dict:
     ms_pkg, wall_pkg = run(cf.step_graph, frames)
     status_pkg = nat.dgsm_sync_status(cf.ctx, stream=s)
     cf.close()
+    # its eight steps (global-timer stamps at the grid barriers), median of 5 frames
+    nat.dgsm_set_profiling(True, ctx=cf.ctx)
+    ph = []
+    for f in range(5):
+        cf.step_eager(poses[7 + f], max_pairs=cf.max_pairs)
+        ph.append(nat.dgsm_crowd_frame_phases(cf.ctx))
+    nat.dgsm_set_profiling(False, ctx=cf.ctx)
+    ph = [sorted(x[k] for x in ph)[2] for k in range(8)]
+    phase_names = ["P1_motion_prep_super_counts", "P2_key_offsets_units_centroids", "P3_super_lists",
+                   "P4_fine_binning", "P5_tile_offsets_items", "P6_tile_lists", "P7_tiles_closed_form",
+                   "P8_attenuate_relight"]
     return {
         "report": "frame",
-        "workload": "crowd8: 1.5M static + 8 x 100k avatars, 4 lights; static 512x512x64 (built once), "
-                    "dynamic 256x256x32 per frame; 2.3M attenuated, 800k relit",
+        "workload": (f"{workload}: {wl['static'].n} static + 8 x {wl['avatars'].n // 8} avatar Gaussians, 4 lights; "
+                     "static 512x512x64 (built once), dynamic 256x256x32 per frame; all attenuated, the avatars "
+                     "relit"),
         "frames": frames, "static_build_s": round(t_static, 3),
         "autotune_ms": {f"tile{t}_chunk{c}": round(v, 3) for (t, c), v in table.items()},
         "chosen": {"tile": tile, "chunk": chunk}, "max_pairs": cf.max_pairs,
@@ -279,6 +291,7 @@ def frame(frames: int = 120) -> dict:
                               "persistent_kernel": round(wall_pk, 3), "persistent_kernel_graph": round(wall_pkg, 3)},
         "graph_nodes_per_frame": nodes, "status_after_replay": status,
         "persistent_graph_nodes_per_frame": nodes_pk, "persistent_status": [status_pk, status_pkg],
+        "persistent_phase_ms": {nm: round(v, 4) for nm, v in zip(phase_names, ph)},
         "stage_ms": {k2: round(v, 4) for k2, v in stages.items()},
     }
 
@@ -309,6 +322,9 @@ def field(n: int = 3_000_000, reps: int = 20) -> dict:
             "flop_per_eval": 2 * (96 * 64 + 3 * 64 * 64 + 64), "kernel": "tc::field_kernel<MODE_UVR> (tcgen05)"}
 
 
-def main(which: str) -> None:
-    fn = {"precision": precision, "surrogate": surrogate, "frame": frame, "field": field}[which]
+def main(which: str, frame_workload: str = "crowd8") -> None:
+    if which == "frame":
+        print(json.dumps(frame(workload=frame_workload)), flush=True)
+        return
+    fn = {"precision": precision, "surrogate": surrogate, "field": field}[which]
     print(json.dumps(fn()), flush=True)

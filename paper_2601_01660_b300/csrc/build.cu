@@ -136,7 +136,9 @@ __global__ void __launch_bounds__(256, 5) fine_count_kernel(
     for (int k = tid; k < FB_WARPS * 64 * 3; k += blockDim.x) (&sm.wm[0][0][0])[k] = 0u;
     for (unsigned long long u = blockIdx.x; u < n_units; u += gridDim.x) {
         const Unit U = units[u];
-        fine_count_unit(U, u, cvals, bin, N, tx, ty, sx, n_tiles, n_super, cones, fmask, tact, sm);
+        fine_count_unit(
+            U, u, cvals, [&](int l, uint32_t g) { return bin[(int64_t)l * N + g]; }, tx, ty, sx, n_tiles, n_super,
+            cones, fmask, tact, sm);
         const uint32_t j = U.ju & 0xffffu, nU = U.ju >> 16;
         if (tid < 64) fcnt[64u * U.u0 + (uint32_t)tid * nU + j] = sm.running[tid];
     }

@@ -644,10 +644,12 @@ __device__ __forceinline__ bool quad_overlap(const BinRec &g, const float4 &c0, 
 // (read them after this returns; the call ends with a barrier).  tact (or
 // nullptr): per (light, tile) 1 if it holds a texel of the region of
 // interest.
+// rec(l, g) gives the binning record of Gaussian g for light l (read from the
+// prep's records, or formed anew).
+template <typename RecF>
 __device__ __forceinline__ void fine_count_unit(const Unit &U, unsigned long long u,
-                                                const uint32_t *__restrict__ cvals,
-                                                const BinRec *__restrict__ bin, int64_t N, int tx, int ty, int sx,
-                                                int n_tiles, int n_super, const float4 *__restrict__ cones,
+                                                const uint32_t *__restrict__ cvals, RecF rec, int tx, int ty,
+                                                int sx, int n_tiles, int n_super, const float4 *__restrict__ cones,
                                                 uint32_t *__restrict__ fmask, const uint8_t *__restrict__ tact,
                                                 const FineSmem &sm) {
     const float4 *planes = cones + 2 * (n_tiles + n_super);
@@ -678,7 +680,7 @@ __device__ __forceinline__ void fine_count_unit(const Unit &U, unsigned long lon
     for (uint32_t s0 = U.start; s0 < U.end; s0 += FB_STAGE) {
         const int ns = (int)min((uint32_t)FB_STAGE, U.end - s0);
         __syncthreads();  // grec of the previous stage is no longer read (and the quad cones are ready)
-        for (int e = tid; e < ns; e += blockDim.x) sm.grec[e] = bin[(int64_t)l * N + cvals[s0 + e]];
+        for (int e = tid; e < ns; e += blockDim.x) sm.grec[e] = rec(l, cvals[s0 + e]);
         __syncthreads();
         const int grp = warp * 32;  // this warp's 32 Gaussians of the stage
         if (grp >= ns) continue;    // words past the unit's end are never read

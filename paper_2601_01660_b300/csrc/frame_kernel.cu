@@ -7,16 +7,18 @@
 // boundaries:
 //
 //   P1  per (light, avatar Gaussian): rigid motion to this frame's pose,
-//       the prep (build and binning records), the super-tile cone tests
-//       counted per (light, super-tile) key; per-object centroid partial sums
+//       the prep (the build record, and the binning record's super-tile cone
+//       tests as a bit mask), counted per (light, super-tile) key; per-object
+//       centroid partial sums
 //   B1
 //   P2  block 0: key offsets, fine-binning units, the centroids
 //   B2
 //   P3  super-tile lists: every (light, Gaussian) writes itself into the
-//       lists of the super-tiles it reaches (warp-aggregated cursors)
+//       lists of the super-tiles it reaches (ranges reserved per block and key)
 //   B3
 //   P4  fine binning, one unit (<= 512 Gaussians of one list) per block at a
-//       time: cone and ellipsoid tests against the 64 tiles, per-tile counts
+//       time: the binning records formed anew from the rest pose, cone and
+//       ellipsoid tests against the 64 tiles, per-tile counts
 //   B4
 //   P5  block 0: tile offsets and the tiles' work items
 //   B5
@@ -101,7 +103,7 @@ struct FrameDev {
     // workspace
     const float4 *cones;
     BuildRec *brec;
-    BinRec *bin;
+    unsigned long long *smask;         // [L N] super-tiles each (light, Gaussian) reaches (n_super <= 64)
     uint32_t *skey_cnt, *skey_cur, *skey_start, *unit_off;  // [L n_super]
     uint32_t *cvals;                   // [capC]
     Unit *units;                       // [max_units]
@@ -236,6 +238,30 @@ __device__ __forceinline__ void att_batch(const FrameDev &d, const AttTabs &at, 
     }
 }
 
+// The binning record of avatar Gaussian g for light l, formed anew from its
+// rest pose and this frame's motion (the same floats as the prep's).
+__device__ __forceinline__ BinRec frame_binrec(const FrameDev &d, const float (*pose)[16], int l, int64_t g) {
+    const float *r = pose[d.segs.n == 1 ? 0 : seg_find(d.segs, g)];
+    const float3 m = pose_point(r, d.rest_means[3 * g], d.rest_means[3 * g + 1], d.rest_means[3 * g + 2]);
+    const float4 q = pose_quat(r, reinterpret_cast<const float4 *>(d.rest_quats)[g]);
+    BinRec br;
+    prep_core((int64_t)l * d.N + g, l, m.x, m.y, m.z, d.scales[3 * g], d.scales[3 * g + 1], d.scales[3 * g + 2], q.x,
+              q.y, q.z, q.w, d.opac[g], d.lights[3 * l], d.lights[3 * l + 1], d.lights[3 * l + 2], d.radii_d, d.Kd,
+              d.kappa, d.eps_cull, nullptr, br, d.status, nullptr, d.beta_mode);
+    return br;
+}
+
+// Super-tiles reached by (light l, Gaussian g) as a bit mask (n_super <= 64).
+__device__ __forceinline__ unsigned long long super_mask(const FrameDev &d, const BinRec &br) {
+    const int mode = (int)br.b.y;
+    unsigned long long m = 0ull;
+    if (mode == 0) return m;
+    const float4 *scones = d.cones + 2 * d.n_tiles;
+    for (int sidx = 0; sidx < d.n_super; ++sidx)
+        if (mode == 2 || cone_overlap(br, scones + 2 * sidx)) m |= 1ull << sidx;
+    return m;
+}
+
 // Exclusive scan over n entries (one block; every thread calls it): get(i)
 // gives entry i, put(i, prefix, value) receives its exclusive prefix.
 // Thread t takes a contiguous run of entries.  Returns the 64-bit total.
@@ -333,11 +359,16 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
             prep_core(idx, l, m.x, m.y, m.z, d.scales[3 * g], d.scales[3 * g + 1], d.scales[3 * g + 2], q.x, q.y,
                       q.z, q.w, d.opac[g], d.lights[3 * l], d.lights[3 * l + 1], d.lights[3 * l + 2], d.radii_d,
                       d.Kd, d.kappa, d.eps_cull, d.brec, br, d.status, nullptr, d.beta_mode);
-            d.bin[idx] = br;
-            const int mode = (int)br.b.y;
-            if (mode != 0)
-                for (int sidx = 0; sidx < d.n_super; ++sidx)
-                    if (mode == 2 || cone_overlap(br, scones + 2 * sidx)) atomicAdd(&hist[l * d.n_super + sidx], 1u);
+            if (d.n_super <= 64) {
+                unsigned long long sm = super_mask(d, br);
+                d.smask[idx] = sm;
+                for (; sm; sm &= sm - 1) atomicAdd(&hist[l * d.n_super + __ffsll(sm) - 1], 1u);
+            } else {
+                const int mode = (int)br.b.y;
+                if (mode != 0)
+                    for (int sidx = 0; sidx < d.n_super; ++sidx)
+                        if (mode == 2 || cone_overlap(br, scones + 2 * sidx)) atomicAdd(&hist[l * d.n_super + sidx], 1u);
+            }
         }
         __syncthreads();
         for (int k = tid; k < nsk; k += FR_THREADS) {
@@ -381,7 +412,7 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
     if (!grid_sync(d, 2)) return;
     stamp(d, 2);
 
-    // ---- P3: super-tile lists (warp-aggregated cursors); the fine-binning units ----
+    // ---- P3: super-tile lists; the fine-binning units ----
     const unsigned long long n_units = __ldcg(&d.ctl->n_units);
     for (int64_t i = gtid; i < (int64_t)n_units; i += gstride) {
         // unit i belongs to the last key whose first unit is <= i (empty keys
@@ -403,43 +434,41 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
         d.units[i] = u;
     }
     if (!__ldcg(&d.ctl->skip)) {
+        // each block counts its (light, Gaussian) pairs per key in shared memory,
+        // reserves one range per key, then writes: a handful of global atomics
+        // per key and block instead of one per warp (a few keys hold most pairs)
+        uint32_t *hist = reinterpret_cast<uint32_t *>(fsm);  // [nsk]
+        uint32_t *curs = hist + nsk;                          // [nsk]
+        for (int k = tid; k < nsk; k += FR_THREADS) hist[k] = 0u;
+        __syncthreads();
         const int64_t total = (int64_t)d.L * N;
         const float4 *scones = d.cones + 2 * d.n_tiles;
-        const unsigned lt = (1u << lane) - 1u;
-        for (int64_t base = gtid - lane; base < total; base += gstride) {
-            const int64_t idx = base + lane;
-            const bool valid = idx < total;
-            int l = 0, mode = 0;
-            int64_t g = 0;
-            BinRec br;
-            br.a = make_float4(0.f, 0.f, 1.f, -1.f);
-            br.b = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (valid) {
-                l = (int)(idx / N);
-                g = idx - (int64_t)l * N;
-                br.a = __ldcg(&d.bin[idx].a);
-                br.b = __ldcg(&d.bin[idx].b);
-                mode = (int)br.b.y;
-            }
-            for (int sidx = 0; sidx < d.n_super; ++sidx) {
-                const bool ok = valid && mode != 0 && (mode == 2 || cone_overlap(br, scones + 2 * sidx));
-                const unsigned ball = __ballot_sync(FULLMASK, ok);
-                if (!ball) continue;
-                const uint32_t key = (uint32_t)(l * d.n_super + sidx);
-                // lanes of one light share the key; a warp spans two lights
-                // only where it crosses a light boundary
-                const int first = __ffs(ball) - 1;
-                const int l0 = __shfl_sync(FULLMASK, l, first);
-                const unsigned same = __ballot_sync(FULLMASK, ok && l == l0);
-                const unsigned grp = same == ball ? ball : __match_any_sync(FULLMASK, ok ? key : 0xffffffffu) & ball;
-                const int leader = ok ? __ffs(grp) - 1 : lane;
-                uint32_t at = 0u;
-                if (ok && lane == leader) at = atomicAdd(d.skey_cur + key, (uint32_t)__popc(grp));
-                at = __shfl_sync(FULLMASK, at, leader);
-                if (ok) {
-                    const uint32_t pos = at + __popc(grp & lt);
-                    if (pos < d.capC) d.cvals[pos] = (uint32_t)g;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int64_t idx = gtid; idx < total; idx += gstride) {
+                const int l = (int)(idx / N);
+                const uint32_t g = (uint32_t)(idx - (int64_t)l * N);
+                uint32_t *cnt = pass == 0 ? hist : curs;
+                auto take = [&](int sidx) {
+                    const uint32_t pos = atomicAdd(&cnt[l * d.n_super + sidx], 1u);
+                    if (pass == 1 && pos < d.capC) d.cvals[pos] = g;
+                };
+                if (d.n_super <= 64) {
+                    for (unsigned long long sm = __ldcg(d.smask + idx); sm; sm &= sm - 1) take(__ffsll(sm) - 1);
+                } else {
+                    const BinRec br = frame_binrec(d, s_pose, l, g);
+                    const int mode = (int)br.b.y;
+                    if (mode != 0)
+                        for (int sidx = 0; sidx < d.n_super; ++sidx)
+                            if (mode == 2 || cone_overlap(br, scones + 2 * sidx)) take(sidx);
                 }
+            }
+            __syncthreads();
+            if (pass == 0) {
+                for (int k = tid; k < nsk; k += FR_THREADS) {
+                    const uint32_t c = hist[k];
+                    curs[k] = c ? atomicAdd(d.skey_cur + k, c) : 0u;
+                }
+                __syncthreads();
             }
         }
     }
@@ -456,8 +485,9 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
             const unsigned long long u = s_next;
             if (u >= n_units) break;
             const Unit U = load_unit(d.units + u);
-            fine_count_unit(U, u, d.cvals, d.bin, N, d.tx, d.ty, d.sx, d.n_tiles, d.n_super, d.cones, d.fmask,
-                            nullptr, sm);
+            fine_count_unit(
+                U, u, d.cvals, [&](int l, uint32_t g) { return frame_binrec(d, s_pose, l, g); }, d.tx, d.ty, d.sx,
+                d.n_tiles, d.n_super, d.cones, d.fmask, nullptr, sm);
             if (tid < 64) {
                 const uint32_t c = sm.running[tid];
                 d.fcnt[64ull * u + tid] = c;
@@ -771,7 +801,7 @@ extern "C" int dgsm_crowd_frame(dgsm_ctx *ctx, const dgsm_crowd_frame_args *a, c
                             al256(sizeof(Item) * (size_t)max_items),                 // items
                             al256(4 * (size_t)cap),                                  // vals
                             al256(sizeof(BuildRec) * (size_t)std::max<int64_t>(LN, 1)),  // brec
-                            al256(sizeof(BinRec) * (size_t)std::max<int64_t>(LN, 1)),    // bin
+                            al256(sizeof(unsigned long long) * (size_t)std::max<int64_t>(LN, 1)),  // smask
                             al256(sizeof(double) * 4 * (size_t)bps * a->n_obj),      // cen_part
                             al256(sizeof(float) * 8 * MAX_OBJECTS)};                 // poses
     size_t total = sz_zero;
@@ -799,7 +829,7 @@ extern "C" int dgsm_crowd_frame(dgsm_ctx *ctx, const dgsm_crowd_frame_args *a, c
     d.items = (Item *)take(sizes[si++]);
     d.vals = (uint32_t *)take(sizes[si++]);
     d.brec = (BuildRec *)take(sizes[si++]);
-    d.bin = (BinRec *)take(sizes[si++]);
+    d.smask = (unsigned long long *)take(sizes[si++]);
     d.cen_part = (double *)take(sizes[si++]);
     float *d_poses = (float *)take(sizes[si++]);
     // per-voxel accumulators and per-tile counters, shared with dgsm_build:
@@ -873,7 +903,7 @@ extern "C" int dgsm_crowd_frame(dgsm_ctx *ctx, const dgsm_crowd_frame_args *a, c
         d.phase_ns = (unsigned long long *)ph;
     }
 
-    const size_t smem = std::max({build_smem_bytes(Kd, 8, p.chunk), FINE_SMEM_BYTES, sizeof(uint32_t) * (size_t)nsk,
+    const size_t smem = std::max({build_smem_bytes(Kd, 8, p.chunk), FINE_SMEM_BYTES, 2 * sizeof(uint32_t) * (size_t)nsk,
                                   sizeof(uint32_t) * (size_t)UNIT_G, relight_smem_bytes()});
     e = cudaFuncSetAttribute(crowd_frame_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "crowd_frame: smem attribute");

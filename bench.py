@@ -566,17 +566,28 @@ def count_launches(args, L):
     return (build + 6) * args.steps
 
 
+def _tile_kernel_sha():
+    """sha256 of the tile kernel's own source: its device code in
+    build_device.cuh (from the closed-form helpers to the end of the file)
+    and its __global__ wrapper in build.cu, so that edits elsewhere keep a
+    profile of it valid."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2601_01660_b300", "csrc")
+    dev = open(os.path.join(csrc, "build_device.cuh")).read()
+    bu = open(os.path.join(csrc, "build.cu")).read()
+    b0 = bu.index("build_tiles_kernel(")
+    b1 = bu.index("\n}\n", b0)
+    return hashlib.sha256((dev[dev.index("// erfc(y) for y >= 0"):] + bu[b0:b1]).encode()).hexdigest()
+
+
 def _profiled_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` from the committed ncu summary of this
     workload, or None when the summary is missing or was taken on another
     version of the kernel source (its sha256 is recorded beside the figure)."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", f"{kernel.replace('_kernel', '')}_{workload}.txt")
-    src = os.path.join(ROOT, "paper_2601_01660_b300", "csrc", "build.cu")
     try:
         fields = dict(line.split(":", 1) for line in open(path) if ":" in line)
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if fields.get("source_sha256", "").strip() != sha:
+        if fields.get("source_sha256", "").strip() != _tile_kernel_sha():
             return None
         return int(fields["dram_bytes_per_launch"].strip())
     except (OSError, KeyError, ValueError):
@@ -587,14 +598,11 @@ def _profiled_pipes(kernel, workload):
     """ncu pipe utilisation (fraction of peak over active cycles) of `kernel`
     from the full capture summarised beside its traffic figure, under the same
     source-hash rule, or None."""
-    import hashlib
     import re
     path = os.path.join(ROOT, "profiles", f"{kernel.replace('_kernel', '')}_{workload}.txt")
-    src = os.path.join(ROOT, "paper_2601_01660_b300", "csrc", "build.cu")
     try:
         text = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if f"source_sha256: {sha}" not in text:
+        if f"source_sha256: {_tile_kernel_sha()}" not in text:
             return None
         m = re.search(r"FMA ([0-9.]+)%, ALU ([0-9.]+)%, XU \(MUFU\) ([0-9.]+)%", text)
         if not m:
@@ -602,7 +610,7 @@ def _profiled_pipes(kernel, workload):
         return {"fma": float(m.group(1)) / 100, "alu": float(m.group(2)) / 100,
                 "xu": float(m.group(3)) / 100,
                 "source": f"ncu --set full on the room550k case (profiles/{kernel.replace('_kernel', '')}_room1p6m.txt)"}
-    except OSError:
+    except (OSError, ValueError):
         return None
 
 

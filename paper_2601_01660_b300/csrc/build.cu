@@ -154,8 +154,7 @@ __global__ void __launch_bounds__(256) fine_emit_kernel(
     if (*keep == 0) return;
     __shared__ uint32_t gidx[UNIT_G];
     const unsigned long long n_units = *n_units_dev;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const unsigned lt = (1u << lane) - 1u;
+    const int tid = threadIdx.x, warp = tid >> 5;
     for (unsigned long long u = blockIdx.x; u < n_units; u += gridDim.x) {
         const Unit U = units[u];
         const int l = (int)(U.key / (uint32_t)n_super), sidx = (int)(U.key - (uint32_t)l * n_super);
@@ -170,22 +169,9 @@ __global__ void __launch_bounds__(256) fine_emit_kernel(
             const int t = warp * 8 + jj;
             const int a = sa * SUPER + t / SUPER, b = sb * SUPER + t % SUPER;
             if (a >= ty || b >= tx) continue;
-            uint32_t pos0 = foff[64u * U.u0 + (uint32_t)t * nU + j];
+            const uint32_t pos0 = foff[64u * U.u0 + (uint32_t)t * nU + j];
             const uint32_t key = (uint32_t)l * (uint32_t)n_tiles + (uint32_t)(a * tx + b);
-            for (int w = 0; w < (ng + 31) / 32; ++w) {
-                const uint32_t p = um[(t * 3 + 0) * MASK_WORDS + w];
-                if (p == 0u) continue;
-                if ((p >> lane) & 1u) {
-                    const uint32_t tt = um[(t * 3 + 1) * MASK_WORDS + w], bb = um[(t * 3 + 2) * MASK_WORDS + w];
-                    const uint32_t hm = ((tt >> lane) & 1u) | (((bb >> lane) & 1u) << 1);
-                    const uint32_t pos = pos0 + __popc(p & lt);
-                    if (pos < cap) {
-                        vals[pos] = gidx[32 * w + lane] | (hm << 30);
-                        if (keys) keys[pos] = key;
-                    }
-                }
-                pos0 += __popc(p);
-            }
+            emit_tile(um, t, ng, pos0, gidx, vals, keys, key, cap);
         }
     }
 }

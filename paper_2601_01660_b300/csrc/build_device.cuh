@@ -788,6 +788,47 @@ __device__ __forceinline__ void fine_count_unit(const Unit &U, unsigned long lon
     __syncthreads();
 }
 
+// Writes the pairs of tile t from one fine-binning unit's bitmaps um (its
+// ng Gaussians' indices in gidx, shared memory) at vals[pos0 ...] in Gaussian
+// order, each index with its half-tile mask (and keys[...] = key when keys
+// != nullptr); positions at or past cap are skipped.  One warp: lane w loads
+// word w of the three bitmaps, so that all the tile's words are in flight
+// together, and the words with pairs are then taken from registers.
+__device__ __forceinline__ void emit_tile(const uint32_t *__restrict__ um, int t, int ng, uint32_t pos0,
+                                          const uint32_t *gidx, uint32_t *__restrict__ vals,
+                                          uint32_t *__restrict__ keys, uint32_t key, uint32_t cap) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (ng + 31) / 32;
+    uint32_t p = 0u, tt = 0u, bb = 0u;
+    if (lane < nw) {
+        p = um[(t * 3 + 0) * MASK_WORDS + lane];
+        tt = um[(t * 3 + 1) * MASK_WORDS + lane];
+        bb = um[(t * 3 + 2) * MASK_WORDS + lane];
+    }
+    const int c = __popc(p);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULLMASK, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t base = pos0 + (uint32_t)(incl - c);
+    const unsigned lt = (1u << lane) - 1u;
+    for (unsigned nz = __ballot_sync(FULLMASK, p != 0u); nz; nz &= nz - 1) {
+        const int w = __ffs(nz) - 1;
+        const uint32_t pw = __shfl_sync(FULLMASK, p, w), tw = __shfl_sync(FULLMASK, tt, w);
+        const uint32_t bw = __shfl_sync(FULLMASK, bb, w), bs = __shfl_sync(FULLMASK, base, w);
+        if ((pw >> lane) & 1u) {
+            const uint32_t hm = ((tw >> lane) & 1u) | (((bw >> lane) & 1u) << 1);
+            const uint32_t pos = bs + __popc(pw & lt);
+            if (pos < cap) {
+                vals[pos] = gidx[32 * w + lane] | (hm << 30);
+                if (keys) keys[pos] = key;
+            }
+        }
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T to_store(float x);
 template <>

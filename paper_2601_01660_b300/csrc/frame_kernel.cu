@@ -554,7 +554,6 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
     }
     if (!__ldcg(&d.ctl->skip)) {
         uint32_t *gidx = reinterpret_cast<uint32_t *>(fsm);  // [UNIT_G]
-        const unsigned lt = (1u << lane) - 1u;
         for (;;) {
             __syncthreads();  // gidx and s_next of the previous unit are no longer read
             if (tid == 0) s_next = atomicAdd(&d.ctl->emit_counter, 1u);
@@ -578,18 +577,7 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
                 uint32_t pos0 = 0u;
                 if (lane == 0) pos0 = atomicAdd(d.tcur + key, c);
                 pos0 = __shfl_sync(FULLMASK, pos0, 0);
-                for (int w = 0; w < (ng + 31) / 32; ++w) {
-                    const uint32_t p = um[(t * 3 + 0) * MASK_WORDS + w];
-                    if (p == 0u) continue;
-                    if ((p >> lane) & 1u) {
-                        const uint32_t tt = um[(t * 3 + 1) * MASK_WORDS + w];
-                        const uint32_t bb = um[(t * 3 + 2) * MASK_WORDS + w];
-                        const uint32_t hm = ((tt >> lane) & 1u) | (((bb >> lane) & 1u) << 1);
-                        const uint32_t pos = pos0 + __popc(p & lt);
-                        if (pos < d.cap) d.vals[pos] = gidx[32 * w + lane] | (hm << 30);
-                    }
-                    pos0 += __popc(p);
-                }
+                emit_tile(um, t, ng, pos0, gidx, d.vals, nullptr, 0u, d.cap);
             }
         }
     }
@@ -642,19 +630,26 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
                     }
                 }
             } else {
-                // avatar receivers: slots g = s * (all threads) + this thread, in
-                // groups of FR_RG; the relight table passes through shared memory
-                // FR_TAB directions at a time (every block runs the same groups)
-                const int64_t nslot = (N + gstride - 1) / gstride;
-                const int ngroups = (int)((nslot + FR_RG - 1) / FR_RG);
+                // avatar receivers in groups of FR_RG consecutive Gaussians, a group
+                // per thread; groups are dealt warp-major across the blocks (warp 0
+                // of every block, then warp 1, ...) so that few avatars fill few
+                // whole warps spread over every SM, and warps without a group skip
+                // the sums.  The relight table passes through shared memory FR_TAB
+                // directions at a time (every block runs the same rounds).
+                const int64_t n_groups = (N + FR_RG - 1) / FR_RG;
+                const int64_t per_round = (int64_t)gridDim.x * FR_THREADS;
+                const int rounds = (int)((n_groups + per_round - 1) / per_round);
                 const int M = d.nth * d.nph;
-                for (int grp = 0; grp < ngroups; ++grp) {
+                for (int rd = 0; rd < rounds; ++rd) {
+                    const int64_t G =
+                        (((int64_t)rd * (FR_THREADS / 32) + warp) * gridDim.x + blockIdx.x) * 32 + lane;
+                    const bool busy = __any_sync(FULLMASK, G < n_groups);
                     float3 n[FR_RG];
 #pragma unroll
                     for (int r = 0; r < FR_RG; ++r) {
-                        const int64_t g = (int64_t)(grp * FR_RG + r) * gstride + gtid;
+                        const int64_t g = G * FR_RG + r;
                         n[r] = make_float3(0.f, 0.f, 1.f);  // a padding slot: summed, never written
-                        if (g < N) {
+                        if (G < n_groups && g < N) {
                             const int o = d.segs.n == 1 ? 0 : seg_find(d.segs, g);
                             const float *pr = s_pose[o];
                             const float3 m =
@@ -673,12 +668,12 @@ __global__ void __launch_bounds__(FR_THREADS, FR_MIN_BLOCKS) crowd_frame_kernel(
                         __syncthreads();  // the previous piece of the table is no longer read
                         relight_table_fill(shs, j0, j1, d.nth, d.nph, tab);
                         __syncthreads();
-                        relight_accumulate_add<FR_RG>(tab, j1 - j0, d.rq, n, acc);
+                        if (busy) relight_accumulate_add<FR_RG>(tab, j1 - j0, d.rq, n, acc);
                     }
 #pragma unroll
                     for (int r = 0; r < FR_RG; ++r) {
-                        const int64_t g = (int64_t)(grp * FR_RG + r) * gstride + gtid;
-                        if (g >= N) continue;
+                        const int64_t g = G * FR_RG + r;
+                        if (G >= n_groups || g >= N) continue;
                         const float *pr = s_pose[d.segs.n == 1 ? 0 : seg_find(d.segs, g)];
                         const float3 m =
                             pose_point(pr, d.rest_means[3 * g], d.rest_means[3 * g + 1], d.rest_means[3 * g + 2]);

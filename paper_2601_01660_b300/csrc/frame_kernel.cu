@@ -60,7 +60,7 @@ constexpr int FR_MAX_SKEYS = 4096;   // lights x super-tiles (the per-block hist
 constexpr int FR_MAX_TKEYS = 65536;  // lights x tiles
 constexpr int FR_TAB = 1024;         // relight directions in shared memory at a time
 constexpr int FR_RG = 3;             // avatar receivers per relight group of a thread
-constexpr int FR_ATT_U = 4;          // static receivers in flight per thread
+constexpr int FR_ATT_U = 2;          // static receivers in flight per thread (1, 3, 4, 8 measured slower)
 constexpr long long FR_BUDGET = 4000000000ll;  // cycles a barrier waits (about 2 s)
 
 // Control words, zeroed before every launch.

@@ -674,22 +674,24 @@ __device__ __forceinline__ void fine_count_unit(const Unit &U, unsigned long lon
     }
     __syncthreads();
     if (tid < 16) quad_cone(sm.tdat, sm.tvalid, tid, sm.qc + 2 * tid);
+    __syncthreads();  // the quad cones are ready
     uint32_t *um = fmask + (size_t)u * 64 * 3 * MASK_WORDS;
     uint32_t (*wm)[3] = sm.wm[warp];
     uint16_t *pl = sm.plist[warp], *pl2 = sm.plist2[warp];
-    for (uint32_t s0 = U.start; s0 < U.end; s0 += FB_STAGE) {
-        const int ns = (int)min((uint32_t)FB_STAGE, U.end - s0);
-        __syncthreads();  // grec of the previous stage is no longer read (and the quad cones are ready)
-        for (int e = tid; e < ns; e += blockDim.x) sm.grec[e] = rec(l, cvals[s0 + e]);
-        __syncthreads();
-        const int grp = warp * 32;  // this warp's 32 Gaussians of the stage
-        if (grp >= ns) continue;    // words past the unit's end are never read
-        const int word = (int)(s0 - U.start + grp) / 32;
+    BinRec *wrec = sm.grec + warp * 32;  // this warp's 32 staged records
+    const int ng = (int)(U.end - U.start);
+    // warp w takes the unit's groups of 32 Gaussians w, w + 8, ... and stages
+    // its own records: no block barrier until the unit is done
+    for (int grp = warp * 32; grp < ng; grp += FB_WARPS * 32) {
+        const int word = grp / 32;
         const int gl = grp + lane;
-        const bool gv = gl < ns;
+        const bool gv = gl < ng;
+        __syncwarp();  // the previous group's records are no longer read
+        if (gv) wrec[lane] = rec(l, cvals[U.start + gl]);
+        __syncwarp();
         BinRec G;
-        G.a = gv ? sm.grec[gl].a : make_float4(0.f, 0.f, 1.f, -1.f);
-        G.b = gv ? sm.grec[gl].b : make_float4(0.f, 0.f, 0.f, 0.f);
+        G.a = gv ? wrec[lane].a : make_float4(0.f, 0.f, 1.f, -1.f);
+        G.b = gv ? wrec[lane].b : make_float4(0.f, 0.f, 0.f, 0.f);
         const bool inside = G.b.y == 2.0f;
         // quads this Gaussian may reach
         uint32_t qm = 0u;
@@ -722,8 +724,8 @@ __device__ __forceinline__ void fine_count_unit(const Unit &U, unsigned long lon
                 gln = pq >> 4;
                 t0 = (2 * (q / 4)) * SUPER + 2 * (q % 4);
                 BinRec Rc;
-                Rc.a = sm.grec[grp + gln].a;
-                Rc.b = sm.grec[grp + gln].b;
+                Rc.a = wrec[gln].a;
+                Rc.b = wrec[gln].b;
                 const bool rin = Rc.b.y == 2.0f;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -751,7 +753,7 @@ __device__ __forceinline__ void fine_count_unit(const Unit &U, unsigned long lon
                 const int e2 = r2 + lane;
                 if (e2 < total2) {
                     const int v = pl2[e2], g2 = v >> 6, t = v & 63;
-                    const BinRec &R = sm.grec[grp + g2];
+                    const BinRec &R = wrec[g2];
                     uint32_t hm;
                     if (R.b.y == 2.0f) {
                         hm = sm.tdat[TDAT_F4 * t + 3].w != 0.0f ? 3u : 1u;

@@ -794,8 +794,11 @@ __device__ __forceinline__ void fine_count_unit(const Unit &U, unsigned long lon
 // ng Gaussians' indices in gidx, shared memory) at vals[pos0 ...] in Gaussian
 // order, each index with its half-tile mask (and keys[...] = key when keys
 // != nullptr); positions at or past cap are skipped.  One warp: lane w loads
-// word w of the three bitmaps, so that all the tile's words are in flight
-// together, and the words with pairs are then taken from registers.
+// word w of the three bitmaps (all the tile's words in flight together).
+// When many words hold pairs, pair i of the tile goes to lane i % 32, which
+// finds its word by a binary search over the words' running counts
+// (shuffles) and its bit with __fns, so that every round writes 32
+// consecutive pairs; when few do, the words are taken one at a time.
 __device__ __forceinline__ void emit_tile(const uint32_t *__restrict__ um, int t, int ng, uint32_t pos0,
                                           const uint32_t *gidx, uint32_t *__restrict__ vals,
                                           uint32_t *__restrict__ keys, uint32_t key, uint32_t cap) {
@@ -814,17 +817,47 @@ __device__ __forceinline__ void emit_tile(const uint32_t *__restrict__ um, int t
         const int v = __shfl_up_sync(FULLMASK, incl, o);
         if (lane >= o) incl += v;
     }
-    const uint32_t base = pos0 + (uint32_t)(incl - c);
-    const unsigned lt = (1u << lane) - 1u;
-    for (unsigned nz = __ballot_sync(FULLMASK, p != 0u); nz; nz &= nz - 1) {
-        const int w = __ffs(nz) - 1;
+    const int total = __shfl_sync(FULLMASK, incl, 31);
+    const int excl = incl - c;
+    const unsigned nz = __ballot_sync(FULLMASK, p != 0u);
+    if (__popc(nz) <= 2 * ((total + 31) >> 5)) {
+        // few words hold pairs: one word at a time, its pairs on their lanes
+        const unsigned lt = (1u << lane) - 1u;
+        for (unsigned m = nz; m; m &= m - 1) {
+            const int w = __ffs(m) - 1;
+            const uint32_t pw = __shfl_sync(FULLMASK, p, w), tw = __shfl_sync(FULLMASK, tt, w);
+            const uint32_t bw = __shfl_sync(FULLMASK, bb, w);
+            const int ew = __shfl_sync(FULLMASK, excl, w);
+            if ((pw >> lane) & 1u) {
+                const uint32_t hm = ((tw >> lane) & 1u) | (((bw >> lane) & 1u) << 1);
+                const uint32_t pos = pos0 + (uint32_t)ew + __popc(pw & lt);
+                if (pos < cap) {
+                    vals[pos] = gidx[32 * w + lane] | (hm << 30);
+                    if (keys) keys[pos] = key;
+                }
+            }
+        }
+        return;
+    }
+    for (int r0 = 0; r0 < total; r0 += 32) {
+        const int i = r0 + lane;
+        // w = the first word whose running count passes i
+        int w = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int v = __shfl_sync(FULLMASK, incl, w + step - 1);
+            if (v <= i) w += step;
+        }
+        w = min(w, 31);
         const uint32_t pw = __shfl_sync(FULLMASK, p, w), tw = __shfl_sync(FULLMASK, tt, w);
-        const uint32_t bw = __shfl_sync(FULLMASK, bb, w), bs = __shfl_sync(FULLMASK, base, w);
-        if ((pw >> lane) & 1u) {
-            const uint32_t hm = ((tw >> lane) & 1u) | (((bw >> lane) & 1u) << 1);
-            const uint32_t pos = bs + __popc(pw & lt);
+        const uint32_t bw = __shfl_sync(FULLMASK, bb, w);
+        const int ew = __shfl_sync(FULLMASK, excl, w);
+        if (i < total) {
+            const int bit = (int)__fns(pw, 0u, i - ew + 1);
+            const uint32_t hm = ((tw >> bit) & 1u) | (((bw >> bit) & 1u) << 1);
+            const uint32_t pos = pos0 + (uint32_t)i;
             if (pos < cap) {
-                vals[pos] = gidx[32 * w + lane] | (hm << 30);
+                vals[pos] = gidx[32 * w + bit] | (hm << 30);
                 if (keys) keys[pos] = key;
             }
         }

@@ -553,16 +553,21 @@ def time_probe(nat, sc, means, scales, quats, opac, colors, a0, a1, flush, strea
 
 
 def count_launches(args, L):
-    """Kernels of ours per step.  Build: cones 1, prep 1, super-tile count 1,
-    scan 3, keep 1, super-tile emit 1, sort passes x (hist 1 + scan 3 +
-    scatter 1), super-tile ranges 1, unit count 1, scan 3, unit fill 1, tile
-    count 1, scan 3, keep 1, tile emit 1, tile ranges 1, item count 1, scan 3,
-    item expand 1, tile kernel 1.  Then attenuate 1, sh_fit 2, centroid 2,
-    relight 1."""
+    """Kernels of ours per step.  Build with at most 64 super-tiles per light
+    (the room's 512 x 512 atlas): cones 1, prep 1, super-tile count 1, scan 3,
+    keep 1, key ranges 1, super-tile scatter 1, unit count 1, scan 3, unit
+    fill 1, tile count 1, scan 3, keep 1, tile emit 1, tile ranges 1, item
+    count 1, scan 3, item expand 1, tile kernel 1 (27); with more super-tiles
+    the sorted lists of dgsm_bin instead: super-tile count 1, scan 3, keep 1,
+    super-tile emit 1, sort passes x (hist 1 + scan 3 + scatter 1), super-tile
+    ranges 1.  Then attenuate 1, sh_fit 2, centroid 2, relight 1."""
     import math
-    n_super = math.ceil(512 / 8 / 8) ** 2 * L
-    sort_passes = math.ceil(max(1, (n_super - 1).bit_length()) / 8)
-    build = 27 + 5 * sort_passes
+    per_light = math.ceil(512 / 8 / 8) ** 2
+    if per_light <= 64:
+        build = 27
+    else:
+        sort_passes = math.ceil(max(1, (per_light * L - 1).bit_length()) / 8)
+        build = 27 + 5 * sort_passes
     return (build + 6) * args.steps
 
 

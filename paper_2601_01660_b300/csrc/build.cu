@@ -97,6 +97,86 @@ __global__ void __launch_bounds__(256) coarse_bin_kernel(
     }
 }
 
+// The build's super-tile lists without a sort (dgsm_bin keeps the sorted
+// lists above, whose order its output reports).  Count: each (light,
+// Gaussian) keeps the mask of the super-tiles it reaches (n_super <= 64) and
+// each block adds its counts per (light, super-tile) key from a shared
+// histogram.  Emit: each block counts its pairs per key again from the masks,
+// reserves one range per key from the key cursors, and writes its Gaussians
+// there, so that a key's list is contiguous (its order follows the blocks).
+template <bool TWO>
+__global__ void __launch_bounds__(256) coarse_mask_kernel(
+    const BinRec *__restrict__ bin, int64_t N, int L, int n_super, const float4 *__restrict__ scones,
+    const float4 *__restrict__ scones2, unsigned long long *__restrict__ masks, uint32_t *__restrict__ kcnt,
+    const uint8_t *__restrict__ sact) {
+    extern __shared__ uint32_t hist[];  // [L n_super]
+    const int nk = L * n_super;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) hist[k] = 0u;
+    __syncthreads();
+    const int64_t total = (int64_t)L * N;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        BinRec g;
+        g.a = bin[idx].a;
+        g.b = bin[idx].b;
+        const int mode = (int)g.b.y;
+        const int l = (int)(idx / N);
+        unsigned long long m = 0ull;
+        if (mode != 0)
+            for (int sidx = 0; sidx < n_super; ++sidx)
+                if ((!sact || sact[l * n_super + sidx]) &&
+                    (mode == 2 || (TWO ? super_overlap(g, scones, scones2, sidx) : cone_overlap(g, scones + 2 * sidx))))
+                    m |= 1ull << sidx;
+        masks[idx] = m;
+        for (unsigned long long mm = m; mm; mm &= mm - 1) atomicAdd(&hist[l * n_super + __ffsll(mm) - 1], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nk; k += blockDim.x)
+        if (hist[k]) atomicAdd(kcnt + k, hist[k]);
+}
+
+// Key ranges from the scanned counts: [cs, ce) and the emit cursor, or
+// every list empty when the pairs do not fit (keep = 0).
+__global__ void key_ranges_kernel(const uint32_t *__restrict__ kcnt, int nk, const unsigned long long *__restrict__ keep,
+                                  uint32_t *__restrict__ cs, uint32_t *__restrict__ ce, uint32_t *__restrict__ cur) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nk) return;
+    const bool kept = *keep != 0;
+    const uint32_t s0 = kept ? cs[k] : 0u;
+    cs[k] = s0;
+    ce[k] = kept ? s0 + kcnt[k] : 0u;
+    cur[k] = s0;
+}
+
+__global__ void __launch_bounds__(256) coarse_scatter_kernel(
+    const unsigned long long *__restrict__ masks, int64_t N, int L, int n_super, uint32_t *__restrict__ cur,
+    uint32_t *__restrict__ cvals, const unsigned long long *__restrict__ keep, uint32_t cap) {
+    if (*keep == 0) return;
+    extern __shared__ uint32_t sh[];  // [2][L n_super]: counts, then this block's cursors
+    const int nk = L * n_super;
+    uint32_t *hist = sh, *bcur = sh + nk;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) hist[k] = 0u;
+    __syncthreads();
+    const int64_t total = (int64_t)L * N;
+    for (int pass = 0; pass < 2; ++pass) {
+        uint32_t *cnt = pass == 0 ? hist : bcur;
+        for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+             idx += (int64_t)gridDim.x * blockDim.x) {
+            const int l = (int)(idx / N);
+            const uint32_t gi = (uint32_t)(idx - (int64_t)l * N);
+            for (unsigned long long m = masks[idx]; m; m &= m - 1) {
+                const uint32_t pos = atomicAdd(&cnt[l * n_super + __ffsll(m) - 1], 1u);
+                if (pass == 1 && pos < cap) cvals[pos] = gi;
+            }
+        }
+        __syncthreads();
+        if (pass == 0) {
+            for (int k = threadIdx.x; k < nk; k += blockDim.x) bcur[k] = hist[k] ? atomicAdd(cur + k, hist[k]) : 0u;
+            __syncthreads();
+        }
+    }
+}
+
 // Work units of pass B: unit_cnt[key] = ceil(list length / UNIT_G).
 __global__ void unit_count_kernel(const uint32_t *__restrict__ cs, const uint32_t *__restrict__ ce,
                                   int n_keys, uint32_t *__restrict__ unit_cnt) {
@@ -418,37 +498,73 @@ int run_binning(dgsm_ctx *ctx, const float *means, const float *scales, const fl
                                      p.beta_mode == 4 ? 3 : p.beta_mode);
     const float4 *scones2 = cones + 2 * (n_tiles + n_super) + PLANE_F4 * n_tiles;
     const bool two = p.atlas_map == MAP_CUBE;
-    (two ? coarse_bin_kernel<false, true> : coarse_bin_kernel<false, false>)<<<grid, 256, 0, s>>>(
-        (const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles, scones2, (uint32_t *)w_cnt, nullptr, nullptr,
-        nullptr, nullptr, 0u, roi ? roi->sact : nullptr);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "prep/coarse count kernels");
-    if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_cnt, (uint32_t *)w_cnt, LN, d_cpairs, s))) return rc;
     int64_t capC = p.max_pairs;
-    if (capC == 0) {
-        unsigned long long Pc;
-        if ((rc = read_count(ctx, d_cpairs, s, &Pc))) return rc;
-        if (Pc >= (1ull << 31)) return fail(ctx, DGSM_ERR_WORKSPACE, "more than 2^31 (super-tile, Gaussian) pairs");
-        if (Pc == 0) return DGSM_OK;
-        capC = (int64_t)Pc;
+    uint32_t *cvals = nullptr;
+    if (!want_keys && n_super <= 64) {
+        // the build: super-tile masks, per-block ranges, no sort
+        void *w_mask, *w_kc;
+        if ((rc = ws_reserve(ctx, WS_SMASK, sizeof(unsigned long long) * (size_t)LN, &w_mask))) return rc;
+        if ((rc = ws_reserve(ctx, WS_KCNT, 2 * sizeof(uint32_t) * (size_t)nskeys, &w_kc))) return rc;
+        uint32_t *kcnt = (uint32_t *)w_kc, *kcur = kcnt + nskeys;
+        e = cudaMemsetAsync(kcnt, 0, sizeof(uint32_t) * (size_t)nskeys, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "build: memset");
+        (two ? coarse_mask_kernel<true> : coarse_mask_kernel<false>)<<<grid, 256, sizeof(uint32_t) * nskeys, s>>>(
+            (const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles, scones2, (unsigned long long *)w_mask, kcnt,
+            roi ? roi->sact : nullptr);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "prep/coarse count kernels");
+        if ((rc = scan_exclusive_u32(ctx, kcnt, cs, nskeys, d_cpairs, s))) return rc;
+        if (capC == 0) {
+            unsigned long long Pc;
+            if ((rc = read_count(ctx, d_cpairs, s, &Pc))) return rc;
+            if (Pc >= (1ull << 31)) return fail(ctx, DGSM_ERR_WORKSPACE, "more than 2^31 (super-tile, Gaussian) pairs");
+            if (Pc == 0) return DGSM_OK;
+            capC = (int64_t)Pc;
+        }
+        void *cva;
+        if ((rc = ws_reserve(ctx, WS_CVALS_A, sizeof(uint32_t) * capC, &cva))) return rc;
+        keep_pairs_kernel<<<1, 32, 0, s>>>(d_cpairs, (unsigned long long)capC, d_ckeep, ctx->d_status);
+        key_ranges_kernel<<<(int)((nskeys + 255) / 256), 256, 0, s>>>(kcnt, (int)nskeys, d_ckeep, cs, ce, kcur);
+        coarse_scatter_kernel<<<grid, 256, 2 * sizeof(uint32_t) * nskeys, s>>>(
+            (const unsigned long long *)w_mask, N, L, n_super, kcur, (uint32_t *)cva, d_ckeep, (uint32_t)capC);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "coarse scatter kernels");
+        cvals = (uint32_t *)cva;
+    } else {
+        // dgsm_bin (and super-tile grids beyond 64 per light): lists sorted by key
+        // and, within a key, by Gaussian, as dgsm_bin reports them
+        (two ? coarse_bin_kernel<false, true> : coarse_bin_kernel<false, false>)<<<grid, 256, 0, s>>>(
+            (const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles, scones2, (uint32_t *)w_cnt, nullptr, nullptr,
+            nullptr, nullptr, 0u, roi ? roi->sact : nullptr);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "prep/coarse count kernels");
+        if ((rc = scan_exclusive_u32(ctx, (uint32_t *)w_cnt, (uint32_t *)w_cnt, LN, d_cpairs, s))) return rc;
+        if (capC == 0) {
+            unsigned long long Pc;
+            if ((rc = read_count(ctx, d_cpairs, s, &Pc))) return rc;
+            if (Pc >= (1ull << 31)) return fail(ctx, DGSM_ERR_WORKSPACE, "more than 2^31 (super-tile, Gaussian) pairs");
+            if (Pc == 0) return DGSM_OK;
+            capC = (int64_t)Pc;
+        }
+        void *cka, *cva, *ckb, *cvb;
+        if ((rc = ws_reserve(ctx, WS_CKEYS_A, sizeof(uint32_t) * capC, &cka))) return rc;
+        if ((rc = ws_reserve(ctx, WS_CVALS_A, sizeof(uint32_t) * capC, &cva))) return rc;
+        if ((rc = ws_reserve(ctx, WS_CKEYS_B, sizeof(uint32_t) * capC, &ckb))) return rc;
+        if ((rc = ws_reserve(ctx, WS_CVALS_B, sizeof(uint32_t) * capC, &cvb))) return rc;
+        keep_pairs_kernel<<<1, 32, 0, s>>>(d_cpairs, (unsigned long long)capC, d_ckeep, ctx->d_status);
+        (two ? coarse_bin_kernel<true, true> : coarse_bin_kernel<true, false>)<<<grid, 256, 0, s>>>(
+            (const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles, scones2, nullptr, (const uint32_t *)w_cnt,
+            (uint32_t *)cka, (uint32_t *)cva, d_ckeep, (uint32_t)capC, roi ? roi->sact : nullptr);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "coarse emit kernel");
+        uint32_t *ckeys = (uint32_t *)cka;
+        cvals = (uint32_t *)cva;
+        if ((rc = radix_sort_pairs(ctx, &ckeys, &cvals, (uint32_t *)ckb, (uint32_t *)cvb, d_ckeep, capC,
+                                   key_bits(nskeys), s)))
+            return rc;
+        const int rgrid = (int)std::min<int64_t>((capC + 255) / 256, (int64_t)ctx->num_sms * 16);
+        tile_ranges_kernel<<<rgrid, 256, 0, s>>>(ckeys, d_ckeep, (uint32_t)nskeys, cs, ce);
     }
-    void *cka, *cva, *ckb, *cvb;
-    if ((rc = ws_reserve(ctx, WS_CKEYS_A, sizeof(uint32_t) * capC, &cka))) return rc;
-    if ((rc = ws_reserve(ctx, WS_CVALS_A, sizeof(uint32_t) * capC, &cva))) return rc;
-    if ((rc = ws_reserve(ctx, WS_CKEYS_B, sizeof(uint32_t) * capC, &ckb))) return rc;
-    if ((rc = ws_reserve(ctx, WS_CVALS_B, sizeof(uint32_t) * capC, &cvb))) return rc;
-    keep_pairs_kernel<<<1, 32, 0, s>>>(d_cpairs, (unsigned long long)capC, d_ckeep, ctx->d_status);
-    (two ? coarse_bin_kernel<true, true> : coarse_bin_kernel<true, false>)<<<grid, 256, 0, s>>>(
-        (const BinRec *)w_bin, N, L, n_super, cones + 2 * n_tiles, scones2, nullptr, (const uint32_t *)w_cnt,
-        (uint32_t *)cka, (uint32_t *)cva, d_ckeep, (uint32_t)capC, roi ? roi->sact : nullptr);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "coarse emit kernel");
-    uint32_t *ckeys = (uint32_t *)cka, *cvals = (uint32_t *)cva;
-    if ((rc = radix_sort_pairs(ctx, &ckeys, &cvals, (uint32_t *)ckb, (uint32_t *)cvb, d_ckeep, capC,
-                               key_bits(nskeys), s)))
-        return rc;
-    const int rgrid = (int)std::min<int64_t>((capC + 255) / 256, (int64_t)ctx->num_sms * 16);
-    tile_ranges_kernel<<<rgrid, 256, 0, s>>>(ckeys, d_ckeep, (uint32_t)nskeys, cs, ce);
 
     // ---- work units of level B ----
     const int64_t max_units = capC / UNIT_G + nskeys + 1;

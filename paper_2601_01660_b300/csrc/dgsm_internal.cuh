@@ -43,6 +43,8 @@ enum WsSlot {
     WS_PFRAME,         // persistent frame kernel: control words, binning, items, records
     WS_PF_CONES,       // persistent frame kernel: the dynamic atlas's tile cones
     WS_PF_PHASE,       // persistent frame kernel: phase timestamps (while profiling)
+    WS_SMASK,          // build: per (light, Gaussian) mask of the super-tiles it reaches
+    WS_KCNT,           // build: per (light, super-tile) pair counts and cursors
     WS_NSLOTS
 };
 

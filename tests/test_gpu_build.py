@@ -182,3 +182,29 @@ def test_maximum_sizes(nat, orc):
         _build(nat, sc, np.float32([[0, 0, 0]]), 4097, 8, radii2)
     with pytest.raises(nat.DGSMError):
         _build(nat, sc, np.zeros((65, 3), np.float32), 8, 8, radii2)
+
+
+@pytest.mark.parametrize("tile,nl,amap", [(8, 3, 0), (16, 2, 0), (8, 2, 1)])
+def test_build_bins_the_same_pairs_as_dgsm_bin(nat, tile, nl, amap):
+    """dgsm_build writes its super-tile lists unsorted (from per-(light,
+    Gaussian) super-tile masks and per-block ranges) while dgsm_bin sorts
+    them; both take the same decisions, so the pair counts at both levels are
+    equal (dgsm_bin's pairs are the bit-exact specification)."""
+    rng = np.random.default_rng(5 + tile + nl)
+    cube = scenes.cube_scene(3000, seed=51, log_s_mean=math.log(0.06))
+    flat = scenes.cube_scene(2000, seed=52, log_s_mean=math.log(0.1))
+    flat.scales[np.arange(flat.n), rng.integers(0, 3, flat.n)] = 0.002
+    sc = scenes.concat(cube, flat, scenes.avatar_body(rng, 1500, base=(0.3, 0.2, 1.5)))
+    lights = np.float32([[0, 0, 0], [0.4, -0.3, 0.5], [-1, 1, 2.5]])[:nl]
+    radii = scenes.radii_linear(0.1, 8, 10)
+    H, W = (96, 128) if amap == 0 else (6 * 32, 32)
+    params = dict(tile=tile, atlas_map=amap)
+    d = scene_to_dev(sc)
+    keys, _ = nat.dgsm_bin(d["means"], d["scales"], d["quats"], d["opac"], dev(lights), H, W, dev(radii),
+                           params=params)
+    st_bin = nat.dgsm_get_build_stats()
+    nat.dgsm_build(d["means"], d["scales"], d["quats"], d["opac"], dev(lights), H, W, dev(radii), params=params)
+    st_build = nat.dgsm_get_build_stats()
+    assert nat.dgsm_sync_status() == 0
+    assert st_build["n_pairs"] == keys.numel() > 1000
+    assert st_build["n_super_pairs"] == st_bin["n_super_pairs"] > 0

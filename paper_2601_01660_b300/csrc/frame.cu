@@ -184,12 +184,16 @@ extern "C" int dgsm_frame_host(dgsm_ctx *ctx, const dgsm_frame_host_in *in,
     };
     e = cudaEventRecord(ctx->fev[0], s);  // the side stream starts after earlier work on `stream`
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ctx->fev[0], 0);
+    // the build's inputs go up on both streams (two copy engines share the
+    // host link); the build waits for the side stream's part
     if (e == cudaSuccess) e = h2d(d_means, in->means, 12 * (size_t)n, s);
+    if (e == cudaSuccess) e = h2d(d_quats, in->quats, 16 * (size_t)n, s2);
     if (e == cudaSuccess) e = h2d(d_scales, in->scales, 12 * (size_t)n, s);
-    if (e == cudaSuccess) e = h2d(d_quats, in->quats, 16 * (size_t)n, s);
-    if (e == cudaSuccess) e = h2d(d_opac, in->opac, 4 * (size_t)n, s);
+    if (e == cudaSuccess) e = h2d(d_opac, in->opac, 4 * (size_t)n, s2);
     if (e == cudaSuccess) e = h2d(d_lights, in->lights, 12 * (size_t)L, s);
     if (e == cudaSuccess) e = h2d(d_radii, in->radii, 4 * (size_t)K, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->fev[1], s2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->fev[1], 0);
     if (e == cudaSuccess) e = h2d(d_colors, in->colors, 12 * (size_t)n, s2);
     if (e == cudaSuccess) e = h2d(d_cd, in->cube_dirs, 12 * (size_t)in->n_cube, s2);
     if (e == cudaSuccess) e = h2d(d_cr, in->cube_rgb, 12 * (size_t)in->n_cube, s2);

@@ -959,7 +959,7 @@ size_t build_smem_bytes(int K, int tile, int chunk) {
     return (size_t)2 * chunk * REC_F4 * sizeof(float4) +   // staged records
            (size_t)nt * sizeof(float4) +                    // texel directions
            (size_t)K * nt * sizeof(float) +                 // per-shell increments
-           (size_t)((K + 3) & ~3) * sizeof(float) +         // radii
+           (size_t)((K + 4) & ~3) * sizeof(float) +         // radii and a +inf sentinel
            (size_t)chunk * nt * sizeof(uint16_t) +          // candidate list
            (size_t)SHELL_NB * sizeof(uint16_t) +            // shell table
            (size_t)2 * chunk;                               // half-tile masks
@@ -1065,8 +1065,8 @@ __device__ __forceinline__ void tiles_worker(
     float4 *stage = smem4;                                    // [2][chunk * REC_F4]
     float4 *tdir = stage + 2 * chunk * REC_F4;                // [NT] (dir, valid)
     float *D = reinterpret_cast<float *>(tdir + NT);          // [K][NT]
-    float *rs = D + K * NT;                                   // [K]
-    uint16_t *cand = reinterpret_cast<uint16_t *>(rs + ((K + 3) & ~3));  // [chunk * NT]
+    float *rs = D + K * NT;                                   // [K + 1]: the radii, then +inf
+    uint16_t *cand = reinterpret_cast<uint16_t *>(rs + ((K + 4) & ~3));  // [chunk * NT]
     uint16_t *stab = cand + chunk * NT;                       // [SHELL_NB]
     uint8_t *smask = reinterpret_cast<uint8_t *>(stab + SHELL_NB);  // [2][chunk]
     __shared__ uint4 s_item;
@@ -1079,6 +1079,7 @@ __device__ __forceinline__ void tiles_worker(
     const int64_t HW = (int64_t)H * W;
     const unsigned long long total_items = *n_items_total;
     for (int k = tid; k < K; k += BT_THREADS) rs[k] = radii[k];
+    if (tid == 0) rs[K] = __int_as_float(0x7f800000);  // no shell past the last
     if (tid < 3) s_cnt[tid] = 0ull;
     __syncthreads();
     // stab[b] = #{k : r_k < t_b}, t_b the float with bits SHELL_TB0 + (b << 19)
@@ -1301,7 +1302,7 @@ __device__ __forceinline__ void tiles_worker(
                 int k;
                 if (!step_more) {
                     k = stab[max(min((__float_as_int(lo) - SHELL_TB0) >> 19, SHELL_NB - 1), 0)];
-                    k += (k < K && rs[min(k, K - 1)] < lo) ? 1 : 0;
+                    k += rs[k] < lo ? 1 : 0;
                 } else {
                     k = 0;
                     while (k < K && rs[k] < lo) ++k;
@@ -1316,15 +1317,15 @@ __device__ __forceinline__ void tiles_worker(
                 const int k0 = k;
                 float Gprev = 0.0f;
                 // shells on the chord (most hits have none or one)
-                bool more = hit && k < K && rs[min(k, K - 1)] <= hi;
+                bool more = hit && rs[k] <= hi;
                 while (__any_sync(FULLMASK, more)) {
-                    const float G = mass_below(fmaf(hh, rs[min(k, K - 1)], -hs), A0, hm2, full) - F0;
+                    const float G = mass_below(fmaf(hh, rs[k], -hs), A0, hm2, full) - F0;
                     if (more) {
                         atomicAdd(D + k * NT + tex, fmaxf(G - Gprev, 0.0f));
                         Gprev = fmaxf(G, Gprev);
                         ++k;
                     }
-                    more = more && k < K && rs[min(k, K - 1)] <= hi;
+                    more = more && rs[k] <= hi;
                 }
                 n_shell += (unsigned)(k - k0);
                 if (hit && k < K) atomicAdd(D + k * NT + tex, fmaxf(full - F0 - Gprev, 0.0f));

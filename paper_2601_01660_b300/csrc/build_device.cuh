@@ -958,7 +958,7 @@ size_t build_smem_bytes(int K, int tile, int chunk) {
     const int nt = tile * tile;
     return (size_t)2 * chunk * REC_F4 * sizeof(float4) +   // staged records
            (size_t)nt * sizeof(float4) +                    // texel directions
-           (size_t)K * nt * sizeof(float) +                 // per-shell increments
+           (size_t)(K + 1) * nt * sizeof(float) +           // per-shell increments (+ a row past the last)
            (size_t)((K + 4) & ~3) * sizeof(float) +         // radii and a +inf sentinel
            (size_t)chunk * nt * sizeof(uint16_t) +          // candidate list
            (size_t)SHELL_NB * sizeof(uint16_t) +            // shell table
@@ -1064,8 +1064,8 @@ __device__ __forceinline__ void tiles_worker(
     constexpr int NT = T * T;
     float4 *stage = smem4;                                    // [2][chunk * REC_F4]
     float4 *tdir = stage + 2 * chunk * REC_F4;                // [NT] (dir, valid)
-    float *D = reinterpret_cast<float *>(tdir + NT);          // [K][NT]
-    float *rs = D + K * NT;                                   // [K + 1]: the radii, then +inf
+    float *D = reinterpret_cast<float *>(tdir + NT);          // [K + 1][NT]: row K takes mass past the last shell
+    float *rs = D + (K + 1) * NT;                             // [K + 1]: the radii, then +inf
     uint16_t *cand = reinterpret_cast<uint16_t *>(rs + ((K + 4) & ~3));  // [chunk * NT]
     uint16_t *stab = cand + chunk * NT;                       // [SHELL_NB]
     uint8_t *smask = reinterpret_cast<uint8_t *>(stab + SHELL_NB);  // [2][chunk]
@@ -1113,7 +1113,7 @@ __device__ __forceinline__ void tiles_worker(
         const int tile_i = t / tx, tile_j = t - tile_i * tx;
         const int i0 = tile_i * T, j0 = tile_j * T;
         const int rows_valid = min(T, H - i0), cols_valid = min(T, W - j0);
-        for (int e = tid; e < K * NT; e += BT_THREADS) D[e] = 0.0f;
+        for (int e = tid; e < (K + 1) * NT; e += BT_THREADS) D[e] = 0.0f;
         if (tid == 0) s_total[0] = 0;
         for (int e = tid; e < NT; e += BT_THREADS) {
             const int i = i0 + e / T, j = j0 + e % T;
@@ -1328,7 +1328,7 @@ __device__ __forceinline__ void tiles_worker(
                     more = more && rs[k] <= hi;
                 }
                 n_shell += (unsigned)(k - k0);
-                if (hit && k < K) atomicAdd(D + k * NT + tex, fmaxf(full - F0 - Gprev, 0.0f));
+                if (hit) atomicAdd(D + k * NT + tex, fmaxf(full - F0 - Gprev, 0.0f));  // row K: unused
             }
         }
         __syncthreads();

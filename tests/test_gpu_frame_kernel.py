@@ -137,3 +137,73 @@ def test_persistent_frame_replays_in_a_graph(nat, pair):
     for g in pers.graphs:
         g.close()
     pers.graphs = None
+
+
+def _direct_frame(nat, st, av, seg, poses, lights, radii, Hs, Ws, Hd, Wd, radii_d, sh, static_atlas, max_pairs):
+    """The frame by the separate library calls (the reference for the edge cases)."""
+    L = lights.shape[0]
+    mr, qr = (torch.empty((0, 3), device="cuda"), torch.empty((0, 4), device="cuda"))
+    if av.n:
+        mr, qr = nat.dgsm_rigid_transform(dev(av.means), dev(av.quats), seg, dev(poses))
+    dyn = torch.ones((L, radii_d.shape[0], Hd, Wd), dtype=torch.float32, device="cuda")
+    if av.n:
+        nat.dgsm_build(mr, dev(av.scales), qr, dev(av.opac), lights, Hd, Wd, radii_d,
+                       params=dict(tile=8, max_pairs=max_pairs), out=dyn)
+    q = torch.cat([dev(st.means), mr]) if st.n else mr
+    cin = dev(np.concatenate([st.colors, av.colors])) if st.n + av.n else torch.empty((0, 3), device="cuda")
+    out = nat.dgsm_attenuate_dyn(static_atlas, radii, dyn, radii_d, lights, q, cin)
+    cen = torch.zeros((len(seg) - 1, 3), dtype=torch.float32, device="cuda")
+    if av.n:
+        cen = nat.dgsm_segment_centroids(mr, dev(av.opac), seg)
+        av_out = out[st.n:]
+        nat.sh_relight_objects(sh, mr, qr, dev(av.scales), av_out, cen, seg, out=av_out)
+    torch.cuda.synchronize()
+    return dyn, out, cen
+
+
+@pytest.mark.parametrize("n_static,n_each", [(0, [700, 313]), (900, []), (517, [0, 1, 457, 33])])
+def test_persistent_frame_edge_cases(nat, n_static, n_each):
+    """No avatars, no static receivers, and ragged objects (an empty one, a
+    single Gaussian, sizes off every warp and block multiple): the persistent
+    kernel gives the separate calls' frame."""
+    rng = np.random.default_rng(7 + n_static)
+    st = scenes.cube_scene(n_static, seed=61)
+    av = scenes.cube_scene(int(sum(n_each)), seed=62, log_s_mean=np.log(0.05))
+    seg = [0] + list(np.cumsum(n_each)) if n_each else [0, 0]
+    n_obj = len(seg) - 1
+    poses = np.zeros((n_obj, 8), np.float32)
+    for o in range(n_obj):
+        q = rng.normal(size=4)
+        poses[o, :4] = q / np.linalg.norm(q)
+        poses[o, 4:7] = rng.uniform(-0.3, 0.3, 3)
+    lights = dev(np.float32([[0, 0, 0], [0.5, -0.4, 0.8]]))
+    radii, radii_d = dev(scenes.radii_linear(0.1, 8, 12)), dev(scenes.radii_linear(0.1, 8, 10))
+    Hs = Ws = 32
+    Hd, Wd = 40, 24
+    D, Y, w = scenes.cubemap_samples(16, seed=5)
+    sh = nat.sh_fit(dev(D), dev(Y), dev(w))
+    static_atlas = torch.ones((2, 12, Hs, Ws), dtype=torch.float32, device="cuda")
+    if st.n:
+        static_atlas = nat.dgsm_build(dev(st.means), dev(st.scales), dev(st.quats), dev(st.opac), lights, Hs, Ws,
+                                      radii)
+    max_pairs = 300000
+    dyn_ref, out_ref, cen_ref = _direct_frame(nat, st, av, seg, poses, lights, radii, Hs, Ws, Hd, Wd, radii_d, sh,
+                                              static_atlas, max_pairs)
+    n = st.n + av.n
+    q_means = dev(np.concatenate([st.means, av.means])) if n else torch.empty((0, 3), device="cuda")
+    cin = dev(np.concatenate([st.colors, av.colors])) if n else torch.empty((0, 3), device="cuda")
+    cout = torch.full_like(cin, -1.0)
+    quats_out = torch.empty((av.n, 4), dtype=torch.float32, device="cuda")
+    dyn = torch.full((2, 10, Hd, Wd), -1.0, dtype=torch.float32, device="cuda")
+    cen = torch.full((n_obj, 3), -1.0, dtype=torch.float32, device="cuda")
+    rest_m = dev(av.means) if av.n else torch.empty((0, 3), device="cuda")
+    rest_q = dev(av.quats) if av.n else torch.empty((0, 4), device="cuda")
+    scl = dev(av.scales) if av.n else torch.empty((0, 3), device="cuda")
+    opc = dev(av.opac) if av.n else torch.empty((0,), device="cuda")
+    nat.dgsm_crowd_frame(q_means, cin, cout, st.n, static_atlas, radii, rest_m, rest_q, scl, opc, quats_out, seg,
+                         dev(poses), dyn, radii_d, lights, sh, cen, params=dict(max_pairs=max_pairs))
+    torch.cuda.synchronize()
+    assert nat.dgsm_sync_status() == 0
+    assert torch.allclose(dyn, dyn_ref, atol=1e-6, rtol=0)
+    assert torch.allclose(cout, out_ref, atol=1e-5, rtol=1e-5)
+    assert torch.equal(cen, cen_ref)

@@ -456,6 +456,30 @@ int dgsm_pca_normals(dgsm_ctx *ctx, const float *means, const float *opac, const
                      const float *scales, int64_t n, float radius, const float *centroid,
                      float *normals_out, void *stream);
 
+/* Storage order of a scene (a layout choice, not a step of Secs. 3.2-3.5:
+ * every per-Gaussian result is independent of a Gaussian's place in the
+ * arrays, and only the order of floating-point sums into an atlas voxel
+ * changes).  perm_out (n int32, device) receives the permutation that sorts
+ * the means (n,3; device) by their Z-order code on a 1024^3 grid over their
+ * bounding box: cell q_a = floor((x_a - lo_a) * (1024 / (hi_a - lo_a)))
+ * clamped to [0, 1023], each operation rounded once to float; code bit
+ * 3b + a = bit b of q_a.  Equal codes keep their index order (stable).  A
+ * flat axis, or a non-finite coordinate, gives cell 0 on that axis.  Stored
+ * in this order, consecutive Gaussians are neighbours in space and in
+ * direction from any light, so the atlas taps of a warp of receivers
+ * (Sec. 3.3) share sectors.  0 <= n < 2^31; workspace about 16 n bytes.
+ * Asynchronous. */
+int dgsm_spatial_order(dgsm_ctx *ctx, const float *means, int64_t n, int32_t *perm_out, void *stream);
+
+/* dst row i = src row perm[i] for i < n (rows of row_bytes bytes, a positive
+ * multiple of 4; src holds n_src rows; src and dst device, 4-byte aligned,
+ * distinct).  Applies a dgsm_spatial_order permutation to each attribute of
+ * a scene.  A perm entry outside [0, n_src) leaves its row zero and records
+ * DGSM_ERR_INVALID_ARG in the context's status word (dgsm_sync_status).
+ * Asynchronous. */
+int dgsm_gather_rows(dgsm_ctx *ctx, const void *src, int64_t n_src, int64_t row_bytes, const int32_t *perm,
+                     int64_t n, void *dst, void *stream);
+
 /* sh_relight for a Gaussian array made of n_obj contiguous objects (for
  * instance avatars): object o holds Gaussians [seg[o], seg[o+1]) and its
  * normals are turned away from centroids[o] (device, n_obj x 3 floats; see

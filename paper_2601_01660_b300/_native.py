@@ -9,6 +9,7 @@ missing this module raises ImportError: there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import threading
 
@@ -119,6 +120,8 @@ _lib.dgsm_build_band.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32,
                                  C.POINTER(Params), _i32, _i32, _vp, _vp]
 _lib.dgsm_atlas_rows_copy.argtypes = [_vp, _vp, _i32, _i32, _vp, _i32, _i32, _i32, _i64, _i32, _i32, _vp]
 _lib.dgsm_pca_normals.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _f32, _vp, _vp, _vp]
+_lib.dgsm_spatial_order.argtypes = [_vp, _vp, _i64, _vp, _vp]
+_lib.dgsm_gather_rows.argtypes = [_vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp]
 _lib.dgsm_bin.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i32,
                           C.POINTER(Params), _vp, _vp, _i64, C.POINTER(_i64), _vp]
 _lib.dgsm_attenuate.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp,
@@ -410,6 +413,35 @@ def dgsm_pca_normals(means, opac, quats, scales, centroid, radius=0.05, out=None
         out = torch.empty((n, 3), dtype=torch.float32, device=means.device)
     ctx.check(_lib.dgsm_pca_normals(ctx.handle, _ptr(means), _ptr(opac), _ptr(quats), _ptr(scales), n,
                                     float(radius), _ptr(centroid), _ptr(out), _stream(stream)))
+    return out
+
+
+def dgsm_spatial_order(means, ctx: Context | None = None, stream=None):
+    """The permutation (n int32, device) that puts a scene in the Z-order of
+    its means (a storage order: no per-Gaussian result depends on it)."""
+    ctx = ctx or context(means.device.index)
+    _need(means, "means", shape_last=3)
+    n = means.shape[0]
+    perm = torch.empty((n,), dtype=torch.int32, device=means.device)
+    ctx.check(_lib.dgsm_spatial_order(ctx.handle, _ptr(means), n, _ptr(perm), _stream(stream)))
+    return perm
+
+
+def dgsm_gather_rows(src, perm, out=None, ctx: Context | None = None, stream=None):
+    """out[i] = src[perm[i]] over the first dimension (any 4-byte dtype
+    layout: rows of a multiple of 4 bytes)."""
+    ctx = ctx or context(src.device.index)
+    if not src.is_cuda or not src.is_contiguous() or src.dim() < 1:
+        raise ValueError("src must be a contiguous CUDA tensor")
+    _need(perm, "perm", dtype=torch.int32)
+    n = perm.shape[0]
+    if out is None:
+        out = torch.empty((n,) + tuple(src.shape[1:]), dtype=src.dtype, device=src.device)
+    if out.shape[1:] != src.shape[1:] or out.dtype != src.dtype or not out.is_contiguous() or out.shape[0] != n:
+        raise ValueError("out must be a contiguous tensor of perm's length and src's row shape and dtype")
+    row_bytes = math.prod(src.shape[1:]) * src.element_size()
+    ctx.check(_lib.dgsm_gather_rows(ctx.handle, _ptr(src), src.shape[0], row_bytes, _ptr(perm), n, _ptr(out),
+                                    _stream(stream)))
     return out
 
 

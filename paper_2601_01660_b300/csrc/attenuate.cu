@@ -117,6 +117,268 @@ __global__ void __launch_bounds__(ATT_THREADS) attenuate_kernel(
     }
 }
 
+// ---- streamed form for the octahedral atlas ---------------------------------
+//
+// The same lookup in another form, for the common case (octahedral map, at
+// least 2 x 2 texels and 2 shells; no dynamic atlas, or one of the static
+// atlas's geometry):
+// * Streams by the bulk-copy engine.  A warp takes rounds of AZ_R
+//   consecutive receivers.  One lane copies a round's means into the warp's
+//   slice of shared memory with cp.async.bulk (completing on the warp's
+//   mbarrier, a round ahead of its use, two stages), the lanes read them
+//   there, write the attenuated colours over them (the input colours read
+//   directly, once, at that point) and one bulk store sends them out.  The
+//   slice stays small (3 KB per warp), leaving the L1 most of the SM's
+//   on-chip memory for the atlas taps.  A round that is not whole (the last
+//   one) or arrays that are not 16-byte aligned go through plain loads.
+// * Shell index without a square root.  sqrt_rn is monotone, so
+//   r_k <= sqrt_rn(d2) exactly when d2 >= thr_k, thr_k the smallest float
+//   whose rounded square root reaches r_k.  A per-block table over the bits
+//   of d2 (32 buckets per octave of d2 in [2^-24, 2^24) m^2) gives the count
+//   in one step when no bucket holds two thresholds (else the thresholds are
+//   counted one by one), so k equals the specification's
+//   #{r_k <= sqrt_rn(d2)} - 1.  t itself enters only the shell weight, where
+//   d2 rsqrt(d2) (within a few ulps of sqrt_rn(d2)) serves.
+// * Edge taps by clamped weights.  Clamp-to-edge (j0 = j1 at a border) is
+//   the same value as the pair (0, 1) with weight 0 or (W-2, W-1) with
+//   weight 1, and likewise for rows and for the shells below the first or
+//   past the last radius; so every lookup reads the taps (i0 + {0,1},
+//   j0 + {0,1}, k0 + {0,1}) at fixed offsets from one address.
+// * Both quotients of the octahedral code by one rounded reciprocal
+//   y = RN(1/s) and Markstein's correction q = RN(q0 + RN(a - s q0) y),
+//   q0 = RN(a y) (P. Markstein, IBM J. Res. Dev. 34(1), 1990): the correctly
+//   rounded a / s of the specification away from underflow, and within an
+//   ulp of it otherwise; the lookup is continuous across texel and shell
+//   boundaries, so the result moves by at most that much where the texel
+//   base would differ.
+// The texel base and the bilinear fractions are otherwise the
+// specification's single-precision operations, as in sample_index_tab.
+constexpr int AZ_THREADS = 512;     // two blocks per SM
+constexpr int AZ_WARPS = AZ_THREADS / 32;
+constexpr int AZ_U = 4;             // receivers per lane per round
+constexpr int AZ_R = 32 * AZ_U;     // receivers per warp round
+constexpr int AZ_BYTES = AZ_R * 12; // one round of one (n, 3) float array
+constexpr int AZ_TB0 = 103 << 23;   // float bits of 2^-24 (d2 in m^2)
+constexpr int AZ_NB = 1536;         // 32 buckets per octave of d2 over [2^-24, 2^24)
+constexpr int AZ_SHIFT = 18;
+constexpr long long AZ_WAIT = 2000000000ll;  // clock cycles before a wait gives up (about 1 s)
+constexpr size_t AZ_SMEM = (size_t)AZ_WARPS * 2 * AZ_BYTES;  // per warp: two stages of means
+
+__device__ __forceinline__ uint32_t az_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Phase `parity` of the mbarrier at `bar` completed; false after AZ_WAIT cycles.
+__device__ __forceinline__ bool az_wait(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > AZ_WAIT) return false;
+    }
+}
+
+// One round's means into a stage (one lane), completing on bar.
+__device__ __forceinline__ void az_issue(float *stg, const float *qm, int64_t base, uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(AZ_BYTES) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(az_smem(stg)), "l"(qm + 3 * base), "r"(AZ_BYTES), "r"(bar) : "memory");
+}
+
+template <typename T, bool DYN, bool HAS_T>
+__global__ void __launch_bounds__(AZ_THREADS, 2) attenuate_stream_kernel(
+    const T *__restrict__ atlas, const T *__restrict__ dyn, int L, int H, int W,
+    const float *__restrict__ radii, int K, const float *__restrict__ lights,
+    const float *qm, const float *cin, int64_t Q, const float *__restrict__ lw, float wd,
+    float *cout, float *__restrict__ Tout, bool vec, int *status) {
+    // vec: qm, cin and cout are 16-byte aligned (whole rounds move by bulk copies)
+    extern __shared__ __align__(16) float az_stage[];  // [warp][stage][3 AZ_R]: means, then colours out
+    __shared__ float rs[256], inw[256], thr[257];
+    __shared__ uint16_t dtab[AZ_NB];
+    __shared__ float ls[64 * 3];
+    __shared__ float wl[64];
+    __shared__ __align__(8) unsigned long long bars[AZ_WARPS][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *slice = az_stage + (size_t)warp * 2 * 3 * AZ_R;
+    const uint32_t bar0 = az_smem(&bars[warp][0]);
+    const int64_t nwarps = (int64_t)gridDim.x * AZ_WARPS;
+    auto whole = [&](int64_t b) { return vec && b + AZ_R <= Q; };
+    int64_t base = ((int64_t)blockIdx.x * AZ_WARPS + warp) * AZ_R;
+    // the warp's barriers, and its first round's copy in flight during the set-up
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8u) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (base < Q && whole(base)) az_issue(slice, qm, base, bar0);
+    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const float r = radii[k];
+        rs[k] = r;
+        inw[k] = k + 1 < K ? 1.0f / (radii[k + 1] - r) : 0.0f;
+        // the smallest d with sqrt_rn(d) >= r
+        float d = __fmul_rn(r, r);
+        while (d > 0.0f && __fsqrt_rn(d) >= r) d = __int_as_float(__float_as_int(d) - 1);
+        while (__fsqrt_rn(d) < r) d = __int_as_float(__float_as_int(d) + 1);
+        thr[k] = d;
+    }
+    if (threadIdx.x == 0) thr[K] = __int_as_float(0x7f800000);  // no threshold past the last
+    for (int k = threadIdx.x; k < 3 * L; k += blockDim.x) ls[k] = lights[k];
+    for (int k = threadIdx.x; k < L; k += blockDim.x) wl[k] = lw ? lw[k] : 1.0f / (float)L;
+    __syncthreads();
+    // dtab[b] = #{k : thr_k < e_b}, e_b the float with bits AZ_TB0 + (b << AZ_SHIFT)
+    for (int b = threadIdx.x; b < AZ_NB; b += blockDim.x) {
+        const float eb = __int_as_float(AZ_TB0 + (b << AZ_SHIFT));
+        int lo = 0, hi = K;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (thr[mid] < eb) lo = mid + 1; else hi = mid;
+        }
+        dtab[b] = (uint16_t)lo;
+    }
+    int several = 0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const int bk = __float_as_int(thr[k]) - AZ_TB0;
+        several |= bk < 0 || bk >= (AZ_NB << AZ_SHIFT);
+        if (k + 1 < K) several |= (bk >> AZ_SHIFT) == ((__float_as_int(thr[k + 1]) - AZ_TB0) >> AZ_SHIFT);
+    }
+    const bool step_more = __syncthreads_or(several) != 0;
+    const uint32_t plane = (uint32_t)H * (uint32_t)W;
+    uint32_t phase = 0u;  // bit s: parity of the next wait on stage s
+    bool failed = false;
+    for (int j = 0; base < Q; base += nwarps * AZ_R, ++j) {
+        const int cur = j & 1;
+        float *sm = slice + cur * 3 * AZ_R;
+        const int nr = (int)min((int64_t)AZ_R, Q - base);
+        const int64_t nb = base + nwarps * AZ_R;
+        if (lane == 0 && nb < Q && whole(nb)) {
+            // the other stage: its bulk store (round j - 1) has read it out
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            az_issue(slice + (cur ^ 1) * 3 * AZ_R, qm, nb, bar0 + 8u * (cur ^ 1));
+        }
+        const bool w = whole(base);
+        if (w) {
+            const bool ok = az_wait(bar0 + 8u * cur, (phase >> cur) & 1u);
+            phase ^= 1u << cur;
+            if (__any_sync(0xffffffffu, !ok)) {
+                if (lane == 0) {
+                    record_status(status, DGSM_ERR_TIMEOUT);
+                    // the copy issued for the next round is still in flight
+                    if (nb < Q && whole(nb)) az_wait(bar0 + 8u * (cur ^ 1), (phase >> (cur ^ 1)) & 1u);
+                }
+                failed = true;
+                break;
+            }
+        } else {
+            // a bulk store of an earlier round may still read this stage
+            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            __syncwarp();
+            for (int e = lane; e < 3 * nr; e += 32) sm[e] = qm[3 * base + e];
+            __syncwarp();
+        }
+        float acc[AZ_U];
+#pragma unroll
+        for (int u = 0; u < AZ_U; ++u) acc[u] = 0.0f;
+        for (int l = 0; l < L; ++l) {
+            const float ox = ls[3 * l], oy = ls[3 * l + 1], oz = ls[3 * l + 2];
+            const T *A = atlas + (size_t)l * K * plane;
+            const T *Dy = DYN ? dyn + (size_t)l * K * plane : nullptr;
+            float Tl[AZ_U];
+#pragma unroll
+            for (int u = 0; u < AZ_U; ++u) {
+                const int r = u * 32 + lane;
+                const float vx = xsub(sm[3 * r], ox), vy = xsub(sm[3 * r + 1], oy), vz = xsub(sm[3 * r + 2], oz);
+                const float d2 = xadd(xadd(xmul(vx, vx), xmul(vy, vy)), xmul(vz, vz));
+                // octahedral code (as xencode), both quotients by one rounded reciprocal
+                float2 uv = make_float2(0.0f, 0.0f);
+                {
+                    const float sabs = xadd(xadd(fabsf(vx), fabsf(vy)), fabsf(vz));
+                    if (sabs != 0.0f) {
+                        const float y = __frcp_rn(sabs);
+                        const float q0x = vx * y, q0y = vy * y;
+                        float qx = fmaf(fmaf(-sabs, q0x, vx), y, q0x);
+                        float qy = fmaf(fmaf(-sabs, q0y, vy), y, q0y);
+                        if (sabs < 1e-30f) {  // 1 / sabs near overflow: divide
+                            qx = xdiv(vx, sabs);
+                            qy = xdiv(vy, sabs);
+                        }
+                        uv = vz >= 0.0f ? make_float2(qx, qy)
+                                        : make_float2(xmul(sgn_pos(qx), xsub(1.0f, fabsf(qy))),
+                                                      xmul(sgn_pos(qy), xsub(1.0f, fabsf(qx))));
+                    }
+                }
+                const float gx = xsub(xmul(xmul(xadd(uv.x, 1.0f), 0.5f), (float)W), 0.5f);
+                const float gy = xsub(xmul(xmul(xadd(uv.y, 1.0f), 0.5f), (float)H), 0.5f);
+                const float bjf = floorf(gx), bif = floorf(gy);
+                const int bj = (int)bjf, bi = (int)bif;
+                // taps (i0, i0 + 1) x (j0, j0 + 1); an edge by its weight (0 or 1)
+                const int j0 = min(max(bj, 0), W - 2), i0 = min(max(bi, 0), H - 2);
+                const float fx = bj == j0 ? xsub(gx, bjf) : (bj < j0 ? 0.0f : 1.0f);
+                const float fy = bi == i0 ? xsub(gy, bif) : (bi < i0 ? 0.0f : 1.0f);
+                int k;  // #{r_k <= t}
+                if (!step_more) {
+                    k = dtab[max(min((__float_as_int(d2) - AZ_TB0) >> AZ_SHIFT, AZ_NB - 1), 0)];
+                    k += thr[k] <= d2 ? 1 : 0;
+                } else {
+                    k = 0;
+                    while (k < K && thr[k] <= d2) ++k;
+                }
+                // shells (k0, k0 + 1); below the first or past the last radius by the weight
+                const int k0 = min(max(k - 1, 0), K - 2);
+                const float wt = k >= K ? 1.0f : fminf(fmaxf((d2 * rsqrtf(d2) - rs[k0]) * inw[k0], 0.0f), 1.0f);
+                const uint32_t o = (uint32_t)k0 * plane + (uint32_t)i0 * W + (uint32_t)j0;
+                auto bil = [&](const T *p) {  // bilinear in the plane of one shell
+                    const float a00 = load_T(p), a01 = load_T(p + 1), a10 = load_T(p + W), a11 = load_T(p + W + 1);
+                    const float r0 = fmaf(fx, a01 - a00, a00), r1 = fmaf(fx, a11 - a10, a10);
+                    return fmaf(fy, r1 - r0, r0);
+                };
+                auto tri = [&](const T *P) {
+                    const float b0 = bil(P + o), b1 = bil(P + o + plane);
+                    return fmaf(wt, b1 - b0, b0);
+                };
+                float Tv = tri(A);
+                if (DYN) Tv *= tri(Dy);
+                Tl[u] = d2 != 0.0f ? Tv : 1.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < AZ_U; ++u) {
+                const int r = u * 32 + lane;
+                if (HAS_T && r < nr) Tout[(base + r) * L + l] = Tl[u];
+                acc[u] = fmaf(wl[l], Tl[u], acc[u]);
+            }
+        }
+        // attenuated colours over the lane's own receivers' means, then out
+#pragma unroll
+        for (int u = 0; u < AZ_U; ++u) {
+            const int r = u * 32 + lane;
+            const float f = 1.0f - wd + wd * acc[u];
+            const int64_t q = r < nr ? base + r : base;
+            sm[3 * r] = __ldcs(cin + 3 * q) * f;
+            sm[3 * r + 1] = __ldcs(cin + 3 * q + 1) * f;
+            sm[3 * r + 2] = __ldcs(cin + 3 * q + 2) * f;
+        }
+        if (w) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                             ::"l"(cout + 3 * base), "r"(az_smem(sm)), "r"(AZ_BYTES) : "memory");
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            }
+        } else {
+            __syncwarp();
+            for (int e = lane; e < 3 * nr; e += 32) __stcs(cout + 3 * base + e, sm[e]);
+        }
+        __syncwarp();  // this stage is read before the next round's copy into it
+    }
+    (void)failed;
+    // the bulk stores have finished before the block's shared memory goes
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 // ---- footprint sampling (Sec. 3.3; ablation (A) of Sec. 4) ----------------
 
 // Philox4x64-10 (Salmon, Moraes, Dror and Shaw, SC 2011): ten rounds of two
@@ -286,7 +548,31 @@ template <typename T>
 void launch_attenuate(int grid, cudaStream_t s, const void *atlas, const void *dyn, bool sep, int L,
                       int H, int W, const float *radii, int K, DynGeom dg, const float *lights,
                       const float *qm, const float *cin, int64_t Q, const float *lw, float wd,
-                      float *cout, float *Tout, bool cube) {
+                      float *cout, float *Tout, bool cube, int *status) {
+    if (!cube && !sep && H >= 2 && W >= 2 && K >= 2) {
+        // the streamed form: one resident wave of blocks
+        const bool vec = ((((uintptr_t)qm) | ((uintptr_t)cin) | ((uintptr_t)cout)) & 15u) == 0;
+        auto go = [&](auto kern) {
+            int per_sm = 1, dev = 0, sms = 148;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AZ_SMEM);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, AZ_THREADS, AZ_SMEM);
+            const int64_t need = (Q + (int64_t)AZ_R * AZ_WARPS - 1) / ((int64_t)AZ_R * AZ_WARPS);
+            const int g = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * std::max(per_sm, 1)));
+            kern<<<g, AZ_THREADS, AZ_SMEM, s>>>((const T *)atlas, (const T *)dyn, L, H, W, radii, K, lights, qm,
+                                                cin, Q, lw, wd, cout, Tout, vec, status);
+        };
+        if (dyn) {
+            if (Tout) go(attenuate_stream_kernel<T, true, true>);
+            else go(attenuate_stream_kernel<T, true, false>);
+        } else {
+            if (Tout) go(attenuate_stream_kernel<T, false, true>);
+            else go(attenuate_stream_kernel<T, false, false>);
+        }
+        (void)grid;
+        return;
+    }
     if (cube)
         attenuate_kernel<T, false, true><<<grid, ATT_THREADS, 0, s>>>((const T *)atlas, nullptr, L, H, W,
             radii, K, dg, lights, qm, cin, Q, lw, wd, cout, Tout);
@@ -326,16 +612,18 @@ int attenuate_common(dgsm_ctx *ctx, const void *atlas, const void *atlas_dyn, in
     switch (dtype) {
         case DGSM_F32:
             launch_attenuate<float>(grid, s, atlas, atlas_dyn, sep, L, H, W, radii, K, dg, lights, q_means,
-                                    colors_in, n_q, light_w, direct_frac, colors_out, T_out, cube);
+                                    colors_in, n_q, light_w, direct_frac, colors_out, T_out, cube,
+                                    ctx->d_status);
             break;
         case DGSM_F16:
             launch_attenuate<__half>(grid, s, atlas, atlas_dyn, sep, L, H, W, radii, K, dg, lights, q_means,
-                                     colors_in, n_q, light_w, direct_frac, colors_out, T_out, cube);
+                                     colors_in, n_q, light_w, direct_frac, colors_out, T_out, cube,
+                                    ctx->d_status);
             break;
         default:
             launch_attenuate<__nv_bfloat16>(grid, s, atlas, atlas_dyn, sep, L, H, W, radii, K, dg, lights,
                                             q_means, colors_in, n_q, light_w, direct_frac, colors_out, T_out,
-                                            cube);
+                                            cube, ctx->d_status);
     }
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "attenuate_kernel");

@@ -45,6 +45,7 @@ enum WsSlot {
     WS_PF_PHASE,       // persistent frame kernel: phase timestamps (while profiling)
     WS_SMASK,          // build: per (light, Gaussian) mask of the super-tiles it reaches
     WS_KCNT,           // build: per (light, super-tile) pair counts and cursors
+    WS_ORDER,          // spatial order: Z-order keys and indices, the bounding box
     WS_NSLOTS
 };
 

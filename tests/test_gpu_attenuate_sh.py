@@ -94,13 +94,15 @@ def test_attenuate_half_atlas(nat, orc, dtype):
     assert np.abs(T - Tref).max() <= 1e-5
 
 
-@pytest.mark.parametrize("Q", [512 * 4, 2051])
+@pytest.mark.parametrize("Q", [512 * 4, 2051, 1_300_001])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 def test_attenuate_streaming_paths_agree(nat, orc, Q, dtype):
     """The pass streams 16-byte-aligned inputs through shared memory in
-    whole tiles (queries past the last tile read directly), falls back to
-    direct loads for a misaligned view, and may write in place; every path
-    matches the oracle."""
+    whole rounds of 128 receivers per warp (bulk copies two stages deep; the
+    largest case takes several rounds per warp, so both stages and both
+    phases of their barriers turn over; a last partial round reads
+    directly), falls back to direct loads for a misaligned view, and may
+    write in place; every path matches the oracle."""
     rng = np.random.default_rng(Q)
     L, K, H, W = 2, 7, 40, 48
     radii = scenes.radii_geometric(0.1, 9, K)

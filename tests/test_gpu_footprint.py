@@ -62,12 +62,16 @@ def test_footprint_matches_oracle(nat, orc, small, mode, n, dtype):
 
 
 def test_footprint_centre_equals_centre_lookup(nat, small):
+    """The footprint pass's centre mode is the centre lookup; the streamed
+    centre-lookup kernel rounds its interpolation in another order (lerps,
+    and d2 rsqrt(d2) for t in the shell weight), so the two agree to a few
+    ulps rather than bit for bit."""
     sc, lights, radii, atlas, q = small
     args = (atlas, dev(radii), dev(lights), dev(q.means))
     c0, T0 = nat.dgsm_attenuate(*args, dev(q.colors), want_T=True)
     c1, T1 = nat.dgsm_attenuate_footprint(*args, dev(q.quats), dev(q.scales), dev(q.colors),
                                           mode="centre", want_T=True)
-    assert torch.equal(T0, T1) and torch.equal(c0, c1)
+    assert torch.allclose(T0, T1, atol=1e-6, rtol=0) and torch.allclose(c0, c1, atol=1e-6, rtol=0)
 
 
 def test_footprint_seed_and_in_place(nat, small):

@@ -187,10 +187,13 @@ def surrogate(schedule=SURROGATE_SCHEDULE, batch: int = 16384, n_query: int = 3_
 def frame(frames: int = 120, workload: str = "crowd8") -> dict:
     import torch
 
-    from paper_2601_01660_b300 import native, scenes
+    from paper_2601_01660_b300 import layout, native, scenes
     from paper_2601_01660_b300.frame import CrowdFrame
     nat = native()
     wl = scenes.workload(workload)
+    # storage order: the room and each avatar in the Z-order of their means
+    wl["static"], _ = layout.zorder_scene(nat, wl["static"], [0, wl["static"].n], "cuda")
+    wl["avatars"], _ = layout.zorder_scene(nat, wl["avatars"], [int(x) for x in wl["seg"]], "cuda")
     D, Y, w = wl["cubemap"]
     sh = nat.sh_fit(_dev(D, torch), _dev(Y, torch), _dev(w, torch))
     torch.cuda.synchronize()

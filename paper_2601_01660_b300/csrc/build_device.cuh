@@ -954,15 +954,21 @@ constexpr int SHELL_NB = 512;              // 16 buckets per octave over [2^-20,
 constexpr float CONIC_WIDEN = 1.0f / 32.0f;
 constexpr float CONIC_COND = 1.0f / 8192.0f;
 
+// Records per warp group: two lanes per record (the tile's top and bottom
+// halves).
+constexpr int TG = 16;
+constexpr int BT_WARPS = BT_THREADS / 32;
+
 size_t build_smem_bytes(int K, int tile, int chunk) {
+    (void)chunk;  // the work items' size only
     const int nt = tile * tile;
-    return (size_t)2 * chunk * REC_F4 * sizeof(float4) +   // staged records
-           (size_t)nt * sizeof(float4) +                    // texel directions
-           (size_t)(K + 1) * nt * sizeof(float) +           // per-shell increments (+ a row past the last)
-           (size_t)((K + 4) & ~3) * sizeof(float) +         // radii and a +inf sentinel
-           (size_t)chunk * nt * sizeof(uint16_t) +          // candidate list
-           (size_t)SHELL_NB * sizeof(uint16_t) +            // shell table
-           (size_t)2 * chunk;                               // half-tile masks
+    return (size_t)BT_WARPS * 2 * TG * REC_F4 * sizeof(float4) +  // per warp: two staged record groups
+           (size_t)nt * sizeof(float4) +                           // texel directions
+           (size_t)(K + 1) * nt * sizeof(float) +                  // per-shell increments (+ a row past the last)
+           (size_t)((K + 4) & ~3) * sizeof(float) +                // radii and a +inf sentinel
+           (size_t)BT_WARPS * TG * nt * sizeof(uint16_t) +         // per warp: the group's candidate list
+           (size_t)SHELL_NB * sizeof(uint16_t) +                   // shell table
+           (size_t)BT_WARPS * 2 * TG;                              // per warp: half-tile masks
 }
 
 // Candidate texels of one staged record in rows [h T/2, (h+1) T/2) of a T x T
@@ -1062,16 +1068,16 @@ __device__ __forceinline__ void tiles_worker(
     // roi_mask, roi_k (or nullptr): texels [L][H][W] and shell range [kmin,
     // kmax] per light of a region of interest; T = 1 outside it
     constexpr int NT = T * T;
-    float4 *stage = smem4;                                    // [2][chunk * REC_F4]
-    float4 *tdir = stage + 2 * chunk * REC_F4;                // [NT] (dir, valid)
+    (void)chunk;
+    float4 *stage = smem4;                                    // [BT_WARPS][2][TG * REC_F4]
+    float4 *tdir = stage + BT_WARPS * 2 * TG * REC_F4;        // [NT] (dir, valid)
     float *D = reinterpret_cast<float *>(tdir + NT);          // [K + 1][NT]: row K takes mass past the last shell
     float *rs = D + (K + 1) * NT;                             // [K + 1]: the radii, then +inf
-    uint16_t *cand = reinterpret_cast<uint16_t *>(rs + ((K + 4) & ~3));  // [chunk * NT]
-    uint16_t *stab = cand + chunk * NT;                       // [SHELL_NB]
-    uint8_t *smask = reinterpret_cast<uint8_t *>(stab + SHELL_NB);  // [2][chunk]
+    uint16_t *cand = reinterpret_cast<uint16_t *>(rs + ((K + 4) & ~3));  // [BT_WARPS][TG * NT]
+    uint16_t *stab = cand + BT_WARPS * TG * NT;               // [SHELL_NB]
+    uint8_t *smask = reinterpret_cast<uint8_t *>(stab + SHELL_NB);  // [BT_WARPS][2][TG]
     __shared__ uint4 s_item;
     __shared__ int s_last;
-    __shared__ int s_total[2];
     __shared__ float4 s_face[3];
     __shared__ unsigned long long s_cnt[3];
 
@@ -1114,7 +1120,6 @@ __device__ __forceinline__ void tiles_worker(
         const int i0 = tile_i * T, j0 = tile_j * T;
         const int rows_valid = min(T, H - i0), cols_valid = min(T, W - j0);
         for (int e = tid; e < (K + 1) * NT; e += BT_THREADS) D[e] = 0.0f;
-        if (tid == 0) s_total[0] = 0;
         for (int e = tid; e < NT; e += BT_THREADS) {
             const int i = i0 + e / T, j = j0 + e % T;
             float x, y, z;
@@ -1193,59 +1198,69 @@ __device__ __forceinline__ void tiles_worker(
         }
         const float4 *src = brec + (int64_t)l * N * REC_F4;
         const int nrec = (int)(end - start);
-        const int nchunks = (nrec + chunk - 1) / chunk;
-        // staging: entry e of a chunk = record e / REC_F4, part e % REC_F4;
-        // a thread owns e = tid, tid + BT_THREADS, tid + 2 BT_THREADS
-        uint32_t gnext[3] = {0u, 0u, 0u};
-        auto load_idx = [&](int c, uint32_t *g) {
-            const int base = (int)start + c * chunk, cnt = min(chunk, (int)end - base);
+        const int ngroups = (nrec + TG - 1) / TG;
+        // Warp w takes the record groups w, w + BT_WARPS, ... of the item (TG
+        // consecutive records each), staged in its own slice of shared memory
+        // one group ahead; it forms their candidate list in its own slice and
+        // evaluates it, with no block barrier until the item's end.  Staging:
+        // lane l copies the float4 parts e = l, l + 32 of the group (record
+        // e / REC_F4, part e % REC_F4).
+        const int warp = tid >> 5;
+        float4 *wst = stage + warp * 2 * TG * REC_F4;
+        uint8_t *wsm = smask + warp * 2 * TG;
+        uint16_t *wc = cand + warp * TG * NT;
+        auto load_idx = [&](int g, uint32_t (&gi)[2]) {
+            const int base = (int)start + g * TG, cnt = min(TG, (int)end - base);
 #pragma unroll
-            for (int hh = 0; hh < 3; ++hh) {
-                const int e = tid + hh * BT_THREADS;
-                g[hh] = e < cnt * REC_F4 ? __ldg(vals + base + e / REC_F4) : 0u;
+            for (int hh = 0; hh < 2; ++hh) {
+                const int e = lane + 32 * hh;
+                gi[hh] = e < cnt * REC_F4 ? __ldg(vals + base + e / REC_F4) : 0u;
             }
         };
-        auto issue = [&](int c, const uint32_t *g) {
-            const int base = (int)start + c * chunk, cnt = min(chunk, (int)end - base);
-            float4 *dst = stage + (c & 1) * chunk * REC_F4;
+        auto issue = [&](int g, int buf, const uint32_t (&gi)[2]) {
+            const int base = (int)start + g * TG, cnt = min(TG, (int)end - base);
+            float4 *dst = wst + buf * TG * REC_F4;
 #pragma unroll
-            for (int hh = 0; hh < 3; ++hh) {
-                const int e = tid + hh * BT_THREADS;
+            for (int hh = 0; hh < 2; ++hh) {
+                const int e = lane + 32 * hh;
                 if (e < cnt * REC_F4) {
-                    cp_async16(dst + e, src + (int64_t)(g[hh] & VAL_IDX) * REC_F4 + e % REC_F4);
-                    if (e % REC_F4 == 0) smask[(c & 1) * chunk + e / REC_F4] = (uint8_t)(g[hh] >> 30);
+                    cp_async16(dst + e, src + (int64_t)(gi[hh] & VAL_IDX) * REC_F4 + e % REC_F4);
+                    if (e % REC_F4 == 0) wsm[buf * TG + e / REC_F4] = (uint8_t)(gi[hh] >> 30);
                 }
             }
             cp_async_commit();
         };
-        if (nchunks > 0) {
-            uint32_t g0[3];
-            load_idx(0, g0);
-            issue(0, g0);
-            if (nchunks > 1) load_idx(1, gnext);
+        uint32_t gnext[2] = {0u, 0u};
+        if (warp < ngroups) {
+            uint32_t g0[2];
+            load_idx(warp, g0);
+            issue(warp, 0, g0);
+            if (warp + BT_WARPS < ngroups) load_idx(warp + BT_WARPS, gnext);
         }
-        const float4 *st = stage;
-        for (int c = 0; c < nchunks; ++c) {
-            cp_async_wait<0>();
-            // chunk c is in shared memory, and every warp is done with chunk c - 1,
-            // whose buffers chunk c + 1 now takes
-            __syncthreads();
-            if (c + 1 < nchunks) {
-                issue(c + 1, gnext);
-                if (c + 2 < nchunks) load_idx(c + 2, gnext);
+        __syncthreads();  // D, the texel directions and the tile's ray family are set
+        for (int g = warp, it = 0; g < ngroups; g += BT_WARPS, ++it) {
+            const int buf = it & 1;
+            if (g + BT_WARPS < ngroups) {
+                // the other buffer's group was consumed before the previous __syncwarp
+                issue(g + BT_WARPS, buf ^ 1, gnext);
+                if (g + 2 * BT_WARPS < ngroups) load_idx(g + 2 * BT_WARPS, gnext);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
             }
-            st = stage + (c & 1) * chunk * REC_F4;
-            const int cnt = min(chunk, (int)end - ((int)start + c * chunk));
-            // candidate list: the threads 2r and 2r + 1 of a pass write the
-            // candidates of record r in the top and bottom half of the tile, at
-            // offsets from a warp scan and one shared counter per warp
-            for (int pa = 0; pa < 2 * cnt; pa += BT_THREADS) {
+            __syncwarp();  // every lane's copies of this group are in shared memory
+            const float4 *st = wst + buf * TG * REC_F4;
+            const int cnt = min(TG, (int)end - ((int)start + g * TG));
+            // candidate list: lanes 2r and 2r + 1 write the candidates of record r
+            // in the top and bottom half of the tile at offsets from a warp scan
+            int total;
+            {
                 uint32_t iv[T / 2];
 #pragma unroll
                 for (int rr = 0; rr < T / 2; ++rr) iv[rr] = 0u;
-                const int r = (pa + tid) >> 1, h = tid & 1;
+                const int r = lane >> 1, h = lane & 1;
                 int nr = 0;
-                if (r < cnt && ((smask[(c & 1) * chunk + r] >> h) & 1u)) {
+                if (r < cnt && ((wsm[buf * TG + r] >> h) & 1u)) {
                     cand_mask<T>(st[r * REC_F4], st[r * REC_F4 + 1], st[r * REC_F4 + 2], st[r * REC_F4 + 3],
                                  h, s_face[0], s_face[1], s_face[2], rows_valid, cols_valid, iv);
 #pragma unroll
@@ -1257,28 +1272,22 @@ __device__ __forceinline__ void tiles_worker(
                     const int v = __shfl_up_sync(FULLMASK, incl, o);
                     if (lane >= o) incl += v;
                 }
-                int wbase = 0;
-                if (lane == 31 && incl > 0) wbase = atomicAdd(&s_total[c & 1], incl);
-                int pos = __shfl_sync(FULLMASK, wbase, 31) + incl - nr;
+                total = __shfl_sync(FULLMASK, incl, 31);
+                int pos = incl - nr;
 #pragma unroll
                 for (int rr = 0; rr < T / 2; ++rr) {
                     const int id0 = (r << 8) | ((h * (T / 2) + rr) * T);
-                    for (int j = (int)(iv[rr] & 255u); j < (int)(iv[rr] >> 8); ++j) cand[pos++] = (uint16_t)(id0 + j);
+                    for (int j = (int)(iv[rr] & 255u); j < (int)(iv[rr] >> 8); ++j) wc[pos++] = (uint16_t)(id0 + j);
                 }
             }
-            __syncthreads();
-            const int total = s_total[c & 1];
-            if (tid == 0) {
-                s_total[(c + 1) & 1] = 0;  // the next chunk's counter
-                n_cand += (unsigned)total;
-            }
-            // warp w takes the batches w, w + 8, ... of 32 consecutive candidates;
-            // the body is straight-line code with predicated deposits (lanes past
-            // the list's end or without a hit deposit nothing)
-            const int warp = tid >> 5;
-            for (int f0 = warp * 32; f0 < total; f0 += BT_THREADS) {
+            __syncwarp();
+            if (lane == 0) n_cand += (unsigned)total;
+            // batches of 32 consecutive candidates; the body is straight-line code
+            // with predicated deposits (lanes past the list's end or without a hit
+            // deposit nothing)
+            for (int f0 = 0; f0 < total; f0 += 32) {
                 const bool valid = f0 + lane < total;
-                const uint32_t id = valid ? cand[f0 + lane] : 0u;
+                const uint32_t id = valid ? wc[f0 + lane] : 0u;
                 const int r = (int)(id >> 8), tex = (int)(id & 255u);
                 const float4 q0 = st[r * REC_F4], q1 = st[r * REC_F4 + 1], q2 = st[r * REC_F4 + 2],
                              q3 = st[r * REC_F4 + 3];
@@ -1330,6 +1339,7 @@ __device__ __forceinline__ void tiles_worker(
                 n_shell += (unsigned)(k - k0);
                 if (hit) atomicAdd(D + k * NT + tex, fmaxf(full - F0 - Gprev, 0.0f));  // row K: unused
             }
+            __syncwarp();  // the group's records and list are no longer read
         }
         __syncthreads();
         // ---- finalize: prefix over shells, T = exp(-tau) (Eq. 4) ----

@@ -17,7 +17,7 @@ namespace {
 constexpr int SUPER = 8;       // super-tile edge, in tiles
 constexpr int REC_F4 = 4;      // float4 per build record
 constexpr int BT_THREADS = 256;
-constexpr int ITEM_CHUNKS = 8;   // a work item holds at most ITEM_CHUNKS * chunk Gaussians
+constexpr int ITEM_CHUNKS = 16;  // a work item holds at most ITEM_CHUNKS * chunk Gaussians
 #ifndef DGSM_BT_MIN_BLOCKS
 #define DGSM_BT_MIN_BLOCKS 4        // resident build blocks per SM the register budget targets
 #endif

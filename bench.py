@@ -625,7 +625,7 @@ def _profiled_pipes(kernel, workload):
         text = open(path).read()
         if f"source_sha256: {_tile_kernel_sha()}" not in text:
             return None
-        m = re.search(r"FMA ([0-9.]+)%, ALU ([0-9.]+)%, XU \(MUFU\) ([0-9.]+)%", text)
+        m = re.search(r"FMA ([0-9.]+)%, ALU ([0-9.]+)%,(?: LSU [0-9.]+%,)? XU \(MUFU\) ([0-9.]+)%", text)
         if not m:
             return None
         return {"fma": float(m.group(1)) / 100, "alu": float(m.group(2)) / 100,

@@ -151,6 +151,12 @@ __global__ void __launch_bounds__(ATT_THREADS) attenuate_kernel(
 //   ulp of it otherwise; the lookup is continuous across texel and shell
 //   boundaries, so the result moves by at most that much where the texel
 //   base would differ.
+// * Two receivers per packed operation.  A lane's receivers u = 2p, 2p + 1
+//   go through the floating-point steps as the two halves of f32x2
+//   operations (fma/add/mul.rn.f32x2, each half rounded as the scalar
+//   operation, x - o as fma(o, -1, x)), which halves the issue slots of the
+//   arithmetic; the integer decisions, the reciprocal and the taps stay per
+//   receiver.
 // The texel base and the bilinear fractions are otherwise the
 // specification's single-precision operations, as in sample_index_tab.
 constexpr int AZ_THREADS = 512;     // two blocks per SM
@@ -287,61 +293,97 @@ __global__ void __launch_bounds__(AZ_THREADS, 2) attenuate_stream_kernel(
             const T *A = atlas + (size_t)l * K * plane;
             const T *Dy = DYN ? dyn + (size_t)l * K * plane : nullptr;
             float Tl[AZ_U];
+            // receivers u = 2p, 2p + 1 as the two halves of packed f32x2
+            // operations (each half rounded as the scalar operation)
 #pragma unroll
-            for (int u = 0; u < AZ_U; ++u) {
-                const int r = u * 32 + lane;
-                const float vx = xsub(sm[3 * r], ox), vy = xsub(sm[3 * r + 1], oy), vz = xsub(sm[3 * r + 2], oz);
-                const float d2 = xadd(xadd(xmul(vx, vx), xmul(vy, vy)), xmul(vz, vz));
+            for (int p = 0; p < AZ_U / 2; ++p) {
+                const int ra = 2 * p * 32 + lane, rb = ra + 32;
+                const float2 M1 = make_float2(-1.0f, -1.0f);
+                // x - o = fma(o, -1, x), rounded once
+                const float2 vx = __ffma2_rn(make_float2(ox, ox), M1, make_float2(sm[3 * ra], sm[3 * rb]));
+                const float2 vy = __ffma2_rn(make_float2(oy, oy), M1, make_float2(sm[3 * ra + 1], sm[3 * rb + 1]));
+                const float2 vz = __ffma2_rn(make_float2(oz, oz), M1, make_float2(sm[3 * ra + 2], sm[3 * rb + 2]));
+                const float2 d2 = __fadd2_rn(__fadd2_rn(__fmul2_rn(vx, vx), __fmul2_rn(vy, vy)), __fmul2_rn(vz, vz));
                 // octahedral code (as xencode), both quotients by one rounded reciprocal
-                float2 uv = make_float2(0.0f, 0.0f);
-                {
-                    const float sabs = xadd(xadd(fabsf(vx), fabsf(vy)), fabsf(vz));
-                    if (sabs != 0.0f) {
-                        const float y = __frcp_rn(sabs);
-                        const float q0x = vx * y, q0y = vy * y;
-                        float qx = fmaf(fmaf(-sabs, q0x, vx), y, q0x);
-                        float qy = fmaf(fmaf(-sabs, q0y, vy), y, q0y);
-                        if (sabs < 1e-30f) {  // 1 / sabs near overflow: divide
-                            qx = xdiv(vx, sabs);
-                            qy = xdiv(vy, sabs);
-                        }
-                        uv = vz >= 0.0f ? make_float2(qx, qy)
-                                        : make_float2(xmul(sgn_pos(qx), xsub(1.0f, fabsf(qy))),
-                                                      xmul(sgn_pos(qy), xsub(1.0f, fabsf(qx))));
+                const float2 sab = __fadd2_rn(__fadd2_rn(make_float2(fabsf(vx.x), fabsf(vx.y)),
+                                                         make_float2(fabsf(vy.x), fabsf(vy.y))),
+                                              make_float2(fabsf(vz.x), fabsf(vz.y)));
+                const float2 y = make_float2(sab.x != 0.0f ? __frcp_rn(sab.x) : 0.0f,
+                                             sab.y != 0.0f ? __frcp_rn(sab.y) : 0.0f);
+                const float2 nsab = make_float2(-sab.x, -sab.y);
+                const float2 q0x = __fmul2_rn(vx, y), q0y = __fmul2_rn(vy, y);
+                float2 qx = __ffma2_rn(__ffma2_rn(nsab, q0x, vx), y, q0x);
+                float2 qy = __ffma2_rn(__ffma2_rn(nsab, q0y, vy), y, q0y);
+                if (sab.x < 1e-30f) {  // 1 / s near overflow (or s = 0): divide
+                    qx.x = sab.x != 0.0f ? xdiv(vx.x, sab.x) : 0.0f;
+                    qy.x = sab.x != 0.0f ? xdiv(vy.x, sab.x) : 0.0f;
+                }
+                if (sab.y < 1e-30f) {
+                    qx.y = sab.y != 0.0f ? xdiv(vx.y, sab.y) : 0.0f;
+                    qy.y = sab.y != 0.0f ? xdiv(vy.y, sab.y) : 0.0f;
+                }
+                float2 ux = qx, uy = qy;
+                if (vz.x < 0.0f && sab.x != 0.0f) {
+                    ux.x = xmul(sgn_pos(qx.x), xsub(1.0f, fabsf(qy.x)));
+                    uy.x = xmul(sgn_pos(qy.x), xsub(1.0f, fabsf(qx.x)));
+                }
+                if (vz.y < 0.0f && sab.y != 0.0f) {
+                    ux.y = xmul(sgn_pos(qx.y), xsub(1.0f, fabsf(qy.y)));
+                    uy.y = xmul(sgn_pos(qy.y), xsub(1.0f, fabsf(qx.y)));
+                }
+                const float2 ONE = make_float2(1.0f, 1.0f), HALF = make_float2(0.5f, 0.5f),
+                             NHALF = make_float2(-0.5f, -0.5f);
+                const float2 gx = __fadd2_rn(__fmul2_rn(__fmul2_rn(__fadd2_rn(ux, ONE), HALF),
+                                                        make_float2((float)W, (float)W)), NHALF);
+                const float2 gy = __fadd2_rn(__fmul2_rn(__fmul2_rn(__fadd2_rn(uy, ONE), HALF),
+                                                        make_float2((float)H, (float)H)), NHALF);
+                const float2 bjf = make_float2(floorf(gx.x), floorf(gx.y));
+                const float2 bif = make_float2(floorf(gy.x), floorf(gy.y));
+                const float2 fxr = __ffma2_rn(bjf, M1, gx), fyr = __ffma2_rn(bif, M1, gy);
+                float2 fx, fy, wt;
+                uint32_t o[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float bjh = h ? bjf.y : bjf.x, bih = h ? bif.y : bif.x;
+                    const int bj = (int)bjh, bi = (int)bih;
+                    // taps (i0, i0 + 1) x (j0, j0 + 1); an edge by its weight (0 or 1)
+                    const int j0 = min(max(bj, 0), W - 2), i0 = min(max(bi, 0), H - 2);
+                    const float fxh = bj == j0 ? (h ? fxr.y : fxr.x) : (bj < j0 ? 0.0f : 1.0f);
+                    const float fyh = bi == i0 ? (h ? fyr.y : fyr.x) : (bi < i0 ? 0.0f : 1.0f);
+                    const float d2h = h ? d2.y : d2.x;
+                    int k;  // #{r_k <= t}
+                    if (!step_more) {
+                        k = dtab[max(min((__float_as_int(d2h) - AZ_TB0) >> AZ_SHIFT, AZ_NB - 1), 0)];
+                        k += thr[k] <= d2h ? 1 : 0;
+                    } else {
+                        k = 0;
+                        while (k < K && thr[k] <= d2h) ++k;
                     }
+                    // shells (k0, k0 + 1); below the first or past the last radius by the weight
+                    const int k0 = min(max(k - 1, 0), K - 2);
+                    const float wth =
+                        k >= K ? 1.0f : fminf(fmaxf((d2h * rsqrtf(d2h) - rs[k0]) * inw[k0], 0.0f), 1.0f);
+                    if (h) { fx.y = fxh; fy.y = fyh; wt.y = wth; }
+                    else { fx.x = fxh; fy.x = fyh; wt.x = wth; }
+                    o[h] = (uint32_t)k0 * plane + (uint32_t)i0 * W + (uint32_t)j0;
                 }
-                const float gx = xsub(xmul(xmul(xadd(uv.x, 1.0f), 0.5f), (float)W), 0.5f);
-                const float gy = xsub(xmul(xmul(xadd(uv.y, 1.0f), 0.5f), (float)H), 0.5f);
-                const float bjf = floorf(gx), bif = floorf(gy);
-                const int bj = (int)bjf, bi = (int)bif;
-                // taps (i0, i0 + 1) x (j0, j0 + 1); an edge by its weight (0 or 1)
-                const int j0 = min(max(bj, 0), W - 2), i0 = min(max(bi, 0), H - 2);
-                const float fx = bj == j0 ? xsub(gx, bjf) : (bj < j0 ? 0.0f : 1.0f);
-                const float fy = bi == i0 ? xsub(gy, bif) : (bi < i0 ? 0.0f : 1.0f);
-                int k;  // #{r_k <= t}
-                if (!step_more) {
-                    k = dtab[max(min((__float_as_int(d2) - AZ_TB0) >> AZ_SHIFT, AZ_NB - 1), 0)];
-                    k += thr[k] <= d2 ? 1 : 0;
-                } else {
-                    k = 0;
-                    while (k < K && thr[k] <= d2) ++k;
-                }
-                // shells (k0, k0 + 1); below the first or past the last radius by the weight
-                const int k0 = min(max(k - 1, 0), K - 2);
-                const float wt = k >= K ? 1.0f : fminf(fmaxf((d2 * rsqrtf(d2) - rs[k0]) * inw[k0], 0.0f), 1.0f);
-                const uint32_t o = (uint32_t)k0 * plane + (uint32_t)i0 * W + (uint32_t)j0;
-                auto bil = [&](const T *p) {  // bilinear in the plane of one shell
-                    const float a00 = load_T(p), a01 = load_T(p + 1), a10 = load_T(p + W), a11 = load_T(p + W + 1);
-                    const float r0 = fmaf(fx, a01 - a00, a00), r1 = fmaf(fx, a11 - a10, a10);
-                    return fmaf(fy, r1 - r0, r0);
+                // lerp(a, b, f) = fma(f, b - a, a), both receivers at once
+                auto lerp2 = [&](float2 a, float2 b, float2 f) { return __ffma2_rn(f, __ffma2_rn(a, M1, b), a); };
+                auto bil2 = [&](const T *P0, const T *P1) {  // bilinear in the plane of one shell
+                    const float2 a00 = make_float2(load_T(P0), load_T(P1));
+                    const float2 a01 = make_float2(load_T(P0 + 1), load_T(P1 + 1));
+                    const float2 a10 = make_float2(load_T(P0 + W), load_T(P1 + W));
+                    const float2 a11 = make_float2(load_T(P0 + W + 1), load_T(P1 + W + 1));
+                    return lerp2(lerp2(a00, a01, fx), lerp2(a10, a11, fx), fy);
                 };
-                auto tri = [&](const T *P) {
-                    const float b0 = bil(P + o), b1 = bil(P + o + plane);
-                    return fmaf(wt, b1 - b0, b0);
+                auto tri2 = [&](const T *P) {
+                    const T *pa = P + o[0], *pb = P + o[1];
+                    return lerp2(bil2(pa, pb), bil2(pa + plane, pb + plane), wt);
                 };
-                float Tv = tri(A);
-                if (DYN) Tv *= tri(Dy);
-                Tl[u] = d2 != 0.0f ? Tv : 1.0f;
+                float2 Tv = tri2(A);
+                if (DYN) Tv = __fmul2_rn(Tv, tri2(Dy));
+                Tl[2 * p] = d2.x != 0.0f ? Tv.x : 1.0f;
+                Tl[2 * p + 1] = d2.y != 0.0f ? Tv.y : 1.0f;
             }
 #pragma unroll
             for (int u = 0; u < AZ_U; ++u) {
@@ -544,31 +586,43 @@ __global__ void sample_index_kernel(const float *__restrict__ pts, int64_t n,
 using namespace dgsm;
 
 namespace {
+// Resident blocks per SM of attenuate_stream_kernel<T, DYN, HAS_T> on device
+// dev (its shared-memory limit raised first), found once per kernel and device.
+template <typename T, bool DYN, bool HAS_T>
+int az_blocks_per_sm(int dev) {
+    auto kern = attenuate_stream_kernel<T, DYN, HAS_T>;
+    static int cache[64] = {};  // blocks per SM + 1 per device (0: not yet found)
+    if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev] - 1;
+    int per_sm = 1;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AZ_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, AZ_THREADS, AZ_SMEM);
+    per_sm = std::max(per_sm, 1);
+    if (dev >= 0 && dev < 64) cache[dev] = per_sm + 1;
+    return per_sm;
+}
+
 template <typename T>
 void launch_attenuate(int grid, cudaStream_t s, const void *atlas, const void *dyn, bool sep, int L,
                       int H, int W, const float *radii, int K, DynGeom dg, const float *lights,
                       const float *qm, const float *cin, int64_t Q, const float *lw, float wd,
-                      float *cout, float *Tout, bool cube, int *status) {
+                      float *cout, float *Tout, bool cube, int *status, int num_sms) {
     if (!cube && !sep && H >= 2 && W >= 2 && K >= 2) {
         // the streamed form: one resident wave of blocks
         const bool vec = ((((uintptr_t)qm) | ((uintptr_t)cin) | ((uintptr_t)cout)) & 15u) == 0;
-        auto go = [&](auto kern) {
-            int per_sm = 1, dev = 0, sms = 148;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AZ_SMEM);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, AZ_THREADS, AZ_SMEM);
+        auto go = [&](auto kern, int per_sm) {
             const int64_t need = (Q + (int64_t)AZ_R * AZ_WARPS - 1) / ((int64_t)AZ_R * AZ_WARPS);
-            const int g = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * std::max(per_sm, 1)));
+            const int g = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms * per_sm));
             kern<<<g, AZ_THREADS, AZ_SMEM, s>>>((const T *)atlas, (const T *)dyn, L, H, W, radii, K, lights, qm,
                                                 cin, Q, lw, wd, cout, Tout, vec, status);
         };
+        int dev = 0;
+        cudaGetDevice(&dev);
         if (dyn) {
-            if (Tout) go(attenuate_stream_kernel<T, true, true>);
-            else go(attenuate_stream_kernel<T, true, false>);
+            if (Tout) go(attenuate_stream_kernel<T, true, true>, az_blocks_per_sm<T, true, true>(dev));
+            else go(attenuate_stream_kernel<T, true, false>, az_blocks_per_sm<T, true, false>(dev));
         } else {
-            if (Tout) go(attenuate_stream_kernel<T, false, true>);
-            else go(attenuate_stream_kernel<T, false, false>);
+            if (Tout) go(attenuate_stream_kernel<T, false, true>, az_blocks_per_sm<T, false, true>(dev));
+            else go(attenuate_stream_kernel<T, false, false>, az_blocks_per_sm<T, false, false>(dev));
         }
         (void)grid;
         return;
@@ -613,17 +667,17 @@ int attenuate_common(dgsm_ctx *ctx, const void *atlas, const void *atlas_dyn, in
         case DGSM_F32:
             launch_attenuate<float>(grid, s, atlas, atlas_dyn, sep, L, H, W, radii, K, dg, lights, q_means,
                                     colors_in, n_q, light_w, direct_frac, colors_out, T_out, cube,
-                                    ctx->d_status);
+                                    ctx->d_status, ctx->num_sms);
             break;
         case DGSM_F16:
             launch_attenuate<__half>(grid, s, atlas, atlas_dyn, sep, L, H, W, radii, K, dg, lights, q_means,
                                      colors_in, n_q, light_w, direct_frac, colors_out, T_out, cube,
-                                    ctx->d_status);
+                                    ctx->d_status, ctx->num_sms);
             break;
         default:
             launch_attenuate<__nv_bfloat16>(grid, s, atlas, atlas_dyn, sep, L, H, W, radii, K, dg, lights,
                                             q_means, colors_in, n_q, light_w, direct_frac, colors_out, T_out,
-                                            cube, ctx->d_status);
+                                            cube, ctx->d_status, ctx->num_sms);
     }
     e = cudaGetLastError();
     return e == cudaSuccess ? DGSM_OK : cuda_fail(ctx, e, "attenuate_kernel");

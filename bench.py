@@ -363,7 +363,7 @@ def run_ours(args, rank, world, local_rank):
     del big_m, big_c
     attenuate["order"] = ("receivers stored in the z-order of their means (dgsm_spatial_order at load); "
                           "back_to_back_generated_order: the same receivers in the generator's random order")
-    attenuate["bound"] = ("issue (about 200 instructions per receiver) and L1 wavefronts; the Z-ordered atlas "
+    attenuate["bound"] = ("L1 (71% of its throughput) and issue (about 186 instructions per receiver); the Z-ordered atlas "
                           "taps hit L1 (0.9 L2 sectors per receiver); profiles/attenuate_room1p6m_x8.md")
     attenuate["footprint_mc8"] = {"ms": round(fpt, 5), "gaussians_per_s": N / (fpt * 1e-3),
                                   "achieved_gbs": round((N * 64) / (fpt * 1e-3) / 1e9, 1),

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(ATT_THREADS) attenuate_kernel(
 // specification's single-precision operations, as in sample_index_tab.
 constexpr int AZ_THREADS = 512;     // two blocks per SM
 constexpr int AZ_WARPS = AZ_THREADS / 32;
-constexpr int AZ_U = 4;             // receivers per lane per round
+constexpr int AZ_U = 6;             // receivers per lane per round
 constexpr int AZ_R = 32 * AZ_U;     // receivers per warp round
 constexpr int AZ_BYTES = AZ_R * 12; // one round of one (n, 3) float array
 constexpr int AZ_TB0 = 103 << 23;   // float bits of 2^-24 (d2 in m^2)

@@ -98,7 +98,7 @@ def test_attenuate_half_atlas(nat, orc, dtype):
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 def test_attenuate_streaming_paths_agree(nat, orc, Q, dtype):
     """The pass streams 16-byte-aligned inputs through shared memory in
-    whole rounds of 128 receivers per warp (bulk copies two stages deep; the
+    whole rounds of 192 receivers per warp (bulk copies two stages deep; the
     largest case takes several rounds per warp, so both stages and both
     phases of their barriers turn over; a last partial round reads
     directly), falls back to direct loads for a misaligned view, and may

@@ -654,6 +654,11 @@ def _measured_peak(key, fallback):
 
 
 def run_e2e(nat, wl, args, evals):
+    """The step through the public host-buffer API: every step copies its
+    inputs from pinned host memory and its colours and SH back.  Timed two
+    ways: frames submitted to the two slots of a FrameQueue in turn (frame
+    f's compute overlaps frame f + 1's copy-in and frame f - 1's copy-out;
+    the line's value), and one blocking dgsm_frame_host call per step."""
     import torch
     sc = wl["occluders"]
     pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
@@ -661,26 +666,42 @@ def run_e2e(nat, wl, args, evals):
     D, Y, w = (pin(a) for a in wl["cubemap"])
     lights, radii = pin(wl["lights"]), pin(wl["radii"])
     sl = sc.meta["avatar"]
-    cout = torch.empty((sc.n, 3), dtype=torch.float32).pin_memory()
-    shout = torch.empty((3, 9), dtype=torch.float32).pin_memory()
-    call = lambda: nat.dgsm_frame_host(h["means"], h["scales"], h["quats"], h["opac"], h["colors"],
-                                       lights, wl["H"], wl["W"], radii, D, Y, w,
-                                       relight_range=(sl.start, sl.stop), colors_out=cout,
-                                       sh_out=shout)
+    outs = [(torch.empty((sc.n, 3), dtype=torch.float32).pin_memory(),
+             torch.empty((3, 9), dtype=torch.float32).pin_memory()) for _ in range(2)]
+    args_in = (h["means"], h["scales"], h["quats"], h["opac"], h["colors"], lights, wl["H"], wl["W"], radii, D, Y, w)
+    call = lambda: nat.dgsm_frame_host(*args_in, relight_range=(sl.start, sl.stop), colors_out=outs[0][0],
+                                       sh_out=outs[0][1])
+    q = nat.FrameQueue()
+    submit = lambda f: q.submit(*args_in, relight_range=(sl.start, sl.stop), colors_out=outs[f % 2][0],
+                                sh_out=outs[f % 2][1])
+    n = max(3, min(args.steps, 20))
     for _ in range(max(1, args.warmup)):
         call()
-    n = max(3, min(args.steps, 20))
+    for f in range(2):
+        q.wait(submit(f))
+    torch.cuda.synchronize()
+    # pipelined: n frames, each submitted before the previous one is waited for
+    t0 = time.perf_counter()
+    slots = [submit(0)]
+    for f in range(1, n):
+        slots.append(submit(f))
+        q.wait(slots[f - 1])
+    q.wait(slots[-1])
+    dt = (time.perf_counter() - t0) / n
+    # blocking: one call per step
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(n):
         call()
-    dt = (time.perf_counter() - t0) / n
+    dt_block = (time.perf_counter() - t0) / n
     h2d = sum(t.numel() * 4 for t in h.values()) + (D.numel() + Y.numel() + w.numel()
                                                     + lights.numel() + radii.numel()) * 4
-    d2h = cout.numel() * 4 + shout.numel() * 4
+    d2h = outs[0][0].numel() * 4 + outs[0][1].numel() * 4
     return {"value": evals / dt, "unit": UNIT, "ms_per_step": round(dt * 1e3, 4),
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "api": "dgsm_frame_host (host buffers, pinned)"}
+            "api": "FrameQueue (dgsm_frame_host_submit / _wait, two slots; host buffers, pinned)",
+            "blocking": {"value": evals / dt_block, "ms_per_step": round(dt_block * 1e3, 4),
+                         "api": "dgsm_frame_host (one blocking call per step)"}}
 
 
 # ----------------------------------------------------------------------------- oracle

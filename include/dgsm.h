@@ -662,6 +662,30 @@ int dgsm_frame_host(dgsm_ctx *ctx, const dgsm_frame_host_in *in, const dgsm_para
                     const dgsm_relight_params *rparams, float *colors_out, float *sh_out,
                     void *stream);
 
+/* dgsm_frame_host's frame, pipelined: submit returns once the frame is
+ * enqueued (the build may block the host briefly to read its pair counts
+ * when params->max_pairs is 0), so that a caller submitting frames to the two
+ * slots in turn overlaps frame f's compute with the copy-in of frame f + 1
+ * and the copy-out of frame f - 1.  The inputs go up on two copy streams of
+ * the context at once; the compute runs on `stream` after everything
+ * submitted there before (frames compute in submission order); the colours
+ * come back on a copy-out stream.  Each slot (0 or 1) holds its own device
+ * copies of the inputs, the atlas and the colours (context workspace); the
+ * host arrays of `in`, colors_out and sh_out (pinned memory makes the copies
+ * asynchronous) must stay valid and unchanged until dgsm_frame_host_wait on
+ * the slot returns.  Submitting to a slot whose frame is in flight waits for
+ * it first.  Returns DGSM_OK, DGSM_ERR_INVALID_ARG, DGSM_ERR_WORKSPACE or
+ * DGSM_ERR_CUDA (enqueue errors); kernel errors of the frame come from the
+ * wait. */
+int dgsm_frame_host_submit(dgsm_ctx *ctx, int slot, const dgsm_frame_host_in *in, const dgsm_params *params,
+                           const dgsm_relight_params *rparams, float *colors_out, float *sh_out,
+                           void *stream);
+
+/* Blocks until the slot's frame is complete (its colours and SH in host
+ * memory) and returns the status its kernels recorded (DGSM_OK, or the
+ * first error code); DGSM_OK at once for a slot with no frame in flight. */
+int dgsm_frame_host_wait(dgsm_ctx *ctx, int slot);
+
 /* Phase timing of dgsm_build.  While enabled, each dgsm_build records three
  * CUDA events on its stream (start; before the tile kernel; after it) for
  * up to 256 builds.  dgsm_profile_collect blocks until they complete and

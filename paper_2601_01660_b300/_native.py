@@ -149,6 +149,9 @@ _lib.dgsm_selftest_wait.argtypes = [_vp, _i32, _i64, _vp]
 _lib.dgsm_weighted_centroid.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp]
 _lib.dgsm_frame_host.argtypes = [_vp, C.POINTER(FrameHostIn), C.POINTER(Params),
                                  C.POINTER(RelightParams), _vp, _vp, _vp]
+_lib.dgsm_frame_host_submit.argtypes = [_vp, _i32, C.POINTER(FrameHostIn), C.POINTER(Params),
+                                       C.POINTER(RelightParams), _vp, _vp, _vp]
+_lib.dgsm_frame_host_wait.argtypes = [_vp, _i32]
 _lib.nf_param_count.restype = C.c_int64
 _lib.nf_param_count.argtypes = []
 _lib.nf_init.argtypes = [_vp, C.c_uint64, _vp, _vp]
@@ -185,7 +188,8 @@ for _fn in ("dgsm_build", "dgsm_get_build_stats", "dgsm_bin", "dgsm_attenuate",
             "nf_tile_error", "nf_attenuate", "sh_relight_objects", "dgsm_segment_centroids",
             "dgsm_rigid_transform", "dgsm_graph_begin", "dgsm_graph_end", "dgsm_graph_launch",
             "dgsm_graph_node_count", "dgsm_autotune_build", "dgsm_attenuate_dyn",
-            "dgsm_measure_alu_peaks"):
+            "dgsm_measure_alu_peaks", "dgsm_frame_host_submit", "dgsm_frame_host_wait",
+            "dgsm_spatial_order", "dgsm_gather_rows"):
     getattr(_lib, _fn).restype = C.c_int
 
 
@@ -927,6 +931,48 @@ def dgsm_frame_host(means, scales, quats, opac, colors, lights, H, W, radii, cub
                                    C.c_void_p(colors_out.data_ptr()), C.c_void_p(sh_out.data_ptr()),
                                    _stream(stream)))
     return colors_out, sh_out
+
+
+class FrameQueue:
+    """Pipelined host frames (dgsm_frame_host_submit / _wait) over two slots.
+
+    submit(...) takes dgsm_frame_host's arguments and returns the slot; the
+    host arrays and the outputs (pinned) must stay alive until wait(slot)."""
+
+    def __init__(self, ctx: Context | None = None, stream=None):
+        self.ctx, self.stream, self.next_slot = ctx or context(), stream, 0
+        self._keep = [None, None]
+
+    def submit(self, means, scales, quats, opac, colors, lights, H, W, radii, cube_dirs, cube_rgb, cube_w,
+               relight_range=(0, 0), lam=1e-3, params=None, rparams=None, colors_out=None, sh_out=None):
+        ts = dict(means=means, scales=scales, quats=quats, opac=opac, colors=colors, lights=lights,
+                  radii=radii, cube_dirs=cube_dirs, cube_rgb=cube_rgb, cube_w=cube_w)
+        for k, t in ts.items():
+            _host(t, k)
+        n = means.shape[0]
+        if colors_out is None:
+            colors_out = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+        if sh_out is None:
+            sh_out = torch.empty((3, 9), dtype=torch.float32).pin_memory()
+        fi = FrameHostIn(*(ts[k].data_ptr() for k in ("means", "scales", "quats", "opac", "colors")),
+                         n, int(relight_range[0]), int(relight_range[1]), lights.data_ptr(),
+                         lights.shape[0], H, W, radii.shape[0], radii.data_ptr(), cube_dirs.data_ptr(),
+                         cube_rgb.data_ptr(), cube_w.data_ptr(), cube_dirs.shape[0], float(lam))
+        p = params if isinstance(params, Params) else Params.make(**(params or {}))
+        rp = rparams if isinstance(rparams, RelightParams) else RelightParams.make(**(rparams or {}))
+        slot = self.next_slot
+        self.ctx.check(_lib.dgsm_frame_host_submit(self.ctx.handle, slot, C.byref(fi), C.byref(p), C.byref(rp),
+                                                   C.c_void_p(colors_out.data_ptr()),
+                                                   C.c_void_p(sh_out.data_ptr()), _stream(self.stream)))
+        self._keep[slot] = (ts, colors_out, sh_out)
+        self.next_slot = 1 - slot
+        return slot
+
+    def wait(self, slot):
+        """The slot's (colors_out, sh_out) once its frame is complete."""
+        self.ctx.check(_lib.dgsm_frame_host_wait(self.ctx.handle, slot))
+        keep, self._keep[slot] = self._keep[slot], None
+        return (keep[1], keep[2]) if keep else (None, None)
 
 
 def dgsm_set_profiling(enable: bool, ctx: Context | None = None):

@@ -114,6 +114,13 @@ extern "C" void dgsm_destroy(dgsm_ctx *ctx) {
     for (int k = 0; k < 4; ++k)
         if (ctx->fev[k]) cudaEventDestroy(ctx->fev[k]);
     if (ctx->side) cudaStreamDestroy(ctx->side);
+    for (int q = 0; q < 2; ++q) {
+        for (int k = 0; k < 6; ++k)
+            if (ctx->fq_ev[q][k]) cudaEventDestroy(ctx->fq_ev[q][k]);
+        if (ctx->fq_h2d[q]) cudaStreamDestroy(ctx->fq_h2d[q]);
+    }
+    if (ctx->fq_d2h) cudaStreamDestroy(ctx->fq_d2h);
+    if (ctx->fq_status) cudaFreeHost(ctx->fq_status);
     delete ctx;
 }
 

@@ -46,6 +46,7 @@ enum WsSlot {
     WS_SMASK,          // build: per (light, Gaussian) mask of the super-tiles it reaches
     WS_KCNT,           // build: per (light, super-tile) pair counts and cursors
     WS_ORDER,          // spatial order: Z-order keys and indices, the bounding box
+    WS_FQ0, WS_FQ1,    // pipelined host frames: each slot's device copies of its frame
     WS_NSLOTS
 };
 
@@ -71,6 +72,13 @@ struct dgsm_ctx {
     // side stream and events of dgsm_frame_host (copies beside compute)
     cudaStream_t side = nullptr;
     cudaEvent_t fev[4] = {};
+    // pipelined host frames (dgsm_frame_host_submit / _wait): two copy-in
+    // streams, one copy-out stream, per slot six events, a pinned status word
+    // and whether a frame is in flight
+    cudaStream_t fq_h2d[2] = {}, fq_d2h = nullptr;
+    cudaEvent_t fq_ev[2][6] = {};
+    int *fq_status = nullptr;
+    bool fq_busy[2] = {};
     // tile cones of the persistent frame kernel: valid for this buffer and atlas size
     void *pf_cones = nullptr;
     int pf_cones_h = 0, pf_cones_w = 0;

@@ -234,3 +234,138 @@ extern "C" int dgsm_frame_host(dgsm_ctx *ctx, const dgsm_frame_host_in *in,
     if (e != cudaSuccess) return cuda_fail(ctx, e, "frame: synchronize");
     return dgsm_sync_status(ctx, stream);
 }
+
+// ---- pipelined host frames -------------------------------------------------
+//
+// dgsm_frame_host's work split so that frames overlap: a frame's inputs go
+// up on the context's two copy-in streams (the two copy engines) as soon as it
+// is submitted, its compute runs on the caller's stream after the frames
+// submitted before it, and its colours come back on a copy-out stream.  While
+// frame f computes, frame f + 1's inputs are copied in and frame f - 1's
+// colours copied out.  Each of the two slots has its own device copies of the
+// inputs, the atlas and the colours; the build's working buffers are the
+// context's, which the caller's stream orders.
+
+extern "C" int dgsm_frame_host_wait(dgsm_ctx *ctx, int slot) {
+    if (!ctx || slot < 0 || slot > 1) return DGSM_ERR_INVALID_ARG;
+    if (!ctx->fq_busy[slot]) return DGSM_OK;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ctx->fq_ev[slot][5]);
+    ctx->fq_busy[slot] = false;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "frame wait: synchronize");
+    const int st = ctx->fq_status[slot];
+    return st == DGSM_OK ? DGSM_OK : fail(ctx, st, "frame wait: a kernel of the frame reported an error");
+}
+
+extern "C" int dgsm_frame_host_submit(dgsm_ctx *ctx, int slot, const dgsm_frame_host_in *in,
+                                      const dgsm_params *params, const dgsm_relight_params *rparams,
+                                      float *colors_out, float *sh_out, void *stream) {
+    DGSM_RANGE("dgsm_frame_host_submit");
+    if (!ctx) return DGSM_ERR_INVALID_ARG;
+    if (slot < 0 || slot > 1) return fail(ctx, DGSM_ERR_INVALID_ARG, "frame submit: slot must be 0 or 1");
+    if (!in || !colors_out) return fail(ctx, DGSM_ERR_INVALID_ARG, "frame submit: null input or output");
+    const int64_t n = in->n;
+    if (n < 0 || in->relight_begin < 0 || in->relight_end < in->relight_begin || in->relight_end > n)
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "frame submit: bad Gaussian count or relight range");
+    if (n > 0 && (!in->means || !in->scales || !in->quats || !in->opac || !in->colors))
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "frame submit: null Gaussian array");
+    if (!in->lights || in->n_lights < 1 || in->n_lights > 64 || !in->radii || in->K < 1 || in->K > 256)
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "frame submit: bad lights or radii");
+    if (in->n_cube < 1 || !in->cube_dirs || !in->cube_rgb || !in->cube_w)
+        return fail(ctx, DGSM_ERR_INVALID_ARG, "frame submit: need cubemap samples");
+    dgsm_params p;
+    if (params) p = *params; else dgsm_default_params(&p);
+    const int L = in->n_lights, K = in->K, H = in->H, W = in->W;
+    if (H < 1 || W < 1 || H > 4096 || W > 4096) return fail(ctx, DGSM_ERR_INVALID_ARG, "frame submit: bad H, W");
+    // the slot's previous frame still reads its buffers: finish it first
+    int rc = dgsm_frame_host_wait(ctx, slot);
+    if (rc) return rc;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    if (!ctx->fq_d2h) {
+        for (int q = 0; e == cudaSuccess && q < 2; ++q)
+            e = cudaStreamCreateWithFlags(&ctx->fq_h2d[q], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->fq_d2h, cudaStreamNonBlocking);
+        for (int q = 0; q < 2; ++q)
+            for (int k = 0; e == cudaSuccess && k < 6; ++k)
+                e = cudaEventCreateWithFlags(&ctx->fq_ev[q][k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocHost(&ctx->fq_status, 2 * sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "frame submit: streams");
+    }
+    const size_t esz = p.atlas_dtype == DGSM_F32 ? 4 : 2;
+    const size_t sz_means = align256(12 * (size_t)n), sz_q = align256(16 * (size_t)n),
+                 sz_op = align256(4 * (size_t)n), sz_l = align256(12 * (size_t)L),
+                 sz_r = align256(4 * (size_t)K), sz_cube3 = align256(12 * (size_t)in->n_cube),
+                 sz_cube1 = align256(4 * (size_t)in->n_cube),
+                 sz_atlas = align256(esz * (size_t)L * K * H * W), sz_small = 256;
+    const size_t total = 4 * sz_means + sz_q + sz_op + sz_l + sz_r + 2 * sz_cube3 + sz_cube1 +
+                         sz_atlas + 2 * sz_small;
+    void *base;
+    if ((rc = ws_reserve(ctx, slot ? WS_FQ1 : WS_FQ0, total, &base))) return rc;
+    char *c = (char *)base;
+    auto take = [&](size_t bytes) { char *r = c; c += bytes; return r; };
+    float *d_means = (float *)take(sz_means), *d_scales = (float *)take(sz_means);
+    float *d_colors = (float *)take(sz_means), *d_out = (float *)take(sz_means);
+    float *d_quats = (float *)take(sz_q), *d_opac = (float *)take(sz_op);
+    float *d_lights = (float *)take(sz_l), *d_radii = (float *)take(sz_r);
+    float *d_cd = (float *)take(sz_cube3), *d_cr = (float *)take(sz_cube3);
+    float *d_cw = (float *)take(sz_cube1);
+    void *d_atlas = take(sz_atlas);
+    float *d_sh = (float *)take(sz_small), *d_cen = (float *)take(sz_small);
+
+    const cudaStream_t s = (cudaStream_t)stream, ca = ctx->fq_h2d[0], cb = ctx->fq_h2d[1], cd = ctx->fq_d2h;
+    cudaEvent_t *ev = ctx->fq_ev[slot];  // inputs a, inputs b, colours and cubemap, attenuated, relit, done
+    auto h2d = [&](void *dst, const void *src, size_t bytes, cudaStream_t st) {
+        return bytes == 0 ? cudaSuccess : cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    // copy in at once: nothing reads this slot's buffers any more
+    e = h2d(d_means, in->means, 12 * (size_t)n, ca);
+    if (e == cudaSuccess) e = h2d(d_quats, in->quats, 16 * (size_t)n, cb);
+    if (e == cudaSuccess) e = h2d(d_scales, in->scales, 12 * (size_t)n, ca);
+    if (e == cudaSuccess) e = h2d(d_opac, in->opac, 4 * (size_t)n, cb);
+    if (e == cudaSuccess) e = h2d(d_lights, in->lights, 12 * (size_t)L, ca);
+    if (e == cudaSuccess) e = h2d(d_radii, in->radii, 4 * (size_t)K, ca);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], ca);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], cb);
+    if (e == cudaSuccess) e = h2d(d_colors, in->colors, 12 * (size_t)n, cb);
+    if (e == cudaSuccess) e = h2d(d_cd, in->cube_dirs, 12 * (size_t)in->n_cube, cb);
+    if (e == cudaSuccess) e = h2d(d_cr, in->cube_rgb, 12 * (size_t)in->n_cube, cb);
+    if (e == cudaSuccess) e = h2d(d_cw, in->cube_w, 4 * (size_t)in->n_cube, cb);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], cb);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[0], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "frame submit: host to device copy");
+    if ((rc = dgsm_build(ctx, d_means, d_scales, d_quats, d_opac, n, d_lights, L, H, W, d_radii, K, &p, d_atlas, s)))
+        return rc;
+    if ((e = cudaStreamWaitEvent(s, ev[2], 0)) != cudaSuccess) return cuda_fail(ctx, e, "frame submit: wait");
+    if ((rc = sh_fit(ctx, d_cd, d_cr, d_cw, in->n_cube, in->lambda, d_sh, nullptr, s))) return rc;
+    if ((rc = dgsm_attenuate(ctx, d_atlas, nullptr, p.atlas_dtype, L, H, W, d_radii, K, d_lights, d_means,
+                             d_colors, n, nullptr, 1.0f, d_out, nullptr, s)))
+        return rc;
+    const int64_t a0 = in->relight_begin, a1 = in->relight_end, na = a1 - a0;
+    // the colours outside the relit range go out while the range is relit
+    e = cudaEventRecord(ev[3], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cd, ev[3], 0);
+    if (e == cudaSuccess && a0 > 0) e = cudaMemcpyAsync(colors_out, d_out, 12 * (size_t)a0, cudaMemcpyDeviceToHost, cd);
+    if (e == cudaSuccess && a1 < n)
+        e = cudaMemcpyAsync(colors_out + 3 * a1, d_out + 3 * a1, 12 * (size_t)(n - a1), cudaMemcpyDeviceToHost, cd);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "frame submit: device to host copy");
+    if (na > 0) {
+        if ((rc = dgsm_weighted_centroid(ctx, d_means + 3 * a0, d_opac + a0, na, d_cen, s))) return rc;
+        if ((rc = sh_relight(ctx, d_sh, d_means + 3 * a0, d_quats + 4 * a0, d_scales + 3 * a0, nullptr, d_cen,
+                             d_out + 3 * a0, na, rparams, d_out + 3 * a0, s)))
+            return rc;
+    }
+    // this frame's status word, then the word cleared for the next frame
+    e = cudaMemcpyAsync(ctx->fq_status + slot, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cd, ev[4], 0);
+    if (e == cudaSuccess && na > 0)
+        e = cudaMemcpyAsync(colors_out + 3 * a0, d_out + 3 * a0, 12 * (size_t)na, cudaMemcpyDeviceToHost, cd);
+    if (e == cudaSuccess && sh_out) e = cudaMemcpyAsync(sh_out, d_sh, 27 * sizeof(float), cudaMemcpyDeviceToHost, cd);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[5], cd);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "frame submit: device to host copy");
+    ctx->fq_busy[slot] = true;
+    return DGSM_OK;
+}

@@ -229,3 +229,33 @@ def test_frame_host_matches_device_calls(nat, orc):
     np.testing.assert_allclose(sh.numpy(), s2.cpu().numpy(), rtol=1e-6, atol=1e-7)
     cen_ref = (sc.means[a0:a1].astype(np.float64) * sc.opac[a0:a1, None]).sum(0) / sc.opac[a0:a1].sum()
     np.testing.assert_allclose(cen.cpu().numpy(), cen_ref, rtol=1e-6, atol=1e-6)
+
+
+def test_pipelined_frames_match_frame_host(nat):
+    """Frames submitted to the two slots in turn (copy-in of the next frame
+    during the current one's compute) give each frame's dgsm_frame_host
+    result, in the right output buffers; waiting on an idle slot is a no-op."""
+    import torch
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+    lights = pin(np.float32([[0, 0, 0], [0.5, 0.2, 1.0]]))
+    radii = pin(scenes.radii_geometric(0.05, 9, 12))
+    D, Y, w = (pin(a) for a in scenes.cubemap_samples(16, seed=5))
+    frames = []
+    for f in range(5):
+        sc = scenes.cube_scene(6000 + 37 * f, seed=20 + f)
+        frames.append(tuple(pin(getattr(sc, k)) for k in ("means", "scales", "quats", "opac", "colors")))
+    ranges = [(4000, 6000), (0, 0), (100, 5000), (0, 6111), (2, 3)]
+    ref = [nat.dgsm_frame_host(*fr, lights, 32, 40, radii, D, Y, w, relight_range=rg)
+           for fr, rg in zip(frames, ranges)]
+    q = nat.FrameQueue()
+    assert q.wait(0) == (None, None)
+    slots, got = [], [None] * 5
+    for f in range(5):
+        slots.append(q.submit(*frames[f], lights, 32, 40, radii, D, Y, w, relight_range=ranges[f]))
+        if f >= 1:
+            got[f - 1] = q.wait(slots[f - 1])
+    got[4] = q.wait(slots[4])
+    assert slots == [0, 1, 0, 1, 0]
+    for f in range(5):
+        np.testing.assert_allclose(got[f][0].numpy(), ref[f][0].numpy(), rtol=2e-5, atol=2e-6)
+        np.testing.assert_allclose(got[f][1].numpy(), ref[f][1].numpy(), rtol=1e-6, atol=1e-7)

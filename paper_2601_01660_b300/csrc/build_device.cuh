@@ -1285,9 +1285,12 @@ __device__ __forceinline__ void tiles_worker(
             // batches of 32 consecutive candidates; the body is straight-line code
             // with predicated deposits (lanes past the list's end or without a hit
             // deposit nothing)
+            // each batch's candidate ids are read one batch ahead
+            uint32_t id_next = lane < total ? wc[lane] : 0u;
             for (int f0 = 0; f0 < total; f0 += 32) {
                 const bool valid = f0 + lane < total;
-                const uint32_t id = valid ? wc[f0 + lane] : 0u;
+                const uint32_t id = id_next;
+                id_next = f0 + 32 + lane < total ? wc[f0 + 32 + lane] : 0u;
                 const int r = (int)(id >> 8), tex = (int)(id & 255u);
                 const float4 q0 = st[r * REC_F4], q1 = st[r * REC_F4 + 1], q2 = st[r * REC_F4 + 2],
                              q3 = st[r * REC_F4 + 3];

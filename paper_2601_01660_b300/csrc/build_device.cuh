@@ -1328,16 +1328,20 @@ __device__ __forceinline__ void tiles_worker(
                 if (__any_sync(FULLMASK, inside)) F0 = inside ? mass_below(-hs, A0, hm2, full) : 0.0f;
                 const int k0 = k;
                 float Gprev = 0.0f;
-                // shells on the chord (most hits have none or one)
-                bool more = hit && rs[k] <= hi;
+                // shells on the chord (most hits have none or one); rk = r_k is
+                // carried in a register (the deposits may alias the radii for
+                // the compiler, which would otherwise load it twice a pass)
+                float rk = rs[k];
+                bool more = hit && rk <= hi;
                 while (__any_sync(FULLMASK, more)) {
-                    const float G = mass_below(fmaf(hh, rs[k], -hs), A0, hm2, full) - F0;
+                    const float G = mass_below(fmaf(hh, rk, -hs), A0, hm2, full) - F0;
                     if (more) {
                         atomicAdd(D + k * NT + tex, fmaxf(G - Gprev, 0.0f));
                         Gprev = fmaxf(G, Gprev);
                         ++k;
+                        rk = rs[k];
                     }
-                    more = more && rs[k] <= hi;
+                    more = more && rk <= hi;
                 }
                 n_shell += (unsigned)(k - k0);
                 if (hit) atomicAdd(D + k * NT + tex, fmaxf(full - F0 - Gprev, 0.0f));  // row K: unused

@@ -965,9 +965,10 @@ size_t build_smem_bytes(int K, int tile, int chunk) {
     return (size_t)BT_WARPS * 2 * TG * REC_F4 * sizeof(float4) +  // per warp: two staged record groups
            (size_t)nt * sizeof(float4) +                           // texel directions
            (size_t)(K + 1) * nt * sizeof(float) +                  // per-shell increments (+ a row past the last)
-           (size_t)((K + 4) & ~3) * sizeof(float) +                // radii and a +inf sentinel
+           (size_t)((K + 5) & ~3) * sizeof(float) +                // radii, a +inf sentinel and one more
            (size_t)BT_WARPS * TG * nt * sizeof(uint16_t) +         // per warp: the group's candidate list
            (size_t)SHELL_NB * sizeof(uint16_t) +                   // shell table
+           (size_t)SHELL_NB * sizeof(float2) +                     // its first two radii
            (size_t)BT_WARPS * 2 * TG;                              // per warp: half-tile masks
 }
 
@@ -1073,9 +1074,10 @@ __device__ __forceinline__ void tiles_worker(
     float4 *tdir = stage + BT_WARPS * 2 * TG * REC_F4;        // [NT] (dir, valid)
     float *D = reinterpret_cast<float *>(tdir + NT);          // [K + 1][NT]: row K takes mass past the last shell
     float *rs = D + (K + 1) * NT;                             // [K + 1]: the radii, then +inf
-    uint16_t *cand = reinterpret_cast<uint16_t *>(rs + ((K + 4) & ~3));  // [BT_WARPS][TG * NT]
+    uint16_t *cand = reinterpret_cast<uint16_t *>(rs + ((K + 5) & ~3));  // [BT_WARPS][TG * NT]
     uint16_t *stab = cand + BT_WARPS * TG * NT;               // [SHELL_NB]
-    uint8_t *smask = reinterpret_cast<uint8_t *>(stab + SHELL_NB);  // [BT_WARPS][2][TG]
+    float2 *stabr = reinterpret_cast<float2 *>(stab + SHELL_NB);    // [SHELL_NB] (r_c, r_c+1), c = stab[b]
+    uint8_t *smask = reinterpret_cast<uint8_t *>(stabr + SHELL_NB);  // [BT_WARPS][2][TG]
     __shared__ uint4 s_item;
     __shared__ int s_last;
     __shared__ float4 s_face[3];
@@ -1085,7 +1087,7 @@ __device__ __forceinline__ void tiles_worker(
     const int64_t HW = (int64_t)H * W;
     const unsigned long long total_items = *n_items_total;
     for (int k = tid; k < K; k += BT_THREADS) rs[k] = radii[k];
-    if (tid == 0) rs[K] = __int_as_float(0x7f800000);  // no shell past the last
+    if (tid == 0) rs[K] = rs[K + 1] = __int_as_float(0x7f800000);  // no shell past the last
     if (tid < 3) s_cnt[tid] = 0ull;
     __syncthreads();
     // stab[b] = #{k : r_k < t_b}, t_b the float with bits SHELL_TB0 + (b << 19)
@@ -1094,6 +1096,7 @@ __device__ __forceinline__ void tiles_worker(
         int c = 0;
         while (c < K && rs[c] < tb) ++c;
         stab[b] = (uint16_t)c;
+        stabr[b] = make_float2(rs[c], rs[c + 1]);
     }
     // a bucket holds several radii (radii closer than 1/16 octave, or outside
     // the table's range): the shell search then counts the radii one by one
@@ -1311,13 +1314,21 @@ __device__ __forceinline__ void tiles_worker(
                 const float lo = ss - half, hi = ss + half;
                 // first shell at or past the chord's start: the table's bucket holds
                 // at most one radius (else step_more is set and the radii are counted)
+                // (the bucket's first two radii come from a table beside it, read
+                // together with it; rk = r_k is carried into the shell loop)
                 int k;
+                float rk;
                 if (!step_more) {
-                    k = stab[max(min((__float_as_int(lo) - SHELL_TB0) >> 19, SHELL_NB - 1), 0)];
-                    k += rs[k] < lo ? 1 : 0;
+                    const int bk = max(min((__float_as_int(lo) - SHELL_TB0) >> 19, SHELL_NB - 1), 0);
+                    k = stab[bk];
+                    const float2 rab = stabr[bk];
+                    const float ra = rab.x, rb = rab.y;
+                    rk = ra < lo ? rb : ra;
+                    k += ra < lo ? 1 : 0;
                 } else {
                     k = 0;
                     while (k < K && rs[k] < lo) ++k;
+                    rk = rs[k];
                 }
                 const float A0 = q3.x * rsa;                  // beta sqrt(pi/(2a))
                 const float hh = g.a * rsa * 0.70710678118f;  // sqrt(a/2)
@@ -1331,7 +1342,6 @@ __device__ __forceinline__ void tiles_worker(
                 // shells on the chord (most hits have none or one); rk = r_k is
                 // carried in a register (the deposits may alias the radii for
                 // the compiler, which would otherwise load it twice a pass)
-                float rk = rs[k];
                 bool more = hit && rk <= hi;
                 while (__any_sync(FULLMASK, more)) {
                     const float G = mass_below(fmaf(hh, rk, -hs), A0, hm2, full) - F0;

@@ -6,10 +6,15 @@ avatars whose atlases are rebuilt every frame:
   1. rigid motion of every avatar to this frame's pose (dgsm_rigid_transform);
   2. the avatars' dynamic atlases for all lights in one build
      (dgsm_build with max_pairs, so that nothing waits on the host);
-  3. attenuation of every Gaussian, static and avatar, by
-     T_static * T_dynamic (dgsm_attenuate_dyn; Sec. 3.3);
-  4. per-avatar alpha-weighted centroids and the SH relight of the avatars
-     (dgsm_segment_centroids, sh_relight_objects; Sec. 3.5).
+  3. per-avatar alpha-weighted centroids and the SH relight of the avatars
+     (dgsm_segment_centroids, sh_relight_objects; Sec. 3.5), on a side
+     stream beside step 2, which they do not need;
+  4. attenuation of every Gaussian, static and avatar (relit), by
+     T_static * T_dynamic (dgsm_attenuate_dyn; Sec. 3.3).
+
+The relight and the attenuation each scale a Gaussian's colour by a
+non-negative factor (Eq. 10's max(0, gamma c s); 1 - w_d + w_d sum_l w_l T_l),
+so relighting first gives the same colours as relighting the attenuated ones.
 
 With persistent=True the four steps run as ONE persistent cooperative
 kernel (dgsm_crowd_frame: grid-wide barriers between the steps instead of
@@ -41,6 +46,7 @@ class CrowdFrame:
         self.device = torch.device(device)
         self.ctx = ctx or nat.Context(self.device.index or 0)
         self.stream = torch.cuda.Stream(device=self.device)
+        self.side = torch.cuda.Stream(device=self.device)  # the relight, beside the dynamic build
         self.seg = [int(x) for x in seg]
         self.n_static, self.n_dyn = static.n, avatars.n
         self.H, self.W, self.H_dyn, self.W_dyn = H, W, H_dyn, W_dyn
@@ -52,6 +58,7 @@ class CrowdFrame:
         self.q_means = torch.empty((n, 3), dtype=torch.float32, device=dv)
         self.q_means[: self.n_static] = _dev(static.means, dv)
         self.colors_in = _dev(np.concatenate([static.colors, avatars.colors]), dv)
+        self.colors_mid = self.colors_in.clone()  # the attenuation's input: avatar rows relit per frame
         self.colors_out = torch.empty_like(self.colors_in)
         self.av_means = self.q_means[self.n_static:]
         self.rest_means = _dev(avatars.means, dv)
@@ -94,16 +101,20 @@ class CrowdFrame:
             return
         nat.dgsm_rigid_transform(self.rest_means, self.rest_quats, self.seg, poses,
                                  means_out=self.av_means, quats_out=self.av_quats, ctx=ctx, stream=s)
+        side = self.side
+        side.wait_stream(s)  # the moved avatars
+        nat.dgsm_segment_centroids(self.av_means, self.av_opac, self.seg, out=self.centroids, ctx=ctx,
+                                   stream=side)
+        av_mid = self.colors_mid[self.n_static:]
+        nat.sh_relight_objects(self.sh, self.av_means, self.av_quats, self.av_scales,
+                               self.colors_in[self.n_static:], self.centroids, self.seg, params=self.rp,
+                               out=av_mid, ctx=ctx, stream=side)
         nat.dgsm_build(self.av_means, self.av_scales, self.av_quats, self.av_opac, self.lights,
                        self.H_dyn, self.W_dyn, self.radii_dyn, params=dict(self.bp, max_pairs=max_pairs),
                        out=self.dyn_atlas, ctx=ctx, stream=s)
+        s.wait_stream(side)
         nat.dgsm_attenuate_dyn(self.static_atlas, self.radii, self.dyn_atlas, self.radii_dyn, self.lights,
-                               self.q_means, self.colors_in, out=self.colors_out, ctx=ctx, stream=s)
-        nat.dgsm_segment_centroids(self.av_means, self.av_opac, self.seg, out=self.centroids, ctx=ctx,
-                                   stream=s)
-        av_out = self.colors_out[self.n_static:]
-        nat.sh_relight_objects(self.sh, self.av_means, self.av_quats, self.av_scales, av_out,
-                               self.centroids, self.seg, params=self.rp, out=av_out, ctx=ctx, stream=s)
+                               self.q_means, self.colors_mid, out=self.colors_out, ctx=ctx, stream=s)
 
     def _write_poses(self, poses):
         """This frame's pinned pose buffer, filled once the frame that last

@@ -143,3 +143,34 @@ def test_relight_is_scaled_colour(orc):
         n = orc.gauss_normal(sc.means[g], sc.scales[g], sc.quats[g], cen)
         s = orc.transfer_scale(sh, n)
         np.testing.assert_allclose(out[g], np.maximum(0, 0.8 * sc.colors[g].astype(np.float64) * s), rtol=1e-12)
+
+
+def test_relight_and_attenuation_commute(orc):
+    """Relighting (Eq. 10: max(0, gamma c s), s clipped to [0, t_max]) and
+    the attenuation (Sec. 3.3: c (1 - w_d + w_d sum_l w_l T_l)) each scale a
+    Gaussian's colour by a factor that is non-negative and does not depend on
+    the colour, so their order does not change the result.  The batched frame
+    relies on this: it relights the avatars from their input colours beside
+    the dynamic build and attenuates the relit colours afterwards."""
+    rng = np.random.default_rng(11)
+    occ = scenes.cube_scene(400, seed=12)
+    recv = scenes.cube_scene(300, seed=13)
+    lights = np.float32([[0, 0, 0], [0.6, -0.4, 0.8]])
+    radii = scenes.radii_linear(0.1, 8, 8)
+    atlas = orc.build_atlas(occ, lights, 16, 24, radii)
+    sh = rng.normal(scale=0.3, size=(3, 9))
+    sh[:, 0] = 2.0
+    cen = recv.means.mean(0)
+    lw, wd = np.float32([0.7, 0.3]), 0.85
+    # attenuate, then relight
+    att = orc.attenuate(atlas, radii, lights, recv.means, recv.colors, light_w=lw, direct_frac=wd)
+    first_att = orc.relight(sh, scenes.Scene(recv.means, recv.scales, recv.quats, recv.opac, np.float32(att)),
+                            cen, gamma=0.8, t_max=1.5)
+    # relight, then attenuate
+    rel = orc.relight(sh, recv, cen, gamma=0.8, t_max=1.5)
+    first_rel = orc.attenuate(atlas, radii, lights, recv.means, np.float32(rel), light_w=lw, direct_frac=wd)
+    # the attenuation is not trivial: some receivers are in shadow
+    f = att / np.maximum(recv.colors.astype(np.float64), 1e-12)
+    assert f.min() < 0.9 and f.max() <= 1.0 + 1e-12
+    # equal up to the float32 rounding of the intermediate colours
+    np.testing.assert_allclose(first_rel, first_att, rtol=2e-7, atol=1e-12)

@@ -78,6 +78,21 @@ def test_build_matches_oracle_every_voxel(nat, orc, H, W, tile, K, chunk):
     assert err.max() <= TOL_F32, (err.max(), np.unravel_index(err.argmax(), err.shape))
 
 
+@pytest.mark.parametrize("radii", [[3.0], [1.5, 4.0], [0.4, 2.5, 6.0], [2.0, 2.05, 2.1, 5.5]])
+def test_build_few_shells_matches_oracle(nat, orc, radii):
+    """One to three shells (the shell table and the shell loop read the radii
+    up to two places past the last, which hold +inf), and radii closer than
+    the table's buckets (the shells then counted one by one)."""
+    sc = scenes.cube_scene(2500, seed=31 + len(radii))
+    lights = np.float32([[0, 0, 0], [0.2, 0.3, -0.1]])
+    radii = np.float32(radii)
+    T_ref = orc.build_atlas(sc, lights, 24, 40, radii)
+    T = _build(nat, sc, lights, 24, 40, radii, chunk=32).double().cpu().numpy()
+    err = np.abs(T - T_ref)
+    assert err.max() <= TOL_F32, (err.max(), np.unravel_index(err.argmax(), err.shape))
+    assert (T < 0.999).any()  # the shells hold shadow
+
+
 @pytest.mark.parametrize("dtype,tol", [("f16", TOL_F16), ("bf16", TOL_BF16)])
 def test_build_half_storage(nat, orc, dtype, tol):
     sc = scenes.cube_scene(2000, seed=77)

@@ -687,11 +687,18 @@ __device__ __forceinline__ void fine_count_unit(const Unit &U, unsigned long lon
         const int gl = grp + lane;
         const bool gv = gl < ng;
         __syncwarp();  // the previous group's records are no longer read
-        if (gv) wrec[lane] = rec(l, cvals[U.start + gl]);
-        __syncwarp();
+        // the lane keeps its own record's cone (G.a, G.b) in registers; the
+        // others read the staged copy
         BinRec G;
-        G.a = gv ? wrec[lane].a : make_float4(0.f, 0.f, 1.f, -1.f);
-        G.b = gv ? wrec[lane].b : make_float4(0.f, 0.f, 0.f, 0.f);
+        G.a = make_float4(0.f, 0.f, 1.f, -1.f);
+        G.b = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gv) {
+            const BinRec R = rec(l, cvals[U.start + gl]);
+            wrec[lane] = R;
+            G.a = R.a;
+            G.b = R.b;
+        }
+        __syncwarp();
         const bool inside = G.b.y == 2.0f;
         // quads this Gaussian may reach
         uint32_t qm = 0u;

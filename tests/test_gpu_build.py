@@ -142,6 +142,32 @@ def test_build_stats_are_consistent(nat):
     assert 0 < st["ray_evals"] <= st["rays_tested"] <= 64 * st["n_pairs"]
 
 
+@pytest.mark.parametrize("workload", ["cube", "room_shapes"])
+def test_ray_evals_match_oracle_count(nat, orc, workload):
+    """The throughput metric's unit, the Gaussian-ray evaluations (pairs whose
+    ray cuts the Gaussian's culling ellipsoid ahead of the light), counted by
+    the GPU build equals the oracle's FP64 count over every texel, up to the
+    pairs that sit on the ellipsoid's boundary (float32 against float64
+    decides them; a few in 10^4)."""
+    if workload == "cube":
+        sc = scenes.cube_scene(4000, seed=21)
+        lights = np.float32([[0, 0, 0], [0.4, -0.3, 0.6]])
+    else:
+        rng = np.random.default_rng(22)
+        sc = scenes.cube_scene(3000, seed=23, log_s_mean=math.log(0.08))
+        sc.scales[np.arange(sc.n), rng.integers(0, 3, sc.n)] = 0.002  # 2 mm thick discs
+        lights = np.float32([[0.1, -0.2, 0.3]])
+    H, W = 40, 56
+    radii = scenes.radii_geometric(0.05, 12, 12)
+    _build(nat, sc, lights, H, W, radii)
+    got = nat.dgsm_get_build_stats()["ray_evals"]
+    L = lights.shape[0]
+    lij = np.stack(np.meshgrid(np.arange(L), np.arange(H), np.arange(W), indexing="ij"), -1).reshape(-1, 3)
+    ref = orc.count_ray_evals(sc, lights, H, W, radii, lij)
+    assert ref > 10_000
+    assert abs(got - ref) <= 5e-4 * ref + 2, (got, ref)
+
+
 def test_nonfinite_input_is_reported(nat):
     sc = scenes.cube_scene(100, seed=2)
     sc.means[7, 1] = np.nan

@@ -416,9 +416,10 @@ int dgsm_selftest_wait(dgsm_ctx *ctx, int32_t arrive, int64_t limit, void *strea
  *   status_out: device int or NULL; receives DGSM_OK or DGSM_ERR_NOT_SPD
  *   (then sh_out is zero).
  * The first call on a device looks up the array's device address and keeps
- * it for the rest of the process; make that first call before any stream
- * capture, and do not call this entry point again after destroying the
- * device's context (cudaDeviceReset), whose addresses it would still use.
+ * it with the id of the context it was taken in; a call whose current
+ * context differs (after cudaDeviceReset, for instance) looks it up again.
+ * Make the first call, and the first after a reset, before any stream
+ * capture.
  * An error that earlier work left pending on the calling thread is returned
  * as DGSM_ERR_CUDA without being cleared.  All calls share the one array:
  * calls that overlap on the GPU (on concurrent streams) race and give wrong

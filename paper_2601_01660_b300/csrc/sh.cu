@@ -1,5 +1,7 @@
 // sh.cu -- HDRI probe fit (Sec. 3.4, Eq. 7, FP64) and per-Gaussian radiance
 // transfer (Sec. 3.5, Eqs. 8-10) on sm_103a.
+#include <cuda.h>  // CUcontext, CUresult: two driver functions looked up at run time
+
 #include <algorithm>
 #include <mutex>
 
@@ -287,19 +289,52 @@ static __device__ __align__(256) double dgsm_fit_scratch[FIT_STATIC_DOUBLES];
 namespace {
 std::mutex g_fit_scratch_mu;
 double *g_fit_scratch_ptr[FIT_STATIC_MAX_DEVICES] = {};
+unsigned long long g_fit_scratch_ctx[FIT_STATIC_MAX_DEVICES] = {};
+
+// The id of the calling thread's current context (cuCtxGetId), or 0 when it
+// cannot be read.  The two driver functions are looked up through the
+// runtime, so the library links no driver library.  Call with
+// g_fit_scratch_mu held.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        looked_up = true;
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS)
+        return id;
+    return 0;
+}
 
 // Device address of the static scratch on `dev` (which must be current).  In
 // host code the symbol names a host-side stand-in, so the address is taken
-// once per device with cudaGetSymbolAddress and cached.  The cache outlives
-// nothing but the device's context: after cudaDeviceReset the address is
-// stale, which the header states.
+// with cudaGetSymbolAddress and cached per device together with the id of
+// the context it was taken in; it is taken again when the current context
+// differs (after cudaDeviceReset, say) or its id cannot be read.
 int fit_scratch_address(int dev, double **out) {
     std::lock_guard<std::mutex> lock(g_fit_scratch_mu);
-    if (!g_fit_scratch_ptr[dev]) {
+    const unsigned long long cid = current_context_id();
+    if (!g_fit_scratch_ptr[dev] || cid == 0 || cid != g_fit_scratch_ctx[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, dgsm_fit_scratch) != cudaSuccess || !p)
             return DGSM_ERR_CUDA;
         g_fit_scratch_ptr[dev] = static_cast<double *>(p);
+        // the runtime has made the device's context current by now
+        g_fit_scratch_ctx[dev] = current_context_id();
     }
     *out = g_fit_scratch_ptr[dev];
     return DGSM_OK;
